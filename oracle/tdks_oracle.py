@@ -1,0 +1,456 @@
+"""FP64 CPU oracle of one real-time TDKS step (test infrastructure, not product code).
+
+Only the tests, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` / ``--impl reference``
+legs of ``bench.py`` may import or run this module.  It shares no code with the CUDA path:
+it reads plain system descriptions (grid, atoms, projectors, k-points, orbitals) and
+recomputes everything from the paper's equations with numpy in float64/complex128.
+
+What it computes (Hartree atomic units, hbar = m = e = 1, A' = A/c):
+
+* Sec. 4.1, Eq. (TDKS_solid): Bloch orbitals w_nk evolve under
+  H_q = 1/2 (-i grad + q)^2 + V_loc + V_NL^q + V_H + V_xc with q = k + A'(t).
+  Isolated systems (Sec. 3.1, Eq. TDKS) are the case q = 0 with zero boundary.
+  The gradient is discretised with 8th-order central differences (4 neighbours per side per
+  axis, the 25-point Laplacian), so 1/2(-i grad+q)^2 -> -1/2 sum_a D2_a - i q.D1 + |q|^2/2.
+* Sec. 3.1: V_ion is a local part plus Kleinman-Bylander separable projectors,
+  V_NL = sum E |beta><beta|; Sec. 4.1 notes the nonlocal part follows the vector potential to
+  keep gauge invariance, which in Bloch form gives projectors beta(r) exp(-i q.(r - R_a)).
+* Program summary / Sec. 1: the evolution operator is a truncated Taylor expansion (4th
+  order here) with a predictor-corrector step for the self-consistent potential.
+* Eq. (rho): rho = 2 sum_p |psi_p|^2 (spin saturated), with k-weights for Bloch orbitals.
+* Eq. (TDKS): Hartree potential e^2 int rho(r')/|r-r'|; periodic cells solve it in G-space,
+  isolated boxes with a zero-padded (Hockney) convolution.
+* Sec. 3.1 LDA: adiabatic local exchange (Slater exchange only in this build).
+* Sec. 3.1: dipole d = -int r (rho - rho0); Eq. (distribution): oscillator-strength spectrum.
+* Eq. (macro_current): macroscopic current including the nonlocal term.
+* Eq. (pulse), Eq. (impulsive_A): fields.
+* Eq. (Maxwell_ms): 1D wave equation driven by the cell currents.
+
+Readings where the paper is silent (stencil order, Taylor order, predictor-corrector form,
+projector shapes, Hockney self-term, kick on a periodic cell ...) are listed in the design
+notes; each is restated at the function that uses it.
+
+Parity status: every function here is pinned by the CPU tests against closed forms, brute
+force or invariants (plane-wave dispersion, dense eigendecomposition, Hockney direct sum,
+Gaussian/cosine charges, J = -dE/dA'/Omega, energy conservation, f-sum slope).  The full
+predictor-corrector step has no closed form: it is pinned only through those invariants.
+"""
+from __future__ import annotations
+
+import math
+import numpy as np
+
+C_LIGHT = 137.035999084
+
+# 8th-order central differences (4 neighbours per side).  Second derivative:
+# f'' ~ (1/h^2)[c0 f(0) + sum_m c_m (f(m) + f(-m))]; first derivative: f' ~ (1/h) sum_m d_m (f(m) - f(-m)).
+FD2 = (-205.0 / 72.0, 8.0 / 5.0, -1.0 / 5.0, 8.0 / 315.0, -1.0 / 560.0)
+FD1 = (4.0 / 5.0, -1.0 / 5.0, 4.0 / 105.0, -1.0 / 280.0)
+
+# numpy axis of each Cartesian direction for arrays laid out [..., z, y, x]
+_AX = {0: -1, 1: -2, 2: -3}
+
+
+# --------------------------------------------------------------------------------------------
+# grid
+# --------------------------------------------------------------------------------------------
+def coords(s):
+    """1D coordinate arrays (x, y, z).  Periodic: r_j = j h on [0, L).
+    Isolated: centred, r_j = (j - (n-1)/2) h (Sec. 2.1 cuboid with vacuum outside)."""
+    out = []
+    for a in range(3):
+        j = np.arange(s.n[a], dtype=np.float64)
+        out.append(j * s.h[a] if s.periodic else (j - (s.n[a] - 1) / 2.0) * s.h[a])
+    return out
+
+
+def cell_volume(s):
+    return float(np.prod([s.n[a] * s.h[a] for a in range(3)]))
+
+
+def shifted(u, m, a, periodic):
+    """Array whose value at grid index j along axis a is u at j + m (periodic wrap, or zero
+    outside the box for isolated systems)."""
+    ax = _AX[a]
+    if periodic:
+        return np.roll(u, -m, axis=ax)
+    out = np.zeros_like(u)
+    n = u.shape[ax]
+    src = [slice(None)] * u.ndim
+    dst = [slice(None)] * u.ndim
+    if m >= 0:
+        src[ax], dst[ax] = slice(m, n), slice(0, n - m)
+    else:
+        src[ax], dst[ax] = slice(0, n + m), slice(-m, n)
+    out[tuple(dst)] = u[tuple(src)]
+    return out
+
+
+def d2(u, a, s):
+    r = FD2[0] * u
+    for m in range(1, 5):
+        r = r + FD2[m] * (shifted(u, m, a, s.periodic) + shifted(u, -m, a, s.periodic))
+    return r / (s.h[a] ** 2)
+
+
+def d1(u, a, s):
+    r = np.zeros_like(u)
+    for m in range(1, 5):
+        r = r + FD1[m - 1] * (shifted(u, m, a, s.periodic) - shifted(u, -m, a, s.periodic))
+    return r / s.h[a]
+
+
+# --------------------------------------------------------------------------------------------
+# ionic potential (Sec. 3.1: local part + Kleinman-Bylander separable part)
+# --------------------------------------------------------------------------------------------
+def local_potential(s):
+    """V_loc on the grid [nz, ny, nx] for pseudo-atoms V_a(r) = -Z erf(|r-R|/sigma)/|r-R|.
+
+    Periodic: the lattice sum in G-space over the grid's reciprocal vectors, G != 0 only
+    (uniform neutralising background; the G=0 constant only shifts orbital phases):
+      V(G) = (1/Omega) sum_a (-4 pi Z_a / G^2) exp(-G^2 sigma_a^2 / 4) exp(-i G.R_a),
+      V(r) = Re sum_G V(G) exp(i G.r).
+    Isolated: the direct sum, with the r -> R limit -2Z/(sigma sqrt(pi))."""
+    x, y, z = coords(s)
+    if s.periodic:
+        g = [2.0 * np.pi * np.fft.fftfreq(s.n[a], d=s.h[a]) for a in range(3)]
+        GX, GY, GZ = g[0][None, None, :], g[1][None, :, None], g[2][:, None, None]
+        G2 = GX ** 2 + GY ** 2 + GZ ** 2
+        G2s = np.where(G2 == 0.0, 1.0, G2)
+        Vg = np.zeros(G2.shape, np.complex128)
+        for at in s.atoms:
+            R = at.R
+            Vg += (-4.0 * np.pi * at.Z / G2s) * np.exp(-G2 * at.sigma ** 2 / 4.0) * \
+                np.exp(-1j * (GX * R[0] + GY * R[1] + GZ * R[2]))
+        Vg[G2 == 0.0] = 0.0
+        Vg /= cell_volume(s)
+        return np.real(np.fft.ifftn(Vg) * G2.size)
+    Z3, Y3, X3 = np.meshgrid(z, y, x, indexing="ij")
+    V = np.zeros((s.n[2], s.n[1], s.n[0]))
+    for at in s.atoms:
+        d = np.sqrt((X3 - at.R[0]) ** 2 + (Y3 - at.R[1]) ** 2 + (Z3 - at.R[2]) ** 2)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            v = -at.Z * _erf(d / at.sigma) / d
+        v[d == 0.0] = -2.0 * at.Z / (at.sigma * math.sqrt(math.pi))
+        V += v
+    return V
+
+
+def _erf(x):
+    from scipy.special import erf
+    return erf(x)
+
+
+def projector_tables(s):
+    """Kleinman-Bylander projector tables, one dict per atom.
+
+    Channels s, px, py, pz with energies (E_s, E_p, E_p, E_p).  Shapes on the grid points
+    within r_cut of the atom (minimum image for periodic cells; isolated: points in the box):
+      g(d) = exp(-d^2 / (2 w^2)) (1 - d^2/r_cut^2)^2,  beta = N {1, dx, dy, dz} g(d),
+    each normalised on the grid so that sum beta^2 dV = 1.  d is the displacement r - R_a of the
+    nearest image, used for the gauge phase exp(i q.d)."""
+    x, y, z = coords(s)
+    L = [s.n[a] * s.h[a] for a in range(3)]
+    if s.periodic and s.proj.r_cut >= 0.5 * min(L):
+        raise ValueError("projector sphere larger than half the cell")
+    tabs = []
+    for at in s.atoms:
+        comps = []
+        for a, c in enumerate((x, y, z)):
+            dd = c - at.R[a]
+            if s.periodic:
+                dd = dd - L[a] * np.round(dd / L[a])
+            comps.append(dd)
+        DX, DY, DZ = comps[0][None, None, :], comps[1][None, :, None], comps[2][:, None, None]
+        D2 = DX ** 2 + DY ** 2 + DZ ** 2
+        inside = D2 < s.proj.r_cut ** 2
+        iz, iy, ix = np.nonzero(inside)
+        idx = (iz * s.n[1] + iy) * s.n[0] + ix
+        d = np.stack([comps[0][ix], comps[1][iy], comps[2][iz]], axis=1)
+        r2 = (d ** 2).sum(axis=1)
+        g = np.exp(-r2 / (2.0 * s.proj.width ** 2)) * (1.0 - r2 / s.proj.r_cut ** 2) ** 2
+        beta = np.stack([g, d[:, 0] * g, d[:, 1] * g, d[:, 2] * g])
+        beta /= np.sqrt((beta ** 2).sum(axis=1, keepdims=True) * s.dV)
+        E = np.array([s.proj.E_s, s.proj.E_p, s.proj.E_p, s.proj.E_p])
+        tabs.append(dict(idx=idx, d=d, beta=beta, E=E))
+    return tabs
+
+
+def projections(s, tabs, q, u, weight_by=None):
+    """c[..., a, p] = sum_{r in S_a} beta_ap(r) exp(i q.d) u(r) dV for a batch u[..., nz, ny, nx].
+    weight_by = axis index b multiplies the sum by d_b (the b_ap moments of the current)."""
+    flat = u.reshape(u.shape[:-3] + (-1,))
+    out = np.zeros(u.shape[:-3] + (len(tabs), 4), np.complex128)
+    for ia, t in enumerate(tabs):
+        ph = np.exp(1j * (t["d"] @ np.asarray(q, dtype=np.float64)))
+        w = ph if weight_by is None else ph * t["d"][:, weight_by]
+        out[..., ia, :] = (flat[..., t["idx"]] * w) @ t["beta"].T * s.dV
+    return out
+
+
+def apply_nonlocal(s, tabs, q, u):
+    """V_NL^q u = sum_ap E_p beta_ap(r) exp(-i q.d) c_ap  (Sec. 3.1 KB form, Sec. 4.1 gauge)."""
+    c = projections(s, tabs, q, u)
+    out = np.zeros(u.shape[:-3] + (u.shape[-3] * u.shape[-2] * u.shape[-1],), np.complex128)
+    for ia, t in enumerate(tabs):
+        ph = np.exp(-1j * (t["d"] @ np.asarray(q, dtype=np.float64)))
+        contrib = ((c[..., ia, :] * t["E"]) @ t["beta"]) * ph
+        out[..., t["idx"]] += contrib        # indices are unique within one atom
+    return out.reshape(u.shape)
+
+
+# --------------------------------------------------------------------------------------------
+# Hamiltonian (Eq. TDKS_solid in Bloch form; Eq. TDKS for isolated, q = 0)
+# --------------------------------------------------------------------------------------------
+def hpsi(s, tabs, V, q, u):
+    """H_q u for a batch u[..., nz, ny, nx] sharing the same q = k + A'.
+    H_q = -1/2 sum_a D2_a - i sum_a q_a D1_a + |q|^2/2 + V(r) + V_NL^q."""
+    q = np.asarray(q, dtype=np.float64)
+    out = np.zeros_like(u)
+    for a in range(3):
+        out += -0.5 * d2(u, a, s)
+        if q[a] != 0.0:
+            out += -1j * q[a] * d1(u, a, s)
+    out += (0.5 * float(q @ q) + V) * u
+    out += apply_nonlocal(s, tabs, q, u)
+    return out
+
+
+def taylor4(s, tabs, V, q, u, dt, order=4):
+    """Truncated Taylor expansion of exp(-i H dt) applied to u: sum_{n<=order} (-i dt H)^n u / n!
+    (Program summary: explicit integration by a truncated Taylor expansion; order 4 here)."""
+    term = u.copy()
+    acc = u.copy()
+    for n in range(1, order + 1):
+        term = (-1j * dt / n) * hpsi(s, tabs, V, q, term)
+        acc = acc + term
+    return acc
+
+
+# --------------------------------------------------------------------------------------------
+# density, Hartree, exchange (Eq. rho, Eq. TDKS, LDA)
+# --------------------------------------------------------------------------------------------
+def density(s, psi):
+    """rho(r) = sum_k w_k sum_n 2 |u_nk(r)|^2 for psi[nk, norb, nz, ny, nx] (Eq. rho)."""
+    return 2.0 * np.einsum("k,kn...->...", np.asarray(s.kw, np.float64), np.abs(psi) ** 2)
+
+
+def box_self_integral(ax, ay, az):
+    """Integral of 1/|r| over the box [0,ax]x[0,ay]x[0,az] (closed form of the Newton potential
+    of a uniform box at its corner)."""
+    a, b, c = ax, ay, az
+    d = math.sqrt(a * a + b * b + c * c)
+    return (a * b * math.log((c + d) / math.hypot(a, b)) + b * c * math.log((a + d) / math.hypot(b, c))
+            + c * a * math.log((b + d) / math.hypot(c, a))
+            - 0.5 * a * a * math.atan(b * c / (a * d)) - 0.5 * b * b * math.atan(c * a / (b * d))
+            - 0.5 * c * c * math.atan(a * b / (c * d)))
+
+
+def hockney_kernel(s):
+    """Green's function 1/|r| on the (2n)^3 zero-padding grid.  Index m maps to the distance
+    m h for m <= n and (2n - m) h above.  The r = 0 cell takes the mean of 1/|r| over one grid
+    cell: g(0) = 8 * box_self_integral(h/2) / dV."""
+    comps = []
+    for a in range(3):
+        m = np.arange(2 * s.n[a])
+        comps.append(np.where(m <= s.n[a], m, 2 * s.n[a] - m) * s.h[a])
+    X, Y, Z = comps[0][None, None, :], comps[1][None, :, None], comps[2][:, None, None]
+    r = np.sqrt(X ** 2 + Y ** 2 + Z ** 2)
+    with np.errstate(divide="ignore"):
+        g = 1.0 / r
+    g[0, 0, 0] = 8.0 * box_self_integral(s.h[0] / 2, s.h[1] / 2, s.h[2] / 2) / s.dV
+    return g
+
+
+def hartree(s, rho):
+    """V_H = int rho(r')/|r - r'| (Eq. TDKS, e = 1).
+    Periodic: V_H(G) = 4 pi rho(G) / G^2, V_H(G=0) = 0.
+    Isolated: V_H(r_i) = dV sum_j g(r_i - r_j) rho_j, evaluated by FFT on the zero-padded grid."""
+    if s.periodic:
+        g = [2.0 * np.pi * np.fft.fftfreq(s.n[a], d=s.h[a]) for a in range(3)]
+        G2 = g[0][None, None, :] ** 2 + g[1][None, :, None] ** 2 + g[2][:, None, None] ** 2
+        rg = np.fft.fftn(rho)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            vg = np.where(G2 == 0.0, 0.0, 4.0 * np.pi * rg / np.where(G2 == 0.0, 1.0, G2))
+        return np.real(np.fft.ifftn(vg))
+    nz, ny, nx = rho.shape
+    pad = np.zeros((2 * nz, 2 * ny, 2 * nx))
+    pad[:nz, :ny, :nx] = rho
+    conv = np.fft.ifftn(np.fft.fftn(pad) * np.fft.fftn(hockney_kernel(s)))
+    return np.real(conv[:nz, :ny, :nx]) * s.dV
+
+
+def lda_x(rho):
+    """Slater exchange (spin-unpolarised LDA exchange):
+    eps_x = -(3/4) (3 rho / pi)^(1/3),  V_x = d(rho eps_x)/d rho = -(3 rho / pi)^(1/3)."""
+    r = np.maximum(rho, 0.0)
+    vx = -np.cbrt(3.0 * r / np.pi)
+    return vx, 0.75 * vx
+
+
+def hxc(s, rho, hartree_on=True, xc_on=True):
+    v = np.zeros_like(rho)
+    if hartree_on:
+        v = v + hartree(s, rho)
+    if xc_on:
+        v = v + lda_x(rho)[0]
+    return v
+
+
+# --------------------------------------------------------------------------------------------
+# fields (Eq. pulse, Eq. impulsive_A)
+# --------------------------------------------------------------------------------------------
+def field_Aprime(f, t):
+    """A'(t) = A(t)/c as a 3-vector."""
+    A0 = np.asarray(f.A0, np.float64)
+    if f.kind == "none":
+        return np.zeros(3)
+    if f.kind == "step":
+        return A0.copy() if t > 0.0 else np.zeros(3)
+    if f.kind == "pulse":
+        if not (0.0 < t < f.T):
+            return np.zeros(3)
+        env = math.cos(math.pi * (t - f.T / 2.0) / f.T) ** 2
+        ph = -f.omega * (t - f.T / 2.0) - 2.0 * math.pi * f.cep
+        return A0 * env * math.sin(ph)      # Im{A0 env e^{i ph}} for real A0
+    raise ValueError(f.kind)
+
+
+# --------------------------------------------------------------------------------------------
+# observables (Eq. macro_current, dipole, energy)
+# --------------------------------------------------------------------------------------------
+def current(s, tabs, psi, Ap):
+    """Macroscopic current density (Eq. macro_current, e = m = 1):
+    J_a = -(1/Omega) sum_k w_k sum_n 2 [ Re sum_r u^* (-i D1_a + q_a) u dV
+                                        + sum_{atom,p} 2 E_p Im(conj(b_ap^(a)) c_ap) ],
+    q = k + A'; c_ap = <p^q|u>, b_ap^(a) the same moment weighted by d_a.  The second term is
+    <u| dV_NL^q / dq_a |u>, the nonlocal current."""
+    J = np.zeros(3)
+    for ik in range(s.nk):
+        q = np.asarray(s.kpts[ik], np.float64) + np.asarray(Ap, np.float64)
+        u = psi[ik]
+        c = projections(s, tabs, q, u)
+        for a in range(3):
+            loc = np.real(np.sum(np.conj(u) * (-1j * d1(u, a, s) + q[a] * u))) * s.dV
+            b = projections(s, tabs, q, u, weight_by=a)
+            nl = np.sum(2.0 * np.array([t["E"] for t in tabs])[None] * np.imag(np.conj(b) * c))
+            J[a] += s.kw[ik] * 2.0 * (loc + nl)
+    return -J / cell_volume(s)
+
+
+def dipole(s, rho, rho0):
+    """d_mu = -int r_mu (rho - rho0) dr (Sec. 3.1, e = 1)."""
+    x, y, z = coords(s)
+    dr = rho - rho0
+    return -np.array([np.sum(dr * x[None, None, :]), np.sum(dr * y[None, :, None]),
+                      np.sum(dr * z[:, None, None])]) * s.dV
+
+
+def band_energy(s, tabs, Vloc, psi, Ap):
+    """sum_k w_k sum_n 2 <u| T_q + V_loc + V_NL^q |u>."""
+    e = 0.0
+    for ik in range(s.nk):
+        q = np.asarray(s.kpts[ik], np.float64) + np.asarray(Ap, np.float64)
+        hu = hpsi(s, tabs, Vloc, q, psi[ik])
+        e += s.kw[ik] * 2.0 * np.real(np.sum(np.conj(psi[ik]) * hu)) * s.dV
+    return e
+
+
+def total_energy(s, tabs, Vloc, psi, Ap, hartree_on=True, xc_on=True):
+    """E = band energy + 1/2 int rho V_H + int rho eps_x."""
+    rho = density(s, psi)
+    e = band_energy(s, tabs, Vloc, psi, Ap)
+    if hartree_on:
+        e += 0.5 * np.sum(rho * hartree(s, rho)) * s.dV
+    if xc_on:
+        e += np.sum(rho * lda_x(rho)[1]) * s.dV
+    return e
+
+
+def norms(s, psi):
+    return (np.abs(psi) ** 2).sum(axis=(-3, -2, -1)) * s.dV
+
+
+# --------------------------------------------------------------------------------------------
+# time step (Taylor + predictor-corrector)
+# --------------------------------------------------------------------------------------------
+def propagate_all(s, tabs, V, psi, Ap, dt):
+    out = np.empty_like(psi)
+    for ik in range(s.nk):
+        q = np.asarray(s.kpts[ik], np.float64) + np.asarray(Ap, np.float64)
+        out[ik] = taylor4(s, tabs, V, q, psi[ik], dt)
+    return out
+
+
+def pc_step(s, tabs, Vloc, psi, vhxc, t, dt, pc=True, hartree_on=True, xc_on=True):
+    """One step t -> t + dt.
+
+    Predictor: psi~ = T4[V_loc + V_Hxc(t)] psi(t); V~ = V_Hxc[rho(psi~)].
+    Corrector: psi(t+dt) = T4[V_loc + (V_Hxc(t) + V~)/2] psi(t); V_Hxc(t+dt) = V_Hxc[rho(t+dt)].
+    Both stages use A'(t + dt/2).  With pc=False the step is T4[V_loc + V_Hxc(t)] alone.
+    Returns (psi(t+dt), V_Hxc(t+dt), rho(t+dt))."""
+    Ap = field_Aprime(s.field, t + 0.5 * dt) if s.periodic else np.zeros(3)
+    vmid = vhxc
+    if pc:
+        pred = propagate_all(s, tabs, Vloc + vhxc, psi, Ap, dt)
+        vpred = hxc(s, density(s, pred), hartree_on, xc_on)
+        vmid = 0.5 * (vhxc + vpred)
+    new = propagate_all(s, tabs, Vloc + vmid, psi, Ap, dt)
+    rho = density(s, new)
+    return new, hxc(s, rho, hartree_on, xc_on), rho
+
+
+def apply_kick(s, psi, kappa):
+    """Isolated impulse (Sec. 3.1): psi(0+) = exp(i kappa . r) phi."""
+    x, y, z = coords(s)
+    ph = np.exp(1j * (kappa[0] * x[None, None, :] + kappa[1] * y[None, :, None]
+                      + kappa[2] * z[:, None, None]))
+    return psi * ph
+
+
+def run(s, psi0, nsteps, pc=True, hartree_on=True, xc_on=True, record=True):
+    """Propagate nsteps; returns final psi and per-step observables (t, J, dipole)."""
+    tabs = projector_tables(s)
+    Vloc = local_potential(s)
+    psi = psi0.copy()
+    rho0 = density(s, psi)
+    vhxc = hxc(s, rho0, hartree_on, xc_on)
+    hist = dict(t=[], J=[], d=[])
+    t = 0.0
+    for _ in range(nsteps):
+        psi, vhxc, rho = pc_step(s, tabs, Vloc, psi, vhxc, t, s.dt, pc, hartree_on, xc_on)
+        t += s.dt
+        if record:
+            hist["t"].append(t)
+            Ap = field_Aprime(s.field, t) if s.periodic else np.zeros(3)
+            hist["J"].append(current(s, tabs, psi, Ap) if s.periodic else np.zeros(3))
+            hist["d"].append(dipole(s, rho, rho0))
+    return psi, vhxc, {k: np.array(v) for k, v in hist.items()}
+
+
+# --------------------------------------------------------------------------------------------
+# analysis: Eq. (distribution), Eq. (Maxwell_ms)
+# --------------------------------------------------------------------------------------------
+def oscillator_strength(t, d, kappa, energies):
+    """df/dE = -(2E/(pi kappa)) Im int_0^T f(t/T) d(t) exp(iEt) dt, f(x) = 1 - 3x^2 + 2x^3.
+    The kick exp(i kappa z) corresponds to F0 = -kappa in Eq. (distribution); the sign makes the
+    spectrum positive and its integral the electron count (f-sum)."""
+    t = np.asarray(t, np.float64)
+    d = np.asarray(d, np.float64)
+    T = t[-1]
+    dt = t[1] - t[0]
+    x = t / T
+    f = 1.0 - 3.0 * x ** 2 + 2.0 * x ** 3
+    E = np.asarray(energies, np.float64)
+    integ = (f * d)[None, :] * np.exp(1j * E[:, None] * t[None, :])
+    return -(2.0 * E / (np.pi * kappa)) * np.imag(integ.sum(axis=1) * dt)
+
+
+def maxwell_step(A_now, A_prev, I, c_dt_dX, dt, c=C_LIGHT):
+    """Leapfrog update of Eq. (Maxwell_ms), (1/c^2) A_tt - A_XX = (4 pi / c) I, interior points:
+    A^{n+1}_X = 2A^n_X - A^{n-1}_X + (c dt/dX)^2 (A_{X+1} - 2A_X + A_{X-1}) + 4 pi c dt^2 I_X.
+    End points are held (the caller supplies its own boundary)."""
+    A_next = A_now.copy()
+    lap = A_now[2:] - 2.0 * A_now[1:-1] + A_now[:-2]
+    A_next[1:-1] = 2.0 * A_now[1:-1] - A_prev[1:-1] + c_dt_dX ** 2 * lap + 4.0 * np.pi * c * dt * dt * I[1:-1]
+    return A_next

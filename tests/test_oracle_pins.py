@@ -1,0 +1,458 @@
+"""Pins of the FP64 oracle against closed forms, brute force and invariants (CPU only).
+
+Each test names the part of the oracle it pins and the mistake it would catch.
+"""
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from oracle import tdks_oracle as O
+from paper_1804_01404_gb300 import workloads as W
+
+
+def _no_atoms(s):
+    s.atoms = []
+    return s
+
+
+# ---------------------------------------------------------------- finite-difference stencil
+def test_fd_coefficients_exact_on_polynomials():
+    """8th-order stencils: D2 exact on polynomials of degree <= 9, D1 on degree <= 8 (exact rational arithmetic):
+    a wrong coefficient or sign fails here."""
+    c = [Fraction(-205, 72), Fraction(8, 5), Fraction(-1, 5), Fraction(8, 315), Fraction(-1, 560)]
+    d = [Fraction(4, 5), Fraction(-1, 5), Fraction(4, 105), Fraction(-1, 280)]
+    assert all(abs(float(x) - y) < 1e-16 for x, y in zip(c, O.FD2))
+    assert all(abs(float(x) - y) < 1e-16 for x, y in zip(d, O.FD1))
+    x0 = Fraction(3, 7)
+    for p in range(10):
+        f = lambda x: x ** p
+        dd = c[0] * f(x0) + sum(c[m] * (f(x0 + m) + f(x0 - m)) for m in range(1, 5))
+        exact2 = p * (p - 1) * x0 ** (p - 2) if p >= 2 else 0
+        assert dd == exact2, p
+        d1 = sum(d[m - 1] * (f(x0 + m) - f(x0 - m)) for m in range(1, 5))
+        exact1 = p * x0 ** (p - 1) if p >= 1 else 0
+        assert (d1 == exact1) == (p <= 8), p       # D1 is exact up to degree 8, not 9
+
+
+def test_plane_wave_dispersion():
+    """Periodic, V = 0, no projectors: plane waves exp(iG.r) are eigenvectors of H_q with the
+    closed-form eigenvalue of the 25-point stencil plus the q.D1 and |q|^2/2 terms."""
+    s = _no_atoms(W.tiny(periodic=True, n=(8, 10, 12)))
+    x, y, z = O.coords(s)
+    q = np.array([0.31, -0.17, 0.23])
+    V = np.zeros((12, 10, 8))
+    rng = np.random.default_rng(3)
+    for _ in range(6):
+        m = [int(rng.integers(-s.n[a] // 2 + 1, s.n[a] // 2)) for a in range(3)]
+        G = [2 * np.pi * m[a] / (s.n[a] * s.h[a]) for a in range(3)]
+        u = np.exp(1j * (G[0] * x[None, None, :] + G[1] * y[None, :, None] + G[2] * z[:, None, None]))
+        lam = 0.5 * q @ q
+        for a in range(3):
+            h = s.h[a]
+            lam += -(0.5 / h ** 2) * (O.FD2[0] + 2 * sum(O.FD2[k] * math.cos(k * G[a] * h) for k in range(1, 5)))
+            lam += q[a] * (2.0 / h) * sum(O.FD1[k - 1] * math.sin(k * G[a] * h) for k in range(1, 5))
+        hu = O.hpsi(s, [], V, q, u)
+        assert np.max(np.abs(hu - lam * u)) < 1e-12 * max(1.0, abs(lam))
+        # and it approaches the continuum value 1/2|G+q|^2 for a smooth wave
+    m = (1, 0, 0)
+    G = 2 * np.pi / (s.n[0] * s.h[0])
+    u = np.exp(1j * G * x)[None, None, :] * np.ones((12, 10, 1))
+    hu = O.hpsi(s, [], V, q, u)
+    cont = 0.5 * ((G + q[0]) ** 2 + q[1] ** 2 + q[2] ** 2)
+    assert abs((hu / u).real.mean() - cont) < 1e-4 * cont
+
+
+def _loop_kinetic_isolated(s, u, V):
+    """Explicit-loop kinetic + local operator with zero boundary (independent of the numpy shifts)."""
+    nx, ny, nz = s.n
+    out = np.zeros_like(u)
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                acc = 0j
+                for a, (idx, n) in enumerate(((i, nx), (j, ny), (k, nz))):
+                    h = s.h[a]
+                    tot = O.FD2[0] * u[k, j, i]
+                    for m in range(1, 5):
+                        for sgn in (1, -1):
+                            p = [i, j, k]
+                            p[a] = idx + sgn * m
+                            if 0 <= p[a] < n:
+                                tot += O.FD2[m] * u[p[2], p[1], p[0]]
+                    acc += -0.5 * tot / h ** 2
+                out[k, j, i] = acc + V[k, j, i] * u[k, j, i]
+    return out
+
+
+def test_isolated_stencil_against_loops():
+    s = _no_atoms(W.tiny(periodic=False, n=(7, 9, 6)))
+    rng = np.random.default_rng(5)
+    u = rng.standard_normal((6, 9, 7)) + 1j * rng.standard_normal((6, 9, 7))
+    V = rng.standard_normal((6, 9, 7))
+    ref = _loop_kinetic_isolated(s, u, V)
+    got = O.hpsi(s, [], V, np.zeros(3), u)
+    assert np.max(np.abs(got - ref)) < 1e-12
+
+
+# ---------------------------------------------------------------- projectors
+def _dense_nonlocal(s, q):
+    """V_NL as a dense matrix, built point by point from its definition with explicit loops
+    (minimum image, normalisation, gauge phase) -- independent of the gather/scatter code."""
+    x, y, z = O.coords(s)
+    L = [s.n[a] * s.h[a] for a in range(3)]
+    N = s.npts
+    M = np.zeros((N, N), np.complex128)
+    E = [s.proj.E_s, s.proj.E_p, s.proj.E_p, s.proj.E_p]
+    for at in s.atoms:
+        P = np.zeros((4, N), np.complex128)
+        for k in range(s.n[2]):
+            for j in range(s.n[1]):
+                for i in range(s.n[0]):
+                    d = np.array([x[i] - at.R[0], y[j] - at.R[1], z[k] - at.R[2]])
+                    if s.periodic:
+                        d = np.array([d[a] - L[a] * round(d[a] / L[a]) for a in range(3)])
+                    r2 = float(d @ d)
+                    if r2 >= s.proj.r_cut ** 2:
+                        continue
+                    g = math.exp(-r2 / (2 * s.proj.width ** 2)) * (1 - r2 / s.proj.r_cut ** 2) ** 2
+                    p = (k * s.n[1] + j) * s.n[0] + i
+                    P[:, p] = np.array([g, d[0] * g, d[1] * g, d[2] * g]) * np.exp(-1j * (q @ d))
+        for c in range(4):
+            nrm = np.sum(np.abs(P[c]) ** 2) * s.dV
+            M += E[c] * np.outer(P[c], P[c].conj()) / nrm * s.dV
+    return M
+
+
+@pytest.mark.parametrize("periodic", [True, False])
+def test_nonlocal_against_dense_definition(periodic):
+    s = W.tiny(periodic=periodic, n=(6, 7, 5), natom=2)
+    q = np.array([0.4, -0.3, 0.25]) if periodic else np.zeros(3)
+    tabs = O.projector_tables(s)
+    for t in tabs:
+        assert np.allclose((t["beta"] ** 2).sum(axis=1) * s.dV, 1.0)
+    M = _dense_nonlocal(s, q)
+    rng = np.random.default_rng(7)
+    u = rng.standard_normal((5, 7, 6)) + 1j * rng.standard_normal((5, 7, 6))
+    got = O.apply_nonlocal(s, tabs, q, u)
+    assert np.max(np.abs(got.ravel() - M @ u.ravel())) < 1e-12 * np.max(np.abs(got))
+    assert np.allclose(M, M.conj().T, atol=1e-14)
+
+
+def test_nonlocal_bloch_supercell_identity():
+    """psi = exp(ik.r) w on a doubled cell is a Gamma function; the supercell's V_NL (q = 0)
+    acting on psi equals exp(ik.r) V_NL^{q=k} w of the primitive cell (gauge phase + minimum image)."""
+    s = W.tiny(periodic=True, n=(6, 6, 6), natom=1)
+    Lx = s.n[0] * s.h[0]
+    k = np.array([np.pi / Lx, 0.0, 0.0])
+    sup = W.tiny(periodic=True, n=(12, 6, 6), natom=1)
+    sup.h = s.h
+    sup.atoms = [s.atoms[0], W.Atom((s.atoms[0].R[0] + Lx, s.atoms[0].R[1], s.atoms[0].R[2]), 2.0, 0.7)]
+    rng = np.random.default_rng(2)
+    w = rng.standard_normal((6, 6, 6)) + 1j * rng.standard_normal((6, 6, 6))
+    x2 = O.coords(sup)[0]
+    ph = np.exp(1j * k[0] * x2)[None, None, :]
+    psi = np.concatenate([w, w], axis=2) * ph
+    lhs = O.apply_nonlocal(sup, O.projector_tables(sup), np.zeros(3), psi)
+    rw = O.apply_nonlocal(s, O.projector_tables(s), k, w)
+    rhs = np.concatenate([rw, rw], axis=2) * ph
+    assert np.max(np.abs(lhs - rhs)) < 1e-12 * np.max(np.abs(lhs))
+
+
+# ---------------------------------------------------------------- Taylor propagator
+def _dense_H(s, tabs, V, q):
+    N = s.npts
+    H = np.zeros((N, N), np.complex128)
+    for j in range(N):
+        e = np.zeros(N, np.complex128)
+        e[j] = 1.0
+        H[:, j] = O.hpsi(s, tabs, V, q, e.reshape(s.n[2], s.n[1], s.n[0])).ravel()
+    return H
+
+
+@pytest.mark.parametrize("periodic", [True, False])
+def test_taylor_against_dense_exponential(periodic):
+    """6^3 grid, frozen V: T4 u against exp(-iH dt) u from a dense eigendecomposition.  The error
+    must equal the closed form sum_j |a_j|^2 |T4(x_j) - exp(-i x_j)|^2 (x_j = E_j dt), and scale
+    as dt^5 (propagator) and dt^6 (norm defect)."""
+    s = W.tiny(periodic=periodic, n=(6, 6, 6), natom=1)
+    tabs = O.projector_tables(s)
+    V = O.local_potential(s)
+    q = np.array([0.2, 0.1, -0.3]) if periodic else np.zeros(3)
+    H = _dense_H(s, tabs, V, q)
+    assert np.max(np.abs(H - H.conj().T)) < 1e-11 * np.max(np.abs(H))
+    E, U = np.linalg.eigh(H)
+    rng = np.random.default_rng(11)
+    u = rng.standard_normal(s.npts) + 1j * rng.standard_normal(s.npts)
+    a = U.conj().T @ u
+    errs, defects = [], []
+    dts = [0.04, 0.02, 0.01, 0.005]
+    for dt in dts:
+        t4 = O.taylor4(s, tabs, V, q, u.reshape(6, 6, 6), dt).ravel()
+        exact = U @ (np.exp(-1j * E * dt) * a)
+        x = E * dt
+        T4x = sum((-1j * x) ** n / math.factorial(n) for n in range(5))
+        closed = np.sqrt(np.sum(np.abs(a) ** 2 * np.abs(T4x - np.exp(-1j * x)) ** 2))
+        err = np.linalg.norm(t4 - exact)
+        assert abs(err - closed) < 1e-9 * closed + 1e-13
+        errs.append(err)
+        defects.append(abs(np.linalg.norm(u) ** 2 - np.linalg.norm(t4) ** 2))
+    s5 = np.polyfit(np.log(dts), np.log(errs), 1)[0]
+    s6 = np.polyfit(np.log(dts), np.log(defects), 1)[0]
+    assert 4.8 < s5 < 5.2, s5
+    assert 5.8 < s6 < 6.2, s6
+
+
+# ---------------------------------------------------------------- Hartree, exchange
+def test_periodic_hartree_cosine_closed_form():
+    s = _no_atoms(W.tiny(periodic=True, n=(8, 10, 12)))
+    x, y, z = O.coords(s)
+    G = np.array([2 * np.pi * 2 / (8 * s.h[0]), 2 * np.pi * 1 / (10 * s.h[1]), -2 * np.pi * 3 / (12 * s.h[2])])
+    phase = G[0] * x[None, None, :] + G[1] * y[None, :, None] + G[2] * z[:, None, None]
+    rho = 0.7 + np.cos(phase)
+    vh = O.hartree(s, rho)
+    assert np.max(np.abs(vh - 4 * np.pi * np.cos(phase) / (G @ G))) < 1e-12
+
+
+def test_periodic_hartree_laplacian():
+    """-FD Laplacian of V_H = 4 pi (rho - <rho>) on a smooth periodic density (to FD accuracy)."""
+    s = _no_atoms(W.tiny(periodic=True, n=(24, 24, 24)))
+    s.h = (0.3, 0.3, 0.3)
+    x, y, z = O.coords(s)
+    L = 24 * 0.3
+    rho = np.zeros((24, 24, 24))
+    for c in ((2.0, 3.0, 4.0), (5.0, 1.0, 2.5)):
+        d2 = sum(((co - cc) - L * np.round((co - cc) / L)) ** 2 for co, cc in
+                 ((x[None, None, :], c[0]), (y[None, :, None], c[1]), (z[:, None, None], c[2])))
+        rho = rho + np.exp(-d2 / 1.2 ** 2)
+    vh = O.hartree(s, rho)
+    lap = sum(O.d2(vh, a, s) for a in range(3))
+    assert np.max(np.abs(-lap - 4 * np.pi * (rho - rho.mean()))) < 2e-3 * np.max(4 * np.pi * rho)
+
+
+def test_box_self_integral():
+    """Corner integral of 1/r over a box: the cube value 6 ln((1+sqrt3)/sqrt2) - pi/2 = 2.3800772...
+    and a numerical quadrature for an anisotropic box."""
+    from scipy import integrate
+    assert abs(8 * O.box_self_integral(0.5, 0.5, 0.5) - 2.380077364) < 1e-8
+    a, b, c = 0.3, 0.5, 0.8
+    num, _ = integrate.tplquad(lambda z, y, x: 1.0 / math.sqrt(x * x + y * y + z * z),
+                               0, a, 0, b, 0, c, epsabs=1e-11, epsrel=1e-11)
+    assert abs(O.box_self_integral(a, b, c) - num) < 1e-8
+
+
+def test_hockney_against_direct_sum():
+    """Zero-padded FFT convolution equals the O(N^2) direct sum with the same kernel."""
+    s = _no_atoms(W.tiny(periodic=False, n=(5, 6, 7)))
+    rng = np.random.default_rng(9)
+    rho = rng.random((7, 6, 5))
+    x, y, z = O.coords(s)
+    Z3, Y3, X3 = np.meshgrid(z, y, x, indexing="ij")
+    P = np.stack([X3.ravel(), Y3.ravel(), Z3.ravel()], axis=1)
+    g0 = 8 * O.box_self_integral(s.h[0] / 2, s.h[1] / 2, s.h[2] / 2) / s.dV
+    direct = np.zeros(len(P))
+    for i in range(len(P)):
+        r = np.linalg.norm(P - P[i], axis=1)
+        g = np.where(r == 0, g0, 1.0 / np.where(r == 0, 1.0, r))
+        direct[i] = np.sum(g * rho.ravel()) * s.dV
+    assert np.max(np.abs(O.hartree(s, rho).ravel() - direct)) < 1e-11 * np.max(np.abs(direct))
+
+
+def test_hockney_gaussian_charge():
+    """Isolated Gaussian charge of unit norm: V = erf(r/s)/r outside the core, to discretisation error."""
+    s = _no_atoms(W.tiny(periodic=False, n=(32, 32, 32)))
+    s.h = (0.35, 0.35, 0.35)
+    x, y, z = O.coords(s)
+    Z3, Y3, X3 = np.meshgrid(z, y, x, indexing="ij")
+    r = np.sqrt(X3 ** 2 + Y3 ** 2 + Z3 ** 2)
+    sg = 1.0
+    rho = np.exp(-r ** 2 / sg ** 2) / (np.pi ** 1.5 * sg ** 3)
+    vh = O.hartree(s, rho)
+    from scipy.special import erf
+    for rc, tol in ((2.0, 3e-4), (3.0, 5e-6)):      # O(h^2) error near the core, vanishing outside
+        mask = r > rc
+        assert np.max(np.abs(vh[mask] - erf(r[mask] / sg) / r[mask])) < tol
+    assert abs(np.sum(rho) * s.dV - 1.0) < 1e-4
+
+
+def test_lda_exchange_closed_forms():
+    """eps_x(r_s = 1) = -0.458165 Ha (Slater exchange of the uniform gas);
+    V_x = d(rho eps_x)/d rho by a central difference."""
+    rho = np.array([3.0 / (4.0 * np.pi)])
+    vx, ex = O.lda_x(rho)
+    assert abs(ex[0] + 0.4581652932831429) < 1e-12
+    r = np.array([0.013, 0.21, 1.7])
+    hstep = 1e-6 * r
+    f = lambda rr: rr * O.lda_x(rr)[1]
+    assert np.allclose((f(r + hstep) - f(r - hstep)) / (2 * hstep), O.lda_x(r)[0], rtol=1e-8)
+
+
+# ---------------------------------------------------------------- local potential
+def test_local_potential_poisson_periodic():
+    """-Laplacian of V_loc = 4 pi (rho_ion - <rho_ion>) with rho_ion = -Z Gaussians of width sigma
+    centred on each atom (image-summed), to FD accuracy: pins scale, sign, width and position."""
+    s = W.tiny(periodic=True, n=(30, 30, 30), natom=2)
+    s.h = (0.28, 0.3, 0.32)
+    s.atoms = [W.Atom((2.1, 4.4, 3.3), 2.0, 1.1), W.Atom((6.0, 5.1, 7.2), 3.0, 1.3)]
+    V = O.local_potential(s)
+    x, y, z = O.coords(s)
+    L = [30 * hh for hh in s.h]
+    rho = np.zeros((30, 30, 30))
+    for at in s.atoms:
+        for ix in (-1, 0, 1):
+            for iy in (-1, 0, 1):
+                for iz in (-1, 0, 1):
+                    d2 = ((x[None, None, :] - at.R[0] - ix * L[0]) ** 2 + (y[None, :, None] - at.R[1] - iy * L[1]) ** 2
+                          + (z[:, None, None] - at.R[2] - iz * L[2]) ** 2)
+                    rho += -at.Z * np.exp(-d2 / at.sigma ** 2) / (np.pi ** 1.5 * at.sigma ** 3)
+    lap = sum(O.d2(V, a, s) for a in range(3))
+    err = np.max(np.abs(-lap - 4 * np.pi * (rho - rho.mean())))
+    assert err < 3e-3 * np.max(np.abs(4 * np.pi * rho))
+
+
+def test_local_potential_isolated_laplacian():
+    s = W.tiny(periodic=False, n=(28, 28, 28), natom=1)
+    s.h = (0.2, 0.2, 0.2)
+    s.atoms = [W.Atom((0.13, -0.07, 0.05), 3.0, 0.9)]
+    V = O.local_potential(s)
+    x, y, z = O.coords(s)
+    at = s.atoms[0]
+    d2 = (x[None, None, :] - at.R[0]) ** 2 + (y[None, :, None] - at.R[1]) ** 2 + (z[:, None, None] - at.R[2]) ** 2
+    rho = -at.Z * np.exp(-d2 / at.sigma ** 2) / (np.pi ** 1.5 * at.sigma ** 3)
+    lap = sum(O.d2(V, a, s) for a in range(3))
+    inner = (slice(5, -5),) * 3
+    assert np.max(np.abs(-lap[inner] - 4 * np.pi * rho[inner])) < 1e-3 * np.max(np.abs(4 * np.pi * rho))
+
+
+# ---------------------------------------------------------------- observables
+def test_current_is_minus_dE_dA():
+    """J = -(1/Omega) dE_band/dA' at fixed orbitals (central difference), including the nonlocal
+    term: pins the current operator and the sign of Eq. (macro_current)."""
+    s = W.tiny(periodic=True, n=(6, 7, 8), natom=2, nk=2, norb=2)
+    tabs = O.projector_tables(s)
+    Vloc = O.local_potential(s)
+    psi = W.initial_orbitals(s, 4)
+    Ap = np.array([0.05, -0.02, 0.03])
+    J = O.current(s, tabs, psi, Ap)
+    eps = 1e-5
+    for a in range(3):
+        dA = np.zeros(3)
+        dA[a] = eps
+        dE = (O.band_energy(s, tabs, Vloc, psi, Ap + dA) - O.band_energy(s, tabs, Vloc, psi, Ap - dA)) / (2 * eps)
+        assert abs(J[a] + dE / O.cell_volume(s)) < 1e-8 * max(1.0, abs(J[a]))
+    # the nonlocal part is not negligible here
+    s0 = W.tiny(periodic=True, n=(6, 7, 8), natom=2, nk=2, norb=2)
+    s0.proj.E_s = s0.proj.E_p = 0.0
+    assert np.max(np.abs(O.current(s0, O.projector_tables(s0), psi, Ap) - J)) > 1e-4 * np.max(np.abs(J))
+
+
+def test_dipole_brute_force():
+    s = _no_atoms(W.tiny(periodic=False, n=(5, 6, 7)))
+    rng = np.random.default_rng(1)
+    rho, rho0 = rng.random((7, 6, 5)), rng.random((7, 6, 5))
+    x, y, z = O.coords(s)
+    ref = np.zeros(3)
+    for k in range(7):
+        for j in range(6):
+            for i in range(5):
+                ref -= np.array([x[i], y[j], z[k]]) * (rho[k, j, i] - rho0[k, j, i]) * s.dV
+    assert np.allclose(O.dipole(s, rho, rho0), ref, atol=1e-13)
+
+
+def test_fsum_slope_after_kick():
+    """Linear H (Hartree/xc off), real orbitals: after psi -> exp(i kappa z) phi, the dipole slope is
+    d'(0) = -kappa N_eff with N_eff = 2 sum_n <phi|[z,[H,z]]|phi> from dense matrices (f-sum / TRK)."""
+    s = W.tiny(periodic=False, n=(6, 6, 6), natom=1, norb=2)
+    tabs = O.projector_tables(s)
+    V = O.local_potential(s)
+    H = _dense_H(s, tabs, V, np.zeros(3))
+    z = O.coords(s)[2]
+    Zd = np.repeat(z, 36)
+    C = Zd[:, None] * (H * Zd[None, :] - Zd[:, None] * H) - (H * Zd[None, :] - Zd[:, None] * H) * Zd[None, :]
+    phi = W.initial_orbitals(s, 2).real
+    phi /= np.sqrt((phi ** 2).sum(axis=(2, 3, 4), keepdims=True) * s.dV)
+    neff = 2 * sum(np.real(phi[0, n].ravel() @ C @ phi[0, n].ravel()) * s.dV for n in range(2))
+    kappa = 1e-3
+    psi = O.apply_kick(s, phi.astype(np.complex128), (0.0, 0.0, kappa))
+    dt = 1e-3
+    rho0 = O.density(s, psi)
+    fwd = np.stack([O.taylor4(s, tabs, V, np.zeros(3), psi[0, n], dt) for n in range(2)])[None]
+    bwd = np.stack([O.taylor4(s, tabs, V, np.zeros(3), psi[0, n], -dt) for n in range(2)])[None]
+    slope = (O.dipole(s, O.density(s, fwd), rho0)[2] - O.dipole(s, O.density(s, bwd), rho0)[2]) / (2 * dt)
+    assert abs(slope - (-kappa * neff)) < 1e-6 * abs(kappa * neff)
+    # the kinetic double commutator alone is close to 1 per electron on a fine enough grid
+    assert 0.5 < neff / 4.0 < 1.5
+
+
+def test_oscillator_strength_sign_and_sum():
+    """A single harmonic mode after the kick, d(t) = -(2 kappa/w) sin(w t): the spectrum must be
+    positive, peak at w, and integrate to the electron count 2 (the mask broadens the line)."""
+    w, kappa = 0.4, 1e-3
+    t = np.arange(1, 40001) * 0.02
+    d = -(2 * kappa / w) * np.sin(w * t)
+    E = np.linspace(0.0, 1.2, 2401)
+    f = O.oscillator_strength(np.concatenate([[0.0], t]), np.concatenate([[0.0], d]), kappa, E)
+    assert abs(E[np.argmax(f)] - w) < 2e-3
+    integral = np.sum(f) * (E[1] - E[0])
+    assert abs(integral - 2.0) < 0.03
+
+
+def test_pulse_field_amplitude():
+    """Eq. (pulse): A' vanishes at both ends; E = -dA'/dt peaks at about E0 = 1e-3 au."""
+    f = W.pulse_field()
+    assert np.allclose(O.field_Aprime(f, 0.0), 0) and np.allclose(O.field_Aprime(f, f.T), 0)
+    t = np.linspace(0, f.T, 200001)
+    A = np.array([O.field_Aprime(f, tt)[2] for tt in t])
+    E = -np.gradient(A, t)
+    assert abs(np.max(np.abs(E)) - 1e-3) < 2e-5
+    assert O.field_Aprime(W.small_periodic().field, 0.01)[2] == 0.001
+
+
+# ---------------------------------------------------------------- whole step: invariants
+def test_energy_conservation_second_order():
+    """No field, Hartree + exchange on, predictor-corrector: the total-energy drift over a fixed
+    time falls at least as dt^2 (measured ratio >= 3.5 for dt -> dt/2)."""
+    s = W.tiny(periodic=True, n=(8, 8, 8), natom=1, norb=2)
+    s.field = W.Field("none")
+    psi0 = W.initial_orbitals(s, 6)
+    tabs = O.projector_tables(s)
+    Vloc = O.local_potential(s)
+    Ap = np.zeros(3)
+    E0 = O.total_energy(s, tabs, Vloc, psi0, Ap)
+    drifts = []
+    for dt, n in ((0.04, 10), (0.02, 20)):
+        s.dt = dt
+        psi, _, _ = O.run(s, psi0, n, record=False)
+        drifts.append(abs(O.total_energy(s, tabs, Vloc, psi, Ap) - E0))
+    assert drifts[1] < drifts[0] / 3.5, drifts
+
+
+def test_pc_reduces_to_taylor_when_potential_frozen():
+    """With Hartree and exchange off the potential does not depend on rho, so the
+    predictor-corrector step must equal one plain Taylor step exactly."""
+    s = W.tiny(periodic=True, n=(6, 6, 6), natom=1, norb=2)
+    psi0 = W.initial_orbitals(s, 1)
+    tabs = O.projector_tables(s)
+    Vloc = O.local_potential(s)
+    a, _, _ = O.pc_step(s, tabs, Vloc, psi0, np.zeros_like(Vloc), 0.0, 0.02, pc=True, hartree_on=False, xc_on=False)
+    b = O.propagate_all(s, tabs, Vloc, psi0, O.field_Aprime(s.field, 0.01), 0.02)
+    assert np.max(np.abs(a - b)) < 1e-15
+
+
+def test_maxwell_leapfrog_closed_forms():
+    """Vacuum: at c dt/dX = 1 leapfrog moves a right-going wave exactly one cell per step.
+    Uniform source: A(t) = 2 pi c I t^2 exactly (the scheme is exact on quadratics)."""
+    X = np.arange(200, dtype=float)
+    f = lambda x: np.exp(-((x - 60.0) / 7.0) ** 2)
+    A_prev, A_now = f(X + 1.0), f(X)
+    for _ in range(30):
+        A_prev, A_now = A_now, O.maxwell_step(A_now, A_prev, np.zeros(200), 1.0, 0.1)
+    assert np.max(np.abs(A_now[1:-1] - f(X - 30.0)[1:-1])) < 1e-12
+    dt, I = 0.05, 0.3
+    A_prev = np.full(30, 2 * np.pi * O.C_LIGHT * I * dt * dt)     # A(-dt)
+    A_now = np.zeros(30)
+    for n in range(1, 6):
+        A_prev, A_now = A_now, O.maxwell_step(A_now, A_prev, np.full(30, I), 0.5, dt)
+        # away from the held end points (their influence moves one cell per step)
+        assert np.allclose(A_now[8:-8], 2 * np.pi * O.C_LIGHT * I * (n * dt) ** 2, rtol=1e-12)
