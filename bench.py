@@ -1,0 +1,333 @@
+#!/usr/bin/env python
+"""Benchmark of one real-time TDKS predictor-corrector step on the GPU (libtdks, C ABI).
+
+Workload: the diamond-lattice crystal response -- 8-atom cubic cell a = 10.26 bohr, 20^3 grid,
+16 orbitals x 64 k-points (4^3 shifted Monkhorst-Pack), sin^2 pulse along z (1.55 eV, 1e-3 au,
+10 fs), dt = 0.02 au, 4th-order Taylor + predictor-corrector + FFT Hartree + LDA exchange,
+FP32 orbitals with FP64 reductions.  A "step" is one full tdks_step: predictor Taylor,
+density, Hartree + exchange, corrector Taylor, density, Hartree + exchange, current and dipole.
+
+Arms:
+  default            the CUDA path; prints one JSON line (rank 0).
+  --impl reference   the FP64 CPU oracle on this host's cores, on a bounded sample of the same
+                     workload (a subset of the k-points), scaled to whole-workload steps/s.
+
+Multi-GPU: every rank propagates its own copy of the workload (independent replicas, no
+collective on the data path); value = total steps of all ranks / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")     # the CPU oracle legs run single-threaded
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "TDKS steps/s & hpsi HBM GB/s vs peak; FP32+learned vs FP64 at ≤1e-4 J err"
+UNIT = "steps/s"
+FP32_LANES_PER_SM = 128
+N_SM = 152
+# algorithmic FP32 flops per grid point per Horner stage of the periodic Hamiltonian:
+# 12 neighbour pairs x (4 adds + 4 FMA) for the Laplacian and q.grad terms (144), diagonal (3),
+# Horner update (4)
+FLOPS_PER_POINT_STAGE = 151
+FLOPS_PER_SPHERE_ENTRY_STAGE = 44   # projection (22) + scatter (22)
+
+
+def workload():
+    from paper_1804_01404_gb300 import workloads as W
+    return W.diamond_crystal()
+
+
+def config_dict(s, extra=None):
+    d = {"workload": "diamond crystal 20^3 grid, 8 atoms, 16 orbitals x 64 k, sin^2 pulse",
+         "grid": list(s.n), "norb": s.norb, "nk": s.nk, "dt": s.dt, "taylor_order": 4,
+         "predictor": "predictor-corrector", "orbitals": "f32", "reductions_poisson": "f64",
+         "l2": "flushed between timed steps (256 MiB write)"}
+    if extra:
+        d.update(extra)
+    return d
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "fallback": True}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    def __init__(self, index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.count(",") >= 7]
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[4 + i]})
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(rows[0][2]), "reasons": reasons,
+                "samples": len(rows)}
+
+
+def run_oracle_sample(nk_sample, nsteps, t0=200.0):
+    """FP64 oracle steps on the first nk_sample k-points of the workload; returns seconds/step."""
+    from oracle import tdks_oracle as O
+    s = workload()
+    s.kpts = s.kpts[:nk_sample]
+    s.kw = np.full(nk_sample, 1.0 / nk_sample)
+    psi = W_initial(s)
+    tabs = O.projector_tables(s)
+    Vloc = O.local_potential(s)
+    v = O.hxc(s, O.density(s, psi))
+    tic = time.perf_counter()
+    t = t0
+    for _ in range(nsteps):
+        psi, v, rho = O.pc_step(s, tabs, Vloc, psi, v, t, s.dt)
+        t += s.dt
+        O.current(s, tabs, psi, O.field_Aprime(s.field, t))
+    return (time.perf_counter() - tic) / nsteps
+
+
+def W_initial(s):
+    from paper_1804_01404_gb300 import workloads as W
+    return W.initial_orbitals(s, 0)
+
+
+def cpu_cores():
+    return 1   # the oracle is single-threaded numpy (BLAS/FFT threads pinned to 1 below)
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return 0
+    s = workload()
+    nk_sample = 2
+    for _ in range(args.warmup):
+        run_oracle_sample(nk_sample, 1)
+    per = [run_oracle_sample(nk_sample, 1) for _ in range(args.steps)]
+    t_sample = float(np.mean(per))
+    t_full = t_sample * s.nk / nk_sample
+    v = 1.0 / t_full
+    sample = (f"{nk_sample} of {s.nk} k-points (all 16 orbitals each, full 20^3 grid) per step, "
+              f"one PC step + current each; steps/s scaled by {s.nk // nk_sample}")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_full * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_dict(s, {"orbitals": "f64"}),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def gpu_arm(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    from paper_1804_01404_gb300.tdks import Context
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    s = workload()
+    psi0 = W_initial(s).astype(np.complex64)
+    u = torch.from_numpy(psi0).to(dev)
+    ctx = Context(s, precision="f32")
+    stream = torch.cuda.current_stream()
+    ctx.update_potential(u)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    t = 0.0
+    t0 = 200.0   # start inside the pulse (A' != 0)
+    for i in range(args.warmup):
+        ctx.step(u, t0 + i * s.dt, s.dt)
+    torch.cuda.synchronize()
+    ctx.stats(reset=True)
+    ctx.profile(True)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank)
+    t = t0 + args.warmup * s.dt
+    for i in range(args.steps):
+        flush.zero_()                                    # evict the 65 MB orbital set from L2
+        evs[i][0].record(stream)
+        ctx.step(u, t, s.dt)
+        evs[i][1].record(stream)
+        t += s.dt
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = float(np.sum(step_ms))
+    st = ctx.stats(reset=True)
+    ctx.profile(False)
+    if world > 1:
+        tt = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    value = world * args.steps / (total_ms / 1e3)
+
+    # dominant kernel: the Taylor kernel (predictor + corrector launches)
+    npts, norb_tot = s.npts, s.nk * s.norb
+    nsph = ctx.query()["nsphere_points"]
+    k_ms = (st["ms"]["taylor_predictor"] + st["ms"]["taylor_corrector"]) / max(
+        1, st["calls"]["taylor_predictor"] + st["calls"]["taylor_corrector"])
+    flops = 4 * norb_tot * (FLOPS_PER_POINT_STAGE * npts + FLOPS_PER_SPHERE_ENTRY_STAGE * nsph)
+    pk = peaks()
+    fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    achieved = flops / (k_ms * 1e-3) / 1e12
+    # HBM view of the same kernel: read psi + write psi' (corrector), 8 B each per point
+    hbm_bytes = 16 * npts * norb_tot
+    roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak, "traffic": None,
+                "kernel": "k_smem_orbital<float, MODE=1> (4 Horner stages, whole orbital in smem)",
+                "avg_launch_ms": k_ms, "flops_per_launch": flops,
+                "peak_note": "FP32 FMA peak = 152 SM x 128 lanes x 2 x max SM clock (derived)",
+                "hbm_view": {"bytes_per_launch": hbm_bytes,
+                             "GBps": hbm_bytes / (k_ms * 1e-3) / 1e9,
+                             "frac_of_measured_hbm": hbm_bytes / (k_ms * 1e-3) / 1e9 / pk["hbm_gbs"]}}
+    phases = {k: v / args.steps for k, v in st["ms"].items()}
+
+    # FP64 path on the same GPU (context numbers): steps/s and the FP32-vs-FP64 current error
+    fp64 = None
+    if not args.skip_fp64 and rank == 0:
+        fp64 = fp64_comparison(s, psi0, dev, nsteps=args.fp64_steps)
+
+    # end to end through the C ABI with host buffers: upload psi(0) from pinned memory, K steps
+    # each reading J and the dipole back to the host, download psi at the end
+    host_in = torch.from_numpy(psi0).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    ctx2 = Context(s, precision="f32")
+    u2 = torch.empty_like(u)
+    ctx2.update_potential(u)  # warm the context
+    torch.cuda.synchronize()
+    tic = time.perf_counter()
+    u2.copy_(host_in, non_blocking=True)
+    ctx2.update_potential(u2)
+    tt = t0
+    for i in range(args.steps):
+        ctx2.step(u2, tt, s.dt)
+        ctx2.read_step_observables()
+        tt += s.dt
+    host_out.copy_(u2, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - tic
+    psi_bytes = psi0.nbytes
+    e2e = {"value": world * args.steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": psi_bytes / args.steps,
+           "d2h_bytes_per_step": psi_bytes / args.steps + 8 * 8,
+           "note": "psi(0) uploaded and psi(T) downloaded once per K steps; J and dipole read "
+                   "back every step (synchronising)"}
+
+    cpu = None
+    if rank == 0 and not args.skip_cpu:
+        nk_sample = 2
+        per = run_oracle_sample(nk_sample, args.cpu_steps)
+        v_cpu = 1.0 / (per * s.nk / nk_sample)
+        cpu = {"value": v_cpu, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+               "sample": f"{args.cpu_steps} PC steps (+current) on {nk_sample} of {s.nk} k-points, "
+                         f"scaled by {s.nk // nk_sample} to whole-workload steps/s"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": config_dict(s, {"parallelism": f"replicas x{world}"}),
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": st["launches"], "clocks": clk,
+                "phase_ms_per_step": phases, "step_ms_min": float(np.min(step_ms)),
+                "fp64": fp64}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def fp64_comparison(s, psi0, dev, nsteps=10):
+    """Same steps with FP64 orbitals: steps/s and max_t |J32 - J64| / max_t |J64|."""
+    import torch
+    from paper_1804_01404_gb300.tdks import Context
+    out = {}
+    js = {}
+    for prec, dt_ in (("f64", torch.complex128), ("f32", torch.complex64)):
+        ctx = Context(s, precision=prec)
+        u = torch.from_numpy(psi0.astype(np.complex128)).to(dev, dt_)
+        ctx.update_potential(u)
+        t = 200.0
+        J = []
+        torch.cuda.synchronize()
+        tic = time.perf_counter()
+        for _ in range(nsteps):
+            ctx.step(u, t, s.dt)
+            t += s.dt
+            J.append(ctx.read_step_observables()["J"])
+        torch.cuda.synchronize()
+        out[prec + "_steps_per_s"] = nsteps / (time.perf_counter() - tic)
+        js[prec] = np.array(J)
+        ctx.close()
+    out["steps"] = nsteps
+    out["J_rel_err_f32_vs_f64"] = float(np.max(np.abs(js["f32"] - js["f64"])) / np.max(np.abs(js["f64"])))
+    out["note"] = "both timed with a host read of J every step"
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--cpu-steps", type=int, default=8)
+    ap.add_argument("--fp64-steps", type=int, default=10)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return reference_arm(args, rank, world)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    try:
+        return gpu_arm(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

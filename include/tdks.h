@@ -1,0 +1,180 @@
+/*
+ * tdks.h -- C ABI of the GB300 real-time TDKS propagator (libtdks.so).
+ *
+ * One time step of real-time, real-space TDDFT as in Noda et al., "SALMON: Scalable Ab-initio
+ * Light-Matter simulator for Optics and Nanoscience" (Comput. Phys. Commun.):
+ *   - Kohn-Sham orbitals on a uniform Cartesian grid (Sec. 2.1), vacuum outside the cuboid or
+ *     periodic in all directions;
+ *   - the Hamiltonian of Eq. (TDKS) (isolated) or Eq. (TDKS_solid) (Bloch orbitals in the velocity
+ *     gauge), with a local pseudopotential and Kleinman-Bylander separable projectors (Sec. 3.1)
+ *     whose phase follows the vector potential (Sec. 4.1);
+ *   - a truncated (4th order) Taylor expansion of exp(-iH dt) and a predictor-corrector step for
+ *     the density-dependent potential (Program summary);
+ *   - the density of Eq. (rho), the Hartree potential of Eq. (TDKS), adiabatic LDA exchange
+ *     (Sec. 3.1), the dipole of Sec. 3.1 and the current of Eq. (macro_current).
+ *
+ * Discrete model (fixed by this library where the paper is silent):
+ *   H_q = -1/2 sum_a D2_a - i sum_a q_a D1_a + |q|^2/2 + V_loc + V_H + V_x + V_NL^q,  q = k + A/c,
+ *   D2, D1: 8th-order central differences (4 neighbours per side per axis: 25-point Laplacian),
+ *   V_NL^q u = sum_{atom, p} E_p beta_p(r) e^{-i q.d} sum_r' beta_p(r') e^{i q.d'} u(r') dV,
+ *   d = r - R_atom (nearest image).  Projectors are s, px, py, pz:
+ *   beta = N {1, dx, dy, dz} exp(-d^2/(2 w^2)) (1 - d^2/rc^2)^2 for |d| < rc, each grid-normalised
+ *   to sum beta^2 dV = 1.  Orbitals are normalised to sum |u|^2 dV = 1, occupation 2, k-weight w_k.
+ *   Units: Hartree atomic units.
+ *
+ * Memory and threading contract:
+ *   - Orbitals are DEVICE arrays owned by the caller, contiguous, layout [nk][norb][nz][ny][nx],
+ *     complex interleaved (re, im): double2 for TDKS_F64, float2 for TDKS_F32.
+ *   - The library owns its internal device workspaces (potentials, projector tables, FFT buffers),
+ *     allocated in tdks_init and released in tdks_destroy.
+ *   - Every call is enqueued on the CUDA stream given to tdks_init and returns without waiting,
+ *     except calls that return host values (tdks_observables, tdks_read_step_observables,
+ *     tdks_check), which synchronise that stream.
+ *   - A context is not thread-safe; use one context per host thread.
+ *   - Errors are returned as tdks_status codes; tdks_last_error() gives a message (thread-local).
+ *     No call throws across the ABI.
+ */
+#ifndef TDKS_H_
+#define TDKS_H_
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TDKS_ABI_VERSION 1
+
+typedef struct tdks_ctx tdks_ctx;
+
+typedef enum {
+  TDKS_OK = 0,
+  TDKS_EINVAL = 1,        /* invalid argument (null pointer, bad size, inconsistent grid/cell) */
+  TDKS_ENOMEM = 2,        /* device or host allocation failed */
+  TDKS_ECUDA = 3,         /* a CUDA runtime call or kernel launch failed */
+  TDKS_ETIMEOUT = 4,      /* a device-side wait gave up (reserved for persistent kernels) */
+  TDKS_ENONFINITE = 5,    /* the norm monitor found a NaN/Inf orbital */
+  TDKS_EUNSUPPORTED = 6   /* a valid request this build does not implement (e.g. grid too large) */
+} tdks_status;
+
+enum { TDKS_F64 = 0, TDKS_F32 = 1 };
+enum { TDKS_FIELD_NONE = 0, TDKS_FIELD_STEP = 1, TDKS_FIELD_PULSE = 2 };
+
+/* Uniform grid (Sec. 2.1).  n = points per axis (x, y, z); h = spacing (bohr).
+ * periodic = 1: periodic cuboid of side L = n h; coordinates r_j = j h.
+ * periodic = 0: vacuum outside the box (orbitals zero outside); coordinates r_j = (j-(n-1)/2) h. */
+typedef struct { int n[3]; double h[3]; int periodic; } tdks_grid;
+
+/* Cell of a periodic grid; must equal n*h per axis within 1e-9 relative.  Ignored if isolated. */
+typedef struct { double L[3]; } tdks_cell;
+
+/* Pseudo-atom: local part V(r) = -Z erf(|r-R|/sigma)/|r-R| (Sec. 3.1 local pseudopotential), and
+ * `proj` = index of its projector set in the tdks_projector array, or -1 for none. */
+typedef struct { double R[3]; double Z; double sigma; int proj; } tdks_atom;
+
+/* Kleinman-Bylander s + p projector set (Sec. 3.1): energies E_s (s) and E_p (px, py, pz),
+ * cutoff radius r_cut and Gaussian width `width` of the shape given above. */
+typedef struct { double E_s, E_p, r_cut, width; } tdks_projector;
+
+/* precision: TDKS_F64 (orbitals, stencil and all reductions in FP64) or TDKS_F32 (FP32 complex
+ * orbitals and stencil; density, current, dipole, norms and the Poisson solve stay in FP64).
+ * hartree, xc: include V_H and LDA exchange (1) or leave them out (0: linear propagation).
+ * pc: predictor-corrector on (1) or a single Taylor step with V(t) (0). */
+typedef struct { int precision; int hartree; int xc; int pc; } tdks_options;
+
+/* Observables returned to the host. */
+typedef struct {
+  double J[3];        /* macroscopic current density, Eq. (macro_current) (periodic only; else 0) */
+  double dipole[3];   /* d = -int r (rho - rho0) dr (Sec. 3.1)                                  */
+  double norm_min;    /* min over orbitals of sum |u|^2 dV                                       */
+  double norm_max;    /* max over orbitals                                                       */
+  double e_band;      /* sum_k w_k sum_n 2 <u|T_q + V_loc + V_NL^q|u>                           */
+  double n_elec;      /* int rho dr                                                              */
+} tdks_obs;
+
+/* Create a context: builds the projector tables (host), the local potential (device), the
+ * FFT plans and buffers.  kpts = [nk][3] Bloch vectors (bohr^-1), kw = [nk] weights (sum 1).
+ * norb = orbitals per k-point.  stream = cudaStream_t (NULL = legacy default stream).
+ * Errors: TDKS_EINVAL for bad sizes or a projector sphere wider than half the periodic cell;
+ * TDKS_EUNSUPPORTED for grids beyond this build's limits; TDKS_ENOMEM; TDKS_ECUDA. */
+tdks_status tdks_init(const tdks_grid* grid, const tdks_cell* cell,
+                      const tdks_atom* atoms, int natom,
+                      const tdks_projector* projectors, int nproj,
+                      const double* kpts, const double* kw, int nk, int norb,
+                      const tdks_options* opts, void* stream, tdks_ctx** out);
+
+/* Spatially uniform field as A'(t) = A(t)/c.  kind = TDKS_FIELD_NONE: A' = 0.
+ * TDKS_FIELD_STEP: A'(t) = A0 for t > 0 (impulsive kick in the velocity gauge, Eq. impulsive_A).
+ * TDKS_FIELD_PULSE: A'(t) = A0 cos^2[pi (t - T/2)/T] sin[-omega (t - T/2) - 2 pi cep], 0 < t < T
+ * (Eq. pulse with a real amplitude A0 already divided by c).  Isolated systems ignore the field. */
+tdks_status tdks_set_field(tdks_ctx* ctx, int kind, const double A0[3], double omega,
+                           double T, double cep);
+
+/* Isolated impulse (Sec. 3.1): u <- exp(i kappa . r) u for all orbitals, in place. */
+tdks_status tdks_kick(tdks_ctx* ctx, void* u_dev, const double kappa[3]);
+
+/* rho <- rho[u] (Eq. rho), V_Hxc(t) <- V_H[rho] + V_x[rho].  The first call also stores rho as
+ * the reference density rho0 of the dipole.  Must be called once before tdks_step. */
+tdks_status tdks_update_potential(tdks_ctx* ctx, const void* u_dev);
+
+/* hu <- H_q u for all orbitals with q = k + Aprime and the current potential
+ * V_loc + V_Hxc(t).  u and hu must not overlap. */
+tdks_status tdks_hpsi(tdks_ctx* ctx, const void* u_dev, void* hu_dev, const double Aprime[3]);
+
+/* u <- sum_{n=0..4} (-i dt H_q)^n u / n! in place (Horner form), with q = k + Aprime and the
+ * current potential V_loc + V_Hxc(t). */
+tdks_status tdks_taylor_step(tdks_ctx* ctx, void* u_dev, double dt, const double Aprime[3]);
+
+/* One predictor-corrector step t -> t + dt, in place (Program summary; Sec. 3.1, 4.1):
+ *   predictor  u~ = T4[V_loc + V_Hxc(t)] u,  V~ = V_Hxc[rho(u~)];
+ *   corrector  u(t+dt) = T4[V_loc + (V_Hxc(t) + V~)/2] u,  V_Hxc(t+dt) = V_Hxc[rho(t+dt)];
+ * both with A'(t + dt/2).  (pc = 0: u(t+dt) = T4[V_loc + V_Hxc(t)] u.)  Afterwards J(t+dt)
+ * (with A'(t+dt)) and the dipole are in the step-observable buffer (tdks_read_step_observables). */
+tdks_status tdks_step(tdks_ctx* ctx, void* u_dev, double t, double dt);
+
+/* Copy the observables written by the last tdks_step to the host (synchronises the stream).
+ * Only J, dipole and n_elec are filled; the other fields are set to 0. */
+tdks_status tdks_read_step_observables(tdks_ctx* ctx, tdks_obs* out);
+
+/* Compute all observables of u with A'(t) = Aprime, against the current rho0 and potential
+ * (synchronises the stream).  Does not change the context's potential. */
+tdks_status tdks_observables(tdks_ctx* ctx, const void* u_dev, const double Aprime[3], tdks_obs* out);
+
+/* Copy context arrays (device-to-device, [nz][ny][nx] doubles) into caller buffers:
+ * which = 0: V_loc; 1: V_Hxc(t); 2: rho(t); 3: rho0. */
+tdks_status tdks_get_grid_array(tdks_ctx* ctx, int which, double* dst_dev);
+
+/* Wait for all work of the context's stream and report any asynchronous CUDA error. */
+tdks_status tdks_check(tdks_ctx* ctx);
+
+/* Phase timing and launch counting.
+ * Phases: 0 predictor Taylor kernel, 1 corrector Taylor kernel (and tdks_taylor_step),
+ * 2 tdks_hpsi kernel, 3 Hartree + exchange (density-to-potential), 4 observables,
+ * 5 everything else (potential combination, memsets).  With timing enabled the library records a
+ * CUDA event pair around each phase on the context stream (a few microseconds of overhead per
+ * step).  `launches` counts this library's kernel launches since the last reset, timing on or off. */
+#define TDKS_NPHASE 6
+typedef struct {
+  long long launches;
+  long long calls[TDKS_NPHASE];
+  double ms[TDKS_NPHASE];
+} tdks_stats;
+
+/* enable = 1 starts recording phase events, 0 stops. */
+tdks_status tdks_profile(tdks_ctx* ctx, int enable);
+
+/* Sum the recorded phase times (synchronises the stream); reset = 1 clears counters and times. */
+tdks_status tdks_stats_read(tdks_ctx* ctx, tdks_stats* out, int reset);
+
+/* Sizes of the context (any pointer may be NULL). */
+tdks_status tdks_query(const tdks_ctx* ctx, int* npts, int* nk, int* norb, int* precision,
+                       int* nsphere_points);
+
+const char* tdks_last_error(void);
+int tdks_abi_version(void);
+void tdks_destroy(tdks_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TDKS_H_ */

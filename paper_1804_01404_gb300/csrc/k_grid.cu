@@ -1,0 +1,486 @@
+// Grid kernels in FP64: FFT Poisson solve (periodic and zero-padded isolated), LDA exchange,
+// potential combination, density, dipole and current reductions, kick, local potential.
+//
+// FFT: batched 1D Stockham transforms in shared memory, one launch per axis, mixed radix
+// (4, 2, 3, 5, ...).  A CTA loads LB lines of the 3D array into shared memory -- for the y and z
+// axes the LB lines are consecutive in x, so every global access is coalesced -- runs all radix
+// stages there, and writes the lines back in natural order.
+#include <cuda_runtime.h>
+
+#include "tdks_internal.h"
+
+namespace tdks {
+
+namespace {
+
+constexpr int kFftThreads = 256;
+constexpr int kMaxRadices = 16;
+
+struct FftPlanArgs {
+  int nrad;
+  int rad[kMaxRadices];
+};
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return double2{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+
+// twiddle exp(dir * 2 pi i t / n) from the table tw[t] = exp(-2 pi i t / n)
+__device__ __forceinline__ double2 twd(const double2* tw, int t, int n, int dir) {
+  double2 w = tw[t % n];
+  if (dir > 0) w.y = -w.y;
+  return w;
+}
+
+template <int R>
+__device__ __forceinline__ void butterfly(const double2* __restrict__ src, double2* __restrict__ dst,
+                                          int n, int Ns, int jb, const double2* tw, int dir) {
+  const int nr = n / R;
+  const int k = jb % Ns;
+  double2 v[R];
+  const int tstep = n / (Ns * R);
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    double2 x = src[jb + r * nr];
+    if (r > 0) x = cmul(x, twd(tw, r * k * tstep, n, dir));
+    v[r] = x;
+  }
+  const int base = (jb / Ns) * Ns * R + k;
+#pragma unroll
+  for (int m = 0; m < R; ++m) {
+    double2 y = v[0];
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+      const double2 t = cmul(v[r], twd(tw, r * m * nr, n, dir));
+      y.x += t.x;
+      y.y += t.y;
+    }
+    dst[base + m * Ns] = y;
+  }
+}
+
+__device__ void butterfly_generic(const double2* __restrict__ src, double2* __restrict__ dst, int n,
+                                  int R, int Ns, int jb, const double2* tw, int dir) {
+  const int nr = n / R;
+  const int k = jb % Ns;
+  const int tstep = n / (Ns * R);
+  const int base = (jb / Ns) * Ns * R + k;
+  for (int m = 0; m < R; ++m) {
+    double2 y = {0.0, 0.0};
+    for (int r = 0; r < R; ++r) {
+      double2 x = src[jb + r * nr];
+      if (r > 0) x = cmul(x, twd(tw, r * k * tstep, n, dir));
+      const double2 w = twd(tw, r * m * nr, n, dir);
+      y.x += x.x * w.x - x.y * w.y;
+      y.y += x.x * w.y + x.y * w.x;
+    }
+    dst[base + m * Ns] = y;
+  }
+}
+
+// data: 3D array [dims2][dims1][dims0]; transform along `axis` for all lines.
+__global__ void __launch_bounds__(kFftThreads) k_fft_lines(double2* data, int n, int nlines, int LB,
+                                                          long long inner, long long outer,
+                                                          long long estride, int xaxis,
+                                                          const double2* __restrict__ tw_g,
+                                                          FftPlanArgs plan, int dir) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* tw = reinterpret_cast<double2*>(smem_raw);
+  double2* b0 = tw + n;
+  double2* b1 = b0 + (size_t)LB * n;
+  const int l0 = blockIdx.x * LB;
+  const int nl = min(LB, nlines - l0);
+  for (int t = threadIdx.x; t < n; t += blockDim.x) tw[t] = tw_g[t];
+  const int tot = nl * n;
+  for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+    int j, e;
+    if (xaxis) { j = idx / n; e = idx - j * n; } else { e = idx / nl; j = idx - e * nl; }
+    const long long l = l0 + j;
+    const long long start = (l / inner) * outer + (l % inner);
+    b0[j * n + e] = data[start + e * estride];
+  }
+  __syncthreads();
+  double2* src = b0;
+  double2* dst = b1;
+  int Ns = 1;
+  for (int s = 0; s < plan.nrad; ++s) {
+    const int R = plan.rad[s];
+    const int nb = n / R;
+    for (int b = threadIdx.x; b < nl * nb; b += blockDim.x) {
+      const int j = b / nb, jb = b - j * nb;
+      const double2* sl = src + j * n;
+      double2* dl = dst + j * n;
+      switch (R) {
+        case 2: butterfly<2>(sl, dl, n, Ns, jb, tw, dir); break;
+        case 3: butterfly<3>(sl, dl, n, Ns, jb, tw, dir); break;
+        case 4: butterfly<4>(sl, dl, n, Ns, jb, tw, dir); break;
+        case 5: butterfly<5>(sl, dl, n, Ns, jb, tw, dir); break;
+        default: butterfly_generic(sl, dl, n, R, Ns, jb, tw, dir); break;
+      }
+    }
+    __syncthreads();
+    double2* t = src; src = dst; dst = t;
+    Ns *= R;
+  }
+  for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+    int j, e;
+    if (xaxis) { j = idx / n; e = idx - j * n; } else { e = idx / nl; j = idx - e * nl; }
+    const long long l = l0 + j;
+    const long long start = (l / inner) * outer + (l % inner);
+    data[start + e * estride] = src[j * n + e];
+  }
+}
+
+__global__ void k_pack_real(const double* __restrict__ src, int nx, int ny, int nz,
+                            double2* __restrict__ dst, int mx, int my, int mz) {
+  const long long total = (long long)mx * my * mz;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(i % mx);
+    const long long r = i / mx;
+    const int y = (int)(r % my), z = (int)(r / my);
+    double v = 0.0;
+    if (x < nx && y < ny && z < nz) v = src[((long long)z * ny + y) * nx + x];
+    dst[i] = double2{v, 0.0};
+  }
+}
+
+__device__ __forceinline__ double freq(int m, int n) { return (m <= (n - 1) / 2) ? m : m - n; }
+
+__global__ void k_poisson_periodic(double2* data, int nx, int ny, int nz, double Lx, double Ly,
+                                   double Lz) {
+  const long long total = (long long)nx * ny * nz;
+  const double inv_n = 1.0 / (double)total;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(i % nx);
+    const long long r = i / nx;
+    const int y = (int)(r % ny), z = (int)(r / ny);
+    const double gx = 2.0 * kPi * freq(x, nx) / Lx, gy = 2.0 * kPi * freq(y, ny) / Ly,
+                 gz = 2.0 * kPi * freq(z, nz) / Lz;
+    const double g2 = gx * gx + gy * gy + gz * gz;
+    const double f = (g2 == 0.0) ? 0.0 : 4.0 * kPi / g2 * inv_n;
+    double2 v = data[i];
+    data[i] = double2{v.x * f, v.y * f};
+  }
+}
+
+__global__ void k_scale_by_real(double2* data, const double* __restrict__ g, double scale,
+                                long long count) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double f = g[i] * scale;
+    double2 v = data[i];
+    data[i] = double2{v.x * f, v.y * f};
+  }
+}
+
+__global__ void k_hxc_epilogue(const double2* __restrict__ fft, int mx, int my,
+                               const double* __restrict__ rho, int nx, int ny, int nz,
+                               double scale_h, int hartree, int xc, double* __restrict__ vhxc) {
+  const long long total = (long long)nx * ny * nz;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(i % nx);
+    const long long r = i / nx;
+    const int y = (int)(r % ny), z = (int)(r / ny);
+    double v = 0.0;
+    if (hartree) v += scale_h * fft[((long long)z * my + y) * mx + x].x;
+    if (xc) v -= cbrt(3.0 * fmax(rho[i], 0.0) / kPi);   // Slater exchange V_x = -(3 rho/pi)^(1/3)
+    vhxc[i] = v;
+  }
+}
+
+__global__ void k_combine(const double* __restrict__ vloc, const double* __restrict__ v1, double a,
+                          const double* __restrict__ v2, double b, double* __restrict__ o64,
+                          float* __restrict__ o32, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double v = vloc[i];
+    if (v1) v += a * v1[i];
+    if (v2) v += b * v2[i];
+    if (o64) o64[i] = v;
+    if (o32) o32[i] = (float)v;
+  }
+}
+
+template <typename C>
+__global__ void k_density(const C* __restrict__ psi, int nk, int norb, int npts,
+                          const double* __restrict__ kw, double* __restrict__ rho) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npts; p += gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int k = 0; k < nk; ++k) {
+      double s = 0.0;
+      for (int n = 0; n < norb; ++n) {
+        const C u = psi[((size_t)k * norb + n) * npts + p];
+        s += (double)u.x * u.x + (double)u.y * u.y;
+      }
+      acc += 2.0 * kw[k] * s;
+    }
+    rho[p] = acc;
+  }
+}
+
+__device__ __forceinline__ double coord(int j, int n, double h, int periodic) {
+  return periodic ? j * h : (j - 0.5 * (n - 1)) * h;
+}
+
+template <typename C>
+__global__ void k_kick(C* psi, long long norb_tot, int nx, int ny, int nz, double hx, double hy,
+                       double hz, int periodic, double kx, double ky, double kz) {
+  const long long npts = (long long)nx * ny * nz;
+  const long long total = npts * norb_tot;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long p = i % npts;
+    const int x = (int)(p % nx);
+    const long long r = p / nx;
+    const int y = (int)(r % ny), z = (int)(r / ny);
+    const double arg = kx * coord(x, nx, hx, periodic) + ky * coord(y, ny, hy, periodic) +
+                       kz * coord(z, nz, hz, periodic);
+    double s, c;
+    sincos(arg, &s, &c);
+    C u = psi[i];
+    const double re = u.x * c - u.y * s, im = u.x * s + u.y * c;
+    psi[i] = C{(decltype(u.x))re, (decltype(u.x))im};
+  }
+}
+
+__global__ void k_vloc_isolated(double* v, int nx, int ny, int nz, double hx, double hy, double hz,
+                                const double* __restrict__ atoms, int natom) {
+  const long long total = (long long)nx * ny * nz;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(i % nx);
+    const long long r = i / nx;
+    const int y = (int)(r % ny), z = (int)(r / ny);
+    const double px = coord(x, nx, hx, 0), py = coord(y, ny, hy, 0), pz = coord(z, nz, hz, 0);
+    double acc = 0.0;
+    for (int a = 0; a < natom; ++a) {
+      const double dx = px - atoms[5 * a], dy = py - atoms[5 * a + 1], dz = pz - atoms[5 * a + 2];
+      const double Z = atoms[5 * a + 3], sg = atoms[5 * a + 4];
+      const double d = sqrt(dx * dx + dy * dy + dz * dz);
+      acc += (d == 0.0) ? -2.0 * Z / (sg * sqrt(kPi)) : -Z * erf(d / sg) / d;
+    }
+    v[i] = acc;
+  }
+}
+
+__global__ void k_hockney(double2* g, int mx, int my, int mz, int nx, int ny, int nz, double hx,
+                          double hy, double hz, double g0) {
+  const long long total = (long long)mx * my * mz;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(i % mx);
+    const long long r = i / mx;
+    const int y = (int)(r % my), z = (int)(r / my);
+    const double dx = ((x <= nx) ? x : mx - x) * hx;
+    const double dy = ((y <= ny) ? y : my - y) * hy;
+    const double dz = ((z <= nz) ? z : mz - z) * hz;
+    const double d = sqrt(dx * dx + dy * dy + dz * dz);
+    g[i] = double2{(i == 0) ? g0 : 1.0 / d, 0.0};
+  }
+}
+
+__global__ void k_real_part(const double2* __restrict__ s, double* __restrict__ d, long long n,
+                            double scale) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    d[i] = s[i].x * scale;
+}
+
+__global__ void k_f32(const double* __restrict__ s, float* __restrict__ d, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    d[i] = (float)s[i];
+}
+
+constexpr int kRedThreads = 256;
+
+__global__ void __launch_bounds__(kRedThreads) k_dipole_partial(
+    const double* __restrict__ rho, const double* __restrict__ rho0, int nx, int ny, int nz,
+    double hx, double hy, double hz, int periodic, double* partials) {
+  __shared__ double red[kRedThreads / 32][4];
+  double acc[4] = {0, 0, 0, 0};
+  const long long total = (long long)nx * ny * nz;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(i % nx);
+    const long long r = i / nx;
+    const int y = (int)(r % ny), z = (int)(r / ny);
+    const double dr = rho[i] - rho0[i];
+    acc[0] += coord(x, nx, hx, periodic) * dr;
+    acc[1] += coord(y, ny, hy, periodic) * dr;
+    acc[2] += coord(z, nz, hz, periodic) * dr;
+    acc[3] += rho[i];
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int j = 0; j < 4; ++j) {
+    double v = acc[j];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[warp][j] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double v = 0;
+    for (int w = 0; w < kRedThreads / 32; ++w) v += red[w][threadIdx.x];
+    partials[blockIdx.x * 4 + threadIdx.x] = v;
+  }
+}
+
+__global__ void k_dipole_final(const double* partials, int nblocks, double dV, double* out) {
+  if (threadIdx.x < 4) {
+    double v = 0;
+    for (int b = 0; b < nblocks; ++b) v += partials[b * 4 + threadIdx.x];
+    out[3 + threadIdx.x] = (threadIdx.x < 3) ? -v * dV : v * dV;   // out[3..5] = d, out[6] = N
+  }
+}
+
+__global__ void k_reduce_current(const double* __restrict__ obs, int nk, int norb,
+                                 const double* __restrict__ kw, double inv_omega, int periodic,
+                                 double* out) {
+  if (threadIdx.x < 3) {
+    double J = 0.0;
+    if (periodic) {
+      for (int k = 0; k < nk; ++k) {
+        double s = 0.0;
+        for (int n = 0; n < norb; ++n) {
+          const double* o = obs + ((size_t)k * norb + n) * 8;
+          s += o[1 + threadIdx.x] + o[4 + threadIdx.x];
+        }
+        J += 2.0 * kw[k] * s;
+      }
+    }
+    out[threadIdx.x] = -J * inv_omega;
+  }
+}
+
+int grid_for(long long n, int threads) {
+  long long b = (n + threads - 1) / threads;
+  if (b > 152 * 16) b = 152 * 16;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+}  // namespace
+
+cudaError_t launch_fft_axis(double2* data, const int dims[3], int axis, int dir, const double2* tw,
+                            const int* radices, int nrad, cudaStream_t s) {
+  const int n = dims[axis];
+  if (nrad > kMaxRadices) return cudaErrorInvalidValue;
+  FftPlanArgs plan;
+  plan.nrad = nrad;
+  for (int i = 0; i < nrad; ++i) plan.rad[i] = radices[i];
+  const long long total = (long long)dims[0] * dims[1] * dims[2];
+  const int nlines = (int)(total / n);
+  long long inner, outer, estride;
+  if (axis == 0) { inner = 1; outer = dims[0]; estride = 1; }
+  else if (axis == 1) { inner = dims[0]; outer = (long long)dims[0] * dims[1]; estride = dims[0]; }
+  else { inner = (long long)dims[0] * dims[1]; outer = 0; estride = inner; }
+  int LB = 16;
+  while (LB > 1 && (size_t)(2 * LB + 1) * n * sizeof(double2) > 96 * 1024) LB /= 2;
+  const size_t smem = (size_t)(2 * LB + 1) * n * sizeof(double2);
+  cudaError_t e = cudaFuncSetAttribute(k_fft_lines, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  const int grid = (nlines + LB - 1) / LB;
+  k_fft_lines<<<grid, kFftThreads, smem, s>>>(data, n, nlines, LB, inner, outer, estride,
+                                              axis == 0 ? 1 : 0, tw, plan, dir);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_real(const double* src, const int n[3], double2* dst, const int m[3],
+                             cudaStream_t s) {
+  const long long tot = (long long)m[0] * m[1] * m[2];
+  k_pack_real<<<grid_for(tot, 256), 256, 0, s>>>(src, n[0], n[1], n[2], dst, m[0], m[1], m[2]);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_poisson_scale_periodic(double2* data, const int n[3], const double h[3],
+                                          cudaStream_t s) {
+  const long long tot = (long long)n[0] * n[1] * n[2];
+  k_poisson_periodic<<<grid_for(tot, 256), 256, 0, s>>>(data, n[0], n[1], n[2], n[0] * h[0],
+                                                         n[1] * h[1], n[2] * h[2]);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_by_real(double2* data, const double* ghat, double scale, size_t count,
+                                 cudaStream_t s) {
+  k_scale_by_real<<<grid_for((long long)count, 256), 256, 0, s>>>(data, ghat, scale, (long long)count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hxc_epilogue(const double2* fft, const int m[3], const double* rho,
+                                const int n[3], double scale_h, int hartree, int xc, double* vhxc,
+                                cudaStream_t s) {
+  const long long tot = (long long)n[0] * n[1] * n[2];
+  k_hxc_epilogue<<<grid_for(tot, 256), 256, 0, s>>>(fft, m[0], m[1], rho, n[0], n[1], n[2],
+                                                     scale_h, hartree, xc, vhxc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_combine_potential(const double* vloc, const double* v1, double a,
+                                     const double* v2, double b, double* v64, float* v32, int npts,
+                                     cudaStream_t s) {
+  k_combine<<<grid_for(npts, 256), 256, 0, s>>>(vloc, v1, a, v2, b, v64, v32, npts);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_density(const typename Cplx<T>::type* psi, int nk, int norb, int npts,
+                           const double* kw, double* rho, cudaStream_t s) {
+  k_density<<<grid_for(npts, 256), 256, 0, s>>>(psi, nk, norb, npts, kw, rho);
+  return cudaGetLastError();
+}
+template cudaError_t launch_density<float>(const float2*, int, int, int, const double*, double*, cudaStream_t);
+template cudaError_t launch_density<double>(const double2*, int, int, int, const double*, double*, cudaStream_t);
+
+template <typename T>
+cudaError_t launch_kick(typename Cplx<T>::type* psi, int norb_tot, const int n[3], const double h[3],
+                        int periodic, const double kappa[3], cudaStream_t s) {
+  const long long tot = (long long)n[0] * n[1] * n[2] * norb_tot;
+  k_kick<<<grid_for(tot, 256), 256, 0, s>>>(psi, norb_tot, n[0], n[1], n[2], h[0], h[1], h[2],
+                                            periodic, kappa[0], kappa[1], kappa[2]);
+  return cudaGetLastError();
+}
+template cudaError_t launch_kick<float>(float2*, int, const int*, const double*, int, const double*, cudaStream_t);
+template cudaError_t launch_kick<double>(double2*, int, const int*, const double*, int, const double*, cudaStream_t);
+
+cudaError_t launch_vloc_isolated(double* v, const int n[3], const double h[3], const double* atoms,
+                                 int natom, cudaStream_t s) {
+  const long long tot = (long long)n[0] * n[1] * n[2];
+  k_vloc_isolated<<<grid_for(tot, 256), 256, 0, s>>>(v, n[0], n[1], n[2], h[0], h[1], h[2], atoms, natom);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hockney_kernel(double2* g, const int m[3], const int n[3], const double h[3],
+                                  double g0, cudaStream_t s) {
+  const long long tot = (long long)m[0] * m[1] * m[2];
+  k_hockney<<<grid_for(tot, 256), 256, 0, s>>>(g, m[0], m[1], m[2], n[0], n[1], n[2], h[0], h[1], h[2], g0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_real_part(const double2* src, double* dst, size_t count, double scale, cudaStream_t s) {
+  k_real_part<<<grid_for((long long)count, 256), 256, 0, s>>>(src, dst, (long long)count, scale);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_f32_from_f64(const double* src, float* dst, size_t count, cudaStream_t s) {
+  k_f32<<<grid_for((long long)count, 256), 256, 0, s>>>(src, dst, (long long)count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dipole(const double* rho, const double* rho0, const int n[3], const double h[3],
+                          int periodic, double* partials, int nblocks, double* out, cudaStream_t s) {
+  k_dipole_partial<<<nblocks, kRedThreads, 0, s>>>(rho, rho0, n[0], n[1], n[2], h[0], h[1], h[2],
+                                                   periodic, partials);
+  k_dipole_final<<<1, 32, 0, s>>>(partials, nblocks, h[0] * h[1] * h[2], out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_current(const double* orb_obs, int nk, int norb, const double* kw,
+                                  double inv_omega, int periodic, double* out, cudaStream_t s) {
+  k_reduce_current<<<1, 32, 0, s>>>(orb_obs, nk, norb, kw, inv_omega, periodic, out);
+  return cudaGetLastError();
+}
+
+}  // namespace tdks

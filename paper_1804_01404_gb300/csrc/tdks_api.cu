@@ -1,0 +1,629 @@
+// C ABI entry points of libtdks: context set-up and the orchestration of one TDKS step.
+// All arithmetic of the step runs in the kernels of k_orbital.cu and k_grid.cu; this file only
+// validates arguments, owns device buffers and enqueues launches on the context's stream.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "tdks_internal.h"
+
+using namespace tdks;
+
+namespace {
+thread_local std::string g_err;
+
+tdks_status fail(tdks_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+}  // namespace
+
+#define TDKS_CUDA(call)                                                                    \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return fail(TDKS_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));         \
+  } while (0)
+
+#define TDKS_TRY(expr)                      \
+  do {                                      \
+    tdks_status s_ = (expr);                \
+    if (s_ != TDKS_OK) return s_;           \
+  } while (0)
+
+struct tdks_ctx {
+  tdks_grid grid{};
+  int npts = 0, nk = 0, norb = 0;
+  tdks_options opt{};
+  double dV = 0, omega = 0;
+  std::vector<double> kpts, kw;
+  cudaStream_t stream = nullptr;
+  // field
+  int field_kind = TDKS_FIELD_NONE;
+  double A0[3] = {0, 0, 0}, f_omega = 0, f_T = 0, f_cep = 0;
+  // projector tables
+  int natom = 0, nsph = 0;
+  int *d_atom_off = nullptr, *d_sph_idx = nullptr, *d_pt_off = nullptr, *d_pt_ent = nullptr,
+      *d_ent_atom = nullptr;
+  double *d_beta64 = nullptr, *d_d64 = nullptr, *d_E64 = nullptr;
+  float *d_beta32 = nullptr, *d_d32 = nullptr, *d_E32 = nullptr;
+  double *d_kpts = nullptr, *d_kw = nullptr;
+  // grid arrays
+  double *d_vloc = nullptr, *d_vhxc = nullptr, *d_vpred = nullptr, *d_rho = nullptr,
+         *d_rho0 = nullptr, *d_rho_tmp = nullptr, *d_v64 = nullptr;
+  float* d_v32 = nullptr;
+  void* d_scratch = nullptr;     // [norb_tot][npts] complex, only for cells whose two copies exceed smem
+  bool have_rho0 = false, have_potential = false;
+  // FFT
+  int m[3] = {0, 0, 0};
+  std::vector<int> rad[3];
+  double2* d_fft = nullptr;
+  double2* d_tw[3] = {nullptr, nullptr, nullptr};
+  double* d_ghat = nullptr;
+  // observables
+  double* d_orb_obs = nullptr;   // [nk*norb*8]
+  double* d_step_obs = nullptr;  // [8]: J[3], d[3], N
+  double* d_partials = nullptr;
+  int red_blocks = 0;
+  std::vector<void*> allocs;
+  // profiling
+  bool profiling = false;
+  long long launches = 0;
+  long long calls[TDKS_NPHASE] = {0};
+  double ms[TDKS_NPHASE] = {0};
+  struct Rec { int phase; cudaEvent_t a, b; };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> event_pool;
+};
+
+namespace {
+
+template <typename P>
+tdks_status dalloc(tdks_ctx* c, P** p, size_t count) {
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(P));
+  if (e != cudaSuccess) return fail(TDKS_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  c->allocs.push_back((void*)*p);
+  return TDKS_OK;
+}
+
+template <typename P>
+tdks_status upload(tdks_ctx* c, P** p, const std::vector<P>& h) {
+  TDKS_TRY(dalloc(c, p, h.size()));
+  if (!h.empty()) TDKS_CUDA(cudaMemcpyAsync(*p, h.data(), h.size() * sizeof(P), cudaMemcpyHostToDevice, c->stream));
+  return TDKS_OK;
+}
+
+void field_at(const tdks_ctx* c, double t, double out[3]) {
+  out[0] = out[1] = out[2] = 0.0;
+  if (!c->grid.periodic) return;
+  if (c->field_kind == TDKS_FIELD_STEP) {
+    if (t > 0.0) for (int a = 0; a < 3; ++a) out[a] = c->A0[a];
+  } else if (c->field_kind == TDKS_FIELD_PULSE) {
+    if (t > 0.0 && t < c->f_T) {
+      const double env = std::cos(kPi * (t - 0.5 * c->f_T) / c->f_T);
+      const double s = std::sin(-c->f_omega * (t - 0.5 * c->f_T) - 2.0 * kPi * c->f_cep);
+      for (int a = 0; a < 3; ++a) out[a] = c->A0[a] * env * env * s;
+    }
+  }
+}
+
+template <typename T>
+OrbArgs<T> make_args(const tdks_ctx* c, const void* in, void* out, const T* V, const double Ap[3],
+                     double dt, double* rho, int write_out) {
+  OrbArgs<T> a;
+  std::memset(&a, 0, sizeof(a));
+  using C = typename Cplx<T>::type;
+  a.psi_in = static_cast<const C*>(in);
+  a.psi_out = static_cast<C*>(out);
+  a.V = V;
+  a.nx = c->grid.n[0]; a.ny = c->grid.n[1]; a.nz = c->grid.n[2];
+  a.npts = c->npts;
+  a.periodic = c->grid.periodic;
+  for (int m = 0; m < 5; ++m) {
+    a.c2x[m] = (T)(-0.5 * kFD2[m] / (c->grid.h[0] * c->grid.h[0]));
+    a.c2y[m] = (T)(-0.5 * kFD2[m] / (c->grid.h[1] * c->grid.h[1]));
+    a.c2z[m] = (T)(-0.5 * kFD2[m] / (c->grid.h[2] * c->grid.h[2]));
+  }
+  for (int m = 0; m < 4; ++m) {
+    a.d1x[m] = (T)(kFD1[m] / c->grid.h[0]);
+    a.d1y[m] = (T)(kFD1[m] / c->grid.h[1]);
+    a.d1z[m] = (T)(kFD1[m] / c->grid.h[2]);
+  }
+  a.norb = c->norb; a.nk = c->nk;
+  a.kpts = c->d_kpts;
+  for (int i = 0; i < 3; ++i) a.Ap[i] = Ap ? Ap[i] : 0.0;
+  a.natom = c->natom; a.nsph = c->nsph;
+  a.atom_off = c->d_atom_off; a.sph_idx = c->d_sph_idx;
+  if (sizeof(T) == 8) {
+    a.sph_beta = (const T*)c->d_beta64; a.sph_d = (const T*)c->d_d64; a.atomE = (const T*)c->d_E64;
+  } else {
+    a.sph_beta = (const T*)c->d_beta32; a.sph_d = (const T*)c->d_d32; a.atomE = (const T*)c->d_E32;
+  }
+  a.pt_off = c->d_pt_off; a.pt_ent = c->d_pt_ent; a.ent_atom = c->d_ent_atom;
+  a.dV = (T)c->dV;
+  a.dt = (T)dt;
+  a.rho = rho;
+  a.kw = c->d_kw;
+  a.write_out = write_out;
+  return a;
+}
+
+bool is_f32(const tdks_ctx* c) { return c->opt.precision == TDKS_F32; }
+
+cudaEvent_t take_event(tdks_ctx* c) {
+  if (!c->event_pool.empty()) {
+    cudaEvent_t e = c->event_pool.back();
+    c->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// RAII phase marker: records an event pair on the context stream when profiling is on.
+struct Phase {
+  tdks_ctx* c;
+  int phase;
+  cudaEvent_t a = nullptr;
+  Phase(tdks_ctx* c_, int p) : c(c_), phase(p) {
+    c->calls[p] += 1;
+    if (c->profiling && (a = take_event(c)) != nullptr) cudaEventRecord(a, c->stream);
+  }
+  ~Phase() {
+    if (!a) return;
+    cudaEvent_t b = take_event(c);
+    if (!b) { c->event_pool.push_back(a); return; }
+    cudaEventRecord(b, c->stream);
+    c->recs.push_back({phase, a, b});
+  }
+};
+
+// V used by the next orbital kernel: V_loc + a * V_Hxc + b * V_pred
+tdks_status set_step_potential(tdks_ctx* c, double a, const double* v2, double b) {
+  Phase ph(c, 5);
+  TDKS_CUDA(launch_combine_potential(c->d_vloc, c->d_vhxc, a, v2, b, c->d_v64,
+                                     is_f32(c) ? c->d_v32 : nullptr, c->npts, c->stream));
+  c->launches += 1;
+  return TDKS_OK;
+}
+
+tdks_status orbital_kernel(tdks_ctx* c, int mode, const void* in, void* out, const double Ap[3],
+                           double dt, double* rho, int write_out) {
+  Phase ph(c, mode == 0 ? 2 : (write_out ? 1 : 0));
+  c->launches += 1;
+  if (is_f32(c)) {
+    auto a = make_args<float>(c, in, out, c->d_v32, Ap, dt, rho, write_out);
+    TDKS_CUDA(launch_smem_orbital<float>(a, mode, static_cast<float2*>(c->d_scratch), c->stream));
+  } else {
+    auto a = make_args<double>(c, in, out, c->d_v64, Ap, dt, rho, write_out);
+    TDKS_CUDA(launch_smem_orbital<double>(a, mode, static_cast<double2*>(c->d_scratch), c->stream));
+  }
+  return TDKS_OK;
+}
+
+tdks_status density(tdks_ctx* c, const void* u, double* rho) {
+  c->launches += 1;
+  if (is_f32(c))
+    TDKS_CUDA(launch_density<float>(static_cast<const float2*>(u), c->nk, c->norb, c->npts, c->d_kw, rho, c->stream));
+  else
+    TDKS_CUDA(launch_density<double>(static_cast<const double2*>(u), c->nk, c->norb, c->npts, c->d_kw, rho, c->stream));
+  return TDKS_OK;
+}
+
+tdks_status fft3d(tdks_ctx* c, int dir) {
+  for (int ax = 0; ax < 3; ++ax)
+    TDKS_CUDA(launch_fft_axis(c->d_fft, c->m, ax, dir, c->d_tw[ax], c->rad[ax].data(),
+                              (int)c->rad[ax].size(), c->stream));
+  c->launches += 3;
+  return TDKS_OK;
+}
+
+// vhxc = V_H[rho] + V_x[rho]
+tdks_status hxc(tdks_ctx* c, const double* rho, double* vhxc) {
+  Phase ph(c, 3);
+  c->launches += c->opt.hartree ? 3 : 1;   // pack, scale, epilogue (+ 6 FFT passes counted in fft3d)
+  if (c->opt.hartree) {
+    TDKS_CUDA(launch_pack_real(rho, c->grid.n, c->d_fft, c->m, c->stream));
+    TDKS_TRY(fft3d(c, -1));
+    if (c->grid.periodic) {
+      TDKS_CUDA(launch_poisson_scale_periodic(c->d_fft, c->m, c->grid.h, c->stream));
+    } else {
+      const double npad = (double)c->m[0] * c->m[1] * c->m[2];
+      TDKS_CUDA(launch_scale_by_real(c->d_fft, c->d_ghat, c->dV / npad, (size_t)npad, c->stream));
+    }
+    TDKS_TRY(fft3d(c, +1));
+  }
+  TDKS_CUDA(launch_hxc_epilogue(c->d_fft, c->m, rho, c->grid.n, 1.0, c->opt.hartree, c->opt.xc,
+                                vhxc, c->stream));
+  return TDKS_OK;
+}
+
+tdks_status orbital_observables(tdks_ctx* c, const void* u, const double Ap[3]) {
+  c->launches += is_f32(c) ? 2 : 1;
+  if (is_f32(c)) {
+    TDKS_CUDA(launch_f32_from_f64(c->d_vloc, c->d_v32, c->npts, c->stream));
+    auto a = make_args<float>(c, u, nullptr, c->d_v32, Ap, 0.0, nullptr, 0);
+    TDKS_CUDA(launch_orbital_observables<float>(a, c->d_orb_obs, c->stream));
+  } else {
+    auto a = make_args<double>(c, u, nullptr, c->d_vloc, Ap, 0.0, nullptr, 0);
+    TDKS_CUDA(launch_orbital_observables<double>(a, c->d_orb_obs, c->stream));
+  }
+  return TDKS_OK;
+}
+
+tdks_status check_ctx(const tdks_ctx* c) {
+  if (!c) return fail(TDKS_EINVAL, "null context");
+  return TDKS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* tdks_last_error(void) { return g_err.c_str(); }
+int tdks_abi_version(void) { return TDKS_ABI_VERSION; }
+
+tdks_status tdks_init(const tdks_grid* grid, const tdks_cell* cell, const tdks_atom* atoms,
+                      int natom, const tdks_projector* projectors, int nproj, const double* kpts,
+                      const double* kw, int nk, int norb, const tdks_options* opts, void* stream,
+                      tdks_ctx** out) {
+  if (!out) return fail(TDKS_EINVAL, "out is null");
+  *out = nullptr;
+  if (!grid || !opts || !kpts || !kw) return fail(TDKS_EINVAL, "null grid, options or k-points");
+  if (natom < 0 || (natom > 0 && !atoms)) return fail(TDKS_EINVAL, "bad atom list");
+  if (nproj < 0 || (nproj > 0 && !projectors)) return fail(TDKS_EINVAL, "bad projector list");
+  if (nk < 1 || norb < 1) return fail(TDKS_EINVAL, "nk and norb must be >= 1");
+  if (opts->precision != TDKS_F64 && opts->precision != TDKS_F32)
+    return fail(TDKS_EINVAL, "precision must be TDKS_F64 or TDKS_F32");
+  for (int a = 0; a < 3; ++a) {
+    if (grid->n[a] < 4 || grid->n[a] > 1024) return fail(TDKS_EINVAL, "grid points per axis must be in [4, 1024]");
+    if (!(grid->h[a] > 0.0)) return fail(TDKS_EINVAL, "grid spacing must be positive");
+  }
+  if (grid->periodic) {
+    if (!cell) return fail(TDKS_EINVAL, "periodic grid needs a cell");
+    for (int a = 0; a < 3; ++a)
+      if (std::fabs(cell->L[a] - grid->n[a] * grid->h[a]) > 1e-9 * cell->L[a])
+        return fail(TDKS_EINVAL, "cell length differs from n*h");
+  }
+  double wsum = 0.0;
+  for (int k = 0; k < nk; ++k) wsum += kw[k];
+  if (std::fabs(wsum - 1.0) > 1e-9) return fail(TDKS_EINVAL, "k-point weights must sum to 1");
+
+  tdks_ctx* c = new tdks_ctx();
+  c->grid = *grid;
+  c->npts = grid->n[0] * grid->n[1] * grid->n[2];
+  c->nk = nk;
+  c->norb = norb;
+  c->opt = *opts;
+  c->dV = grid->h[0] * grid->h[1] * grid->h[2];
+  c->omega = c->dV * c->npts;
+  c->kpts.assign(kpts, kpts + 3 * nk);
+  c->kw.assign(kw, kw + nk);
+  c->stream = static_cast<cudaStream_t>(stream);
+
+  auto bail = [&](tdks_status s) { tdks_destroy(c); return s; };
+
+  ProjectorTables T;
+  std::string err;
+  if (!build_projector_tables(*grid, atoms, natom, projectors, nproj, T, err))
+    return bail(fail(TDKS_EINVAL, err));
+  c->natom = T.natom;
+  c->nsph = (int)T.idx.size();
+  const bool fits = is_f32(c) ? smem_orbital_fits<float>(c->npts, c->nsph, c->natom)
+                              : smem_orbital_fits<double>(c->npts, c->nsph, c->natom);
+  if (!fits) return bail(fail(TDKS_EUNSUPPORTED, "grid too large for the shared-memory orbital kernels"));
+
+  tdks_status s;
+  if ((s = upload(c, &c->d_atom_off, T.atom_off)) != TDKS_OK) return bail(s);
+  if ((s = upload(c, &c->d_sph_idx, T.idx)) != TDKS_OK) return bail(s);
+  if ((s = upload(c, &c->d_pt_off, T.pt_off)) != TDKS_OK) return bail(s);
+  if ((s = upload(c, &c->d_pt_ent, T.pt_ent)) != TDKS_OK) return bail(s);
+  if ((s = upload(c, &c->d_ent_atom, T.ent_atom)) != TDKS_OK) return bail(s);
+  if ((s = upload(c, &c->d_beta64, T.beta)) != TDKS_OK) return bail(s);
+  if ((s = upload(c, &c->d_d64, T.d)) != TDKS_OK) return bail(s);
+  if ((s = upload(c, &c->d_E64, T.E)) != TDKS_OK) return bail(s);
+  {
+    std::vector<float> b(T.beta.begin(), T.beta.end()), d(T.d.begin(), T.d.end()), E(T.E.begin(), T.E.end());
+    if ((s = upload(c, &c->d_beta32, b)) != TDKS_OK) return bail(s);
+    if ((s = upload(c, &c->d_d32, d)) != TDKS_OK) return bail(s);
+    if ((s = upload(c, &c->d_E32, E)) != TDKS_OK) return bail(s);
+  }
+  if ((s = upload(c, &c->d_kpts, c->kpts)) != TDKS_OK) return bail(s);
+  if ((s = upload(c, &c->d_kw, c->kw)) != TDKS_OK) return bail(s);
+
+  const size_t np = c->npts;
+  double** grids[] = {&c->d_vloc, &c->d_vhxc, &c->d_vpred, &c->d_rho, &c->d_rho0, &c->d_rho_tmp, &c->d_v64};
+  for (double** g : grids) {
+    if ((s = dalloc(c, g, np)) != TDKS_OK) return bail(s);
+    if (cudaMemsetAsync(*g, 0, np * sizeof(double), c->stream) != cudaSuccess)
+      return bail(fail(TDKS_ECUDA, "memset"));
+  }
+  if ((s = dalloc(c, &c->d_v32, np)) != TDKS_OK) return bail(s);
+  const bool scratch = is_f32(c) ? smem_orbital_needs_scratch<float>(c->npts, c->nsph, c->natom)
+                                 : smem_orbital_needs_scratch<double>(c->npts, c->nsph, c->natom);
+  if (scratch) {
+    const size_t csz = is_f32(c) ? sizeof(float2) : sizeof(double2);
+    unsigned char* p = nullptr;
+    if ((s = dalloc(c, &p, csz * np * (size_t)nk * norb)) != TDKS_OK) return bail(s);
+    c->d_scratch = p;
+  }
+  if ((s = dalloc(c, &c->d_orb_obs, (size_t)nk * norb * 8)) != TDKS_OK) return bail(s);
+  if ((s = dalloc(c, &c->d_step_obs, 8)) != TDKS_OK) return bail(s);
+  c->red_blocks = 304;
+  if ((s = dalloc(c, &c->d_partials, (size_t)c->red_blocks * 4)) != TDKS_OK) return bail(s);
+  cudaMemsetAsync(c->d_step_obs, 0, 8 * sizeof(double), c->stream);
+
+  // FFT set-up: periodic transforms are n^3, isolated ones (2n)^3 (zero padding)
+  for (int a = 0; a < 3; ++a) {
+    c->m[a] = grid->periodic ? grid->n[a] : 2 * grid->n[a];
+    if (!fft_radices(c->m[a], c->rad[a]))
+      return bail(fail(TDKS_EUNSUPPORTED, "FFT length with a prime factor above 31"));
+    std::vector<double2> tw(c->m[a]);
+    for (int t = 0; t < c->m[a]; ++t)
+      tw[t] = double2{std::cos(2.0 * kPi * t / c->m[a]), -std::sin(2.0 * kPi * t / c->m[a])};
+    if ((s = upload(c, &c->d_tw[a], tw)) != TDKS_OK) return bail(s);
+  }
+  const size_t nfft = (size_t)c->m[0] * c->m[1] * c->m[2];
+  if ((s = dalloc(c, &c->d_fft, nfft)) != TDKS_OK) return bail(s);
+
+  // local potential
+  if (grid->periodic) {
+    std::vector<double> vg;
+    local_potential_gspace(*grid, atoms, natom, vg);
+    if (cudaMemcpyAsync(c->d_fft, vg.data(), vg.size() * sizeof(double), cudaMemcpyHostToDevice,
+                        c->stream) != cudaSuccess)
+      return bail(fail(TDKS_ECUDA, "upload V(G)"));
+    if ((s = fft3d(c, +1)) != TDKS_OK) return bail(s);
+    if (launch_real_part(c->d_fft, c->d_vloc, np, 1.0, c->stream) != cudaSuccess)
+      return bail(fail(TDKS_ECUDA, "real part"));
+  } else {
+    std::vector<double> at(5 * (size_t)natom);
+    for (int i = 0; i < natom; ++i) {
+      for (int a = 0; a < 3; ++a) at[5 * i + a] = atoms[i].R[a];
+      at[5 * i + 3] = atoms[i].Z;
+      at[5 * i + 4] = atoms[i].sigma;
+      if (!(atoms[i].sigma > 0.0)) return bail(fail(TDKS_EINVAL, "atom sigma must be positive"));
+    }
+    double* d_at = nullptr;
+    if ((s = upload(c, &d_at, at)) != TDKS_OK) return bail(s);
+    if (launch_vloc_isolated(c->d_vloc, grid->n, grid->h, d_at, natom, c->stream) != cudaSuccess)
+      return bail(fail(TDKS_ECUDA, "vloc"));
+    // Hockney Green's function spectrum
+    const double g0 = cell_mean_inverse_distance(grid->h[0], grid->h[1], grid->h[2]);
+    if (launch_hockney_kernel(c->d_fft, c->m, grid->n, grid->h, g0, c->stream) != cudaSuccess)
+      return bail(fail(TDKS_ECUDA, "hockney"));
+    if ((s = fft3d(c, -1)) != TDKS_OK) return bail(s);
+    if ((s = dalloc(c, &c->d_ghat, nfft)) != TDKS_OK) return bail(s);
+    if (launch_real_part(c->d_fft, c->d_ghat, nfft, 1.0, c->stream) != cudaSuccess)
+      return bail(fail(TDKS_ECUDA, "ghat"));
+  }
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return bail(fail(TDKS_ECUDA, std::string("init: ") + cudaGetErrorString(cudaGetLastError())));
+  *out = c;
+  return TDKS_OK;
+}
+
+void tdks_destroy(tdks_ctx* c) {
+  if (!c) return;
+  if (c->stream || !c->allocs.empty()) cudaStreamSynchronize(c->stream);
+  for (auto& r : c->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+  for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
+  for (void* p : c->allocs) cudaFree(p);
+  delete c;
+}
+
+tdks_status tdks_set_field(tdks_ctx* c, int kind, const double A0[3], double omega, double T, double cep) {
+  TDKS_TRY(check_ctx(c));
+  if (kind < TDKS_FIELD_NONE || kind > TDKS_FIELD_PULSE) return fail(TDKS_EINVAL, "unknown field kind");
+  if (kind != TDKS_FIELD_NONE && !A0) return fail(TDKS_EINVAL, "null A0");
+  if (kind == TDKS_FIELD_PULSE && !(T > 0.0)) return fail(TDKS_EINVAL, "pulse duration must be positive");
+  c->field_kind = kind;
+  for (int a = 0; a < 3; ++a) c->A0[a] = A0 ? A0[a] : 0.0;
+  c->f_omega = omega;
+  c->f_T = T;
+  c->f_cep = cep;
+  return TDKS_OK;
+}
+
+tdks_status tdks_kick(tdks_ctx* c, void* u, const double kappa[3]) {
+  TDKS_TRY(check_ctx(c));
+  if (!u || !kappa) return fail(TDKS_EINVAL, "null argument");
+  const int tot = c->nk * c->norb;
+  if (is_f32(c))
+    TDKS_CUDA(launch_kick<float>(static_cast<float2*>(u), tot, c->grid.n, c->grid.h, c->grid.periodic, kappa, c->stream));
+  else
+    TDKS_CUDA(launch_kick<double>(static_cast<double2*>(u), tot, c->grid.n, c->grid.h, c->grid.periodic, kappa, c->stream));
+  return TDKS_OK;
+}
+
+tdks_status tdks_update_potential(tdks_ctx* c, const void* u) {
+  TDKS_TRY(check_ctx(c));
+  if (!u) return fail(TDKS_EINVAL, "null orbitals");
+  TDKS_TRY(density(c, u, c->d_rho));
+  TDKS_TRY(hxc(c, c->d_rho, c->d_vhxc));
+  if (!c->have_rho0) {
+    TDKS_CUDA(cudaMemcpyAsync(c->d_rho0, c->d_rho, c->npts * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    c->have_rho0 = true;
+  }
+  c->have_potential = true;
+  return TDKS_OK;
+}
+
+tdks_status tdks_hpsi(tdks_ctx* c, const void* u, void* hu, const double Ap[3]) {
+  TDKS_TRY(check_ctx(c));
+  if (!u || !hu) return fail(TDKS_EINVAL, "null orbitals");
+  if (u == hu) return fail(TDKS_EINVAL, "u and hu must not alias");
+  TDKS_TRY(set_step_potential(c, 1.0, nullptr, 0.0));
+  return orbital_kernel(c, 0, u, hu, Ap, 0.0, nullptr, 1);
+}
+
+tdks_status tdks_taylor_step(tdks_ctx* c, void* u, double dt, const double Ap[3]) {
+  TDKS_TRY(check_ctx(c));
+  if (!u) return fail(TDKS_EINVAL, "null orbitals");
+  TDKS_TRY(set_step_potential(c, 1.0, nullptr, 0.0));
+  return orbital_kernel(c, 1, u, u, Ap, dt, nullptr, 1);
+}
+
+tdks_status tdks_step(tdks_ctx* c, void* u, double t, double dt) {
+  TDKS_TRY(check_ctx(c));
+  if (!u) return fail(TDKS_EINVAL, "null orbitals");
+  if (!c->have_potential) return fail(TDKS_EINVAL, "call tdks_update_potential before tdks_step");
+  double Amid[3], Aend[3];
+  field_at(c, t + 0.5 * dt, Amid);
+  field_at(c, t + dt, Aend);
+  const size_t gb = c->npts * sizeof(double);
+  if (c->opt.pc && (c->opt.hartree || c->opt.xc)) {
+    // predictor: T4 with V(t); only its density is kept
+    TDKS_TRY(set_step_potential(c, 1.0, nullptr, 0.0));
+    {
+      Phase ph(c, 5);
+      TDKS_CUDA(cudaMemsetAsync(c->d_rho_tmp, 0, gb, c->stream));
+    }
+    TDKS_TRY(orbital_kernel(c, 1, u, u, Amid, dt, c->d_rho_tmp, 0));
+    TDKS_TRY(hxc(c, c->d_rho_tmp, c->d_vpred));
+    // corrector: T4 with the mid-point potential
+    TDKS_TRY(set_step_potential(c, 0.5, c->d_vpred, 0.5));
+  } else {
+    TDKS_TRY(set_step_potential(c, 1.0, nullptr, 0.0));
+  }
+  {
+    Phase ph(c, 5);
+    TDKS_CUDA(cudaMemsetAsync(c->d_rho, 0, gb, c->stream));
+  }
+  TDKS_TRY(orbital_kernel(c, 1, u, u, Amid, dt, c->d_rho, 1));
+  TDKS_TRY(hxc(c, c->d_rho, c->d_vhxc));
+  // observables at t + dt
+  Phase ph(c, 4);
+  c->launches += c->grid.periodic ? 3 : 2;   // reduce_current (or memset) + dipole partial + final
+  if (c->grid.periodic) {
+    TDKS_TRY(orbital_observables(c, u, Aend));
+    TDKS_CUDA(launch_reduce_current(c->d_orb_obs, c->nk, c->norb, c->d_kw, 1.0 / c->omega, 1,
+                                    c->d_step_obs, c->stream));
+  } else {
+    TDKS_CUDA(cudaMemsetAsync(c->d_step_obs, 0, 3 * sizeof(double), c->stream));
+  }
+  TDKS_CUDA(launch_dipole(c->d_rho, c->d_rho0, c->grid.n, c->grid.h, c->grid.periodic,
+                          c->d_partials, c->red_blocks, c->d_step_obs, c->stream));
+  return TDKS_OK;
+}
+
+tdks_status tdks_read_step_observables(tdks_ctx* c, tdks_obs* o) {
+  TDKS_TRY(check_ctx(c));
+  if (!o) return fail(TDKS_EINVAL, "null output");
+  double h[8];
+  TDKS_CUDA(cudaMemcpyAsync(h, c->d_step_obs, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+  TDKS_CUDA(cudaStreamSynchronize(c->stream));
+  std::memset(o, 0, sizeof(*o));
+  for (int a = 0; a < 3; ++a) { o->J[a] = h[a]; o->dipole[a] = h[3 + a]; }
+  o->n_elec = h[6];
+  return TDKS_OK;
+}
+
+tdks_status tdks_observables(tdks_ctx* c, const void* u, const double Ap[3], tdks_obs* o) {
+  TDKS_TRY(check_ctx(c));
+  if (!u || !o) return fail(TDKS_EINVAL, "null argument");
+  double A[3] = {0, 0, 0};
+  if (Ap && c->grid.periodic) for (int a = 0; a < 3; ++a) A[a] = Ap[a];
+  TDKS_TRY(density(c, u, c->d_rho_tmp));
+  const double* r0 = c->have_rho0 ? c->d_rho0 : c->d_rho_tmp;
+  TDKS_CUDA(launch_dipole(c->d_rho_tmp, r0, c->grid.n, c->grid.h, c->grid.periodic, c->d_partials,
+                          c->red_blocks, c->d_step_obs, c->stream));
+  TDKS_TRY(orbital_observables(c, u, A));
+  const size_t no = (size_t)c->nk * c->norb;
+  std::vector<double> ob(no * 8);
+  double so[8];
+  TDKS_CUDA(cudaMemcpyAsync(ob.data(), c->d_orb_obs, ob.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  TDKS_CUDA(cudaMemcpyAsync(so, c->d_step_obs, sizeof(so), cudaMemcpyDeviceToHost, c->stream));
+  TDKS_CUDA(cudaStreamSynchronize(c->stream));
+  std::memset(o, 0, sizeof(*o));
+  o->norm_min = 1e300;
+  o->norm_max = -1e300;
+  double J[3] = {0, 0, 0}, eb = 0.0;
+  bool finite = true;
+  for (int k = 0; k < c->nk; ++k) {
+    double js[3] = {0, 0, 0}, es = 0.0;
+    for (int n = 0; n < c->norb; ++n) {
+      const double* v = &ob[((size_t)k * c->norb + n) * 8];
+      for (int a = 0; a < 3; ++a) js[a] += v[1 + a] + v[4 + a];
+      es += v[7];
+      o->norm_min = std::fmin(o->norm_min, v[0]);
+      o->norm_max = std::fmax(o->norm_max, v[0]);
+      if (!std::isfinite(v[0])) finite = false;
+    }
+    for (int a = 0; a < 3; ++a) J[a] += 2.0 * c->kw[k] * js[a];
+    eb += 2.0 * c->kw[k] * es;
+  }
+  for (int a = 0; a < 3; ++a) {
+    o->J[a] = c->grid.periodic ? -J[a] / c->omega : 0.0;
+    o->dipole[a] = so[3 + a];
+  }
+  o->e_band = eb;
+  o->n_elec = so[6];
+  if (!finite) return fail(TDKS_ENONFINITE, "non-finite orbital norm");
+  return TDKS_OK;
+}
+
+tdks_status tdks_get_grid_array(tdks_ctx* c, int which, double* dst) {
+  TDKS_TRY(check_ctx(c));
+  if (!dst) return fail(TDKS_EINVAL, "null destination");
+  const double* src = nullptr;
+  switch (which) {
+    case 0: src = c->d_vloc; break;
+    case 1: src = c->d_vhxc; break;
+    case 2: src = c->d_rho; break;
+    case 3: src = c->d_rho0; break;
+    default: return fail(TDKS_EINVAL, "unknown grid array");
+  }
+  TDKS_CUDA(cudaMemcpyAsync(dst, src, c->npts * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  return TDKS_OK;
+}
+
+tdks_status tdks_check(tdks_ctx* c) {
+  TDKS_TRY(check_ctx(c));
+  TDKS_CUDA(cudaStreamSynchronize(c->stream));
+  TDKS_CUDA(cudaGetLastError());
+  return TDKS_OK;
+}
+
+tdks_status tdks_profile(tdks_ctx* c, int enable) {
+  TDKS_TRY(check_ctx(c));
+  c->profiling = enable != 0;
+  return TDKS_OK;
+}
+
+tdks_status tdks_stats_read(tdks_ctx* c, tdks_stats* out, int reset) {
+  TDKS_TRY(check_ctx(c));
+  if (!out) return fail(TDKS_EINVAL, "null output");
+  TDKS_CUDA(cudaStreamSynchronize(c->stream));
+  for (auto& r : c->recs) {
+    float ms = 0.0f;
+    TDKS_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
+    c->ms[r.phase] += ms;
+    c->event_pool.push_back(r.a);
+    c->event_pool.push_back(r.b);
+  }
+  c->recs.clear();
+  out->launches = c->launches;
+  for (int p = 0; p < TDKS_NPHASE; ++p) { out->calls[p] = c->calls[p]; out->ms[p] = c->ms[p]; }
+  if (reset) {
+    c->launches = 0;
+    for (int p = 0; p < TDKS_NPHASE; ++p) { c->calls[p] = 0; c->ms[p] = 0.0; }
+  }
+  return TDKS_OK;
+}
+
+tdks_status tdks_query(const tdks_ctx* c, int* npts, int* nk, int* norb, int* precision, int* nsph) {
+  TDKS_TRY(check_ctx(c));
+  if (npts) *npts = c->npts;
+  if (nk) *nk = c->nk;
+  if (norb) *norb = c->norb;
+  if (precision) *precision = c->opt.precision;
+  if (nsph) *nsph = c->nsph;
+  return TDKS_OK;
+}
+
+}  // extern "C"

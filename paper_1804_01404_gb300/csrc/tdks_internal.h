@@ -1,0 +1,142 @@
+// Internal declarations shared by the libtdks translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/tdks.h"
+
+namespace tdks {
+
+// 8th-order central differences, 4 neighbours per side:
+// f'' ~ (1/h^2)[c0 f0 + sum_m c_m (f_m + f_-m)],  f' ~ (1/h) sum_m d_m (f_m - f_-m).
+constexpr double kFD2[5] = {-205.0 / 72.0, 8.0 / 5.0, -1.0 / 5.0, 8.0 / 315.0, -1.0 / 560.0};
+constexpr double kFD1[4] = {4.0 / 5.0, -1.0 / 5.0, 4.0 / 105.0, -1.0 / 280.0};
+constexpr double kPi = 3.14159265358979323846;
+
+template <typename T> struct Cplx;
+template <> struct Cplx<float> { using type = float2; };
+template <> struct Cplx<double> { using type = double2; };
+
+// Host-built projector tables (Kleinman-Bylander s, px, py, pz per atom with projectors).
+struct ProjectorTables {
+  int natom = 0;                  // atoms that carry projectors
+  std::vector<int> atom_off;      // [natom+1] entry ranges
+  std::vector<int> idx;           // [nsph] grid index (z*ny + y)*nx + x
+  std::vector<double> beta;       // [nsph*4] normalised beta_s, beta_px, beta_py, beta_pz
+  std::vector<double> d;          // [nsph*3] displacement from the atom (nearest image)
+  std::vector<double> E;          // [natom*4] E_s, E_p, E_p, E_p
+  std::vector<int> pt_off;        // [npts+1] point -> entries (CSR)
+  std::vector<int> pt_ent;        // [nsph]  entry ids sorted by grid point
+  std::vector<int> ent_atom;      // [nsph]  atom of each entry
+};
+
+// Build projector tables; returns false with a message on invalid input.
+bool build_projector_tables(const tdks_grid& g, const tdks_atom* atoms, int natom,
+                            const tdks_projector* proj, int nproj, ProjectorTables& out,
+                            std::string& err);
+
+// Periodic local potential in G-space on the FFT grid, layout [nz][ny][nx] complex (re, im):
+// V(G) = (1/Omega) sum_a (-4 pi Z / G^2) exp(-G^2 sigma^2/4) exp(-i G.R), V(0) = 0.
+void local_potential_gspace(const tdks_grid& g, const tdks_atom* atoms, int natom,
+                            std::vector<double>& vg_interleaved);
+
+// Mean of 1/|r| over one grid cell centred at the origin, times nothing: returns
+// (1/dV) * integral over [-hx/2,hx/2]x[-hy/2,hy/2]x[-hz/2,hz/2] of 1/|r|.
+double cell_mean_inverse_distance(double hx, double hy, double hz);
+
+// Factorisation of an FFT length into radices (4, 2, 3, 5, then any prime).
+bool fft_radices(int n, std::vector<int>& radices);
+
+// ---------------------------------------------------------------------------------------------
+// device-side argument blocks
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+struct OrbArgs {
+  using C = typename Cplx<T>::type;
+  const C* psi_in;          // [norb_tot][npts]
+  C* psi_out;               // output (Hu, or the propagated orbital); may alias psi_in for Taylor
+  const T* V;               // [npts] local potential of this call
+  int nx, ny, nz, npts, periodic;
+  T c2x[5], c2y[5], c2z[5]; // -1/2 * FD2[m] / h^2
+  T d1x[4], d1y[4], d1z[4]; // FD1[m] / h
+  int norb, nk;
+  const double* kpts;       // [nk*3]
+  double Ap[3];             // A'(t) added to every k
+  // projectors
+  int natom, nsph;
+  const int* atom_off;
+  const int* sph_idx;
+  const T* sph_beta;        // [nsph*4]
+  const T* sph_d;           // [nsph*3]
+  const T* atomE;           // [natom*4]
+  const int* pt_off;
+  const int* pt_ent;
+  const int* ent_atom;
+  T dV;
+  T dt;
+  double* rho;              // nullable: rho += 2 w_k |u_out|^2
+  const double* kw;
+  int write_out;            // write psi_out (Taylor) -- predictor passes only accumulate rho
+};
+
+// Orbital kernels (k_orbital.cu)
+// mode 0: H u, 1: T4.  scratch = [norb_tot][npts] global buffer, needed only when
+// smem_orbital_needs_scratch() (two shared-memory copies of the orbital do not fit).
+template <typename T>
+cudaError_t launch_smem_orbital(const OrbArgs<T>& a, int mode, typename Cplx<T>::type* scratch,
+                                cudaStream_t s);
+template <typename T>
+bool smem_orbital_needs_scratch(int npts, int nsph, int natom);
+template <typename T>
+size_t smem_orbital_bytes(int npts, int nsph, int natom);
+template <typename T>
+bool smem_orbital_fits(int npts, int nsph, int natom);
+
+// Per-orbital observables: out[orb*8 + {0..7}] =
+// {norm, jloc_x, jloc_y, jloc_z, jnl_x, jnl_y, jnl_z, <u|T_q + V + V_NL|u>} (with a.V = V_loc)
+template <typename T>
+cudaError_t launch_orbital_observables(const OrbArgs<T>& a, double* out, cudaStream_t s);
+
+// Grid kernels (k_grid.cu)
+cudaError_t launch_fft_axis(double2* data, const int dims[3], int axis, int dir,
+                            const double2* tw, const int* radices, int nrad, cudaStream_t s);
+cudaError_t launch_pack_real(const double* src, const int n[3], double2* dst, const int m[3],
+                             cudaStream_t s);
+cudaError_t launch_poisson_scale_periodic(double2* data, const int n[3], const double h[3],
+                                          cudaStream_t s);
+cudaError_t launch_scale_by_real(double2* data, const double* ghat, double scale, size_t count,
+                                 cudaStream_t s);
+// vhxc = scale_h * Re(fft[crop]) (if hartree) + V_x[rho] (if xc)
+cudaError_t launch_hxc_epilogue(const double2* fft, const int m[3], const double* rho,
+                                const int n[3], double scale_h, int hartree, int xc,
+                                double* vhxc, cudaStream_t s);
+// vstep64 = vloc + a*v1 + b*v2 (v2 nullable), and vstep32 = (float)vstep64 (nullable)
+cudaError_t launch_combine_potential(const double* vloc, const double* v1, double a,
+                                     const double* v2, double b, double* v64, float* v32,
+                                     int npts, cudaStream_t s);
+template <typename T>
+cudaError_t launch_density(const typename Cplx<T>::type* psi, int nk, int norb, int npts,
+                           const double* kw, double* rho, cudaStream_t s);
+template <typename T>
+cudaError_t launch_kick(typename Cplx<T>::type* psi, int norb_tot, const int n[3],
+                        const double h[3], int periodic, const double kappa[3], cudaStream_t s);
+cudaError_t launch_vloc_isolated(double* v, const int n[3], const double h[3],
+                                 const double* atoms /*[natom*5]: R, Z, sigma*/, int natom,
+                                 cudaStream_t s);
+cudaError_t launch_hockney_kernel(double2* g, const int m[3], const int n[3], const double h[3],
+                                  double g0, cudaStream_t s);
+cudaError_t launch_real_part(const double2* src, double* dst, size_t count, double scale,
+                             cudaStream_t s);
+// dipole: partials then final (deterministic two-pass); out[3..5] = d, out[6] = int rho
+cudaError_t launch_dipole(const double* rho, const double* rho0, const int n[3], const double h[3],
+                          int periodic, double* partials, int nblocks, double* out,
+                          cudaStream_t s);
+// J from per-orbital observables; writes out[0..2] = J (zero if isolated)
+cudaError_t launch_reduce_current(const double* orb_obs, int nk, int norb, const double* kw,
+                                  double inv_omega, int periodic, double* out, cudaStream_t s);
+cudaError_t launch_f32_from_f64(const double* src, float* dst, size_t count, cudaStream_t s);
+
+}  // namespace tdks

@@ -1,0 +1,233 @@
+"""Thin ctypes binding of libtdks.so (argument marshalling only).
+
+Every step of the propagation runs in the library's CUDA kernels; this module converts a
+system description into the C structs of include/tdks.h and passes device pointers of torch
+tensors.  There is no CPU fallback: if libtdks.so is missing or CUDA is unavailable the calls fail.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtdks.so")
+
+TDKS_F64, TDKS_F32 = 0, 1
+FIELD_NONE, FIELD_STEP, FIELD_PULSE = 0, 1, 2
+STATUS = {0: "TDKS_OK", 1: "TDKS_EINVAL", 2: "TDKS_ENOMEM", 3: "TDKS_ECUDA", 4: "TDKS_ETIMEOUT",
+          5: "TDKS_ENONFINITE", 6: "TDKS_EUNSUPPORTED"}
+
+
+class TdksError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Grid(C.Structure):
+    _fields_ = [("n", C.c_int * 3), ("h", C.c_double * 3), ("periodic", C.c_int)]
+
+
+class Cell(C.Structure):
+    _fields_ = [("L", C.c_double * 3)]
+
+
+class AtomC(C.Structure):
+    _fields_ = [("R", C.c_double * 3), ("Z", C.c_double), ("sigma", C.c_double), ("proj", C.c_int)]
+
+
+class ProjectorC(C.Structure):
+    _fields_ = [("E_s", C.c_double), ("E_p", C.c_double), ("r_cut", C.c_double), ("width", C.c_double)]
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int), ("hartree", C.c_int), ("xc", C.c_int), ("pc", C.c_int)]
+
+
+class Obs(C.Structure):
+    _fields_ = [("J", C.c_double * 3), ("dipole", C.c_double * 3), ("norm_min", C.c_double),
+                ("norm_max", C.c_double), ("e_band", C.c_double), ("n_elec", C.c_double)]
+
+    def as_dict(self):
+        return dict(J=np.array(self.J[:]), dipole=np.array(self.dipole[:]), norm_min=self.norm_min,
+                    norm_max=self.norm_max, e_band=self.e_band, n_elec=self.n_elec)
+
+
+NPHASE = 6
+PHASES = ("taylor_predictor", "taylor_corrector", "hpsi", "hartree_xc", "observables", "other")
+
+
+class Stats(C.Structure):
+    _fields_ = [("launches", C.c_longlong), ("calls", C.c_longlong * NPHASE), ("ms", C.c_double * NPHASE)]
+
+    def as_dict(self):
+        return dict(launches=int(self.launches),
+                    calls={p: int(self.calls[i]) for i, p in enumerate(PHASES)},
+                    ms={p: float(self.ms[i]) for i, p in enumerate(PHASES)})
+
+
+_lib = None
+_D3 = C.c_double * 3
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libtdks.so and declare its signatures.  Raises if the library was not built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} not found: build it with `python -m paper_1804_01404_gb300.build`")
+    lib = C.CDLL(path)
+    vp, i, d = C.c_void_p, C.c_int, C.c_double
+    sig = {
+        "tdks_init": [C.POINTER(Grid), C.POINTER(Cell), C.POINTER(AtomC), i, C.POINTER(ProjectorC), i,
+                      C.POINTER(C.c_double), C.POINTER(C.c_double), i, i, C.POINTER(Options), vp,
+                      C.POINTER(vp)],
+        "tdks_set_field": [vp, i, _D3, d, d, d],
+        "tdks_kick": [vp, vp, _D3],
+        "tdks_update_potential": [vp, vp],
+        "tdks_hpsi": [vp, vp, vp, _D3],
+        "tdks_taylor_step": [vp, vp, d, _D3],
+        "tdks_step": [vp, vp, d, d],
+        "tdks_read_step_observables": [vp, C.POINTER(Obs)],
+        "tdks_observables": [vp, vp, _D3, C.POINTER(Obs)],
+        "tdks_get_grid_array": [vp, i, vp],
+        "tdks_check": [vp],
+        "tdks_profile": [vp, i],
+        "tdks_stats_read": [vp, C.POINTER(Stats), i],
+        "tdks_query": [vp, C.POINTER(i), C.POINTER(i), C.POINTER(i), C.POINTER(i), C.POINTER(i)],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = C.c_int
+    lib.tdks_last_error.restype = C.c_char_p
+    lib.tdks_last_error.argtypes = []
+    lib.tdks_abi_version.restype = C.c_int
+    lib.tdks_destroy.argtypes = [vp]
+    lib.tdks_destroy.restype = None
+    _lib = lib
+    return lib
+
+
+def _check(status):
+    if status != 0:
+        raise TdksError(status, _lib.tdks_last_error().decode())
+
+
+def _vec3(v):
+    return _D3(*[float(x) for x in (v if v is not None else (0.0, 0.0, 0.0))])
+
+
+def _ptr(t, dtype=None):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
+        raise ValueError("expected a contiguous CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"expected dtype {dtype}, got {t.dtype}")
+    return C.c_void_p(t.data_ptr())
+
+
+class Context:
+    """One propagation context (libtdks tdks_ctx) for a system description.
+
+    `system` needs: n, h, periodic, atoms (R, Z, sigma), proj (E_s, E_p, r_cut, width), kpts, kw,
+    norb, field.  Orbitals are torch tensors [nk, norb, nz, ny, nx], complex128 (f64) or
+    complex64 (f32), on the current CUDA device."""
+
+    def __init__(self, system, precision="f64", hartree=True, xc=True, pc=True, stream=None):
+        import torch
+        lib = load_library()
+        self.lib = lib
+        self.system = system
+        self.precision = precision
+        self.cdtype = torch.complex128 if precision == "f64" else torch.complex64
+        g = Grid((C.c_int * 3)(*system.n), (C.c_double * 3)(*system.h), 1 if system.periodic else 0)
+        cell = Cell((C.c_double * 3)(*[system.n[a] * system.h[a] for a in range(3)]))
+        natom = len(system.atoms)
+        atoms = (AtomC * max(natom, 1))()
+        for i, at in enumerate(system.atoms):
+            atoms[i] = AtomC(_D3(*at.R), at.Z, at.sigma, 0)
+        pr = ProjectorC(system.proj.E_s, system.proj.E_p, system.proj.r_cut, system.proj.width)
+        kp = np.ascontiguousarray(np.asarray(system.kpts, np.float64).reshape(-1))
+        kw = np.ascontiguousarray(np.asarray(system.kw, np.float64))
+        opts = Options(TDKS_F64 if precision == "f64" else TDKS_F32, int(hartree), int(xc), int(pc))
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        ctx = C.c_void_p()
+        _check(lib.tdks_init(C.byref(g), C.byref(cell), atoms, natom, C.byref(pr), 1,
+                             kp.ctypes.data_as(C.POINTER(C.c_double)),
+                             kw.ctypes.data_as(C.POINTER(C.c_double)), len(kw), int(system.norb),
+                             C.byref(opts), C.c_void_p(stream.cuda_stream), C.byref(ctx)))
+        self.ctx = ctx
+        f = getattr(system, "field", None)
+        if f is not None and f.kind != "none":
+            kind = {"step": FIELD_STEP, "pulse": FIELD_PULSE}[f.kind]
+            self.set_field(kind, f.A0, f.omega, f.T, f.cep)
+
+    def __del__(self):
+        try:
+            if getattr(self, "ctx", None) is not None and self.ctx.value:
+                self.lib.tdks_destroy(self.ctx)
+                self.ctx = None
+        except Exception:
+            pass
+
+    def close(self):
+        self.__del__()
+
+    # ---- calls (asynchronous on the context stream unless stated)
+    def set_field(self, kind, A0, omega=0.0, T=0.0, cep=0.0):
+        _check(self.lib.tdks_set_field(self.ctx, int(kind), _vec3(A0), float(omega), float(T), float(cep)))
+
+    def kick(self, u, kappa):
+        _check(self.lib.tdks_kick(self.ctx, _ptr(u, self.cdtype), _vec3(kappa)))
+
+    def update_potential(self, u):
+        _check(self.lib.tdks_update_potential(self.ctx, _ptr(u, self.cdtype)))
+
+    def hpsi(self, u, hu, Aprime=None):
+        _check(self.lib.tdks_hpsi(self.ctx, _ptr(u, self.cdtype), _ptr(hu, self.cdtype), _vec3(Aprime)))
+
+    def taylor_step(self, u, dt, Aprime=None):
+        _check(self.lib.tdks_taylor_step(self.ctx, _ptr(u, self.cdtype), float(dt), _vec3(Aprime)))
+
+    def step(self, u, t, dt):
+        _check(self.lib.tdks_step(self.ctx, _ptr(u, self.cdtype), float(t), float(dt)))
+
+    def read_step_observables(self):
+        o = Obs()
+        _check(self.lib.tdks_read_step_observables(self.ctx, C.byref(o)))
+        return o.as_dict()
+
+    def observables(self, u, Aprime=None):
+        o = Obs()
+        _check(self.lib.tdks_observables(self.ctx, _ptr(u, self.cdtype), _vec3(Aprime), C.byref(o)))
+        return o.as_dict()
+
+    def grid_array(self, which):
+        """0: V_loc, 1: V_Hxc(t), 2: rho(t), 3: rho0 -> torch float64 [nz, ny, nx] on the device."""
+        import torch
+        n = self.system.n
+        out = torch.empty((n[2], n[1], n[0]), dtype=torch.float64, device="cuda")
+        _check(self.lib.tdks_get_grid_array(self.ctx, int(which), _ptr(out)))
+        return out
+
+    def profile(self, enable=True):
+        _check(self.lib.tdks_profile(self.ctx, int(enable)))
+
+    def stats(self, reset=False):
+        st = Stats()
+        _check(self.lib.tdks_stats_read(self.ctx, C.byref(st), int(reset)))
+        return st.as_dict()
+
+    def check(self):
+        _check(self.lib.tdks_check(self.ctx))
+
+    def query(self):
+        v = [C.c_int() for _ in range(5)]
+        _check(self.lib.tdks_query(self.ctx, *[C.byref(x) for x in v]))
+        return dict(zip(("npts", "nk", "norb", "precision", "nsphere_points"), [x.value for x in v]))

@@ -132,12 +132,16 @@ def random_cluster_atoms(natom=128, radius=14.0, dmin=3.0, seed=1):
     """Uniform random positions in a sphere (rejection-sampled to >= dmin apart), Z 50/50 of {1, 4}."""
     rng = np.random.default_rng(seed)
     pos = []
-    while len(pos) < natom:
+    for _ in range(1000 * natom + 1000):
+        if len(pos) == natom:
+            break
         p = rng.uniform(-radius, radius, 3)
         if np.dot(p, p) > radius * radius:
             continue
         if all(np.linalg.norm(p - q) >= dmin for q in pos):
             pos.append(p)
+    if len(pos) < natom:
+        raise ValueError(f"cannot place {natom} atoms {dmin} bohr apart in a sphere of radius {radius}")
     Z = rng.permutation(np.array([1.0] * (natom // 2) + [4.0] * (natom - natom // 2)))
     return [Atom(tuple(p), float(z)) for p, z in zip(pos, Z)]
 

@@ -1,0 +1,74 @@
+"""C-ABI checks that need no GPU: the library builds, loads and exports every declared symbol,
+and host-side argument validation rejects bad input before any CUDA call."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1804_01404_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1804_01404_gb300 import build, tdks
+    if not os.path.exists(tdks.LIB_PATH):
+        build.build()
+    return tdks.load_library()
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "tdks.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(tdks_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_symbols()
+    assert "tdks_init" in names and "tdks_step" in names and len(names) >= 14
+    for n in names:
+        assert hasattr(lib, n), n
+    assert lib.tdks_abi_version() == 1
+
+
+def _init(lib, s, **kw):
+    from paper_1804_01404_gb300 import tdks as T
+    g = T.Grid((C.c_int * 3)(*kw.get("n", s.n)), (C.c_double * 3)(*s.h), int(s.periodic))
+    L = kw.get("L", [s.n[a] * s.h[a] for a in range(3)])
+    cell = T.Cell((C.c_double * 3)(*L))
+    atoms = (T.AtomC * max(1, len(s.atoms)))()
+    for i, at in enumerate(s.atoms):
+        atoms[i] = T.AtomC((C.c_double * 3)(*at.R), at.Z, at.sigma, kw.get("proj", 0))
+    pr = T.ProjectorC(s.proj.E_s, s.proj.E_p, kw.get("r_cut", s.proj.r_cut), s.proj.width)
+    kp = np.ascontiguousarray(np.asarray(s.kpts, np.float64).ravel())
+    kwt = np.ascontiguousarray(np.asarray(kw.get("kw", s.kw), np.float64))
+    opts = T.Options(kw.get("precision", 0), 1, 1, 1)
+    ctx = C.c_void_p()
+    st = lib.tdks_init(C.byref(g), C.byref(cell), atoms, len(s.atoms), C.byref(pr), 1,
+                       kp.ctypes.data_as(C.POINTER(C.c_double)), kwt.ctypes.data_as(C.POINTER(C.c_double)),
+                       len(kwt), kw.get("norb", s.norb), C.byref(opts), None, C.byref(ctx))
+    return st, lib.tdks_last_error().decode()
+
+
+@pytest.mark.parametrize("case,expect", [
+    (dict(n=(3, 6, 6)), "grid points"),
+    (dict(norb=0), "norb"),
+    (dict(kw=[0.5]), "weights"),
+    (dict(L=[1.0, 1.0, 1.0]), "cell length"),
+    (dict(precision=7), "precision"),
+    (dict(r_cut=2.0), "half the periodic cell"),
+    (dict(proj=5), "projector index"),
+])
+def test_host_validation(lib, case, expect):
+    s = W.tiny(periodic=True, n=(6, 6, 6), natom=1)
+    st, msg = _init(lib, s, **case)
+    assert st == 1, (st, msg)          # TDKS_EINVAL, returned before any device call
+    assert expect in msg
+
+
+def test_null_context_rejected(lib):
+    assert lib.tdks_hpsi(None, None, None, (C.c_double * 3)()) == 1
+    assert lib.tdks_step(None, None, 0.0, 0.02) == 1
