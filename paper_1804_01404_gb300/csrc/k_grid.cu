@@ -206,15 +206,16 @@ __global__ void k_combine(const double* __restrict__ vloc, const double* __restr
 template <typename C>
 __global__ void k_density(const C* __restrict__ psi, int nk, int norb, int npts,
                           const double* __restrict__ kw, double* __restrict__ rho) {
+  using R = decltype(C{}.x);
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npts; p += gridDim.x * blockDim.x) {
     double acc = 0.0;
     for (int k = 0; k < nk; ++k) {
-      double s = 0.0;
+      R s = 0;                        // per-k partial in the orbital precision
       for (int n = 0; n < norb; ++n) {
         const C u = psi[((size_t)k * norb + n) * npts + p];
-        s += (double)u.x * u.x + (double)u.y * u.y;
+        s += u.x * u.x + u.y * u.y;
       }
-      acc += 2.0 * kw[k] * s;
+      acc += 2.0 * kw[k] * (double)s;
     }
     rho[p] = acc;
   }
@@ -335,23 +336,26 @@ __global__ void k_dipole_final(const double* partials, int nblocks, double dV, d
   }
 }
 
-__global__ void k_reduce_current(const double* __restrict__ obs, int nk, int norb,
-                                 const double* __restrict__ kw, double inv_omega, int periodic,
-                                 double* out) {
-  if (threadIdx.x < 3) {
-    double J = 0.0;
-    if (periodic) {
-      for (int k = 0; k < nk; ++k) {
-        double s = 0.0;
-        for (int n = 0; n < norb; ++n) {
-          const double* o = obs + ((size_t)k * norb + n) * 8;
-          s += o[1 + threadIdx.x] + o[4 + threadIdx.x];
-        }
-        J += 2.0 * kw[k] * s;
-      }
+// J_d = -(1/Omega) sum_k w_k sum_n 2 (jloc_d + jnl_d): one block, fixed-order tree reduction.
+__global__ void __launch_bounds__(256) k_reduce_current(const double* __restrict__ obs, int nk, int norb,
+                                                        const double* __restrict__ kw, double inv_omega,
+                                                        int periodic, double* out) {
+  __shared__ double red[3][256];
+  double acc[3] = {0, 0, 0};
+  const int tot = nk * norb;
+  if (periodic)
+    for (int o = threadIdx.x; o < tot; o += blockDim.x) {
+      const double w = 2.0 * kw[o / norb];
+      for (int d = 0; d < 3; ++d) acc[d] += w * (obs[(size_t)o * 8 + 1 + d] + obs[(size_t)o * 8 + 4 + d]);
     }
-    out[threadIdx.x] = -J * inv_omega;
+  for (int d = 0; d < 3; ++d) red[d][threadIdx.x] = acc[d];
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h)
+      for (int d = 0; d < 3; ++d) red[d][threadIdx.x] += red[d][threadIdx.x + h];
+    __syncthreads();
   }
+  if (threadIdx.x < 3) out[threadIdx.x] = -red[threadIdx.x][0] * inv_omega;
 }
 
 int grid_for(long long n, int threads) {
@@ -479,7 +483,7 @@ cudaError_t launch_dipole(const double* rho, const double* rho0, const int n[3],
 
 cudaError_t launch_reduce_current(const double* orb_obs, int nk, int norb, const double* kw,
                                   double inv_omega, int periodic, double* out, cudaStream_t s) {
-  k_reduce_current<<<1, 32, 0, s>>>(orb_obs, nk, norb, kw, inv_omega, periodic, out);
+  k_reduce_current<<<1, 256, 0, s>>>(orb_obs, nk, norb, kw, inv_omega, periodic, out);
   return cudaGetLastError();
 }
 

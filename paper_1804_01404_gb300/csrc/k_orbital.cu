@@ -1,12 +1,18 @@
-// Orbital kernels with the whole orbital resident in shared memory.
+// Orbital kernels with the whole orbital resident in shared memory ("cell" kernels).
 //
 // One CTA owns one orbital (k, n).  It copies the orbital into shared memory once, applies the
-// Hamiltonian of Eq. (TDKS_solid) -- 25-point Laplacian, -i q.grad (9-point first derivative
-// per axis), |q|^2/2 + V, and the Kleinman-Bylander projectors with the gauge phase of Sec. 4.1
-// -- and, for the Taylor propagator, runs all four Horner stages
+// Hamiltonian of Eq. (TDKS_solid) -- 25-point Laplacian, -i q.grad (9-point first derivative per
+// axis), |q|^2/2 + V, and the Kleinman-Bylander projectors with the gauge phase of Sec. 4.1 -- and,
+// for the Taylor propagator, runs all four Horner stages
 //     v <- psi + (-i dt / m) H v,   m = 4, 3, 2, 1
 // without leaving the SM, so one Taylor step reads and writes the orbital in HBM once.
-// The density of Eq. (rho) is accumulated from the final stage (FP64 atomics).
+//
+// Work split inside the CTA: a thread owns one (x, y) column segment and marches along z,
+// keeping the nine z-values u(z-4..z+4) of its column in registers; the 16 x/y neighbours come
+// from shared memory through offsets computed once per column.  Complex FP32 arithmetic uses the
+// packed f32x2 instructions.  The nonlocal scatter runs as a separate pass over the grid points
+// that lie inside a projector sphere.  The last pass writes the orbital, accumulates the density
+// of Eq. (rho) (FP64 atomics) and, on request, the norm and the current of Eq. (macro_current).
 #include <cuda_runtime.h>
 
 #include "tdks_internal.h"
@@ -15,61 +21,89 @@ namespace tdks {
 
 namespace {
 
-template <typename T> struct Vec;
-template <> struct Vec<float> {
+// ------------------------------------------------------------------ complex helpers
+template <typename T> struct CM;
+
+template <> struct CM<float> {
   using C = float2;
+  static __device__ __forceinline__ unsigned long long pk(float2 v) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(v.x), "f"(v.y));
+    return r;
+  }
+  static __device__ __forceinline__ float2 up(unsigned long long r) {
+    float2 v;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+    return v;
+  }
+  static __device__ __forceinline__ C add(C a, C b) {
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk(a)), "l"(pk(b)));
+    return up(d);
+  }
+  static __device__ __forceinline__ C sub(C a, C b) {
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk(a)), "l"(pk(b)));
+    return up(d);
+  }
+  // acc + s * a  (s real, broadcast to both lanes)
+  static __device__ __forceinline__ C fma(float s, C a, C acc) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(pk(a)), "l"(pk(make_float2(s, s))), "l"(pk(acc)));
+    return up(d);
+  }
   static __device__ __forceinline__ void sincos_(float x, float* s, float* c) { sincosf(x, s, c); }
 };
-template <> struct Vec<double> {
+
+template <> struct CM<double> {
   using C = double2;
+  static __device__ __forceinline__ C add(C a, C b) { return C{a.x + b.x, a.y + b.y}; }
+  static __device__ __forceinline__ C sub(C a, C b) { return C{a.x - b.x, a.y - b.y}; }
+  static __device__ __forceinline__ C fma(double s, C a, C acc) {
+    return C{__fma_rn(s, a.x, acc.x), __fma_rn(s, a.y, acc.y)};
+  }
   static __device__ __forceinline__ void sincos_(double x, double* s, double* c) { sincos(x, s, c); }
 };
 
+// ------------------------------------------------------------------ shared-memory layout
 template <typename T>
-struct SmemLayout {
+struct Smem {
   using C = typename Cplx<T>::type;
-  C* v;      // [npts] current Horner vector
+  C* v;      // [nz * pstride] current vector
+  C* nxt;    // [nz * pstride] next vector (double-buffer mode)
   C* ph;     // [nsph] exp(i q.d)
-  C* ec;     // [natom*4] E_p * c_ap
+  C* ec;     // [natom*4] E_p * dV * c_ap
 };
 
 template <typename T>
-__device__ __forceinline__ SmemLayout<T> carve(unsigned char* raw, int npts, int nsph) {
+inline size_t cell_smem_bytes(int nz, int pstride, int nsph, int natom, bool dbuf) {
   using C = typename Cplx<T>::type;
-  SmemLayout<T> L;
-  L.v = reinterpret_cast<C*>(raw);
-  L.ph = L.v + npts;
-  L.ec = L.ph + nsph;
-  return L;
+  const size_t vsz = (size_t)nz * pstride;
+  return sizeof(C) * (vsz * (dbuf ? 2 : 1) + nsph + 4 * (size_t)natom);
 }
 
-// point index -> (x, y, z) without integer division (exact for the grid sizes used here)
-__device__ __forceinline__ void unpack(int p, int nx, int ny, float inx, float iny, int& x, int& y,
-                                       int& z) {
-  int row = __float2int_rd((p + 0.5f) * inx);
-  x = p - row * nx;
-  z = __float2int_rd((row + 0.5f) * iny);
-  y = row - z * ny;
-}
+constexpr int kNT = 512;               // threads per CTA (upper bound)
+constexpr size_t kSmemLimit = 220 * 1024;
 
-// Projections of the shared-memory vector: ec[a*4+p] = E_p * dV * sum_i beta_ip ph_i v(idx_i).
-template <typename T, int NT>
-__device__ __forceinline__ void project(const OrbArgs<T>& a, SmemLayout<T> L) {
+// Projections of the shared-memory vector:  ec[a*4+p] = E_p dV sum_i beta_ip ph_i v(idx_i).
+template <typename T>
+__device__ __forceinline__ void project(const OrbArgs<T>& a, const typename Cplx<T>::type* v,
+                                        const typename Cplx<T>::type* ph,
+                                        typename Cplx<T>::type* ec) {
   using C = typename Cplx<T>::type;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int at = warp; at < a.natom; at += NT / 32) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int at = warp; at < a.natom; at += nw) {
     T acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    const int e0 = a.atom_off[at], e1 = a.atom_off[at + 1];
-    for (int i = e0 + lane; i < e1; i += 32) {
-      const C v = L.v[a.sph_idx[i]];
-      const C ph = L.ph[i];
-      const T re = v.x * ph.x - v.y * ph.y;
-      const T im = v.x * ph.y + v.y * ph.x;
+    const int e1 = a.atom_off[at + 1];
+    for (int i = a.atom_off[at] + lane; i < e1; i += 32) {
+      const C u = v[a.sph_sidx[i]];
+      const C f = ph[i];
+      const T re = u.x * f.x - u.y * f.y, im = u.x * f.y + u.y * f.x;
+      const T* b = a.sph_beta + 4 * i;
 #pragma unroll
       for (int p = 0; p < 4; ++p) {
-        const T b = a.sph_beta[i * 4 + p];
-        acc[2 * p] += b * re;
-        acc[2 * p + 1] += b * im;
+        acc[2 * p] += b[p] * re;
+        acc[2 * p + 1] += b[p] * im;
       }
     }
 #pragma unroll
@@ -78,389 +112,418 @@ __device__ __forceinline__ void project(const OrbArgs<T>& a, SmemLayout<T> L) {
       for (int j = 0; j < 8; ++j) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], o);
     if (lane < 4) {
       const T s = a.atomE[at * 4 + lane] * a.dV;
-      C c;
-      c.x = acc[2 * lane] * s;
-      c.y = acc[2 * lane + 1] * s;
-      L.ec[at * 4 + lane] = c;
+      ec[at * 4 + lane] = C{acc[2 * lane] * s, acc[2 * lane + 1] * s};
     }
   }
 }
 
-// (H_q v)(p) from the shared-memory vector.
 template <typename T, bool PER>
-__device__ __forceinline__ typename Cplx<T>::type apply_h(const OrbArgs<T>& a, SmemLayout<T> L,
-                                                          int p, int x, int y, int z, T diag,
-                                                          const T* gx, const T* gy, const T* gz) {
+struct Column {
+  int col, x, y, z0, z1;
+  int ix[8], iy[8];   // in-plane index of x+-m, y+-m neighbours (pad index when outside)
+};
+
+template <typename T, bool PER>
+__device__ __forceinline__ Column<T, PER> make_column(const OrbArgs<T>& a, int item) {
+  Column<T, PER> c;
+  const int nxy = a.nx * a.ny;
+  c.col = item % nxy;
+  const int seg = item / nxy;
+  c.y = c.col / a.nx;
+  c.x = c.col - c.y * a.nx;
+  c.z0 = seg * a.zlen;
+  c.z1 = min(a.nz, c.z0 + a.zlen);
+#pragma unroll
+  for (int m = 1; m <= 4; ++m) {
+    int xp = c.x + m, xm = c.x - m, yp = c.y + m, ym = c.y - m;
+    if (PER) {
+      xp -= (xp >= a.nx) ? a.nx : 0; xm += (xm < 0) ? a.nx : 0;
+      yp -= (yp >= a.ny) ? a.ny : 0; ym += (ym < 0) ? a.ny : 0;
+      c.ix[2 * (m - 1)] = c.y * a.nx + xp;
+      c.ix[2 * (m - 1) + 1] = c.y * a.nx + xm;
+      c.iy[2 * (m - 1)] = yp * a.nx + c.x;
+      c.iy[2 * (m - 1) + 1] = ym * a.nx + c.x;
+    } else {
+      c.ix[2 * (m - 1)] = (xp < a.nx) ? c.y * a.nx + xp : nxy;
+      c.ix[2 * (m - 1) + 1] = (xm >= 0) ? c.y * a.nx + xm : nxy;
+      c.iy[2 * (m - 1)] = (yp < a.ny) ? yp * a.nx + c.x : nxy;
+      c.iy[2 * (m - 1) + 1] = (ym >= 0) ? ym * a.nx + c.x : nxy;
+    }
+  }
+  return c;
+}
+
+template <typename T, bool PER>
+__device__ __forceinline__ typename Cplx<T>::type zload(const OrbArgs<T>& a,
+                                                        const typename Cplx<T>::type* v, int zz,
+                                                        int col) {
   using C = typename Cplx<T>::type;
-  const int nx = a.nx, ny = a.ny, nz = a.nz;
-  const int sxy = nx * ny;
-  const C u0 = L.v[p];
-  const T vloc = a.V[p] + diag;
-  T re = vloc * u0.x, im = vloc * u0.y;
-  const int row = p - x;
-  // x neighbours
+  if (PER) {
+    zz += (zz < 0) ? a.nz : 0;
+    zz -= (zz >= a.nz) ? a.nz : 0;
+  } else if (zz < 0 || zz >= a.nz) {
+    return C{0, 0};
+  }
+  return v[zz * a.pstride + col];
+}
+
+// Local part of (H v) at (x, y, z) of a column: diag*v + S + (-i) D, z-neighbours from window w.
+template <typename T, bool PER>
+__device__ __forceinline__ typename Cplx<T>::type local_h(const OrbArgs<T>& a,
+                                                          const Column<T, PER>& c,
+                                                          const typename Cplx<T>::type* v,
+                                                          const typename Cplx<T>::type* w, int zb,
+                                                          T diag, const T* gx, const T* gy,
+                                                          const T* gz) {
+  using C = typename Cplx<T>::type;
+  using M = CM<T>;
+  C S = M::fma(diag, w[4], C{0, 0});
+  C D = C{0, 0};
 #pragma unroll
   for (int m = 1; m <= 4; ++m) {
-    int xp = x + m, xm = x - m;
-    C up, um;
+    const C xp = v[zb + c.ix[2 * (m - 1)]], xm = v[zb + c.ix[2 * (m - 1) + 1]];
+    const C yp = v[zb + c.iy[2 * (m - 1)]], ym = v[zb + c.iy[2 * (m - 1) + 1]];
+    const C zp = w[4 + m], zm = w[4 - m];
+    S = M::fma(a.c2x[m], M::add(xp, xm), S);
+    S = M::fma(a.c2y[m], M::add(yp, ym), S);
+    S = M::fma(a.c2z[m], M::add(zp, zm), S);
     if (PER) {
-      xp -= (xp >= nx) ? nx : 0;
-      xm += (xm < 0) ? nx : 0;
-      up = L.v[row + xp];
-      um = L.v[row + xm];
-    } else {
-      up = (xp < nx) ? L.v[row + xp] : C{0, 0};
-      um = (xm >= 0) ? L.v[row + xm] : C{0, 0};
+      D = M::fma(gx[m - 1], M::sub(xp, xm), D);
+      D = M::fma(gy[m - 1], M::sub(yp, ym), D);
+      D = M::fma(gz[m - 1], M::sub(zp, zm), D);
     }
-    const T sr = up.x + um.x, si = up.y + um.y, dr = up.x - um.x, di = up.y - um.y;
-    re += a.c2x[m] * sr;
-    im += a.c2x[m] * si;
-    if (PER) { re += gx[m - 1] * di; im -= gx[m - 1] * dr; }
   }
-  // y neighbours
-  const int plane = z * sxy + x;
-#pragma unroll
-  for (int m = 1; m <= 4; ++m) {
-    int yp = y + m, ym = y - m;
-    C up, um;
-    if (PER) {
-      yp -= (yp >= ny) ? ny : 0;
-      ym += (ym < 0) ? ny : 0;
-      up = L.v[plane + yp * nx];
-      um = L.v[plane + ym * nx];
-    } else {
-      up = (yp < ny) ? L.v[plane + yp * nx] : C{0, 0};
-      um = (ym >= 0) ? L.v[plane + ym * nx] : C{0, 0};
-    }
-    const T sr = up.x + um.x, si = up.y + um.y, dr = up.x - um.x, di = up.y - um.y;
-    re += a.c2y[m] * sr;
-    im += a.c2y[m] * si;
-    if (PER) { re += gy[m - 1] * di; im -= gy[m - 1] * dr; }
-  }
-  // z neighbours
-  const int col = p - z * sxy;
-#pragma unroll
-  for (int m = 1; m <= 4; ++m) {
-    int zp = z + m, zm = z - m;
-    C up, um;
-    if (PER) {
-      zp -= (zp >= nz) ? nz : 0;
-      zm += (zm < 0) ? nz : 0;
-      up = L.v[col + zp * sxy];
-      um = L.v[col + zm * sxy];
-    } else {
-      up = (zp < nz) ? L.v[col + zp * sxy] : C{0, 0};
-      um = (zm >= 0) ? L.v[col + zm * sxy] : C{0, 0};
-    }
-    const T sr = up.x + um.x, si = up.y + um.y, dr = up.x - um.x, di = up.y - um.y;
-    re += a.c2z[m] * sr;
-    im += a.c2z[m] * si;
-    if (PER) { re += gz[m - 1] * di; im -= gz[m - 1] * dr; }
-  }
-  // nonlocal: sum over projector entries touching this point
-  const int e0 = a.pt_off[p], e1 = a.pt_off[p + 1];
-  for (int e = e0; e < e1; ++e) {
+  if (PER) S = C{S.x + D.y, S.y - D.x};   // + (-i) D
+  return S;
+}
+
+// Nonlocal value at sphere point s: sum over its entries of conj(ph_i) sum_p beta_ip ec_ap.
+template <typename T>
+__device__ __forceinline__ typename Cplx<T>::type nonlocal_at(const OrbArgs<T>& a, int s,
+                                                              const typename Cplx<T>::type* ph,
+                                                              const typename Cplx<T>::type* ec) {
+  using C = typename Cplx<T>::type;
+  T re = 0, im = 0;
+  const int e1 = a.sp_off[s + 1];
+  for (int e = a.sp_off[s]; e < e1; ++e) {
     const int i = a.pt_ent[e];
     const int at = a.ent_atom[i];
     T sr = 0, si = 0;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const T b = a.sph_beta[i * 4 + q];
-      const C c = L.ec[at * 4 + q];
-      sr += b * c.x;
-      si += b * c.y;
+      const C cc = ec[at * 4 + q];
+      sr += b * cc.x;
+      si += b * cc.y;
     }
-    const C ph = L.ph[i];   // multiply by conj(ph)
-    re += sr * ph.x + si * ph.y;
-    im += si * ph.x - sr * ph.y;
+    const C f = ph[i];
+    re += sr * f.x + si * f.y;
+    im += si * f.x - sr * f.y;
   }
   return C{re, im};
 }
 
 template <typename T>
-__device__ __forceinline__ void orbital_q(const OrbArgs<T>& a, int k, T q[3]) {
+__device__ __forceinline__ void set_phases(const OrbArgs<T>& a, typename Cplx<T>::type* ph,
+                                           const T q[3]) {
+  for (int i = threadIdx.x; i < a.nsph; i += blockDim.x) {
+    const T arg = q[0] * a.sph_d[3 * i] + q[1] * a.sph_d[3 * i + 1] + q[2] * a.sph_d[3 * i + 2];
+    T s, c;
+    CM<T>::sincos_(arg, &s, &c);
+    ph[i] = typename Cplx<T>::type{c, s};
+  }
+}
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double t = 0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < nw; ++w) t += red[w];
+  return t;   // valid in thread 0
+}
+
+// MODE 0: out = H v.   MODE 1: out = T4 v (Horner), rho += 2 w_k |out|^2, optional fused
+// observables.   MODE 2: observables only (norm, current, <v|H|v> with a.V).
+// DBUF: next vector in shared memory; otherwise in the orbital's slice of `scratch`.
+template <typename T, int MODE, bool PER, bool DBUF, bool OBS>
+__global__ void __launch_bounds__(kNT) k_cell(OrbArgs<T> a, typename Cplx<T>::type* scratch) {
+  using C = typename Cplx<T>::type;
+  using M = CM<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[kNT / 32];
+  const int nxy = a.nx * a.ny;
+  const int ps = a.pstride;
+  const int vsz = a.nz * ps;
+  Smem<T> L;
+  L.v = reinterpret_cast<C*>(smem_raw);
+  L.nxt = L.v + vsz;
+  L.ph = L.v + (DBUF ? 2 * vsz : vsz);
+  L.ec = L.ph + a.nsph;
+  const int orb = blockIdx.x;
+  const int k = orb / a.norb;
+  const C* psi = a.psi_in + (size_t)orb * a.npts;
+  C* gnxt = DBUF ? nullptr : scratch + (size_t)orb * a.npts;
+  T q[3];
   q[0] = (T)(a.kpts[3 * k] + a.Ap[0]);
   q[1] = (T)(a.kpts[3 * k + 1] + a.Ap[1]);
   q[2] = (T)(a.kpts[3 * k + 2] + a.Ap[2]);
-}
-
-// Load the orbital and the per-entry phases exp(i q.d); returns diag term c0 sum + |q|^2/2 and
-// the first-derivative weights q_a d_m / h_a.
-template <typename T, int NT, bool PER>
-__device__ __forceinline__ T prologue(const OrbArgs<T>& a, SmemLayout<T> L,
-                                      const typename Cplx<T>::type* psi, T gx[4], T gy[4],
-                                      T gz[4]) {
-  const int k = blockIdx.x / a.norb;
-  T q[3];
-  orbital_q(a, k, q);
-  for (int p = threadIdx.x; p < a.npts; p += NT) L.v[p] = psi[p];
-  for (int i = threadIdx.x; i < a.nsph; i += NT) {
-    const T arg = q[0] * a.sph_d[3 * i] + q[1] * a.sph_d[3 * i + 1] + q[2] * a.sph_d[3 * i + 2];
-    T s, c;
-    Vec<T>::sincos_(arg, &s, &c);
-    L.ph[i] = typename Cplx<T>::type{c, s};
-  }
+  T gx[4], gy[4], gz[4];
 #pragma unroll
   for (int m = 0; m < 4; ++m) {
-    gx[m] = PER ? q[0] * a.d1x[m] : T(0);
-    gy[m] = PER ? q[1] * a.d1y[m] : T(0);
-    gz[m] = PER ? q[2] * a.d1z[m] : T(0);
+    gx[m] = q[0] * a.d1x[m];
+    gy[m] = q[1] * a.d1y[m];
+    gz[m] = q[2] * a.d1z[m];
   }
-  return a.c2x[0] + a.c2y[0] + a.c2z[0] + T(0.5) * (q[0] * q[0] + q[1] * q[1] + q[2] * q[2]);
-}
+  const T diag0 = a.c2x[0] + a.c2y[0] + a.c2z[0] + T(0.5) * (q[0] * q[0] + q[1] * q[1] + q[2] * q[2]);
 
-// MODE 0: psi_out = H psi_in.  MODE 1: psi_out = T4 psi_in (Horner), rho += 2 w_k |psi_out|^2.
-// DBUF: the next Horner vector goes to a second shared-memory buffer; otherwise to the
-// orbital's slice of a global scratch array (large FP64 cells), copied back after a barrier.
-template <typename T, int NT, int MODE, bool PER, bool DBUF>
-__global__ void __launch_bounds__(NT) k_smem_orbital(OrbArgs<T> a, typename Cplx<T>::type* scratch) {
-  using C = typename Cplx<T>::type;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  SmemLayout<T> L = carve<T>(smem_raw, a.npts, a.nsph);
-  C* nxt = DBUF ? L.ec + 4 * a.natom : scratch + (size_t)blockIdx.x * a.npts;
-  const int orb = blockIdx.x;
-  const C* psi = a.psi_in + (size_t)orb * a.npts;
-  C* out = a.psi_out + (size_t)orb * a.npts;
-  T gx[4], gy[4], gz[4];
-  const T diag = prologue<T, NT, PER>(a, L, psi, gx, gy, gz);
-  const float inx = 1.0f / a.nx, iny = 1.0f / a.ny;
-  const double w = (MODE == 1 && a.rho) ? 2.0 * a.kw[orb / a.norb] : 0.0;
+  // load the orbital (pad elements zero), phases
+  for (int i = threadIdx.x; i < vsz; i += blockDim.x) {
+    const int z = i / ps, r = i - z * ps;
+    const C u = (r < nxy) ? psi[z * nxy + r] : C{0, 0};
+    L.v[i] = u;
+    if (DBUF) L.nxt[i] = C{0, 0};
+  }
+  set_phases<T>(a, L.ph, q);
   __syncthreads();
+
+  const int nitems = nxy * a.nseg;
   constexpr int NSTAGE = (MODE == 1) ? 4 : 1;
 #pragma unroll 1
   for (int st = 0; st < NSTAGE; ++st) {
     if (a.natom > 0) {
-      project<T, NT>(a, L);
+      project<T>(a, L.v, L.ph, L.ec);
       __syncthreads();
     }
     const T coef = a.dt / T(4 - st);
-    const bool last = (st + 1 == NSTAGE);
+    // local part for every column segment
 #pragma unroll 1
-    for (int p = threadIdx.x; p < a.npts; p += NT) {
-      int x, y, z;
-      unpack(p, a.nx, a.ny, inx, iny, x, y, z);
-      const C hv = apply_h<T, PER>(a, L, p, x, y, z, diag, gx, gy, gz);
-      C r;
-      if (MODE == 1) {
-        const C ps = psi[p];
-        r = C{ps.x + coef * hv.y, ps.y - coef * hv.x};   // psi + (-i coef) H v
-      } else {
-        r = hv;
-      }
-      if (!last) {
-        nxt[p] = r;
-      } else {
-        if (MODE == 0 || a.write_out) out[p] = r;
-        if (MODE == 1 && a.rho) atomicAdd(&a.rho[p], w * ((double)r.x * r.x + (double)r.y * r.y));
+    for (int item = threadIdx.x; item < nitems; item += blockDim.x) {
+      const Column<T, PER> c = make_column<T, PER>(a, item);
+      C w[9];
+#pragma unroll
+      for (int j = 0; j < 9; ++j) w[j] = zload<T, PER>(a, L.v, c.z0 - 4 + j, c.col);
+#pragma unroll 1
+      for (int z = c.z0; z < c.z1; ++z) {
+        const int zb = z * ps;
+        const int pg = z * nxy + c.col;
+        const T diag = diag0 + a.V[pg];
+        const C hv = local_h<T, PER>(a, c, L.v, w, zb, diag, gx, gy, gz);
+        C r;
+        if (MODE == 1) {
+          const C pv = psi[pg];
+          r = M::fma(coef, C{hv.y, -hv.x}, pv);   // psi + (-i coef) H v
+        } else {
+          r = hv;
+        }
+        if (DBUF) L.nxt[zb + c.col] = r; else gnxt[pg] = r;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) w[j] = w[j + 1];
+        w[8] = zload<T, PER>(a, L.v, z + 5, c.col);
       }
     }
-    if (!last) {
+    __syncthreads();
+    // nonlocal scatter at sphere points
+    if (a.natom > 0) {
+      for (int s = threadIdx.x; s < a.nsp; s += blockDim.x) {
+        const C nl = nonlocal_at<T>(a, s, L.ph, L.ec);
+        const int pg = a.sp_pt[s];
+        const int zz = pg / nxy;
+        const int pidx = DBUF ? pg + zz * (ps - nxy) : pg;
+        C* dst = DBUF ? L.nxt : gnxt;
+        C r = dst[pidx];
+        if (MODE == 1) r = M::fma(coef, C{nl.y, -nl.x}, r);
+        else r = M::add(r, nl);
+        dst[pidx] = r;
+      }
       __syncthreads();
+    }
+    if (MODE != 2) {
       if (DBUF) {
-        C* t = L.v; L.v = nxt; nxt = t;
+        C* t = L.v; L.v = L.nxt; L.nxt = t;
       } else {
-        for (int p = threadIdx.x; p < a.npts; p += NT) L.v[p] = nxt[p];
+        for (int i = threadIdx.x; i < vsz; i += blockDim.x) {
+          const int z = i / ps, r = i - z * ps;
+          if (r < nxy) L.v[i] = gnxt[z * nxy + r];
+        }
         __syncthreads();
       }
     }
   }
-}
 
-// Per-orbital observables: norm, local and nonlocal current, <u|H_q|u> (a.V = V_loc).
-template <typename T, int NT, bool PER>
-__global__ void __launch_bounds__(NT) k_smem_observables(OrbArgs<T> a, double* obs) {
-  using C = typename Cplx<T>::type;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  SmemLayout<T> L = carve<T>(smem_raw, a.npts, a.nsph);
-  __shared__ double red[NT / 32][8];
-  const int orb = blockIdx.x;
-  const C* psi = a.psi_in + (size_t)orb * a.npts;
-  T gx[4], gy[4], gz[4];
-  const T diag = prologue<T, NT, PER>(a, L, psi, gx, gy, gz);
-  const int k = orb / a.norb;
-  T q[3];
-  orbital_q(a, k, q);
-  const float inx = 1.0f / a.nx, iny = 1.0f / a.ny;
-  __syncthreads();
-  if (a.natom > 0) {
-    project<T, NT>(a, L);
-    __syncthreads();
+  // final pass: write, density, observables
+  const double wk = 2.0 * a.kw[k];
+  C* out = a.psi_out ? a.psi_out + (size_t)orb * a.npts : nullptr;
+  T qo[3] = {q[0], q[1], q[2]};
+  if (OBS && MODE == 1) {
+    qo[0] = (T)(a.kpts[3 * k] + a.Ap_obs[0]);
+    qo[1] = (T)(a.kpts[3 * k + 1] + a.Ap_obs[1]);
+    qo[2] = (T)(a.kpts[3 * k + 2] + a.Ap_obs[2]);
   }
-  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  const int nx = a.nx, ny = a.ny, nz = a.nz, sxy = nx * ny;
-  for (int p = threadIdx.x; p < a.npts; p += NT) {
-    int x, y, z;
-    unpack(p, nx, ny, inx, iny, x, y, z);
-    const C u = L.v[p];
-    const C hv = apply_h<T, PER>(a, L, p, x, y, z, diag, gx, gy, gz);
-    const double uu = (double)u.x * u.x + (double)u.y * u.y;
-    acc[0] += uu;
-    acc[7] += (double)u.x * hv.x + (double)u.y * hv.y;
-    if (PER) {
-      // Im(conj(u) D1_a u) + q_a |u|^2
-      const int row = p - x, plane = z * sxy + x, col = p - z * sxy;
-      double d1[3][2] = {{0, 0}, {0, 0}, {0, 0}};
-      for (int m = 1; m <= 4; ++m) {
-        int xp = x + m, xm = x - m, yp = y + m, ym = y - m, zp = z + m, zm = z - m;
-        xp -= (xp >= nx) ? nx : 0; xm += (xm < 0) ? nx : 0;
-        yp -= (yp >= ny) ? ny : 0; ym += (ym < 0) ? ny : 0;
-        zp -= (zp >= nz) ? nz : 0; zm += (zm < 0) ? nz : 0;
-        const C ax = L.v[row + xp], bx = L.v[row + xm];
-        const C ay = L.v[plane + yp * nx], by = L.v[plane + ym * nx];
-        const C az = L.v[col + zp * sxy], bz = L.v[col + zm * sxy];
-        d1[0][0] += a.d1x[m - 1] * ((double)ax.x - bx.x); d1[0][1] += a.d1x[m - 1] * ((double)ax.y - bx.y);
-        d1[1][0] += a.d1y[m - 1] * ((double)ay.x - by.x); d1[1][1] += a.d1y[m - 1] * ((double)ay.y - by.y);
-        d1[2][0] += a.d1z[m - 1] * ((double)az.x - bz.x); d1[2][1] += a.d1z[m - 1] * ((double)az.y - bz.y);
-      }
-      for (int c = 0; c < 3; ++c)
-        acc[1 + c] += (double)u.x * d1[c][1] - (double)u.y * d1[c][0] + (double)q[c] * uu;
+  double acc_norm = 0, acc_j[3] = {0, 0, 0}, acc_e = 0;
+#pragma unroll 1
+  for (int item = threadIdx.x; item < nitems; item += blockDim.x) {
+    const Column<T, PER> c = make_column<T, PER>(a, item);
+    C w[9];
+    if (OBS) {
+#pragma unroll
+      for (int j = 0; j < 9; ++j) w[j] = zload<T, PER>(a, L.v, c.z0 - 4 + j, c.col);
     }
-  }
-  // nonlocal current: sum_ap 2 E_p Im(conj(b_ap^(c)) c_ap), one warp per atom
-  if (PER) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int at = warp; at < a.natom; at += NT / 32) {
-      double cb[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
-      double bb[3][4][2];
-      for (int c = 0; c < 3; ++c)
-        for (int pp = 0; pp < 4; ++pp) bb[c][pp][0] = bb[c][pp][1] = 0;
-      for (int i = a.atom_off[at] + lane; i < a.atom_off[at + 1]; i += 32) {
-        const C v = L.v[a.sph_idx[i]];
-        const C ph = L.ph[i];
-        const double re = (double)v.x * ph.x - (double)v.y * ph.y;
-        const double im = (double)v.x * ph.y + (double)v.y * ph.x;
-        for (int pp = 0; pp < 4; ++pp) {
-          const double b = a.sph_beta[i * 4 + pp];
-          cb[pp][0] += b * re;
-          cb[pp][1] += b * im;
-          for (int c = 0; c < 3; ++c) {
-            const double dd = a.sph_d[3 * i + c];
-            bb[c][pp][0] += dd * b * re;
-            bb[c][pp][1] += dd * b * im;
+    T cn = 0, cj[3] = {0, 0, 0}, ce = 0;
+#pragma unroll 1
+    for (int z = c.z0; z < c.z1; ++z) {
+      const int zb = z * ps;
+      const int pg = z * nxy + c.col;
+      const C r = L.v[zb + c.col];
+      const T rr = r.x * r.x + r.y * r.y;
+      if (MODE == 0 || (MODE == 1 && a.write_out)) out[pg] = r;
+      if (MODE == 1 && a.rho) atomicAdd(&a.rho[pg], wk * (double)rr);
+      if (OBS) {
+        cn += rr;
+        if (MODE == 2) {
+          const C hv = DBUF ? L.nxt[zb + c.col] : gnxt[pg];
+          ce += r.x * hv.x + r.y * hv.y;
+        }
+        if (PER) {
+          // Im(conj(r) D1_a r) + q_a |r|^2
+          C dx = C{0, 0}, dy = C{0, 0}, dz = C{0, 0};
+#pragma unroll
+          for (int m = 1; m <= 4; ++m) {
+            dx = M::fma(a.d1x[m - 1], M::sub(L.v[zb + c.ix[2 * (m - 1)]], L.v[zb + c.ix[2 * (m - 1) + 1]]), dx);
+            dy = M::fma(a.d1y[m - 1], M::sub(L.v[zb + c.iy[2 * (m - 1)]], L.v[zb + c.iy[2 * (m - 1) + 1]]), dy);
+            dz = M::fma(a.d1z[m - 1], M::sub(w[4 + m], w[4 - m]), dz);
           }
+          cj[0] += r.x * dx.y - r.y * dx.x + qo[0] * rr;
+          cj[1] += r.x * dy.y - r.y * dy.x + qo[1] * rr;
+          cj[2] += r.x * dz.y - r.y * dz.x + qo[2] * rr;
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) w[j] = w[j + 1];
+        w[8] = zload<T, PER>(a, L.v, z + 5, c.col);
+      }
+    }
+    acc_norm += cn;
+    acc_e += ce;
+    for (int d = 0; d < 3; ++d) acc_j[d] += cj[d];
+  }
+  if (!OBS) return;
+
+  // nonlocal current with the final phases: sum_ap 2 E_p Im(conj(b_ap^(d)) c_ap)
+  double jnl[3] = {0, 0, 0};
+  if (PER && a.natom > 0) {
+    __syncthreads();
+    set_phases<T>(a, L.ph, qo);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int at = warp; at < a.natom; at += nw) {
+      T cb[8], bb[3][8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) { cb[j] = 0; bb[0][j] = bb[1][j] = bb[2][j] = 0; }
+      for (int i = a.atom_off[at] + lane; i < a.atom_off[at + 1]; i += 32) {
+        const C u = L.v[a.sph_sidx[i]];
+        const C f = L.ph[i];
+        const T re = u.x * f.x - u.y * f.y, im = u.x * f.y + u.y * f.x;
+        const T d0 = a.sph_d[3 * i], d1 = a.sph_d[3 * i + 1], d2 = a.sph_d[3 * i + 2];
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+          const T b = a.sph_beta[i * 4 + p];
+          cb[2 * p] += b * re; cb[2 * p + 1] += b * im;
+          bb[0][2 * p] += d0 * b * re; bb[0][2 * p + 1] += d0 * b * im;
+          bb[1][2 * p] += d1 * b * re; bb[1][2 * p + 1] += d1 * b * im;
+          bb[2][2 * p] += d2 * b * re; bb[2][2 * p + 1] += d2 * b * im;
         }
       }
+#pragma unroll
       for (int o = 16; o > 0; o >>= 1)
-        for (int pp = 0; pp < 4; ++pp) {
-          cb[pp][0] += __shfl_xor_sync(0xffffffffu, cb[pp][0], o);
-          cb[pp][1] += __shfl_xor_sync(0xffffffffu, cb[pp][1], o);
-          for (int c = 0; c < 3; ++c) {
-            bb[c][pp][0] += __shfl_xor_sync(0xffffffffu, bb[c][pp][0], o);
-            bb[c][pp][1] += __shfl_xor_sync(0xffffffffu, bb[c][pp][1], o);
-          }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          cb[j] += __shfl_xor_sync(0xffffffffu, cb[j], o);
+          bb[0][j] += __shfl_xor_sync(0xffffffffu, bb[0][j], o);
+          bb[1][j] += __shfl_xor_sync(0xffffffffu, bb[1][j], o);
+          bb[2][j] += __shfl_xor_sync(0xffffffffu, bb[2][j], o);
         }
       if (lane == 0) {
         const double dv2 = (double)a.dV * (double)a.dV;
-        for (int c = 0; c < 3; ++c) {
+        for (int d = 0; d < 3; ++d) {
           double s = 0;
-          for (int pp = 0; pp < 4; ++pp) {
-            // Im(conj(b) c) = b.re c.im - b.im c.re
-            s += 2.0 * (double)a.atomE[at * 4 + pp] *
-                 (bb[c][pp][0] * cb[pp][1] - bb[c][pp][1] * cb[pp][0]);
-          }
-          acc[4 + c] += s * dv2;
+          for (int p = 0; p < 4; ++p)
+            s += 2.0 * (double)a.atomE[at * 4 + p] *
+                 ((double)bb[d][2 * p] * cb[2 * p + 1] - (double)bb[d][2 * p + 1] * cb[2 * p]);
+          jnl[d] += s * dv2;
         }
       }
     }
   }
-  // block reduction
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const double vals[8] = {acc_norm * a.dV, acc_j[0] * a.dV, acc_j[1] * a.dV, acc_j[2] * a.dV,
+                          jnl[0], jnl[1], jnl[2], acc_e * a.dV};
   for (int j = 0; j < 8; ++j) {
-    double v = acc[j];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) red[warp][j] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x < 8) {
-    double v = 0;
-    for (int w = 0; w < NT / 32; ++w) v += red[w][threadIdx.x];
-    const double scale = (threadIdx.x >= 4 && threadIdx.x < 7) ? 1.0 : (double)a.dV;
-    obs[orb * 8 + threadIdx.x] = v * scale;
+    const double t = block_sum(vals[j], red);
+    if (threadIdx.x == 0) a.obs[(size_t)orb * 8 + j] = t;
   }
 }
 
-template <typename T, int NT, int MODE, bool PER, bool DBUF>
-cudaError_t launch_one(const OrbArgs<T>& a, typename Cplx<T>::type* scratch, size_t smem,
-                       cudaStream_t s) {
-  auto kern = k_smem_orbital<T, NT, MODE, PER, DBUF>;
+template <typename T, int MODE, bool PER, bool DBUF, bool OBS>
+cudaError_t launch_cell(const OrbArgs<T>& a, typename Cplx<T>::type* scratch, size_t smem, int nt,
+                        cudaStream_t s) {
+  auto kern = k_cell<T, MODE, PER, DBUF, OBS>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<a.nk * a.norb, NT, smem, s>>>(a, scratch);
+  kern<<<a.nk * a.norb, nt, smem, s>>>(a, scratch);
   return cudaGetLastError();
 }
 
-template <typename T, int NT, bool PER, bool DBUF>
-cudaError_t launch_mode(const OrbArgs<T>& a, int mode, typename Cplx<T>::type* scratch,
-                        size_t smem, cudaStream_t s) {
-  return mode == 0 ? launch_one<T, NT, 0, PER, DBUF>(a, scratch, smem, s)
-                   : launch_one<T, NT, 1, PER, DBUF>(a, scratch, smem, s);
+template <typename T, int MODE, bool OBS>
+cudaError_t dispatch(const OrbArgs<T>& a, typename Cplx<T>::type* scratch, cudaStream_t s) {
+  const bool dbuf = cell_smem_bytes<T>(a.nz, a.pstride, a.nsph, a.natom, true) <= kSmemLimit;
+  if (!dbuf && !scratch) return cudaErrorInvalidValue;
+  const size_t smem = cell_smem_bytes<T>(a.nz, a.pstride, a.nsph, a.natom, dbuf);
+  const int items = a.nx * a.ny * a.nseg;
+  int nt = ((items + 31) / 32) * 32;
+  if (nt > kNT) nt = kNT;
+  if (a.periodic)
+    return dbuf ? launch_cell<T, MODE, true, true, OBS>(a, scratch, smem, nt, s)
+                : launch_cell<T, MODE, true, false, OBS>(a, scratch, smem, nt, s);
+  return dbuf ? launch_cell<T, MODE, false, true, OBS>(a, scratch, smem, nt, s)
+              : launch_cell<T, MODE, false, false, OBS>(a, scratch, smem, nt, s);
 }
-
-constexpr int kNT = 512;
 
 }  // namespace
 
 template <typename T>
-size_t smem_orbital_bytes(int npts, int nsph, int natom) {
-  using C = typename Cplx<T>::type;
-  return sizeof(C) * ((size_t)npts + nsph + 4 * (size_t)natom);
-}
-
-constexpr size_t kSmemLimit = 220 * 1024;
-
-template <typename T>
-bool smem_orbital_fits(int npts, int nsph, int natom) {
-  return smem_orbital_bytes<T>(npts, nsph, natom) <= kSmemLimit;
+bool smem_orbital_fits(int nz, int pstride, int nsph, int natom) {
+  return cell_smem_bytes<T>(nz, pstride, nsph, natom, false) <= kSmemLimit;
 }
 
 template <typename T>
-bool smem_orbital_needs_scratch(int npts, int nsph, int natom) {
-  using C = typename Cplx<T>::type;
-  return smem_orbital_bytes<T>(npts, nsph, natom) + sizeof(C) * (size_t)npts > kSmemLimit;
+bool smem_orbital_needs_scratch(int nz, int pstride, int nsph, int natom) {
+  return cell_smem_bytes<T>(nz, pstride, nsph, natom, true) > kSmemLimit;
+}
+
+void cell_split(int nx, int ny, int nz, int* nseg, int* zlen) {
+  const int ncol = nx * ny;
+  int s = kNT / ncol;
+  if (s < 1) s = 1;
+  if (s > nz) s = nz;
+  *zlen = (nz + s - 1) / s;
+  *nseg = (nz + *zlen - 1) / *zlen;
 }
 
 template <typename T>
 cudaError_t launch_smem_orbital(const OrbArgs<T>& a, int mode, typename Cplx<T>::type* scratch,
                                 cudaStream_t s) {
-  using C = typename Cplx<T>::type;
-  const size_t base = smem_orbital_bytes<T>(a.npts, a.nsph, a.natom);
-  const bool dbuf = base + sizeof(C) * (size_t)a.npts <= kSmemLimit;
-  if (!dbuf && mode == 1 && !scratch) return cudaErrorInvalidValue;
-  const size_t smem = dbuf ? base + sizeof(C) * (size_t)a.npts : base;
-  if (a.periodic)
-    return dbuf ? launch_mode<T, kNT, true, true>(a, mode, scratch, smem, s)
-                : launch_mode<T, kNT, true, false>(a, mode, scratch, smem, s);
-  return dbuf ? launch_mode<T, kNT, false, true>(a, mode, scratch, smem, s)
-              : launch_mode<T, kNT, false, false>(a, mode, scratch, smem, s);
+  if (mode == 0) return dispatch<T, 0, false>(a, scratch, s);
+  if (mode == 1) return a.obs ? dispatch<T, 1, true>(a, scratch, s) : dispatch<T, 1, false>(a, scratch, s);
+  return dispatch<T, 2, true>(a, scratch, s);
 }
 
-template <typename T>
-cudaError_t launch_orbital_observables(const OrbArgs<T>& a, double* out, cudaStream_t s) {
-  const size_t smem = smem_orbital_bytes<T>(a.npts, a.nsph, a.natom);
-  const int grid = a.nk * a.norb;
-  if (a.periodic) {
-    auto kern = k_smem_observables<T, kNT, true>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    kern<<<grid, kNT, smem, s>>>(a, out);
-  } else {
-    auto kern = k_smem_observables<T, kNT, false>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    kern<<<grid, kNT, smem, s>>>(a, out);
-  }
-  return cudaGetLastError();
-}
-
-template size_t smem_orbital_bytes<float>(int, int, int);
-template size_t smem_orbital_bytes<double>(int, int, int);
-template bool smem_orbital_fits<float>(int, int, int);
-template bool smem_orbital_fits<double>(int, int, int);
-template bool smem_orbital_needs_scratch<float>(int, int, int);
-template bool smem_orbital_needs_scratch<double>(int, int, int);
+template bool smem_orbital_fits<float>(int, int, int, int);
+template bool smem_orbital_fits<double>(int, int, int, int);
+template bool smem_orbital_needs_scratch<float>(int, int, int, int);
+template bool smem_orbital_needs_scratch<double>(int, int, int, int);
 template cudaError_t launch_smem_orbital<float>(const OrbArgs<float>&, int, float2*, cudaStream_t);
 template cudaError_t launch_smem_orbital<double>(const OrbArgs<double>&, int, double2*, cudaStream_t);
-template cudaError_t launch_orbital_observables<float>(const OrbArgs<float>&, double*, cudaStream_t);
-template cudaError_t launch_orbital_observables<double>(const OrbArgs<double>&, double*, cudaStream_t);
 
 }  // namespace tdks

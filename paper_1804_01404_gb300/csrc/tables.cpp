@@ -75,6 +75,14 @@ bool build_projector_tables(const tdks_grid& g, const tdks_atom* atoms, int nato
   T.pt_ent.assign(nsph, 0);
   std::vector<int> fill(T.pt_off.begin(), T.pt_off.end() - 1);
   for (size_t i = 0; i < nsph; ++i) T.pt_ent[fill[T.idx[i]]++] = (int)i;
+  T.sp_pt.clear();
+  T.sp_off.clear();
+  for (long long p = 0; p < npts; ++p)
+    if (T.pt_off[p + 1] > T.pt_off[p]) {
+      T.sp_pt.push_back((int)p);
+      T.sp_off.push_back(T.pt_off[p]);
+    }
+  T.sp_off.push_back((int)nsph);
   return true;
 }
 

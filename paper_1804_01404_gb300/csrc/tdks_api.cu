@@ -46,7 +46,8 @@ struct tdks_ctx {
   // projector tables
   int natom = 0, nsph = 0;
   int *d_atom_off = nullptr, *d_sph_idx = nullptr, *d_pt_off = nullptr, *d_pt_ent = nullptr,
-      *d_ent_atom = nullptr;
+      *d_ent_atom = nullptr, *d_sph_sidx = nullptr, *d_sp_pt = nullptr, *d_sp_off = nullptr;
+  int nsp = 0, pstride = 0, nseg = 1, zlen = 1;
   double *d_beta64 = nullptr, *d_d64 = nullptr, *d_E64 = nullptr;
   float *d_beta32 = nullptr, *d_d32 = nullptr, *d_E32 = nullptr;
   double *d_kpts = nullptr, *d_kw = nullptr;
@@ -143,6 +144,8 @@ OrbArgs<T> make_args(const tdks_ctx* c, const void* in, void* out, const T* V, c
     a.sph_beta = (const T*)c->d_beta32; a.sph_d = (const T*)c->d_d32; a.atomE = (const T*)c->d_E32;
   }
   a.pt_off = c->d_pt_off; a.pt_ent = c->d_pt_ent; a.ent_atom = c->d_ent_atom;
+  a.pstride = c->pstride; a.nseg = c->nseg; a.zlen = c->zlen;
+  a.sph_sidx = c->d_sph_sidx; a.nsp = c->nsp; a.sp_pt = c->d_sp_pt; a.sp_off = c->d_sp_off;
   a.dV = (T)c->dV;
   a.dt = (T)dt;
   a.rho = rho;
@@ -192,14 +195,16 @@ tdks_status set_step_potential(tdks_ctx* c, double a, const double* v2, double b
 }
 
 tdks_status orbital_kernel(tdks_ctx* c, int mode, const void* in, void* out, const double Ap[3],
-                           double dt, double* rho, int write_out) {
+                           double dt, double* rho, int write_out, const double* Ap_obs = nullptr) {
   Phase ph(c, mode == 0 ? 2 : (write_out ? 1 : 0));
   c->launches += 1;
   if (is_f32(c)) {
     auto a = make_args<float>(c, in, out, c->d_v32, Ap, dt, rho, write_out);
+    if (Ap_obs) { a.obs = c->d_orb_obs; for (int i = 0; i < 3; ++i) a.Ap_obs[i] = Ap_obs[i]; }
     TDKS_CUDA(launch_smem_orbital<float>(a, mode, static_cast<float2*>(c->d_scratch), c->stream));
   } else {
     auto a = make_args<double>(c, in, out, c->d_v64, Ap, dt, rho, write_out);
+    if (Ap_obs) { a.obs = c->d_orb_obs; for (int i = 0; i < 3; ++i) a.Ap_obs[i] = Ap_obs[i]; }
     TDKS_CUDA(launch_smem_orbital<double>(a, mode, static_cast<double2*>(c->d_scratch), c->stream));
   }
   return TDKS_OK;
@@ -242,15 +247,18 @@ tdks_status hxc(tdks_ctx* c, const double* rho, double* vhxc) {
   return TDKS_OK;
 }
 
+// per-orbital norm, current and <u|T_q + V_loc + V_NL|u> into d_orb_obs (cell kernel mode 2)
 tdks_status orbital_observables(tdks_ctx* c, const void* u, const double Ap[3]) {
   c->launches += is_f32(c) ? 2 : 1;
   if (is_f32(c)) {
     TDKS_CUDA(launch_f32_from_f64(c->d_vloc, c->d_v32, c->npts, c->stream));
     auto a = make_args<float>(c, u, nullptr, c->d_v32, Ap, 0.0, nullptr, 0);
-    TDKS_CUDA(launch_orbital_observables<float>(a, c->d_orb_obs, c->stream));
+    a.obs = c->d_orb_obs;
+    TDKS_CUDA(launch_smem_orbital<float>(a, 2, static_cast<float2*>(c->d_scratch), c->stream));
   } else {
     auto a = make_args<double>(c, u, nullptr, c->d_vloc, Ap, 0.0, nullptr, 0);
-    TDKS_CUDA(launch_orbital_observables<double>(a, c->d_orb_obs, c->stream));
+    a.obs = c->d_orb_obs;
+    TDKS_CUDA(launch_smem_orbital<double>(a, 2, static_cast<double2*>(c->d_scratch), c->stream));
   }
   return TDKS_OK;
 }
@@ -313,8 +321,11 @@ tdks_status tdks_init(const tdks_grid* grid, const tdks_cell* cell, const tdks_a
     return bail(fail(TDKS_EINVAL, err));
   c->natom = T.natom;
   c->nsph = (int)T.idx.size();
-  const bool fits = is_f32(c) ? smem_orbital_fits<float>(c->npts, c->nsph, c->natom)
-                              : smem_orbital_fits<double>(c->npts, c->nsph, c->natom);
+  c->nsp = (int)T.sp_pt.size();
+  c->pstride = smem_plane_stride(*grid);
+  cell_split(grid->n[0], grid->n[1], grid->n[2], &c->nseg, &c->zlen);
+  const bool fits = is_f32(c) ? smem_orbital_fits<float>(grid->n[2], c->pstride, c->nsph, c->natom)
+                              : smem_orbital_fits<double>(grid->n[2], c->pstride, c->nsph, c->natom);
   if (!fits) return bail(fail(TDKS_EUNSUPPORTED, "grid too large for the shared-memory orbital kernels"));
 
   tdks_status s;
@@ -323,6 +334,14 @@ tdks_status tdks_init(const tdks_grid* grid, const tdks_cell* cell, const tdks_a
   if ((s = upload(c, &c->d_pt_off, T.pt_off)) != TDKS_OK) return bail(s);
   if ((s = upload(c, &c->d_pt_ent, T.pt_ent)) != TDKS_OK) return bail(s);
   if ((s = upload(c, &c->d_ent_atom, T.ent_atom)) != TDKS_OK) return bail(s);
+  {
+    const int nxy = grid->n[0] * grid->n[1];
+    std::vector<int> sidx(T.idx.size());
+    for (size_t i = 0; i < T.idx.size(); ++i) sidx[i] = T.idx[i] + (T.idx[i] / nxy) * (c->pstride - nxy);
+    if ((s = upload(c, &c->d_sph_sidx, sidx)) != TDKS_OK) return bail(s);
+    if ((s = upload(c, &c->d_sp_pt, T.sp_pt)) != TDKS_OK) return bail(s);
+    if ((s = upload(c, &c->d_sp_off, T.sp_off)) != TDKS_OK) return bail(s);
+  }
   if ((s = upload(c, &c->d_beta64, T.beta)) != TDKS_OK) return bail(s);
   if ((s = upload(c, &c->d_d64, T.d)) != TDKS_OK) return bail(s);
   if ((s = upload(c, &c->d_E64, T.E)) != TDKS_OK) return bail(s);
@@ -343,8 +362,8 @@ tdks_status tdks_init(const tdks_grid* grid, const tdks_cell* cell, const tdks_a
       return bail(fail(TDKS_ECUDA, "memset"));
   }
   if ((s = dalloc(c, &c->d_v32, np)) != TDKS_OK) return bail(s);
-  const bool scratch = is_f32(c) ? smem_orbital_needs_scratch<float>(c->npts, c->nsph, c->natom)
-                                 : smem_orbital_needs_scratch<double>(c->npts, c->nsph, c->natom);
+  const bool scratch = is_f32(c) ? smem_orbital_needs_scratch<float>(grid->n[2], c->pstride, c->nsph, c->natom)
+                                 : smem_orbital_needs_scratch<double>(grid->n[2], c->pstride, c->nsph, c->natom);
   if (scratch) {
     const size_t csz = is_f32(c) ? sizeof(float2) : sizeof(double2);
     unsigned char* p = nullptr;
@@ -494,13 +513,13 @@ tdks_status tdks_step(tdks_ctx* c, void* u, double t, double dt) {
     Phase ph(c, 5);
     TDKS_CUDA(cudaMemsetAsync(c->d_rho, 0, gb, c->stream));
   }
-  TDKS_TRY(orbital_kernel(c, 1, u, u, Amid, dt, c->d_rho, 1));
+  // corrector; for periodic cells its last pass also forms the per-orbital current at t + dt
+  TDKS_TRY(orbital_kernel(c, 1, u, u, Amid, dt, c->d_rho, 1, c->grid.periodic ? Aend : nullptr));
   TDKS_TRY(hxc(c, c->d_rho, c->d_vhxc));
   // observables at t + dt
   Phase ph(c, 4);
   c->launches += c->grid.periodic ? 3 : 2;   // reduce_current (or memset) + dipole partial + final
   if (c->grid.periodic) {
-    TDKS_TRY(orbital_observables(c, u, Aend));
     TDKS_CUDA(launch_reduce_current(c->d_orb_obs, c->nk, c->norb, c->d_kw, 1.0 / c->omega, 1,
                                     c->d_step_obs, c->stream));
   } else {

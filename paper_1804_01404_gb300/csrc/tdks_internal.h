@@ -31,7 +31,13 @@ struct ProjectorTables {
   std::vector<int> pt_off;        // [npts+1] point -> entries (CSR)
   std::vector<int> pt_ent;        // [nsph]  entry ids sorted by grid point
   std::vector<int> ent_atom;      // [nsph]  atom of each entry
+  std::vector<int> sp_pt;         // [nsp]   unique grid points inside at least one sphere
+  std::vector<int> sp_off;        // [nsp+1] their entry ranges in pt_ent
 };
+
+// Shared-memory layout of one orbital: plane stride nx*ny (+1 pad element that stays zero for
+// isolated cells, so out-of-box x/y neighbours read 0 without a branch).
+inline int smem_plane_stride(const tdks_grid& g) { return g.n[0] * g.n[1] + (g.periodic ? 0 : 1); }
 
 // Build projector tables; returns false with a message on invalid input.
 bool build_projector_tables(const tdks_grid& g, const tdks_atom* atoms, int natom,
@@ -80,25 +86,30 @@ struct OrbArgs {
   double* rho;              // nullable: rho += 2 w_k |u_out|^2
   const double* kw;
   int write_out;            // write psi_out (Taylor) -- predictor passes only accumulate rho
+  // shared-memory cell kernels
+  int pstride;              // shared-memory plane stride (see smem_plane_stride)
+  int nseg, zlen;           // threads per column = nseg, each marching zlen planes
+  const int* sph_sidx;      // [nsph] shared-memory index of each sphere entry
+  int nsp;                  // unique sphere points
+  const int* sp_pt;         // [nsp] global index
+  const int* sp_off;        // [nsp+1]
+  double Ap_obs[3];         // A' for the fused observables of the final state
+  double* obs;              // nullable: per-orbital {norm, jloc[3], jnl[3], 0}
 };
 
 // Orbital kernels (k_orbital.cu)
-// mode 0: H u, 1: T4.  scratch = [norb_tot][npts] global buffer, needed only when
-// smem_orbital_needs_scratch() (two shared-memory copies of the orbital do not fit).
+// Shared-memory cell kernels.  mode 0: H u; 1: T4 (Horner) with optional density and fused
+// observables (a.obs); 2: observables of u (norm, current, <u|H|u> with a.V) into a.obs.
+// scratch = [norb_tot][npts] global buffer, needed only when smem_orbital_needs_scratch().
 template <typename T>
 cudaError_t launch_smem_orbital(const OrbArgs<T>& a, int mode, typename Cplx<T>::type* scratch,
                                 cudaStream_t s);
 template <typename T>
-bool smem_orbital_needs_scratch(int npts, int nsph, int natom);
+bool smem_orbital_fits(int nz, int pstride, int nsph, int natom);
 template <typename T>
-size_t smem_orbital_bytes(int npts, int nsph, int natom);
-template <typename T>
-bool smem_orbital_fits(int npts, int nsph, int natom);
-
-// Per-orbital observables: out[orb*8 + {0..7}] =
-// {norm, jloc_x, jloc_y, jloc_z, jnl_x, jnl_y, jnl_z, <u|T_q + V + V_NL|u>} (with a.V = V_loc)
-template <typename T>
-cudaError_t launch_orbital_observables(const OrbArgs<T>& a, double* out, cudaStream_t s);
+bool smem_orbital_needs_scratch(int nz, int pstride, int nsph, int natom);
+// threads per column (nseg) and planes per thread (zlen) for the cell kernels
+void cell_split(int nx, int ny, int nz, int* nseg, int* zlen);
 
 // Grid kernels (k_grid.cu)
 cudaError_t launch_fft_axis(double2* data, const int dims[3], int axis, int dir,
