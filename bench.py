@@ -251,6 +251,10 @@ def gpu_arm(args, rank, world, local_rank):
            "note": "psi(0) uploaded and psi(T) downloaded once per K steps; J and dipole read "
                    "back every step (synchronising)"}
 
+    hpsi = None
+    if rank == 0 and not args.skip_hpsi:
+        hpsi = hpsi_cluster(dev)
+
     cpu = None
     if rank == 0 and not args.skip_cpu:
         nk_sample = 2
@@ -268,9 +272,54 @@ def gpu_arm(args, rank, world, local_rank):
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": st["launches"], "clocks": clk,
                 "phase_ms_per_step": phases, "step_ms_min": float(np.min(step_ms)),
-                "fp64": fp64}
+                "fp64": fp64, "hpsi_cluster": hpsi}
         print(json.dumps(line), flush=True)
     return 0
+
+
+def hpsi_cluster(dev, reps=10):
+    """tdks_hpsi on the isolated cluster (96^3 grid, 128 atoms, 256 orbitals, FP32): the large-grid
+    TMA tile path.  Orbital fields are random (hpsi time does not depend on their values); 1.8 GB
+    of orbitals is far above L2, so every launch streams from HBM.  Algorithmic bytes: read u and
+    write H u, 16 B per orbital-point."""
+    import torch
+    from paper_1804_01404_gb300 import workloads as W
+    from paper_1804_01404_gb300.tdks import Context
+    s = W.isolated_cluster()
+    g = torch.Generator(device=dev)
+    g.manual_seed(1)
+    u = torch.randn((s.nk, s.norb, s.n[2], s.n[1], s.n[0]), dtype=torch.complex64, device=dev, generator=g)
+    u *= (1.0 / np.sqrt(s.npts * s.dV))
+    hu = torch.empty_like(u)
+    ctx = Context(s, precision="f32")
+    ctx.update_potential(u)
+    for _ in range(3):
+        ctx.hpsi(u, hu)
+    torch.cuda.synchronize()
+    ctx.stats(reset=True)
+    ctx.profile(True)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        ctx.hpsi(u, hu)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    st = ctx.stats(reset=True)
+    ctx.check()
+    ms = e0.elapsed_time(e1) / reps
+    k_ms = st["ms"]["hpsi"] / max(1, st["calls"]["hpsi"])
+    nbytes = 16 * s.npts * s.nk * s.norb
+    pk = peaks()
+    res = {"workload": "isolated cluster 96^3, 128 atoms, 256 orbitals, FP32", "calls": reps,
+           "ms_per_hpsi": ms, "ms_per_hpsi_phase": k_ms, "bytes_per_hpsi": nbytes,
+           "GBps": nbytes / (k_ms * 1e-3) / 1e9, "peak_GBps": pk["hbm_gbs"],
+           "frac_of_measured_hbm": nbytes / (k_ms * 1e-3) / 1e9 / pk["hbm_gbs"],
+           "kernels": "k_gproject + k_tile<float,0> (TMA planes) + k_gscatter"}
+    ctx.close()
+    del u, hu
+    torch.cuda.empty_cache()
+    return res
 
 
 def fp64_comparison(s, psi0, dev, nsteps=10):
@@ -309,6 +358,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-hpsi", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=8)
     ap.add_argument("--fp64-steps", type=int, default=10)
     args = ap.parse_args()

@@ -358,6 +358,43 @@ __global__ void __launch_bounds__(256) k_reduce_current(const double* __restrict
   if (threadIdx.x < 3) out[threadIdx.x] = -red[threadIdx.x][0] * inv_omega;
 }
 
+template <typename C>
+__global__ void __launch_bounds__(256) k_orbital_dots(const C* __restrict__ u, const C* __restrict__ hu,
+                                                      int npts, double dV, double* out) {
+  __shared__ double red[2][256];
+  const int o = blockIdx.x;
+  const C* a = u + (size_t)o * npts;
+  const C* b = hu ? hu + (size_t)o * npts : nullptr;
+  double n = 0, e = 0;
+  for (int p = threadIdx.x; p < npts; p += blockDim.x) {
+    const C x = a[p];
+    n += (double)x.x * x.x + (double)x.y * x.y;
+    if (b) { const C y = b[p]; e += (double)x.x * y.x + (double)x.y * y.y; }
+  }
+  red[0][threadIdx.x] = n;
+  red[1][threadIdx.x] = e;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) { red[0][threadIdx.x] += red[0][threadIdx.x + h]; red[1][threadIdx.x] += red[1][threadIdx.x + h]; }
+    __syncthreads();
+  }
+  if (threadIdx.x < 8) {
+    double v = 0;
+    if (threadIdx.x == 0) v = red[0][0] * dV;
+    if (threadIdx.x == 7) v = red[1][0] * dV;
+    out[(size_t)o * 8 + threadIdx.x] = v;
+  }
+}
+
+__global__ void k_fold_density(const float* __restrict__ r32, int nk, int npts,
+                               const double* __restrict__ kw, double* __restrict__ rho) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npts; p += gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int k = 0; k < nk; ++k) acc += kw[k] * (double)r32[(size_t)k * npts + p];
+    rho[p] = acc;
+  }
+}
+
 int grid_for(long long n, int threads) {
   long long b = (n + threads - 1) / threads;
   if (b > 152 * 16) b = 152 * 16;
@@ -486,5 +523,20 @@ cudaError_t launch_reduce_current(const double* orb_obs, int nk, int norb, const
   k_reduce_current<<<1, 256, 0, s>>>(orb_obs, nk, norb, kw, inv_omega, periodic, out);
   return cudaGetLastError();
 }
+
+cudaError_t launch_fold_density(const float* rho32, int nk, int npts, const double* kw, double* rho,
+                                cudaStream_t s) {
+  k_fold_density<<<grid_for(npts, 256), 256, 0, s>>>(rho32, nk, npts, kw, rho);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_orbital_dots(const typename Cplx<T>::type* u, const typename Cplx<T>::type* hu,
+                                int norb_tot, int npts, double dV, double* out, cudaStream_t s) {
+  k_orbital_dots<<<norb_tot, 256, 0, s>>>(u, hu, npts, dV, out);
+  return cudaGetLastError();
+}
+template cudaError_t launch_orbital_dots<float>(const float2*, const float2*, int, int, double, double*, cudaStream_t);
+template cudaError_t launch_orbital_dots<double>(const double2*, const double2*, int, int, double, double*, cudaStream_t);
 
 }  // namespace tdks

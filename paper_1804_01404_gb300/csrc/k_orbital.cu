@@ -12,7 +12,8 @@
 // from shared memory through offsets computed once per column.  Complex FP32 arithmetic uses the
 // packed f32x2 instructions.  The nonlocal scatter runs as a separate pass over the grid points
 // that lie inside a projector sphere.  The last pass writes the orbital, accumulates the density
-// of Eq. (rho) (FP64 atomics) and, on request, the norm and the current of Eq. (macro_current).
+// of Eq. (rho) (FP64 atomics; FP32 orbitals add into per-k FP32 partials folded in FP64) and, on
+// request, the norm and the current of Eq. (macro_current).
 #include <cuda_runtime.h>
 
 #include "tdks_internal.h"
@@ -177,23 +178,28 @@ __device__ __forceinline__ typename Cplx<T>::type local_h(const OrbArgs<T>& a,
                                                           const T* gz) {
   using C = typename Cplx<T>::type;
   using M = CM<T>;
-  C S = M::fma(diag, w[4], C{0, 0});
-  C D = C{0, 0};
+  // independent accumulators per axis keep the FMA chains short
+  C Sx = M::fma(diag, w[4], C{0, 0}), Sy = C{0, 0}, Sz = C{0, 0};
+  C Dx = C{0, 0}, Dy = C{0, 0}, Dz = C{0, 0};
 #pragma unroll
   for (int m = 1; m <= 4; ++m) {
     const C xp = v[zb + c.ix[2 * (m - 1)]], xm = v[zb + c.ix[2 * (m - 1) + 1]];
     const C yp = v[zb + c.iy[2 * (m - 1)]], ym = v[zb + c.iy[2 * (m - 1) + 1]];
     const C zp = w[4 + m], zm = w[4 - m];
-    S = M::fma(a.c2x[m], M::add(xp, xm), S);
-    S = M::fma(a.c2y[m], M::add(yp, ym), S);
-    S = M::fma(a.c2z[m], M::add(zp, zm), S);
+    Sx = M::fma(a.c2x[m], M::add(xp, xm), Sx);
+    Sy = M::fma(a.c2y[m], M::add(yp, ym), Sy);
+    Sz = M::fma(a.c2z[m], M::add(zp, zm), Sz);
     if (PER) {
-      D = M::fma(gx[m - 1], M::sub(xp, xm), D);
-      D = M::fma(gy[m - 1], M::sub(yp, ym), D);
-      D = M::fma(gz[m - 1], M::sub(zp, zm), D);
+      Dx = M::fma(gx[m - 1], M::sub(xp, xm), Dx);
+      Dy = M::fma(gy[m - 1], M::sub(yp, ym), Dy);
+      Dz = M::fma(gz[m - 1], M::sub(zp, zm), Dz);
     }
   }
-  if (PER) S = C{S.x + D.y, S.y - D.x};   // + (-i) D
+  C S = M::add(M::add(Sx, Sy), Sz);
+  if (PER) {
+    const C D = M::add(M::add(Dx, Dy), Dz);
+    S = C{S.x + D.y, S.y - D.x};   // + (-i) D
+  }
   return S;
 }
 
@@ -306,15 +312,21 @@ __global__ void __launch_bounds__(kNT) k_cell(OrbArgs<T> a, typename Cplx<T>::ty
       C w[9];
 #pragma unroll
       for (int j = 0; j < 9; ++j) w[j] = zload<T, PER>(a, L.v, c.z0 - 4 + j, c.col);
+      T vnext = a.V[c.z0 * nxy + c.col];
+      C pnext = (MODE == 1) ? psi[c.z0 * nxy + c.col] : C{0, 0};
 #pragma unroll 1
       for (int z = c.z0; z < c.z1; ++z) {
         const int zb = z * ps;
         const int pg = z * nxy + c.col;
-        const T diag = diag0 + a.V[pg];
+        const T diag = diag0 + vnext;
+        const C pv = pnext;
+        if (z + 1 < c.z1) {                   // prefetch the next plane's V and psi
+          vnext = a.V[pg + nxy];
+          if (MODE == 1) pnext = psi[pg + nxy];
+        }
         const C hv = local_h<T, PER>(a, c, L.v, w, zb, diag, gx, gy, gz);
         C r;
         if (MODE == 1) {
-          const C pv = psi[pg];
           r = M::fma(coef, C{hv.y, -hv.x}, pv);   // psi + (-i coef) H v
         } else {
           r = hv;
@@ -380,7 +392,10 @@ __global__ void __launch_bounds__(kNT) k_cell(OrbArgs<T> a, typename Cplx<T>::ty
       const C r = L.v[zb + c.col];
       const T rr = r.x * r.x + r.y * r.y;
       if (MODE == 0 || (MODE == 1 && a.write_out)) out[pg] = r;
-      if (MODE == 1 && a.rho) atomicAdd(&a.rho[pg], wk * (double)rr);
+      if (MODE == 1) {
+        if (a.rho32) atomicAdd(&a.rho32[(size_t)k * a.npts + pg], 2.0f * (float)rr);
+        else if (a.rho) atomicAdd(&a.rho[pg], wk * (double)rr);
+      }
       if (OBS) {
         cn += rr;
         if (MODE == 2) {

@@ -55,7 +55,12 @@ struct tdks_ctx {
   double *d_vloc = nullptr, *d_vhxc = nullptr, *d_vpred = nullptr, *d_rho = nullptr,
          *d_rho0 = nullptr, *d_rho_tmp = nullptr, *d_v64 = nullptr;
   float* d_v32 = nullptr;
+  float* d_rho32 = nullptr;      // [nk][npts] per-k FP32 density partials (FP32 orbitals)
   void* d_scratch = nullptr;     // [norb_tot][npts] complex, only for cells whose two copies exceed smem
+  // large isolated grids (tile kernels): two Horner buffers and the projection coefficients
+  bool tiled = false;
+  void *d_bufA = nullptr, *d_bufB = nullptr, *d_ec = nullptr;
+  int* d_err = nullptr;
   bool have_rho0 = false, have_potential = false;
   // FFT
   int m[3] = {0, 0, 0};
@@ -194,14 +199,90 @@ tdks_status set_step_potential(tdks_ctx* c, double a, const double* v2, double b
   return TDKS_OK;
 }
 
+template <typename T>
+TileArgs<T> make_tile_args(const tdks_ctx* c, const T* V) {
+  TileArgs<T> a;
+  std::memset(&a, 0, sizeof(a));
+  a.nx = c->grid.n[0]; a.ny = c->grid.n[1]; a.nz = c->grid.n[2];
+  a.npts = c->npts;
+  a.norb_tot = c->nk * c->norb;
+  a.V = V;
+  for (int m = 0; m < 5; ++m) {
+    a.c2x[m] = (T)(-0.5 * kFD2[m] / (c->grid.h[0] * c->grid.h[0]));
+    a.c2y[m] = (T)(-0.5 * kFD2[m] / (c->grid.h[1] * c->grid.h[1]));
+    a.c2z[m] = (T)(-0.5 * kFD2[m] / (c->grid.h[2] * c->grid.h[2]));
+  }
+  a.diag = a.c2x[0] + a.c2y[0] + a.c2z[0];
+  a.err = c->d_err;
+  a.natom = c->natom; a.nsp = c->nsp;
+  a.atom_off = c->d_atom_off; a.sph_idx = c->d_sph_idx;
+  a.sph_beta = sizeof(T) == 8 ? (const T*)c->d_beta64 : (const T*)c->d_beta32;
+  a.atomE = sizeof(T) == 8 ? (const T*)c->d_E64 : (const T*)c->d_E32;
+  a.dV = (T)c->dV;
+  a.ec = static_cast<typename Cplx<T>::type*>(c->d_ec);
+  a.sp_pt = c->d_sp_pt; a.sp_off = c->d_sp_off; a.pt_ent = c->d_pt_ent; a.ent_atom = c->d_ent_atom;
+  return a;
+}
+
+// Large isolated grids: H u (mode 0) or T4 u (mode 1, Horner through the two work buffers).
+template <typename T>
+tdks_status tiled_kernel(tdks_ctx* c, int mode, const void* in, void* out, double dt, double* rho,
+                         int write_out) {
+  using C = typename Cplx<T>::type;
+  const T* V = sizeof(T) == 8 ? (const T*)c->d_v64 : (const T*)c->d_v32;
+  TileArgs<T> a = make_tile_args<T>(c, V);
+  if (mode == 0) {
+    a.out = static_cast<C*>(out);
+    TDKS_CUDA(launch_tile_project<T>(a, static_cast<const C*>(in), c->stream));
+    TDKS_CUDA(launch_tile_stage<T>(a, in, 0, c->stream));
+    TDKS_CUDA(launch_tile_scatter<T>(a, a.out, 0, c->stream));
+    c->launches += 3;
+    return TDKS_OK;
+  }
+  const C* u = static_cast<const C*>(in);
+  C* A = static_cast<C*>(c->d_bufA);
+  C* B = static_cast<C*>(c->d_bufB);
+  C* fin = write_out ? static_cast<C*>(out) : B;
+  C* dst[4] = {A, B, A, fin};
+  const C* v = u;
+  a.psi = u;
+  for (int st = 0; st < 4; ++st) {
+    a.coef = (T)(dt / (4 - st));
+    a.out = dst[st];
+    TDKS_CUDA(launch_tile_project<T>(a, v, c->stream));
+    TDKS_CUDA(launch_tile_stage<T>(a, v, 1, c->stream));
+    TDKS_CUDA(launch_tile_scatter<T>(a, a.out, 1, c->stream));
+    c->launches += 3;
+    v = a.out;
+  }
+  if (rho) {
+    TDKS_CUDA(launch_density<T>(fin, c->nk, c->norb, c->npts, c->d_kw, rho, c->stream));
+    c->launches += 1;
+  }
+  return TDKS_OK;
+}
+
 tdks_status orbital_kernel(tdks_ctx* c, int mode, const void* in, void* out, const double Ap[3],
                            double dt, double* rho, int write_out, const double* Ap_obs = nullptr) {
   Phase ph(c, mode == 0 ? 2 : (write_out ? 1 : 0));
+  if (c->tiled)
+    return is_f32(c) ? tiled_kernel<float>(c, mode, in, out, dt, rho, write_out)
+                     : tiled_kernel<double>(c, mode, in, out, dt, rho, write_out);
   c->launches += 1;
   if (is_f32(c)) {
     auto a = make_args<float>(c, in, out, c->d_v32, Ap, dt, rho, write_out);
+    if (rho) {
+      // per-k FP32 partial densities, folded into rho in FP64 afterwards
+      TDKS_CUDA(cudaMemsetAsync(c->d_rho32, 0, sizeof(float) * (size_t)c->nk * c->npts, c->stream));
+      a.rho = nullptr;
+      a.rho32 = c->d_rho32;
+    }
     if (Ap_obs) { a.obs = c->d_orb_obs; for (int i = 0; i < 3; ++i) a.Ap_obs[i] = Ap_obs[i]; }
     TDKS_CUDA(launch_smem_orbital<float>(a, mode, static_cast<float2*>(c->d_scratch), c->stream));
+    if (rho) {
+      TDKS_CUDA(launch_fold_density(c->d_rho32, c->nk, c->npts, c->d_kw, rho, c->stream));
+      c->launches += 1;
+    }
   } else {
     auto a = make_args<double>(c, in, out, c->d_v64, Ap, dt, rho, write_out);
     if (Ap_obs) { a.obs = c->d_orb_obs; for (int i = 0; i < 3; ++i) a.Ap_obs[i] = Ap_obs[i]; }
@@ -249,6 +330,18 @@ tdks_status hxc(tdks_ctx* c, const double* rho, double* vhxc) {
 
 // per-orbital norm, current and <u|T_q + V_loc + V_NL|u> into d_orb_obs (cell kernel mode 2)
 tdks_status orbital_observables(tdks_ctx* c, const void* u, const double Ap[3]) {
+  if (c->tiled) {   // isolated: no current; H u with V_loc into the work buffer, then dots
+    TDKS_TRY(set_step_potential(c, 0.0, nullptr, 0.0));
+    TDKS_TRY(orbital_kernel(c, 0, u, c->d_bufA, Ap, 0.0, nullptr, 1));
+    c->launches += 1;
+    if (is_f32(c))
+      TDKS_CUDA(launch_orbital_dots<float>(static_cast<const float2*>(u), static_cast<const float2*>(c->d_bufA),
+                                           c->nk * c->norb, c->npts, c->dV, c->d_orb_obs, c->stream));
+    else
+      TDKS_CUDA(launch_orbital_dots<double>(static_cast<const double2*>(u), static_cast<const double2*>(c->d_bufA),
+                                            c->nk * c->norb, c->npts, c->dV, c->d_orb_obs, c->stream));
+    return TDKS_OK;
+  }
   c->launches += is_f32(c) ? 2 : 1;
   if (is_f32(c)) {
     TDKS_CUDA(launch_f32_from_f64(c->d_vloc, c->d_v32, c->npts, c->stream));
@@ -326,7 +419,14 @@ tdks_status tdks_init(const tdks_grid* grid, const tdks_cell* cell, const tdks_a
   cell_split(grid->n[0], grid->n[1], grid->n[2], &c->nseg, &c->zlen);
   const bool fits = is_f32(c) ? smem_orbital_fits<float>(grid->n[2], c->pstride, c->nsph, c->natom)
                               : smem_orbital_fits<double>(grid->n[2], c->pstride, c->nsph, c->natom);
-  if (!fits) return bail(fail(TDKS_EUNSUPPORTED, "grid too large for the shared-memory orbital kernels"));
+  if (!fits) {
+    const int eb = is_f32(c) ? 8 : 16;
+    if (grid->periodic || !tile_supported(grid->n[0], grid->n[1], grid->n[2], eb))
+      return bail(fail(TDKS_EUNSUPPORTED,
+                       "grid too large for the shared-memory cell kernels; the tiled kernels need an "
+                       "isolated grid with nx * element size a multiple of 16 bytes"));
+    c->tiled = true;
+  }
 
   tdks_status s;
   if ((s = upload(c, &c->d_atom_off, T.atom_off)) != TDKS_OK) return bail(s);
@@ -362,8 +462,21 @@ tdks_status tdks_init(const tdks_grid* grid, const tdks_cell* cell, const tdks_a
       return bail(fail(TDKS_ECUDA, "memset"));
   }
   if ((s = dalloc(c, &c->d_v32, np)) != TDKS_OK) return bail(s);
-  const bool scratch = is_f32(c) ? smem_orbital_needs_scratch<float>(grid->n[2], c->pstride, c->nsph, c->natom)
-                                 : smem_orbital_needs_scratch<double>(grid->n[2], c->pstride, c->nsph, c->natom);
+  if ((s = dalloc(c, &c->d_err, 1)) != TDKS_OK) return bail(s);
+  if (is_f32(c) && !c->tiled)
+    if ((s = dalloc(c, &c->d_rho32, np * (size_t)nk)) != TDKS_OK) return bail(s);
+  cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
+  if (c->tiled) {
+    const size_t csz = is_f32(c) ? sizeof(float2) : sizeof(double2);
+    unsigned char *pa = nullptr, *pb = nullptr, *pe = nullptr;
+    if ((s = dalloc(c, &pa, csz * np * (size_t)nk * norb)) != TDKS_OK) return bail(s);
+    if ((s = dalloc(c, &pb, csz * np * (size_t)nk * norb)) != TDKS_OK) return bail(s);
+    if ((s = dalloc(c, &pe, csz * 4 * (size_t)(c->natom > 0 ? c->natom : 1) * nk * norb)) != TDKS_OK) return bail(s);
+    c->d_bufA = pa; c->d_bufB = pb; c->d_ec = pe;
+  }
+  const bool scratch = !c->tiled &&
+      (is_f32(c) ? smem_orbital_needs_scratch<float>(grid->n[2], c->pstride, c->nsph, c->natom)
+                 : smem_orbital_needs_scratch<double>(grid->n[2], c->pstride, c->nsph, c->natom));
   if (scratch) {
     const size_t csz = is_f32(c) ? sizeof(float2) : sizeof(double2);
     unsigned char* p = nullptr;
@@ -605,6 +718,12 @@ tdks_status tdks_check(tdks_ctx* c) {
   TDKS_TRY(check_ctx(c));
   TDKS_CUDA(cudaStreamSynchronize(c->stream));
   TDKS_CUDA(cudaGetLastError());
+  int err = 0;
+  TDKS_CUDA(cudaMemcpy(&err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (err != 0) {
+    cudaMemset(c->d_err, 0, sizeof(int));
+    return fail((tdks_status)err, "a device-side wait timed out (kernel gave up and returned)");
+  }
   return TDKS_OK;
 }
 

@@ -83,7 +83,8 @@ struct OrbArgs {
   const int* ent_atom;
   T dV;
   T dt;
-  double* rho;              // nullable: rho += 2 w_k |u_out|^2
+  double* rho;              // nullable: rho += 2 w_k |u_out|^2 (FP64 orbitals)
+  float* rho32;             // FP32 orbitals: rho32[k][p] += 2 |u_out|^2, folded into rho later
   const double* kw;
   int write_out;            // write psi_out (Taylor) -- predictor passes only accumulate rho
   // shared-memory cell kernels
@@ -110,6 +111,45 @@ template <typename T>
 bool smem_orbital_needs_scratch(int nz, int pstride, int nsph, int natom);
 // threads per column (nseg) and planes per thread (zlen) for the cell kernels
 void cell_split(int nx, int ny, int nz, int* nseg, int* zlen);
+
+// Large isolated grids (k_tile.cu): one Horner stage / H application per launch.
+template <typename T>
+struct TileArgs {
+  using C = typename Cplx<T>::type;
+  int nx, ny, nz, npts, norb_tot;
+  const C* psi;             // Horner base (mode 1)
+  C* out;
+  const T* V;               // [npts]
+  T c2x[5], c2y[5], c2z[5]; // -1/2 FD2[m] / h^2
+  T diag;                   // c2x[0] + c2y[0] + c2z[0]
+  T coef;                   // dt / m (mode 1)
+  int* err;                 // device error word (TDKS_ETIMEOUT on a timed-out wait)
+  // projectors (q = 0)
+  int natom, nsp;
+  const int* atom_off;
+  const int* sph_idx;
+  const T* sph_beta;
+  const T* atomE;
+  T dV;
+  C* ec;                    // [norb_tot][natom][4] E_p dV c_ap
+  const int* sp_pt;
+  const int* sp_off;
+  const int* pt_ent;
+  const int* ent_atom;
+};
+bool tile_supported(int nx, int ny, int nz, int elem_bytes);
+// local part of one stage: mode 0 out = H_loc vin, mode 1 out = psi + (-i coef) H_loc vin
+template <typename T>
+cudaError_t launch_tile_stage(const TileArgs<T>& a, const void* vin, int mode, cudaStream_t s);
+template <typename T>
+cudaError_t launch_tile_project(const TileArgs<T>& a, const typename Cplx<T>::type* v, cudaStream_t s);
+// out += V_NL (mode 0) or out += (-i coef) V_NL (mode 1) at sphere points, from a.ec
+template <typename T>
+cudaError_t launch_tile_scatter(const TileArgs<T>& a, typename Cplx<T>::type* out, int mode, cudaStream_t s);
+// per-orbital out[o*8+0] = sum |u|^2 dV, out[o*8+7] = Re sum conj(u) hu dV (hu nullable)
+template <typename T>
+cudaError_t launch_orbital_dots(const typename Cplx<T>::type* u, const typename Cplx<T>::type* hu,
+                                int norb_tot, int npts, double dV, double* out, cudaStream_t s);
 
 // Grid kernels (k_grid.cu)
 cudaError_t launch_fft_axis(double2* data, const int dims[3], int axis, int dir,
@@ -149,5 +189,8 @@ cudaError_t launch_dipole(const double* rho, const double* rho0, const int n[3],
 cudaError_t launch_reduce_current(const double* orb_obs, int nk, int norb, const double* kw,
                                   double inv_omega, int periodic, double* out, cudaStream_t s);
 cudaError_t launch_f32_from_f64(const double* src, float* dst, size_t count, cudaStream_t s);
+// rho[p] = sum_k w_k rho32[k][p] in FP64 (fixed order)
+cudaError_t launch_fold_density(const float* rho32, int nk, int npts, const double* kw, double* rho,
+                                cudaStream_t s);
 
 }  // namespace tdks
