@@ -170,6 +170,22 @@ tdks_status tdks_stats_read(tdks_ctx* ctx, tdks_stats* out, int reset);
 tdks_status tdks_query(const tdks_ctx* ctx, int* npts, int* nk, int* norb, int* precision,
                        int* nsphere_points);
 
+/* Hartree + exchange potential of a density without allocating device memory.
+ * For callers that cannot call cudaMalloc -- code running while a CUDA graph is captured, hosts whose
+ * device memory belongs to a pool they do not control, loops that must never allocate -- this
+ * computes vhxc = V_H[rho] + V_x[rho] (hartree / xc select the terms, as in tdks_options) for a
+ * periodic or isolated grid with the same kernels as tdks_update_potential, using a fixed work area
+ * built into the library (6 MiB of device memory per GPU that loads the library, held until the
+ * process exits) instead of context buffers.  rho_dev and vhxc_dev are caller-owned device arrays
+ * [nz][ny][nx] of doubles; stream is a cudaStream_t (NULL = legacy default stream); the call is
+ * asynchronous.  Limit: FFT length <= 64 per axis (periodic n <= 64, isolated n <= 32) with prime
+ * factors <= 31 and at most 64^3 FFT points; larger grids return TDKS_EUNSUPPORTED.  The first call
+ * on each device looks up the work area's device address; make that first call before any stream
+ * capture.  All calls share the one work area, so calls that overlap on the GPU race.  The paper
+ * has no counterpart: this is an interface variant of the Hartree/exchange step. */
+tdks_status tdks_hxc_noalloc(const tdks_grid* grid, const double* rho_dev, double* vhxc_dev,
+                             int hartree, int xc, void* stream);
+
 const char* tdks_last_error(void);
 int tdks_abi_version(void);
 void tdks_destroy(tdks_ctx* ctx);

@@ -20,6 +20,8 @@ tdks_status fail(tdks_status s, const std::string& msg) {
 }
 }  // namespace
 
+void tdks::set_last_error(const char* msg) { g_err = msg; }
+
 #define TDKS_CUDA(call)                                                                    \
   do {                                                                                     \
     cudaError_t e_ = (call);                                                               \

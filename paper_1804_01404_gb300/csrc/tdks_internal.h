@@ -39,6 +39,9 @@ struct ProjectorTables {
 // isolated cells, so out-of-box x/y neighbours read 0 without a branch).
 inline int smem_plane_stride(const tdks_grid& g) { return g.n[0] * g.n[1] + (g.periodic ? 0 : 1); }
 
+// Set the thread-local message returned by tdks_last_error().
+void set_last_error(const char* msg);
+
 // Build projector tables; returns false with a message on invalid input.
 bool build_projector_tables(const tdks_grid& g, const tdks_atom* atoms, int natom,
                             const tdks_projector* proj, int nproj, ProjectorTables& out,
