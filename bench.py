@@ -277,7 +277,7 @@ def gpu_arm(args, rank, world, local_rank):
     return 0
 
 
-def hpsi_cluster(dev, reps=10):
+def hpsi_cluster(dev, reps=10, norb=256):
     """tdks_hpsi on the isolated cluster (96^3 grid, 128 atoms, 256 orbitals, FP32): the large-grid
     TMA tile path.  Orbital fields are random (hpsi time does not depend on their values); 1.8 GB
     of orbitals is far above L2, so every launch streams from HBM.  Algorithmic bytes: read u and
@@ -285,7 +285,7 @@ def hpsi_cluster(dev, reps=10):
     import torch
     from paper_1804_01404_gb300 import workloads as W
     from paper_1804_01404_gb300.tdks import Context
-    s = W.isolated_cluster()
+    s = W.isolated_cluster(norb=norb)
     g = torch.Generator(device=dev)
     g.manual_seed(1)
     u = torch.randn((s.nk, s.norb, s.n[2], s.n[1], s.n[0]), dtype=torch.complex64, device=dev, generator=g)
@@ -311,7 +311,7 @@ def hpsi_cluster(dev, reps=10):
     k_ms = st["ms"]["hpsi"] / max(1, st["calls"]["hpsi"])
     nbytes = 16 * s.npts * s.nk * s.norb
     pk = peaks()
-    res = {"workload": "isolated cluster 96^3, 128 atoms, 256 orbitals, FP32", "calls": reps,
+    res = {"workload": f"isolated cluster 96^3, 128 atoms, {norb} orbitals, FP32", "calls": reps,
            "ms_per_hpsi": ms, "ms_per_hpsi_phase": k_ms, "bytes_per_hpsi": nbytes,
            "GBps": nbytes / (k_ms * 1e-3) / 1e9, "peak_GBps": pk["hbm_gbs"],
            "frac_of_measured_hbm": nbytes / (k_ms * 1e-3) / 1e9 / pk["hbm_gbs"],
@@ -359,6 +359,10 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-hpsi", action="store_true")
+    ap.add_argument("--only", default="", choices=["", "hpsi"],
+                    help="hpsi: only the tdks_hpsi measurement on the isolated cluster (profiling)")
+    ap.add_argument("--hpsi-norb", type=int, default=256)
+    ap.add_argument("--hpsi-reps", type=int, default=10)
     ap.add_argument("--cpu-steps", type=int, default=8)
     ap.add_argument("--fp64-steps", type=int, default=10)
     args = ap.parse_args()
@@ -368,6 +372,13 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return reference_arm(args, rank, world)
+    if args.only == "hpsi":
+        import torch
+        torch.cuda.set_device(local_rank)
+        if rank == 0:
+            print(json.dumps({"hpsi_cluster": hpsi_cluster(torch.device("cuda", local_rank),
+                                                           reps=args.hpsi_reps, norb=args.hpsi_norb)}))
+        return 0
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
