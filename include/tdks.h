@@ -90,6 +90,8 @@ typedef struct {
   double norm_max;    /* max over orbitals                                                       */
   double e_band;      /* sum_k w_k sum_n 2 <u|T_q + V_loc + V_NL^q|u>                           */
   double n_elec;      /* int rho dr                                                              */
+  double residual;    /* tdks_step: ||V_Hxc(t+dt) - V~||_2 / ||V_Hxc(t+dt)||_2 of the predicted V~   */
+  double fallbacks;   /* tdks_step: predicted steps rejected so far (redone with the plain PC)       */
 } tdks_obs;
 
 /* Create a context: builds the projector tables (host), the local potential (device), the
@@ -133,7 +135,7 @@ tdks_status tdks_taylor_step(tdks_ctx* ctx, void* u_dev, double dt, const double
 tdks_status tdks_step(tdks_ctx* ctx, void* u_dev, double t, double dt);
 
 /* Copy the observables written by the last tdks_step to the host (synchronises the stream).
- * Only J, dipole and n_elec are filled; the other fields are set to 0. */
+ * J, dipole, n_elec, residual and fallbacks are filled; the other fields are set to 0. */
 tdks_status tdks_read_step_observables(tdks_ctx* ctx, tdks_obs* out);
 
 /* Compute all observables of u with A'(t) = Aprime, against the current rho0 and potential
@@ -146,6 +148,50 @@ tdks_status tdks_get_grid_array(tdks_ctx* ctx, int which, double* dst_dev);
 
 /* Wait for all work of the context's stream and report any asynchronous CUDA error. */
 tdks_status tdks_check(tdks_ctx* ctx);
+
+/* ---- Predictor of the self-consistent potential -------------------------------------------
+ * TDKS_PRED_PC (default): predictor-corrector as in tdks_step.
+ * TDKS_PRED_EXTRAP: V~(t+dt) = 2 V_Hxc(t) - V_Hxc(t-dt) replaces the predictor half-step.
+ * TDKS_PRED_LEARNED: V~(t+dt) = 2 V_Hxc(t) - V_Hxc(t-dt) + s * NN(...) (network below).
+ * In the two predicted modes a step runs one Taylor propagation with (V_Hxc(t) + V~)/2, forms
+ * V_Hxc(t+dt) and the misfit r = ||V_Hxc(t+dt) - V~|| / ||V_Hxc(t+dt)||; if r > threshold the step is
+ * undone and redone with the plain predictor-corrector (fallback).  Predicted steps need the last
+ * four potentials: the first three steps after tdks_update_potential always use the PC.  These
+ * modes read r on the host every step (one stream synchronisation per step). */
+enum { TDKS_PRED_PC = 0, TDKS_PRED_EXTRAP = 1, TDKS_PRED_LEARNED = 2 };
+tdks_status tdks_set_predictor(tdks_ctx* ctx, int mode, double threshold);
+
+/* ---- Learned potential predictor ------------------------------------------------------------
+ * A 3-layer 3D convolutional network (4 -> 16 -> 16 -> 1 channels, 3^3 kernels with bias, SiLU,
+ * circular padding for periodic grids, zero padding for isolated ones) with BF16 weights and
+ * activations and FP32 accumulation.  Inputs from V0..V3 = V_Hxc(t), V_Hxc(t-dt), V_Hxc(t-2dt),
+ * V_Hxc(t-3dt): (V0-V1)/s, (V1-V2)/s, (V2-V3)/s, (V0-<V0>)/s_V with s = rms(V0-V1) and
+ * s_V = rms(V0-<V0>); output y with V~ = 2 V0 - V1 + s y.  Loss: mean squared error of y against
+ * (V_Hxc(t+dt) - 2 V0 + V1)/s.  TDKS_NN_NPARAMS FP32 parameters, laid out W1[16][4][27], b1[16],
+ * W2[16][16][27], b2[16], W3[1][16][27], b3[1]. */
+#define TDKS_NN_NPARAMS 9105
+
+/* Allocate the network buffers and initialise the parameters from `seed` (uniform in
+ * +-1/sqrt(fan_in), last layer x0.1, biases 0) with a zeroed Adam state. */
+tdks_status tdks_nn_init(tdks_ctx* ctx, unsigned long long seed);
+
+/* Get (set = 0) or set (set = 1) the FP32 parameters through a host array of n = TDKS_NN_NPARAMS. */
+tdks_status tdks_nn_params(tdks_ctx* ctx, float* host, int n, int set);
+
+/* Train on a trajectory of potentials vseq_dev = [nt][npts] (device, FP64, V_Hxc at consecutive
+ * steps): samples t = 3..nt-2, shuffled with `seed`, mini-batches of `batch`, Adam with learning
+ * rate lr, `epochs` passes.  loss_out (host, nullable) receives the mean loss of every epoch.
+ * Synchronises the stream once per epoch. */
+tdks_status tdks_nn_train(tdks_ctx* ctx, const double* vseq_dev, int nt, int epochs, int batch,
+                          double lr, unsigned long long seed, double* loss_out);
+
+/* vpred_dev <- V~ from vhist_dev = [4][npts] (V0, V1, V2, V3); use_net = 0 gives 2 V0 - V1. */
+tdks_status tdks_nn_predict(tdks_ctx* ctx, const double* vhist_dev, double* vpred_dev, int use_net);
+
+/* Loss and parameter gradient of one sample (vhist_dev = [4][npts], vnext_dev = V_Hxc(t+dt)), without
+ * updating the parameters; grad_host = [TDKS_NN_NPARAMS] (synchronises the stream). */
+tdks_status tdks_nn_gradient(tdks_ctx* ctx, const double* vhist_dev, const double* vnext_dev,
+                             double* loss_host, float* grad_host);
 
 /* Phase timing and launch counting.
  * Phases: 0 predictor Taylor kernel, 1 corrector Taylor kernel (and tdks_taylor_step),

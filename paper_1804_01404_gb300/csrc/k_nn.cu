@@ -1,0 +1,350 @@
+// Learned potential predictor: a 3-layer 3D convolutional network (4 -> 16 -> 16 -> 1 channels,
+// 3^3 kernels, SiLU) that predicts the Hartree-exchange potential of the next step from the last
+// four, replacing the predictor half-step of the predictor-corrector scheme (Program summary).
+//
+// Storage: activations and weights that feed a convolution are BF16 values (weights are kept as
+// FP32 masters and read through their BF16 rounding); every product is accumulated in FP32.
+// Training is plain backpropagation with Adam; the weight gradient is reduced over grid points by
+// per-block partials summed in a fixed order, so a training run is deterministic.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "tdks_internal.h"
+
+namespace tdks {
+
+namespace {
+
+using bf16 = __nv_bfloat16;
+
+__device__ __forceinline__ int nb_index(const NNGrid& g, int x, int y, int z, int dx, int dy, int dz) {
+  int xx = x + dx, yy = y + dy, zz = z + dz;
+  if (g.periodic) {
+    xx += (xx < 0) ? g.nx : 0; xx -= (xx >= g.nx) ? g.nx : 0;
+    yy += (yy < 0) ? g.ny : 0; yy -= (yy >= g.ny) ? g.ny : 0;
+    zz += (zz < 0) ? g.nz : 0; zz -= (zz >= g.nz) ? g.nz : 0;
+  } else if (xx < 0 || xx >= g.nx || yy < 0 || yy >= g.ny || zz < 0 || zz >= g.nz) {
+    return -1;
+  }
+  return (zz * g.ny + yy) * g.nx + xx;
+}
+
+__device__ __forceinline__ void coords(const NNGrid& g, int p, int& x, int& y, int& z) {
+  x = p % g.nx;
+  const int r = p / g.nx;
+  y = r % g.ny;
+  z = r / g.ny;
+}
+
+__device__ __forceinline__ float silu(float y) { return y / (1.0f + expf(-y)); }
+__device__ __forceinline__ float dsilu(float y) {
+  const float s = 1.0f / (1.0f + expf(-y));
+  return s * (1.0f + y * (1.0f - s));
+}
+
+// y[co][p] = b[co] + sum_{kk, ci} W[co][ci][kk] x[ci][nb(p, kk)];  a = bf16(SiLU(y)) if ACT
+template <int CIN, int COUT, bool ACT>
+__global__ void __launch_bounds__(256) k_nn_fwd(NNGrid g, const bf16* __restrict__ x,
+                                                const float* __restrict__ W, const float* __restrict__ b,
+                                                float* __restrict__ y, bf16* __restrict__ a) {
+  __shared__ float Ws[27][CIN][COUT];
+  for (int i = threadIdx.x; i < COUT * CIN * 27; i += blockDim.x) {
+    const int co = i / (CIN * 27), r = i % (CIN * 27), ci = r / 27, kk = r % 27;
+    Ws[kk][ci][co] = W[i];
+  }
+  __syncthreads();
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < g.npts; p += gridDim.x * blockDim.x) {
+    int px, py, pz;
+    coords(g, p, px, py, pz);
+    float acc[COUT];
+#pragma unroll
+    for (int co = 0; co < COUT; ++co) acc[co] = b[co];
+    for (int kk = 0; kk < 27; ++kk) {
+      const int q = nb_index(g, px, py, pz, kk % 3 - 1, (kk / 3) % 3 - 1, kk / 9 - 1);
+      if (q < 0) continue;
+#pragma unroll
+      for (int ci = 0; ci < CIN; ++ci) {
+        const float xv = __bfloat162float(x[(size_t)ci * g.npts + q]);
+#pragma unroll
+        for (int co = 0; co < COUT; ++co) acc[co] = fmaf(Ws[kk][ci][co], xv, acc[co]);
+      }
+    }
+#pragma unroll
+    for (int co = 0; co < COUT; ++co) {
+      y[(size_t)co * g.npts + p] = acc[co];
+      if (ACT) a[(size_t)co * g.npts + p] = __float2bfloat16(silu(acc[co]));
+    }
+  }
+}
+
+// dyprev[ci][q] = SiLU'(yprev[ci][q]) * sum_{kk, co} W[co][ci][kk] dy[co][p],  nb(p, kk) = q
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(256) k_nn_bwd_data(NNGrid g, const float* __restrict__ dy,
+                                                     const float* __restrict__ W,
+                                                     const float* __restrict__ yprev,
+                                                     float* __restrict__ dyprev) {
+  __shared__ float Ws[27][COUT][CIN];
+  for (int i = threadIdx.x; i < COUT * CIN * 27; i += blockDim.x) {
+    const int co = i / (CIN * 27), r = i % (CIN * 27), ci = r / 27, kk = r % 27;
+    Ws[kk][co][ci] = W[i];
+  }
+  __syncthreads();
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < g.npts; q += gridDim.x * blockDim.x) {
+    int qx, qy, qz;
+    coords(g, q, qx, qy, qz);
+    float acc[CIN];
+#pragma unroll
+    for (int ci = 0; ci < CIN; ++ci) acc[ci] = 0.0f;
+    for (int kk = 0; kk < 27; ++kk) {
+      const int p = nb_index(g, qx, qy, qz, -(kk % 3 - 1), -((kk / 3) % 3 - 1), -(kk / 9 - 1));
+      if (p < 0) continue;
+#pragma unroll
+      for (int co = 0; co < COUT; ++co) {
+        const float d = dy[(size_t)co * g.npts + p];
+#pragma unroll
+        for (int ci = 0; ci < CIN; ++ci) acc[ci] = fmaf(Ws[kk][co][ci], d, acc[ci]);
+      }
+    }
+#pragma unroll
+    for (int ci = 0; ci < CIN; ++ci)
+      dyprev[(size_t)ci * g.npts + q] = acc[ci] * dsilu(yprev[(size_t)ci * g.npts + q]);
+  }
+}
+
+constexpr int PB = 128;   // grid points per weight-gradient block
+
+// part[blk][w]: w < COUT*CIN*27 -> sum_p dy[co][p] x[ci][nb(p, kk)], else bias: sum_p dy[co][p]
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(256) k_nn_bwd_weight(NNGrid g, const float* __restrict__ dy,
+                                                       const bf16* __restrict__ x,
+                                                       float* __restrict__ part) {
+  __shared__ float dys[COUT][PB];
+  __shared__ int nbs[27][PB];
+  constexpr int NW = COUT * CIN * 27 + COUT;
+  const int p0 = blockIdx.x * PB;
+  const int np = min(PB, g.npts - p0);
+  for (int i = threadIdx.x; i < COUT * PB; i += blockDim.x) {
+    const int co = i / PB, j = i % PB;
+    dys[co][j] = (j < np) ? dy[(size_t)co * g.npts + p0 + j] : 0.0f;
+  }
+  for (int i = threadIdx.x; i < 27 * PB; i += blockDim.x) {
+    const int kk = i / PB, j = i % PB;
+    int q = -1;
+    if (j < np) {
+      int px, py, pz;
+      coords(g, p0 + j, px, py, pz);
+      q = nb_index(g, px, py, pz, kk % 3 - 1, (kk / 3) % 3 - 1, kk / 9 - 1);
+    }
+    nbs[kk][j] = q;
+  }
+  __syncthreads();
+  for (int w = threadIdx.x; w < NW; w += blockDim.x) {
+    float acc = 0.0f;
+    if (w < COUT * CIN * 27) {
+      const int co = w / (CIN * 27), r = w % (CIN * 27), ci = r / 27, kk = r % 27;
+      const bf16* xc = x + (size_t)ci * g.npts;
+      for (int j = 0; j < np; ++j) {
+        const int q = nbs[kk][j];
+        if (q >= 0) acc = fmaf(dys[co][j], __bfloat162float(xc[q]), acc);
+      }
+    } else {
+      const int co = w - COUT * CIN * 27;
+      for (int j = 0; j < np; ++j) acc += dys[co][j];
+    }
+    part[(size_t)blockIdx.x * NW + w] = acc;
+  }
+}
+
+// grad[w] += sum_blk part[blk][w]   (fixed order)
+__global__ void k_nn_reduce(const float* __restrict__ part, int nblk, int nw, float* __restrict__ grad) {
+  for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < nw; w += gridDim.x * blockDim.x) {
+    float acc = 0.0f;
+    for (int b = 0; b < nblk; ++b) acc += part[(size_t)b * nw + w];
+    grad[w] += acc;
+  }
+}
+
+// dout = 2 (out - t) / n; loss partial sums per block, then added to *loss in fixed order
+__global__ void __launch_bounds__(256) k_nn_loss(const float* __restrict__ out, const float* __restrict__ t,
+                                                 int n, float* __restrict__ dout, double* loss) {
+  __shared__ double red[256];
+  float acc = 0.0f;
+  for (int p = threadIdx.x; p < n; p += blockDim.x) {
+    const float d = out[p] - t[p];
+    dout[p] = 2.0f * d / (float)n;
+    acc += d * d;
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *loss += red[0] / n;
+}
+
+// Adam on FP32 masters; wq = parameters rounded through BF16 (what the convolutions read)
+__global__ void k_nn_adam(float* __restrict__ p, float* __restrict__ g, float* __restrict__ m,
+                          float* __restrict__ v, float* __restrict__ wq, int n, float lr, float b1,
+                          float b2, float eps, float c1, float c2, float gscale) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float gi = g[i] * gscale;
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    p[i] = pi;
+    wq[i] = __bfloat162float(__float2bfloat16(pi));
+    g[i] = 0.0f;
+  }
+}
+
+__global__ void k_nn_round(const float* __restrict__ p, float* __restrict__ wq, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    wq[i] = __bfloat162float(__float2bfloat16(p[i]));
+}
+
+// stats[0] = s = rms(V0 - V1), stats[1] = mean(V0), stats[2] = s_V = rms(V0 - mean V0)
+__global__ void __launch_bounds__(1024) k_nn_stats(const double* __restrict__ V0, const double* __restrict__ V1,
+                                                   int n, double* stats) {
+  __shared__ double r0[1024], r1[1024], r2[1024];
+  float a = 0, b = 0, c = 0;           // per-thread partials in FP32, combined in FP64
+  for (int p = threadIdx.x; p < n; p += blockDim.x) {
+    const float d = (float)(V0[p] - V1[p]);
+    const float v = (float)V0[p];
+    a += d * d;
+    b += v;
+    c += v * v;
+  }
+  r0[threadIdx.x] = a; r1[threadIdx.x] = b; r2[threadIdx.x] = c;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) { r0[threadIdx.x] += r0[threadIdx.x + h]; r1[threadIdx.x] += r1[threadIdx.x + h]; r2[threadIdx.x] += r2[threadIdx.x + h]; }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double mean = r1[0] / n;
+    stats[0] = sqrt(fmax(r0[0] / n, 1e-300));
+    stats[1] = mean;
+    stats[2] = sqrt(fmax(r2[0] / n - mean * mean, 1e-300));
+  }
+}
+
+__global__ void k_nn_pack(const double* __restrict__ V0, const double* __restrict__ V1,
+                          const double* __restrict__ V2, const double* __restrict__ V3,
+                          const double* __restrict__ Vnext, const double* __restrict__ stats, int n,
+                          bf16* __restrict__ x, float* __restrict__ target) {
+  const double s = stats[0], m = stats[1], sv = stats[2];
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    x[p] = __float2bfloat16((float)((V0[p] - V1[p]) / s));
+    x[(size_t)n + p] = __float2bfloat16((float)((V1[p] - V2[p]) / s));
+    x[2 * (size_t)n + p] = __float2bfloat16((float)((V2[p] - V3[p]) / s));
+    x[3 * (size_t)n + p] = __float2bfloat16((float)((V0[p] - m) / sv));
+    if (Vnext) target[p] = (float)((Vnext[p] - (2.0 * V0[p] - V1[p])) / s);
+  }
+}
+
+// V~ = 2 V0 - V1 + s * out   (out nullable: linear extrapolation)
+__global__ void k_nn_apply(const double* __restrict__ V0, const double* __restrict__ V1,
+                           const float* __restrict__ out, const double* __restrict__ stats, int n,
+                           double* __restrict__ vpred) {
+  const double s = out ? stats[0] : 0.0;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x)
+    vpred[p] = 2.0 * V0[p] - V1[p] + (out ? s * (double)out[p] : 0.0);
+}
+
+// res = ||Vnew - Vpred||_2 / ||Vnew||_2
+__global__ void __launch_bounds__(1024) k_residual(const double* __restrict__ Vnew, const double* __restrict__ Vpred,
+                                                   int n, double* res) {
+  __shared__ double r0[1024], r1[1024];
+  float a = 0, b = 0;                  // per-thread partials in FP32, combined in FP64
+  for (int p = threadIdx.x; p < n; p += blockDim.x) {
+    const float d = (float)(Vnew[p] - Vpred[p]);
+    const float v = (float)Vnew[p];
+    a += d * d;
+    b += v * v;
+  }
+  r0[threadIdx.x] = a; r1[threadIdx.x] = b;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) { r0[threadIdx.x] += r0[threadIdx.x + h]; r1[threadIdx.x] += r1[threadIdx.x + h]; }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *res = sqrt(r0[0] / fmax(r1[0], 1e-300));
+}
+
+int blocks_for(int n) {
+  int b = (n + 255) / 256;
+  return b > 152 * 8 ? 152 * 8 : (b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+int nn_part_blocks(int npts) { return (npts + PB - 1) / PB; }
+
+inline const bf16* B16(const unsigned short* p) { return reinterpret_cast<const bf16*>(p); }
+inline bf16* B16(unsigned short* p) { return reinterpret_cast<bf16*>(p); }
+
+cudaError_t nn_forward(const NNBuffers& B, const NNGrid& g, cudaStream_t s) {
+  const int nb = blocks_for(g.npts);
+  k_nn_fwd<4, 16, true><<<nb, 256, 0, s>>>(g, B16(B.x0), B.wq + kNNOff[0], B.wq + kNNOff[1], B.y1, B16(B.a1));
+  k_nn_fwd<16, 16, true><<<nb, 256, 0, s>>>(g, B16(B.a1), B.wq + kNNOff[2], B.wq + kNNOff[3], B.y2, B16(B.a2));
+  k_nn_fwd<16, 1, false><<<nb, 256, 0, s>>>(g, B16(B.a2), B.wq + kNNOff[4], B.wq + kNNOff[5], B.out, nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t nn_backward(const NNBuffers& B, const NNGrid& g, cudaStream_t s) {
+  const int nb = blocks_for(g.npts);
+  const int nblk = nn_part_blocks(g.npts);
+  // layer 3: weight gradient and the gradient into layer 2
+  k_nn_bwd_weight<16, 1><<<nblk, 256, 0, s>>>(g, B.dout, B16(B.a2), B.part);
+  k_nn_reduce<<<blocks_for(16 * 27 + 1), 256, 0, s>>>(B.part, nblk, 16 * 27 + 1, B.grad + kNNOff[4]);
+  k_nn_bwd_data<16, 1><<<nb, 256, 0, s>>>(g, B.dout, B.wq + kNNOff[4], B.y2, B.dy2);
+  // layer 2
+  k_nn_bwd_weight<16, 16><<<nblk, 256, 0, s>>>(g, B.dy2, B16(B.a1), B.part);
+  k_nn_reduce<<<blocks_for(16 * 16 * 27 + 16), 256, 0, s>>>(B.part, nblk, 16 * 16 * 27 + 16, B.grad + kNNOff[2]);
+  k_nn_bwd_data<16, 16><<<nb, 256, 0, s>>>(g, B.dy2, B.wq + kNNOff[2], B.y1, B.dy1);
+  // layer 1 (no gradient into the inputs)
+  k_nn_bwd_weight<4, 16><<<nblk, 256, 0, s>>>(g, B.dy1, B16(B.x0), B.part);
+  k_nn_reduce<<<blocks_for(16 * 4 * 27 + 16), 256, 0, s>>>(B.part, nblk, 16 * 4 * 27 + 16, B.grad + kNNOff[0]);
+  return cudaGetLastError();
+}
+
+cudaError_t nn_loss(const NNBuffers& B, const NNGrid& g, double* loss_acc, cudaStream_t s) {
+  k_nn_loss<<<1, 256, 0, s>>>(B.out, B.target, g.npts, B.dout, loss_acc);
+  return cudaGetLastError();
+}
+
+cudaError_t nn_adam(const NNBuffers& B, float lr, int t, float gscale, cudaStream_t s) {
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.0f - powf(b1, (float)t), c2 = 1.0f - powf(b2, (float)t);
+  k_nn_adam<<<blocks_for(kNNParams), 256, 0, s>>>(B.params, B.grad, B.m, B.v, B.wq, kNNParams, lr, b1, b2,
+                                                   1e-8f, c1, c2, gscale);
+  return cudaGetLastError();
+}
+
+cudaError_t nn_round_weights(const NNBuffers& B, cudaStream_t s) {
+  k_nn_round<<<blocks_for(kNNParams), 256, 0, s>>>(B.params, B.wq, kNNParams);
+  return cudaGetLastError();
+}
+
+cudaError_t nn_inputs(const NNBuffers& B, const NNGrid& g, const double* V0, const double* V1,
+                      const double* V2, const double* V3, const double* Vnext, cudaStream_t s) {
+  k_nn_stats<<<1, 1024, 0, s>>>(V0, V1, g.npts, B.stats);
+  k_nn_pack<<<blocks_for(g.npts), 256, 0, s>>>(V0, V1, V2, V3, Vnext, B.stats, g.npts, B16(B.x0), B.target);
+  return cudaGetLastError();
+}
+
+cudaError_t nn_apply(const NNBuffers& B, const NNGrid& g, const double* V0, const double* V1,
+                     bool use_net, double* vpred, cudaStream_t s) {
+  k_nn_apply<<<blocks_for(g.npts), 256, 0, s>>>(V0, V1, use_net ? B.out : nullptr, B.stats, g.npts, vpred);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual(const double* Vnew, const double* Vpred, int n, double* res, cudaStream_t s) {
+  k_residual<<<1, 1024, 0, s>>>(Vnew, Vpred, n, res);
+  return cudaGetLastError();
+}
+
+}  // namespace tdks

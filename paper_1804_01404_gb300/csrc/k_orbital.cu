@@ -27,32 +27,11 @@ template <typename T> struct CM;
 
 template <> struct CM<float> {
   using C = float2;
-  static __device__ __forceinline__ unsigned long long pk(float2 v) {
-    unsigned long long r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(v.x), "f"(v.y));
-    return r;
-  }
-  static __device__ __forceinline__ float2 up(unsigned long long r) {
-    float2 v;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
-    return v;
-  }
-  static __device__ __forceinline__ C add(C a, C b) {
-    unsigned long long d;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk(a)), "l"(pk(b)));
-    return up(d);
-  }
-  static __device__ __forceinline__ C sub(C a, C b) {
-    unsigned long long d;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk(a)), "l"(pk(b)));
-    return up(d);
-  }
+  // packed f32x2 arithmetic (one instruction for the real and imaginary parts)
+  static __device__ __forceinline__ C add(C a, C b) { return __fadd2_rn(a, b); }
+  static __device__ __forceinline__ C sub(C a, C b) { return __ffma2_rn(make_float2(-1.0f, -1.0f), b, a); }
   // acc + s * a  (s real, broadcast to both lanes)
-  static __device__ __forceinline__ C fma(float s, C a, C acc) {
-    unsigned long long d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(pk(a)), "l"(pk(make_float2(s, s))), "l"(pk(acc)));
-    return up(d);
-  }
+  static __device__ __forceinline__ C fma(float s, C a, C acc) { return __ffma2_rn(make_float2(s, s), a, acc); }
   static __device__ __forceinline__ void sincos_(float x, float* s, float* c) { sincosf(x, s, c); }
 };
 

@@ -67,26 +67,8 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, i
 template <typename T> struct TM;
 template <> struct TM<float> {
   using C = float2;
-  static __device__ __forceinline__ unsigned long long pk(float2 v) {
-    unsigned long long r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(v.x), "f"(v.y));
-    return r;
-  }
-  static __device__ __forceinline__ float2 up(unsigned long long r) {
-    float2 v;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
-    return v;
-  }
-  static __device__ __forceinline__ C add(C a, C b) {
-    unsigned long long d;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk(a)), "l"(pk(b)));
-    return up(d);
-  }
-  static __device__ __forceinline__ C fma(float s, C a, C acc) {
-    unsigned long long d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(pk(a)), "l"(pk(make_float2(s, s))), "l"(pk(acc)));
-    return up(d);
-  }
+  static __device__ __forceinline__ C add(C a, C b) { return __fadd2_rn(a, b); }
+  static __device__ __forceinline__ C fma(float s, C a, C acc) { return __ffma2_rn(make_float2(s, s), a, acc); }
 };
 template <> struct TM<double> {
   using C = double2;

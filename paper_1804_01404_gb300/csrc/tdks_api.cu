@@ -3,6 +3,7 @@
 // validates arguments, owns device buffers and enqueues launches on the context's stream.
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -76,6 +77,19 @@ struct tdks_ctx {
   double* d_partials = nullptr;
   int red_blocks = 0;
   std::vector<void*> allocs;
+  // potential history (V_Hxc at t, t-dt, t-2dt, t-3dt) and the predictor
+  double* d_vhist = nullptr;     // [4][npts] ring
+  int hist_head = 0, hist_count = 0;
+  int pred_mode = TDKS_PRED_PC;
+  double pred_thr = 1e-5;
+  double* d_vnew = nullptr;      // V_Hxc(t+dt) of a predicted step before acceptance
+  double* d_resid = nullptr;     // device residual
+  double* h_resid = nullptr;     // pinned host copy
+  void* d_backup = nullptr;      // orbitals at t (predicted steps)
+  double fallbacks = 0, last_resid = 0;
+  bool nn_ready = false;
+  NNBuffers nn{};
+  int nn_step = 0;
   // profiling
   bool profiling = false;
   long long launches = 0;
@@ -162,6 +176,21 @@ OrbArgs<T> make_args(const tdks_ctx* c, const void* in, void* out, const T* V, c
 }
 
 bool is_f32(const tdks_ctx* c) { return c->opt.precision == TDKS_F32; }
+
+double* hist_slot(tdks_ctx* c, int j) {   // V_Hxc(t - j dt)
+  return c->d_vhist + (size_t)((c->hist_head - j + 8) % 4) * c->npts;
+}
+
+tdks_status hist_push(tdks_ctx* c, const double* v) {
+  c->hist_head = (c->hist_head + 1) % 4;
+  TDKS_CUDA(cudaMemcpyAsync(hist_slot(c, 0), v, c->npts * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  if (c->hist_count < 4) c->hist_count += 1;
+  return TDKS_OK;
+}
+
+NNGrid nn_grid(const tdks_ctx* c) {
+  return NNGrid{c->grid.n[0], c->grid.n[1], c->grid.n[2], c->npts, c->grid.periodic};
+}
 
 cudaEvent_t take_event(tdks_ctx* c) {
   if (!c->event_pool.empty()) {
@@ -465,6 +494,10 @@ tdks_status tdks_init(const tdks_grid* grid, const tdks_cell* cell, const tdks_a
   }
   if ((s = dalloc(c, &c->d_v32, np)) != TDKS_OK) return bail(s);
   if ((s = dalloc(c, &c->d_err, 1)) != TDKS_OK) return bail(s);
+  if ((s = dalloc(c, &c->d_vhist, 4 * np)) != TDKS_OK) return bail(s);
+  if ((s = dalloc(c, &c->d_vnew, np)) != TDKS_OK) return bail(s);
+  if ((s = dalloc(c, &c->d_resid, 2)) != TDKS_OK) return bail(s);
+  if (cudaMallocHost((void**)&c->h_resid, sizeof(double)) != cudaSuccess) return bail(fail(TDKS_ENOMEM, "pinned"));
   if (is_f32(c) && !c->tiled)
     if ((s = dalloc(c, &c->d_rho32, np * (size_t)nk)) != TDKS_OK) return bail(s);
   cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
@@ -547,6 +580,7 @@ void tdks_destroy(tdks_ctx* c) {
   for (auto& r : c->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
   for (void* p : c->allocs) cudaFree(p);
+  if (c->h_resid) cudaFreeHost(c->h_resid);
   delete c;
 }
 
@@ -584,6 +618,8 @@ tdks_status tdks_update_potential(tdks_ctx* c, const void* u) {
     c->have_rho0 = true;
   }
   c->have_potential = true;
+  c->hist_count = 0;
+  TDKS_TRY(hist_push(c, c->d_vhxc));
   return TDKS_OK;
 }
 
@@ -602,15 +638,12 @@ tdks_status tdks_taylor_step(tdks_ctx* c, void* u, double dt, const double Ap[3]
   return orbital_kernel(c, 1, u, u, Ap, dt, nullptr, 1);
 }
 
-tdks_status tdks_step(tdks_ctx* c, void* u, double t, double dt) {
-  TDKS_TRY(check_ctx(c));
-  if (!u) return fail(TDKS_EINVAL, "null orbitals");
-  if (!c->have_potential) return fail(TDKS_EINVAL, "call tdks_update_potential before tdks_step");
-  double Amid[3], Aend[3];
-  field_at(c, t + 0.5 * dt, Amid);
-  field_at(c, t + dt, Aend);
+// plain predictor-corrector (or single Taylor step) from u; leaves V_Hxc(t+dt) in d_vhxc and the
+// predictor's potential in d_vpred
+tdks_status pc_step(tdks_ctx* c, void* u, const double Amid[3], const double Aend[3], double dt) {
   const size_t gb = c->npts * sizeof(double);
-  if (c->opt.pc && (c->opt.hartree || c->opt.xc)) {
+  const bool pc = c->opt.pc && (c->opt.hartree || c->opt.xc);
+  if (pc) {
     // predictor: T4 with V(t); only its density is kept
     TDKS_TRY(set_step_potential(c, 1.0, nullptr, 0.0));
     {
@@ -631,6 +664,63 @@ tdks_status tdks_step(tdks_ctx* c, void* u, double t, double dt) {
   // corrector; for periodic cells its last pass also forms the per-orbital current at t + dt
   TDKS_TRY(orbital_kernel(c, 1, u, u, Amid, dt, c->d_rho, 1, c->grid.periodic ? Aend : nullptr));
   TDKS_TRY(hxc(c, c->d_rho, c->d_vhxc));
+  if (pc) {   // the PC's own misfit, for scale
+    TDKS_CUDA(launch_residual(c->d_vhxc, c->d_vpred, c->npts, c->d_resid, c->stream));
+    c->launches += 1;
+  }
+  return TDKS_OK;
+}
+
+// One step with a predicted V~(t+dt) in place of the predictor half-step.  Returns accepted = false
+// (and u restored) when the misfit exceeds the threshold.
+tdks_status predicted_step(tdks_ctx* c, void* u, const double Amid[3], const double Aend[3], double dt,
+                           bool* accepted) {
+  const size_t gb = c->npts * sizeof(double);
+  const size_t obytes = (size_t)c->nk * c->norb * c->npts * (is_f32(c) ? sizeof(float2) : sizeof(double2));
+  const NNGrid g = nn_grid(c);
+  const bool net = c->pred_mode == TDKS_PRED_LEARNED;
+  {
+    Phase ph(c, 5);
+    if (net) {
+      TDKS_CUDA(nn_inputs(c->nn, g, hist_slot(c, 0), hist_slot(c, 1), hist_slot(c, 2), hist_slot(c, 3), nullptr, c->stream));
+      TDKS_CUDA(nn_forward(c->nn, g, c->stream));
+      c->launches += 5;
+    }
+    TDKS_CUDA(nn_apply(c->nn, g, hist_slot(c, 0), hist_slot(c, 1), net, c->d_vpred, c->stream));
+    TDKS_CUDA(cudaMemcpyAsync(c->d_backup, u, obytes, cudaMemcpyDeviceToDevice, c->stream));
+    TDKS_CUDA(cudaMemsetAsync(c->d_rho, 0, gb, c->stream));
+    c->launches += 1;
+  }
+  TDKS_TRY(set_step_potential(c, 0.5, c->d_vpred, 0.5));
+  TDKS_TRY(orbital_kernel(c, 1, u, u, Amid, dt, c->d_rho, 1, c->grid.periodic ? Aend : nullptr));
+  TDKS_TRY(hxc(c, c->d_rho, c->d_vnew));
+  TDKS_CUDA(launch_residual(c->d_vnew, c->d_vpred, c->npts, c->d_resid, c->stream));
+  c->launches += 1;
+  TDKS_CUDA(cudaMemcpyAsync(c->h_resid, c->d_resid, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  TDKS_CUDA(cudaStreamSynchronize(c->stream));
+  c->last_resid = *c->h_resid;
+  *accepted = std::isfinite(c->last_resid) && c->last_resid <= c->pred_thr;
+  if (*accepted) {
+    TDKS_CUDA(cudaMemcpyAsync(c->d_vhxc, c->d_vnew, gb, cudaMemcpyDeviceToDevice, c->stream));
+  } else {
+    TDKS_CUDA(cudaMemcpyAsync(u, c->d_backup, obytes, cudaMemcpyDeviceToDevice, c->stream));
+    c->fallbacks += 1;
+  }
+  return TDKS_OK;
+}
+
+tdks_status tdks_step(tdks_ctx* c, void* u, double t, double dt) {
+  TDKS_TRY(check_ctx(c));
+  if (!u) return fail(TDKS_EINVAL, "null orbitals");
+  if (!c->have_potential) return fail(TDKS_EINVAL, "call tdks_update_potential before tdks_step");
+  double Amid[3], Aend[3];
+  field_at(c, t + 0.5 * dt, Amid);
+  field_at(c, t + dt, Aend);
+  bool done = false;
+  if (c->pred_mode != TDKS_PRED_PC && c->hist_count >= 4 && (c->opt.hartree || c->opt.xc))
+    TDKS_TRY(predicted_step(c, u, Amid, Aend, dt, &done));
+  if (!done) TDKS_TRY(pc_step(c, u, Amid, Aend, dt));
+  TDKS_TRY(hist_push(c, c->d_vhxc));
   // observables at t + dt
   Phase ph(c, 4);
   c->launches += c->grid.periodic ? 3 : 2;   // reduce_current (or memset) + dipole partial + final
@@ -648,12 +738,15 @@ tdks_status tdks_step(tdks_ctx* c, void* u, double t, double dt) {
 tdks_status tdks_read_step_observables(tdks_ctx* c, tdks_obs* o) {
   TDKS_TRY(check_ctx(c));
   if (!o) return fail(TDKS_EINVAL, "null output");
-  double h[8];
+  double h[8], r = 0.0;
   TDKS_CUDA(cudaMemcpyAsync(h, c->d_step_obs, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+  TDKS_CUDA(cudaMemcpyAsync(&r, c->d_resid, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   TDKS_CUDA(cudaStreamSynchronize(c->stream));
   std::memset(o, 0, sizeof(*o));
   for (int a = 0; a < 3; ++a) { o->J[a] = h[a]; o->dipole[a] = h[3 + a]; }
   o->n_elec = h[6];
+  o->residual = r;
+  o->fallbacks = c->fallbacks;
   return TDKS_OK;
 }
 
@@ -726,6 +819,160 @@ tdks_status tdks_check(tdks_ctx* c) {
     cudaMemset(c->d_err, 0, sizeof(int));
     return fail((tdks_status)err, "a device-side wait timed out (kernel gave up and returned)");
   }
+  return TDKS_OK;
+}
+
+tdks_status tdks_set_predictor(tdks_ctx* c, int mode, double threshold) {
+  TDKS_TRY(check_ctx(c));
+  if (mode < TDKS_PRED_PC || mode > TDKS_PRED_LEARNED) return fail(TDKS_EINVAL, "unknown predictor mode");
+  if (!(threshold > 0.0)) return fail(TDKS_EINVAL, "threshold must be positive");
+  if (mode == TDKS_PRED_LEARNED && !c->nn_ready) return fail(TDKS_EINVAL, "call tdks_nn_init first");
+  if (mode != TDKS_PRED_PC && !c->d_backup) {
+    const size_t obytes = (size_t)c->nk * c->norb * c->npts * (is_f32(c) ? sizeof(float2) : sizeof(double2));
+    unsigned char* p = nullptr;
+    TDKS_TRY(dalloc(c, &p, obytes));
+    c->d_backup = p;
+  }
+  if (mode != TDKS_PRED_PC && !c->nn_ready) {   // the extrapolation uses the network's buffers too
+    TDKS_TRY(tdks_nn_init(c, 0));
+  }
+  c->pred_mode = mode;
+  c->pred_thr = threshold;
+  return TDKS_OK;
+}
+
+namespace {
+unsigned long long splitmix64(unsigned long long& x) {
+  unsigned long long z = (x += 0x9E3779B97F4A7C15ULL);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+double uniform01(unsigned long long& x) { return (splitmix64(x) >> 11) * (1.0 / 9007199254740992.0); }
+}  // namespace
+
+tdks_status tdks_nn_init(tdks_ctx* c, unsigned long long seed) {
+  TDKS_TRY(check_ctx(c));
+  NNBuffers& B = c->nn;
+  const size_t np = c->npts;
+  if (!c->nn_ready) {
+    TDKS_TRY(dalloc(c, &B.x0, 4 * np));
+    TDKS_TRY(dalloc(c, &B.a1, 16 * np));
+    TDKS_TRY(dalloc(c, &B.a2, 16 * np));
+    TDKS_TRY(dalloc(c, &B.y1, 16 * np));
+    TDKS_TRY(dalloc(c, &B.y2, 16 * np));
+    TDKS_TRY(dalloc(c, &B.dy1, 16 * np));
+    TDKS_TRY(dalloc(c, &B.dy2, 16 * np));
+    TDKS_TRY(dalloc(c, &B.out, np));
+    TDKS_TRY(dalloc(c, &B.target, np));
+    TDKS_TRY(dalloc(c, &B.dout, np));
+    TDKS_TRY(dalloc(c, &B.part, (size_t)nn_part_blocks(c->npts) * (16 * 16 * 27 + 16)));
+    TDKS_TRY(dalloc(c, &B.params, kNNParams));
+    TDKS_TRY(dalloc(c, &B.grad, kNNParams));
+    TDKS_TRY(dalloc(c, &B.m, kNNParams));
+    TDKS_TRY(dalloc(c, &B.v, kNNParams));
+    TDKS_TRY(dalloc(c, &B.wq, kNNParams));
+    TDKS_TRY(dalloc(c, &B.stats, 4));
+    TDKS_TRY(dalloc(c, &B.loss, 1));
+  }
+  std::vector<float> p(kNNParams, 0.0f);
+  const int fan[3] = {4 * 27, 16 * 27, 16 * 27};
+  const int woff[3] = {kNNOff[0], kNNOff[2], kNNOff[4]}, wlen[3] = {16 * 4 * 27, 16 * 16 * 27, 16 * 27};
+  unsigned long long st = seed * 0x2545F4914F6CDD1DULL + 1;
+  for (int l = 0; l < 3; ++l) {
+    const double bound = (l == 2 ? 0.1 : 1.0) / std::sqrt((double)fan[l]);
+    for (int i = 0; i < wlen[l]; ++i) p[woff[l] + i] = (float)((2.0 * uniform01(st) - 1.0) * bound);
+  }
+  TDKS_CUDA(cudaMemcpyAsync(B.params, p.data(), kNNParams * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+  TDKS_CUDA(cudaMemsetAsync(B.grad, 0, kNNParams * sizeof(float), c->stream));
+  TDKS_CUDA(cudaMemsetAsync(B.m, 0, kNNParams * sizeof(float), c->stream));
+  TDKS_CUDA(cudaMemsetAsync(B.v, 0, kNNParams * sizeof(float), c->stream));
+  TDKS_CUDA(nn_round_weights(B, c->stream));
+  TDKS_CUDA(cudaStreamSynchronize(c->stream));
+  c->nn_ready = true;
+  c->nn_step = 0;
+  return TDKS_OK;
+}
+
+tdks_status tdks_nn_params(tdks_ctx* c, float* host, int n, int set) {
+  TDKS_TRY(check_ctx(c));
+  if (!c->nn_ready) return fail(TDKS_EINVAL, "call tdks_nn_init first");
+  if (!host || n != kNNParams) return fail(TDKS_EINVAL, "host buffer must hold TDKS_NN_NPARAMS floats");
+  if (set) {
+    TDKS_CUDA(cudaMemcpyAsync(c->nn.params, host, n * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    TDKS_CUDA(nn_round_weights(c->nn, c->stream));
+  } else {
+    TDKS_CUDA(cudaMemcpyAsync(host, c->nn.params, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+  }
+  TDKS_CUDA(cudaStreamSynchronize(c->stream));
+  return TDKS_OK;
+}
+
+tdks_status tdks_nn_train(tdks_ctx* c, const double* vseq, int nt, int epochs, int batch, double lr,
+                          unsigned long long seed, double* loss_out) {
+  TDKS_TRY(check_ctx(c));
+  if (!c->nn_ready) return fail(TDKS_EINVAL, "call tdks_nn_init first");
+  if (!vseq || nt < 5 || epochs < 1 || batch < 1 || !(lr > 0.0)) return fail(TDKS_EINVAL, "bad training arguments");
+  const NNGrid g = nn_grid(c);
+  const size_t np = c->npts;
+  std::vector<int> order;
+  for (int t = 3; t + 1 < nt; ++t) order.push_back(t);
+  unsigned long long st = seed * 0x9E3779B97F4A7C15ULL + 7;
+  for (int ep = 0; ep < epochs; ++ep) {
+    for (size_t i = order.size(); i > 1; --i) std::swap(order[i - 1], order[splitmix64(st) % i]);
+    TDKS_CUDA(cudaMemsetAsync(c->nn.loss, 0, sizeof(double), c->stream));
+    for (size_t b0 = 0; b0 < order.size(); b0 += batch) {
+      const size_t b1 = std::min(order.size(), b0 + (size_t)batch);
+      for (size_t i = b0; i < b1; ++i) {
+        const int t = order[i];
+        const double* V0 = vseq + (size_t)t * np;
+        TDKS_CUDA(nn_inputs(c->nn, g, V0, V0 - np, V0 - 2 * np, V0 - 3 * np, V0 + np, c->stream));
+        TDKS_CUDA(nn_forward(c->nn, g, c->stream));
+        TDKS_CUDA(nn_loss(c->nn, g, c->nn.loss, c->stream));
+        TDKS_CUDA(nn_backward(c->nn, g, c->stream));
+        c->launches += 15;
+      }
+      c->nn_step += 1;
+      TDKS_CUDA(nn_adam(c->nn, (float)lr, c->nn_step, 1.0f / (float)(b1 - b0), c->stream));
+      c->launches += 1;
+    }
+    double l = 0.0;
+    TDKS_CUDA(cudaMemcpyAsync(&l, c->nn.loss, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    TDKS_CUDA(cudaStreamSynchronize(c->stream));
+    if (loss_out) loss_out[ep] = l / (double)order.size();
+  }
+  return TDKS_OK;
+}
+
+tdks_status tdks_nn_predict(tdks_ctx* c, const double* vhist, double* vpred, int use_net) {
+  TDKS_TRY(check_ctx(c));
+  if (!c->nn_ready) return fail(TDKS_EINVAL, "call tdks_nn_init first");
+  if (!vhist || !vpred) return fail(TDKS_EINVAL, "null argument");
+  const NNGrid g = nn_grid(c);
+  const size_t np = c->npts;
+  TDKS_CUDA(nn_inputs(c->nn, g, vhist, vhist + np, vhist + 2 * np, vhist + 3 * np, nullptr, c->stream));
+  if (use_net) TDKS_CUDA(nn_forward(c->nn, g, c->stream));
+  TDKS_CUDA(nn_apply(c->nn, g, vhist, vhist + np, use_net != 0, vpred, c->stream));
+  return TDKS_OK;
+}
+
+tdks_status tdks_nn_gradient(tdks_ctx* c, const double* vhist, const double* vnext, double* loss,
+                             float* grad) {
+  TDKS_TRY(check_ctx(c));
+  if (!c->nn_ready) return fail(TDKS_EINVAL, "call tdks_nn_init first");
+  if (!vhist || !vnext || !loss || !grad) return fail(TDKS_EINVAL, "null argument");
+  const NNGrid g = nn_grid(c);
+  const size_t np = c->npts;
+  TDKS_CUDA(cudaMemsetAsync(c->nn.grad, 0, kNNParams * sizeof(float), c->stream));
+  TDKS_CUDA(cudaMemsetAsync(c->nn.loss, 0, sizeof(double), c->stream));
+  TDKS_CUDA(nn_inputs(c->nn, g, vhist, vhist + np, vhist + 2 * np, vhist + 3 * np, vnext, c->stream));
+  TDKS_CUDA(nn_forward(c->nn, g, c->stream));
+  TDKS_CUDA(nn_loss(c->nn, g, c->nn.loss, c->stream));
+  TDKS_CUDA(nn_backward(c->nn, g, c->stream));
+  TDKS_CUDA(cudaMemcpyAsync(grad, c->nn.grad, kNNParams * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+  TDKS_CUDA(cudaMemcpyAsync(loss, c->nn.loss, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  TDKS_CUDA(cudaMemsetAsync(c->nn.grad, 0, kNNParams * sizeof(float), c->stream));
+  TDKS_CUDA(cudaStreamSynchronize(c->stream));
   return TDKS_OK;
 }
 

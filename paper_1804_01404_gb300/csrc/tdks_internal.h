@@ -154,6 +154,31 @@ template <typename T>
 cudaError_t launch_orbital_dots(const typename Cplx<T>::type* u, const typename Cplx<T>::type* hu,
                                 int norb_tot, int npts, double dV, double* out, cudaStream_t s);
 
+// Learned potential predictor (k_nn.cu).  Parameter layout (FP32 masters, as in the oracle):
+// W1 [16][4][27], b1 [16], W2 [16][16][27], b2 [16], W3 [1][16][27], b3 [1].
+constexpr int kNNParams = 9105;
+constexpr int kNNOff[6] = {0, 1728, 1744, 8656, 8672, 9104};
+struct NNGrid { int nx, ny, nz, npts, periodic; };
+struct NNBuffers {
+  unsigned short *x0, *a1, *a2;                   // BF16 conv inputs [4|16|16][npts]
+  float *y1, *y2, *out, *target, *dout, *dy1, *dy2, *part;
+  float *params, *grad, *m, *v, *wq;              // [kNNParams]; wq = BF16-rounded params
+  double* stats;                                  // s, mean V0, s_V
+  double* loss;                                   // accumulator
+};
+int nn_part_blocks(int npts);
+cudaError_t nn_inputs(const NNBuffers& B, const NNGrid& g, const double* V0, const double* V1,
+                      const double* V2, const double* V3, const double* Vnext, cudaStream_t s);
+cudaError_t nn_forward(const NNBuffers& B, const NNGrid& g, cudaStream_t s);
+cudaError_t nn_loss(const NNBuffers& B, const NNGrid& g, double* loss_acc, cudaStream_t s);
+cudaError_t nn_backward(const NNBuffers& B, const NNGrid& g, cudaStream_t s);   // grad +=
+cudaError_t nn_adam(const NNBuffers& B, float lr, int t, float gscale, cudaStream_t s);
+cudaError_t nn_round_weights(const NNBuffers& B, cudaStream_t s);
+// vpred = 2 V0 - V1 (+ s * out if use_net)
+cudaError_t nn_apply(const NNBuffers& B, const NNGrid& g, const double* V0, const double* V1,
+                     bool use_net, double* vpred, cudaStream_t s);
+cudaError_t launch_residual(const double* Vnew, const double* Vpred, int n, double* res, cudaStream_t s);
+
 // Grid kernels (k_grid.cu)
 cudaError_t launch_fft_axis(double2* data, const int dims[3], int axis, int dir,
                             const double2* tw, const int* radices, int nrad, cudaStream_t s);

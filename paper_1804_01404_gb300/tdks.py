@@ -15,6 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libtdks.so")
 
 TDKS_F64, TDKS_F32 = 0, 1
+PRED_PC, PRED_EXTRAP, PRED_LEARNED = 0, 1, 2
+NN_NPARAMS = 9105
 FIELD_NONE, FIELD_STEP, FIELD_PULSE = 0, 1, 2
 STATUS = {0: "TDKS_OK", 1: "TDKS_EINVAL", 2: "TDKS_ENOMEM", 3: "TDKS_ECUDA", 4: "TDKS_ETIMEOUT",
           5: "TDKS_ENONFINITE", 6: "TDKS_EUNSUPPORTED"}
@@ -48,11 +50,13 @@ class Options(C.Structure):
 
 class Obs(C.Structure):
     _fields_ = [("J", C.c_double * 3), ("dipole", C.c_double * 3), ("norm_min", C.c_double),
-                ("norm_max", C.c_double), ("e_band", C.c_double), ("n_elec", C.c_double)]
+                ("norm_max", C.c_double), ("e_band", C.c_double), ("n_elec", C.c_double),
+                ("residual", C.c_double), ("fallbacks", C.c_double)]
 
     def as_dict(self):
         return dict(J=np.array(self.J[:]), dipole=np.array(self.dipole[:]), norm_min=self.norm_min,
-                    norm_max=self.norm_max, e_band=self.e_band, n_elec=self.n_elec)
+                    norm_max=self.norm_max, e_band=self.e_band, n_elec=self.n_elec,
+                    residual=self.residual, fallbacks=self.fallbacks)
 
 
 NPHASE = 6
@@ -96,6 +100,12 @@ def load_library(path: str = LIB_PATH):
         "tdks_get_grid_array": [vp, i, vp],
         "tdks_check": [vp],
         "tdks_profile": [vp, i],
+        "tdks_set_predictor": [vp, i, d],
+        "tdks_nn_init": [vp, C.c_ulonglong],
+        "tdks_nn_params": [vp, C.POINTER(C.c_float), i, i],
+        "tdks_nn_train": [vp, vp, i, i, i, d, C.c_ulonglong, C.POINTER(C.c_double)],
+        "tdks_nn_predict": [vp, vp, vp, i],
+        "tdks_nn_gradient": [vp, vp, vp, C.POINTER(C.c_double), C.POINTER(C.c_float)],
         "tdks_stats_read": [vp, C.POINTER(Stats), i],
         "tdks_query": [vp, C.POINTER(i), C.POINTER(i), C.POINTER(i), C.POINTER(i), C.POINTER(i)],
     }
@@ -215,6 +225,37 @@ class Context:
         out = torch.empty((n[2], n[1], n[0]), dtype=torch.float64, device="cuda")
         _check(self.lib.tdks_get_grid_array(self.ctx, int(which), _ptr(out)))
         return out
+
+    # ---- predictor and learned network
+    def set_predictor(self, mode, threshold=1e-5):
+        _check(self.lib.tdks_set_predictor(self.ctx, int(mode), float(threshold)))
+
+    def nn_init(self, seed=0):
+        _check(self.lib.tdks_nn_init(self.ctx, int(seed)))
+
+    def nn_params(self, values=None):
+        """Get the FP32 parameters (values=None) or set them."""
+        buf = np.zeros(NN_NPARAMS, np.float32) if values is None else np.ascontiguousarray(values, np.float32)
+        _check(self.lib.tdks_nn_params(self.ctx, buf.ctypes.data_as(C.POINTER(C.c_float)), NN_NPARAMS,
+                                       0 if values is None else 1))
+        return buf
+
+    def nn_train(self, vseq, epochs=1, batch=8, lr=1e-3, seed=0):
+        """vseq: CUDA float64 tensor [nt, nz, ny, nx] of consecutive V_Hxc; returns per-epoch loss."""
+        loss = np.zeros(epochs)
+        _check(self.lib.tdks_nn_train(self.ctx, _ptr(vseq), int(vseq.shape[0]), int(epochs), int(batch),
+                                      float(lr), int(seed), loss.ctypes.data_as(C.POINTER(C.c_double))))
+        return loss
+
+    def nn_predict(self, vhist, vpred, use_net=True):
+        _check(self.lib.tdks_nn_predict(self.ctx, _ptr(vhist), _ptr(vpred), int(use_net)))
+
+    def nn_gradient(self, vhist, vnext):
+        g = np.zeros(NN_NPARAMS, np.float32)
+        loss = C.c_double()
+        _check(self.lib.tdks_nn_gradient(self.ctx, _ptr(vhist), _ptr(vnext), C.byref(loss),
+                                         g.ctypes.data_as(C.POINTER(C.c_float))))
+        return loss.value, g
 
     def profile(self, enable=True):
         _check(self.lib.tdks_profile(self.ctx, int(enable)))
