@@ -79,8 +79,11 @@ typedef struct { double E_s, E_p, r_cut, width; } tdks_projector;
 /* precision: TDKS_F64 (orbitals, stencil and all reductions in FP64) or TDKS_F32 (FP32 complex
  * orbitals and stencil; density, current, dipole, norms and the Poisson solve stay in FP64).
  * hartree, xc: include V_H and LDA exchange (1) or leave them out (0: linear propagation).
- * pc: predictor-corrector on (1) or a single Taylor step with V(t) (0). */
-typedef struct { int precision; int hartree; int xc; int pc; } tdks_options;
+ * pc: predictor-corrector on (1) or a single Taylor step with V(t) (0).
+ * ncell: number of independent copies of the system propagated together (0 or 1: one).  With
+ * ncell > 1 (periodic grids only) orbitals are [ncell][nk][norb][nz][ny][nx] and every cell has its
+ * own density and potential; this is the batch of microscopic cells of the multiscale mode. */
+typedef struct { int precision; int hartree; int xc; int pc; int ncell; } tdks_options;
 
 /* Observables returned to the host. */
 typedef struct {
@@ -149,10 +152,26 @@ tdks_status tdks_get_grid_array(tdks_ctx* ctx, int which, double* dst_dev);
 /* Wait for all work of the context's stream and report any asynchronous CUDA error. */
 tdks_status tdks_check(tdks_ctx* ctx);
 
+/* ---- Multiscale light propagation (Sec. 5) ----------------------------------------------------
+ * A 1D grid of nX points (spacing dX, bohr) carries the z-component A(X) of the vector potential of
+ * Eq. (Maxwell_ms); the ncell cells of the context sit at X = m0 .. m0 + ncell - 1 (1 <= m0,
+ * m0 + ncell <= nX - 1), the other points are vacuum.  One tdks_ms_step: A(X, t+dt) by leapfrog from
+ * the cells' currents I(X, t), first-order Mur absorbing boundaries at both ends; then every cell
+ * takes one tdks_step-like predictor-corrector step with its own A'(t+dt/2) = (A(X,t)+A(X,t+dt))/(2c)
+ * along z (Eq. TDKS_ms), and its current density J_z at t+dt (with A(X,t+dt)) becomes I(X, t+dt).
+ * A_now, A_prev (host, [nX]): A at t = 0 and t = -dt (set the incident pulse here). */
+tdks_status tdks_ms_init(tdks_ctx* ctx, int nX, int m0, double dX, const double* A_now,
+                         const double* A_prev);
+tdks_status tdks_ms_step(tdks_ctx* ctx, void* u_dev, double t, double dt);
+/* Copy A(X, t) and I(X, t) (host arrays of nX, either may be NULL); synchronises the stream. */
+tdks_status tdks_ms_read(tdks_ctx* ctx, double* A_host, double* I_host);
+
 /* ---- Predictor of the self-consistent potential -------------------------------------------
  * TDKS_PRED_PC (default): predictor-corrector as in tdks_step.
- * TDKS_PRED_EXTRAP: V~(t+dt) = 2 V_Hxc(t) - V_Hxc(t-dt) replaces the predictor half-step.
- * TDKS_PRED_LEARNED: V~(t+dt) = 2 V_Hxc(t) - V_Hxc(t-dt) + s * NN(...) (network below).
+ * TDKS_PRED_EXTRAP: the cubic through the last four potentials, V~(t+dt) = 4 V_Hxc(t)
+ *   - 6 V_Hxc(t-dt) + 4 V_Hxc(t-2dt) - V_Hxc(t-3dt), replaces the predictor half-step (the
+ *   no-network baseline of the learned predictor).
+ * TDKS_PRED_LEARNED: V~(t+dt) = that cubic + s3 * NN(...) (network below).
  * In the two predicted modes a step runs one Taylor propagation with (V_Hxc(t) + V~)/2, forms
  * V_Hxc(t+dt) and the misfit r = ||V_Hxc(t+dt) - V~|| / ||V_Hxc(t+dt)||; if r > threshold the step is
  * undone and redone with the plain predictor-corrector (fallback).  Predicted steps need the last
@@ -164,10 +183,11 @@ tdks_status tdks_set_predictor(tdks_ctx* ctx, int mode, double threshold);
 /* ---- Learned potential predictor ------------------------------------------------------------
  * A 3-layer 3D convolutional network (4 -> 16 -> 16 -> 1 channels, 3^3 kernels with bias, SiLU,
  * circular padding for periodic grids, zero padding for isolated ones) with BF16 weights and
- * activations and FP32 accumulation.  Inputs from V0..V3 = V_Hxc(t), V_Hxc(t-dt), V_Hxc(t-2dt),
- * V_Hxc(t-3dt): (V0-V1)/s, (V1-V2)/s, (V2-V3)/s, (V0-<V0>)/s_V with s = rms(V0-V1) and
- * s_V = rms(V0-<V0>); output y with V~ = 2 V0 - V1 + s y.  Loss: mean squared error of y against
- * (V_Hxc(t+dt) - 2 V0 + V1)/s.  TDKS_NN_NPARAMS FP32 parameters, laid out W1[16][4][27], b1[16],
+ * activations and FP32 accumulation.  From V0..V3 = V_Hxc(t), V_Hxc(t-dt), V_Hxc(t-2dt),
+ * V_Hxc(t-3dt) and the backward differences D1 = V0-V1, D2 = V0-2V1+V2, D3 = V0-3V1+3V2-V3 (FP64),
+ * the inputs are D1/s1, D2/s2, D3/s3, (V0-<V0>)/s_V, each s the root mean square of its field
+ * (floored at 1e-13 rms(V0)); the output y corrects the cubic extrapolation C = 4 V0 - 6 V1 + 4 V2
+ * - V3: V~ = C + s3 y.  Loss: mean squared error of y against (V_Hxc(t+dt) - C)/s3.  TDKS_NN_NPARAMS FP32 parameters, laid out W1[16][4][27], b1[16],
  * W2[16][16][27], b2[16], W3[1][16][27], b3[1]. */
 #define TDKS_NN_NPARAMS 9105
 
@@ -185,8 +205,9 @@ tdks_status tdks_nn_params(tdks_ctx* ctx, float* host, int n, int set);
 tdks_status tdks_nn_train(tdks_ctx* ctx, const double* vseq_dev, int nt, int epochs, int batch,
                           double lr, unsigned long long seed, double* loss_out);
 
-/* vpred_dev <- V~ from vhist_dev = [4][npts] (V0, V1, V2, V3); use_net = 0 gives 2 V0 - V1. */
-tdks_status tdks_nn_predict(tdks_ctx* ctx, const double* vhist_dev, double* vpred_dev, int use_net);
+/* vpred_dev <- V~ from vhist_dev = [4][npts] (V0, V1, V2, V3): mode 0 = linear extrapolation
+ * 2 V0 - V1, 1 = cubic extrapolation, 2 = the network. */
+tdks_status tdks_nn_predict(tdks_ctx* ctx, const double* vhist_dev, double* vpred_dev, int mode);
 
 /* Loss and parameter gradient of one sample (vhist_dev = [4][npts], vnext_dev = V_Hxc(t+dt)), without
  * updating the parameters; grad_host = [TDKS_NN_NPARAMS] (synchronises the stream). */

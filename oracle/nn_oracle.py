@@ -2,11 +2,15 @@
 
 The network replaces the predictor half-step of the predictor-corrector scheme (Program summary:
 "a predictor-corrector step when necessary"): from the last four Hartree-exchange potentials it
-predicts the next one.  Inputs (channels, normalised per sample):
-    x0 = (V(t) - V(t-dt)) / s,  x1 = (V(t-dt) - V(t-2dt)) / s,  x2 = (V(t-2dt) - V(t-3dt)) / s,
-    x3 = (V(t) - <V(t)>) / s_V,
-with s = rms(V(t) - V(t-dt)) and s_V = rms(V(t) - <V(t)>).  Output y: the correction to the linear
-extrapolation, V~(t+dt) = 2 V(t) - V(t-dt) + s * y.
+predicts the next one.  With the backward differences of V0..V3 = V(t), V(t-dt), V(t-2dt), V(t-3dt)
+    D1 = V0 - V1,  D2 = V0 - 2 V1 + V2,  D3 = V0 - 3 V1 + 3 V2 - V3,
+the input channels (normalised per sample by their root mean square) are
+    x0 = D1 / s1,  x1 = D2 / s2,  x2 = D3 / s3,  x3 = (V0 - <V0>) / s_V,
+and the output y is a learned correction to the cubic extrapolation through the four potentials,
+in units of s3:
+    V~(t+dt) = 4 V0 - 6 V1 + 4 V2 - V3 + s3 * y.
+A network that outputs zero reproduces the cubic, the best no-network baseline.  Each scale is
+floored at 1e-13 rms(V0), so a difference that vanishes to rounding is not amplified.
 Network: conv3d 4->16, SiLU, conv3d 16->16, SiLU, conv3d 16->1, 3^3 kernels with bias, periodic
 (circular) padding for periodic cells, zero padding for isolated ones.  Loss: mean squared error.
 
@@ -109,23 +113,36 @@ def loss_and_grad(params, x, target, periodic):
     return loss, pack([dW1, db1, dW2, db2, dW3, db3])
 
 
+FLOOR = 1e-13
+
+
+def rms(a):
+    return float(np.sqrt(np.mean(a * a)))
+
+
+def cubic_extrapolation(V0, V1, V2, V3):
+    """No-network baseline: the cubic through the last four potentials, evaluated at t + dt."""
+    return 4.0 * V0 - 6.0 * V1 + 4.0 * V2 - V3
+
+
 def inputs(V0, V1, V2, V3):
-    """Normalised input channels and the scale s (see module docstring)."""
-    s = np.sqrt(np.mean((V0 - V1) ** 2))
+    """Normalised input channels and the output scale s3 (see module docstring)."""
+    D1, D2, D3 = V0 - V1, V0 - 2.0 * V1 + V2, V0 - 3.0 * V1 + 3.0 * V2 - V3
     m = V0.mean()
-    sv = np.sqrt(np.mean((V0 - m) ** 2))
-    x = np.stack([(V0 - V1) / s, (V1 - V2) / s, (V2 - V3) / s, (V0 - m) / sv])
-    return x, s
+    fl = FLOOR * rms(V0) + 1e-300
+    s1, s2, s3, sv = (max(rms(D), fl) for D in (D1, D2, D3, V0 - m))
+    x = np.stack([D1 / s1, D2 / s2, D3 / s3, (V0 - m) / sv])
+    return x, s3
 
 
 def predict(params, V0, V1, V2, V3, periodic):
-    x, s = inputs(V0, V1, V2, V3)
+    x, s3 = inputs(V0, V1, V2, V3)
     out, _ = forward(params, x, periodic)
-    return 2.0 * V0 - V1 + s * out
+    return cubic_extrapolation(V0, V1, V2, V3) + s3 * out
 
 
-def target(V0, V1, Vnext, s):
-    return (Vnext - (2.0 * V0 - V1)) / s
+def target(V0, V1, V2, V3, Vnext, s3):
+    return (Vnext - cubic_extrapolation(V0, V1, V2, V3)) / s3
 
 
 def residual(Vnew, Vpred):

@@ -382,14 +382,15 @@ def propagate_all(s, tabs, V, psi, Ap, dt):
     return out
 
 
-def pc_step(s, tabs, Vloc, psi, vhxc, t, dt, pc=True, hartree_on=True, xc_on=True):
+def pc_step(s, tabs, Vloc, psi, vhxc, t, dt, pc=True, hartree_on=True, xc_on=True, Ap=None):
     """One step t -> t + dt.
 
     Predictor: psi~ = T4[V_loc + V_Hxc(t)] psi(t); V~ = V_Hxc[rho(psi~)].
     Corrector: psi(t+dt) = T4[V_loc + (V_Hxc(t) + V~)/2] psi(t); V_Hxc(t+dt) = V_Hxc[rho(t+dt)].
-    Both stages use A'(t + dt/2).  With pc=False the step is T4[V_loc + V_Hxc(t)] alone.
-    Returns (psi(t+dt), V_Hxc(t+dt), rho(t+dt))."""
-    Ap = field_Aprime(s.field, t + 0.5 * dt) if s.periodic else np.zeros(3)
+    Both stages use A'(t + dt/2) (from s.field, or the given Ap).  With pc=False the step is
+    T4[V_loc + V_Hxc(t)] alone.  Returns (psi(t+dt), V_Hxc(t+dt), rho(t+dt))."""
+    if Ap is None:
+        Ap = field_Aprime(s.field, t + 0.5 * dt) if s.periodic else np.zeros(3)
     vmid = vhxc
     if pc:
         pred = propagate_all(s, tabs, Vloc + vhxc, psi, Ap, dt)
@@ -446,6 +447,15 @@ def oscillator_strength(t, d, kappa, energies):
     return -(2.0 * E / (np.pi * kappa)) * np.imag(integ.sum(axis=1) * dt)
 
 
+def mur_boundary(A_next, A_now, c_dt_dX):
+    """First-order Mur absorbing boundary at both ends of the 1D grid (waves leave the box):
+    A_0^{n+1} = A_1^n + k (A_1^{n+1} - A_0^n), k = (c dt - dX)/(c dt + dX), mirrored at the right end."""
+    k = (c_dt_dX - 1.0) / (c_dt_dX + 1.0)
+    A_next[0] = A_now[1] + k * (A_next[1] - A_now[0])
+    A_next[-1] = A_now[-2] + k * (A_next[-2] - A_now[-1])
+    return A_next
+
+
 def maxwell_step(A_now, A_prev, I, c_dt_dX, dt, c=C_LIGHT):
     """Leapfrog update of Eq. (Maxwell_ms), (1/c^2) A_tt - A_XX = (4 pi / c) I, interior points:
     A^{n+1}_X = 2A^n_X - A^{n-1}_X + (c dt/dX)^2 (A_{X+1} - 2A_X + A_{X-1}) + 4 pi c dt^2 I_X.
@@ -454,3 +464,22 @@ def maxwell_step(A_now, A_prev, I, c_dt_dX, dt, c=C_LIGHT):
     lap = A_now[2:] - 2.0 * A_now[1:-1] + A_now[:-2]
     A_next[1:-1] = 2.0 * A_now[1:-1] - A_prev[1:-1] + c_dt_dX ** 2 * lap + 4.0 * np.pi * c * dt * dt * I[1:-1]
     return A_next
+
+
+def multiscale_step(s, tabs, Vloc, cells, A_now, A_prev, I, m0, dX, t, dt, c=C_LIGHT):
+    """One step of the coupled system (Sec. 5): Eq. (Maxwell_ms) by leapfrog with the cell currents
+    I(X, t) and Mur boundaries gives A(X, t+dt); every microscopic cell X = m0 + j then takes one
+    predictor-corrector step of Eq. (TDKS_ms) with A'(t+dt/2) = (A(X,t) + A(X,t+dt))/(2c) along z,
+    and its current at t+dt (Eq. macro_current, with A'(t+dt)) becomes I(X, t+dt).
+    cells: list of (psi, vhxc) per material point; returns (cells, A_next, A_now, I_next)."""
+    c_dt_dX = c * dt / dX
+    A_next = mur_boundary(maxwell_step(A_now, A_prev, I, c_dt_dX, dt, c), A_now, c_dt_dX)
+    I_next = np.zeros_like(I)
+    out = []
+    for j, (psi, vhxc) in enumerate(cells):
+        X = m0 + j
+        Amid = np.array([0.0, 0.0, 0.5 * (A_now[X] + A_next[X]) / c])
+        psi, vhxc, _ = pc_step(s, tabs, Vloc, psi, vhxc, t, dt, Ap=Amid)
+        I_next[X] = current(s, tabs, psi, np.array([0.0, 0.0, A_next[X] / c]))[2]
+        out.append((psi, vhxc))
+    return out, A_next, A_now, I_next

@@ -148,13 +148,15 @@ __global__ void k_pack_real(const double* __restrict__ src, int nx, int ny, int 
 __device__ __forceinline__ double freq(int m, int n) { return (m <= (n - 1) / 2) ? m : m - n; }
 
 __global__ void k_poisson_periodic(double2* data, int nx, int ny, int nz, double Lx, double Ly,
-                                   double Lz) {
-  const long long total = (long long)nx * ny * nz;
-  const double inv_n = 1.0 / (double)total;
+                                   double Lz, int batch) {
+  const long long cellsz = (long long)nx * ny * nz;
+  const long long total = cellsz * batch;
+  const double inv_n = 1.0 / (double)cellsz;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
-    const int x = (int)(i % nx);
-    const long long r = i / nx;
+    const long long j = i % cellsz;
+    const int x = (int)(j % nx);
+    const long long r = j / nx;
     const int y = (int)(r % ny), z = (int)(r / ny);
     const double gx = 2.0 * kPi * freq(x, nx) / Lx, gy = 2.0 * kPi * freq(y, ny) / Ly,
                  gz = 2.0 * kPi * freq(z, nz) / Lz;
@@ -193,9 +195,9 @@ __global__ void k_hxc_epilogue(const double2* __restrict__ fft, int mx, int my,
 
 __global__ void k_combine(const double* __restrict__ vloc, const double* __restrict__ v1, double a,
                           const double* __restrict__ v2, double b, double* __restrict__ o64,
-                          float* __restrict__ o32, int n) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    double v = vloc[i];
+                          float* __restrict__ o32, int npts, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double v = vloc[i % npts];
     if (v1) v += a * v1[i];
     if (v2) v += b * v2[i];
     if (o64) o64[i] = v;
@@ -343,10 +345,12 @@ __global__ void __launch_bounds__(256) k_reduce_current(const double* __restrict
   __shared__ double red[3][256];
   double acc[3] = {0, 0, 0};
   const int tot = nk * norb;
+  const double* ob = obs + (size_t)blockIdx.x * tot * 8;   // this block's cell
+  out += blockIdx.x * 8;
   if (periodic)
     for (int o = threadIdx.x; o < tot; o += blockDim.x) {
       const double w = 2.0 * kw[o / norb];
-      for (int d = 0; d < 3; ++d) acc[d] += w * (obs[(size_t)o * 8 + 1 + d] + obs[(size_t)o * 8 + 4 + d]);
+      for (int d = 0; d < 3; ++d) acc[d] += w * (ob[(size_t)o * 8 + 1 + d] + ob[(size_t)o * 8 + 4 + d]);
     }
   for (int d = 0; d < 3; ++d) red[d][threadIdx.x] = acc[d];
   __syncthreads();
@@ -387,11 +391,12 @@ __global__ void __launch_bounds__(256) k_orbital_dots(const C* __restrict__ u, c
 }
 
 __global__ void k_fold_density(const float* __restrict__ r32, int nk, int npts,
-                               const double* __restrict__ kw, double* __restrict__ rho) {
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npts; p += gridDim.x * blockDim.x) {
+                               const double* __restrict__ kw, double* __restrict__ rho, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const long long cell = i / npts, p = i - cell * npts;
     double acc = 0.0;
-    for (int k = 0; k < nk; ++k) acc += kw[k] * (double)r32[(size_t)k * npts + p];
-    rho[p] = acc;
+    for (int k = 0; k < nk; ++k) acc += kw[k] * (double)r32[(cell * nk + k) * npts + p];
+    rho[i] = acc;
   }
 }
 
@@ -405,18 +410,18 @@ int grid_for(long long n, int threads) {
 }  // namespace
 
 cudaError_t launch_fft_axis(double2* data, const int dims[3], int axis, int dir, const double2* tw,
-                            const int* radices, int nrad, cudaStream_t s) {
+                            const int* radices, int nrad, cudaStream_t s, int batch) {
   const int n = dims[axis];
   if (nrad > kMaxRadices) return cudaErrorInvalidValue;
   FftPlanArgs plan;
   plan.nrad = nrad;
   for (int i = 0; i < nrad; ++i) plan.rad[i] = radices[i];
-  const long long total = (long long)dims[0] * dims[1] * dims[2];
+  const long long total = (long long)dims[0] * dims[1] * dims[2] * batch;
   const int nlines = (int)(total / n);
   long long inner, outer, estride;
   if (axis == 0) { inner = 1; outer = dims[0]; estride = 1; }
   else if (axis == 1) { inner = dims[0]; outer = (long long)dims[0] * dims[1]; estride = dims[0]; }
-  else { inner = (long long)dims[0] * dims[1]; outer = 0; estride = inner; }
+  else { inner = (long long)dims[0] * dims[1]; outer = inner * dims[2]; estride = inner; }
   int LB = 16;
   while (LB > 1 && (size_t)(2 * LB + 1) * n * sizeof(double2) > 96 * 1024) LB /= 2;
   const size_t smem = (size_t)(2 * LB + 1) * n * sizeof(double2);
@@ -437,10 +442,10 @@ cudaError_t launch_pack_real(const double* src, const int n[3], double2* dst, co
 }
 
 cudaError_t launch_poisson_scale_periodic(double2* data, const int n[3], const double h[3],
-                                          cudaStream_t s) {
-  const long long tot = (long long)n[0] * n[1] * n[2];
+                                          cudaStream_t s, int batch) {
+  const long long tot = (long long)n[0] * n[1] * n[2] * batch;
   k_poisson_periodic<<<grid_for(tot, 256), 256, 0, s>>>(data, n[0], n[1], n[2], n[0] * h[0],
-                                                         n[1] * h[1], n[2] * h[2]);
+                                                         n[1] * h[1], n[2] * h[2], batch);
   return cudaGetLastError();
 }
 
@@ -461,8 +466,9 @@ cudaError_t launch_hxc_epilogue(const double2* fft, const int m[3], const double
 
 cudaError_t launch_combine_potential(const double* vloc, const double* v1, double a,
                                      const double* v2, double b, double* v64, float* v32, int npts,
-                                     cudaStream_t s) {
-  k_combine<<<grid_for(npts, 256), 256, 0, s>>>(vloc, v1, a, v2, b, v64, v32, npts);
+                                     cudaStream_t s, int batch) {
+  const long long n = (long long)npts * batch;
+  k_combine<<<grid_for(n, 256), 256, 0, s>>>(vloc, v1, a, v2, b, v64, v32, npts, n);
   return cudaGetLastError();
 }
 
@@ -519,14 +525,53 @@ cudaError_t launch_dipole(const double* rho, const double* rho0, const int n[3],
 }
 
 cudaError_t launch_reduce_current(const double* orb_obs, int nk, int norb, const double* kw,
-                                  double inv_omega, int periodic, double* out, cudaStream_t s) {
-  k_reduce_current<<<1, 256, 0, s>>>(orb_obs, nk, norb, kw, inv_omega, periodic, out);
+                                  double inv_omega, int periodic, double* out, cudaStream_t s, int ncell) {
+  k_reduce_current<<<ncell, 256, 0, s>>>(orb_obs, nk, norb, kw, inv_omega, periodic, out);
+  return cudaGetLastError();
+}
+
+// Leapfrog of (1/c^2) A_tt - A_XX = (4 pi / c) I on the interior, first-order Mur at both ends, and
+// the cells' A' = A/c along z at t + dt/2 (mean of both levels) and t + dt.
+__global__ void k_maxwell(const double* __restrict__ Ap, const double* __restrict__ An, double* __restrict__ Anext,
+                          const double* __restrict__ I, int nX, int m0, int ncell, double cdx, double src,
+                          double inv_c, double* __restrict__ mid, double* __restrict__ end) {
+  for (int X = 1 + threadIdx.x; X < nX - 1; X += blockDim.x)
+    Anext[X] = 2.0 * An[X] - Ap[X] + cdx * cdx * (An[X + 1] - 2.0 * An[X] + An[X - 1]) + src * I[X];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double k = (cdx - 1.0) / (cdx + 1.0);
+    Anext[0] = An[1] + k * (Anext[1] - An[0]);
+    Anext[nX - 1] = An[nX - 2] + k * (Anext[nX - 2] - An[nX - 1]);
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
+    const int X = m0 + c;
+    mid[3 * c] = 0.0; mid[3 * c + 1] = 0.0; mid[3 * c + 2] = 0.5 * (An[X] + Anext[X]) * inv_c;
+    end[3 * c] = 0.0; end[3 * c + 1] = 0.0; end[3 * c + 2] = Anext[X] * inv_c;
+  }
+}
+
+__global__ void k_ms_current(const double* __restrict__ step_obs, int ncell, int m0, double* __restrict__ I) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += gridDim.x * blockDim.x)
+    I[m0 + c] = step_obs[(size_t)c * 8 + 2];
+}
+
+cudaError_t launch_maxwell(const double* A_prev, const double* A_now, double* A_next, const double* I,
+                           int nX, int m0, int ncell, double c_dt_dX, double src, double inv_c,
+                           double* ap_mid, double* ap_end, cudaStream_t s) {
+  k_maxwell<<<1, 1024, 0, s>>>(A_prev, A_now, A_next, I, nX, m0, ncell, c_dt_dX, src, inv_c, ap_mid, ap_end);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ms_current(const double* step_obs, int ncell, int m0, double* I, cudaStream_t s) {
+  k_ms_current<<<(ncell + 255) / 256, 256, 0, s>>>(step_obs, ncell, m0, I);
   return cudaGetLastError();
 }
 
 cudaError_t launch_fold_density(const float* rho32, int nk, int npts, const double* kw, double* rho,
-                                cudaStream_t s) {
-  k_fold_density<<<grid_for(npts, 256), 256, 0, s>>>(rho32, nk, npts, kw, rho);
+                                cudaStream_t s, int ncell) {
+  const long long n = (long long)npts * ncell;
+  k_fold_density<<<grid_for(n, 256), 256, 0, s>>>(rho32, nk, npts, kw, rho, n);
   return cudaGetLastError();
 }
 

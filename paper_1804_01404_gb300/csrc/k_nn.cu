@@ -205,53 +205,71 @@ __global__ void k_nn_round(const float* __restrict__ p, float* __restrict__ wq, 
     wq[i] = __bfloat162float(__float2bfloat16(p[i]));
 }
 
-// stats[0] = s = rms(V0 - V1), stats[1] = mean(V0), stats[2] = s_V = rms(V0 - mean V0)
+// Differences D1 = V0 - V1, D2 = V0 - 2 V1 + V2, D3 = V0 - 3 V1 + 3 V2 - V3 (formed in FP64).
+// stats = {s1, s2, s3, mean V0, s_V}: root mean squares of D1, D2, D3 and V0 - mean V0, each
+// floored at 1e-13 rms(V0); per-thread FP32 partials combined in FP64.
 __global__ void __launch_bounds__(1024) k_nn_stats(const double* __restrict__ V0, const double* __restrict__ V1,
+                                                   const double* __restrict__ V2, const double* __restrict__ V3,
                                                    int n, double* stats) {
-  __shared__ double r0[1024], r1[1024], r2[1024];
-  float a = 0, b = 0, c = 0;           // per-thread partials in FP32, combined in FP64
+  __shared__ double r[5][1024];
+  float a1 = 0, a2 = 0, a3 = 0, b = 0, c = 0;
   for (int p = threadIdx.x; p < n; p += blockDim.x) {
-    const float d = (float)(V0[p] - V1[p]);
+    const float d1 = (float)(V0[p] - V1[p]);
+    const float d2 = (float)(V0[p] - 2.0 * V1[p] + V2[p]);
+    const float d3 = (float)(V0[p] - 3.0 * V1[p] + 3.0 * V2[p] - V3[p]);
     const float v = (float)V0[p];
-    a += d * d;
-    b += v;
-    c += v * v;
+    a1 += d1 * d1; a2 += d2 * d2; a3 += d3 * d3; b += v; c += v * v;
   }
-  r0[threadIdx.x] = a; r1[threadIdx.x] = b; r2[threadIdx.x] = c;
+  r[0][threadIdx.x] = a1; r[1][threadIdx.x] = a2; r[2][threadIdx.x] = a3; r[3][threadIdx.x] = b; r[4][threadIdx.x] = c;
   __syncthreads();
   for (int h = blockDim.x / 2; h > 0; h >>= 1) {
-    if (threadIdx.x < h) { r0[threadIdx.x] += r0[threadIdx.x + h]; r1[threadIdx.x] += r1[threadIdx.x + h]; r2[threadIdx.x] += r2[threadIdx.x + h]; }
+    if (threadIdx.x < h)
+      for (int k = 0; k < 5; ++k) r[k][threadIdx.x] += r[k][threadIdx.x + h];
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    const double mean = r1[0] / n;
-    stats[0] = sqrt(fmax(r0[0] / n, 1e-300));
-    stats[1] = mean;
-    stats[2] = sqrt(fmax(r2[0] / n - mean * mean, 1e-300));
+    const double mean = r[3][0] / n;
+    const double fl = 1e-13 * sqrt(r[4][0] / n) + 1e-300;
+    stats[0] = fmax(sqrt(r[0][0] / n), fl);
+    stats[1] = fmax(sqrt(r[1][0] / n), fl);
+    stats[2] = fmax(sqrt(r[2][0] / n), fl);
+    stats[3] = mean;
+    stats[4] = fmax(sqrt(fmax(r[4][0] / n - mean * mean, 0.0)), fl);
   }
+}
+
+__device__ __forceinline__ double cubic(double v0, double v1, double v2, double v3) {
+  return 4.0 * v0 - 6.0 * v1 + 4.0 * v2 - v3;
 }
 
 __global__ void k_nn_pack(const double* __restrict__ V0, const double* __restrict__ V1,
                           const double* __restrict__ V2, const double* __restrict__ V3,
                           const double* __restrict__ Vnext, const double* __restrict__ stats, int n,
                           bf16* __restrict__ x, float* __restrict__ target) {
-  const double s = stats[0], m = stats[1], sv = stats[2];
+  const double s1 = stats[0], s2 = stats[1], s3 = stats[2], m = stats[3], sv = stats[4];
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
-    x[p] = __float2bfloat16((float)((V0[p] - V1[p]) / s));
-    x[(size_t)n + p] = __float2bfloat16((float)((V1[p] - V2[p]) / s));
-    x[2 * (size_t)n + p] = __float2bfloat16((float)((V2[p] - V3[p]) / s));
+    const double d1 = V0[p] - V1[p], d2 = V0[p] - 2.0 * V1[p] + V2[p];
+    const double d3 = V0[p] - 3.0 * V1[p] + 3.0 * V2[p] - V3[p];
+    x[p] = __float2bfloat16((float)(d1 / s1));
+    x[(size_t)n + p] = __float2bfloat16((float)(d2 / s2));
+    x[2 * (size_t)n + p] = __float2bfloat16((float)(d3 / s3));
     x[3 * (size_t)n + p] = __float2bfloat16((float)((V0[p] - m) / sv));
-    if (Vnext) target[p] = (float)((Vnext[p] - (2.0 * V0[p] - V1[p])) / s);
+    if (Vnext) target[p] = (float)((Vnext[p] - cubic(V0[p], V1[p], V2[p], V3[p])) / s3);
   }
 }
 
-// V~ = 2 V0 - V1 + s * out   (out nullable: linear extrapolation)
+// mode 0: V~ = 2 V0 - V1;  1: cubic 4 V0 - 6 V1 + 4 V2 - V3;  2: cubic + s3 * out
 __global__ void k_nn_apply(const double* __restrict__ V0, const double* __restrict__ V1,
+                           const double* __restrict__ V2, const double* __restrict__ V3,
                            const float* __restrict__ out, const double* __restrict__ stats, int n,
-                           double* __restrict__ vpred) {
-  const double s = out ? stats[0] : 0.0;
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x)
-    vpred[p] = 2.0 * V0[p] - V1[p] + (out ? s * (double)out[p] : 0.0);
+                           int mode, double* __restrict__ vpred) {
+  const double s3 = (mode == 2) ? stats[2] : 0.0;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    double v;
+    if (mode == 0) v = 2.0 * V0[p] - V1[p];
+    else v = cubic(V0[p], V1[p], V2[p], V3[p]) + (mode == 2 ? s3 * (double)out[p] : 0.0);
+    vpred[p] = v;
+  }
 }
 
 // res = ||Vnew - Vpred||_2 / ||Vnew||_2
@@ -331,14 +349,14 @@ cudaError_t nn_round_weights(const NNBuffers& B, cudaStream_t s) {
 
 cudaError_t nn_inputs(const NNBuffers& B, const NNGrid& g, const double* V0, const double* V1,
                       const double* V2, const double* V3, const double* Vnext, cudaStream_t s) {
-  k_nn_stats<<<1, 1024, 0, s>>>(V0, V1, g.npts, B.stats);
+  k_nn_stats<<<1, 1024, 0, s>>>(V0, V1, V2, V3, g.npts, B.stats);
   k_nn_pack<<<blocks_for(g.npts), 256, 0, s>>>(V0, V1, V2, V3, Vnext, B.stats, g.npts, B16(B.x0), B.target);
   return cudaGetLastError();
 }
 
 cudaError_t nn_apply(const NNBuffers& B, const NNGrid& g, const double* V0, const double* V1,
-                     bool use_net, double* vpred, cudaStream_t s) {
-  k_nn_apply<<<blocks_for(g.npts), 256, 0, s>>>(V0, V1, use_net ? B.out : nullptr, B.stats, g.npts, vpred);
+                     const double* V2, const double* V3, int mode, double* vpred, cudaStream_t s) {
+  k_nn_apply<<<blocks_for(g.npts), 256, 0, s>>>(V0, V1, V2, V3, B.out, B.stats, g.npts, mode, vpred);
   return cudaGetLastError();
 }
 

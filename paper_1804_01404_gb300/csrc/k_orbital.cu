@@ -249,13 +249,16 @@ __global__ void __launch_bounds__(kNT) k_cell(OrbArgs<T> a, typename Cplx<T>::ty
   L.ph = L.v + (DBUF ? 2 * vsz : vsz);
   L.ec = L.ph + a.nsph;
   const int orb = blockIdx.x;
-  const int k = orb / a.norb;
+  const int cell = orb / (a.nk * a.norb);
+  const int k = (orb - cell * a.nk * a.norb) / a.norb;
   const C* psi = a.psi_in + (size_t)orb * a.npts;
   C* gnxt = DBUF ? nullptr : scratch + (size_t)orb * a.npts;
+  const double* ap = a.Ap_cell ? a.Ap_cell + 3 * cell : a.Ap;
+  const T* Vc = a.V + (size_t)cell * a.vstride;
   T q[3];
-  q[0] = (T)(a.kpts[3 * k] + a.Ap[0]);
-  q[1] = (T)(a.kpts[3 * k + 1] + a.Ap[1]);
-  q[2] = (T)(a.kpts[3 * k + 2] + a.Ap[2]);
+  q[0] = (T)(a.kpts[3 * k] + ap[0]);
+  q[1] = (T)(a.kpts[3 * k + 1] + ap[1]);
+  q[2] = (T)(a.kpts[3 * k + 2] + ap[2]);
   T gx[4], gy[4], gz[4];
 #pragma unroll
   for (int m = 0; m < 4; ++m) {
@@ -291,7 +294,7 @@ __global__ void __launch_bounds__(kNT) k_cell(OrbArgs<T> a, typename Cplx<T>::ty
       C w[9];
 #pragma unroll
       for (int j = 0; j < 9; ++j) w[j] = zload<T, PER>(a, L.v, c.z0 - 4 + j, c.col);
-      T vnext = a.V[c.z0 * nxy + c.col];
+      T vnext = Vc[c.z0 * nxy + c.col];
       C pnext = (MODE == 1) ? psi[c.z0 * nxy + c.col] : C{0, 0};
 #pragma unroll 1
       for (int z = c.z0; z < c.z1; ++z) {
@@ -300,7 +303,7 @@ __global__ void __launch_bounds__(kNT) k_cell(OrbArgs<T> a, typename Cplx<T>::ty
         const T diag = diag0 + vnext;
         const C pv = pnext;
         if (z + 1 < c.z1) {                   // prefetch the next plane's V and psi
-          vnext = a.V[pg + nxy];
+          vnext = Vc[pg + nxy];
           if (MODE == 1) pnext = psi[pg + nxy];
         }
         const C hv = local_h<T, PER>(a, c, L.v, w, zb, diag, gx, gy, gz);
@@ -350,9 +353,10 @@ __global__ void __launch_bounds__(kNT) k_cell(OrbArgs<T> a, typename Cplx<T>::ty
   C* out = a.psi_out ? a.psi_out + (size_t)orb * a.npts : nullptr;
   T qo[3] = {q[0], q[1], q[2]};
   if (OBS && MODE == 1) {
-    qo[0] = (T)(a.kpts[3 * k] + a.Ap_obs[0]);
-    qo[1] = (T)(a.kpts[3 * k + 1] + a.Ap_obs[1]);
-    qo[2] = (T)(a.kpts[3 * k + 2] + a.Ap_obs[2]);
+    const double* apo = a.Ap_obs_cell ? a.Ap_obs_cell + 3 * cell : a.Ap_obs;
+    qo[0] = (T)(a.kpts[3 * k] + apo[0]);
+    qo[1] = (T)(a.kpts[3 * k + 1] + apo[1]);
+    qo[2] = (T)(a.kpts[3 * k + 2] + apo[2]);
   }
   double acc_norm = 0, acc_j[3] = {0, 0, 0}, acc_e = 0;
 #pragma unroll 1
@@ -372,8 +376,8 @@ __global__ void __launch_bounds__(kNT) k_cell(OrbArgs<T> a, typename Cplx<T>::ty
       const T rr = r.x * r.x + r.y * r.y;
       if (MODE == 0 || (MODE == 1 && a.write_out)) out[pg] = r;
       if (MODE == 1) {
-        if (a.rho32) atomicAdd(&a.rho32[(size_t)k * a.npts + pg], 2.0f * (float)rr);
-        else if (a.rho) atomicAdd(&a.rho[pg], wk * (double)rr);
+        if (a.rho32) atomicAdd(&a.rho32[((size_t)cell * a.nk + k) * a.npts + pg], 2.0f * (float)rr);
+        else if (a.rho) atomicAdd(&a.rho[(size_t)cell * a.npts + pg], wk * (double)rr);
       }
       if (OBS) {
         cn += rr;
@@ -465,7 +469,7 @@ cudaError_t launch_cell(const OrbArgs<T>& a, typename Cplx<T>::type* scratch, si
   auto kern = k_cell<T, MODE, PER, DBUF, OBS>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<a.nk * a.norb, nt, smem, s>>>(a, scratch);
+  kern<<<a.ncell * a.nk * a.norb, nt, smem, s>>>(a, scratch);
   return cudaGetLastError();
 }
 

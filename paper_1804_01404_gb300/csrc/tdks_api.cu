@@ -38,7 +38,13 @@ void tdks::set_last_error(const char* msg) { g_err = msg; }
 
 struct tdks_ctx {
   tdks_grid grid{};
-  int npts = 0, nk = 0, norb = 0;
+  int npts = 0, nk = 0, norb = 0, ncell = 1;
+  // multiscale: A(X) at three time levels (ring), cell currents I(X), per-cell A'
+  int nX = 0, m0 = 0, ms_head = 0;
+  double dX = 0;
+  bool ms_ready = false;
+  double *d_A[3] = {nullptr, nullptr, nullptr}, *d_I = nullptr, *d_ap_mid = nullptr, *d_ap_end = nullptr;
+  const double *cur_ap_mid = nullptr, *cur_ap_end = nullptr;
   tdks_options opt{};
   double dV = 0, omega = 0;
   std::vector<double> kpts, kw;
@@ -159,6 +165,10 @@ OrbArgs<T> make_args(const tdks_ctx* c, const void* in, void* out, const T* V, c
   for (int i = 0; i < 3; ++i) a.Ap[i] = Ap ? Ap[i] : 0.0;
   a.natom = c->natom; a.nsph = c->nsph;
   a.atom_off = c->d_atom_off; a.sph_idx = c->d_sph_idx;
+  a.ncell = c->ncell;
+  a.vstride = c->ncell > 1 ? c->npts : 0;
+  a.Ap_cell = c->cur_ap_mid;
+  a.Ap_obs_cell = c->cur_ap_end;
   if (sizeof(T) == 8) {
     a.sph_beta = (const T*)c->d_beta64; a.sph_d = (const T*)c->d_d64; a.atomE = (const T*)c->d_E64;
   } else {
@@ -225,7 +235,7 @@ struct Phase {
 tdks_status set_step_potential(tdks_ctx* c, double a, const double* v2, double b) {
   Phase ph(c, 5);
   TDKS_CUDA(launch_combine_potential(c->d_vloc, c->d_vhxc, a, v2, b, c->d_v64,
-                                     is_f32(c) ? c->d_v32 : nullptr, c->npts, c->stream));
+                                     is_f32(c) ? c->d_v32 : nullptr, c->npts, c->stream, c->ncell));
   c->launches += 1;
   return TDKS_OK;
 }
@@ -304,14 +314,14 @@ tdks_status orbital_kernel(tdks_ctx* c, int mode, const void* in, void* out, con
     auto a = make_args<float>(c, in, out, c->d_v32, Ap, dt, rho, write_out);
     if (rho) {
       // per-k FP32 partial densities, folded into rho in FP64 afterwards
-      TDKS_CUDA(cudaMemsetAsync(c->d_rho32, 0, sizeof(float) * (size_t)c->nk * c->npts, c->stream));
+      TDKS_CUDA(cudaMemsetAsync(c->d_rho32, 0, sizeof(float) * (size_t)c->ncell * c->nk * c->npts, c->stream));
       a.rho = nullptr;
       a.rho32 = c->d_rho32;
     }
     if (Ap_obs) { a.obs = c->d_orb_obs; for (int i = 0; i < 3; ++i) a.Ap_obs[i] = Ap_obs[i]; }
     TDKS_CUDA(launch_smem_orbital<float>(a, mode, static_cast<float2*>(c->d_scratch), c->stream));
     if (rho) {
-      TDKS_CUDA(launch_fold_density(c->d_rho32, c->nk, c->npts, c->d_kw, rho, c->stream));
+      TDKS_CUDA(launch_fold_density(c->d_rho32, c->nk, c->npts, c->d_kw, rho, c->stream, c->ncell));
       c->launches += 1;
     }
   } else {
@@ -323,18 +333,22 @@ tdks_status orbital_kernel(tdks_ctx* c, int mode, const void* in, void* out, con
 }
 
 tdks_status density(tdks_ctx* c, const void* u, double* rho) {
-  c->launches += 1;
-  if (is_f32(c))
-    TDKS_CUDA(launch_density<float>(static_cast<const float2*>(u), c->nk, c->norb, c->npts, c->d_kw, rho, c->stream));
-  else
-    TDKS_CUDA(launch_density<double>(static_cast<const double2*>(u), c->nk, c->norb, c->npts, c->d_kw, rho, c->stream));
+  const size_t per = (size_t)c->nk * c->norb * c->npts;
+  for (int cell = 0; cell < c->ncell; ++cell) {
+    c->launches += 1;
+    double* r = rho + (size_t)cell * c->npts;
+    if (is_f32(c))
+      TDKS_CUDA(launch_density<float>(static_cast<const float2*>(u) + cell * per, c->nk, c->norb, c->npts, c->d_kw, r, c->stream));
+    else
+      TDKS_CUDA(launch_density<double>(static_cast<const double2*>(u) + cell * per, c->nk, c->norb, c->npts, c->d_kw, r, c->stream));
+  }
   return TDKS_OK;
 }
 
 tdks_status fft3d(tdks_ctx* c, int dir) {
   for (int ax = 0; ax < 3; ++ax)
     TDKS_CUDA(launch_fft_axis(c->d_fft, c->m, ax, dir, c->d_tw[ax], c->rad[ax].data(),
-                              (int)c->rad[ax].size(), c->stream));
+                              (int)c->rad[ax].size(), c->stream, c->ncell));
   c->launches += 3;
   return TDKS_OK;
 }
@@ -343,18 +357,21 @@ tdks_status fft3d(tdks_ctx* c, int dir) {
 tdks_status hxc(tdks_ctx* c, const double* rho, double* vhxc) {
   Phase ph(c, 3);
   c->launches += c->opt.hartree ? 3 : 1;   // pack, scale, epilogue (+ 6 FFT passes counted in fft3d)
+  // a batch of periodic cells is handled as one grid stacked along z for the pointwise kernels
+  const int ns[3] = {c->grid.n[0], c->grid.n[1], c->grid.n[2] * c->ncell};
+  const int ms[3] = {c->m[0], c->m[1], c->m[2] * c->ncell};
   if (c->opt.hartree) {
-    TDKS_CUDA(launch_pack_real(rho, c->grid.n, c->d_fft, c->m, c->stream));
+    TDKS_CUDA(launch_pack_real(rho, ns, c->d_fft, ms, c->stream));
     TDKS_TRY(fft3d(c, -1));
     if (c->grid.periodic) {
-      TDKS_CUDA(launch_poisson_scale_periodic(c->d_fft, c->m, c->grid.h, c->stream));
+      TDKS_CUDA(launch_poisson_scale_periodic(c->d_fft, c->m, c->grid.h, c->stream, c->ncell));
     } else {
       const double npad = (double)c->m[0] * c->m[1] * c->m[2];
       TDKS_CUDA(launch_scale_by_real(c->d_fft, c->d_ghat, c->dV / npad, (size_t)npad, c->stream));
     }
     TDKS_TRY(fft3d(c, +1));
   }
-  TDKS_CUDA(launch_hxc_epilogue(c->d_fft, c->m, rho, c->grid.n, 1.0, c->opt.hartree, c->opt.xc,
+  TDKS_CUDA(launch_hxc_epilogue(c->d_fft, ms, rho, ns, 1.0, c->opt.hartree, c->opt.xc,
                                 vhxc, c->stream));
   return TDKS_OK;
 }
@@ -411,6 +428,8 @@ tdks_status tdks_init(const tdks_grid* grid, const tdks_cell* cell, const tdks_a
   if (nk < 1 || norb < 1) return fail(TDKS_EINVAL, "nk and norb must be >= 1");
   if (opts->precision != TDKS_F64 && opts->precision != TDKS_F32)
     return fail(TDKS_EINVAL, "precision must be TDKS_F64 or TDKS_F32");
+  if (opts->ncell < 0 || opts->ncell > 65536) return fail(TDKS_EINVAL, "ncell must be in [0, 65536]");
+  if (opts->ncell > 1 && !grid->periodic) return fail(TDKS_EINVAL, "ncell > 1 needs a periodic grid");
   for (int a = 0; a < 3; ++a) {
     if (grid->n[a] < 4 || grid->n[a] > 1024) return fail(TDKS_EINVAL, "grid points per axis must be in [4, 1024]");
     if (!(grid->h[a] > 0.0)) return fail(TDKS_EINVAL, "grid spacing must be positive");
@@ -428,6 +447,7 @@ tdks_status tdks_init(const tdks_grid* grid, const tdks_cell* cell, const tdks_a
   tdks_ctx* c = new tdks_ctx();
   c->grid = *grid;
   c->npts = grid->n[0] * grid->n[1] * grid->n[2];
+  c->ncell = opts->ncell > 1 ? opts->ncell : 1;
   c->nk = nk;
   c->norb = norb;
   c->opt = *opts;
@@ -486,20 +506,22 @@ tdks_status tdks_init(const tdks_grid* grid, const tdks_cell* cell, const tdks_a
   if ((s = upload(c, &c->d_kw, c->kw)) != TDKS_OK) return bail(s);
 
   const size_t np = c->npts;
-  double** grids[] = {&c->d_vloc, &c->d_vhxc, &c->d_vpred, &c->d_rho, &c->d_rho0, &c->d_rho_tmp, &c->d_v64};
+  const size_t npc = np * c->ncell;        // per-cell arrays
+  double** grids[] = {&c->d_vhxc, &c->d_vpred, &c->d_rho, &c->d_rho0, &c->d_rho_tmp, &c->d_v64};
+  if ((s = dalloc(c, &c->d_vloc, np)) != TDKS_OK) return bail(s);
   for (double** g : grids) {
-    if ((s = dalloc(c, g, np)) != TDKS_OK) return bail(s);
-    if (cudaMemsetAsync(*g, 0, np * sizeof(double), c->stream) != cudaSuccess)
+    if ((s = dalloc(c, g, npc)) != TDKS_OK) return bail(s);
+    if (cudaMemsetAsync(*g, 0, npc * sizeof(double), c->stream) != cudaSuccess)
       return bail(fail(TDKS_ECUDA, "memset"));
   }
-  if ((s = dalloc(c, &c->d_v32, np)) != TDKS_OK) return bail(s);
+  if ((s = dalloc(c, &c->d_v32, npc)) != TDKS_OK) return bail(s);
   if ((s = dalloc(c, &c->d_err, 1)) != TDKS_OK) return bail(s);
   if ((s = dalloc(c, &c->d_vhist, 4 * np)) != TDKS_OK) return bail(s);
-  if ((s = dalloc(c, &c->d_vnew, np)) != TDKS_OK) return bail(s);
+  if ((s = dalloc(c, &c->d_vnew, npc)) != TDKS_OK) return bail(s);
   if ((s = dalloc(c, &c->d_resid, 2)) != TDKS_OK) return bail(s);
   if (cudaMallocHost((void**)&c->h_resid, sizeof(double)) != cudaSuccess) return bail(fail(TDKS_ENOMEM, "pinned"));
   if (is_f32(c) && !c->tiled)
-    if ((s = dalloc(c, &c->d_rho32, np * (size_t)nk)) != TDKS_OK) return bail(s);
+    if ((s = dalloc(c, &c->d_rho32, npc * (size_t)nk)) != TDKS_OK) return bail(s);
   cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
   if (c->tiled) {
     const size_t csz = is_f32(c) ? sizeof(float2) : sizeof(double2);
@@ -515,14 +537,14 @@ tdks_status tdks_init(const tdks_grid* grid, const tdks_cell* cell, const tdks_a
   if (scratch) {
     const size_t csz = is_f32(c) ? sizeof(float2) : sizeof(double2);
     unsigned char* p = nullptr;
-    if ((s = dalloc(c, &p, csz * np * (size_t)nk * norb)) != TDKS_OK) return bail(s);
+    if ((s = dalloc(c, &p, csz * npc * (size_t)nk * norb)) != TDKS_OK) return bail(s);
     c->d_scratch = p;
   }
-  if ((s = dalloc(c, &c->d_orb_obs, (size_t)nk * norb * 8)) != TDKS_OK) return bail(s);
-  if ((s = dalloc(c, &c->d_step_obs, 8)) != TDKS_OK) return bail(s);
+  if ((s = dalloc(c, &c->d_orb_obs, (size_t)c->ncell * nk * norb * 8)) != TDKS_OK) return bail(s);
+  if ((s = dalloc(c, &c->d_step_obs, 8 * (size_t)c->ncell)) != TDKS_OK) return bail(s);
   c->red_blocks = 304;
   if ((s = dalloc(c, &c->d_partials, (size_t)c->red_blocks * 4)) != TDKS_OK) return bail(s);
-  cudaMemsetAsync(c->d_step_obs, 0, 8 * sizeof(double), c->stream);
+  cudaMemsetAsync(c->d_step_obs, 0, 8 * sizeof(double) * c->ncell, c->stream);
 
   // FFT set-up: periodic transforms are n^3, isolated ones (2n)^3 (zero padding)
   for (int a = 0; a < 3; ++a) {
@@ -535,7 +557,7 @@ tdks_status tdks_init(const tdks_grid* grid, const tdks_cell* cell, const tdks_a
     if ((s = upload(c, &c->d_tw[a], tw)) != TDKS_OK) return bail(s);
   }
   const size_t nfft = (size_t)c->m[0] * c->m[1] * c->m[2];
-  if ((s = dalloc(c, &c->d_fft, nfft)) != TDKS_OK) return bail(s);
+  if ((s = dalloc(c, &c->d_fft, nfft * c->ncell)) != TDKS_OK) return bail(s);
 
   // local potential
   if (grid->periodic) {
@@ -544,7 +566,10 @@ tdks_status tdks_init(const tdks_grid* grid, const tdks_cell* cell, const tdks_a
     if (cudaMemcpyAsync(c->d_fft, vg.data(), vg.size() * sizeof(double), cudaMemcpyHostToDevice,
                         c->stream) != cudaSuccess)
       return bail(fail(TDKS_ECUDA, "upload V(G)"));
-    if ((s = fft3d(c, +1)) != TDKS_OK) return bail(s);
+    for (int ax = 0; ax < 3; ++ax)
+      if (launch_fft_axis(c->d_fft, c->m, ax, +1, c->d_tw[ax], c->rad[ax].data(), (int)c->rad[ax].size(),
+                          c->stream, 1) != cudaSuccess)
+        return bail(fail(TDKS_ECUDA, "V_loc transform"));
     if (launch_real_part(c->d_fft, c->d_vloc, np, 1.0, c->stream) != cudaSuccess)
       return bail(fail(TDKS_ECUDA, "real part"));
   } else {
@@ -641,7 +666,7 @@ tdks_status tdks_taylor_step(tdks_ctx* c, void* u, double dt, const double Ap[3]
 // plain predictor-corrector (or single Taylor step) from u; leaves V_Hxc(t+dt) in d_vhxc and the
 // predictor's potential in d_vpred
 tdks_status pc_step(tdks_ctx* c, void* u, const double Amid[3], const double Aend[3], double dt) {
-  const size_t gb = c->npts * sizeof(double);
+  const size_t gb = (size_t)c->ncell * c->npts * sizeof(double);
   const bool pc = c->opt.pc && (c->opt.hartree || c->opt.xc);
   if (pc) {
     // predictor: T4 with V(t); only its density is kept
@@ -665,7 +690,7 @@ tdks_status pc_step(tdks_ctx* c, void* u, const double Amid[3], const double Aen
   TDKS_TRY(orbital_kernel(c, 1, u, u, Amid, dt, c->d_rho, 1, c->grid.periodic ? Aend : nullptr));
   TDKS_TRY(hxc(c, c->d_rho, c->d_vhxc));
   if (pc) {   // the PC's own misfit, for scale
-    TDKS_CUDA(launch_residual(c->d_vhxc, c->d_vpred, c->npts, c->d_resid, c->stream));
+    TDKS_CUDA(launch_residual(c->d_vhxc, c->d_vpred, c->npts * c->ncell, c->d_resid, c->stream));
     c->launches += 1;
   }
   return TDKS_OK;
@@ -686,7 +711,8 @@ tdks_status predicted_step(tdks_ctx* c, void* u, const double Amid[3], const dou
       TDKS_CUDA(nn_forward(c->nn, g, c->stream));
       c->launches += 5;
     }
-    TDKS_CUDA(nn_apply(c->nn, g, hist_slot(c, 0), hist_slot(c, 1), net, c->d_vpred, c->stream));
+    TDKS_CUDA(nn_apply(c->nn, g, hist_slot(c, 0), hist_slot(c, 1), hist_slot(c, 2), hist_slot(c, 3),
+                       net ? 2 : 1, c->d_vpred, c->stream));
     TDKS_CUDA(cudaMemcpyAsync(c->d_backup, u, obytes, cudaMemcpyDeviceToDevice, c->stream));
     TDKS_CUDA(cudaMemsetAsync(c->d_rho, 0, gb, c->stream));
     c->launches += 1;
@@ -726,14 +752,78 @@ tdks_status tdks_step(tdks_ctx* c, void* u, double t, double dt) {
   c->launches += c->grid.periodic ? 3 : 2;   // reduce_current (or memset) + dipole partial + final
   if (c->grid.periodic) {
     TDKS_CUDA(launch_reduce_current(c->d_orb_obs, c->nk, c->norb, c->d_kw, 1.0 / c->omega, 1,
-                                    c->d_step_obs, c->stream));
+                                    c->d_step_obs, c->stream, c->ncell));
   } else {
     TDKS_CUDA(cudaMemsetAsync(c->d_step_obs, 0, 3 * sizeof(double), c->stream));
   }
   TDKS_CUDA(launch_dipole(c->d_rho, c->d_rho0, c->grid.n, c->grid.h, c->grid.periodic,
-                          c->d_partials, c->red_blocks, c->d_step_obs, c->stream));
+                          c->d_partials, c->red_blocks, c->d_step_obs, c->stream));   // cell 0
   return TDKS_OK;
 }
+
+tdks_status tdks_ms_init(tdks_ctx* c, int nX, int m0, double dX, const double* A_now, const double* A_prev) {
+  TDKS_TRY(check_ctx(c));
+  if (!c->grid.periodic) return fail(TDKS_EINVAL, "the multiscale mode needs periodic cells");
+  if (!A_now || !A_prev || nX < 3 || m0 < 1 || m0 + c->ncell > nX - 1 || !(dX > 0.0))
+    return fail(TDKS_EINVAL, "need nX >= 3, 1 <= m0, m0 + ncell <= nX - 1, dX > 0 and both A levels");
+  if (!c->ms_ready || nX != c->nX) {
+    for (int i = 0; i < 3; ++i) TDKS_TRY(dalloc(c, &c->d_A[i], nX));
+    TDKS_TRY(dalloc(c, &c->d_I, nX));
+    if (!c->d_ap_mid) {
+      TDKS_TRY(dalloc(c, &c->d_ap_mid, 3 * (size_t)c->ncell));
+      TDKS_TRY(dalloc(c, &c->d_ap_end, 3 * (size_t)c->ncell));
+    }
+  }
+  c->nX = nX; c->m0 = m0; c->dX = dX; c->ms_head = 0;
+  TDKS_CUDA(cudaMemcpyAsync(c->d_A[0], A_now, nX * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  TDKS_CUDA(cudaMemcpyAsync(c->d_A[2], A_prev, nX * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  TDKS_CUDA(cudaMemsetAsync(c->d_I, 0, nX * sizeof(double), c->stream));
+  TDKS_CUDA(cudaStreamSynchronize(c->stream));
+  c->ms_ready = true;
+  return TDKS_OK;
+}
+
+tdks_status tdks_ms_step(tdks_ctx* c, void* u, double t, double dt) {
+  TDKS_TRY(check_ctx(c));
+  if (!u) return fail(TDKS_EINVAL, "null orbitals");
+  if (!c->ms_ready) return fail(TDKS_EINVAL, "call tdks_ms_init first");
+  if (!c->have_potential) return fail(TDKS_EINVAL, "call tdks_update_potential before tdks_ms_step");
+  (void)t;
+  const double cl = 137.035999084;
+  const int h = c->ms_head;
+  double* Aprev = c->d_A[(h + 2) % 3];
+  double* Anow = c->d_A[h];
+  double* Anext = c->d_A[(h + 1) % 3];
+  {
+    Phase ph(c, 5);
+    TDKS_CUDA(launch_maxwell(Aprev, Anow, Anext, c->d_I, c->nX, c->m0, c->ncell, cl * dt / c->dX,
+                             4.0 * kPi * cl * dt * dt, 1.0 / cl, c->d_ap_mid, c->d_ap_end, c->stream));
+    c->launches += 1;
+  }
+  const double zero[3] = {0.0, 0.0, 0.0};
+  c->cur_ap_mid = c->d_ap_mid;
+  c->cur_ap_end = c->d_ap_end;
+  const tdks_status st = pc_step(c, u, zero, zero, dt);
+  c->cur_ap_mid = c->cur_ap_end = nullptr;
+  TDKS_TRY(st);
+  Phase ph(c, 4);
+  TDKS_CUDA(launch_reduce_current(c->d_orb_obs, c->nk, c->norb, c->d_kw, 1.0 / c->omega, 1,
+                                  c->d_step_obs, c->stream, c->ncell));
+  TDKS_CUDA(launch_ms_current(c->d_step_obs, c->ncell, c->m0, c->d_I, c->stream));
+  c->launches += 2;
+  c->ms_head = (h + 1) % 3;
+  return TDKS_OK;
+}
+
+tdks_status tdks_ms_read(tdks_ctx* c, double* A_host, double* I_host) {
+  TDKS_TRY(check_ctx(c));
+  if (!c->ms_ready) return fail(TDKS_EINVAL, "call tdks_ms_init first");
+  if (A_host) TDKS_CUDA(cudaMemcpyAsync(A_host, c->d_A[c->ms_head], c->nX * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  if (I_host) TDKS_CUDA(cudaMemcpyAsync(I_host, c->d_I, c->nX * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  TDKS_CUDA(cudaStreamSynchronize(c->stream));
+  return TDKS_OK;
+}
+
 
 tdks_status tdks_read_step_observables(tdks_ctx* c, tdks_obs* o) {
   TDKS_TRY(check_ctx(c));
@@ -753,6 +843,7 @@ tdks_status tdks_read_step_observables(tdks_ctx* c, tdks_obs* o) {
 tdks_status tdks_observables(tdks_ctx* c, const void* u, const double Ap[3], tdks_obs* o) {
   TDKS_TRY(check_ctx(c));
   if (!u || !o) return fail(TDKS_EINVAL, "null argument");
+  if (c->ncell > 1) return fail(TDKS_EUNSUPPORTED, "tdks_observables needs ncell = 1");
   double A[3] = {0, 0, 0};
   if (Ap && c->grid.periodic) for (int a = 0; a < 3; ++a) A[a] = Ap[a];
   TDKS_TRY(density(c, u, c->d_rho_tmp));
@@ -827,6 +918,7 @@ tdks_status tdks_set_predictor(tdks_ctx* c, int mode, double threshold) {
   if (mode < TDKS_PRED_PC || mode > TDKS_PRED_LEARNED) return fail(TDKS_EINVAL, "unknown predictor mode");
   if (!(threshold > 0.0)) return fail(TDKS_EINVAL, "threshold must be positive");
   if (mode == TDKS_PRED_LEARNED && !c->nn_ready) return fail(TDKS_EINVAL, "call tdks_nn_init first");
+  if (mode != TDKS_PRED_PC && c->ncell > 1) return fail(TDKS_EUNSUPPORTED, "predicted steps need ncell = 1");
   if (mode != TDKS_PRED_PC && !c->d_backup) {
     const size_t obytes = (size_t)c->nk * c->norb * c->npts * (is_f32(c) ? sizeof(float2) : sizeof(double2));
     unsigned char* p = nullptr;
@@ -872,7 +964,7 @@ tdks_status tdks_nn_init(tdks_ctx* c, unsigned long long seed) {
     TDKS_TRY(dalloc(c, &B.m, kNNParams));
     TDKS_TRY(dalloc(c, &B.v, kNNParams));
     TDKS_TRY(dalloc(c, &B.wq, kNNParams));
-    TDKS_TRY(dalloc(c, &B.stats, 4));
+    TDKS_TRY(dalloc(c, &B.stats, 8));
     TDKS_TRY(dalloc(c, &B.loss, 1));
   }
   std::vector<float> p(kNNParams, 0.0f);
@@ -944,15 +1036,16 @@ tdks_status tdks_nn_train(tdks_ctx* c, const double* vseq, int nt, int epochs, i
   return TDKS_OK;
 }
 
-tdks_status tdks_nn_predict(tdks_ctx* c, const double* vhist, double* vpred, int use_net) {
+tdks_status tdks_nn_predict(tdks_ctx* c, const double* vhist, double* vpred, int mode) {
   TDKS_TRY(check_ctx(c));
   if (!c->nn_ready) return fail(TDKS_EINVAL, "call tdks_nn_init first");
   if (!vhist || !vpred) return fail(TDKS_EINVAL, "null argument");
+  if (mode < 0 || mode > 2) return fail(TDKS_EINVAL, "mode must be 0 (linear), 1 (cubic) or 2 (network)");
   const NNGrid g = nn_grid(c);
   const size_t np = c->npts;
   TDKS_CUDA(nn_inputs(c->nn, g, vhist, vhist + np, vhist + 2 * np, vhist + 3 * np, nullptr, c->stream));
-  if (use_net) TDKS_CUDA(nn_forward(c->nn, g, c->stream));
-  TDKS_CUDA(nn_apply(c->nn, g, vhist, vhist + np, use_net != 0, vpred, c->stream));
+  if (mode == 2) TDKS_CUDA(nn_forward(c->nn, g, c->stream));
+  TDKS_CUDA(nn_apply(c->nn, g, vhist, vhist + np, vhist + 2 * np, vhist + 3 * np, mode, vpred, c->stream));
   return TDKS_OK;
 }
 

@@ -99,6 +99,11 @@ struct OrbArgs {
   const int* sp_off;        // [nsp+1]
   double Ap_obs[3];         // A' for the fused observables of the final state
   double* obs;              // nullable: per-orbital {norm, jloc[3], jnl[3], 0}
+  // batches of cells (multiscale): orbitals are [ncell][nk][norb], potentials [ncell][npts]
+  int ncell;                // cells in the batch (1 for a single system)
+  long long vstride;        // offset of a cell's potential (0: one potential shared by all)
+  const double* Ap_cell;    // nullable: [ncell][3] A' per cell, replaces Ap
+  const double* Ap_obs_cell;// nullable: [ncell][3], replaces Ap_obs
 };
 
 // Orbital kernels (k_orbital.cu)
@@ -163,7 +168,7 @@ struct NNBuffers {
   unsigned short *x0, *a1, *a2;                   // BF16 conv inputs [4|16|16][npts]
   float *y1, *y2, *out, *target, *dout, *dy1, *dy2, *part;
   float *params, *grad, *m, *v, *wq;              // [kNNParams]; wq = BF16-rounded params
-  double* stats;                                  // s, mean V0, s_V
+  double* stats;                                  // rms D1, rms D2, rms D3, mean V0, rms(V0 - mean)
   double* loss;                                   // accumulator
 };
 int nn_part_blocks(int npts);
@@ -174,28 +179,31 @@ cudaError_t nn_loss(const NNBuffers& B, const NNGrid& g, double* loss_acc, cudaS
 cudaError_t nn_backward(const NNBuffers& B, const NNGrid& g, cudaStream_t s);   // grad +=
 cudaError_t nn_adam(const NNBuffers& B, float lr, int t, float gscale, cudaStream_t s);
 cudaError_t nn_round_weights(const NNBuffers& B, cudaStream_t s);
-// vpred = 2 V0 - V1 (+ s * out if use_net)
+// vpred: mode 0 = 2 V0 - V1, 1 = cubic 4 V0 - 6 V1 + 4 V2 - V3, 2 = cubic + s3 * out
 cudaError_t nn_apply(const NNBuffers& B, const NNGrid& g, const double* V0, const double* V1,
-                     bool use_net, double* vpred, cudaStream_t s);
+                     const double* V2, const double* V3, int mode, double* vpred, cudaStream_t s);
 cudaError_t launch_residual(const double* Vnew, const double* Vpred, int n, double* res, cudaStream_t s);
 
 // Grid kernels (k_grid.cu)
+// batch = number of consecutive [dims2][dims1][dims0] arrays transformed together
 cudaError_t launch_fft_axis(double2* data, const int dims[3], int axis, int dir,
-                            const double2* tw, const int* radices, int nrad, cudaStream_t s);
+                            const double2* tw, const int* radices, int nrad, cudaStream_t s,
+                            int batch = 1);
 cudaError_t launch_pack_real(const double* src, const int n[3], double2* dst, const int m[3],
                              cudaStream_t s);
 cudaError_t launch_poisson_scale_periodic(double2* data, const int n[3], const double h[3],
-                                          cudaStream_t s);
+                                          cudaStream_t s, int batch = 1);
 cudaError_t launch_scale_by_real(double2* data, const double* ghat, double scale, size_t count,
                                  cudaStream_t s);
 // vhxc = scale_h * Re(fft[crop]) (if hartree) + V_x[rho] (if xc)
 cudaError_t launch_hxc_epilogue(const double2* fft, const int m[3], const double* rho,
                                 const int n[3], double scale_h, int hartree, int xc,
                                 double* vhxc, cudaStream_t s);
-// vstep64 = vloc + a*v1 + b*v2 (v2 nullable), and vstep32 = (float)vstep64 (nullable)
+// vstep64 = vloc + a*v1 + b*v2 (v2 nullable), and vstep32 = (float)vstep64 (nullable);
+// v1, v2, v64, v32 hold `batch` potentials of npts points, vloc one shared potential
 cudaError_t launch_combine_potential(const double* vloc, const double* v1, double a,
                                      const double* v2, double b, double* v64, float* v32,
-                                     int npts, cudaStream_t s);
+                                     int npts, cudaStream_t s, int batch = 1);
 template <typename T>
 cudaError_t launch_density(const typename Cplx<T>::type* psi, int nk, int norb, int npts,
                            const double* kw, double* rho, cudaStream_t s);
@@ -213,12 +221,19 @@ cudaError_t launch_real_part(const double2* src, double* dst, size_t count, doub
 cudaError_t launch_dipole(const double* rho, const double* rho0, const int n[3], const double h[3],
                           int periodic, double* partials, int nblocks, double* out,
                           cudaStream_t s);
-// J from per-orbital observables; writes out[0..2] = J (zero if isolated)
+// J from per-orbital observables; writes out[c*8 + 0..2] = J of cell c (zero if isolated)
 cudaError_t launch_reduce_current(const double* orb_obs, int nk, int norb, const double* kw,
-                                  double inv_omega, int periodic, double* out, cudaStream_t s);
+                                  double inv_omega, int periodic, double* out, cudaStream_t s,
+                                  int ncell = 1);
+// 1D Maxwell leapfrog (Eq. Maxwell_ms) with Mur boundaries; A'(X) of the cells at t+dt/2 and t+dt
+cudaError_t launch_maxwell(const double* A_prev, const double* A_now, double* A_next, const double* I,
+                           int nX, int m0, int ncell, double c_dt_dX, double src, double inv_c,
+                           double* ap_mid, double* ap_end, cudaStream_t s);
+// I[m0 + c] = step_obs[c*8 + 2]
+cudaError_t launch_ms_current(const double* step_obs, int ncell, int m0, double* I, cudaStream_t s);
 cudaError_t launch_f32_from_f64(const double* src, float* dst, size_t count, cudaStream_t s);
-// rho[p] = sum_k w_k rho32[k][p] in FP64 (fixed order)
+// rho[c][p] = sum_k w_k rho32[c][k][p] in FP64 (fixed order)
 cudaError_t launch_fold_density(const float* rho32, int nk, int npts, const double* kw, double* rho,
-                                cudaStream_t s);
+                                cudaStream_t s, int ncell = 1);
 
 }  // namespace tdks

@@ -45,7 +45,8 @@ class ProjectorC(C.Structure):
 
 
 class Options(C.Structure):
-    _fields_ = [("precision", C.c_int), ("hartree", C.c_int), ("xc", C.c_int), ("pc", C.c_int)]
+    _fields_ = [("precision", C.c_int), ("hartree", C.c_int), ("xc", C.c_int), ("pc", C.c_int),
+                ("ncell", C.c_int)]
 
 
 class Obs(C.Structure):
@@ -101,6 +102,9 @@ def load_library(path: str = LIB_PATH):
         "tdks_check": [vp],
         "tdks_profile": [vp, i],
         "tdks_set_predictor": [vp, i, d],
+        "tdks_ms_init": [vp, i, i, d, C.POINTER(C.c_double), C.POINTER(C.c_double)],
+        "tdks_ms_step": [vp, vp, d, d],
+        "tdks_ms_read": [vp, C.POINTER(C.c_double), C.POINTER(C.c_double)],
         "tdks_nn_init": [vp, C.c_ulonglong],
         "tdks_nn_params": [vp, C.POINTER(C.c_float), i, i],
         "tdks_nn_train": [vp, vp, i, i, i, d, C.c_ulonglong, C.POINTER(C.c_double)],
@@ -147,7 +151,7 @@ class Context:
     norb, field.  Orbitals are torch tensors [nk, norb, nz, ny, nx], complex128 (f64) or
     complex64 (f32), on the current CUDA device."""
 
-    def __init__(self, system, precision="f64", hartree=True, xc=True, pc=True, stream=None):
+    def __init__(self, system, precision="f64", hartree=True, xc=True, pc=True, stream=None, ncell=1):
         import torch
         lib = load_library()
         self.lib = lib
@@ -163,7 +167,8 @@ class Context:
         pr = ProjectorC(system.proj.E_s, system.proj.E_p, system.proj.r_cut, system.proj.width)
         kp = np.ascontiguousarray(np.asarray(system.kpts, np.float64).reshape(-1))
         kw = np.ascontiguousarray(np.asarray(system.kw, np.float64))
-        opts = Options(TDKS_F64 if precision == "f64" else TDKS_F32, int(hartree), int(xc), int(pc))
+        opts = Options(TDKS_F64 if precision == "f64" else TDKS_F32, int(hartree), int(xc), int(pc), int(ncell))
+        self.ncell = int(ncell)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
@@ -226,6 +231,24 @@ class Context:
         _check(self.lib.tdks_get_grid_array(self.ctx, int(which), _ptr(out)))
         return out
 
+    # ---- multiscale
+    def ms_init(self, dX, m0, A_now, A_prev):
+        a = np.ascontiguousarray(A_now, np.float64)
+        b = np.ascontiguousarray(A_prev, np.float64)
+        self.nX = len(a)
+        _check(self.lib.tdks_ms_init(self.ctx, len(a), int(m0), float(dX), a.ctypes.data_as(C.POINTER(C.c_double)),
+                                     b.ctypes.data_as(C.POINTER(C.c_double))))
+
+    def ms_step(self, u, t, dt):
+        _check(self.lib.tdks_ms_step(self.ctx, _ptr(u, self.cdtype), float(t), float(dt)))
+
+    def ms_read(self):
+        A = np.zeros(self.nX)
+        I = np.zeros(self.nX)
+        _check(self.lib.tdks_ms_read(self.ctx, A.ctypes.data_as(C.POINTER(C.c_double)),
+                                     I.ctypes.data_as(C.POINTER(C.c_double))))
+        return A, I
+
     # ---- predictor and learned network
     def set_predictor(self, mode, threshold=1e-5):
         _check(self.lib.tdks_set_predictor(self.ctx, int(mode), float(threshold)))
@@ -247,8 +270,9 @@ class Context:
                                       float(lr), int(seed), loss.ctypes.data_as(C.POINTER(C.c_double))))
         return loss
 
-    def nn_predict(self, vhist, vpred, use_net=True):
-        _check(self.lib.tdks_nn_predict(self.ctx, _ptr(vhist), _ptr(vpred), int(use_net)))
+    def nn_predict(self, vhist, vpred, mode=2):
+        """mode 0: linear extrapolation, 1: cubic extrapolation, 2: the network."""
+        _check(self.lib.tdks_nn_predict(self.ctx, _ptr(vhist), _ptr(vpred), int(mode)))
 
     def nn_gradient(self, vhist, vnext):
         g = np.zeros(NN_NPARAMS, np.float32)

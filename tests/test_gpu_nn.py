@@ -29,12 +29,12 @@ def _ctx(s, precision="f64"):
 
 
 def _hist(s, seed):
+    """Five consecutive potentials with generic (non-polynomial) time dependence."""
     rng = np.random.default_rng(seed)
     shape = (s.n[2], s.n[1], s.n[0])
-    base = rng.standard_normal(shape)
-    d = 0.01 * rng.standard_normal(shape)
-    c = 0.002 * rng.standard_normal(shape)
-    V = [base + k * d + k * k * c for k in range(5)]        # V(t-3dt) .. V(t+dt)
+    base, d, c, e = (rng.standard_normal(shape) for _ in range(4))
+    V = [base + 0.01 * np.sin(0.3 * k) * d + 0.002 * np.cos(0.7 * k) * c + 0.001 * np.sin(1.3 * k) * e
+         for k in range(5)]                                 # V(t-3dt) .. V(t+dt)
     return V[3], V[2], V[1], V[0], V[4]
 
 
@@ -64,13 +64,15 @@ def test_nn_forward_parity(name):
     V0, V1, V2, V3, _ = _hist(s, 2)
     vh = torch.from_numpy(np.stack([V0, V1, V2, V3])).to("cuda")
     vp = torch.empty_like(vh[0])
-    ctx.nn_predict(vh, vp, use_net=True)
-    got = (vp.cpu().numpy() - (2 * V0 - V1))
+    ctx.nn_predict(vh, vp, mode=2)
+    got = (vp.cpu().numpy() - N.cubic_extrapolation(V0, V1, V2, V3))
     out, sc, _ = _emulated_forward(params, V0, V1, V2, V3, s.periodic)
     ref = sc * out
     assert np.linalg.norm(got - ref) < 1e-3 * np.linalg.norm(ref)
-    ctx.nn_predict(vh, vp, use_net=False)
+    ctx.nn_predict(vh, vp, mode=0)
     assert np.max(np.abs(vp.cpu().numpy() - (2 * V0 - V1))) < 1e-14 * np.max(np.abs(V0))
+    ctx.nn_predict(vh, vp, mode=1)
+    assert np.max(np.abs(vp.cpu().numpy() - N.cubic_extrapolation(V0, V1, V2, V3))) < 1e-13 * np.max(np.abs(V0))
 
 
 @pytest.mark.parametrize("name", list(SYS))
@@ -88,7 +90,7 @@ def test_nn_gradient_parity(name):
     # oracle gradient through the same BF16-rounded tensors
     out, sc, (x, y1, a1, y2, a2) = _emulated_forward(params, V0, V1, V2, V3, s.periodic)
     W1, b1, W2, b2, W3, b3 = N.unpack(bf16(params))
-    t = N.target(V0, V1, V4, sc)
+    t = N.target(V0, V1, V2, V3, V4, sc)
     n = out.size
     dout = (2.0 / n) * (out - t)
     da2, dW3, db3 = N.conv_bwd(a2, W3, dout[None], s.periodic)
@@ -112,7 +114,7 @@ def test_nn_training_reduces_loss():
     rng = np.random.default_rng(7)
     shape = (8, 8, 8)
     base, d, c = rng.standard_normal(shape), 0.01 * rng.standard_normal(shape), 0.001 * rng.standard_normal(shape)
-    seq = np.stack([base + k * d + 0.5 * k * k * c * np.cos(0.05 * k) for k in range(40)])
+    seq = np.stack([base + np.sin(0.2 * k) * d + np.cos(0.35 * k) * c for k in range(40)])
     vseq = torch.from_numpy(seq).to("cuda")
     loss = ctx.nn_train(vseq, epochs=30, batch=4, lr=3e-3, seed=2)
     assert np.all(np.isfinite(loss))

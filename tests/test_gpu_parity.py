@@ -218,3 +218,20 @@ def test_diamond_full_size_one_step():
         assert _rel(ud.cpu().numpy().astype(np.complex128), ref) < tol
         assert np.max(np.abs(o["J"] - Jref)) < jtol * np.max(np.abs(Jref))
         ctx.close()
+
+
+def test_norm_monitor_reports_nonfinite():
+    """A NaN planted in one orbital on the host is reported by the norm monitor as
+    TDKS_ENONFINITE; the context stays usable afterwards."""
+    from paper_1804_01404_gb300.tdks import TdksError
+    s = W.small_periodic()
+    psi = W.initial_orbitals(s, 0)
+    ctx = _ctx(s)
+    ctx.update_potential(_dev(psi, "f64"))
+    bad = psi.copy()
+    bad[0, 3, 5, 6, 7] = np.nan
+    with pytest.raises(TdksError) as ei:
+        ctx.observables(_dev(bad, "f64"))
+    assert ei.value.status == 5
+    o = ctx.observables(_dev(psi, "f64"))
+    assert abs(o["norm_max"] - 1.0) < 1e-12

@@ -63,14 +63,32 @@ def test_silu_derivative():
     assert np.allclose((N.silu(y + h) - N.silu(y - h)) / (2 * h), N.dsilu(y), atol=1e-8)
 
 
-def test_zero_network_is_linear_extrapolation():
-    """With all weights zero the prediction is exactly 2 V(t) - V(t-dt), and the target of a
-    potential that moves linearly in time is zero."""
+def test_zero_network_is_cubic_extrapolation():
+    """With all weights zero the prediction is the cubic through the four potentials; a potential
+    cubic in time is predicted exactly (target 0), and its vanishing fourth difference is not
+    amplified by the normalisation (floored scales)."""
     rng = np.random.default_rng(4)
-    V0, D = rng.standard_normal((2, 4, 5, 6))
-    V1, V2, V3 = V0 - D, V0 - 2 * D, V0 - 3 * D
+    V0, D, Q, R = rng.standard_normal((4, 4, 5, 6))
+    V = [V0 - k * D + 0.5 * k * k * Q - k ** 3 * R / 6 for k in range(5)]     # V(t - k dt), k = -1..3 below
+    Vnext = V0 + D + 0.5 * Q + R / 6
     p = np.zeros(N.NPARAMS)
-    assert np.allclose(N.predict(p, V0, V1, V2, V3, True), 2 * V0 - V1)
-    x, s = N.inputs(V0, V1, V2, V3)
-    assert np.allclose(N.target(V0, V1, V0 + D, s), 0.0)
-    assert abs(s - np.sqrt(np.mean(D ** 2))) < 1e-14
+    assert np.allclose(N.predict(p, *V[:4], True), N.cubic_extrapolation(*V[:4]))
+    assert np.allclose(N.cubic_extrapolation(*V[:4]), Vnext)
+    x, s3 = N.inputs(*V[:4])
+    assert np.all(np.isfinite(x)) and np.max(np.abs(x)) < 50
+    assert np.max(np.abs(N.target(*V[:4], Vnext, s3))) < 1e-10
+
+
+def test_scales_and_channels():
+    """Channels are the backward differences over their root mean squares; a quadratic potential has
+    a third difference at rounding level, which the floor keeps from being blown up to O(1)."""
+    rng = np.random.default_rng(8)
+    V = rng.standard_normal((4, 4, 5, 6))
+    x, s3 = N.inputs(*V)
+    D2 = V[0] - 2 * V[1] + V[2]
+    D3 = V[0] - 3 * V[1] + 3 * V[2] - V[3]
+    assert np.allclose(x[1] * N.rms(D2), D2) and abs(s3 - N.rms(D3)) < 1e-14
+    V0, D, Q = rng.standard_normal((3, 4, 5, 6))
+    Vq = [V0 - k * D + 0.5 * k * k * Q for k in range(4)]
+    xq, _ = N.inputs(*Vq)
+    assert np.max(np.abs(xq[2])) < 0.1

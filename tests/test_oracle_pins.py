@@ -456,3 +456,38 @@ def test_maxwell_leapfrog_closed_forms():
         A_prev, A_now = A_now, O.maxwell_step(A_now, A_prev, np.full(30, I), 0.5, dt)
         # away from the held end points (their influence moves one cell per step)
         assert np.allclose(A_now[8:-8], 2 * np.pi * O.C_LIGHT * I * (n * dt) ** 2, rtol=1e-12)
+
+
+def test_mur_boundary_absorbs():
+    """A pulse leaving the 1D box through a Mur boundary leaves almost nothing behind (the first-order
+    condition is exact for normal incidence at c dt = dX and small otherwise)."""
+    X = np.arange(300, dtype=float)
+    f = lambda x: np.exp(-((x - 150.0) / 12.0) ** 2)
+    k = 0.5
+    A_prev, A_now = f(X + k), f(X)            # right-going at speed k cells per step
+    for _ in range(500):
+        A_next = O.mur_boundary(O.maxwell_step(A_now, A_prev, np.zeros(300), k, 0.1), A_now, k)
+        A_prev, A_now = A_now, A_next
+    assert np.max(np.abs(A_now)) < 0.02
+
+
+def test_multiscale_without_coupling_is_independent_cells():
+    """If the material current is zero (no occupied response: cells given zero orbitals is not allowed,
+    so compare against direct per-cell steps) each cell's step equals pc_step with A'(t+dt/2) taken
+    from the Maxwell field at its point."""
+    s = W.tiny(periodic=True, n=(6, 6, 6), natom=1, norb=2)
+    tabs = O.projector_tables(s)
+    Vloc = O.local_potential(s)
+    psi0 = W.initial_orbitals(s, 3)
+    v0 = O.hxc(s, O.density(s, psi0))
+    nX, m0 = 8, 3
+    A_now = np.linspace(0.0, 0.7, nX)
+    A_prev = A_now * 0.99
+    I = np.zeros(nX)
+    cells, A_next, _, I_next = O.multiscale_step(s, tabs, Vloc, [(psi0, v0), (psi0, v0)], A_now, A_prev, I, m0, 250.0, 0.0, 0.02)
+    for j in range(2):
+        X = m0 + j
+        Amid = np.array([0, 0, 0.5 * (A_now[X] + A_next[X]) / O.C_LIGHT])
+        ref, _, _ = O.pc_step(s, tabs, Vloc, psi0, v0, 0.0, 0.02, Ap=Amid)
+        assert np.max(np.abs(cells[j][0] - ref)) < 1e-14
+        assert abs(I_next[X] - O.current(s, tabs, ref, [0, 0, A_next[X] / O.C_LIGHT])[2]) < 1e-15
