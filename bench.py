@@ -151,91 +151,172 @@ def reference_arm(args, rank, world):
     return 0
 
 
+def timed_steps(ctx, u, s, t0, warmup, steps, flush, record_j=False):
+    """Run warmup + timed steps; every timed step is bracketed by CUDA events on the context
+    stream, with an L2 flush (not timed) before it.  Returns (per-step ms, J history, stats)."""
+    import torch
+    stream = torch.cuda.current_stream()
+    t = t0
+    J = []
+    for _ in range(warmup):
+        ctx.step(u, t, s.dt)
+        t += s.dt
+        if record_j:
+            J.append(ctx.read_step_observables()["J"])
+    torch.cuda.synchronize()
+    ctx.stats(reset=True)
+    ctx.profile(True)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for i in range(steps):
+        flush.zero_()                                    # evict the 65 MB orbital set from L2
+        evs[i][0].record(stream)
+        ctx.step(u, t, s.dt)
+        evs[i][1].record(stream)
+        t += s.dt
+        if record_j:
+            J.append(ctx.read_step_observables()["J"])
+    torch.cuda.synchronize()
+    st = ctx.stats(reset=True)
+    ctx.profile(False)
+    return [a.elapsed_time(b) for a, b in evs], np.array(J), st
+
+
+def train_predictor(s, t0, ntraj=4, nsteps=300, epochs=3):
+    """Network weights trained on trajectories the method itself generates (seeds 1..ntraj, the
+    bench state uses seed 0), FP32 path."""
+    from paper_1804_01404_gb300 import learned as L
+    from paper_1804_01404_gb300 import workloads as W
+    from paper_1804_01404_gb300.tdks import Context
+    tic = time.perf_counter()
+    trajs = [L.trajectory(s, W.initial_orbitals(s, seed), nsteps, "f32", t0=t0) for seed in range(1, ntraj + 1)]
+    ctx = Context(s, precision="f32")
+    ctx.nn_init(1)
+    loss = L.train(ctx, trajs, epochs=epochs, batch=8, lr=1e-3, seed=3)
+    held = L.trajectory(s, W.initial_orbitals(s, 101), 60, "f32", t0=t0)
+    mis = {name: float(np.mean(L.misfits(ctx, held, m))) for name, m in (("linear", 0), ("cubic", 1), ("network", 2))}
+    params = ctx.nn_params()
+    ctx.close()
+    return params, {"train_loss_per_epoch": [float(x) for x in loss], "heldout_misfit_mean": mis,
+                    "training_s": time.perf_counter() - tic,
+                    "data": f"{ntraj} trajectories x {nsteps} steps (seeds 1-{ntraj}), held-out seed 101"}
+
+
 def gpu_arm(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
+    from paper_1804_01404_gb300 import tdks as T
     from paper_1804_01404_gb300.tdks import Context
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     s = workload()
     psi0 = W_initial(s).astype(np.complex64)
-    u = torch.from_numpy(psi0).to(dev)
-    ctx = Context(s, precision="f32")
-    stream = torch.cuda.current_stream()
-    ctx.update_potential(u)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    t = 0.0
     t0 = 200.0   # start inside the pulse (A' != 0)
-    for i in range(args.warmup):
-        ctx.step(u, t0 + i * s.dt, s.dt)
+
+    # FP64 predictor-corrector reference current over the same steps (judge of the error bound)
+    nref = args.warmup + args.steps
+    ctx64 = Context(s, precision="f64")
+    u64 = torch.from_numpy(psi0.astype(np.complex128)).to(dev)
+    ctx64.update_potential(u64)
+    J64, t = [], t0
     torch.cuda.synchronize()
-    ctx.stats(reset=True)
-    ctx.profile(True)
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clocks = ClockSampler(local_rank)
-    t = t0 + args.warmup * s.dt
-    for i in range(args.steps):
-        flush.zero_()                                    # evict the 65 MB orbital set from L2
-        evs[i][0].record(stream)
-        ctx.step(u, t, s.dt)
-        evs[i][1].record(stream)
+    tic = time.perf_counter()
+    for _ in range(nref):
+        ctx64.step(u64, t, s.dt)
         t += s.dt
+        J64.append(ctx64.read_step_observables()["J"])
     torch.cuda.synchronize()
+    f64_sps = nref / (time.perf_counter() - tic)
+    J64 = np.array(J64)
+    ctx64.close()
+    del u64
+
+    def jerr(J):
+        return float(np.max(np.abs(J - J64)) / np.max(np.abs(J64)))
+
+    # plain predictor-corrector, FP32 orbitals
+    ctx = Context(s, precision="f32")
+    u = torch.from_numpy(psi0).to(dev)
+    ctx.update_potential(u)
     if world > 1:
         dist.barrier()
+    clocks = ClockSampler(local_rank)
+    pc_ms, J_pc, st_pc = timed_steps(ctx, u, s, t0, args.warmup, args.steps, flush, record_j=True)
+    ctx.close()
+
+    # learned predictor (PC fallback) and the cubic-extrapolation ablation
+    params, train_info = train_predictor(s, t0) if not args.skip_learned else (None, None)
+    modes = {}
+    if params is not None:
+        for name, mode in (("learned", T.PRED_LEARNED), ("cubic", T.PRED_EXTRAP)):
+            c2 = Context(s, precision="f32")
+            u2 = torch.from_numpy(psi0).to(dev)
+            c2.update_potential(u2)
+            c2.nn_init(0)
+            c2.nn_params(params)
+            c2.set_predictor(mode, 1e-5)
+            ms, J, st = timed_steps(c2, u2, s, t0, args.warmup, args.steps, flush, record_j=True)
+            o = c2.read_step_observables()
+            modes[name] = dict(ms=ms, J=J, st=st, fallbacks=o["fallbacks"])
+            c2.close()
     clk = clocks.stop()
-    step_ms = [a.elapsed_time(b) for a, b in evs]
+
+    head = modes.get("learned")
+    step_ms = head["ms"] if head else pc_ms
+    st = head["st"] if head else st_pc
     total_ms = float(np.sum(step_ms))
-    st = ctx.stats(reset=True)
-    ctx.profile(False)
     if world > 1:
         tt = torch.tensor([total_ms], device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         total_ms = float(tt.item())
     value = world * args.steps / (total_ms / 1e3)
 
-    # dominant kernel: the Taylor kernel (predictor + corrector launches)
+    # dominant kernel: the Taylor kernel of the PC run (predictor + corrector launches)
     npts, norb_tot = s.npts, s.nk * s.norb
-    nsph = ctx.query()["nsphere_points"]
-    k_ms = (st["ms"]["taylor_predictor"] + st["ms"]["taylor_corrector"]) / max(
-        1, st["calls"]["taylor_predictor"] + st["calls"]["taylor_corrector"])
+    nsph = W_nsph(s)
+    k_ms = (st_pc["ms"]["taylor_predictor"] + st_pc["ms"]["taylor_corrector"]) / max(
+        1, st_pc["calls"]["taylor_predictor"] + st_pc["calls"]["taylor_corrector"])
     flops = 4 * norb_tot * (FLOPS_PER_POINT_STAGE * npts + FLOPS_PER_SPHERE_ENTRY_STAGE * nsph)
     pk = peaks()
     fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     achieved = flops / (k_ms * 1e-3) / 1e12
-    # HBM view of the same kernel: read psi + write psi' (corrector), 8 B each per point
     hbm_bytes = 16 * npts * norb_tot
     roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak, "traffic": None,
-                "kernel": "k_smem_orbital<float, MODE=1> (4 Horner stages, whole orbital in smem)",
+                "kernel": "k_cell<float, MODE=1> (4 Horner stages, whole orbital in shared memory)",
                 "avg_launch_ms": k_ms, "flops_per_launch": flops,
-                "peak_note": "FP32 FMA peak = 152 SM x 128 lanes x 2 x max SM clock (derived)",
+                "peak_note": "FP32 peak = 152 SM x 128 lanes x 2 flop x max SM clock (derived, not measured)",
                 "hbm_view": {"bytes_per_launch": hbm_bytes,
                              "GBps": hbm_bytes / (k_ms * 1e-3) / 1e9,
                              "frac_of_measured_hbm": hbm_bytes / (k_ms * 1e-3) / 1e9 / pk["hbm_gbs"]}}
-    phases = {k: v / args.steps for k, v in st["ms"].items()}
 
-    # FP64 path on the same GPU (context numbers): steps/s and the FP32-vs-FP64 current error
-    fp64 = None
-    if not args.skip_fp64 and rank == 0:
-        fp64 = fp64_comparison(s, psi0, dev, nsteps=args.fp64_steps)
+    predictors = {"pc": {"steps_per_s": args.steps / (np.sum(pc_ms) / 1e3),
+                         "J_rel_err_vs_f64_pc": jerr(J_pc),
+                         "phase_ms_per_step": {k: v / args.steps for k, v in st_pc["ms"].items()}}}
+    for name, m in modes.items():
+        predictors[name] = {"steps_per_s": args.steps / (np.sum(m["ms"]) / 1e3), "J_rel_err_vs_f64_pc": jerr(m["J"]),
+                            "fallbacks": m["fallbacks"], "steps": args.warmup + args.steps,
+                            "phase_ms_per_step": {k: v / args.steps for k, v in m["st"]["ms"].items()}}
+    predictors["f64_pc_steps_per_s_host_synced"] = f64_sps
+    if train_info:
+        predictors["training"] = train_info
 
-    # end to end through the C ABI with host buffers: upload psi(0) from pinned memory, K steps
-    # each reading J and the dipole back to the host, download psi at the end
+    # end to end through the C ABI with host buffers (same predictor as the headline)
     host_in = torch.from_numpy(psi0).pin_memory()
     host_out = torch.empty_like(host_in).pin_memory()
     ctx2 = Context(s, precision="f32")
     u2 = torch.empty_like(u)
-    ctx2.update_potential(u)  # warm the context
+    if params is not None:
+        ctx2.nn_init(0)
+        ctx2.nn_params(params)
     torch.cuda.synchronize()
     tic = time.perf_counter()
     u2.copy_(host_in, non_blocking=True)
     ctx2.update_potential(u2)
+    if params is not None:
+        ctx2.set_predictor(T.PRED_LEARNED, 1e-5)
     tt = t0
     for i in range(args.steps):
         ctx2.step(u2, tt, s.dt)
@@ -247,9 +328,10 @@ def gpu_arm(args, rank, world, local_rank):
     psi_bytes = psi0.nbytes
     e2e = {"value": world * args.steps / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": psi_bytes / args.steps,
-           "d2h_bytes_per_step": psi_bytes / args.steps + 8 * 8,
-           "note": "psi(0) uploaded and psi(T) downloaded once per K steps; J and dipole read "
-                   "back every step (synchronising)"}
+           "d2h_bytes_per_step": psi_bytes / args.steps + 10 * 8,
+           "note": "psi(0) uploaded and psi(T) downloaded once per K steps; J, dipole and the "
+                   "predictor misfit read back every step (synchronising)"}
+    ctx2.close()
 
     hpsi = None
     if rank == 0 and not args.skip_hpsi:
@@ -268,13 +350,25 @@ def gpu_arm(args, rank, world, local_rank):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": config_dict(s, {"parallelism": f"replicas x{world}"}),
+                "config": config_dict(s, {"parallelism": f"replicas x{world}",
+                                          "predictor": "learned (PC fallback at misfit > 1e-5)" if head
+                                          else "predictor-corrector"}),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": st["launches"], "clocks": clk,
-                "phase_ms_per_step": phases, "step_ms_min": float(np.min(step_ms)),
-                "fp64": fp64, "hpsi_cluster": hpsi}
+                "phase_ms_per_step": {k: v / args.steps for k, v in st["ms"].items()},
+                "step_ms_min": float(np.min(step_ms)),
+                "J_rel_err_vs_f64": jerr(head["J"]) if head else jerr(J_pc),
+                "predictors": predictors, "hpsi_cluster": hpsi}
         print(json.dumps(line), flush=True)
     return 0
+
+
+def W_nsph(s):
+    from paper_1804_01404_gb300.tdks import Context
+    c = Context(s, precision="f32")
+    n = c.query()["nsphere_points"]
+    c.close()
+    return n
 
 
 def hpsi_cluster(dev, reps=10, norb=256):
@@ -322,34 +416,6 @@ def hpsi_cluster(dev, reps=10, norb=256):
     return res
 
 
-def fp64_comparison(s, psi0, dev, nsteps=10):
-    """Same steps with FP64 orbitals: steps/s and max_t |J32 - J64| / max_t |J64|."""
-    import torch
-    from paper_1804_01404_gb300.tdks import Context
-    out = {}
-    js = {}
-    for prec, dt_ in (("f64", torch.complex128), ("f32", torch.complex64)):
-        ctx = Context(s, precision=prec)
-        u = torch.from_numpy(psi0.astype(np.complex128)).to(dev, dt_)
-        ctx.update_potential(u)
-        t = 200.0
-        J = []
-        torch.cuda.synchronize()
-        tic = time.perf_counter()
-        for _ in range(nsteps):
-            ctx.step(u, t, s.dt)
-            t += s.dt
-            J.append(ctx.read_step_observables()["J"])
-        torch.cuda.synchronize()
-        out[prec + "_steps_per_s"] = nsteps / (time.perf_counter() - tic)
-        js[prec] = np.array(J)
-        ctx.close()
-    out["steps"] = nsteps
-    out["J_rel_err_f32_vs_f64"] = float(np.max(np.abs(js["f32"] - js["f64"])) / np.max(np.abs(js["f64"])))
-    out["note"] = "both timed with a host read of J every step"
-    return out
-
-
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -357,7 +423,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--skip-cpu", action="store_true")
-    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-learned", action="store_true")
     ap.add_argument("--skip-hpsi", action="store_true")
     ap.add_argument("--only", default="", choices=["", "hpsi"],
                     help="hpsi: only the tdks_hpsi measurement on the isolated cluster (profiling)")
