@@ -62,7 +62,7 @@ inline size_t cell_smem_bytes(int nz, int pstride, int nsph, int natom, bool dbu
   return sizeof(C) * (vsz * (dbuf ? 2 : 1) + nsph + 4 * (size_t)natom);
 }
 
-constexpr int kNT = 512;               // threads per CTA (upper bound)
+constexpr int kNT = 832;               // threads per CTA (upper bound)
 constexpr size_t kSmemLimit = 220 * 1024;
 
 // Projections of the shared-memory vector:  ec[a*4+p] = E_p dV sum_i beta_ip ph_i v(idx_i).
@@ -147,14 +147,13 @@ __device__ __forceinline__ typename Cplx<T>::type zload(const OrbArgs<T>& a,
   return v[zz * a.pstride + col];
 }
 
-// Local part of (H v) at (x, y, z) of a column: diag*v + S + (-i) D, z-neighbours from window w.
+// Local part of (H v) at (x, y, z) of a column: diag*v + S + (-i) q.D, z-neighbours from window w.
 template <typename T, bool PER>
 __device__ __forceinline__ typename Cplx<T>::type local_h(const OrbArgs<T>& a,
                                                           const Column<T, PER>& c,
                                                           const typename Cplx<T>::type* v,
                                                           const typename Cplx<T>::type* w, int zb,
-                                                          T diag, const T* gx, const T* gy,
-                                                          const T* gz) {
+                                                          T diag, const T* q) {
   using C = typename Cplx<T>::type;
   using M = CM<T>;
   // independent accumulators per axis keep the FMA chains short
@@ -169,15 +168,15 @@ __device__ __forceinline__ typename Cplx<T>::type local_h(const OrbArgs<T>& a,
     Sy = M::fma(a.c2y[m], M::add(yp, ym), Sy);
     Sz = M::fma(a.c2z[m], M::add(zp, zm), Sz);
     if (PER) {
-      Dx = M::fma(gx[m - 1], M::sub(xp, xm), Dx);
-      Dy = M::fma(gy[m - 1], M::sub(yp, ym), Dy);
-      Dz = M::fma(gz[m - 1], M::sub(zp, zm), Dz);
+      Dx = M::fma(a.d1x[m - 1], M::sub(xp, xm), Dx);
+      Dy = M::fma(a.d1y[m - 1], M::sub(yp, ym), Dy);
+      Dz = M::fma(a.d1z[m - 1], M::sub(zp, zm), Dz);
     }
   }
   C S = M::add(M::add(Sx, Sy), Sz);
   if (PER) {
-    const C D = M::add(M::add(Dx, Dy), Dz);
-    S = C{S.x + D.y, S.y - D.x};   // + (-i) D
+    const C D = M::fma(q[2], Dz, M::fma(q[1], Dy, M::fma(q[0], Dx, C{0, 0})));
+    S = C{S.x + D.y, S.y - D.x};   // + (-i) q.D
   }
   return S;
 }
@@ -231,6 +230,53 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return t;   // valid in thread 0
 }
 
+// sum over atoms of sum_p 2 E_p Im(conj(b_ap^(d)) c_ap) dV^2 (the nonlocal current of one orbital),
+// one warp per atom; valid in lane 0 of each warp (summed later by block_sum).
+template <typename T>
+__device__ __forceinline__ void nonlocal_current(const OrbArgs<T>& a, const typename Cplx<T>::type* v,
+                                                 const typename Cplx<T>::type* ph, double jnl[3]) {
+  using C = typename Cplx<T>::type;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int at = warp; at < a.natom; at += nw) {
+    T cb[8], bb[3][8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) { cb[j] = 0; bb[0][j] = bb[1][j] = bb[2][j] = 0; }
+    for (int i = a.atom_off[at] + lane; i < a.atom_off[at + 1]; i += 32) {
+      const C u = v[a.sph_sidx[i]];
+      const C f = ph[i];
+      const T re = u.x * f.x - u.y * f.y, im = u.x * f.y + u.y * f.x;
+      const T d0 = a.sph_d[3 * i], d1 = a.sph_d[3 * i + 1], d2 = a.sph_d[3 * i + 2];
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        const T b = a.sph_beta[i * 4 + p];
+        cb[2 * p] += b * re; cb[2 * p + 1] += b * im;
+        bb[0][2 * p] += d0 * b * re; bb[0][2 * p + 1] += d0 * b * im;
+        bb[1][2 * p] += d1 * b * re; bb[1][2 * p + 1] += d1 * b * im;
+        bb[2][2 * p] += d2 * b * re; bb[2][2 * p + 1] += d2 * b * im;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        cb[j] += __shfl_xor_sync(0xffffffffu, cb[j], o);
+        bb[0][j] += __shfl_xor_sync(0xffffffffu, bb[0][j], o);
+        bb[1][j] += __shfl_xor_sync(0xffffffffu, bb[1][j], o);
+        bb[2][j] += __shfl_xor_sync(0xffffffffu, bb[2][j], o);
+      }
+    if (lane == 0) {
+      const double dv2 = (double)a.dV * (double)a.dV;
+      for (int d = 0; d < 3; ++d) {
+        double sacc = 0;
+        for (int p = 0; p < 4; ++p)
+          sacc += 2.0 * (double)a.atomE[at * 4 + p] *
+                  ((double)bb[d][2 * p] * cb[2 * p + 1] - (double)bb[d][2 * p + 1] * cb[2 * p]);
+        jnl[d] += sacc * dv2;
+      }
+    }
+  }
+}
+
 // MODE 0: out = H v.   MODE 1: out = T4 v (Horner), rho += 2 w_k |out|^2, optional fused
 // observables.   MODE 2: observables only (norm, current, <v|H|v> with a.V).
 // DBUF: next vector in shared memory; otherwise in the orbital's slice of `scratch`.
@@ -259,13 +305,6 @@ __global__ void __launch_bounds__(kNT) k_cell(OrbArgs<T> a, typename Cplx<T>::ty
   q[0] = (T)(a.kpts[3 * k] + ap[0]);
   q[1] = (T)(a.kpts[3 * k + 1] + ap[1]);
   q[2] = (T)(a.kpts[3 * k + 2] + ap[2]);
-  T gx[4], gy[4], gz[4];
-#pragma unroll
-  for (int m = 0; m < 4; ++m) {
-    gx[m] = q[0] * a.d1x[m];
-    gy[m] = q[1] * a.d1y[m];
-    gz[m] = q[2] * a.d1z[m];
-  }
   const T diag0 = a.c2x[0] + a.c2y[0] + a.c2z[0] + T(0.5) * (q[0] * q[0] + q[1] * q[1] + q[2] * q[2]);
 
   // load the orbital (pad elements zero), phases
@@ -306,7 +345,7 @@ __global__ void __launch_bounds__(kNT) k_cell(OrbArgs<T> a, typename Cplx<T>::ty
           vnext = Vc[pg + nxy];
           if (MODE == 1) pnext = psi[pg + nxy];
         }
-        const C hv = local_h<T, PER>(a, c, L.v, w, zb, diag, gx, gy, gz);
+        const C hv = local_h<T, PER>(a, c, L.v, w, zb, diag, q);
         C r;
         if (MODE == 1) {
           r = M::fma(coef, C{hv.y, -hv.x}, pv);   // psi + (-i coef) H v
@@ -415,45 +454,7 @@ __global__ void __launch_bounds__(kNT) k_cell(OrbArgs<T> a, typename Cplx<T>::ty
     __syncthreads();
     set_phases<T>(a, L.ph, qo);
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int at = warp; at < a.natom; at += nw) {
-      T cb[8], bb[3][8];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) { cb[j] = 0; bb[0][j] = bb[1][j] = bb[2][j] = 0; }
-      for (int i = a.atom_off[at] + lane; i < a.atom_off[at + 1]; i += 32) {
-        const C u = L.v[a.sph_sidx[i]];
-        const C f = L.ph[i];
-        const T re = u.x * f.x - u.y * f.y, im = u.x * f.y + u.y * f.x;
-        const T d0 = a.sph_d[3 * i], d1 = a.sph_d[3 * i + 1], d2 = a.sph_d[3 * i + 2];
-#pragma unroll
-        for (int p = 0; p < 4; ++p) {
-          const T b = a.sph_beta[i * 4 + p];
-          cb[2 * p] += b * re; cb[2 * p + 1] += b * im;
-          bb[0][2 * p] += d0 * b * re; bb[0][2 * p + 1] += d0 * b * im;
-          bb[1][2 * p] += d1 * b * re; bb[1][2 * p + 1] += d1 * b * im;
-          bb[2][2 * p] += d2 * b * re; bb[2][2 * p + 1] += d2 * b * im;
-        }
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          cb[j] += __shfl_xor_sync(0xffffffffu, cb[j], o);
-          bb[0][j] += __shfl_xor_sync(0xffffffffu, bb[0][j], o);
-          bb[1][j] += __shfl_xor_sync(0xffffffffu, bb[1][j], o);
-          bb[2][j] += __shfl_xor_sync(0xffffffffu, bb[2][j], o);
-        }
-      if (lane == 0) {
-        const double dv2 = (double)a.dV * (double)a.dV;
-        for (int d = 0; d < 3; ++d) {
-          double s = 0;
-          for (int p = 0; p < 4; ++p)
-            s += 2.0 * (double)a.atomE[at * 4 + p] *
-                 ((double)bb[d][2 * p] * cb[2 * p + 1] - (double)bb[d][2 * p + 1] * cb[2 * p]);
-          jnl[d] += s * dv2;
-        }
-      }
-    }
+    nonlocal_current<T>(a, L.v, L.ph, jnl);
   }
   const double vals[8] = {acc_norm * a.dV, acc_j[0] * a.dV, acc_j[1] * a.dV, acc_j[2] * a.dV,
                           jnl[0], jnl[1], jnl[2], acc_e * a.dV};

@@ -3,13 +3,16 @@
 //
 // A CTA owns a TX x TY column tile of one orbital and walks z = 0..nz-1.  Planes of the tile plus
 // a 4-point halo in x and y arrive in a ring of NS shared-memory slots by TMA
-// (cp.async.bulk.tensor.4d, completion on an mbarrier per slot); coordinates outside the box are
-// zero-filled by the copy engine, which is exactly the vacuum boundary of an isolated system
-// (Sec. 2.1).  Every thread owns one (x, y) column and keeps its nine z-values in registers, so
-// each plane is read from HBM once and the 16 in-plane neighbours come from shared memory at
-// compile-time offsets.  The nonlocal projectors are applied by the separate gather/scatter kernels
-// below.  Waits on the mbarriers give up after a bounded number of polls: the CTA then sets the
-// context error flag, drains its own copies (again bounded) and exits.
+// (cp.async.bulk.tensor.4d); coordinates outside the box are zero-filled by the copy engine, which
+// is exactly the vacuum boundary of an isolated system (Sec. 2.1).  The CTA is warp-specialised:
+// one producer warp issues the plane copies (completion on a "full" mbarrier per slot) and refills
+// a slot once every consumer warp has released it (an "empty" mbarrier per slot); eight consumer
+// warps each own two rows of the tile and keep the nine z-values of their columns in registers, so
+// each plane is read from HBM once, the 16 in-plane neighbours come from shared memory at
+// compile-time offsets, and no block-wide barrier is taken per plane.  The nonlocal projectors are
+// applied by the separate gather/scatter kernels below.  Every mbarrier wait gives up after a
+// bounded number of polls: the CTA then sets the context error flag, the producer drains its own
+// copies (again bounded) and all warps exit.
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
@@ -20,9 +23,11 @@ namespace tdks {
 
 namespace {
 
-constexpr int TX = 32, TY = 8, NS = 8;
+constexpr int TX = 32, TY = 16, NS = 8;
 constexpr int SX = TX + 8, SY = TY + 8;          // slot shape (complex elements)
-constexpr int NT = TX * TY;
+constexpr int RPT = 2;                           // tile rows per consumer thread
+constexpr int NCW = TX * TY / RPT / 32;          // consumer warps
+constexpr int NT = (NCW + 1) * 32;               // + one producer warp
 constexpr long long kSpinLimit = 1LL << 22;
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
@@ -31,6 +36,10 @@ __device__ __forceinline__ unsigned smem_u32(const void* p) {
 
 __device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 __device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
@@ -46,6 +55,10 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
       : "r"(smem_u32(bar)), "r"(parity)
       : "memory");
   return ok != 0;
+}
+
+__device__ __forceinline__ bool volatile_abort(int* flag) {
+  return *reinterpret_cast<volatile int*>(flag) != 0;
 }
 
 // bounded wait; returns false on timeout
@@ -89,92 +102,126 @@ __global__ void __launch_bounds__(NT) k_tile(const __grid_constant__ CUtensorMap
   extern __shared__ unsigned char smem_raw[];
   // TMA destinations 128-byte aligned (the launch requests 128 spare bytes)
   C* ring = reinterpret_cast<C*>((reinterpret_cast<size_t>(smem_raw) + 127) & ~size_t(127));
-  __shared__ __align__(8) unsigned long long bars[NS];
+  __shared__ __align__(8) unsigned long long full[NS], empty[NS];
+  __shared__ int s_abort;
 
   const int tilesx = (a.nx + TX - 1) / TX;
   const int bx = blockIdx.x % tilesx, by = blockIdx.x / tilesx;
   const int orb = blockIdx.y;
   const int x0 = bx * TX, y0 = by * TY;
-  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
-  const int x = x0 + tx, y = y0 + ty;
-  const bool inside = (x < a.nx) && (y < a.ny);
   const int nplanes = a.nz + 8;                    // z = -4 .. nz+3
-  const int own = (ty + 4) * SX + (tx + 4);
-  int issued = 0;                                  // planes issued (thread 0 only)
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
-    for (int i = 0; i < NS; ++i) mbar_init(&bars[i], 1);
+    s_abort = 0;
+    for (int i = 0; i < NS; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], NCW);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  auto issue = [&](int j) {
-    const int slot = j % NS;
-    mbar_expect_tx(&bars[slot], kSlotBytes);
-    tma_load_4d(ring + slot * SX * SY, &vmap, E * (x0 - 4), y0 - 4, j - 4, orb, &bars[slot]);
-    issued = j + 1;
-  };
-  if (threadIdx.x == 0)
-    for (int j = 0; j < NS && j < nplanes; ++j) issue(j);
 
-  bool timeout = false;
-  C w[9];
-  // window planes j = 0..7 (z = -4..3)
-  for (int j = 0; j < 8; ++j) {
-    if (!timeout && !mbar_wait(&bars[j % NS], (j / NS) & 1)) timeout = true;
-    w[j] = ring[(j % NS) * SX * SY + own];
-  }
-  bool aborted = __syncthreads_or(timeout) != 0;
-  if (threadIdx.x == 0 && !aborted) {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    for (int j = NS; j < NS + 4 && j < nplanes; ++j) issue(j);
+  if (warp == NCW) {
+    // ---------------- producer warp: one lane issues every plane copy
+    if (lane == 0) {
+      int issued = 0;
+      bool ok = true;
+      for (int j = 0; j < nplanes && ok; ++j) {
+        const int slot = j % NS;
+        if (j >= NS && !mbar_wait(&empty[slot], ((j / NS) - 1) & 1)) { ok = false; break; }
+        if (volatile_abort(&s_abort)) { ok = false; break; }
+        mbar_expect_tx(&full[slot], kSlotBytes);
+        tma_load_4d(ring + slot * SX * SY, &vmap, E * (x0 - 4), y0 - 4, j - 4, orb, &full[slot]);
+        issued = j + 1;
+      }
+      if (!ok) {
+        atomicExch(&s_abort, 1);
+        atomicExch(a.err, (int)TDKS_ETIMEOUT);
+      }
+      // the most recent copy of every slot has landed before this warp leaves, so no copy is in
+      // flight when the CTA's shared memory is released (bounded waits)
+      for (int j = (issued > NS ? issued - NS : 0); j < issued; ++j) mbar_wait(&full[j % NS], (j / NS) & 1);
+    }
+    return;
   }
 
+  // ---------------- consumer warps: thread (tx, ty) owns rows ty and ty + TY/2 of column tx
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+  const int x = x0 + tx;
+  const int yr[RPT] = {y0 + ty, y0 + ty + TY / 2};
+  const int own[RPT] = {(ty + 4) * SX + (tx + 4), (ty + TY / 2 + 4) * SX + (tx + 4)};
+  bool inside[RPT];
   const size_t plane = (size_t)a.nx * a.ny;
   const size_t obase = (size_t)orb * plane * a.nz;
-  const size_t col = (size_t)y * a.nx + x;
-  const T coef = a.coef;
-  C pnext = C{0, 0};
-  T vnext = 0;
-  if (inside) {
-    if (MODE == 1) pnext = a.psi[obase + col];
-    vnext = a.V[col];
+  size_t col[RPT];
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) {
+    inside[r] = (x < a.nx) && (yr[r] < a.ny);
+    col[r] = (size_t)yr[r] * a.nx + x;
   }
-  for (int z = 0; z < a.nz && !aborted; ++z) {
+  bool timeout = false;
+  C w[RPT][9];
+  // window planes j = 0..7 (z = -4..3); planes 0..3 are released right away
+  for (int j = 0; j < 8; ++j) {
+    if (!timeout && !mbar_wait(&full[j % NS], (j / NS) & 1)) timeout = true;
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) w[r][j] = ring[(j % NS) * SX * SY + own[r]];
+    if (j < 4) {
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[j % NS]);
+    }
+  }
+  const T coef = a.coef;
+  C pnext[RPT];
+  T vnext[RPT];
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) {
+    pnext[r] = C{0, 0};
+    vnext[r] = 0;
+    if (inside[r]) {
+      if (MODE == 1) pnext[r] = a.psi[obase + col[r]];
+      vnext[r] = a.V[col[r]];
+    }
+  }
+  for (int z = 0; z < a.nz; ++z) {
+    if (timeout || volatile_abort(&s_abort)) break;
     const int jc = z + 4;
     const int jn = z + 8;
-    if (!mbar_wait(&bars[jn % NS], (jn / NS) & 1)) timeout = true;
-    w[8] = ring[(jn % NS) * SX * SY + own];
-    const C pv = pnext;
-    const T vv = vnext;
-    if (inside && z + 1 < a.nz) {                   // prefetch the next plane's psi and V
-      if (MODE == 1) pnext = a.psi[obase + (size_t)(z + 1) * plane + col];
-      vnext = a.V[(size_t)(z + 1) * plane + col];
-    }
-    const C* s = ring + (jc % NS) * SX * SY + own;
-    C S = M::fma(a.diag + vv, w[4], C{0, 0});
+    if (!mbar_wait(&full[jn % NS], (jn / NS) & 1)) { timeout = true; break; }
+    const C* sbase = ring + (jc % NS) * SX * SY;
 #pragma unroll
-    for (int m = 1; m <= 4; ++m) {
-      S = M::fma(a.c2x[m], M::add(s[m], s[-m]), S);
-      S = M::fma(a.c2y[m], M::add(s[m * SX], s[-m * SX]), S);
-      S = M::fma(a.c2z[m], M::add(w[4 + m], w[4 - m]), S);
-    }
-    if (inside && !timeout) {
-      const size_t o = obase + (size_t)z * plane + col;
-      if (MODE == 1) a.out[o] = M::fma(coef, C{S.y, -S.x}, pv);   // psi + (-i coef) H v
-      else a.out[o] = S;
-    }
+    for (int r = 0; r < RPT; ++r) {
+      w[r][8] = ring[(jn % NS) * SX * SY + own[r]];
+      const C pv = pnext[r];
+      const T vv = vnext[r];
+      if (inside[r] && z + 1 < a.nz) {             // prefetch the next plane's psi and V
+        if (MODE == 1) pnext[r] = a.psi[obase + (size_t)(z + 1) * plane + col[r]];
+        vnext[r] = a.V[(size_t)(z + 1) * plane + col[r]];
+      }
+      const C* s = sbase + own[r];
+      C Sx = M::fma(a.diag + vv, w[r][4], C{0, 0}), Sy = C{0, 0}, Sz = C{0, 0};
 #pragma unroll
-    for (int j = 0; j < 8; ++j) w[j] = w[j + 1];
-    aborted = __syncthreads_or(timeout) != 0;       // every thread is done with plane jc
-    if (threadIdx.x == 0 && !aborted && jc + NS < nplanes) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue(jc + NS);
+      for (int m = 1; m <= 4; ++m) {
+        Sx = M::fma(a.c2x[m], M::add(s[m], s[-m]), Sx);
+        Sy = M::fma(a.c2y[m], M::add(s[m * SX], s[-m * SX]), Sy);
+        Sz = M::fma(a.c2z[m], M::add(w[r][4 + m], w[r][4 - m]), Sz);
+      }
+      const C S = M::add(M::add(Sx, Sy), Sz);
+      if (inside[r]) {
+        const size_t o = obase + (size_t)z * plane + col[r];
+        if (MODE == 1) a.out[o] = M::fma(coef, C{S.y, -S.x}, pv);   // psi + (-i coef) H v
+        else a.out[o] = S;
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) w[r][j] = w[r][j + 1];
     }
+    __syncwarp();                                  // this warp is done with plane jc
+    if (lane == 0) mbar_arrive(&empty[jc % NS]);
   }
-  if (aborted && threadIdx.x == 0) {
+  if (timeout) {
+    atomicExch(&s_abort, 1);
     atomicExch(a.err, (int)TDKS_ETIMEOUT);
-    // drain the most recent copy of every slot before shared memory is released (bounded)
-    for (int j = (issued > NS ? issued - NS : 0); j < issued; ++j) mbar_wait(&bars[j % NS], (j / NS) & 1);
   }
 }
 
@@ -277,7 +324,7 @@ template <typename T>
 cudaError_t launch_tile_stage(const TileArgs<T>& a, const void* vin, int mode, cudaStream_t s) {
   CUtensorMap map;
   if (!encode_map<T>(&map, vin, a.nx, a.ny, a.nz, a.norb_tot)) return cudaErrorInvalidValue;
-  const dim3 grid(((a.nx + TX - 1) / TX) * ((a.ny + TY - 1) / TY), a.norb_tot);
+  const dim3 grid(((a.nx + TX - 1) / TX) * ((a.ny + TY - 1) / TY), a.norb_tot);   // NT threads
   const size_t smem = (size_t)NS * SX * SY * sizeof(typename Cplx<T>::type) + 128;
   if (mode == 1) {
     cudaError_t e = cudaFuncSetAttribute(k_tile<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
