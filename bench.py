@@ -409,7 +409,17 @@ def hpsi_cluster(dev, reps=10, norb=256):
            "ms_per_hpsi": ms, "ms_per_hpsi_phase": k_ms, "bytes_per_hpsi": nbytes,
            "GBps": nbytes / (k_ms * 1e-3) / 1e9, "peak_GBps": pk["hbm_gbs"],
            "frac_of_measured_hbm": nbytes / (k_ms * 1e-3) / 1e9 / pk["hbm_gbs"],
-           "kernels": "k_gproject + k_tile<float,0> (TMA planes) + k_gscatter"}
+           "kernels": "k_gproject + tile stencil (TMA planes) + k_gscatter"}
+    variant, tune_ms = ctx.tile_variant()
+    names = ["k_tile<float> (1 point/thread, 3 CTAs/SM)", "k_tile<float> (1 point/thread, 2 CTAs/SM) + L2 prefetch",
+             "k_tile4<8> (2x2 points/thread, 8 consumer warps) + L2 prefetch"]
+    res["stencil_variant"] = {"hpsi": names[variant[0]], "horner_stage": names[variant[1]]}
+    # the tuner's timings of the stencil kernel alone (no projectors), 2 launches each at init:
+    # H v moves 16 B per orbital-point, a Horner stage 24 B (reads v and psi, writes the result)
+    res["stencil_only_GBps"] = {
+        "hpsi": {names[v]: (nbytes / (t * 1e-3) / 1e9 if t > 0 else None) for v, t in enumerate(tune_ms[0])},
+        "horner_stage": {names[v]: (1.5 * nbytes / (t * 1e-3) / 1e9 if t > 0 else None)
+                         for v, t in enumerate(tune_ms[1])}}
     ctx.close()
     del u, hu
     torch.cuda.empty_cache()

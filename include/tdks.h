@@ -237,6 +237,20 @@ tdks_status tdks_stats_read(tdks_ctx* ctx, tdks_stats* out, int reset);
 tdks_status tdks_query(const tdks_ctx* ctx, int* npts, int* nk, int* norb, int* precision,
                        int* nsphere_points);
 
+/* Stencil kernel of large isolated grids (the TMA tile kernels; no counterpart in the paper, whose
+ * stencil runs on CPU cores).  At tdks_init a context that uses them times every variant once on its
+ * own grid and orbital count (the stencil alone, as H v and as a Horner stage, on zeroed work buffers)
+ * and keeps the fastest for each of the two.
+ * Variants (FP32): 0 = one grid point per thread, registers capped for 3 CTAs per SM, no L2 prefetch;
+ * 1 = one point per thread, 2 CTAs per SM, TMA L2 prefetch of the planes 8 ahead; 2 = 2 x 2 points
+ * per thread, 8 consumer warps, prefetch 8.  FP64: 0 and 1 (one CTA per SM, without / with prefetch).
+ *   set       : -1 leaves the choice as it is; 0..2 forces that variant for both uses.
+ *   variant   : receives the variants in use [H v, Horner stage] (may be NULL).
+ *   tune_ms   : receives the 6 tuning times in ms [use][variant], -1 where not timed (may be NULL).
+ * Errors: EUNSUPPORTED if the context does not use the tile kernels or the variant needs FP32;
+ * EINVAL for set outside -1..2. */
+tdks_status tdks_tile_variant(tdks_ctx* ctx, int set, int* variant, float* tune_ms);
+
 /* Hartree + exchange potential of a density without allocating device memory.
  * For callers that cannot call cudaMalloc -- code running while a CUDA graph is captured, hosts whose
  * device memory belongs to a pool they do not control, loops that must never allocate -- this

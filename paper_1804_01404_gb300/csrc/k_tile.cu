@@ -13,6 +13,8 @@
 // applied by the separate gather/scatter kernels below.  Every mbarrier wait gives up after a
 // bounded number of polls: the CTA then sets the context error flag, the producer drains its own
 // copies (again bounded) and all warps exit.
+#include <cstring>
+
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
@@ -77,28 +79,80 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
+// L2 prefetch of one box of a tensor map (no shared memory, no completion to wait for).
+__device__ __forceinline__ void tma_prefetch_4d(const CUtensorMap* map, int c0, int c1, int c2, int c3) {
+  asm volatile("cp.async.bulk.prefetch.tensor.4d.L2.global.tile [%0, {%1, %2, %3, %4}];"
+               ::"l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+               : "memory");
+}
+
+// Producer of a plane ring: one thread issues the TMA copy of every plane z = -4 .. nz+3 of the
+// (SXx x SYx)-element window whose interior starts at (x0, y0), refilling a slot once all consumer
+// warps have arrived on its "empty" barrier.  The ring alone keeps only NSx - 5 planes in flight (the
+// consumers hold five); with pf > 0 the producer also asks L2 for the plane pf ahead of each copy,
+// and, given pmap (the Horner base psi, interior box), for the psi plane the consumers reach about
+// pf planes later, so DRAM sees enough requests in flight without more shared memory.  On a
+// timed-out wait it raises the abort flag and the error word; in every case it waits (bounded) for
+// its own most recent copies before returning, so no copy is in flight when the CTA exits.
+template <typename C, int NSx, int SXx, int SYx>
+__device__ __forceinline__ void tile_producer(const CUtensorMap* map, const CUtensorMap* pmap, int pf,
+                                              C* ring, unsigned long long* full,
+                                              unsigned long long* empty, int* abort_flag, int* err,
+                                              int x0, int y0, int orb, int nplanes) {
+  constexpr int E = sizeof(C) / 8;
+  constexpr unsigned kSlotBytes = SXx * SYx * sizeof(C);
+  const int nz = nplanes - 8;
+  int issued = 0;
+  bool ok = true;
+  for (int j = 0; j < nplanes; ++j) {
+    const int slot = j % NSx;
+    if (j >= NSx && !mbar_wait(&empty[slot], ((j / NSx) - 1) & 1)) { ok = false; break; }
+    if (volatile_abort(abort_flag)) { ok = false; break; }
+    if (pf > 0) {
+      const int zp = j + pf - 4;                   // plane of the ring source pf ahead
+      if (zp >= 0 && zp < nz) tma_prefetch_4d(map, E * (x0 - 4), y0 - 4, zp, orb);
+      const int zq = j + pf - NSx - 4;             // psi plane the consumers reach ~pf planes later
+      if (pmap && zq >= 0 && zq < nz) tma_prefetch_4d(pmap, E * x0, y0, zq, orb);
+    }
+    mbar_expect_tx(&full[slot], kSlotBytes);
+    tma_load_4d(ring + slot * SXx * SYx, map, E * (x0 - 4), y0 - 4, j - 4, orb, &full[slot]);
+    issued = j + 1;
+  }
+  if (!ok) {
+    atomicExch(abort_flag, 1);
+    atomicExch(err, (int)TDKS_ETIMEOUT);
+  }
+  for (int j = (issued > NSx ? issued - NSx : 0); j < issued; ++j) mbar_wait(&full[j % NSx], (j / NSx) & 1);
+}
+
+// Complex-by-real arithmetic of the stencil.  K is the coefficient operand: a duplicated pair for the
+// packed FP32 instructions (so one register pair per coefficient is built once, outside the loop),
+// a scalar for FP64.
 template <typename T> struct TM;
 template <> struct TM<float> {
   using C = float2;
+  using K = float2;
+  static __device__ __forceinline__ K k(float s) { return make_float2(s, s); }
   static __device__ __forceinline__ C add(C a, C b) { return __fadd2_rn(a, b); }
-  static __device__ __forceinline__ C fma(float s, C a, C acc) { return __ffma2_rn(make_float2(s, s), a, acc); }
+  static __device__ __forceinline__ C fma(K s, C a, C acc) { return __ffma2_rn(s, a, acc); }
 };
 template <> struct TM<double> {
   using C = double2;
+  using K = double;
+  static __device__ __forceinline__ K k(double s) { return s; }
   static __device__ __forceinline__ C add(C a, C b) { return C{a.x + b.x, a.y + b.y}; }
-  static __device__ __forceinline__ C fma(double s, C a, C acc) {
+  static __device__ __forceinline__ C fma(K s, C a, C acc) {
     return C{__fma_rn(s, a.x, acc.x), __fma_rn(s, a.y, acc.y)};
   }
 };
 
 // MODE 0: out = H_loc v.  MODE 1: out = psi + (-i coef) H_loc v.   (H_loc: everything but V_NL;
 // q = 0 for isolated systems.)
-template <typename T, int MODE>
-__global__ void __launch_bounds__(NT) k_tile(const __grid_constant__ CUtensorMap vmap, TileArgs<T> a) {
+template <typename T, int MODE, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_tile(const __grid_constant__ CUtensorMap vmap,
+                                             const __grid_constant__ CUtensorMap pmap, TileArgs<T> a) {
   using C = typename Cplx<T>::type;
   using M = TM<T>;
-  constexpr int E = sizeof(C) / 8;                 // 8-byte tensor elements per complex value
-  constexpr unsigned kSlotBytes = SX * SY * sizeof(C);
   extern __shared__ unsigned char smem_raw[];
   // TMA destinations 128-byte aligned (the launch requests 128 spare bytes)
   C* ring = reinterpret_cast<C*>((reinterpret_cast<size_t>(smem_raw) + 127) & ~size_t(127));
@@ -123,26 +177,9 @@ __global__ void __launch_bounds__(NT) k_tile(const __grid_constant__ CUtensorMap
   __syncthreads();
 
   if (warp == NCW) {
-    // ---------------- producer warp: one lane issues every plane copy
-    if (lane == 0) {
-      int issued = 0;
-      bool ok = true;
-      for (int j = 0; j < nplanes && ok; ++j) {
-        const int slot = j % NS;
-        if (j >= NS && !mbar_wait(&empty[slot], ((j / NS) - 1) & 1)) { ok = false; break; }
-        if (volatile_abort(&s_abort)) { ok = false; break; }
-        mbar_expect_tx(&full[slot], kSlotBytes);
-        tma_load_4d(ring + slot * SX * SY, &vmap, E * (x0 - 4), y0 - 4, j - 4, orb, &full[slot]);
-        issued = j + 1;
-      }
-      if (!ok) {
-        atomicExch(&s_abort, 1);
-        atomicExch(a.err, (int)TDKS_ETIMEOUT);
-      }
-      // the most recent copy of every slot has landed before this warp leaves, so no copy is in
-      // flight when the CTA's shared memory is released (bounded waits)
-      for (int j = (issued > NS ? issued - NS : 0); j < issued; ++j) mbar_wait(&full[j % NS], (j / NS) & 1);
-    }
+    if (lane == 0)
+      tile_producer<C, NS, SX, SY>(&vmap, MODE == 1 ? &pmap : nullptr, a.prefetch, ring, full, empty, &s_abort,
+                                   a.err, x0, y0, orb, nplanes);
     return;
   }
 
@@ -160,6 +197,10 @@ __global__ void __launch_bounds__(NT) k_tile(const __grid_constant__ CUtensorMap
     inside[r] = (x < a.nx) && (yr[r] < a.ny);
     col[r] = (size_t)yr[r] * a.nx + x;
   }
+  // c2y[m] = ry c2x[m] and c2z[m] = rz c2x[m] (the axes differ only by 1/h^2): one coefficient per
+  // neighbour distance, S = (diag + V) u + sum_m c2x[m] (X_m + ry Y_m + rz Z_m)
+  using K = typename M::K;
+  const K ry = M::k(a.ry), rz = M::k(a.rz);
   bool timeout = false;
   C w[RPT][9];
   // window planes j = 0..7 (z = -4..3); planes 0..3 are released right away
@@ -173,15 +214,21 @@ __global__ void __launch_bounds__(NT) k_tile(const __grid_constant__ CUtensorMap
     }
   }
   const T coef = a.coef;
+  // psi one plane ahead; V (L2-resident, shared by all orbitals) VD planes ahead, two when the
+  // register cap leaves room for it
+  constexpr int VD = MINB <= 2 ? 2 : 1;
   C pnext[RPT];
-  T vnext[RPT];
+  T vq[RPT][VD];
 #pragma unroll
   for (int r = 0; r < RPT; ++r) {
     pnext[r] = C{0, 0};
-    vnext[r] = 0;
+#pragma unroll
+    for (int d = 0; d < VD; ++d) vq[r][d] = 0;
     if (inside[r]) {
       if (MODE == 1) pnext[r] = a.psi[obase + col[r]];
-      vnext[r] = a.V[col[r]];
+#pragma unroll
+      for (int d = 0; d < VD; ++d)
+        if (d < a.nz) vq[r][d] = a.V[(size_t)d * plane + col[r]];
     }
   }
   for (int z = 0; z < a.nz; ++z) {
@@ -194,23 +241,22 @@ __global__ void __launch_bounds__(NT) k_tile(const __grid_constant__ CUtensorMap
     for (int r = 0; r < RPT; ++r) {
       w[r][8] = ring[(jn % NS) * SX * SY + own[r]];
       const C pv = pnext[r];
-      const T vv = vnext[r];
-      if (inside[r] && z + 1 < a.nz) {             // prefetch the next plane's psi and V
-        if (MODE == 1) pnext[r] = a.psi[obase + (size_t)(z + 1) * plane + col[r]];
-        vnext[r] = a.V[(size_t)(z + 1) * plane + col[r]];
-      }
-      const C* s = sbase + own[r];
-      C Sx = M::fma(a.diag + vv, w[r][4], C{0, 0}), Sy = C{0, 0}, Sz = C{0, 0};
+      const T vv = vq[r][0];
 #pragma unroll
-      for (int m = 1; m <= 4; ++m) {
-        Sx = M::fma(a.c2x[m], M::add(s[m], s[-m]), Sx);
-        Sy = M::fma(a.c2y[m], M::add(s[m * SX], s[-m * SX]), Sy);
-        Sz = M::fma(a.c2z[m], M::add(w[r][4 + m], w[r][4 - m]), Sz);
+      for (int d = 0; d + 1 < VD; ++d) vq[r][d] = vq[r][d + 1];
+      if (inside[r] && z + 1 < a.nz) {             // prefetch psi of plane z+1 and V of plane z+VD
+        if (MODE == 1) pnext[r] = a.psi[obase + (size_t)(z + 1) * plane + col[r]];
+        if (z + VD < a.nz) vq[r][VD - 1] = a.V[(size_t)(z + VD) * plane + col[r]];
       }
-      const C S = M::add(M::add(Sx, Sy), Sz);
+      const C* sp = sbase + own[r];
+      C S = M::fma(M::k(a.diag + vv), w[r][4], C{0, 0});
+#pragma unroll
+      for (int m = 1; m <= 4; ++m)
+        S = M::fma(M::k(a.c2x[m]), M::fma(rz, M::add(w[r][4 + m], w[r][4 - m]),
+                                          M::fma(ry, M::add(sp[m * SX], sp[-m * SX]), M::add(sp[m], sp[-m]))), S);
       if (inside[r]) {
         const size_t o = obase + (size_t)z * plane + col[r];
-        if (MODE == 1) a.out[o] = M::fma(coef, C{S.y, -S.x}, pv);   // psi + (-i coef) H v
+        if (MODE == 1) a.out[o] = M::fma(M::k(coef), C{S.y, -S.x}, pv);   // psi + (-i coef) H v
         else a.out[o] = S;
       }
 #pragma unroll
@@ -225,37 +271,257 @@ __global__ void __launch_bounds__(NT) k_tile(const __grid_constant__ CUtensorMap
   }
 }
 
-// Projections for large grids: one CTA per orbital, one warp per atom at a time.
-// ec[orb][a][p] = E_p dV sum_i beta_ip v(idx_i)   (isolated: q = 0, no phase)
-template <typename T>
-__global__ void __launch_bounds__(256) k_gproject(TileArgs<T> a, const typename Cplx<T>::type* v) {
-  using C = typename Cplx<T>::type;
-  const int orb = blockIdx.x;
-  const C* u = v + (size_t)orb * a.npts;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int at = warp; at < a.natom; at += nw) {
-    T acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (int i = a.atom_off[at] + lane; i < a.atom_off[at + 1]; i += 32) {
-      const C x = u[a.sph_idx[i]];
-      const T* b = a.sph_beta + 4 * i;
+// FP32 variant with 2 x 2 register blocking.  Shared-memory bandwidth, not HBM, limits the kernel
+// above on this GPU: it reads 17 complex values (136 B) from shared memory per output point,
+// while the shared-memory / HBM bandwidth ratio leaves room for about 90 B per point at full HBM
+// speed.  Here each consumer thread owns two adjacent columns of two adjacent rows: one 16-byte
+// load brings both columns of a row, the x-neighbours of a row pair come from four such loads,
+// and the y-neighbours are shared by the two rows, so shared-memory traffic falls to 72 B per
+// point and the instruction count roughly halves.  A warp covers 16 column pairs x 2 row pairs of
+// a 32 x (4 NCW) tile.  The z loop is unrolled by the window length 9, so the register window
+// rotates by renaming instead of moving values.
+template <int NCW>
+struct B4 {
+  static constexpr int TX = 32, TY = 4 * NCW, NS = 8;
+  static constexpr int SX = TX + 8, SY = TY + 8;
+  static constexpr int NT = (NCW + 1) * 32;
+  static constexpr int MINB = NCW == 4 ? 2 : 1;   // resident CTAs per SM the register budget allows
+};
+
+__device__ __forceinline__ float4 lds4(const float2* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ float2 lo(float4 q) { return make_float2(q.x, q.y); }
+__device__ __forceinline__ float2 hi(float4 q) { return make_float2(q.z, q.w); }
+__device__ __forceinline__ float2 sum2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 fma2s(float s, float2 a, float2 acc) {
+  return __ffma2_rn(make_float2(s, s), a, acc);
+}
+
+template <int MODE, int NCW>
+__global__ void __launch_bounds__(B4<NCW>::NT, B4<NCW>::MINB) k_tile4(const __grid_constant__ CUtensorMap vmap,
+                                                      const __grid_constant__ CUtensorMap pmap,
+                                                      TileArgs<float> a) {
+  using G = B4<NCW>;
+  constexpr int TX = G::TX, TY = G::TY, NS = G::NS, SX = G::SX, SY = G::SY, SS = SX * SY;
+  extern __shared__ unsigned char smem_raw[];
+  float2* ring = reinterpret_cast<float2*>((reinterpret_cast<size_t>(smem_raw) + 127) & ~size_t(127));
+  __shared__ __align__(8) unsigned long long full[NS], empty[NS];
+  __shared__ int s_abort;
+
+  const int tilesx = (a.nx + TX - 1) / TX;
+  const int x0 = (blockIdx.x % tilesx) * TX, y0 = (blockIdx.x / tilesx) * TY;
+  const int orb = blockIdx.y;
+  const int nz = a.nz;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    s_abort = 0;
+    for (int i = 0; i < NS; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], NCW);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (warp == NCW) {
+    if (lane == 0)
+      tile_producer<float2, NS, SX, SY>(&vmap, MODE == 1 ? &pmap : nullptr, a.prefetch, ring, full, empty,
+                                        &s_abort, a.err, x0, y0, orb, nz + 8);
+    return;
+  }
+
+  const int lx = 2 * (lane & 15);                  // tile column of the pair (even)
+  const int ly = 4 * warp + 2 * (lane >> 4);       // first of the two tile rows
+  const int x = x0 + lx, y = y0 + ly;
+  // nx is even, so both columns of a pair are inside together
+  const bool in0 = (x < a.nx) && (y < a.ny), in1 = (x < a.nx) && (y + 1 < a.ny);
+  const int o0 = (ly + 4) * SX + (lx + 4);         // slot offset of the row-0 pair (16-byte aligned)
+  const int o1 = o0 + SX;
+  const size_t plane = (size_t)a.nx * a.ny;
+  const size_t g0 = (size_t)orb * plane * nz + (size_t)y * a.nx + x;   // row-0 pair, plane z = 0
+  const size_t v0 = (size_t)y * a.nx + x;
+
+  float2 w0a[9], w0b[9], w1a[9], w1b[9];
+  bool timeout = false;
 #pragma unroll
-      for (int p = 0; p < 4; ++p) {
-        acc[2 * p] += b[p] * x.x;
-        acc[2 * p + 1] += b[p] * x.y;
+  for (int j = 0; j < 8; ++j) {
+    if (!timeout && !mbar_wait(&full[j % NS], (j / NS) & 1)) timeout = true;
+    const float4 p0 = lds4(ring + (j % NS) * SS + o0), p1 = lds4(ring + (j % NS) * SS + o1);
+    w0a[j] = lo(p0); w0b[j] = hi(p0); w1a[j] = lo(p1); w1b[j] = hi(p1);
+    if (j < 4) {
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[j % NS]);
+    }
+  }
+  // c2y[m] = ry c2x[m] and c2z[m] = rz c2x[m] for every m (the axes differ only by 1/h^2), so each
+  // neighbour distance costs one coefficient: S += c2x[m] (X_m + ry Y_m + rz Z_m)
+  const float2 c1 = make_float2(a.c2x[1], a.c2x[1]), c2 = make_float2(a.c2x[2], a.c2x[2]);
+  const float2 c3 = make_float2(a.c2x[3], a.c2x[3]), c4 = make_float2(a.c2x[4], a.c2x[4]);
+  const float2 ry = make_float2(a.ry, a.ry), rz = make_float2(a.rz, a.rz);
+  const float diag = a.diag, coef = a.coef;
+  float2 vn0 = make_float2(0.f, 0.f), vn1 = vn0;
+  float4 pn0 = make_float4(0.f, 0.f, 0.f, 0.f), pn1 = pn0;
+  if (in0) {
+    vn0 = *reinterpret_cast<const float2*>(a.V + v0);
+    if (MODE == 1) pn0 = *reinterpret_cast<const float4*>(a.psi + g0);
+  }
+  if (in1) {
+    vn1 = *reinterpret_cast<const float2*>(a.V + v0 + a.nx);
+    if (MODE == 1) pn1 = *reinterpret_cast<const float4*>(a.psi + g0 + a.nx);
+  }
+
+  for (int zb = 0; zb < nz && !timeout; zb += 9) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const int z = zb + k;
+      if (z >= nz) break;
+      if (volatile_abort(&s_abort)) { timeout = true; break; }
+      const int jc = z + 4, jn = z + 8;
+      // register slots of planes z .. z+8 (z multiple-of-9 aligned at zb)
+      const int rc = (k + 4) % 9, rn = (k + 8) % 9;
+      if (!mbar_wait(&full[jn % NS], (jn / NS) & 1)) { timeout = true; break; }
+      {
+        const float2* sn = ring + (jn % NS) * SS;
+        const float4 p0 = lds4(sn + o0), p1 = lds4(sn + o1);
+        w0a[rn] = lo(p0); w0b[rn] = hi(p0); w1a[rn] = lo(p1); w1b[rn] = hi(p1);
+      }
+      const float2* sc = ring + (jc % NS) * SS;
+      const float2 V0 = vn0, V1 = vn1;
+      const float4 P0 = pn0, P1 = pn1;
+      if (z + 1 < nz) {                            // prefetch the next plane's V and psi
+        const size_t dz = (size_t)(z + 1) * plane;
+        if (in0) {
+          vn0 = *reinterpret_cast<const float2*>(a.V + v0 + dz);
+          if (MODE == 1) pn0 = *reinterpret_cast<const float4*>(a.psi + g0 + dz);
+        }
+        if (in1) {
+          vn1 = *reinterpret_cast<const float2*>(a.V + v0 + a.nx + dz);
+          if (MODE == 1) pn1 = *reinterpret_cast<const float4*>(a.psi + g0 + a.nx + dz);
+        }
+      }
+      // The three axes are summed in turn (z from the register window, then y, then x from shared
+      // memory), with a compiler fence between the phases so that at most eight 16-byte loads are in
+      // registers next to the window: S = (diag + V) u + rz Tz + ry Ty + Tx, T_a = sum_m c_m (pair sums).
+#define TDKS_AXIS(T, l1, r1, l2, r2, l3, r3, l4, r4)                                           \
+  T = __ffma2_rn(c4, sum2(l4, r4), __ffma2_rn(c3, sum2(l3, r3),                                  \
+      __ffma2_rn(c2, sum2(l2, r2), __ffma2_rn(c1, sum2(l1, r1), T))));
+#define TDKS_ZPART(S, dv, W)                                                                     \
+  {                                                                                              \
+    float2 Tz = make_float2(0.f, 0.f);                                                           \
+    TDKS_AXIS(Tz, W[(k + 3) % 9], W[(k + 5) % 9], W[(k + 2) % 9], W[(k + 6) % 9],                \
+              W[(k + 1) % 9], W[(k + 7) % 9], W[k % 9], W[(k + 8) % 9])                          \
+    S = __ffma2_rn(rz, Tz, fma2s(dv, W[rc], make_float2(0.f, 0.f)));                             \
+  }
+      float2 S0a, S0b, S1a, S1b;
+      TDKS_ZPART(S0a, diag + V0.x, w0a)
+      TDKS_ZPART(S0b, diag + V0.y, w0b)
+      TDKS_ZPART(S1a, diag + V1.x, w1a)
+      TDKS_ZPART(S1b, diag + V1.y, w1b)
+      asm volatile("" ::: "memory");
+      {
+        // y-neighbour pairs: rows ly-1 .. ly-4 and ly+2 .. ly+5
+        const float4 Ym1 = lds4(sc + o0 - SX), Ym2 = lds4(sc + o0 - 2 * SX), Ym3 = lds4(sc + o0 - 3 * SX), Ym4 = lds4(sc + o0 - 4 * SX);
+        const float4 Yp1 = lds4(sc + o1 + SX), Yp2 = lds4(sc + o1 + 2 * SX), Yp3 = lds4(sc + o1 + 3 * SX), Yp4 = lds4(sc + o1 + 4 * SX);
+        float2 T0a = make_float2(0.f, 0.f), T0b = T0a, T1a = T0a, T1b = T0a;
+        TDKS_AXIS(T0a, lo(Ym1), w1a[rc], lo(Ym2), lo(Yp1), lo(Ym3), lo(Yp2), lo(Ym4), lo(Yp3))
+        TDKS_AXIS(T0b, hi(Ym1), w1b[rc], hi(Ym2), hi(Yp1), hi(Ym3), hi(Yp2), hi(Ym4), hi(Yp3))
+        TDKS_AXIS(T1a, w0a[rc], lo(Yp1), lo(Ym1), lo(Yp2), lo(Ym2), lo(Yp3), lo(Ym3), lo(Yp4))
+        TDKS_AXIS(T1b, w0b[rc], hi(Yp1), hi(Ym1), hi(Yp2), hi(Ym2), hi(Yp3), hi(Ym3), hi(Yp4))
+        S0a = __ffma2_rn(ry, T0a, S0a);
+        S0b = __ffma2_rn(ry, T0b, S0b);
+        S1a = __ffma2_rn(ry, T1a, S1a);
+        S1b = __ffma2_rn(ry, T1b, S1b);
+      }
+      asm volatile("" ::: "memory");
+      {
+        // x-neighbour pairs of row 0 (offsets -4/-3, -2/-1, +2/+3, +4/+5)
+        const float4 Am2 = lds4(sc + o0 - 4), Am1 = lds4(sc + o0 - 2), Ap1 = lds4(sc + o0 + 2), Ap2 = lds4(sc + o0 + 4);
+        TDKS_AXIS(S0a, hi(Am1), w0b[rc], lo(Am1), lo(Ap1), hi(Am2), hi(Ap1), lo(Am2), lo(Ap2))
+        TDKS_AXIS(S0b, w0a[rc], lo(Ap1), hi(Am1), hi(Ap1), lo(Am1), lo(Ap2), hi(Am2), hi(Ap2))
+      }
+      {
+        // row 1
+        const float4 Am2 = lds4(sc + o1 - 4), Am1 = lds4(sc + o1 - 2), Ap1 = lds4(sc + o1 + 2), Ap2 = lds4(sc + o1 + 4);
+        TDKS_AXIS(S1a, hi(Am1), w1b[rc], lo(Am1), lo(Ap1), hi(Am2), hi(Ap1), lo(Am2), lo(Ap2))
+        TDKS_AXIS(S1b, w1a[rc], lo(Ap1), hi(Am1), hi(Ap1), lo(Am1), lo(Ap2), hi(Am2), hi(Ap2))
+      }
+      __syncwarp();                                // this warp is done with plane jc
+      if (lane == 0) mbar_arrive(&empty[jc % NS]);
+#undef TDKS_ZPART
+#undef TDKS_AXIS
+      const size_t o = g0 + (size_t)z * plane;
+      if (MODE == 1) {
+        // psi + (-i coef) S = psi + coef (S.y, -S.x)
+        const float2 mc = make_float2(coef, -coef);
+        const float2 r0a = __ffma2_rn(mc, make_float2(S0a.y, S0a.x), lo(P0));
+        const float2 r0b = __ffma2_rn(mc, make_float2(S0b.y, S0b.x), hi(P0));
+        const float2 r1a = __ffma2_rn(mc, make_float2(S1a.y, S1a.x), lo(P1));
+        const float2 r1b = __ffma2_rn(mc, make_float2(S1b.y, S1b.x), hi(P1));
+        if (in0) *reinterpret_cast<float4*>(a.out + o) = make_float4(r0a.x, r0a.y, r0b.x, r0b.y);
+        if (in1) *reinterpret_cast<float4*>(a.out + o + a.nx) = make_float4(r1a.x, r1a.y, r1b.x, r1b.y);
+      } else {
+        if (in0) *reinterpret_cast<float4*>(a.out + o) = make_float4(S0a.x, S0a.y, S0b.x, S0b.y);
+        if (in1) *reinterpret_cast<float4*>(a.out + o + a.nx) = make_float4(S1a.x, S1a.y, S1b.x, S1b.y);
       }
     }
+  }
+  if (timeout) {
+    atomicExch(&s_abort, 1);
+    atomicExch(a.err, (int)TDKS_ETIMEOUT);
+  }
+}
+
+// Projections for large grids.  A CTA takes one atom and kOB orbitals, one warp per kOB / 4 of them;
+// the lanes stride over the atom's sphere points and each loaded index and beta row serves every
+// orbital of the warp, so the index -> value load chain is paid once per point, not once per orbital.
+// ec[orb][a][p] = E_p dV sum_i beta_ip v(idx_i)   (isolated: q = 0, no phase)
+constexpr int kOB = 16;
+template <typename T>
+__global__ void __launch_bounds__(128) k_gproject(TileArgs<T> a, const typename Cplx<T>::type* v) {
+  using C = typename Cplx<T>::type;
+  constexpr int OW = kOB / 4;                      // orbitals per warp
+  const int at = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int ob = blockIdx.y * kOB + warp * OW;
+  const int i0 = a.atom_off[at], i1 = a.atom_off[at + 1];
+  T acc[OW][8];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
+  for (int o = 0; o < OW; ++o)
 #pragma unroll
-      for (int j = 0; j < 8; ++j) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], o);
-    if (lane < 4) {
+    for (int j = 0; j < 8; ++j) acc[o][j] = 0;
+  for (int i = i0 + lane; i < i1; i += 32) {
+    const int idx = a.sph_idx[i];
+    T b[4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) b[p] = a.sph_beta[4 * i + p];
+    C x[OW];
+#pragma unroll
+    for (int o = 0; o < OW; ++o) x[o] = ob + o < a.norb_tot ? v[(size_t)(ob + o) * a.npts + idx] : C{0, 0};
+#pragma unroll
+    for (int o = 0; o < OW; ++o)
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        acc[o][2 * p] += b[p] * x[o].x;
+        acc[o][2 * p + 1] += b[p] * x[o].y;
+      }
+  }
+#pragma unroll
+  for (int o = 0; o < OW; ++o) {
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[o][j] += __shfl_xor_sync(0xffffffffu, acc[o][j], s);
+    if (lane < 4 && ob + o < a.norb_tot) {
       const T sc = a.atomE[at * 4 + lane] * a.dV;
-      a.ec[((size_t)orb * a.natom + at) * 4 + lane] = C{acc[2 * lane] * sc, acc[2 * lane + 1] * sc};
+      T re = acc[o][0], im = acc[o][1];           // select projector `lane` without dynamic indexing
+#pragma unroll
+      for (int p = 1; p < 4; ++p)
+        if (lane == p) { re = acc[o][2 * p]; im = acc[o][2 * p + 1]; }
+      a.ec[((size_t)(ob + o) * a.natom + at) * 4 + lane] = C{re * sc, im * sc};
     }
   }
 }
 
-// out[p] += f * V_NL v at sphere points, f = 1 (H) or -i coef (Horner stage).
+// out[p] += f * V_NL v at sphere points, f = 1 (H) or -i coef (Horner stage); one thread per
+// (sphere point, orbital).
 template <typename T, int MODE>
 __global__ void __launch_bounds__(256) k_gscatter(TileArgs<T> a, typename Cplx<T>::type* out) {
   using C = typename Cplx<T>::type;
@@ -297,20 +563,52 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
 }
 
 template <typename T>
-bool encode_map(CUtensorMap* map, const void* base, int nx, int ny, int nz, int norb_tot) {
+bool encode_map(CUtensorMap* map, const void* base, int nx, int ny, int nz, int norb_tot, int bx, int by) {
   auto enc = get_encode();
   if (!enc) return false;
   constexpr int E = sizeof(typename Cplx<T>::type) / 8;
   const cuuint64_t dims[4] = {(cuuint64_t)E * nx, (cuuint64_t)ny, (cuuint64_t)nz, (cuuint64_t)norb_tot};
   const cuuint64_t strides[3] = {(cuuint64_t)8 * E * nx, (cuuint64_t)8 * E * nx * ny,
                                  (cuuint64_t)8 * E * nx * ny * nz};
-  const cuuint32_t box[4] = {(cuuint32_t)(E * SX), (cuuint32_t)SY, 1, 1};
+  const cuuint32_t box[4] = {(cuuint32_t)(E * bx), (cuuint32_t)by, 1, 1};
   const cuuint32_t estr[4] = {1, 1, 1, 1};
   CUresult r = enc(map, E == 1 ? CU_TENSOR_MAP_DATA_TYPE_INT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4,
                    const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
+}
+
+template <int MODE, int NCW>
+cudaError_t launch_tile4(const TileArgs<float>& a, const CUtensorMap& pmap, const void* vin, cudaStream_t s) {
+  using G = B4<NCW>;
+  CUtensorMap map;
+  if (!encode_map<float>(&map, vin, a.nx, a.ny, a.nz, a.norb_tot, G::SX, G::SY)) return cudaErrorInvalidValue;
+  const dim3 grid(((a.nx + G::TX - 1) / G::TX) * ((a.ny + G::TY - 1) / G::TY), a.norb_tot);
+  const size_t smem = (size_t)G::NS * G::SX * G::SY * sizeof(float2) + 128;
+  cudaError_t e = cudaFuncSetAttribute(k_tile4<MODE, NCW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_tile4<MODE, NCW><<<grid, G::NT, smem, s>>>(map, pmap, a);
+  return cudaGetLastError();
+}
+
+template <typename T, int MINB>
+cudaError_t launch_tile_plain(const TileArgs<T>& a, const CUtensorMap& pmap, const void* vin, int mode,
+                              cudaStream_t s) {
+  CUtensorMap map;
+  if (!encode_map<T>(&map, vin, a.nx, a.ny, a.nz, a.norb_tot, SX, SY)) return cudaErrorInvalidValue;
+  const dim3 grid(((a.nx + TX - 1) / TX) * ((a.ny + TY - 1) / TY), a.norb_tot);   // NT threads
+  const size_t smem = (size_t)NS * SX * SY * sizeof(typename Cplx<T>::type) + 128;
+  if (mode == 1) {
+    cudaError_t e = cudaFuncSetAttribute(k_tile<T, 1, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_tile<T, 1, MINB><<<grid, NT, smem, s>>>(map, pmap, a);
+  } else {
+    cudaError_t e = cudaFuncSetAttribute(k_tile<T, 0, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_tile<T, 0, MINB><<<grid, NT, smem, s>>>(map, pmap, a);
+  }
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -320,28 +618,35 @@ bool tile_supported(int nx, int ny, int nz, int elem_bytes) {
   return ((size_t)nx * elem_bytes) % 16 == 0 && nz >= 1 && get_encode() != nullptr;
 }
 
+// Variant table of the tile stencil (kernel, resident CTAs per SM the registers are capped for, L2
+// prefetch distance in planes).  FP32: 0 = k_tile, 3 CTAs, no prefetch; 1 = k_tile, 2 CTAs, 8;
+// 2 = k_tile4<8> (2 x 2 points per thread), 8.  FP64 (one CTA per SM, as the ring fills shared
+// memory): 0 = no prefetch, 1 = prefetch 8.
 template <typename T>
-cudaError_t launch_tile_stage(const TileArgs<T>& a, const void* vin, int mode, cudaStream_t s) {
-  CUtensorMap map;
-  if (!encode_map<T>(&map, vin, a.nx, a.ny, a.nz, a.norb_tot)) return cudaErrorInvalidValue;
-  const dim3 grid(((a.nx + TX - 1) / TX) * ((a.ny + TY - 1) / TY), a.norb_tot);   // NT threads
-  const size_t smem = (size_t)NS * SX * SY * sizeof(typename Cplx<T>::type) + 128;
-  if (mode == 1) {
-    cudaError_t e = cudaFuncSetAttribute(k_tile<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_tile<T, 1><<<grid, NT, smem, s>>>(map, a);
-  } else {
-    cudaError_t e = cudaFuncSetAttribute(k_tile<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_tile<T, 0><<<grid, NT, smem, s>>>(map, a);
+cudaError_t launch_tile_stage(const TileArgs<T>& a0, const void* vin, int mode, cudaStream_t s) {
+  TileArgs<T> a = a0;
+  a.prefetch = a.variant == 0 ? 0 : 8;
+  // psi map (interior box) for the L2 prefetch of the Horner base; unused in mode 0
+  CUtensorMap pmap;
+  std::memset(&pmap, 0, sizeof(pmap));
+  if (mode == 1 && a.prefetch > 0) {
+    const int by = sizeof(T) == 4 && a.variant == 2 ? B4<8>::TY : TY;
+    if (!encode_map<T>(&pmap, a.psi, a.nx, a.ny, a.nz, a.norb_tot, TX, by)) return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
+  if constexpr (sizeof(T) == 4) {
+    if (a.variant == 2) return mode == 1 ? launch_tile4<1, 8>(a, pmap, vin, s) : launch_tile4<0, 8>(a, pmap, vin, s);
+    if (a.variant == 1) return launch_tile_plain<T, 2>(a, pmap, vin, mode, s);
+    return launch_tile_plain<T, 3>(a, pmap, vin, mode, s);
+  } else {
+    return launch_tile_plain<T, 1>(a, pmap, vin, mode, s);
+  }
 }
 
 template <typename T>
 cudaError_t launch_tile_project(const TileArgs<T>& a, const typename Cplx<T>::type* v, cudaStream_t s) {
   if (a.natom == 0) return cudaSuccess;
-  k_gproject<T><<<a.norb_tot, 256, 0, s>>>(a, v);
+  const dim3 grid(a.natom, (a.norb_tot + kOB - 1) / kOB);
+  k_gproject<T><<<grid, 128, 0, s>>>(a, v);
   return cudaGetLastError();
 }
 

@@ -68,6 +68,8 @@ struct tdks_ctx {
   void* d_scratch = nullptr;     // [norb_tot][npts] complex, only for cells whose two copies exceed smem
   // large isolated grids (tile kernels): two Horner buffers and the projection coefficients
   bool tiled = false;
+  int tile_variant[2] = {0, 0};  // stencil variant of the tiled path for H v / Horner stages
+  float tile_ms[2][kTileVariants] = {{-1.f, -1.f, -1.f}, {-1.f, -1.f, -1.f}};
   void *d_bufA = nullptr, *d_bufB = nullptr, *d_ec = nullptr;
   int* d_err = nullptr;
   bool have_rho0 = false, have_potential = false;
@@ -254,6 +256,9 @@ TileArgs<T> make_tile_args(const tdks_ctx* c, const T* V) {
     a.c2z[m] = (T)(-0.5 * kFD2[m] / (c->grid.h[2] * c->grid.h[2]));
   }
   a.diag = a.c2x[0] + a.c2y[0] + a.c2z[0];
+  a.ry = (T)((c->grid.h[0] * c->grid.h[0]) / (c->grid.h[1] * c->grid.h[1]));
+  a.rz = (T)((c->grid.h[0] * c->grid.h[0]) / (c->grid.h[2] * c->grid.h[2]));
+  a.variant = c->tile_variant[0];
   a.err = c->d_err;
   a.natom = c->natom; a.nsp = c->nsp;
   a.atom_off = c->d_atom_off; a.sph_idx = c->d_sph_idx;
@@ -287,6 +292,7 @@ tdks_status tiled_kernel(tdks_ctx* c, int mode, const void* in, void* out, doubl
   C* dst[4] = {A, B, A, fin};
   const C* v = u;
   a.psi = u;
+  a.variant = c->tile_variant[1];
   for (int st = 0; st < 4; ++st) {
     a.coef = (T)(dt / (4 - st));
     a.out = dst[st];
@@ -410,6 +416,62 @@ tdks_status check_ctx(const tdks_ctx* c) {
 }
 
 }  // namespace
+
+// Stencil autotuner of the tiled path: every variant runs the stencil alone (H v, and a Horner stage
+// with psi = v) on the zeroed work buffers, one untimed and two timed launches each, and the fastest
+// per mode is kept.
+tdks_status tune_tile(tdks_ctx* c) {
+  c->tile_variant[0] = c->tile_variant[1] = 0;
+  if (!c->tiled) return TDKS_OK;
+  const int nvar = is_f32(c) ? kTileVariants : 2;   // FP64 has variants 0 and 1
+  const size_t n = (size_t)c->npts * c->nk * c->norb;
+  const size_t csz = is_f32(c) ? sizeof(float2) : sizeof(double2);
+  TDKS_CUDA(cudaMemsetAsync(c->d_bufA, 0, n * csz, c->stream));
+  TDKS_CUDA(cudaMemsetAsync(c->d_v32, 0, (size_t)c->npts * sizeof(float), c->stream));
+  TDKS_CUDA(cudaMemsetAsync(c->d_v64, 0, (size_t)c->npts * sizeof(double), c->stream));
+  cudaEvent_t e0, e1;
+  TDKS_CUDA(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return fail(TDKS_ECUDA, "event"); }
+  cudaError_t err = cudaSuccess;
+  for (int mode = 0; mode < 2 && err == cudaSuccess; ++mode) {
+    float best = 0.f;
+    for (int v = 0; v < nvar && err == cudaSuccess; ++v) {
+      auto run = [&]() -> cudaError_t {
+        if (is_f32(c)) {
+          TileArgs<float> a = make_tile_args<float>(c, c->d_v32);
+          a.variant = v;
+          a.psi = static_cast<const float2*>(c->d_bufA);
+          a.out = static_cast<float2*>(c->d_bufB);
+          a.coef = 0.01f;
+          return launch_tile_stage<float>(a, c->d_bufA, mode, c->stream);
+        }
+        TileArgs<double> a = make_tile_args<double>(c, c->d_v64);
+        a.variant = v;
+        a.psi = static_cast<const double2*>(c->d_bufA);
+        a.out = static_cast<double2*>(c->d_bufB);
+        a.coef = 0.01;
+        return launch_tile_stage<double>(a, c->d_bufA, mode, c->stream);
+      };
+      err = run();
+      if (err == cudaSuccess) err = cudaEventRecord(e0, c->stream);
+      for (int r = 0; r < 2 && err == cudaSuccess; ++r) err = run();
+      if (err == cudaSuccess) err = cudaEventRecord(e1, c->stream);
+      if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+      if (err != cudaSuccess) break;
+      c->tile_ms[mode][v] = 0.5f * ms;
+      if (v == 0 || c->tile_ms[mode][v] < best) { best = c->tile_ms[mode][v]; c->tile_variant[mode] = v; }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err != cudaSuccess) return fail(TDKS_ECUDA, std::string("tile tuning: ") + cudaGetErrorString(err));
+  int h_err = 0;
+  TDKS_CUDA(cudaMemcpy(&h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (h_err != 0) return fail((tdks_status)h_err, "tile tuning: a stencil kernel gave up waiting for its copies");
+  return TDKS_OK;
+}
 
 extern "C" {
 
@@ -593,6 +655,7 @@ tdks_status tdks_init(const tdks_grid* grid, const tdks_cell* cell, const tdks_a
     if (launch_real_part(c->d_fft, c->d_ghat, nfft, 1.0, c->stream) != cudaSuccess)
       return bail(fail(TDKS_ECUDA, "ghat"));
   }
+  if ((s = tune_tile(c)) != TDKS_OK) return bail(s);
   if (cudaStreamSynchronize(c->stream) != cudaSuccess)
     return bail(fail(TDKS_ECUDA, std::string("init: ") + cudaGetErrorString(cudaGetLastError())));
   *out = c;
@@ -1093,6 +1156,19 @@ tdks_status tdks_stats_read(tdks_ctx* c, tdks_stats* out, int reset) {
     c->launches = 0;
     for (int p = 0; p < TDKS_NPHASE; ++p) { c->calls[p] = 0; c->ms[p] = 0.0; }
   }
+  return TDKS_OK;
+}
+
+tdks_status tdks_tile_variant(tdks_ctx* c, int set, int* variant, float* tune_ms) {
+  TDKS_TRY(check_ctx(c));
+  if (set < -1 || set >= kTileVariants) return fail(TDKS_EINVAL, "tile variant outside -1..2");
+  if (!c->tiled) return fail(TDKS_EUNSUPPORTED, "this context does not use the tile kernels");
+  if (set > 1 && !is_f32(c)) return fail(TDKS_EUNSUPPORTED, "tile variant 2 is FP32 only");
+  if (set >= 0) c->tile_variant[0] = c->tile_variant[1] = set;
+  if (variant) { variant[0] = c->tile_variant[0]; variant[1] = c->tile_variant[1]; }
+  if (tune_ms)
+    for (int m = 0; m < 2; ++m)
+      for (int v = 0; v < kTileVariants; ++v) tune_ms[m * kTileVariants + v] = c->tile_ms[m][v];
   return TDKS_OK;
 }
 

@@ -130,8 +130,11 @@ struct TileArgs {
   const T* V;               // [npts]
   T c2x[5], c2y[5], c2z[5]; // -1/2 FD2[m] / h^2
   T diag;                   // c2x[0] + c2y[0] + c2z[0]
+  T ry, rz;                 // hx^2 / hy^2 and hx^2 / hz^2 (c2y = ry c2x, c2z = rz c2x)
   T coef;                   // dt / m (mode 1)
   int* err;                 // device error word (TDKS_ETIMEOUT on a timed-out wait)
+  int variant;              // stencil variant (kernel + L2 prefetch), see launch_tile_stage
+  int prefetch;             // L2 prefetch distance in planes (set by launch_tile_stage)
   // projectors (q = 0)
   int natom, nsp;
   const int* atom_off;
@@ -146,6 +149,7 @@ struct TileArgs {
   const int* ent_atom;
 };
 bool tile_supported(int nx, int ny, int nz, int elem_bytes);
+constexpr int kTileVariants = 3;
 // local part of one stage: mode 0 out = H_loc vin, mode 1 out = psi + (-i coef) H_loc vin
 template <typename T>
 cudaError_t launch_tile_stage(const TileArgs<T>& a, const void* vin, int mode, cudaStream_t s);

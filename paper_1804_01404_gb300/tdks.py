@@ -112,6 +112,7 @@ def load_library(path: str = LIB_PATH):
         "tdks_nn_gradient": [vp, vp, vp, C.POINTER(C.c_double), C.POINTER(C.c_float)],
         "tdks_stats_read": [vp, C.POINTER(Stats), i],
         "tdks_query": [vp, C.POINTER(i), C.POINTER(i), C.POINTER(i), C.POINTER(i), C.POINTER(i)],
+        "tdks_tile_variant": [vp, i, C.POINTER(i), C.POINTER(C.c_float)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -291,6 +292,14 @@ class Context:
 
     def check(self):
         _check(self.lib.tdks_check(self.ctx))
+
+    def tile_variant(self, set=-1):
+        """Stencil variants of the tiled path (tdks_tile_variant): returns ([H v, Horner] variants,
+        tuning ms [[H v x 3], [Horner x 3]])."""
+        v = (C.c_int * 2)()
+        ms = (C.c_float * 6)()
+        _check(self.lib.tdks_tile_variant(self.ctx, int(set), v, ms))
+        return [v[0], v[1]], [[float(x) for x in ms[:3]], [float(x) for x in ms[3:]]]
 
     def query(self):
         v = [C.c_int() for _ in range(5)]

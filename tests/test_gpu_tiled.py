@@ -102,3 +102,40 @@ def test_tiled_observables():
     assert abs(o["norm_max"] - nrm.max()) < 1e-12 and abs(o["norm_min"] - nrm.min()) < 1e-12
     eb = O.band_energy(S, O.projector_tables(S), O.local_potential(S), psi, np.zeros(3))
     assert abs(o["e_band"] - eb) < 1e-11 * abs(eb)
+
+
+@pytest.mark.parametrize("precision,variant", [("f32", 0), ("f32", 1), ("f32", 2), ("f64", 0), ("f64", 1)])
+def test_tiled_variants_hpsi_and_taylor(precision, variant):
+    """Every stencil variant (one point per thread for 3 CTAs per SM, or for 2 with L2 prefetch; FP32
+    2 x 2 blocks) against the oracle, on the anisotropic ragged grid (h differs per axis, so
+    the per-axis coefficient ratios of the blocked variants are exercised)."""
+    psi = W.initial_orbitals(S, 6)
+    ctx = _ctx(S, precision)
+    v, ms = ctx.tile_variant(variant)
+    nvar = 3 if precision == "f32" else 2
+    assert v == [variant, variant] and all(m > 0 for row in ms for m in row[:nvar])
+    tol = 2e-5 if precision == "f32" else 1e-12
+    ctx.update_potential(_dev(psi, precision))
+    ud = _dev(psi, precision)
+    hu = torch.empty_like(ud)
+    ctx.hpsi(ud, hu)
+    tabs = O.projector_tables(S)
+    V = O.local_potential(S) + O.hxc(S, O.density(S, psi))
+    for b in range(psi.shape[0]):
+        ref = O.hpsi(S, tabs, V, np.zeros(3), psi[b])
+        assert _rel(hu.cpu().numpy()[b].astype(np.complex128), ref) < tol
+    ctx.taylor_step(ud, 0.02)
+    ctx.check()
+    for b in range(psi.shape[0]):
+        ref = O.taylor4(S, tabs, V, np.zeros(3), psi[b], 0.02)
+        assert _rel(ud.cpu().numpy()[b].astype(np.complex128), ref) < tol
+
+
+def test_tile_variant_rules():
+    from paper_1804_01404_gb300.tdks import TdksError
+    c64 = _ctx(S, "f64")
+    assert all(v in (0, 1) for v in c64.tile_variant()[0])
+    with pytest.raises(TdksError):
+        c64.tile_variant(2)
+    with pytest.raises(TdksError):
+        _ctx(S, "f32").tile_variant(3)
