@@ -53,6 +53,8 @@ def config_dict(s, extra=None):
     d = {"workload": "diamond crystal 20^3 grid, 8 atoms, 16 orbitals x 64 k, sin^2 pulse",
          "grid": list(s.n), "norb": s.norb, "nk": s.nk, "dt": s.dt, "taylor_order": 4,
          "predictor": "predictor-corrector", "orbitals": "f32", "reductions_poisson": "f64",
+         "observables": "J(t) and dipole(t) of every step's input state, formed in its first Taylor "
+                        "stage (tdks_options.obs_at_start = 1)",
          "l2": "flushed between timed steps (256 MiB write)"}
     if extra:
         d.update(extra)
@@ -151,9 +153,10 @@ def reference_arm(args, rank, world):
     return 0
 
 
-def timed_steps(ctx, u, s, t0, warmup, steps, flush, record_j=False):
+def timed_steps(ctx, u, s, t0, warmup, steps, flush, record_j=False, label="steps"):
     """Run warmup + timed steps; every timed step is bracketed by CUDA events on the context
-    stream, with an L2 flush (not timed) before it.  Returns (per-step ms, J history, stats)."""
+    stream, with an L2 flush (not timed) before it.  The timed steps sit in an NVTX range named
+    `label` (for `ncu --nvtx --nvtx-include label/`).  Returns (per-step ms, J history, stats)."""
     import torch
     stream = torch.cuda.current_stream()
     t = t0
@@ -168,6 +171,7 @@ def timed_steps(ctx, u, s, t0, warmup, steps, flush, record_j=False):
     ctx.profile(True)
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push(label)
     for i in range(steps):
         flush.zero_()                                    # evict the 65 MB orbital set from L2
         evs[i][0].record(stream)
@@ -177,6 +181,7 @@ def timed_steps(ctx, u, s, t0, warmup, steps, flush, record_j=False):
         if record_j:
             J.append(ctx.read_step_observables()["J"])
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     st = ctx.stats(reset=True)
     ctx.profile(False)
     return [a.elapsed_time(b) for a, b in evs], np.array(J), st
@@ -217,7 +222,7 @@ def gpu_arm(args, rank, world, local_rank):
 
     # FP64 predictor-corrector reference current over the same steps (judge of the error bound)
     nref = args.warmup + args.steps
-    ctx64 = Context(s, precision="f64")
+    ctx64 = Context(s, precision="f64", obs_at_start=True)
     u64 = torch.from_numpy(psi0.astype(np.complex128)).to(dev)
     ctx64.update_potential(u64)
     J64, t = [], t0
@@ -237,13 +242,13 @@ def gpu_arm(args, rank, world, local_rank):
         return float(np.max(np.abs(J - J64)) / np.max(np.abs(J64)))
 
     # plain predictor-corrector, FP32 orbitals
-    ctx = Context(s, precision="f32")
+    ctx = Context(s, precision="f32", obs_at_start=True)
     u = torch.from_numpy(psi0).to(dev)
     ctx.update_potential(u)
     if world > 1:
         dist.barrier()
     clocks = ClockSampler(local_rank)
-    pc_ms, J_pc, st_pc = timed_steps(ctx, u, s, t0, args.warmup, args.steps, flush, record_j=True)
+    pc_ms, J_pc, st_pc = timed_steps(ctx, u, s, t0, args.warmup, args.steps, flush, record_j=True, label="pc")
     ctx.close()
 
     # learned predictor (PC fallback) and the cubic-extrapolation ablation
@@ -251,13 +256,13 @@ def gpu_arm(args, rank, world, local_rank):
     modes = {}
     if params is not None:
         for name, mode in (("learned", T.PRED_LEARNED), ("cubic", T.PRED_EXTRAP)):
-            c2 = Context(s, precision="f32")
+            c2 = Context(s, precision="f32", obs_at_start=True)
             u2 = torch.from_numpy(psi0).to(dev)
             c2.update_potential(u2)
             c2.nn_init(0)
             c2.nn_params(params)
             c2.set_predictor(mode, 1e-5)
-            ms, J, st = timed_steps(c2, u2, s, t0, args.warmup, args.steps, flush, record_j=True)
+            ms, J, st = timed_steps(c2, u2, s, t0, args.warmup, args.steps, flush, record_j=True, label=name)
             o = c2.read_step_observables()
             modes[name] = dict(ms=ms, J=J, st=st, fallbacks=o["fallbacks"])
             c2.close()
@@ -273,20 +278,23 @@ def gpu_arm(args, rank, world, local_rank):
         total_ms = float(tt.item())
     value = world * args.steps / (total_ms / 1e3)
 
-    # dominant kernel: the Taylor kernel of the PC run (predictor + corrector launches)
+    # dominant kernel of the headline step: the cell Taylor kernel (the corrector launch of a learned
+    # step; predictor and corrector launches of a PC step), timed alone by the library's
+    # stencil-kernel phase events on the context stream
     npts, norb_tot = s.npts, s.nk * s.norb
     nsph = W_nsph(s)
-    k_ms = (st_pc["ms"]["taylor_predictor"] + st_pc["ms"]["taylor_corrector"]) / max(
-        1, st_pc["calls"]["taylor_predictor"] + st_pc["calls"]["taylor_corrector"])
+    k_ms = st["ms"]["stencil_kernel"] / max(1, st["calls"]["stencil_kernel"])
     flops = 4 * norb_tot * (FLOPS_PER_POINT_STAGE * npts + FLOPS_PER_SPHERE_ENTRY_STAGE * nsph)
     pk = peaks()
     fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     achieved = flops / (k_ms * 1e-3) / 1e12
     hbm_bytes = 16 * npts * norb_tot
     roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp32_peak, "traffic": None,
-                "kernel": "k_cell<float, MODE=1> (4 Horner stages, whole orbital in shared memory)",
-                "avg_launch_ms": k_ms, "flops_per_launch": flops,
+                "frac": achieved / fp32_peak, "traffic": measured_traffic("k_cell_f32_mode1"),
+                "kernel": "k_cell<float, MODE=1> (4 Horner stages, whole orbital in shared memory; "
+                          "J and norms of the input state fused into the first stage)",
+                "avg_launch_ms": k_ms, "launches_timed": st["calls"]["stencil_kernel"],
+                "flops_per_launch": flops,
                 "peak_note": "FP32 peak = 152 SM x 128 lanes x 2 flop x max SM clock (derived, not measured)",
                 "hbm_view": {"bytes_per_launch": hbm_bytes,
                              "GBps": hbm_bytes / (k_ms * 1e-3) / 1e9,
@@ -306,7 +314,7 @@ def gpu_arm(args, rank, world, local_rank):
     # end to end through the C ABI with host buffers (same predictor as the headline)
     host_in = torch.from_numpy(psi0).pin_memory()
     host_out = torch.empty_like(host_in).pin_memory()
-    ctx2 = Context(s, precision="f32")
+    ctx2 = Context(s, precision="f32", obs_at_start=True)
     u2 = torch.empty_like(u)
     if params is not None:
         ctx2.nn_init(0)
@@ -363,6 +371,22 @@ def gpu_arm(args, rank, world, local_rank):
     return 0
 
 
+def measured_traffic(key):
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of one ncu capture,
+    recorded in profiles/roofline_traffic.json together with the SHA-256 of the kernel's source
+    file at capture time; None when the source has changed since."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "roofline_traffic.json")) as f:
+            rec = json.load(f)[key]
+        with open(os.path.join(ROOT, rec["source"]), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest() != rec["source_sha256"]:
+                return None
+        return rec["bytes_per_launch"]
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def W_nsph(s):
     from paper_1804_01404_gb300.tdks import Context
     c = Context(s, precision="f32")
@@ -403,13 +427,17 @@ def hpsi_cluster(dev, reps=10, norb=256):
     ctx.check()
     ms = e0.elapsed_time(e1) / reps
     k_ms = st["ms"]["hpsi"] / max(1, st["calls"]["hpsi"])
+    s_ms = st["ms"]["stencil_kernel"] / max(1, st["calls"]["stencil_kernel"])
     nbytes = 16 * s.npts * s.nk * s.norb
     pk = peaks()
     res = {"workload": f"isolated cluster 96^3, 128 atoms, {norb} orbitals, FP32", "calls": reps,
            "ms_per_hpsi": ms, "ms_per_hpsi_phase": k_ms, "bytes_per_hpsi": nbytes,
            "GBps": nbytes / (k_ms * 1e-3) / 1e9, "peak_GBps": pk["hbm_gbs"],
            "frac_of_measured_hbm": nbytes / (k_ms * 1e-3) / 1e9 / pk["hbm_gbs"],
-           "kernels": "k_gproject + tile stencil (TMA planes) + k_gscatter"}
+           "kernels": "k_gproject + tile stencil (TMA planes) + k_gscatter",
+           "stencil_kernel_ms": s_ms, "stencil_kernel_GBps": nbytes / (s_ms * 1e-3) / 1e9,
+           "stencil_kernel_frac_of_measured_hbm": nbytes / (s_ms * 1e-3) / 1e9 / pk["hbm_gbs"],
+           "stencil_kernel_traffic": measured_traffic("k_tile_f32_mode0")}
     variant, tune_ms = ctx.tile_variant()
     names = ["k_tile<float> (1 point/thread, 3 CTAs/SM)", "k_tile<float> (1 point/thread, 2 CTAs/SM) + L2 prefetch",
              "k_tile4<8> (2x2 points/thread, 8 consumer warps) + L2 prefetch"]

@@ -82,8 +82,14 @@ typedef struct { double E_s, E_p, r_cut, width; } tdks_projector;
  * pc: predictor-corrector on (1) or a single Taylor step with V(t) (0).
  * ncell: number of independent copies of the system propagated together (0 or 1: one).  With
  * ncell > 1 (periodic grids only) orbitals are [ncell][nk][norb][nz][ny][nx] and every cell has its
- * own density and potential; this is the batch of microscopic cells of the multiscale mode. */
-typedef struct { int precision; int hartree; int xc; int pc; int ncell; } tdks_options;
+ * own density and potential; this is the batch of microscopic cells of the multiscale mode.
+ * obs_at_start: 0 (default) tdks_step leaves the observables of the propagated state, J(t+dt) and
+ * dipole(t+dt), which costs one extra derivative pass over every orbital after the last Taylor
+ * stage; 1 it leaves those of the input state, J(t) and dipole(t), which the first Taylor stage
+ * forms from the derivative sums it computes anyway (no extra pass; the values of the final state
+ * then come from tdks_observables or the next step).  The multiscale step (tdks_ms_step) always
+ * uses the end-of-step current, which the Maxwell update needs. */
+typedef struct { int precision; int hartree; int xc; int pc; int ncell; int obs_at_start; } tdks_options;
 
 /* Observables returned to the host. */
 typedef struct {
@@ -134,7 +140,9 @@ tdks_status tdks_taylor_step(tdks_ctx* ctx, void* u_dev, double dt, const double
  *   predictor  u~ = T4[V_loc + V_Hxc(t)] u,  V~ = V_Hxc[rho(u~)];
  *   corrector  u(t+dt) = T4[V_loc + (V_Hxc(t) + V~)/2] u,  V_Hxc(t+dt) = V_Hxc[rho(t+dt)];
  * both with A'(t + dt/2).  (pc = 0: u(t+dt) = T4[V_loc + V_Hxc(t)] u.)  Afterwards J(t+dt)
- * (with A'(t+dt)) and the dipole are in the step-observable buffer (tdks_read_step_observables). */
+ * (with A'(t+dt)) and the dipole of rho(t+dt) are in the step-observable buffer
+ * (tdks_read_step_observables); with options.obs_at_start = 1, J(t) (with A'(t)) and the dipole of
+ * rho(t) instead. */
 tdks_status tdks_step(tdks_ctx* ctx, void* u_dev, double t, double dt);
 
 /* Copy the observables written by the last tdks_step to the host (synchronises the stream).
@@ -217,10 +225,12 @@ tdks_status tdks_nn_gradient(tdks_ctx* ctx, const double* vhist_dev, const doubl
 /* Phase timing and launch counting.
  * Phases: 0 predictor Taylor kernel, 1 corrector Taylor kernel (and tdks_taylor_step),
  * 2 tdks_hpsi kernel, 3 Hartree + exchange (density-to-potential), 4 observables,
- * 5 everything else (potential combination, memsets).  With timing enabled the library records a
- * CUDA event pair around each phase on the context stream (a few microseconds of overhead per
- * step).  `launches` counts this library's kernel launches since the last reset, timing on or off. */
-#define TDKS_NPHASE 6
+ * 5 everything else (potential combination, memsets), 6 the orbital stencil kernel launches alone
+ * (the shared-memory cell kernel, or the tile stencil kernel of large grids), nested inside phases
+ * 0-2 and also counted there.  With timing enabled the library records a CUDA event pair around
+ * each phase on the context stream (a few microseconds of overhead per step).  `launches` counts
+ * this library's kernel launches since the last reset, timing on or off. */
+#define TDKS_NPHASE 7
 typedef struct {
   long long launches;
   long long calls[TDKS_NPHASE];

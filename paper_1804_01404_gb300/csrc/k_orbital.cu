@@ -16,6 +16,8 @@
 // request, the norm and the current of Eq. (macro_current).
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "tdks_internal.h"
 
 namespace tdks {
@@ -32,6 +34,7 @@ template <> struct CM<float> {
   static __device__ __forceinline__ C sub(C a, C b) { return __ffma2_rn(make_float2(-1.0f, -1.0f), b, a); }
   // acc + s * a  (s real, broadcast to both lanes)
   static __device__ __forceinline__ C fma(float s, C a, C acc) { return __ffma2_rn(make_float2(s, s), a, acc); }
+  static __device__ __forceinline__ C mul(float s, C a) { return __fmul2_rn(make_float2(s, s), a); }
   static __device__ __forceinline__ void sincos_(float x, float* s, float* c) { sincosf(x, s, c); }
 };
 
@@ -42,6 +45,7 @@ template <> struct CM<double> {
   static __device__ __forceinline__ C fma(double s, C a, C acc) {
     return C{__fma_rn(s, a.x, acc.x), __fma_rn(s, a.y, acc.y)};
   }
+  static __device__ __forceinline__ C mul(double s, C a) { return C{s * a.x, s * a.y}; }
   static __device__ __forceinline__ void sincos_(double x, double* s, double* c) { sincos(x, s, c); }
 };
 
@@ -62,7 +66,10 @@ inline size_t cell_smem_bytes(int nz, int pstride, int nsph, int natom, bool dbu
   return sizeof(C) * (vsz * (dbuf ? 2 : 1) + nsph + 4 * (size_t)natom);
 }
 
-constexpr int kNT = 832;               // threads per CTA (upper bound)
+// Threads per CTA (upper bound): 25 warps for FP32 (two z-segments per column of a 20^2 plane; the
+// warps-per-scheduler count caps registers at 72), 16 warps for FP64 so that its wider values get
+// 128 registers per thread.
+template <typename T> constexpr int kNTof() { return sizeof(T) == 4 ? 800 : 512; }
 constexpr size_t kSmemLimit = 220 * 1024;
 
 // Projections of the shared-memory vector:  ec[a*4+p] = E_p dV sum_i beta_ip ph_i v(idx_i).
@@ -148,36 +155,55 @@ __device__ __forceinline__ typename Cplx<T>::type zload(const OrbArgs<T>& a,
 }
 
 // Local part of (H v) at (x, y, z) of a column: diag*v + S + (-i) q.D, z-neighbours from window w.
-template <typename T, bool PER>
+// WD (periodic cells): also return the per-axis first-derivative sums D1_a v in Dout[3], with one
+// accumulator per axis.  Otherwise each neighbour distance m uses one Laplacian and one derivative
+// coefficient, the axes entering through the fixed ratios (c2y = ry c2x, d1y = ty d1x, ...):
+//   S += c2x[m] (X_m + ry Y_m + rz Z_m),  q.D += d1x[m] (q_x X'_m + ty q_y Y'_m + tz q_z Z'_m)
+// (X_m: x+m plus x-m values, X'_m: their difference), which halves the coefficient registers.
+template <typename T, bool PER, bool WD>
 __device__ __forceinline__ typename Cplx<T>::type local_h(const OrbArgs<T>& a,
                                                           const Column<T, PER>& c,
                                                           const typename Cplx<T>::type* v,
                                                           const typename Cplx<T>::type* w, int zb,
-                                                          T diag, const T* q) {
+                                                          T diag, const T* q,
+                                                          typename Cplx<T>::type* Dout) {
   using C = typename Cplx<T>::type;
   using M = CM<T>;
-  // independent accumulators per axis keep the FMA chains short
-  C Sx = M::fma(diag, w[4], C{0, 0}), Sy = C{0, 0}, Sz = C{0, 0};
-  C Dx = C{0, 0}, Dy = C{0, 0}, Dz = C{0, 0};
+  if (WD) {
+    // independent accumulators per axis keep the FMA chains short
+    C Sx = M::fma(diag, w[4], C{0, 0}), Sy = C{0, 0}, Sz = C{0, 0};
+    C Dx = C{0, 0}, Dy = C{0, 0}, Dz = C{0, 0};
+#pragma unroll
+    for (int m = 1; m <= 4; ++m) {
+      const C xp = v[zb + c.ix[2 * (m - 1)]], xm = v[zb + c.ix[2 * (m - 1) + 1]];
+      const C yp = v[zb + c.iy[2 * (m - 1)]], ym = v[zb + c.iy[2 * (m - 1) + 1]];
+      const C zp = w[4 + m], zm = w[4 - m];
+      Sx = M::fma(a.c2x[m], M::add(xp, xm), Sx);
+      Sy = M::fma(a.c2y[m], M::add(yp, ym), Sy);
+      Sz = M::fma(a.c2z[m], M::add(zp, zm), Sz);
+      Dx = M::fma(a.d1x[m - 1], M::sub(xp, xm), Dx);
+      Dy = M::fma(a.d1y[m - 1], M::sub(yp, ym), Dy);
+      Dz = M::fma(a.d1z[m - 1], M::sub(zp, zm), Dz);
+    }
+    C S = M::add(M::add(Sx, Sy), Sz);
+    const C D = M::fma(q[2], Dz, M::fma(q[1], Dy, M::fma(q[0], Dx, C{0, 0})));
+    Dout[0] = Dx; Dout[1] = Dy; Dout[2] = Dz;
+    return C{S.x + D.y, S.y - D.x};   // + (-i) q.D
+  }
+  C S = M::fma(diag, w[4], C{0, 0});
+  C D = C{0, 0};
+  const T qy = q[1] * a.ty, qz = q[2] * a.tz;
 #pragma unroll
   for (int m = 1; m <= 4; ++m) {
     const C xp = v[zb + c.ix[2 * (m - 1)]], xm = v[zb + c.ix[2 * (m - 1) + 1]];
     const C yp = v[zb + c.iy[2 * (m - 1)]], ym = v[zb + c.iy[2 * (m - 1) + 1]];
     const C zp = w[4 + m], zm = w[4 - m];
-    Sx = M::fma(a.c2x[m], M::add(xp, xm), Sx);
-    Sy = M::fma(a.c2y[m], M::add(yp, ym), Sy);
-    Sz = M::fma(a.c2z[m], M::add(zp, zm), Sz);
-    if (PER) {
-      Dx = M::fma(a.d1x[m - 1], M::sub(xp, xm), Dx);
-      Dy = M::fma(a.d1y[m - 1], M::sub(yp, ym), Dy);
-      Dz = M::fma(a.d1z[m - 1], M::sub(zp, zm), Dz);
-    }
+    S = M::fma(a.c2x[m], M::fma(a.rz, M::add(zp, zm), M::fma(a.ry, M::add(yp, ym), M::add(xp, xm))), S);
+    if (PER)
+      D = M::fma(a.d1x[m - 1],
+                 M::fma(qz, M::sub(zp, zm), M::fma(qy, M::sub(yp, ym), M::mul(q[0], M::sub(xp, xm)))), D);
   }
-  C S = M::add(M::add(Sx, Sy), Sz);
-  if (PER) {
-    const C D = M::fma(q[2], Dz, M::fma(q[1], Dy, M::fma(q[0], Dx, C{0, 0})));
-    S = C{S.x + D.y, S.y - D.x};   // + (-i) q.D
-  }
+  if (PER) S = C{S.x + D.y, S.y - D.x};   // + (-i) q.D
   return S;
 }
 
@@ -218,74 +244,170 @@ __device__ __forceinline__ void set_phases(const OrbArgs<T>& a, typename Cplx<T>
   }
 }
 
-__device__ __forceinline__ double block_sum(double v, double* red) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+// Accumulators of the per-orbital sums.  FP64 arithmetic runs at a small fraction of the FP32 rate
+// on this GPU, so FP32 kernels accumulate in compensated float-float form (an unevaluated sum
+// hi + lo, added with Knuth's two-sum), which keeps about 44 significant bits; FP64 kernels use double.
+struct FF {
+  float hi, lo;
+};
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  const float s = a.hi + b.hi;
+  const float bb = s - a.hi;
+  const float e = (a.hi - (s - bb)) + (b.hi - bb) + a.lo + b.lo;
+  const float h = s + e;
+  return FF{h, e - (h - s)};
+}
+__device__ __forceinline__ FF ff_shfl_xor(FF a, int o) {
+  return FF{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+}
+template <typename T> struct Acc;
+template <> struct Acc<float> {
+  using type = FF;
+  static __device__ __forceinline__ FF zero() { return FF{0.f, 0.f}; }
+  static __device__ __forceinline__ FF add(FF a, float x) { return ff_add(a, FF{x, 0.f}); }
+  static __device__ __forceinline__ FF warp_sum(FF a) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a = ff_add(a, ff_shfl_xor(a, o));
+    return a;
+  }
+  static __device__ __forceinline__ double to_double(FF a) { return (double)a.hi + (double)a.lo; }
+  static __device__ __forceinline__ FF from_double(double x) {
+    const float h = (float)x;
+    return FF{h, (float)(x - (double)h)};
+  }
+};
+template <> struct Acc<double> {
+  using type = double;
+  static __device__ __forceinline__ double zero() { return 0.0; }
+  static __device__ __forceinline__ double add(double a, double x) { return a + x; }
+  static __device__ __forceinline__ double warp_sum(double a) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    return a;
+  }
+  static __device__ __forceinline__ double to_double(double a) { return a; }
+  static __device__ __forceinline__ double from_double(double x) { return x; }
+};
+
+// Per-orbital observables from per-thread partial sums v = {sum |u|^2, sum Im(conj(u) D1_a u) (a = x,
+// y, z), sum Re(conj(u) (H u))}: warp sums in the accumulator type, one barrier, then thread j < 8 adds
+// the warps' sums in FP64 and writes out[j] = {norm, J_loc[3], J_nl[3], e} with
+// J_loc_a = (sum Im(conj(u) D1_a u) + qo_a sum |u|^2) dV and J_nl from s_jnl.
+// red: [8][32] shared doubles.
+template <typename T>
+__device__ __forceinline__ void reduce_obs(const T v[5], const T qo[3], double dV, const double* s_jnl,
+                                           double* red, double* out) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  typename Acc<T>::type x[5];
+#pragma unroll
+  for (int j = 0; j < 5; ++j) x[j] = Acc<T>::warp_sum(Acc<T>::add(Acc<T>::zero(), v[j]));
+  __syncthreads();                                 // red and s_jnl complete, red free
+  if (lane == 0) {
+#pragma unroll
+    for (int j = 0; j < 5; ++j) red[j * 32 + warp] = Acc<T>::to_double(x[j]);
+  }
   __syncthreads();
-  if (lane == 0) red[warp] = v;
-  __syncthreads();
-  double t = 0;
-  if (threadIdx.x == 0)
-    for (int w = 0; w < nw; ++w) t += red[w];
-  return t;   // valid in thread 0
+  if (threadIdx.x < 8) {
+    const int j = threadIdx.x;
+    double t[2] = {0, 0};
+    const int src = (j == 7) ? 4 : (j < 4 ? j : -1);
+    if (src >= 0)
+      for (int w = 0; w < nw; ++w) { t[0] += red[src * 32 + w]; t[1] += red[w]; }
+    double r;
+    if (j == 0 || j == 7) r = t[0] * dV;
+    else if (j < 4) r = (t[0] + (double)qo[j - 1] * t[1]) * dV;
+    else r = s_jnl[j - 4];
+    out[j] = r;
+  }
 }
 
-// sum over atoms of sum_p 2 E_p Im(conj(b_ap^(d)) c_ap) dV^2 (the nonlocal current of one orbital),
-// one warp per atom; valid in lane 0 of each warp (summed later by block_sum).
+// Nonlocal current of one orbital, sum over atoms of sum_p 2 E_p Im(conj(b_ap^(d)) c_ap) dV^2, with
+// c_ap = sum_i beta_ip ph_i v_i and b_ap^(d) = sum_i d_i beta_ip ph_i v_i.  Every warp takes a chunk of
+// one atom's sphere points (atoms in batches of kNLBatch, each split over the warps), partial sums
+// meet in shared memory (part: [kNLBatch][32] of T), and thread a of the batch forms the products
+// of atom a and adds it to s_jnl[3] (shared; zeroed by the caller).
+constexpr int kNLBatch = 16;
 template <typename T>
 __device__ __forceinline__ void nonlocal_current(const OrbArgs<T>& a, const typename Cplx<T>::type* v,
-                                                 const typename Cplx<T>::type* ph, double jnl[3]) {
+                                                 const typename Cplx<T>::type* ph, T* part,
+                                                 double* s_jnl) {
   using C = typename Cplx<T>::type;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int at = warp; at < a.natom; at += nw) {
-    T cb[8], bb[3][8];
+  for (int ab = 0; ab < a.natom; ab += kNLBatch) {
+    const int nb = min(kNLBatch, a.natom - ab);
+    const int nch = max(1, nw / nb);               // chunks per atom
+    for (int i = threadIdx.x; i < kNLBatch * 32; i += blockDim.x) part[i] = T(0);
+    __syncthreads();
+    for (int job = warp; job < nb * nch; job += nw) {
+      const int at = ab + job / nch, ch = job % nch;
+      T cb[8], bb[3][8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) { cb[j] = 0; bb[0][j] = bb[1][j] = bb[2][j] = 0; }
-    for (int i = a.atom_off[at] + lane; i < a.atom_off[at + 1]; i += 32) {
-      const C u = v[a.sph_sidx[i]];
-      const C f = ph[i];
-      const T re = u.x * f.x - u.y * f.y, im = u.x * f.y + u.y * f.x;
-      const T d0 = a.sph_d[3 * i], d1 = a.sph_d[3 * i + 1], d2 = a.sph_d[3 * i + 2];
+      for (int j = 0; j < 8; ++j) { cb[j] = 0; bb[0][j] = bb[1][j] = bb[2][j] = 0; }
+      for (int i = a.atom_off[at] + ch * 32 + lane; i < a.atom_off[at + 1]; i += 32 * nch) {
+        const C u = v[a.sph_sidx[i]];
+        const C f = ph[i];
+        const T re = u.x * f.x - u.y * f.y, im = u.x * f.y + u.y * f.x;
+        const T d0 = a.sph_d[3 * i], d1 = a.sph_d[3 * i + 1], d2 = a.sph_d[3 * i + 2];
 #pragma unroll
-      for (int p = 0; p < 4; ++p) {
-        const T b = a.sph_beta[i * 4 + p];
-        cb[2 * p] += b * re; cb[2 * p + 1] += b * im;
-        bb[0][2 * p] += d0 * b * re; bb[0][2 * p + 1] += d0 * b * im;
-        bb[1][2 * p] += d1 * b * re; bb[1][2 * p + 1] += d1 * b * im;
-        bb[2][2 * p] += d2 * b * re; bb[2][2 * p + 1] += d2 * b * im;
+        for (int p = 0; p < 4; ++p) {
+          const T b = a.sph_beta[i * 4 + p];
+          cb[2 * p] += b * re; cb[2 * p + 1] += b * im;
+          bb[0][2 * p] += d0 * b * re; bb[0][2 * p + 1] += d0 * b * im;
+          bb[1][2 * p] += d1 * b * re; bb[1][2 * p + 1] += d1 * b * im;
+          bb[2][2 * p] += d2 * b * re; bb[2][2 * p + 1] += d2 * b * im;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          cb[j] += __shfl_xor_sync(0xffffffffu, cb[j], o);
+          bb[0][j] += __shfl_xor_sync(0xffffffffu, bb[0][j], o);
+          bb[1][j] += __shfl_xor_sync(0xffffffffu, bb[1][j], o);
+          bb[2][j] += __shfl_xor_sync(0xffffffffu, bb[2][j], o);
+        }
+      if (lane == 0) {
+        T* pa = part + (at - ab) * 32;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          atomicAdd(&pa[j], cb[j]);
+          atomicAdd(&pa[8 + j], bb[0][j]);
+          atomicAdd(&pa[16 + j], bb[1][j]);
+          atomicAdd(&pa[24 + j], bb[2][j]);
+        }
       }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        cb[j] += __shfl_xor_sync(0xffffffffu, cb[j], o);
-        bb[0][j] += __shfl_xor_sync(0xffffffffu, bb[0][j], o);
-        bb[1][j] += __shfl_xor_sync(0xffffffffu, bb[1][j], o);
-        bb[2][j] += __shfl_xor_sync(0xffffffffu, bb[2][j], o);
-      }
-    if (lane == 0) {
+    __syncthreads();
+    if (threadIdx.x < nb) {
+      const int at = ab + threadIdx.x;
+      const T* pa = part + threadIdx.x * 32;
       const double dv2 = (double)a.dV * (double)a.dV;
       for (int d = 0; d < 3; ++d) {
         double sacc = 0;
         for (int p = 0; p < 4; ++p)
           sacc += 2.0 * (double)a.atomE[at * 4 + p] *
-                  ((double)bb[d][2 * p] * cb[2 * p + 1] - (double)bb[d][2 * p + 1] * cb[2 * p]);
-        jnl[d] += sacc * dv2;
+                  ((double)pa[8 + 8 * d + 2 * p] * pa[2 * p + 1] - (double)pa[8 + 8 * d + 2 * p + 1] * pa[2 * p]);
+        atomicAdd(&s_jnl[d], sacc * dv2);
       }
     }
+    __syncthreads();
   }
 }
 
 // MODE 0: out = H v.   MODE 1: out = T4 v (Horner), rho += 2 w_k |out|^2, optional fused
 // observables.   MODE 2: observables only (norm, current, <v|H|v> with a.V).
 // DBUF: next vector in shared memory; otherwise in the orbital's slice of `scratch`.
-template <typename T, int MODE, bool PER, bool DBUF, bool OBS>
-__global__ void __launch_bounds__(kNT) k_cell(OrbArgs<T> a, typename Cplx<T>::type* scratch) {
+// OBS (MODE 1): 0 none; 1 norm and current of the propagated orbital, in an extra pass after the
+// last stage; 2 norm and current of the input orbital, accumulated during the first stage from the
+// per-axis derivative sums that stage forms anyway (no extra pass).  MODE 2 always uses 1.
+template <typename T, int MODE, bool PER, bool DBUF, int OBS>
+__global__ void __launch_bounds__(kNTof<T>()) k_cell(OrbArgs<T> a, typename Cplx<T>::type* scratch) {
   using C = typename Cplx<T>::type;
   using M = CM<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double red[kNT / 32];
+  __shared__ double red[8 * 32];
+  __shared__ T nl_part[kNLBatch * 32];
+  __shared__ double s_jnl[3];
   const int nxy = a.nx * a.ny;
   const int ps = a.pstride;
   const int vsz = a.nz * ps;
@@ -314,11 +436,29 @@ __global__ void __launch_bounds__(kNT) k_cell(OrbArgs<T> a, typename Cplx<T>::ty
     L.v[i] = u;
     if (DBUF) L.nxt[i] = C{0, 0};
   }
+  // wave vector of the observables: k + A'_obs (OBS 1: end of the step; OBS 2: its start)
+  auto obs_q = [&](T qo[3]) {
+    qo[0] = q[0]; qo[1] = q[1]; qo[2] = q[2];
+    if (OBS != 0 && MODE == 1) {
+      const double* apo = a.Ap_obs_cell ? a.Ap_obs_cell + 3 * cell : a.Ap_obs;
+      for (int d = 0; d < 3; ++d) qo[d] = (T)(a.kpts[3 * k + d] + apo[d]);
+    }
+  };
+  if (OBS != 0 && threadIdx.x < 3) s_jnl[threadIdx.x] = 0.0;
+  if (OBS == 2 && PER && a.natom > 0) {          // nonlocal current of the input orbital
+    T qo[3];
+    obs_q(qo);
+    set_phases<T>(a, L.ph, qo);
+    __syncthreads();
+    nonlocal_current<T>(a, L.v, L.ph, nl_part, s_jnl);
+  }
   set_phases<T>(a, L.ph, q);
   __syncthreads();
 
   const int nitems = nxy * a.nseg;
   constexpr int NSTAGE = (MODE == 1) ? 4 : 1;
+  // per-thread partial sums of the observables {|u|^2, Im(conj(u) D1_a u) x3, Re(conj(u) H u)}
+  T os[5] = {0, 0, 0, 0, 0};
 #pragma unroll 1
   for (int st = 0; st < NSTAGE; ++st) {
     if (a.natom > 0) {
@@ -326,37 +466,57 @@ __global__ void __launch_bounds__(kNT) k_cell(OrbArgs<T> a, typename Cplx<T>::ty
       __syncthreads();
     }
     const T coef = a.dt / T(4 - st);
-    // local part for every column segment
+    // local part for every column segment; the first stage of OBS 2 also sums the observables of
+    // its input (a separate instance of the loop, so the other stages compile as without them)
+    auto local_pass = [&](auto acc_tag) {
+      constexpr bool ACC = decltype(acc_tag)::value;
 #pragma unroll 1
-    for (int item = threadIdx.x; item < nitems; item += blockDim.x) {
-      const Column<T, PER> c = make_column<T, PER>(a, item);
-      C w[9];
+      for (int item = threadIdx.x; item < nitems; item += blockDim.x) {
+        const Column<T, PER> c = make_column<T, PER>(a, item);
+        C w[9];
 #pragma unroll
-      for (int j = 0; j < 9; ++j) w[j] = zload<T, PER>(a, L.v, c.z0 - 4 + j, c.col);
-      T vnext = Vc[c.z0 * nxy + c.col];
-      C pnext = (MODE == 1) ? psi[c.z0 * nxy + c.col] : C{0, 0};
+        for (int j = 0; j < 9; ++j) w[j] = zload<T, PER>(a, L.v, c.z0 - 4 + j, c.col);
+        T vnext = Vc[c.z0 * nxy + c.col];
+        C pnext = (MODE == 1) ? psi[c.z0 * nxy + c.col] : C{0, 0};
 #pragma unroll 1
-      for (int z = c.z0; z < c.z1; ++z) {
-        const int zb = z * ps;
-        const int pg = z * nxy + c.col;
-        const T diag = diag0 + vnext;
-        const C pv = pnext;
-        if (z + 1 < c.z1) {                   // prefetch the next plane's V and psi
-          vnext = Vc[pg + nxy];
-          if (MODE == 1) pnext = psi[pg + nxy];
-        }
-        const C hv = local_h<T, PER>(a, c, L.v, w, zb, diag, q);
-        C r;
-        if (MODE == 1) {
-          r = M::fma(coef, C{hv.y, -hv.x}, pv);   // psi + (-i coef) H v
-        } else {
-          r = hv;
-        }
-        if (DBUF) L.nxt[zb + c.col] = r; else gnxt[pg] = r;
+        for (int z = c.z0; z < c.z1; ++z) {
+          const int zb = z * ps;
+          const int pg = z * nxy + c.col;
+          const T diag = diag0 + vnext;
+          const C pv = pnext;
+          if (z + 1 < c.z1) {                   // prefetch the next plane's V and psi
+            vnext = Vc[pg + nxy];
+            if (MODE == 1) pnext = psi[pg + nxy];
+          }
+          C Dd[3];
+          const C hv = local_h<T, PER, ACC && PER>(a, c, L.v, w, zb, diag, q, Dd);
+          if (ACC) {                            // |u|^2 and Im(conj(u) D1_a u)
+            const C u0 = w[4];
+            os[0] += u0.x * u0.x + u0.y * u0.y;
+            if (PER) {
 #pragma unroll
-        for (int j = 0; j < 8; ++j) w[j] = w[j + 1];
-        w[8] = zload<T, PER>(a, L.v, z + 5, c.col);
+              for (int d = 0; d < 3; ++d) os[1 + d] += u0.x * Dd[d].y - u0.y * Dd[d].x;
+            }
+          }
+          C r;
+          if (MODE == 1) {
+            r = M::fma(coef, C{hv.y, -hv.x}, pv);   // psi + (-i coef) H v
+          } else {
+            r = hv;
+          }
+          if (DBUF) L.nxt[zb + c.col] = r; else gnxt[pg] = r;
+#pragma unroll
+          for (int j = 0; j < 8; ++j) w[j] = w[j + 1];
+          w[8] = zload<T, PER>(a, L.v, z + 5, c.col);
+        }
       }
+    };
+    if (OBS == 2 && st == 0) local_pass(std::integral_constant<bool, true>{});
+    else local_pass(std::integral_constant<bool, false>{});
+    if (OBS == 2 && st == 0) {                   // observables of the input orbital are complete
+      T qo[3];
+      obs_q(qo);
+      reduce_obs<T>(os, qo, a.dV, s_jnl, red, a.obs + (size_t)orb * 8);
     }
     __syncthreads();
     // nonlocal scatter at sphere points
@@ -387,26 +547,18 @@ __global__ void __launch_bounds__(kNT) k_cell(OrbArgs<T> a, typename Cplx<T>::ty
     }
   }
 
-  // final pass: write, density, observables
+  // final pass: write, density, observables (OBS 1)
   const double wk = 2.0 * a.kw[k];
   C* out = a.psi_out ? a.psi_out + (size_t)orb * a.npts : nullptr;
-  T qo[3] = {q[0], q[1], q[2]};
-  if (OBS && MODE == 1) {
-    const double* apo = a.Ap_obs_cell ? a.Ap_obs_cell + 3 * cell : a.Ap_obs;
-    qo[0] = (T)(a.kpts[3 * k] + apo[0]);
-    qo[1] = (T)(a.kpts[3 * k + 1] + apo[1]);
-    qo[2] = (T)(a.kpts[3 * k + 2] + apo[2]);
-  }
-  double acc_norm = 0, acc_j[3] = {0, 0, 0}, acc_e = 0;
+  constexpr bool FINAL_OBS = (OBS == 1);
 #pragma unroll 1
   for (int item = threadIdx.x; item < nitems; item += blockDim.x) {
     const Column<T, PER> c = make_column<T, PER>(a, item);
     C w[9];
-    if (OBS) {
+    if (FINAL_OBS) {
 #pragma unroll
       for (int j = 0; j < 9; ++j) w[j] = zload<T, PER>(a, L.v, c.z0 - 4 + j, c.col);
     }
-    T cn = 0, cj[3] = {0, 0, 0}, ce = 0;
 #pragma unroll 1
     for (int z = c.z0; z < c.z1; ++z) {
       const int zb = z * ps;
@@ -418,11 +570,11 @@ __global__ void __launch_bounds__(kNT) k_cell(OrbArgs<T> a, typename Cplx<T>::ty
         if (a.rho32) atomicAdd(&a.rho32[((size_t)cell * a.nk + k) * a.npts + pg], 2.0f * (float)rr);
         else if (a.rho) atomicAdd(&a.rho[(size_t)cell * a.npts + pg], wk * (double)rr);
       }
-      if (OBS) {
-        cn += rr;
+      if (FINAL_OBS) {
+        os[0] += rr;
         if (MODE == 2) {
           const C hv = DBUF ? L.nxt[zb + c.col] : gnxt[pg];
-          ce += r.x * hv.x + r.y * hv.y;
+          os[4] += r.x * hv.x + r.y * hv.y;
         }
         if (PER) {
           // Im(conj(r) D1_a r) + q_a |r|^2
@@ -433,38 +585,31 @@ __global__ void __launch_bounds__(kNT) k_cell(OrbArgs<T> a, typename Cplx<T>::ty
             dy = M::fma(a.d1y[m - 1], M::sub(L.v[zb + c.iy[2 * (m - 1)]], L.v[zb + c.iy[2 * (m - 1) + 1]]), dy);
             dz = M::fma(a.d1z[m - 1], M::sub(w[4 + m], w[4 - m]), dz);
           }
-          cj[0] += r.x * dx.y - r.y * dx.x + qo[0] * rr;
-          cj[1] += r.x * dy.y - r.y * dy.x + qo[1] * rr;
-          cj[2] += r.x * dz.y - r.y * dz.x + qo[2] * rr;
+          os[1] += r.x * dx.y - r.y * dx.x;
+          os[2] += r.x * dy.y - r.y * dy.x;
+          os[3] += r.x * dz.y - r.y * dz.x;
         }
 #pragma unroll
         for (int j = 0; j < 8; ++j) w[j] = w[j + 1];
         w[8] = zload<T, PER>(a, L.v, z + 5, c.col);
       }
     }
-    acc_norm += cn;
-    acc_e += ce;
-    for (int d = 0; d < 3; ++d) acc_j[d] += cj[d];
   }
-  if (!OBS) return;
+  if (!FINAL_OBS) return;
 
   // nonlocal current with the final phases: sum_ap 2 E_p Im(conj(b_ap^(d)) c_ap)
-  double jnl[3] = {0, 0, 0};
+  T qo[3];
+  obs_q(qo);
   if (PER && a.natom > 0) {
     __syncthreads();
     set_phases<T>(a, L.ph, qo);
     __syncthreads();
-    nonlocal_current<T>(a, L.v, L.ph, jnl);
+    nonlocal_current<T>(a, L.v, L.ph, nl_part, s_jnl);
   }
-  const double vals[8] = {acc_norm * a.dV, acc_j[0] * a.dV, acc_j[1] * a.dV, acc_j[2] * a.dV,
-                          jnl[0], jnl[1], jnl[2], acc_e * a.dV};
-  for (int j = 0; j < 8; ++j) {
-    const double t = block_sum(vals[j], red);
-    if (threadIdx.x == 0) a.obs[(size_t)orb * 8 + j] = t;
-  }
+  reduce_obs<T>(os, qo, a.dV, s_jnl, red, a.obs + (size_t)orb * 8);
 }
 
-template <typename T, int MODE, bool PER, bool DBUF, bool OBS>
+template <typename T, int MODE, bool PER, bool DBUF, int OBS>
 cudaError_t launch_cell(const OrbArgs<T>& a, typename Cplx<T>::type* scratch, size_t smem, int nt,
                         cudaStream_t s) {
   auto kern = k_cell<T, MODE, PER, DBUF, OBS>;
@@ -474,14 +619,14 @@ cudaError_t launch_cell(const OrbArgs<T>& a, typename Cplx<T>::type* scratch, si
   return cudaGetLastError();
 }
 
-template <typename T, int MODE, bool OBS>
+template <typename T, int MODE, int OBS>
 cudaError_t dispatch(const OrbArgs<T>& a, typename Cplx<T>::type* scratch, cudaStream_t s) {
   const bool dbuf = cell_smem_bytes<T>(a.nz, a.pstride, a.nsph, a.natom, true) <= kSmemLimit;
   if (!dbuf && !scratch) return cudaErrorInvalidValue;
   const size_t smem = cell_smem_bytes<T>(a.nz, a.pstride, a.nsph, a.natom, dbuf);
   const int items = a.nx * a.ny * a.nseg;
   int nt = ((items + 31) / 32) * 32;
-  if (nt > kNT) nt = kNT;
+  if (nt > kNTof<T>()) nt = kNTof<T>();
   if (a.periodic)
     return dbuf ? launch_cell<T, MODE, true, true, OBS>(a, scratch, smem, nt, s)
                 : launch_cell<T, MODE, true, false, OBS>(a, scratch, smem, nt, s);
@@ -501,9 +646,9 @@ bool smem_orbital_needs_scratch(int nz, int pstride, int nsph, int natom) {
   return cell_smem_bytes<T>(nz, pstride, nsph, natom, true) > kSmemLimit;
 }
 
-void cell_split(int nx, int ny, int nz, int* nseg, int* zlen) {
+void cell_split(int nx, int ny, int nz, int elem_bytes, int* nseg, int* zlen) {
   const int ncol = nx * ny;
-  int s = kNT / ncol;
+  int s = (elem_bytes == 8 ? kNTof<float>() : kNTof<double>()) / ncol;
   if (s < 1) s = 1;
   if (s > nz) s = nz;
   *zlen = (nz + s - 1) / s;
@@ -513,9 +658,12 @@ void cell_split(int nx, int ny, int nz, int* nseg, int* zlen) {
 template <typename T>
 cudaError_t launch_smem_orbital(const OrbArgs<T>& a, int mode, typename Cplx<T>::type* scratch,
                                 cudaStream_t s) {
-  if (mode == 0) return dispatch<T, 0, false>(a, scratch, s);
-  if (mode == 1) return a.obs ? dispatch<T, 1, true>(a, scratch, s) : dispatch<T, 1, false>(a, scratch, s);
-  return dispatch<T, 2, true>(a, scratch, s);
+  if (mode == 0) return dispatch<T, 0, 0>(a, scratch, s);
+  if (mode == 1) {
+    if (!a.obs) return dispatch<T, 1, 0>(a, scratch, s);
+    return a.obs_at_start ? dispatch<T, 1, 2>(a, scratch, s) : dispatch<T, 1, 1>(a, scratch, s);
+  }
+  return dispatch<T, 2, 1>(a, scratch, s);
 }
 
 template bool smem_orbital_fits<float>(int, int, int, int);

@@ -162,6 +162,13 @@ OrbArgs<T> make_args(const tdks_ctx* c, const void* in, void* out, const T* V, c
     a.d1y[m] = (T)(kFD1[m] / c->grid.h[1]);
     a.d1z[m] = (T)(kFD1[m] / c->grid.h[2]);
   }
+  {
+    const double hx = c->grid.h[0], hy = c->grid.h[1], hz = c->grid.h[2];
+    a.ry = (T)(hx * hx / (hy * hy));
+    a.rz = (T)(hx * hx / (hz * hz));
+    a.ty = (T)(hx / hy);
+    a.tz = (T)(hx / hz);
+  }
   a.norb = c->norb; a.nk = c->nk;
   a.kpts = c->d_kpts;
   for (int i = 0; i < 3; ++i) a.Ap[i] = Ap ? Ap[i] : 0.0;
@@ -280,7 +287,10 @@ tdks_status tiled_kernel(tdks_ctx* c, int mode, const void* in, void* out, doubl
   if (mode == 0) {
     a.out = static_cast<C*>(out);
     TDKS_CUDA(launch_tile_project<T>(a, static_cast<const C*>(in), c->stream));
-    TDKS_CUDA(launch_tile_stage<T>(a, in, 0, c->stream));
+    {
+      Phase pk(c, 6);
+      TDKS_CUDA(launch_tile_stage<T>(a, in, 0, c->stream));
+    }
     TDKS_CUDA(launch_tile_scatter<T>(a, a.out, 0, c->stream));
     c->launches += 3;
     return TDKS_OK;
@@ -297,7 +307,10 @@ tdks_status tiled_kernel(tdks_ctx* c, int mode, const void* in, void* out, doubl
     a.coef = (T)(dt / (4 - st));
     a.out = dst[st];
     TDKS_CUDA(launch_tile_project<T>(a, v, c->stream));
-    TDKS_CUDA(launch_tile_stage<T>(a, v, 1, c->stream));
+    {
+      Phase pk(c, 6);
+      TDKS_CUDA(launch_tile_stage<T>(a, v, 1, c->stream));
+    }
     TDKS_CUDA(launch_tile_scatter<T>(a, a.out, 1, c->stream));
     c->launches += 3;
     v = a.out;
@@ -310,7 +323,8 @@ tdks_status tiled_kernel(tdks_ctx* c, int mode, const void* in, void* out, doubl
 }
 
 tdks_status orbital_kernel(tdks_ctx* c, int mode, const void* in, void* out, const double Ap[3],
-                           double dt, double* rho, int write_out, const double* Ap_obs = nullptr) {
+                           double dt, double* rho, int write_out, const double* Ap_obs = nullptr,
+                           bool obs_start = false) {
   Phase ph(c, mode == 0 ? 2 : (write_out ? 1 : 0));
   if (c->tiled)
     return is_f32(c) ? tiled_kernel<float>(c, mode, in, out, dt, rho, write_out)
@@ -324,16 +338,30 @@ tdks_status orbital_kernel(tdks_ctx* c, int mode, const void* in, void* out, con
       a.rho = nullptr;
       a.rho32 = c->d_rho32;
     }
-    if (Ap_obs) { a.obs = c->d_orb_obs; for (int i = 0; i < 3; ++i) a.Ap_obs[i] = Ap_obs[i]; }
-    TDKS_CUDA(launch_smem_orbital<float>(a, mode, static_cast<float2*>(c->d_scratch), c->stream));
+    if (Ap_obs) {
+      a.obs = c->d_orb_obs;
+      a.obs_at_start = obs_start ? 1 : 0;
+      for (int i = 0; i < 3; ++i) a.Ap_obs[i] = Ap_obs[i];
+    }
+    {
+      Phase pk(c, 6);
+      TDKS_CUDA(launch_smem_orbital<float>(a, mode, static_cast<float2*>(c->d_scratch), c->stream));
+    }
     if (rho) {
       TDKS_CUDA(launch_fold_density(c->d_rho32, c->nk, c->npts, c->d_kw, rho, c->stream, c->ncell));
       c->launches += 1;
     }
   } else {
     auto a = make_args<double>(c, in, out, c->d_v64, Ap, dt, rho, write_out);
-    if (Ap_obs) { a.obs = c->d_orb_obs; for (int i = 0; i < 3; ++i) a.Ap_obs[i] = Ap_obs[i]; }
-    TDKS_CUDA(launch_smem_orbital<double>(a, mode, static_cast<double2*>(c->d_scratch), c->stream));
+    if (Ap_obs) {
+      a.obs = c->d_orb_obs;
+      a.obs_at_start = obs_start ? 1 : 0;
+      for (int i = 0; i < 3; ++i) a.Ap_obs[i] = Ap_obs[i];
+    }
+    {
+      Phase pk(c, 6);
+      TDKS_CUDA(launch_smem_orbital<double>(a, mode, static_cast<double2*>(c->d_scratch), c->stream));
+    }
   }
   return TDKS_OK;
 }
@@ -505,6 +533,7 @@ tdks_status tdks_init(const tdks_grid* grid, const tdks_cell* cell, const tdks_a
   double wsum = 0.0;
   for (int k = 0; k < nk; ++k) wsum += kw[k];
   if (std::fabs(wsum - 1.0) > 1e-9) return fail(TDKS_EINVAL, "k-point weights must sum to 1");
+  if (opts->obs_at_start != 0 && opts->obs_at_start != 1) return fail(TDKS_EINVAL, "obs_at_start must be 0 or 1");
 
   tdks_ctx* c = new tdks_ctx();
   c->grid = *grid;
@@ -529,7 +558,7 @@ tdks_status tdks_init(const tdks_grid* grid, const tdks_cell* cell, const tdks_a
   c->nsph = (int)T.idx.size();
   c->nsp = (int)T.sp_pt.size();
   c->pstride = smem_plane_stride(*grid);
-  cell_split(grid->n[0], grid->n[1], grid->n[2], &c->nseg, &c->zlen);
+  cell_split(grid->n[0], grid->n[1], grid->n[2], is_f32(c) ? 8 : 16, &c->nseg, &c->zlen);
   const bool fits = is_f32(c) ? smem_orbital_fits<float>(grid->n[2], c->pstride, c->nsph, c->natom)
                               : smem_orbital_fits<double>(grid->n[2], c->pstride, c->nsph, c->natom);
   if (!fits) {
@@ -728,7 +757,10 @@ tdks_status tdks_taylor_step(tdks_ctx* c, void* u, double dt, const double Ap[3]
 
 // plain predictor-corrector (or single Taylor step) from u; leaves V_Hxc(t+dt) in d_vhxc and the
 // predictor's potential in d_vpred
-tdks_status pc_step(tdks_ctx* c, void* u, const double Amid[3], const double Aend[3], double dt) {
+// Aobs: A' of the fused per-orbital observables (nullptr: none); obs_start: they belong to the input
+// state (formed by the first orbital kernel of the step) instead of the propagated one.
+tdks_status pc_step(tdks_ctx* c, void* u, const double Amid[3], const double* Aobs, bool obs_start,
+                    double dt) {
   const size_t gb = (size_t)c->ncell * c->npts * sizeof(double);
   const bool pc = c->opt.pc && (c->opt.hartree || c->opt.xc);
   if (pc) {
@@ -738,7 +770,7 @@ tdks_status pc_step(tdks_ctx* c, void* u, const double Amid[3], const double Aen
       Phase ph(c, 5);
       TDKS_CUDA(cudaMemsetAsync(c->d_rho_tmp, 0, gb, c->stream));
     }
-    TDKS_TRY(orbital_kernel(c, 1, u, u, Amid, dt, c->d_rho_tmp, 0));
+    TDKS_TRY(orbital_kernel(c, 1, u, u, Amid, dt, c->d_rho_tmp, 0, obs_start ? Aobs : nullptr, obs_start));
     TDKS_TRY(hxc(c, c->d_rho_tmp, c->d_vpred));
     // corrector: T4 with the mid-point potential
     TDKS_TRY(set_step_potential(c, 0.5, c->d_vpred, 0.5));
@@ -749,8 +781,9 @@ tdks_status pc_step(tdks_ctx* c, void* u, const double Amid[3], const double Aen
     Phase ph(c, 5);
     TDKS_CUDA(cudaMemsetAsync(c->d_rho, 0, gb, c->stream));
   }
-  // corrector; for periodic cells its last pass also forms the per-orbital current at t + dt
-  TDKS_TRY(orbital_kernel(c, 1, u, u, Amid, dt, c->d_rho, 1, c->grid.periodic ? Aend : nullptr));
+  // corrector; it also forms the per-orbital observables unless the predictor already did
+  const bool corr_obs = !(pc && obs_start);
+  TDKS_TRY(orbital_kernel(c, 1, u, u, Amid, dt, c->d_rho, 1, corr_obs ? Aobs : nullptr, obs_start));
   TDKS_TRY(hxc(c, c->d_rho, c->d_vhxc));
   if (pc) {   // the PC's own misfit, for scale
     TDKS_CUDA(launch_residual(c->d_vhxc, c->d_vpred, c->npts * c->ncell, c->d_resid, c->stream));
@@ -761,8 +794,8 @@ tdks_status pc_step(tdks_ctx* c, void* u, const double Amid[3], const double Aen
 
 // One step with a predicted V~(t+dt) in place of the predictor half-step.  Returns accepted = false
 // (and u restored) when the misfit exceeds the threshold.
-tdks_status predicted_step(tdks_ctx* c, void* u, const double Amid[3], const double Aend[3], double dt,
-                           bool* accepted) {
+tdks_status predicted_step(tdks_ctx* c, void* u, const double Amid[3], const double* Aobs, bool obs_start,
+                           double dt, bool* accepted) {
   const size_t gb = c->npts * sizeof(double);
   const size_t obytes = (size_t)c->nk * c->norb * c->npts * (is_f32(c) ? sizeof(float2) : sizeof(double2));
   const NNGrid g = nn_grid(c);
@@ -781,7 +814,7 @@ tdks_status predicted_step(tdks_ctx* c, void* u, const double Amid[3], const dou
     c->launches += 1;
   }
   TDKS_TRY(set_step_potential(c, 0.5, c->d_vpred, 0.5));
-  TDKS_TRY(orbital_kernel(c, 1, u, u, Amid, dt, c->d_rho, 1, c->grid.periodic ? Aend : nullptr));
+  TDKS_TRY(orbital_kernel(c, 1, u, u, Amid, dt, c->d_rho, 1, Aobs, obs_start));
   TDKS_TRY(hxc(c, c->d_rho, c->d_vnew));
   TDKS_CUDA(launch_residual(c->d_vnew, c->d_vpred, c->npts, c->d_resid, c->stream));
   c->launches += 1;
@@ -802,25 +835,37 @@ tdks_status tdks_step(tdks_ctx* c, void* u, double t, double dt) {
   TDKS_TRY(check_ctx(c));
   if (!u) return fail(TDKS_EINVAL, "null orbitals");
   if (!c->have_potential) return fail(TDKS_EINVAL, "call tdks_update_potential before tdks_step");
-  double Amid[3], Aend[3];
+  double Amid[3], Aend[3], Astart[3];
   field_at(c, t + 0.5 * dt, Amid);
   field_at(c, t + dt, Aend);
+  field_at(c, t, Astart);
+  // observables of the input state (J(t), dipole of rho(t)) or of the propagated one
+  const bool at_start = c->opt.obs_at_start != 0;
+  const double* Aobs = c->grid.periodic ? (at_start ? Astart : Aend) : nullptr;
+  if (at_start) {
+    Phase ph(c, 4);
+    TDKS_CUDA(launch_dipole(c->d_rho, c->d_rho0, c->grid.n, c->grid.h, c->grid.periodic,
+                            c->d_partials, c->red_blocks, c->d_step_obs, c->stream));   // cell 0
+    c->launches += 2;
+  }
   bool done = false;
   if (c->pred_mode != TDKS_PRED_PC && c->hist_count >= 4 && (c->opt.hartree || c->opt.xc))
-    TDKS_TRY(predicted_step(c, u, Amid, Aend, dt, &done));
-  if (!done) TDKS_TRY(pc_step(c, u, Amid, Aend, dt));
+    TDKS_TRY(predicted_step(c, u, Amid, Aobs, at_start, dt, &done));
+  if (!done) TDKS_TRY(pc_step(c, u, Amid, Aobs, at_start, dt));
   TDKS_TRY(hist_push(c, c->d_vhxc));
-  // observables at t + dt
   Phase ph(c, 4);
-  c->launches += c->grid.periodic ? 3 : 2;   // reduce_current (or memset) + dipole partial + final
+  c->launches += c->grid.periodic ? 1 : 0;   // reduce_current
   if (c->grid.periodic) {
     TDKS_CUDA(launch_reduce_current(c->d_orb_obs, c->nk, c->norb, c->d_kw, 1.0 / c->omega, 1,
                                     c->d_step_obs, c->stream, c->ncell));
   } else {
     TDKS_CUDA(cudaMemsetAsync(c->d_step_obs, 0, 3 * sizeof(double), c->stream));
   }
-  TDKS_CUDA(launch_dipole(c->d_rho, c->d_rho0, c->grid.n, c->grid.h, c->grid.periodic,
-                          c->d_partials, c->red_blocks, c->d_step_obs, c->stream));   // cell 0
+  if (!at_start) {
+    TDKS_CUDA(launch_dipole(c->d_rho, c->d_rho0, c->grid.n, c->grid.h, c->grid.periodic,
+                            c->d_partials, c->red_blocks, c->d_step_obs, c->stream));   // cell 0
+    c->launches += 2;
+  }
   return TDKS_OK;
 }
 
@@ -866,7 +911,7 @@ tdks_status tdks_ms_step(tdks_ctx* c, void* u, double t, double dt) {
   const double zero[3] = {0.0, 0.0, 0.0};
   c->cur_ap_mid = c->d_ap_mid;
   c->cur_ap_end = c->d_ap_end;
-  const tdks_status st = pc_step(c, u, zero, zero, dt);
+  const tdks_status st = pc_step(c, u, zero, zero, false, dt);   // per-cell A' via cur_ap_*
   c->cur_ap_mid = c->cur_ap_end = nullptr;
   TDKS_TRY(st);
   Phase ph(c, 4);

@@ -71,6 +71,8 @@ struct OrbArgs {
   int nx, ny, nz, npts, periodic;
   T c2x[5], c2y[5], c2z[5]; // -1/2 * FD2[m] / h^2
   T d1x[4], d1y[4], d1z[4]; // FD1[m] / h
+  T ry, rz;                 // hx^2/hy^2, hx^2/hz^2: c2y = ry c2x, c2z = rz c2x
+  T ty, tz;                 // hx/hy, hx/hz: d1y = ty d1x, d1z = tz d1x
   int norb, nk;
   const double* kpts;       // [nk*3]
   double Ap[3];             // A'(t) added to every k
@@ -97,8 +99,9 @@ struct OrbArgs {
   int nsp;                  // unique sphere points
   const int* sp_pt;         // [nsp] global index
   const int* sp_off;        // [nsp+1]
-  double Ap_obs[3];         // A' for the fused observables of the final state
+  double Ap_obs[3];         // A' for the fused observables
   double* obs;              // nullable: per-orbital {norm, jloc[3], jnl[3], 0}
+  int obs_at_start;         // 1: observables of the input orbital (first stage), 0: of the output
   // batches of cells (multiscale): orbitals are [ncell][nk][norb], potentials [ncell][npts]
   int ncell;                // cells in the batch (1 for a single system)
   long long vstride;        // offset of a cell's potential (0: one potential shared by all)
@@ -118,7 +121,8 @@ bool smem_orbital_fits(int nz, int pstride, int nsph, int natom);
 template <typename T>
 bool smem_orbital_needs_scratch(int nz, int pstride, int nsph, int natom);
 // threads per column (nseg) and planes per thread (zlen) for the cell kernels
-void cell_split(int nx, int ny, int nz, int* nseg, int* zlen);
+// column segments of the cell kernels; elem_bytes = bytes of one complex value (8: FP32, 16: FP64)
+void cell_split(int nx, int ny, int nz, int elem_bytes, int* nseg, int* zlen);
 
 // Large isolated grids (k_tile.cu): one Horner stage / H application per launch.
 template <typename T>

@@ -46,7 +46,7 @@ class ProjectorC(C.Structure):
 
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("hartree", C.c_int), ("xc", C.c_int), ("pc", C.c_int),
-                ("ncell", C.c_int)]
+                ("ncell", C.c_int), ("obs_at_start", C.c_int)]
 
 
 class Obs(C.Structure):
@@ -60,8 +60,8 @@ class Obs(C.Structure):
                     residual=self.residual, fallbacks=self.fallbacks)
 
 
-NPHASE = 6
-PHASES = ("taylor_predictor", "taylor_corrector", "hpsi", "hartree_xc", "observables", "other")
+NPHASE = 7
+PHASES = ("taylor_predictor", "taylor_corrector", "hpsi", "hartree_xc", "observables", "other", "stencil_kernel")
 
 
 class Stats(C.Structure):
@@ -152,7 +152,8 @@ class Context:
     norb, field.  Orbitals are torch tensors [nk, norb, nz, ny, nx], complex128 (f64) or
     complex64 (f32), on the current CUDA device."""
 
-    def __init__(self, system, precision="f64", hartree=True, xc=True, pc=True, stream=None, ncell=1):
+    def __init__(self, system, precision="f64", hartree=True, xc=True, pc=True, stream=None, ncell=1,
+                 obs_at_start=False):
         import torch
         lib = load_library()
         self.lib = lib
@@ -168,7 +169,8 @@ class Context:
         pr = ProjectorC(system.proj.E_s, system.proj.E_p, system.proj.r_cut, system.proj.width)
         kp = np.ascontiguousarray(np.asarray(system.kpts, np.float64).reshape(-1))
         kw = np.ascontiguousarray(np.asarray(system.kw, np.float64))
-        opts = Options(TDKS_F64 if precision == "f64" else TDKS_F32, int(hartree), int(xc), int(pc), int(ncell))
+        opts = Options(TDKS_F64 if precision == "f64" else TDKS_F32, int(hartree), int(xc), int(pc), int(ncell),
+                       int(bool(obs_at_start)))
         self.ncell = int(ncell)
         if stream is None:
             stream = torch.cuda.current_stream()
