@@ -7,6 +7,8 @@
 // stages there, and writes the lines back in natural order.
 #include <cuda_runtime.h>
 
+#include "ff.cuh"
+#include "grid_sum.cuh"
 #include "tdks_internal.h"
 
 namespace tdks {
@@ -299,10 +301,12 @@ __global__ void k_f32(const double* __restrict__ s, float* __restrict__ d, long 
 
 constexpr int kRedThreads = 256;
 
-__global__ void __launch_bounds__(kRedThreads) k_dipole_partial(
+// d_mu = -sum r_mu (rho - rho0) dV and N = sum rho dV, summed over all CTAs by grid_sum;
+// out[3..5] = d, out[6] = N.
+__global__ void __launch_bounds__(kRedThreads) k_dipole(
     const double* __restrict__ rho, const double* __restrict__ rho0, int nx, int ny, int nz,
-    double hx, double hy, double hz, int periodic, double* partials) {
-  __shared__ double red[kRedThreads / 32][4];
+    double hx, double hy, double hz, int periodic, double* partials, unsigned* ticket, double* out) {
+  __shared__ double tot[4];
   double acc[4] = {0, 0, 0, 0};
   const long long total = (long long)nx * ny * nz;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
@@ -316,25 +320,10 @@ __global__ void __launch_bounds__(kRedThreads) k_dipole_partial(
     acc[2] += coord(z, nz, hz, periodic) * dr;
     acc[3] += rho[i];
   }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int j = 0; j < 4; ++j) {
-    double v = acc[j];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) red[warp][j] = v;
-  }
-  __syncthreads();
+  if (!grid_sum<4>(acc, partials, ticket, tot)) return;
   if (threadIdx.x < 4) {
-    double v = 0;
-    for (int w = 0; w < kRedThreads / 32; ++w) v += red[w][threadIdx.x];
-    partials[blockIdx.x * 4 + threadIdx.x] = v;
-  }
-}
-
-__global__ void k_dipole_final(const double* partials, int nblocks, double dV, double* out) {
-  if (threadIdx.x < 4) {
-    double v = 0;
-    for (int b = 0; b < nblocks; ++b) v += partials[b * 4 + threadIdx.x];
-    out[3 + threadIdx.x] = (threadIdx.x < 3) ? -v * dV : v * dV;   // out[3..5] = d, out[6] = N
+    const double dV = hx * hy * hz;
+    out[3 + threadIdx.x] = (threadIdx.x < 3) ? -tot[threadIdx.x] * dV : tot[threadIdx.x] * dV;
   }
 }
 
@@ -390,13 +379,36 @@ __global__ void __launch_bounds__(256) k_orbital_dots(const C* __restrict__ u, c
   }
 }
 
-__global__ void k_fold_density(const float* __restrict__ r32, int nk, int npts,
-                               const double* __restrict__ kw, double* __restrict__ rho, long long n) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const long long cell = i / npts, p = i - cell * npts;
-    double acc = 0.0;
-    for (int k = 0; k < nk; ++k) acc += kw[k] * (double)r32[(cell * nk + k) * npts + p];
-    rho[i] = acc;
+// rho[cell][p] = sum_k w_k rho32[cell][k][p].  Four lanes share a point, each summing every fourth
+// k in float-float (ff.cuh) with the weights split into float pairs once per CTA, then the lanes add
+// their sums by shuffles; one FP64 conversion per point.
+constexpr int kFoldLanes = 4;
+__global__ void __launch_bounds__(256) k_fold_density(const float* __restrict__ r32, int nk, int npts,
+                                                      const double* __restrict__ kw, double* __restrict__ rho,
+                                                      long long n) {
+  extern __shared__ float wsplit[];                 // [nk][2]
+  for (int k = threadIdx.x; k < nk; k += blockDim.x) {
+    const double w = kw[k];
+    const float wh = (float)w;
+    wsplit[2 * k] = wh;
+    wsplit[2 * k + 1] = (float)(w - (double)wh);
+  }
+  __syncthreads();
+  const long long total = n * kFoldLanes;
+  for (long long t0 = (long long)blockIdx.x * blockDim.x; t0 < total; t0 += (long long)gridDim.x * blockDim.x) {
+    const long long t = t0 + threadIdx.x;           // every lane of the warp runs the iteration
+    const bool act = t < total;
+    const long long i = act ? t / kFoldLanes : 0;
+    const int part = (int)(t % kFoldLanes);
+    FF acc{0.f, 0.f};
+    if (act) {
+      const long long cell = i / npts, p = i - cell * npts;
+      for (int k = part; k < nk; k += kFoldLanes)
+        acc = ff_add(acc, ff_mul(wsplit[2 * k], wsplit[2 * k + 1], r32[(cell * nk + k) * npts + p]));
+    }
+#pragma unroll
+    for (int o = 1; o < kFoldLanes; o <<= 1) acc = ff_add(acc, ff_shfl_xor(acc, o));
+    if (act && part == 0) rho[i] = ff_to_double(acc);
   }
 }
 
@@ -517,10 +529,10 @@ cudaError_t launch_f32_from_f64(const double* src, float* dst, size_t count, cud
 }
 
 cudaError_t launch_dipole(const double* rho, const double* rho0, const int n[3], const double h[3],
-                          int periodic, double* partials, int nblocks, double* out, cudaStream_t s) {
-  k_dipole_partial<<<nblocks, kRedThreads, 0, s>>>(rho, rho0, n[0], n[1], n[2], h[0], h[1], h[2],
-                                                   periodic, partials);
-  k_dipole_final<<<1, 32, 0, s>>>(partials, nblocks, h[0] * h[1] * h[2], out);
+                          int periodic, double* partials, unsigned* ticket, double* out, cudaStream_t s) {
+  const long long total = (long long)n[0] * n[1] * n[2];
+  k_dipole<<<grid_sum_blocks(total, kRedThreads), kRedThreads, 0, s>>>(rho, rho0, n[0], n[1], n[2], h[0], h[1],
+                                                                       h[2], periodic, partials, ticket, out);
   return cudaGetLastError();
 }
 
@@ -571,7 +583,8 @@ cudaError_t launch_ms_current(const double* step_obs, int ncell, int m0, double*
 cudaError_t launch_fold_density(const float* rho32, int nk, int npts, const double* kw, double* rho,
                                 cudaStream_t s, int ncell) {
   const long long n = (long long)npts * ncell;
-  k_fold_density<<<grid_for(n, 256), 256, 0, s>>>(rho32, nk, npts, kw, rho, n);
+  k_fold_density<<<grid_for(n * kFoldLanes, 256), 256, 2 * sizeof(float) * (size_t)nk, s>>>(rho32, nk, npts, kw,
+                                                                                            rho, n);
   return cudaGetLastError();
 }
 

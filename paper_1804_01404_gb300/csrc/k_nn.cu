@@ -9,6 +9,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include "grid_sum.cuh"
 #include "tdks_internal.h"
 
 namespace tdks {
@@ -42,37 +43,58 @@ __device__ __forceinline__ float dsilu(float y) {
   return s * (1.0f + y * (1.0f - s));
 }
 
-// y[co][p] = b[co] + sum_{kk, ci} W[co][ci][kk] x[ci][nb(p, kk)];  a = bf16(SiLU(y)) if ACT
-template <int CIN, int COUT, bool ACT>
+// y[co][p] = b[co] + sum_{kk, ci} W[co][ci][kk] x[ci][nb(p, kk)];  a = bf16(SiLU(y)) if ACT.
+// Each point is shared by G = (COUT / COP) * CIS adjacent lanes: a lane forms COP outputs over
+// CIN / CIS input channels, and lanes that split the input channels add their sums by shuffles.
+// (A point per thread would leave most SMs idle on the grids of these cells.)
+template <int CIN, int COUT, bool ACT, int COP, int CIS>
 __global__ void __launch_bounds__(256) k_nn_fwd(NNGrid g, const bf16* __restrict__ x,
                                                 const float* __restrict__ W, const float* __restrict__ b,
                                                 float* __restrict__ y, bf16* __restrict__ a) {
+  constexpr int GO = COUT / COP, G = GO * CIS, CIP = CIN / CIS;
+  static_assert(GO * COP == COUT && CIP * CIS == CIN && 32 % G == 0, "lane split");
   __shared__ float Ws[27][CIN][COUT];
   for (int i = threadIdx.x; i < COUT * CIN * 27; i += blockDim.x) {
     const int co = i / (CIN * 27), r = i % (CIN * 27), ci = r / 27, kk = r % 27;
     Ws[kk][ci][co] = W[i];
   }
   __syncthreads();
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < g.npts; p += gridDim.x * blockDim.x) {
+  const long long total = (long long)g.npts * G;
+  for (long long t0 = (long long)blockIdx.x * blockDim.x; t0 < total; t0 += (long long)gridDim.x * blockDim.x) {
+    const long long t = t0 + threadIdx.x;           // every lane of the warp runs the iteration
+    const bool act = t < total;
+    const int p = act ? (int)(t / G) : 0;
+    const int gi = (int)(t % G);
+    const int og = gi % GO, cs = gi / GO;           // output group, input-channel split
     int px, py, pz;
     coords(g, p, px, py, pz);
-    float acc[COUT];
+    float acc[COP];
 #pragma unroll
-    for (int co = 0; co < COUT; ++co) acc[co] = b[co];
+    for (int o = 0; o < COP; ++o) acc[o] = (cs == 0) ? b[og * COP + o] : 0.f;
     for (int kk = 0; kk < 27; ++kk) {
-      const int q = nb_index(g, px, py, pz, kk % 3 - 1, (kk / 3) % 3 - 1, kk / 9 - 1);
+      const int q = act ? nb_index(g, px, py, pz, kk % 3 - 1, (kk / 3) % 3 - 1, kk / 9 - 1) : -1;
       if (q < 0) continue;
 #pragma unroll
-      for (int ci = 0; ci < CIN; ++ci) {
+      for (int c = 0; c < CIP; ++c) {
+        const int ci = cs * CIP + c;
         const float xv = __bfloat162float(x[(size_t)ci * g.npts + q]);
 #pragma unroll
-        for (int co = 0; co < COUT; ++co) acc[co] = fmaf(Ws[kk][ci][co], xv, acc[co]);
+        for (int o = 0; o < COP; ++o) acc[o] = fmaf(Ws[kk][ci][og * COP + o], xv, acc[o]);
       }
     }
+    if (CIS > 1) {
 #pragma unroll
-    for (int co = 0; co < COUT; ++co) {
-      y[(size_t)co * g.npts + p] = acc[co];
-      if (ACT) a[(size_t)co * g.npts + p] = __float2bfloat16(silu(acc[co]));
+      for (int sft = GO; sft < G; sft <<= 1)
+#pragma unroll
+        for (int o = 0; o < COP; ++o) acc[o] += __shfl_xor_sync(0xffffffffu, acc[o], sft);
+    }
+    if (act && cs == 0) {
+#pragma unroll
+      for (int o = 0; o < COP; ++o) {
+        const int co = og * COP + o;
+        y[(size_t)co * g.npts + p] = acc[o];
+        if (ACT) a[(size_t)co * g.npts + p] = __float2bfloat16(silu(acc[o]));
+      }
     }
   }
 }
@@ -207,34 +229,26 @@ __global__ void k_nn_round(const float* __restrict__ p, float* __restrict__ wq, 
 
 // Differences D1 = V0 - V1, D2 = V0 - 2 V1 + V2, D3 = V0 - 3 V1 + 3 V2 - V3 (formed in FP64).
 // stats = {s1, s2, s3, mean V0, s_V}: root mean squares of D1, D2, D3 and V0 - mean V0, each
-// floored at 1e-13 rms(V0); per-thread FP32 partials combined in FP64.
-__global__ void __launch_bounds__(1024) k_nn_stats(const double* __restrict__ V0, const double* __restrict__ V1,
-                                                   const double* __restrict__ V2, const double* __restrict__ V3,
-                                                   int n, double* stats) {
-  __shared__ double r[5][1024];
-  float a1 = 0, a2 = 0, a3 = 0, b = 0, c = 0;
-  for (int p = threadIdx.x; p < n; p += blockDim.x) {
-    const float d1 = (float)(V0[p] - V1[p]);
-    const float d2 = (float)(V0[p] - 2.0 * V1[p] + V2[p]);
-    const float d3 = (float)(V0[p] - 3.0 * V1[p] + 3.0 * V2[p] - V3[p]);
-    const float v = (float)V0[p];
-    a1 += d1 * d1; a2 += d2 * d2; a3 += d3 * d3; b += v; c += v * v;
+// floored at 1e-13 rms(V0); summed over all CTAs by grid_sum.
+__global__ void __launch_bounds__(256) k_nn_stats(const double* __restrict__ V0, const double* __restrict__ V1,
+                                                  const double* __restrict__ V2, const double* __restrict__ V3,
+                                                  int n, double* partials, unsigned* ticket, double* stats) {
+  __shared__ double tot[5];
+  double acc[5] = {0, 0, 0, 0, 0};
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    const double v0 = V0[p], v1 = V1[p], v2 = V2[p], v3 = V3[p];
+    const double d1 = v0 - v1, d2 = d1 - (v1 - v2), d3 = d2 - ((v1 - v2) - (v2 - v3));
+    acc[0] += d1 * d1; acc[1] += d2 * d2; acc[2] += d3 * d3; acc[3] += v0; acc[4] += v0 * v0;
   }
-  r[0][threadIdx.x] = a1; r[1][threadIdx.x] = a2; r[2][threadIdx.x] = a3; r[3][threadIdx.x] = b; r[4][threadIdx.x] = c;
-  __syncthreads();
-  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
-    if (threadIdx.x < h)
-      for (int k = 0; k < 5; ++k) r[k][threadIdx.x] += r[k][threadIdx.x + h];
-    __syncthreads();
-  }
+  if (!grid_sum<5>(acc, partials, ticket, tot)) return;
   if (threadIdx.x == 0) {
-    const double mean = r[3][0] / n;
-    const double fl = 1e-13 * sqrt(r[4][0] / n) + 1e-300;
-    stats[0] = fmax(sqrt(r[0][0] / n), fl);
-    stats[1] = fmax(sqrt(r[1][0] / n), fl);
-    stats[2] = fmax(sqrt(r[2][0] / n), fl);
+    const double mean = tot[3] / n;
+    const double fl = 1e-13 * sqrt(tot[4] / n) + 1e-300;
+    stats[0] = fmax(sqrt(tot[0] / n), fl);
+    stats[1] = fmax(sqrt(tot[1] / n), fl);
+    stats[2] = fmax(sqrt(tot[2] / n), fl);
     stats[3] = mean;
-    stats[4] = fmax(sqrt(fmax(r[4][0] / n - mean * mean, 0.0)), fl);
+    stats[4] = fmax(sqrt(fmax(tot[4] / n - mean * mean, 0.0)), fl);
   }
 }
 
@@ -272,24 +286,18 @@ __global__ void k_nn_apply(const double* __restrict__ V0, const double* __restri
   }
 }
 
-// res = ||Vnew - Vpred||_2 / ||Vnew||_2
-__global__ void __launch_bounds__(1024) k_residual(const double* __restrict__ Vnew, const double* __restrict__ Vpred,
-                                                   int n, double* res) {
-  __shared__ double r0[1024], r1[1024];
-  float a = 0, b = 0;                  // per-thread partials in FP32, combined in FP64
-  for (int p = threadIdx.x; p < n; p += blockDim.x) {
-    const float d = (float)(Vnew[p] - Vpred[p]);
-    const float v = (float)Vnew[p];
-    a += d * d;
-    b += v * v;
+// res = ||Vnew - Vpred||_2 / ||Vnew||_2, summed over all CTAs by grid_sum
+__global__ void __launch_bounds__(256) k_residual(const double* __restrict__ Vnew, const double* __restrict__ Vpred,
+                                                  int n, double* partials, unsigned* ticket, double* res) {
+  __shared__ double tot[2];
+  double acc[2] = {0, 0};
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+    const double d = Vnew[p] - Vpred[p], v = Vnew[p];
+    acc[0] += d * d;
+    acc[1] += v * v;
   }
-  r0[threadIdx.x] = a; r1[threadIdx.x] = b;
-  __syncthreads();
-  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
-    if (threadIdx.x < h) { r0[threadIdx.x] += r0[threadIdx.x + h]; r1[threadIdx.x] += r1[threadIdx.x + h]; }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) *res = sqrt(r0[0] / fmax(r1[0], 1e-300));
+  if (!grid_sum<2>(acc, partials, ticket, tot)) return;
+  if (threadIdx.x == 0) *res = sqrt(tot[0] / fmax(tot[1], 1e-300));
 }
 
 int blocks_for(int n) {
@@ -305,10 +313,11 @@ inline const bf16* B16(const unsigned short* p) { return reinterpret_cast<const 
 inline bf16* B16(unsigned short* p) { return reinterpret_cast<bf16*>(p); }
 
 cudaError_t nn_forward(const NNBuffers& B, const NNGrid& g, cudaStream_t s) {
-  const int nb = blocks_for(g.npts);
-  k_nn_fwd<4, 16, true><<<nb, 256, 0, s>>>(g, B16(B.x0), B.wq + kNNOff[0], B.wq + kNNOff[1], B.y1, B16(B.a1));
-  k_nn_fwd<16, 16, true><<<nb, 256, 0, s>>>(g, B16(B.a1), B.wq + kNNOff[2], B.wq + kNNOff[3], B.y2, B16(B.a2));
-  k_nn_fwd<16, 1, false><<<nb, 256, 0, s>>>(g, B16(B.a2), B.wq + kNNOff[4], B.wq + kNNOff[5], B.out, nullptr);
+  // four lanes per point in every layer (4 outputs each; the last layer splits its 16 inputs)
+  const int nb = blocks_for(4 * g.npts);
+  k_nn_fwd<4, 16, true, 4, 1><<<nb, 256, 0, s>>>(g, B16(B.x0), B.wq + kNNOff[0], B.wq + kNNOff[1], B.y1, B16(B.a1));
+  k_nn_fwd<16, 16, true, 4, 1><<<nb, 256, 0, s>>>(g, B16(B.a1), B.wq + kNNOff[2], B.wq + kNNOff[3], B.y2, B16(B.a2));
+  k_nn_fwd<16, 1, false, 1, 4><<<nb, 256, 0, s>>>(g, B16(B.a2), B.wq + kNNOff[4], B.wq + kNNOff[5], B.out, nullptr);
   return cudaGetLastError();
 }
 
@@ -349,7 +358,7 @@ cudaError_t nn_round_weights(const NNBuffers& B, cudaStream_t s) {
 
 cudaError_t nn_inputs(const NNBuffers& B, const NNGrid& g, const double* V0, const double* V1,
                       const double* V2, const double* V3, const double* Vnext, cudaStream_t s) {
-  k_nn_stats<<<1, 1024, 0, s>>>(V0, V1, V2, V3, g.npts, B.stats);
+  k_nn_stats<<<grid_sum_blocks(g.npts, 256), 256, 0, s>>>(V0, V1, V2, V3, g.npts, B.red, B.ticket, B.stats);
   k_nn_pack<<<blocks_for(g.npts), 256, 0, s>>>(V0, V1, V2, V3, Vnext, B.stats, g.npts, B16(B.x0), B.target);
   return cudaGetLastError();
 }
@@ -360,8 +369,9 @@ cudaError_t nn_apply(const NNBuffers& B, const NNGrid& g, const double* V0, cons
   return cudaGetLastError();
 }
 
-cudaError_t launch_residual(const double* Vnew, const double* Vpred, int n, double* res, cudaStream_t s) {
-  k_residual<<<1, 1024, 0, s>>>(Vnew, Vpred, n, res);
+cudaError_t launch_residual(const double* Vnew, const double* Vpred, int n, double* partials, unsigned* ticket,
+                            double* res, cudaStream_t s) {
+  k_residual<<<grid_sum_blocks(n, 256), 256, 0, s>>>(Vnew, Vpred, n, partials, ticket, res);
   return cudaGetLastError();
 }
 

@@ -18,6 +18,7 @@
 
 #include <type_traits>
 
+#include "ff.cuh"
 #include "tdks_internal.h"
 
 namespace tdks {
@@ -245,21 +246,8 @@ __device__ __forceinline__ void set_phases(const OrbArgs<T>& a, typename Cplx<T>
 }
 
 // Accumulators of the per-orbital sums.  FP64 arithmetic runs at a small fraction of the FP32 rate
-// on this GPU, so FP32 kernels accumulate in compensated float-float form (an unevaluated sum
-// hi + lo, added with Knuth's two-sum), which keeps about 44 significant bits; FP64 kernels use double.
-struct FF {
-  float hi, lo;
-};
-__device__ __forceinline__ FF ff_add(FF a, FF b) {
-  const float s = a.hi + b.hi;
-  const float bb = s - a.hi;
-  const float e = (a.hi - (s - bb)) + (b.hi - bb) + a.lo + b.lo;
-  const float h = s + e;
-  return FF{h, e - (h - s)};
-}
-__device__ __forceinline__ FF ff_shfl_xor(FF a, int o) {
-  return FF{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
-}
+// on this GPU, so FP32 kernels accumulate in compensated float-float form (ff.cuh); FP64 kernels
+// use double.
 template <typename T> struct Acc;
 template <> struct Acc<float> {
   using type = FF;

@@ -82,7 +82,8 @@ struct tdks_ctx {
   // observables
   double* d_orb_obs = nullptr;   // [nk*norb*8]
   double* d_step_obs = nullptr;  // [8]: J[3], d[3], N
-  double* d_partials = nullptr;
+  double* d_partials = nullptr;   // [304][4] grid_sum partials (residual, dipole)
+  unsigned* d_ticket = nullptr;   // grid_sum ticket, zero between launches
   int red_blocks = 0;
   std::vector<void*> allocs;
   // potential history (V_Hxc at t, t-dt, t-2dt, t-3dt) and the predictor
@@ -635,6 +636,8 @@ tdks_status tdks_init(const tdks_grid* grid, const tdks_cell* cell, const tdks_a
   if ((s = dalloc(c, &c->d_step_obs, 8 * (size_t)c->ncell)) != TDKS_OK) return bail(s);
   c->red_blocks = 304;
   if ((s = dalloc(c, &c->d_partials, (size_t)c->red_blocks * 4)) != TDKS_OK) return bail(s);
+  if ((s = dalloc(c, &c->d_ticket, 1)) != TDKS_OK) return bail(s);
+  cudaMemsetAsync(c->d_ticket, 0, sizeof(unsigned), c->stream);
   cudaMemsetAsync(c->d_step_obs, 0, 8 * sizeof(double) * c->ncell, c->stream);
 
   // FFT set-up: periodic transforms are n^3, isolated ones (2n)^3 (zero padding)
@@ -786,7 +789,7 @@ tdks_status pc_step(tdks_ctx* c, void* u, const double Amid[3], const double* Ao
   TDKS_TRY(orbital_kernel(c, 1, u, u, Amid, dt, c->d_rho, 1, corr_obs ? Aobs : nullptr, obs_start));
   TDKS_TRY(hxc(c, c->d_rho, c->d_vhxc));
   if (pc) {   // the PC's own misfit, for scale
-    TDKS_CUDA(launch_residual(c->d_vhxc, c->d_vpred, c->npts * c->ncell, c->d_resid, c->stream));
+    TDKS_CUDA(launch_residual(c->d_vhxc, c->d_vpred, c->npts * c->ncell, c->d_partials, c->d_ticket, c->d_resid, c->stream));
     c->launches += 1;
   }
   return TDKS_OK;
@@ -816,7 +819,7 @@ tdks_status predicted_step(tdks_ctx* c, void* u, const double Amid[3], const dou
   TDKS_TRY(set_step_potential(c, 0.5, c->d_vpred, 0.5));
   TDKS_TRY(orbital_kernel(c, 1, u, u, Amid, dt, c->d_rho, 1, Aobs, obs_start));
   TDKS_TRY(hxc(c, c->d_rho, c->d_vnew));
-  TDKS_CUDA(launch_residual(c->d_vnew, c->d_vpred, c->npts, c->d_resid, c->stream));
+  TDKS_CUDA(launch_residual(c->d_vnew, c->d_vpred, c->npts, c->d_partials, c->d_ticket, c->d_resid, c->stream));
   c->launches += 1;
   TDKS_CUDA(cudaMemcpyAsync(c->h_resid, c->d_resid, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   TDKS_CUDA(cudaStreamSynchronize(c->stream));
@@ -845,8 +848,8 @@ tdks_status tdks_step(tdks_ctx* c, void* u, double t, double dt) {
   if (at_start) {
     Phase ph(c, 4);
     TDKS_CUDA(launch_dipole(c->d_rho, c->d_rho0, c->grid.n, c->grid.h, c->grid.periodic,
-                            c->d_partials, c->red_blocks, c->d_step_obs, c->stream));   // cell 0
-    c->launches += 2;
+                            c->d_partials, c->d_ticket, c->d_step_obs, c->stream));   // cell 0
+    c->launches += 1;
   }
   bool done = false;
   if (c->pred_mode != TDKS_PRED_PC && c->hist_count >= 4 && (c->opt.hartree || c->opt.xc))
@@ -863,8 +866,8 @@ tdks_status tdks_step(tdks_ctx* c, void* u, double t, double dt) {
   }
   if (!at_start) {
     TDKS_CUDA(launch_dipole(c->d_rho, c->d_rho0, c->grid.n, c->grid.h, c->grid.periodic,
-                            c->d_partials, c->red_blocks, c->d_step_obs, c->stream));   // cell 0
-    c->launches += 2;
+                            c->d_partials, c->d_ticket, c->d_step_obs, c->stream));   // cell 0
+    c->launches += 1;
   }
   return TDKS_OK;
 }
@@ -956,8 +959,7 @@ tdks_status tdks_observables(tdks_ctx* c, const void* u, const double Ap[3], tdk
   if (Ap && c->grid.periodic) for (int a = 0; a < 3; ++a) A[a] = Ap[a];
   TDKS_TRY(density(c, u, c->d_rho_tmp));
   const double* r0 = c->have_rho0 ? c->d_rho0 : c->d_rho_tmp;
-  TDKS_CUDA(launch_dipole(c->d_rho_tmp, r0, c->grid.n, c->grid.h, c->grid.periodic, c->d_partials,
-                          c->red_blocks, c->d_step_obs, c->stream));
+  TDKS_CUDA(launch_dipole(c->d_rho_tmp, r0, c->grid.n, c->grid.h, c->grid.periodic, c->d_partials, c->d_ticket, c->d_step_obs, c->stream));
   TDKS_TRY(orbital_observables(c, u, A));
   const size_t no = (size_t)c->nk * c->norb;
   std::vector<double> ob(no * 8);
@@ -1074,6 +1076,9 @@ tdks_status tdks_nn_init(tdks_ctx* c, unsigned long long seed) {
     TDKS_TRY(dalloc(c, &B.wq, kNNParams));
     TDKS_TRY(dalloc(c, &B.stats, 8));
     TDKS_TRY(dalloc(c, &B.loss, 1));
+    TDKS_TRY(dalloc(c, &B.red, 304 * 5));
+    TDKS_TRY(dalloc(c, &B.ticket, 1));
+    TDKS_CUDA(cudaMemsetAsync(B.ticket, 0, sizeof(unsigned), c->stream));
   }
   std::vector<float> p(kNNParams, 0.0f);
   const int fan[3] = {4 * 27, 16 * 27, 16 * 27};

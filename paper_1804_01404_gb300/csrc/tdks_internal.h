@@ -178,6 +178,8 @@ struct NNBuffers {
   float *params, *grad, *m, *v, *wq;              // [kNNParams]; wq = BF16-rounded params
   double* stats;                                  // rms D1, rms D2, rms D3, mean V0, rms(V0 - mean)
   double* loss;                                   // accumulator
+  double* red;                                    // [304][5] grid_sum partials of the statistics
+  unsigned* ticket;                               // grid_sum ticket (zero between launches)
 };
 int nn_part_blocks(int npts);
 cudaError_t nn_inputs(const NNBuffers& B, const NNGrid& g, const double* V0, const double* V1,
@@ -190,7 +192,9 @@ cudaError_t nn_round_weights(const NNBuffers& B, cudaStream_t s);
 // vpred: mode 0 = 2 V0 - V1, 1 = cubic 4 V0 - 6 V1 + 4 V2 - V3, 2 = cubic + s3 * out
 cudaError_t nn_apply(const NNBuffers& B, const NNGrid& g, const double* V0, const double* V1,
                      const double* V2, const double* V3, int mode, double* vpred, cudaStream_t s);
-cudaError_t launch_residual(const double* Vnew, const double* Vpred, int n, double* res, cudaStream_t s);
+// partials: [304][2] doubles, ticket: one unsigned that is zero between launches (grid_sum)
+cudaError_t launch_residual(const double* Vnew, const double* Vpred, int n, double* partials, unsigned* ticket,
+                            double* res, cudaStream_t s);
 
 // Grid kernels (k_grid.cu)
 // batch = number of consecutive [dims2][dims1][dims0] arrays transformed together
@@ -226,8 +230,9 @@ cudaError_t launch_hockney_kernel(double2* g, const int m[3], const int n[3], co
 cudaError_t launch_real_part(const double2* src, double* dst, size_t count, double scale,
                              cudaStream_t s);
 // dipole: partials then final (deterministic two-pass); out[3..5] = d, out[6] = int rho
+// out[3..5] = dipole, out[6] = electron count; partials: [304][4] doubles, ticket: grid_sum ticket
 cudaError_t launch_dipole(const double* rho, const double* rho0, const int n[3], const double h[3],
-                          int periodic, double* partials, int nblocks, double* out,
+                          int periodic, double* partials, unsigned* ticket, double* out,
                           cudaStream_t s);
 // J from per-orbital observables; writes out[c*8 + 0..2] = J of cell c (zero if isolated)
 cudaError_t launch_reduce_current(const double* orb_obs, int nk, int norb, const double* kw,
