@@ -438,6 +438,13 @@ def hpsi_cluster(dev, reps=10, norb=256):
            "stencil_kernel_ms": s_ms, "stencil_kernel_GBps": nbytes / (s_ms * 1e-3) / 1e9,
            "stencil_kernel_frac_of_measured_hbm": nbytes / (s_ms * 1e-3) / 1e9 / pk["hbm_gbs"],
            "stencil_kernel_traffic": measured_traffic("k_tile_f32_mode0")}
+    # density + Hockney Poisson (192^3 FFTs, FP64) + LDA exchange of the same orbitals
+    ctx.stats(reset=True)
+    for _ in range(3):
+        ctx.update_potential(u)
+    torch.cuda.synchronize()
+    sx = ctx.stats(reset=True)
+    res["update_potential_hartree_xc_ms"] = sx["ms"]["hartree_xc"] / max(1, sx["calls"]["hartree_xc"])
     variant, tune_ms = ctx.tile_variant()
     names = ["k_tile<float> (1 point/thread, 3 CTAs/SM)", "k_tile<float> (1 point/thread, 2 CTAs/SM) + L2 prefetch",
              "k_tile4<8> (2x2 points/thread, 8 consumer warps) + L2 prefetch"]

@@ -34,30 +34,69 @@ __device__ __forceinline__ double2 twd(const double2* tw, int t, int n, int dir)
   return w;
 }
 
+// One radix-R step of a Stockham transform: inputs src[jb + r n/R] times the stage twiddles
+// exp(dir 2 pi i r k / (Ns R)), then an R-point DFT with exp(dir 2 pi i r m / R), outputs to
+// dst[(jb / Ns) Ns R + k + m Ns].  The small DFTs of R = 2, 3, 4, 5 are written out in their
+// standard split forms (sums and differences of conjugate pairs), so a radix-4 step costs three
+// complex products and a radix-5 step four instead of R^2.
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return double2{a.x + b.x, a.y + b.y}; }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return double2{a.x - b.x, a.y - b.y}; }
+__device__ __forceinline__ double2 cscale(double s, double2 a) { return double2{s * a.x, s * a.y}; }
+// dir * i * a
+__device__ __forceinline__ double2 cmul_di(int dir, double2 a) {
+  return dir > 0 ? double2{-a.y, a.x} : double2{a.y, -a.x};
+}
+
 template <int R>
 __device__ __forceinline__ void butterfly(const double2* __restrict__ src, double2* __restrict__ dst,
                                           int n, int Ns, int jb, const double2* tw, int dir) {
   const int nr = n / R;
   const int k = jb % Ns;
+  const int tstep = n / (Ns * R);                 // r k tstep < n: no reduction needed
   double2 v[R];
-  const int tstep = n / (Ns * R);
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     double2 x = src[jb + r * nr];
-    if (r > 0) x = cmul(x, twd(tw, r * k * tstep, n, dir));
+    if (r > 0 && k > 0) {
+      double2 w = tw[r * k * tstep];
+      if (dir > 0) w.y = -w.y;
+      x = cmul(x, w);
+    }
     v[r] = x;
   }
   const int base = (jb / Ns) * Ns * R + k;
-#pragma unroll
-  for (int m = 0; m < R; ++m) {
-    double2 y = v[0];
-#pragma unroll
-    for (int r = 1; r < R; ++r) {
-      const double2 t = cmul(v[r], twd(tw, r * m * nr, n, dir));
-      y.x += t.x;
-      y.y += t.y;
-    }
-    dst[base + m * Ns] = y;
+  if (R == 2) {
+    dst[base] = cadd(v[0], v[1]);
+    dst[base + Ns] = csub(v[0], v[1]);
+  } else if (R == 3) {
+    constexpr double h3 = 0.86602540378443864676;  // sin(2 pi / 3)
+    const double2 t = cadd(v[1], v[2]);
+    const double2 sm = csub(v[0], cscale(0.5, t));
+    const double2 d = cmul_di(dir, cscale(h3, csub(v[1], v[2])));
+    dst[base] = cadd(v[0], t);
+    dst[base + Ns] = cadd(sm, d);
+    dst[base + 2 * Ns] = csub(sm, d);
+  } else if (R == 4) {
+    const double2 a = cadd(v[0], v[2]), b = csub(v[0], v[2]);
+    const double2 c = cadd(v[1], v[3]), d = cmul_di(dir, csub(v[1], v[3]));
+    dst[base] = cadd(a, c);
+    dst[base + Ns] = cadd(b, d);
+    dst[base + 2 * Ns] = csub(a, c);
+    dst[base + 3 * Ns] = csub(b, d);
+  } else {                                          // R == 5
+    constexpr double c1 = 0.30901699437494742410, c2 = -0.80901699437494742410;   // cos(2 pi/5), cos(4 pi/5)
+    constexpr double s1 = 0.95105651629515357212, s2 = 0.58778525229247312917;    // sin(2 pi/5), sin(4 pi/5)
+    const double2 a1 = cadd(v[1], v[4]), a2 = cadd(v[2], v[3]);
+    const double2 b1 = csub(v[1], v[4]), b2 = csub(v[2], v[3]);
+    const double2 t1 = cadd(v[0], cadd(cscale(c1, a1), cscale(c2, a2)));
+    const double2 t2 = cadd(v[0], cadd(cscale(c2, a1), cscale(c1, a2)));
+    const double2 u1 = cmul_di(dir, cadd(cscale(s1, b1), cscale(s2, b2)));
+    const double2 u2 = cmul_di(dir, csub(cscale(s2, b1), cscale(s1, b2)));
+    dst[base] = cadd(v[0], cadd(a1, a2));
+    dst[base + Ns] = cadd(t1, u1);
+    dst[base + 4 * Ns] = csub(t1, u1);
+    dst[base + 2 * Ns] = cadd(t2, u2);
+    dst[base + 3 * Ns] = csub(t2, u2);
   }
 }
 
@@ -434,8 +473,11 @@ cudaError_t launch_fft_axis(double2* data, const int dims[3], int axis, int dir,
   if (axis == 0) { inner = 1; outer = dims[0]; estride = 1; }
   else if (axis == 1) { inner = dims[0]; outer = (long long)dims[0] * dims[1]; estride = dims[0]; }
   else { inner = (long long)dims[0] * dims[1]; outer = inner * dims[2]; estride = inner; }
+  // lines per CTA: at most 16 and what 96 KB of shared memory holds, and few enough that the
+  // lines spread over all SMs (two CTAs per SM), since each SM's FP64 rate bounds its share
   int LB = 16;
   while (LB > 1 && (size_t)(2 * LB + 1) * n * sizeof(double2) > 96 * 1024) LB /= 2;
+  while (LB > 1 && nlines / LB < 2 * 152) LB /= 2;
   const size_t smem = (size_t)(2 * LB + 1) * n * sizeof(double2);
   cudaError_t e = cudaFuncSetAttribute(k_fft_lines, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
