@@ -52,7 +52,7 @@ typedef enum {
   TDKS_EINVAL = 1,        /* invalid argument (null pointer, bad size, inconsistent grid/cell) */
   TDKS_ENOMEM = 2,        /* device or host allocation failed */
   TDKS_ECUDA = 3,         /* a CUDA runtime call or kernel launch failed */
-  TDKS_ETIMEOUT = 4,      /* a device-side wait gave up (reserved for persistent kernels) */
+  TDKS_ETIMEOUT = 4,      /* a device-side wait of a tile kernel gave up (see tdks_set_wait_test) */
   TDKS_ENONFINITE = 5,    /* the norm monitor found a NaN/Inf orbital */
   TDKS_EUNSUPPORTED = 6   /* a valid request this build does not implement (e.g. grid too large) */
 } tdks_status;
@@ -260,6 +260,17 @@ tdks_status tdks_query(const tdks_ctx* ctx, int* npts, int* nk, int* norb, int* 
  * Errors: EUNSUPPORTED if the context does not use the tile kernels or the variant needs FP32;
  * EINVAL for set outside -1..2. */
 tdks_status tdks_tile_variant(tdks_ctx* ctx, int set, int* variant, float* tune_ms);
+
+/* Test hook of the device-side timeout path (no counterpart in the paper).  The tile kernels of large
+ * isolated grids wait on shared-memory barriers for their TMA plane copies; every wait gives up after
+ * a number of polls, sets the context's error word and the kernel returns (tdks_check then reports
+ * TDKS_ETIMEOUT and clears the word; the context stays usable).
+ *   wait_limit : polls per wait, 0 restores the default (2^22).  The final wait for the kernel's own
+ *                copies in flight always uses the default, so no copy lands after its CTA exits.
+ *   stop_after : >= 0 makes the copy producer issue only that many planes, so the stencil warps wait
+ *                for a plane that never arrives and must give up; -1 (default) issues all planes.
+ * Errors: EINVAL for wait_limit < 0. */
+tdks_status tdks_set_wait_test(tdks_ctx* ctx, long long wait_limit, int stop_after);
 
 /* Hartree + exchange potential of a density without allocating device memory.
  * For callers that cannot call cudaMalloc -- code running while a CUDA graph is captured, hosts whose

@@ -64,8 +64,8 @@ __device__ __forceinline__ bool volatile_abort(int* flag) {
 }
 
 // bounded wait; returns false on timeout
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
-  for (long long i = 0; i < kSpinLimit; ++i)
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, long long limit = kSpinLimit) {
+  for (long long i = 0; i < limit; ++i)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
@@ -94,19 +94,24 @@ __device__ __forceinline__ void tma_prefetch_4d(const CUtensorMap* map, int c0, 
 // pf planes later, so DRAM sees enough requests in flight without more shared memory.  On a
 // timed-out wait it raises the abort flag and the error word; in every case it waits (bounded) for
 // its own most recent copies before returning, so no copy is in flight when the CTA exits.
+// limit: polls per wait (the drain at the end always uses the full kSpinLimit, so copies in flight
+// land before the CTA exits).  stop_after >= 0 issues only that many planes (the timeout test: the
+// consumers then wait for a plane that never comes and must give up).
 template <typename C, int NSx, int SXx, int SYx>
 __device__ __forceinline__ void tile_producer(const CUtensorMap* map, const CUtensorMap* pmap, int pf,
                                               C* ring, unsigned long long* full,
                                               unsigned long long* empty, int* abort_flag, int* err,
-                                              int x0, int y0, int orb, int nplanes) {
+                                              int x0, int y0, int orb, int nplanes, long long limit,
+                                              int stop_after) {
   constexpr int E = sizeof(C) / 8;
   constexpr unsigned kSlotBytes = SXx * SYx * sizeof(C);
   const int nz = nplanes - 8;
   int issued = 0;
   bool ok = true;
   for (int j = 0; j < nplanes; ++j) {
+    if (stop_after >= 0 && j >= stop_after) break;
     const int slot = j % NSx;
-    if (j >= NSx && !mbar_wait(&empty[slot], ((j / NSx) - 1) & 1)) { ok = false; break; }
+    if (j >= NSx && !mbar_wait(&empty[slot], ((j / NSx) - 1) & 1, limit)) { ok = false; break; }
     if (volatile_abort(abort_flag)) { ok = false; break; }
     if (pf > 0) {
       const int zp = j + pf - 4;                   // plane of the ring source pf ahead
@@ -179,7 +184,7 @@ __global__ void __launch_bounds__(NT, MINB) k_tile(const __grid_constant__ CUten
   if (warp == NCW) {
     if (lane == 0)
       tile_producer<C, NS, SX, SY>(&vmap, MODE == 1 ? &pmap : nullptr, a.prefetch, ring, full, empty, &s_abort,
-                                   a.err, x0, y0, orb, nplanes);
+                                   a.err, x0, y0, orb, nplanes, a.wait_limit, a.stop_after);
     return;
   }
 
@@ -205,7 +210,7 @@ __global__ void __launch_bounds__(NT, MINB) k_tile(const __grid_constant__ CUten
   C w[RPT][9];
   // window planes j = 0..7 (z = -4..3); planes 0..3 are released right away
   for (int j = 0; j < 8; ++j) {
-    if (!timeout && !mbar_wait(&full[j % NS], (j / NS) & 1)) timeout = true;
+    if (!timeout && !mbar_wait(&full[j % NS], (j / NS) & 1, a.wait_limit)) timeout = true;
 #pragma unroll
     for (int r = 0; r < RPT; ++r) w[r][j] = ring[(j % NS) * SX * SY + own[r]];
     if (j < 4) {
@@ -235,7 +240,7 @@ __global__ void __launch_bounds__(NT, MINB) k_tile(const __grid_constant__ CUten
     if (timeout || volatile_abort(&s_abort)) break;
     const int jc = z + 4;
     const int jn = z + 8;
-    if (!mbar_wait(&full[jn % NS], (jn / NS) & 1)) { timeout = true; break; }
+    if (!mbar_wait(&full[jn % NS], (jn / NS) & 1, a.wait_limit)) { timeout = true; break; }
     const C* sbase = ring + (jc % NS) * SX * SY;
 #pragma unroll
     for (int r = 0; r < RPT; ++r) {
@@ -324,7 +329,7 @@ __global__ void __launch_bounds__(B4<NCW>::NT, B4<NCW>::MINB) k_tile4(const __gr
   if (warp == NCW) {
     if (lane == 0)
       tile_producer<float2, NS, SX, SY>(&vmap, MODE == 1 ? &pmap : nullptr, a.prefetch, ring, full, empty,
-                                        &s_abort, a.err, x0, y0, orb, nz + 8);
+                                        &s_abort, a.err, x0, y0, orb, nz + 8, a.wait_limit, a.stop_after);
     return;
   }
 
@@ -343,7 +348,7 @@ __global__ void __launch_bounds__(B4<NCW>::NT, B4<NCW>::MINB) k_tile4(const __gr
   bool timeout = false;
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
-    if (!timeout && !mbar_wait(&full[j % NS], (j / NS) & 1)) timeout = true;
+    if (!timeout && !mbar_wait(&full[j % NS], (j / NS) & 1, a.wait_limit)) timeout = true;
     const float4 p0 = lds4(ring + (j % NS) * SS + o0), p1 = lds4(ring + (j % NS) * SS + o1);
     w0a[j] = lo(p0); w0b[j] = hi(p0); w1a[j] = lo(p1); w1b[j] = hi(p1);
     if (j < 4) {
@@ -377,7 +382,7 @@ __global__ void __launch_bounds__(B4<NCW>::NT, B4<NCW>::MINB) k_tile4(const __gr
       const int jc = z + 4, jn = z + 8;
       // register slots of planes z .. z+8 (z multiple-of-9 aligned at zb)
       const int rc = (k + 4) % 9, rn = (k + 8) % 9;
-      if (!mbar_wait(&full[jn % NS], (jn / NS) & 1)) { timeout = true; break; }
+      if (!mbar_wait(&full[jn % NS], (jn / NS) & 1, a.wait_limit)) { timeout = true; break; }
       {
         const float2* sn = ring + (jn % NS) * SS;
         const float4 p0 = lds4(sn + o0), p1 = lds4(sn + o1);

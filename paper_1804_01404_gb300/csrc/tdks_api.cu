@@ -69,6 +69,8 @@ struct tdks_ctx {
   // large isolated grids (tile kernels): two Horner buffers and the projection coefficients
   bool tiled = false;
   int tile_variant[2] = {0, 0};  // stencil variant of the tiled path for H v / Horner stages
+  long long wait_limit = 1LL << 22;  // polls per device-side wait of the tile kernels
+  int stop_after = -1;              // timeout test: planes the tile producer issues (-1: all)
   float tile_ms[2][kTileVariants] = {{-1.f, -1.f, -1.f}, {-1.f, -1.f, -1.f}};
   void *d_bufA = nullptr, *d_bufB = nullptr, *d_ec = nullptr;
   int* d_err = nullptr;
@@ -267,6 +269,8 @@ TileArgs<T> make_tile_args(const tdks_ctx* c, const T* V) {
   a.ry = (T)((c->grid.h[0] * c->grid.h[0]) / (c->grid.h[1] * c->grid.h[1]));
   a.rz = (T)((c->grid.h[0] * c->grid.h[0]) / (c->grid.h[2] * c->grid.h[2]));
   a.variant = c->tile_variant[0];
+  a.wait_limit = c->wait_limit;
+  a.stop_after = c->stop_after;
   a.err = c->d_err;
   a.natom = c->natom; a.nsp = c->nsp;
   a.atom_off = c->d_atom_off; a.sph_idx = c->d_sph_idx;
@@ -1219,6 +1223,14 @@ tdks_status tdks_tile_variant(tdks_ctx* c, int set, int* variant, float* tune_ms
   if (tune_ms)
     for (int m = 0; m < 2; ++m)
       for (int v = 0; v < kTileVariants; ++v) tune_ms[m * kTileVariants + v] = c->tile_ms[m][v];
+  return TDKS_OK;
+}
+
+tdks_status tdks_set_wait_test(tdks_ctx* c, long long wait_limit, int stop_after) {
+  TDKS_TRY(check_ctx(c));
+  if (wait_limit < 0) return fail(TDKS_EINVAL, "wait_limit must be >= 0");
+  c->wait_limit = wait_limit > 0 ? wait_limit : (1LL << 22);
+  c->stop_after = stop_after < 0 ? -1 : stop_after;
   return TDKS_OK;
 }
 

@@ -137,6 +137,8 @@ struct TileArgs {
   T ry, rz;                 // hx^2 / hy^2 and hx^2 / hz^2 (c2y = ry c2x, c2z = rz c2x)
   T coef;                   // dt / m (mode 1)
   int* err;                 // device error word (TDKS_ETIMEOUT on a timed-out wait)
+  long long wait_limit;     // polls per mbarrier wait before giving up (TDKS_ETIMEOUT)
+  int stop_after;           // >= 0: the producer issues only this many planes (timeout test)
   int variant;              // stencil variant (kernel + L2 prefetch), see launch_tile_stage
   int prefetch;             // L2 prefetch distance in planes (set by launch_tile_stage)
   // projectors (q = 0)

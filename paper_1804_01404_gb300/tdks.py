@@ -113,6 +113,7 @@ def load_library(path: str = LIB_PATH):
         "tdks_stats_read": [vp, C.POINTER(Stats), i],
         "tdks_query": [vp, C.POINTER(i), C.POINTER(i), C.POINTER(i), C.POINTER(i), C.POINTER(i)],
         "tdks_tile_variant": [vp, i, C.POINTER(i), C.POINTER(C.c_float)],
+        "tdks_set_wait_test": [vp, C.c_longlong, i],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -302,6 +303,10 @@ class Context:
         ms = (C.c_float * 6)()
         _check(self.lib.tdks_tile_variant(self.ctx, int(set), v, ms))
         return [v[0], v[1]], [[float(x) for x in ms[:3]], [float(x) for x in ms[3:]]]
+
+    def set_wait_test(self, wait_limit=0, stop_after=-1):
+        """Timeout-path test hook (tdks_set_wait_test); defaults restore normal operation."""
+        _check(self.lib.tdks_set_wait_test(self.ctx, int(wait_limit), int(stop_after)))
 
     def query(self):
         v = [C.c_int() for _ in range(5)]

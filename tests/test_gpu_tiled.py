@@ -139,3 +139,29 @@ def test_tile_variant_rules():
         c64.tile_variant(2)
     with pytest.raises(TdksError):
         _ctx(S, "f32").tile_variant(3)
+
+
+def test_wait_timeout_is_reported_and_context_recovers():
+    """The failure path of the tile kernels without a GPU fault: the copy producer stops after two
+    planes, the stencil warps wait for a third that never arrives, give up after a short poll limit
+    and report TDKS_ETIMEOUT through tdks_check; the same context then computes H u correctly."""
+    from paper_1804_01404_gb300.tdks import TdksError
+    psi = W.initial_orbitals(S, 7)
+    for precision, tol in (("f32", 2e-5), ("f64", 1e-12)):
+        ctx = _ctx(S, precision)
+        ud = _dev(psi, precision)
+        ctx.update_potential(ud)
+        hu = torch.empty_like(ud)
+        ctx.set_wait_test(wait_limit=2000, stop_after=2)
+        ctx.hpsi(ud, hu)
+        with pytest.raises(TdksError) as err:
+            ctx.check()
+        assert err.value.status == 4                        # TDKS_ETIMEOUT
+        ctx.check()                                         # the error word was cleared
+        ctx.set_wait_test()
+        ctx.hpsi(ud, hu)
+        ctx.check()
+        tabs = O.projector_tables(S)
+        V = O.local_potential(S) + O.hxc(S, O.density(S, psi))
+        ref = O.hpsi(S, tabs, V, np.zeros(3), psi[0])
+        assert _rel(hu.cpu().numpy()[0].astype(np.complex128), ref) < tol
