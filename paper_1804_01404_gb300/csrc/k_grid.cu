@@ -119,9 +119,10 @@ __device__ void butterfly_generic(const double2* __restrict__ src, double2* __re
   }
 }
 
-// data: 3D array [dims2][dims1][dims0]; transform along `axis` for all lines.
+// data: 3D array [dims2][dims1][dims0]; transform lines along one axis.  Line l starts at
+// (l % cnt_lo) * s_lo + (l / cnt_lo) * s_hi (the two other coordinates), elements estride apart.
 __global__ void __launch_bounds__(kFftThreads) k_fft_lines(double2* data, int n, int nlines, int LB,
-                                                          long long inner, long long outer,
+                                                          long long cnt_lo, long long s_lo, long long s_hi,
                                                           long long estride, int xaxis,
                                                           const double2* __restrict__ tw_g,
                                                           FftPlanArgs plan, int dir) {
@@ -137,7 +138,7 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_lines(double2* data, int n,
     int j, e;
     if (xaxis) { j = idx / n; e = idx - j * n; } else { e = idx / nl; j = idx - e * nl; }
     const long long l = l0 + j;
-    const long long start = (l / inner) * outer + (l % inner);
+    const long long start = (l % cnt_lo) * s_lo + (l / cnt_lo) * s_hi;
     b0[j * n + e] = data[start + e * estride];
   }
   __syncthreads();
@@ -167,7 +168,7 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_lines(double2* data, int n,
     int j, e;
     if (xaxis) { j = idx / n; e = idx - j * n; } else { e = idx / nl; j = idx - e * nl; }
     const long long l = l0 + j;
-    const long long start = (l / inner) * outer + (l % inner);
+    const long long start = (l % cnt_lo) * s_lo + (l / cnt_lo) * s_hi;
     data[start + e * estride] = src[j * n + e];
   }
 }
@@ -461,18 +462,23 @@ int grid_for(long long n, int threads) {
 }  // namespace
 
 cudaError_t launch_fft_axis(double2* data, const int dims[3], int axis, int dir, const double2* tw,
-                            const int* radices, int nrad, cudaStream_t s, int batch) {
+                            const int* radices, int nrad, cudaStream_t s, int batch, int lim_lo, int lim_hi) {
   const int n = dims[axis];
   if (nrad > kMaxRadices) return cudaErrorInvalidValue;
   FftPlanArgs plan;
   plan.nrad = nrad;
   for (int i = 0; i < nrad; ++i) plan.rad[i] = radices[i];
-  const long long total = (long long)dims[0] * dims[1] * dims[2] * batch;
-  const int nlines = (int)(total / n);
-  long long inner, outer, estride;
-  if (axis == 0) { inner = 1; outer = dims[0]; estride = 1; }
-  else if (axis == 1) { inner = dims[0]; outer = (long long)dims[0] * dims[1]; estride = dims[0]; }
-  else { inner = (long long)dims[0] * dims[1]; outer = inner * dims[2]; estride = inner; }
+  // the two other coordinates of a line: lo (faster) and hi; hi of the last axis runs over the batch
+  long long cnt_lo, cnt_hi, s_lo, s_hi, estride;
+  const long long d01 = (long long)dims[0] * dims[1];
+  if (axis == 0) { cnt_lo = dims[1]; cnt_hi = (long long)dims[2] * batch; s_lo = dims[0]; s_hi = d01; estride = 1; }
+  else if (axis == 1) { cnt_lo = dims[0]; cnt_hi = (long long)dims[2] * batch; s_lo = 1; s_hi = d01; estride = dims[0]; }
+  else { cnt_lo = d01; cnt_hi = batch; s_lo = 1; s_hi = d01 * dims[2]; estride = d01; }
+  // pruned transforms: only the lines with lo < lim_lo and hi < lim_hi (a zero-padded input, or
+  // an output of which only a corner is used)
+  const long long use_lo = (lim_lo > 0 && lim_lo < cnt_lo) ? lim_lo : cnt_lo;
+  const long long use_hi = (lim_hi > 0 && lim_hi < cnt_hi) ? lim_hi : cnt_hi;
+  const int nlines = (int)(use_lo * use_hi);
   // lines per CTA: at most 16 and what 96 KB of shared memory holds, and few enough that the
   // lines spread over all SMs (two CTAs per SM), since each SM's FP64 rate bounds its share
   int LB = 16;
@@ -483,7 +489,7 @@ cudaError_t launch_fft_axis(double2* data, const int dims[3], int axis, int dir,
                                        (int)smem);
   if (e != cudaSuccess) return e;
   const int grid = (nlines + LB - 1) / LB;
-  k_fft_lines<<<grid, kFftThreads, smem, s>>>(data, n, nlines, LB, inner, outer, estride,
+  k_fft_lines<<<grid, kFftThreads, smem, s>>>(data, n, nlines, LB, use_lo, s_lo, s_hi, estride,
                                               axis == 0 ? 1 : 0, tw, plan, dir);
   return cudaGetLastError();
 }

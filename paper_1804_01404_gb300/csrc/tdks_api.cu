@@ -392,6 +392,24 @@ tdks_status fft3d(tdks_ctx* c, int dir) {
   return TDKS_OK;
 }
 
+// Zero-padded convolution of an isolated grid (Hockney): the density occupies the n^3 corner of
+// the (2n)^3 box and only that corner of the result is used, so the forward x-pass skips the lines
+// with y >= n or z >= n (all zero), the forward y-pass those with z >= n, and the inverse passes
+// mirror this (y-pass: z < n; x-pass: y < n and z < n): 3.5 full passes of work instead of 6.
+tdks_status fft3d_padded(tdks_ctx* c, int dir) {
+  const int* n = c->grid.n;
+  const int order[3] = {0, 1, 2};
+  for (int i = 0; i < 3; ++i) {
+    const int ax = dir < 0 ? order[i] : order[2 - i];
+    const int lo = ax == 0 ? n[1] : 0;             // x-lines: y < n; y-lines: all x
+    const int hi = ax == 2 ? 0 : n[2];             // x- and y-lines: z < n
+    TDKS_CUDA(launch_fft_axis(c->d_fft, c->m, ax, dir, c->d_tw[ax], c->rad[ax].data(),
+                              (int)c->rad[ax].size(), c->stream, 1, lo, hi));
+  }
+  c->launches += 3;
+  return TDKS_OK;
+}
+
 // vhxc = V_H[rho] + V_x[rho]
 tdks_status hxc(tdks_ctx* c, const double* rho, double* vhxc) {
   Phase ph(c, 3);
@@ -401,14 +419,16 @@ tdks_status hxc(tdks_ctx* c, const double* rho, double* vhxc) {
   const int ms[3] = {c->m[0], c->m[1], c->m[2] * c->ncell};
   if (c->opt.hartree) {
     TDKS_CUDA(launch_pack_real(rho, ns, c->d_fft, ms, c->stream));
-    TDKS_TRY(fft3d(c, -1));
     if (c->grid.periodic) {
+      TDKS_TRY(fft3d(c, -1));
       TDKS_CUDA(launch_poisson_scale_periodic(c->d_fft, c->m, c->grid.h, c->stream, c->ncell));
+      TDKS_TRY(fft3d(c, +1));
     } else {
+      TDKS_TRY(fft3d_padded(c, -1));
       const double npad = (double)c->m[0] * c->m[1] * c->m[2];
       TDKS_CUDA(launch_scale_by_real(c->d_fft, c->d_ghat, c->dV / npad, (size_t)npad, c->stream));
+      TDKS_TRY(fft3d_padded(c, +1));
     }
-    TDKS_TRY(fft3d(c, +1));
   }
   TDKS_CUDA(launch_hxc_epilogue(c->d_fft, ms, rho, ns, 1.0, c->opt.hartree, c->opt.xc,
                                 vhxc, c->stream));

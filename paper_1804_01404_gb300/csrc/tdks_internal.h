@@ -200,9 +200,11 @@ cudaError_t launch_residual(const double* Vnew, const double* Vpred, int n, doub
 
 // Grid kernels (k_grid.cu)
 // batch = number of consecutive [dims2][dims1][dims0] arrays transformed together
+// lim_lo / lim_hi > 0: transform only the lines whose two other coordinates (lo: the faster of
+// them, hi: the slower, batch included for the last axis) are below the limits
 cudaError_t launch_fft_axis(double2* data, const int dims[3], int axis, int dir,
                             const double2* tw, const int* radices, int nrad, cudaStream_t s,
-                            int batch = 1);
+                            int batch = 1, int lim_lo = 0, int lim_hi = 0);
 cudaError_t launch_pack_real(const double* src, const int n[3], double2* dst, const int m[3],
                              cudaStream_t s);
 cudaError_t launch_poisson_scale_periodic(double2* data, const int n[3], const double h[3],
