@@ -417,11 +417,14 @@ __global__ void __launch_bounds__(kNTof<T>()) k_cell(OrbArgs<T> a, typename Cplx
   q[2] = (T)(a.kpts[3 * k + 2] + ap[2]);
   const T diag0 = a.c2x[0] + a.c2y[0] + a.c2z[0] + T(0.5) * (q[0] * q[0] + q[1] * q[1] + q[2] * q[2]);
 
-  // load the orbital (pad elements zero), phases
+  // load the orbital (pad elements zero), phases; a predicted step also keeps a copy of its input
+  // (the fallback restores it), written here while the values pass through
+  C* bk = a.backup ? a.backup + (size_t)orb * a.npts : nullptr;
   for (int i = threadIdx.x; i < vsz; i += blockDim.x) {
     const int z = i / ps, r = i - z * ps;
     const C u = (r < nxy) ? psi[z * nxy + r] : C{0, 0};
     L.v[i] = u;
+    if (bk && r < nxy) bk[z * nxy + r] = u;
     if (DBUF) L.nxt[i] = C{0, 0};
   }
   // wave vector of the observables: k + A'_obs (OBS 1: end of the step; OBS 2: its start)

@@ -97,6 +97,7 @@ struct tdks_ctx {
   double* d_resid = nullptr;     // device residual
   double* h_resid = nullptr;     // pinned host copy
   void* d_backup = nullptr;      // orbitals at t (predicted steps)
+  void* cur_backup = nullptr;    // set while the corrector of a predicted step writes the backup
   double fallbacks = 0, last_resid = 0;
   bool nn_ready = false;
   NNBuffers nn{};
@@ -181,6 +182,7 @@ OrbArgs<T> make_args(const tdks_ctx* c, const void* in, void* out, const T* V, c
   a.vstride = c->ncell > 1 ? c->npts : 0;
   a.Ap_cell = c->cur_ap_mid;
   a.Ap_obs_cell = c->cur_ap_end;
+  a.backup = static_cast<C*>(c->cur_backup);
   if (sizeof(T) == 8) {
     a.sph_beta = (const T*)c->d_beta64; a.sph_d = (const T*)c->d_d64; a.atomE = (const T*)c->d_E64;
   } else {
@@ -836,12 +838,17 @@ tdks_status predicted_step(tdks_ctx* c, void* u, const double Amid[3], const dou
     }
     TDKS_CUDA(nn_apply(c->nn, g, hist_slot(c, 0), hist_slot(c, 1), hist_slot(c, 2), hist_slot(c, 3),
                        net ? 2 : 1, c->d_vpred, c->stream));
-    TDKS_CUDA(cudaMemcpyAsync(c->d_backup, u, obytes, cudaMemcpyDeviceToDevice, c->stream));
+    // the shared-memory cell kernel writes the backup while it loads the orbitals; the tile path
+    // copies it first
+    if (c->tiled) TDKS_CUDA(cudaMemcpyAsync(c->d_backup, u, obytes, cudaMemcpyDeviceToDevice, c->stream));
     TDKS_CUDA(cudaMemsetAsync(c->d_rho, 0, gb, c->stream));
     c->launches += 1;
   }
   TDKS_TRY(set_step_potential(c, 0.5, c->d_vpred, 0.5));
-  TDKS_TRY(orbital_kernel(c, 1, u, u, Amid, dt, c->d_rho, 1, Aobs, obs_start));
+  c->cur_backup = c->tiled ? nullptr : c->d_backup;
+  const tdks_status cs = orbital_kernel(c, 1, u, u, Amid, dt, c->d_rho, 1, Aobs, obs_start);
+  c->cur_backup = nullptr;
+  TDKS_TRY(cs);
   TDKS_TRY(hxc(c, c->d_rho, c->d_vnew));
   TDKS_CUDA(launch_residual(c->d_vnew, c->d_vpred, c->npts, c->d_partials, c->d_ticket, c->d_resid, c->stream));
   c->launches += 1;

@@ -102,6 +102,7 @@ struct OrbArgs {
   double Ap_obs[3];         // A' for the fused observables
   double* obs;              // nullable: per-orbital {norm, jloc[3], jnl[3], 0}
   int obs_at_start;         // 1: observables of the input orbital (first stage), 0: of the output
+  C* backup;                // nullable: copy of the input orbitals, written while they are loaded
   // batches of cells (multiscale): orbitals are [ncell][nk][norb], potentials [ncell][npts]
   int ncell;                // cells in the batch (1 for a single system)
   long long vstride;        // offset of a cell's potential (0: one potential shared by all)
