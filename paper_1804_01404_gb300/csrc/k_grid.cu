@@ -5,6 +5,8 @@
 // (4, 2, 3, 5, ...).  A CTA loads LB lines of the 3D array into shared memory -- for the y and z
 // axes the LB lines are consecutive in x, so every global access is coalesced -- runs all radix
 // stages there, and writes the lines back in natural order.
+#include <cstring>
+
 #include <cuda_runtime.h>
 
 #include "ff.cuh"
@@ -119,13 +121,42 @@ __device__ void butterfly_generic(const double2* __restrict__ src, double2* __re
   }
 }
 
+// Optional work fused into a line pass, so the Hartree + exchange solve takes five launches:
+//   load_real  (x pass, forward): lines are read from a real array [n2*batch][n1][n0], zero padded
+//              to the transform box, instead of from `data` (replaces a packing kernel);
+//   spectral   (z pass): after the forward transform each value is multiplied by the Poisson
+//              factor of its wave vector (periodic: 4 pi / G^2 / N, G = 0 dropped; isolated: the
+//              Hockney spectrum ghat times gscale) and the line is transformed back in place;
+//   store_epi  (x pass, inverse): instead of writing the line back, the inside points n0 x n1 x n2
+//              get vhxc = Re(value) + V_x(rho), with V_x = -(3 rho / pi)^(1/3) if xc.
+__device__ __forceinline__ double freq(int m, int n) { return (m <= (n - 1) / 2) ? m : m - n; }
+
+//   zero_from  (forward y and z passes of a padded box): elements e >= zero_from of every line are
+//              taken as zero instead of read (that part of the box was never written).
+struct FftHooks {
+  int load_real;
+  int zero_from;
+  const double* rsrc;
+  int n0, n1, n2;                 // unpadded extent of rsrc / vhxc (n2 per cell)
+  int spectral;                   // 0 none, 1 periodic, 2 Hockney
+  double L[3];
+  double inv_n;
+  const double* ghat;
+  double gscale;
+  int store_epi;
+  double* vhxc;
+  const double* rho;
+  int xc;
+};
+
 // data: 3D array [dims2][dims1][dims0]; transform lines along one axis.  Line l starts at
 // (l % cnt_lo) * s_lo + (l / cnt_lo) * s_hi (the two other coordinates), elements estride apart.
 __global__ void __launch_bounds__(kFftThreads) k_fft_lines(double2* data, int n, int nlines, int LB,
                                                           long long cnt_lo, long long s_lo, long long s_hi,
                                                           long long estride, int xaxis,
                                                           const double2* __restrict__ tw_g,
-                                                          FftPlanArgs plan, int dir) {
+                                                          FftPlanArgs plan, int dir, int m0, int m1, int m2,
+                                                          FftHooks hk) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double2* tw = reinterpret_cast<double2*>(smem_raw);
   double2* b0 = tw + n;
@@ -134,42 +165,98 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_lines(double2* data, int n,
   const int nl = min(LB, nlines - l0);
   for (int t = threadIdx.x; t < n; t += blockDim.x) tw[t] = tw_g[t];
   const int tot = nl * n;
+  // grid coordinates (x, y, z within the box, cell) of element e of local line j
+  auto coords3 = [&](int j, int e, int& x, int& y, int& z) {
+    const long long start = ((l0 + j) % cnt_lo) * s_lo + ((l0 + j) / cnt_lo) * s_hi + e * estride;
+    x = (int)(start % m0);
+    const long long r = start / m0;
+    y = (int)(r % m1);
+    z = (int)(r / m1);                            // includes the cell: z + cell * m2
+  };
   for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
     int j, e;
     if (xaxis) { j = idx / n; e = idx - j * n; } else { e = idx / nl; j = idx - e * nl; }
     const long long l = l0 + j;
     const long long start = (l % cnt_lo) * s_lo + (l / cnt_lo) * s_hi;
-    b0[j * n + e] = data[start + e * estride];
+    if (hk.load_real) {
+      int x, y, z;
+      coords3(j, e, x, y, z);
+      const int cell = z / m2, zc = z - cell * m2;
+      double v = 0.0;
+      if (x < hk.n0 && y < hk.n1 && zc < hk.n2)
+        v = hk.rsrc[(((long long)cell * hk.n2 + zc) * hk.n1 + y) * hk.n0 + x];
+      b0[j * n + e] = double2{v, 0.0};
+    } else if (hk.zero_from > 0 && e >= hk.zero_from) {
+      b0[j * n + e] = double2{0.0, 0.0};
+    } else {
+      b0[j * n + e] = data[start + e * estride];
+    }
   }
   __syncthreads();
   double2* src = b0;
   double2* dst = b1;
-  int Ns = 1;
-  for (int s = 0; s < plan.nrad; ++s) {
-    const int R = plan.rad[s];
-    const int nb = n / R;
-    for (int b = threadIdx.x; b < nl * nb; b += blockDim.x) {
-      const int j = b / nb, jb = b - j * nb;
-      const double2* sl = src + j * n;
-      double2* dl = dst + j * n;
-      switch (R) {
-        case 2: butterfly<2>(sl, dl, n, Ns, jb, tw, dir); break;
-        case 3: butterfly<3>(sl, dl, n, Ns, jb, tw, dir); break;
-        case 4: butterfly<4>(sl, dl, n, Ns, jb, tw, dir); break;
-        case 5: butterfly<5>(sl, dl, n, Ns, jb, tw, dir); break;
-        default: butterfly_generic(sl, dl, n, R, Ns, jb, tw, dir); break;
+  auto transform = [&](int d) {
+    int Ns = 1;
+    for (int s = 0; s < plan.nrad; ++s) {
+      const int R = plan.rad[s];
+      const int nb = n / R;
+      for (int b = threadIdx.x; b < nl * nb; b += blockDim.x) {
+        const int j = b / nb, jb = b - j * nb;
+        const double2* sl = src + j * n;
+        double2* dl = dst + j * n;
+        switch (R) {
+          case 2: butterfly<2>(sl, dl, n, Ns, jb, tw, d); break;
+          case 3: butterfly<3>(sl, dl, n, Ns, jb, tw, d); break;
+          case 4: butterfly<4>(sl, dl, n, Ns, jb, tw, d); break;
+          case 5: butterfly<5>(sl, dl, n, Ns, jb, tw, d); break;
+          default: butterfly_generic(sl, dl, n, R, Ns, jb, tw, d); break;
+        }
       }
+      __syncthreads();
+      double2* t = src; src = dst; dst = t;
+      Ns *= R;
+    }
+  };
+  transform(dir);
+  if (hk.spectral) {
+    for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+      const int j = idx / n, e = idx - j * n;
+      int x, y, z;
+      coords3(j, e, x, y, z);
+      double f;
+      if (hk.spectral == 1) {
+        const int zc = z % m2;
+        const double gx = 2.0 * kPi * freq(x, m0) / hk.L[0], gy = 2.0 * kPi * freq(y, m1) / hk.L[1],
+                     gz = 2.0 * kPi * freq(zc, m2) / hk.L[2];
+        const double g2 = gx * gx + gy * gy + gz * gz;
+        f = (g2 == 0.0) ? 0.0 : 4.0 * kPi / g2 * hk.inv_n;
+      } else {
+        f = hk.ghat[((long long)z * m1 + y) * m0 + x] * hk.gscale;
+      }
+      const double2 v = src[idx];
+      src[idx] = double2{v.x * f, v.y * f};
     }
     __syncthreads();
-    double2* t = src; src = dst; dst = t;
-    Ns *= R;
+    transform(-dir);
   }
   for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
     int j, e;
     if (xaxis) { j = idx / n; e = idx - j * n; } else { e = idx / nl; j = idx - e * nl; }
-    const long long l = l0 + j;
-    const long long start = (l % cnt_lo) * s_lo + (l / cnt_lo) * s_hi;
-    data[start + e * estride] = src[j * n + e];
+    if (hk.store_epi) {
+      int x, y, z;
+      coords3(j, e, x, y, z);
+      const int cell = z / m2, zc = z - cell * m2;
+      if (x < hk.n0 && y < hk.n1 && zc < hk.n2) {
+        const long long o = (((long long)cell * hk.n2 + zc) * hk.n1 + y) * hk.n0 + x;
+        double v = src[j * n + e].x;
+        if (hk.xc) v -= cbrt(3.0 * fmax(hk.rho[o], 0.0) / kPi);   // Slater exchange
+        hk.vhxc[o] = v;
+      }
+    } else {
+      const long long l = l0 + j;
+      const long long start = (l % cnt_lo) * s_lo + (l / cnt_lo) * s_hi;
+      data[start + e * estride] = src[j * n + e];
+    }
   }
 }
 
@@ -186,8 +273,6 @@ __global__ void k_pack_real(const double* __restrict__ src, int nx, int ny, int 
     dst[i] = double2{v, 0.0};
   }
 }
-
-__device__ __forceinline__ double freq(int m, int n) { return (m <= (n - 1) / 2) ? m : m - n; }
 
 __global__ void k_poisson_periodic(double2* data, int nx, int ny, int nz, double Lx, double Ly,
                                    double Lz, int batch) {
@@ -461,8 +546,21 @@ int grid_for(long long n, int threads) {
 
 }  // namespace
 
+cudaError_t launch_fft_axis_hooked(double2* data, const int dims[3], int axis, int dir, const double2* tw,
+                                   const int* radices, int nrad, cudaStream_t s, int batch, int lim_lo,
+                                   int lim_hi, const void* hooks);
+
 cudaError_t launch_fft_axis(double2* data, const int dims[3], int axis, int dir, const double2* tw,
                             const int* radices, int nrad, cudaStream_t s, int batch, int lim_lo, int lim_hi) {
+  FftHooks hk;
+  std::memset(&hk, 0, sizeof(hk));
+  return launch_fft_axis_hooked(data, dims, axis, dir, tw, radices, nrad, s, batch, lim_lo, lim_hi, &hk);
+}
+
+cudaError_t launch_fft_axis_hooked(double2* data, const int dims[3], int axis, int dir, const double2* tw,
+                                   const int* radices, int nrad, cudaStream_t s, int batch, int lim_lo,
+                                   int lim_hi, const void* hooks) {
+  const FftHooks& hk = *static_cast<const FftHooks*>(hooks);
   const int n = dims[axis];
   if (nrad > kMaxRadices) return cudaErrorInvalidValue;
   FftPlanArgs plan;
@@ -490,8 +588,46 @@ cudaError_t launch_fft_axis(double2* data, const int dims[3], int axis, int dir,
   if (e != cudaSuccess) return e;
   const int grid = (nlines + LB - 1) / LB;
   k_fft_lines<<<grid, kFftThreads, smem, s>>>(data, n, nlines, LB, use_lo, s_lo, s_hi, estride,
-                                              axis == 0 ? 1 : 0, tw, plan, dir);
+                                              axis == 0 ? 1 : 0, tw, plan, dir, dims[0], dims[1], dims[2], hk);
   return cudaGetLastError();
+}
+
+// Hartree (periodic 4 pi / G^2, or Hockney with the kernel spectrum ghat) + exchange in five line
+// passes: x forward from the real density, y forward, z forward-multiply-inverse, y inverse, and
+// x inverse writing vhxc (see FftHooks).
+cudaError_t launch_hartree_xc_fused(double2* work, const int m[3], const int n[3], int batch, int periodic,
+                                    const double h[3], const double* ghat, double gscale,
+                                    double2* const tw[3], const int* const rad[3], const int nrad[3],
+                                    const double* rho, int xc, double* vhxc, cudaStream_t s) {
+  FftHooks base;
+  std::memset(&base, 0, sizeof(base));
+  base.n0 = n[0]; base.n1 = n[1]; base.n2 = n[2];
+  const int lo_x = periodic ? 0 : n[1], hi_xy = periodic ? 0 : n[2];
+  cudaError_t e;
+  FftHooks h1 = base;
+  h1.load_real = 1;
+  h1.rsrc = rho;
+  if ((e = launch_fft_axis_hooked(work, m, 0, -1, tw[0], rad[0], nrad[0], s, batch, lo_x, hi_xy, &h1)) != cudaSuccess) return e;
+  // the padded box (isolated) is written only where the density is: the forward y and z passes
+  // read the rest as zeros
+  FftHooks h2 = base;
+  h2.zero_from = periodic ? 0 : n[1];
+  if ((e = launch_fft_axis_hooked(work, m, 1, -1, tw[1], rad[1], nrad[1], s, batch, 0, hi_xy, &h2)) != cudaSuccess) return e;
+  FftHooks h3 = base;
+  h3.zero_from = periodic ? 0 : n[2];
+  h3.spectral = periodic ? 1 : 2;
+  for (int a = 0; a < 3; ++a) h3.L[a] = m[a] * h[a];
+  h3.inv_n = 1.0 / ((double)m[0] * m[1] * m[2]);
+  h3.ghat = ghat;
+  h3.gscale = gscale;
+  if ((e = launch_fft_axis_hooked(work, m, 2, -1, tw[2], rad[2], nrad[2], s, batch, 0, 0, &h3)) != cudaSuccess) return e;
+  if ((e = launch_fft_axis_hooked(work, m, 1, +1, tw[1], rad[1], nrad[1], s, batch, 0, hi_xy, &base)) != cudaSuccess) return e;
+  FftHooks h5 = base;
+  h5.store_epi = 1;
+  h5.vhxc = vhxc;
+  h5.rho = rho;
+  h5.xc = xc;
+  return launch_fft_axis_hooked(work, m, 0, +1, tw[0], rad[0], nrad[0], s, batch, lo_x, hi_xy, &h5);
 }
 
 cudaError_t launch_pack_real(const double* src, const int n[3], double2* dst, const int m[3],

@@ -394,46 +394,25 @@ tdks_status fft3d(tdks_ctx* c, int dir) {
   return TDKS_OK;
 }
 
-// Zero-padded convolution of an isolated grid (Hockney): the density occupies the n^3 corner of
-// the (2n)^3 box and only that corner of the result is used, so the forward x-pass skips the lines
-// with y >= n or z >= n (all zero), the forward y-pass those with z >= n, and the inverse passes
-// mirror this (y-pass: z < n; x-pass: y < n and z < n): 3.5 full passes of work instead of 6.
-tdks_status fft3d_padded(tdks_ctx* c, int dir) {
-  const int* n = c->grid.n;
-  const int order[3] = {0, 1, 2};
-  for (int i = 0; i < 3; ++i) {
-    const int ax = dir < 0 ? order[i] : order[2 - i];
-    const int lo = ax == 0 ? n[1] : 0;             // x-lines: y < n; y-lines: all x
-    const int hi = ax == 2 ? 0 : n[2];             // x- and y-lines: z < n
-    TDKS_CUDA(launch_fft_axis(c->d_fft, c->m, ax, dir, c->d_tw[ax], c->rad[ax].data(),
-                              (int)c->rad[ax].size(), c->stream, 1, lo, hi));
-  }
-  c->launches += 3;
-  return TDKS_OK;
-}
-
 // vhxc = V_H[rho] + V_x[rho]
 tdks_status hxc(tdks_ctx* c, const double* rho, double* vhxc) {
   Phase ph(c, 3);
-  c->launches += c->opt.hartree ? 3 : 1;   // pack, scale, epilogue (+ 6 FFT passes counted in fft3d)
   // a batch of periodic cells is handled as one grid stacked along z for the pointwise kernels
   const int ns[3] = {c->grid.n[0], c->grid.n[1], c->grid.n[2] * c->ncell};
   const int ms[3] = {c->m[0], c->m[1], c->m[2] * c->ncell};
   if (c->opt.hartree) {
-    TDKS_CUDA(launch_pack_real(rho, ns, c->d_fft, ms, c->stream));
-    if (c->grid.periodic) {
-      TDKS_TRY(fft3d(c, -1));
-      TDKS_CUDA(launch_poisson_scale_periodic(c->d_fft, c->m, c->grid.h, c->stream, c->ncell));
-      TDKS_TRY(fft3d(c, +1));
-    } else {
-      TDKS_TRY(fft3d_padded(c, -1));
-      const double npad = (double)c->m[0] * c->m[1] * c->m[2];
-      TDKS_CUDA(launch_scale_by_real(c->d_fft, c->d_ghat, c->dV / npad, (size_t)npad, c->stream));
-      TDKS_TRY(fft3d_padded(c, +1));
-    }
+    // five line passes with the packing, the Poisson factor and the exchange epilogue fused in
+    const double npad = (double)c->m[0] * c->m[1] * c->m[2];
+    const int* rad[3] = {c->rad[0].data(), c->rad[1].data(), c->rad[2].data()};
+    const int nrad[3] = {(int)c->rad[0].size(), (int)c->rad[1].size(), (int)c->rad[2].size()};
+    TDKS_CUDA(launch_hartree_xc_fused(c->d_fft, c->m, c->grid.n, c->ncell, c->grid.periodic, c->grid.h,
+                                      c->d_ghat, c->dV / npad, c->d_tw, rad, nrad, rho, c->opt.xc,
+                                      vhxc, c->stream));
+    c->launches += 5;
+    return TDKS_OK;
   }
-  TDKS_CUDA(launch_hxc_epilogue(c->d_fft, ms, rho, ns, 1.0, c->opt.hartree, c->opt.xc,
-                                vhxc, c->stream));
+  c->launches += 1;
+  TDKS_CUDA(launch_hxc_epilogue(c->d_fft, ms, rho, ns, 1.0, 0, c->opt.xc, vhxc, c->stream));
   return TDKS_OK;
 }
 
