@@ -220,7 +220,7 @@ def gpu_arm(args, rank, world, local_rank):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     t0 = 200.0   # start inside the pulse (A' != 0)
 
-    # FP64 predictor-corrector reference current over the same steps (judge of the error bound)
+    # FP64 predictor-corrector reference current over the same steps (the reference of the error bound)
     nref = args.warmup + args.steps
     ctx64 = Context(s, precision="f64", obs_at_start=True)
     u64 = torch.from_numpy(psi0.astype(np.complex128)).to(dev)
