@@ -174,6 +174,9 @@ tdks_status tdks_ms_step(tdks_ctx* ctx, void* u_dev, double t, double dt);
 /* Copy A(X, t) and I(X, t) (host arrays of nX, either may be NULL); synchronises the stream. */
 tdks_status tdks_ms_read(tdks_ctx* ctx, double* A_host, double* I_host);
 
+/* Points of the Maxwell grid of the multiscale mode (0 before tdks_ms_init or a restored state). */
+tdks_status tdks_ms_size(const tdks_ctx* ctx, int* nX);
+
 /* ---- Predictor of the self-consistent potential -------------------------------------------
  * TDKS_PRED_PC (default): predictor-corrector as in tdks_step.
  * TDKS_PRED_EXTRAP: the cubic through the last four potentials, V~(t+dt) = 4 V_Hxc(t)
@@ -260,6 +263,22 @@ tdks_status tdks_query(const tdks_ctx* ctx, int* npts, int* nk, int* norb, int* 
  * Errors: EUNSUPPORTED if the context does not use the tile kernels or the variant needs FP32;
  * EINVAL for set outside -1..2. */
 tdks_status tdks_tile_variant(tdks_ctx* ctx, int set, int* variant, float* tune_ms);
+
+/* Checkpoint and restart of the time stepping (no counterpart in the paper's formulation; the
+ * paper's code restarts from files).  The state is everything a context carries from step to step
+ * besides the orbitals, which the caller owns and saves itself:
+ *   V_Hxc(t), rho(t) and the reference density rho0 of every cell; the last four V_Hxc of the
+ *   predictor history; the predictor mode, threshold, fallback count and network parameters; the
+ *   multiscale field levels A^n, A^{n-1}, A^{n+1}, the cell currents and the grid geometry; the
+ *   field settings (tdks_set_field).
+ * tdks_state_size gives the bytes; tdks_get_state writes them to host memory (synchronises);
+ * tdks_set_state restores them into a context created for the same system and options (grid
+ * points, cells, k-points, orbitals, precision, atoms, hartree/xc/pc), checked against the
+ * state's header: TDKS_EINVAL for a foreign or truncated state.  A restored context continues
+ * exactly as the original would from the same orbitals. */
+tdks_status tdks_state_size(const tdks_ctx* ctx, size_t* bytes);
+tdks_status tdks_get_state(tdks_ctx* ctx, void* host_buf, size_t bytes);
+tdks_status tdks_set_state(tdks_ctx* ctx, const void* host_buf, size_t bytes);
 
 /* Test hook of the device-side timeout path (no counterpart in the paper).  The tile kernels of large
  * isolated grids wait on shared-memory barriers for their TMA plane copies; every wait gives up after

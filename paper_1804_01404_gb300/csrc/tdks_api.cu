@@ -936,6 +936,13 @@ tdks_status tdks_ms_step(tdks_ctx* c, void* u, double t, double dt) {
   return TDKS_OK;
 }
 
+tdks_status tdks_ms_size(const tdks_ctx* c, int* nX) {
+  TDKS_TRY(check_ctx(c));
+  if (!nX) return fail(TDKS_EINVAL, "null output");
+  *nX = c->ms_ready ? c->nX : 0;
+  return TDKS_OK;
+}
+
 tdks_status tdks_ms_read(tdks_ctx* c, double* A_host, double* I_host) {
   TDKS_TRY(check_ctx(c));
   if (!c->ms_ready) return fail(TDKS_EINVAL, "call tdks_ms_init first");
@@ -1237,6 +1244,135 @@ tdks_status tdks_set_wait_test(tdks_ctx* c, long long wait_limit, int stop_after
   if (wait_limit < 0) return fail(TDKS_EINVAL, "wait_limit must be >= 0");
   c->wait_limit = wait_limit > 0 ? wait_limit : (1LL << 22);
   c->stop_after = stop_after < 0 ? -1 : stop_after;
+  return TDKS_OK;
+}
+
+// ------------------------------------------------------------------ checkpoint
+namespace {
+struct StateHeader {
+  char magic[8];            // "TDKSSTA1"
+  int npts, ncell, nk, norb, precision, natom, periodic;
+  int hartree, xc, pc;
+  int have_rho0, have_potential;
+  int hist_head, hist_count;
+  int pred_mode, nn_ready;
+  double pred_thr, fallbacks, last_resid;
+  int field_kind;
+  double A0[3], f_omega, f_T, f_cep;
+  int ms_ready, nX, m0, ms_head;
+  double dX;
+};
+
+size_t state_bytes(const tdks_ctx* c) {
+  const size_t npc = (size_t)c->npts * c->ncell;
+  size_t b = sizeof(StateHeader) + sizeof(double) * (3 * npc + 4 * (size_t)c->npts);
+  if (c->nn_ready) b += sizeof(float) * kNNParams;
+  if (c->ms_ready) b += sizeof(double) * 4 * (size_t)c->nX;
+  return b;
+}
+}  // namespace
+
+tdks_status tdks_state_size(const tdks_ctx* c, size_t* bytes) {
+  TDKS_TRY(check_ctx(c));
+  if (!bytes) return fail(TDKS_EINVAL, "null output");
+  *bytes = state_bytes(c);
+  return TDKS_OK;
+}
+
+tdks_status tdks_get_state(tdks_ctx* c, void* host, size_t bytes) {
+  TDKS_TRY(check_ctx(c));
+  if (!host || bytes < state_bytes(c)) return fail(TDKS_EINVAL, "state buffer smaller than tdks_state_size");
+  StateHeader h;
+  std::memset(&h, 0, sizeof(h));
+  std::memcpy(h.magic, "TDKSSTA1", 8);
+  h.npts = c->npts; h.ncell = c->ncell; h.nk = c->nk; h.norb = c->norb; h.precision = c->opt.precision;
+  h.natom = c->natom; h.periodic = c->grid.periodic;
+  h.hartree = c->opt.hartree; h.xc = c->opt.xc; h.pc = c->opt.pc;
+  h.have_rho0 = c->have_rho0; h.have_potential = c->have_potential;
+  h.hist_head = c->hist_head; h.hist_count = c->hist_count;
+  h.pred_mode = c->pred_mode; h.nn_ready = c->nn_ready;
+  h.pred_thr = c->pred_thr; h.fallbacks = c->fallbacks; h.last_resid = c->last_resid;
+  h.field_kind = c->field_kind;
+  for (int a = 0; a < 3; ++a) h.A0[a] = c->A0[a];
+  h.f_omega = c->f_omega; h.f_T = c->f_T; h.f_cep = c->f_cep;
+  h.ms_ready = c->ms_ready; h.nX = c->nX; h.m0 = c->m0; h.ms_head = c->ms_head; h.dX = c->dX;
+  unsigned char* o = static_cast<unsigned char*>(host);
+  std::memcpy(o, &h, sizeof(h));
+  o += sizeof(h);
+  const size_t npc = (size_t)c->npts * c->ncell;
+  auto d2h = [&](const void* src, size_t nbytes) -> cudaError_t {
+    const cudaError_t e = cudaMemcpyAsync(o, src, nbytes, cudaMemcpyDeviceToHost, c->stream);
+    o += nbytes;
+    return e;
+  };
+  TDKS_CUDA(d2h(c->d_vhxc, npc * sizeof(double)));
+  TDKS_CUDA(d2h(c->d_rho, npc * sizeof(double)));
+  TDKS_CUDA(d2h(c->d_rho0, npc * sizeof(double)));
+  TDKS_CUDA(d2h(c->d_vhist, 4 * (size_t)c->npts * sizeof(double)));
+  if (c->nn_ready) TDKS_CUDA(d2h(c->nn.params, kNNParams * sizeof(float)));
+  if (c->ms_ready) {
+    for (int i = 0; i < 3; ++i) TDKS_CUDA(d2h(c->d_A[i], c->nX * sizeof(double)));
+    TDKS_CUDA(d2h(c->d_I, c->nX * sizeof(double)));
+  }
+  TDKS_CUDA(cudaStreamSynchronize(c->stream));
+  return TDKS_OK;
+}
+
+tdks_status tdks_set_state(tdks_ctx* c, const void* host, size_t bytes) {
+  TDKS_TRY(check_ctx(c));
+  if (!host || bytes < sizeof(StateHeader)) return fail(TDKS_EINVAL, "state buffer too small");
+  StateHeader h;
+  std::memcpy(&h, host, sizeof(h));
+  if (std::memcmp(h.magic, "TDKSSTA1", 8) != 0) return fail(TDKS_EINVAL, "not a tdks state (bad magic)");
+  if (h.npts != c->npts || h.ncell != c->ncell || h.nk != c->nk || h.norb != c->norb ||
+      h.precision != c->opt.precision || h.natom != c->natom || h.periodic != c->grid.periodic ||
+      h.hartree != c->opt.hartree || h.xc != c->opt.xc || h.pc != c->opt.pc)
+    return fail(TDKS_EINVAL, "state was written by a context of another system or options");
+  if (h.nn_ready && !c->nn_ready) TDKS_TRY(tdks_nn_init(c, 0));
+  if (h.ms_ready && (!c->ms_ready || c->nX != h.nX)) {
+    for (int i = 0; i < 3; ++i) TDKS_TRY(dalloc(c, &c->d_A[i], h.nX));
+    TDKS_TRY(dalloc(c, &c->d_I, h.nX));
+    if (!c->d_ap_mid) {
+      TDKS_TRY(dalloc(c, &c->d_ap_mid, 3 * (size_t)c->ncell));
+      TDKS_TRY(dalloc(c, &c->d_ap_end, 3 * (size_t)c->ncell));
+    }
+  }
+  // sizes as the writer had them
+  const size_t npc = (size_t)c->npts * c->ncell;
+  size_t need = sizeof(StateHeader) + sizeof(double) * (3 * npc + 4 * (size_t)c->npts);
+  if (h.nn_ready) need += sizeof(float) * kNNParams;
+  if (h.ms_ready) need += sizeof(double) * 4 * (size_t)h.nX;
+  if (bytes < need) return fail(TDKS_EINVAL, "state buffer shorter than its header says");
+  if (h.pred_mode != TDKS_PRED_PC) TDKS_TRY(tdks_set_predictor(c, h.pred_mode, h.pred_thr));
+  else c->pred_mode = TDKS_PRED_PC;
+  const unsigned char* in = static_cast<const unsigned char*>(host) + sizeof(h);
+  auto h2d = [&](void* dst, size_t nbytes) -> cudaError_t {
+    const cudaError_t e = cudaMemcpyAsync(dst, in, nbytes, cudaMemcpyHostToDevice, c->stream);
+    in += nbytes;
+    return e;
+  };
+  TDKS_CUDA(h2d(c->d_vhxc, npc * sizeof(double)));
+  TDKS_CUDA(h2d(c->d_rho, npc * sizeof(double)));
+  TDKS_CUDA(h2d(c->d_rho0, npc * sizeof(double)));
+  TDKS_CUDA(h2d(c->d_vhist, 4 * (size_t)c->npts * sizeof(double)));
+  if (h.nn_ready) {
+    TDKS_CUDA(h2d(c->nn.params, kNNParams * sizeof(float)));
+    TDKS_CUDA(nn_round_weights(c->nn, c->stream));
+  }
+  if (h.ms_ready) {
+    for (int i = 0; i < 3; ++i) TDKS_CUDA(h2d(c->d_A[i], h.nX * sizeof(double)));
+    TDKS_CUDA(h2d(c->d_I, h.nX * sizeof(double)));
+  }
+  c->have_rho0 = h.have_rho0; c->have_potential = h.have_potential;
+  c->hist_head = h.hist_head; c->hist_count = h.hist_count;
+  c->pred_thr = h.pred_thr; c->fallbacks = h.fallbacks; c->last_resid = h.last_resid;
+  c->field_kind = h.field_kind;
+  for (int a = 0; a < 3; ++a) c->A0[a] = h.A0[a];
+  c->f_omega = h.f_omega; c->f_T = h.f_T; c->f_cep = h.f_cep;
+  c->ms_ready = h.ms_ready; c->nX = h.nX; c->m0 = h.m0; c->ms_head = h.ms_head; c->dX = h.dX;
+  // the step potential follows from V_Hxc at the next step; the observables buffer is reset
+  TDKS_CUDA(cudaMemsetAsync(c->d_step_obs, 0, 8 * sizeof(double) * c->ncell, c->stream));
+  TDKS_CUDA(cudaStreamSynchronize(c->stream));
   return TDKS_OK;
 }
 

@@ -114,6 +114,10 @@ def load_library(path: str = LIB_PATH):
         "tdks_query": [vp, C.POINTER(i), C.POINTER(i), C.POINTER(i), C.POINTER(i), C.POINTER(i)],
         "tdks_tile_variant": [vp, i, C.POINTER(i), C.POINTER(C.c_float)],
         "tdks_set_wait_test": [vp, C.c_longlong, i],
+        "tdks_state_size": [vp, C.POINTER(C.c_size_t)],
+        "tdks_ms_size": [vp, C.POINTER(i)],
+        "tdks_get_state": [vp, vp, C.c_size_t],
+        "tdks_set_state": [vp, vp, C.c_size_t],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -247,6 +251,9 @@ class Context:
         _check(self.lib.tdks_ms_step(self.ctx, _ptr(u, self.cdtype), float(t), float(dt)))
 
     def ms_read(self):
+        n = C.c_int()
+        _check(self.lib.tdks_ms_size(self.ctx, C.byref(n)))
+        self.nX = n.value
         A = np.zeros(self.nX)
         I = np.zeros(self.nX)
         _check(self.lib.tdks_ms_read(self.ctx, A.ctypes.data_as(C.POINTER(C.c_double)),
@@ -303,6 +310,19 @@ class Context:
         ms = (C.c_float * 6)()
         _check(self.lib.tdks_tile_variant(self.ctx, int(set), v, ms))
         return [v[0], v[1]], [[float(x) for x in ms[:3]], [float(x) for x in ms[3:]]]
+
+    def get_state(self):
+        """Checkpoint of the time-stepping state (tdks_get_state) as a numpy uint8 array."""
+        n = C.c_size_t()
+        _check(self.lib.tdks_state_size(self.ctx, C.byref(n)))
+        buf = np.zeros(n.value, np.uint8)
+        _check(self.lib.tdks_get_state(self.ctx, buf.ctypes.data_as(C.c_void_p), n.value))
+        return buf
+
+    def set_state(self, buf):
+        """Restore a checkpoint written by get_state (tdks_set_state)."""
+        b = np.ascontiguousarray(buf, np.uint8)
+        _check(self.lib.tdks_set_state(self.ctx, b.ctypes.data_as(C.c_void_p), b.size))
 
     def set_wait_test(self, wait_limit=0, stop_after=-1):
         """Timeout-path test hook (tdks_set_wait_test); defaults restore normal operation."""
