@@ -153,6 +153,19 @@ def reference_arm(args, rank, world):
     return 0
 
 
+def replica_throughput(total_ms, steps, world, device=None):
+    """Whole-job throughput of `world` independent replicas that each timed `steps` steps in
+    `total_ms`: the slowest rank bounds the job (max over ranks through torch.distributed when
+    world > 1).  Returns (max total ms, steps/s of all ranks together)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        tt = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    return total_ms, world * steps / (total_ms / 1e3)
+
+
 def timed_steps(ctx, u, s, t0, warmup, steps, flush, record_j=False, label="steps"):
     """Run warmup + timed steps; every timed step is bracketed by CUDA events on the context
     stream, with an L2 flush (not timed) before it.  The timed steps sit in an NVTX range named
@@ -271,12 +284,7 @@ def gpu_arm(args, rank, world, local_rank):
     head = modes.get("learned")
     step_ms = head["ms"] if head else pc_ms
     st = head["st"] if head else st_pc
-    total_ms = float(np.sum(step_ms))
-    if world > 1:
-        tt = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
-    value = world * args.steps / (total_ms / 1e3)
+    total_ms, value = replica_throughput(float(np.sum(step_ms)), args.steps, world, dev)
 
     # dominant kernel of the headline step: the cell Taylor kernel (the corrector launch of a learned
     # step; predictor and corrector launches of a PC step), timed alone by the library's
