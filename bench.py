@@ -241,6 +241,8 @@ def gpu_arm(args, rank, world, local_rank):
     ctx64.update_potential(u64)
     J64, t = [], t0
     torch.cuda.synchronize()
+    ctx64.stats(reset=True)
+    ctx64.profile(True)
     tic = time.perf_counter()
     for _ in range(nref):
         ctx64.step(u64, t, s.dt)
@@ -248,6 +250,7 @@ def gpu_arm(args, rank, world, local_rank):
         J64.append(ctx64.read_step_observables()["J"])
     torch.cuda.synchronize()
     f64_sps = nref / (time.perf_counter() - tic)
+    st64 = ctx64.stats(reset=True)
     J64 = np.array(J64)
     ctx64.close()
     del u64
@@ -317,6 +320,12 @@ def gpu_arm(args, rank, world, local_rank):
                             "fallbacks": m["fallbacks"], "steps": args.warmup + args.steps,
                             "phase_ms_per_step": {k: v / args.steps for k, v in m["st"]["ms"].items()}}
     predictors["f64_pc_steps_per_s_host_synced"] = f64_sps
+    # the FP64 path is bound by the FP64 pipes: its cell kernel against the measured FP64 FMA rate
+    k64 = st64["ms"]["stencil_kernel"] / max(1, st64["calls"]["stencil_kernel"])
+    fp64_peak = T.probe_fp64()
+    predictors["f64_cell_kernel"] = {"avg_launch_ms": k64, "achieved_tflops": flops / (k64 * 1e-3) / 1e12,
+                                     "peak_tflops": fp64_peak, "peak_note": "measured FP64 FMA rate (tdks_probe_fp64)",
+                                     "frac": flops / (k64 * 1e-3) / 1e12 / fp64_peak}
     if train_info:
         predictors["training"] = train_info
 

@@ -280,6 +280,11 @@ tdks_status tdks_state_size(const tdks_ctx* ctx, size_t* bytes);
 tdks_status tdks_get_state(tdks_ctx* ctx, void* host_buf, size_t bytes);
 tdks_status tdks_set_state(tdks_ctx* ctx, const void* host_buf, size_t bytes);
 
+/* Measured FP64 FMA throughput of the current device in TFLOP/s (a 2-flop FMA counts 2), for the
+ * roofline of the FP64 path; runs some tens of milliseconds of FMA chains on every SM (synchronises the
+ * device; no context needed).  No counterpart in the paper. */
+tdks_status tdks_probe_fp64(double* tflops);
+
 /* Test hook of the device-side timeout path (no counterpart in the paper).  The tile kernels of large
  * isolated grids wait on shared-memory barriers for their TMA plane copies; every wait gives up after
  * a number of polls, sets the context's error word and the kernel returns (tdks_check then reports

@@ -116,6 +116,7 @@ def load_library(path: str = LIB_PATH):
         "tdks_set_wait_test": [vp, C.c_longlong, i],
         "tdks_state_size": [vp, C.POINTER(C.c_size_t)],
         "tdks_ms_size": [vp, C.POINTER(i)],
+        "tdks_probe_fp64": [C.POINTER(C.c_double)],
         "tdks_get_state": [vp, vp, C.c_size_t],
         "tdks_set_state": [vp, vp, C.c_size_t],
     }
@@ -130,6 +131,14 @@ def load_library(path: str = LIB_PATH):
     lib.tdks_destroy.restype = None
     _lib = lib
     return lib
+
+
+def probe_fp64():
+    """Measured FP64 FMA throughput of the current CUDA device, TFLOP/s (tdks_probe_fp64)."""
+    lib = load_library()
+    x = C.c_double()
+    _check(lib.tdks_probe_fp64(C.byref(x)))
+    return x.value
 
 
 def _check(status):

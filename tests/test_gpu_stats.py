@@ -32,3 +32,11 @@ def test_stencil_phase_nested_in_taylor_phases():
     assert 0 < st["ms"]["stencil_kernel"] <= taylor_ms
     assert st["launches"] >= taylor_calls
     assert ctx.stats(reset=True)["launches"] == 0
+
+
+def test_fp64_probe_is_plausible():
+    """The FP64 FMA-rate probe behind the FP64 path's roofline returns a finite rate well below the
+    FP32 rate of the device (FP64 runs at a small fraction of it here)."""
+    from paper_1804_01404_gb300 import tdks as T
+    r = T.probe_fp64()
+    assert np.isfinite(r) and 0.05 < r < 100.0
