@@ -50,7 +50,10 @@ def _emulated_forward(params, V0, V1, V2, V3, periodic):
     return out, s, (x, y1, a1, y2, a2)
 
 
-SYS = {"periodic": W.tiny(periodic=True, n=(8, 9, 10)), "isolated": W.tiny(periodic=False, n=(9, 8, 7))}
+# tiny grids, the bench crystal's 20^3 grid, and the 48^3 isolated grid of the cluster variant the
+# predictor is meant for
+SYS = {"periodic": W.tiny(periodic=True, n=(8, 9, 10)), "isolated": W.tiny(periodic=False, n=(9, 8, 7)),
+       "crystal20": W.tiny(periodic=True, n=(20, 20, 20)), "cluster48": W.tiny(periodic=False, n=(48, 48, 48))}
 
 
 @pytest.mark.parametrize("name", list(SYS))
