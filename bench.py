@@ -281,7 +281,7 @@ def gpu_arm(args, rank, world, local_rank):
             c2.set_predictor(mode, 1e-5)
             ms, J, st = timed_steps(c2, u2, s, t0, args.warmup, args.steps, flush, record_j=True, label=name)
             o = c2.read_step_observables()
-            modes[name] = dict(ms=ms, J=J, st=st, fallbacks=o["fallbacks"])
+            modes[name] = dict(ms=ms, J=J, st=st, fallbacks=o["fallbacks"], cell_scheme=c2.cell_variant())
             c2.close()
     clk = clocks.stop()
 
@@ -306,6 +306,7 @@ def gpu_arm(args, rank, world, local_rank):
                 "kernel": "k_cell<float, MODE=1> (4 Horner stages, whole orbital in shared memory; "
                           "J and norms of the input state fused into the first stage)",
                 "avg_launch_ms": k_ms, "launches_timed": st["calls"]["stencil_kernel"],
+                "buffer_scheme": cell_scheme(head["cell_scheme"] if head else None),
                 "flops_per_launch": flops,
                 "peak_note": "FP32 peak = 152 SM x 128 lanes x 2 flop x max SM clock (derived, not measured)",
                 "hbm_view": {"bytes_per_launch": hbm_bytes,
@@ -363,6 +364,10 @@ def gpu_arm(args, rank, world, local_rank):
     if rank == 0 and not args.skip_hpsi:
         hpsi = hpsi_cluster(dev)
 
+    others = None
+    if rank == 0 and not args.skip_workloads:
+        others = workload_steps(dev)
+
     cpu = None
     if rank == 0 and not args.skip_cpu:
         nk_sample = 2
@@ -384,9 +389,19 @@ def gpu_arm(args, rank, world, local_rank):
                 "phase_ms_per_step": {k: v / args.steps for k, v in st["ms"].items()},
                 "step_ms_min": float(np.min(step_ms)),
                 "J_rel_err_vs_f64": jerr(head["J"]) if head else jerr(J_pc),
-                "predictors": predictors, "hpsi_cluster": hpsi}
+                "predictors": predictors, "hpsi_cluster": hpsi,
+                "other_workloads": others}
         print(json.dumps(line), flush=True)
     return 0
+
+
+def cell_scheme(v):
+    """The cell kernel's buffer scheme picked by the library's tuner at context creation
+    (tdks_cell_variant), with the tuning times of one Taylor launch of each."""
+    if v is None:
+        return None
+    names = ["two shared-memory copies", "one copy swept in place"]
+    return {"in_use": names[v[0]], "tune_ms": {n: (t if t > 0 else None) for n, t in zip(names, v[1])}}
 
 
 def measured_traffic(key):
@@ -479,6 +494,114 @@ def hpsi_cluster(dev, reps=10, norb=256):
     return res
 
 
+def smooth_random_orbitals(shape, dV, dev, seed, passes=3):
+    """Seeded random complex fields, low-passed by repeated 3-point box averages along x, y and z and
+    normalised to sum |u|^2 dV = 1: smooth orbital-like inputs whose step time equals that of the
+    method's own orbitals (the kernels' work does not depend on the values)."""
+    import torch
+    g = torch.Generator(device=dev)
+    g.manual_seed(seed)
+    u = torch.randn(shape, dtype=torch.complex64, device=dev, generator=g)
+    for _ in range(passes):
+        for ax in (-1, -2, -3):
+            u = (u + torch.roll(u, 1, ax) + torch.roll(u, -1, ax)) * (1.0 / 3.0)
+    nrm = torch.sqrt((u.abs() ** 2).sum(dim=(-1, -2, -3), keepdim=True) * dV)
+    return (u / nrm).contiguous()
+
+
+def workload_steps(dev, warmup=2, steps=5):
+    """Full steps of the two large workloads, timed over a few steps (CUDA events on the context
+    stream) after warm-up:
+      * isolated cluster: 96^3 grid (h = 0.4), 128 atoms, 256 orbitals, FP32, impulse kick,
+        predictor-corrector with Hockney Hartree, tiled TMA stencil;
+      * multiscale: 256 microscopic cells (16^3, 8 atoms, 16 orbitals x 8 k) on a 1D Maxwell grid
+        (dX = 250 bohr), one coupled step = TDKS PC step of every cell + current + Maxwell update.
+    "effective hpsi GB/s" = 2 Taylor steps x 4 H applications x 16 B per orbital-point / step time
+    (the unfused-equivalent stream; it exceeds the HBM peak when orbitals stay on chip)."""
+    import torch
+    from paper_1804_01404_gb300 import workloads as W
+    from paper_1804_01404_gb300.tdks import Context
+    stream = torch.cuda.current_stream()
+    out = {}
+
+    def run(ctx, one_step, label):
+        for _ in range(warmup):
+            one_step()
+        torch.cuda.synchronize()
+        ctx.stats(reset=True)
+        ctx.profile(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push(label)
+        e0.record(stream)
+        for _ in range(steps):
+            one_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        st = ctx.stats(reset=True)
+        ctx.profile(False)
+        ctx.check()
+        return e0.elapsed_time(e1) / steps, st
+
+    # isolated cluster
+    s = W.isolated_cluster()
+    u = smooth_random_orbitals((s.nk, s.norb, s.n[2], s.n[1], s.n[0]), s.dV, dev, seed=11)
+    ctx = Context(s, precision="f32")
+    ctx.kick(u, s.kick)
+    ctx.update_potential(u)
+    tt = [0.0]
+
+    def cl_step():
+        ctx.step(u, tt[0], s.dt)
+        tt[0] += s.dt
+    ms, st = run(ctx, cl_step, "cluster_steps")
+    opts = s.npts * s.nk * s.norb
+    out["cluster_96"] = {
+        "workload": "isolated cluster 96^3 (h = 0.4), 128 atoms, 256 orbitals x 1 k, FP32 orbitals, "
+                    "impulse kick, predictor-corrector, Hockney Hartree",
+        "steps_timed": steps, "warmup": warmup, "ms_per_step": ms, "steps_per_s": 1e3 / ms,
+        "orbital_points": opts, "effective_hpsi_GBps": 8 * 16 * opts / (ms * 1e-3) / 1e9,
+        "phase_ms_per_step": {k: v / steps for k, v in st["ms"].items()},
+        "launches_per_step": st["launches"] / steps,
+        "l2": "orbitals 1.81 GB, far above L2"}
+    ctx.close()
+    del u
+    torch.cuda.empty_cache()
+
+    # batched multiscale cells
+    s = W.multiscale_cell()
+    ncell, m0, dX = 256, 4, 250.0
+    nX = m0 + ncell + 4
+    X = np.arange(nX)
+    A_now = 0.3 * np.sin(2 * np.pi * X / 64.0)
+    A_prev = 0.3 * np.sin(2 * np.pi * (X + 0.5) / 64.0)
+    psi = W.initial_orbitals(s, 3).astype(np.complex64)
+    u = torch.from_numpy(psi).to(dev).unsqueeze(0).repeat(ncell, 1, 1, 1, 1, 1).contiguous()
+    ctx = Context(s, precision="f32", ncell=ncell)
+    ctx.update_potential(u)
+    ctx.ms_init(dX, m0, A_now, A_prev)
+    tt = [0.0]
+
+    def ms_step():
+        ctx.ms_step(u, tt[0], s.dt)
+        tt[0] += s.dt
+    ms, st = run(ctx, ms_step, "multiscale_steps")
+    opts = ncell * s.npts * s.nk * s.norb
+    out["multiscale_256"] = {
+        "workload": f"{ncell} cells of 16^3, 8 atoms, 16 orbitals x 8 k each, FP32 orbitals, on a {nX}-point "
+                    "1D Maxwell grid (dX = 250 bohr); one coupled step",
+        "steps_timed": steps, "warmup": warmup, "ms_per_step": ms, "steps_per_s": 1e3 / ms,
+        "cell_steps_per_s": ncell * 1e3 / ms,
+        "orbital_points": opts, "effective_hpsi_GBps": 8 * 16 * opts / (ms * 1e-3) / 1e9,
+        "phase_ms_per_step": {k: v / steps for k, v in st["ms"].items()},
+        "launches_per_step": st["launches"] / steps,
+        "l2": "orbitals 1.07 GB, far above L2"}
+    ctx.close()
+    del u
+    torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -488,8 +611,11 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-learned", action="store_true")
     ap.add_argument("--skip-hpsi", action="store_true")
-    ap.add_argument("--only", default="", choices=["", "hpsi"],
-                    help="hpsi: only the tdks_hpsi measurement on the isolated cluster (profiling)")
+    ap.add_argument("--skip-workloads", action="store_true",
+                    help="skip the few-step timings of the isolated cluster and multiscale workloads")
+    ap.add_argument("--only", default="", choices=["", "hpsi", "workloads"],
+                    help="hpsi: only the tdks_hpsi measurement on the isolated cluster (profiling); "
+                         "workloads: only the cluster and multiscale step timings")
     ap.add_argument("--hpsi-norb", type=int, default=256)
     ap.add_argument("--hpsi-reps", type=int, default=10)
     ap.add_argument("--cpu-steps", type=int, default=8)
@@ -507,6 +633,12 @@ def main():
         if rank == 0:
             print(json.dumps({"hpsi_cluster": hpsi_cluster(torch.device("cuda", local_rank),
                                                            reps=args.hpsi_reps, norb=args.hpsi_norb)}))
+        return 0
+    if args.only == "workloads":
+        import torch
+        torch.cuda.set_device(local_rank)
+        if rank == 0:
+            print(json.dumps({"other_workloads": workload_steps(torch.device("cuda", local_rank))}))
         return 0
     if world > 1:
         import torch.distributed as dist

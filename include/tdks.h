@@ -264,6 +264,21 @@ tdks_status tdks_query(const tdks_ctx* ctx, int* npts, int* nk, int* norb, int* 
  * EINVAL for set outside -1..2. */
 tdks_status tdks_tile_variant(tdks_ctx* ctx, int set, int* variant, float* tune_ms);
 
+/* Buffer scheme of the shared-memory cell kernels for the Taylor propagator (Eq. taylor, Horner
+ * form; no counterpart in the paper).  0 = two orbital copies in shared memory (or a global scratch
+ * slice when two do not fit), one stage reading one and writing the other; 1 = one copy swept in
+ * place plane by plane, one thread per (x, y) column, for planes of at most 448 points -- half the
+ * shared memory, so two FP32 CTAs share an SM.  The arithmetic per grid point and per projection is
+ * the same in both; the norm and current sums of an orbital are split over the CTA's warps and may
+ * add in another order.  At tdks_init a cell context on which scheme 1 applies times one Taylor launch of each on
+ * zeroed orbitals and keeps the faster.
+ *   set       : -1 leaves the choice as it is; 0 or 1 forces that scheme.
+ *   variant   : receives the scheme in use (may be NULL).
+ *   tune_ms   : receives the 2 tuning times in ms, -1 where not timed (may be NULL).
+ * Errors: EUNSUPPORTED if the context uses the tile kernels, or set = 1 where scheme 1 does not
+ * apply; EINVAL for set outside -1..1. */
+tdks_status tdks_cell_variant(tdks_ctx* ctx, int set, int* variant, float* tune_ms);
+
 /* Checkpoint and restart of the time stepping (no counterpart in the paper's formulation; the
  * paper's code restarts from files).  The state is everything a context carries from step to step
  * besides the orbitals, which the caller owns and saves itself:

@@ -43,14 +43,47 @@ __device__ __forceinline__ float dsilu(float y) {
   return s * (1.0f + y * (1.0f - s));
 }
 
+__device__ __forceinline__ double cubic(double v0, double v1, double v2, double v3) {
+  return 4.0 * v0 - 6.0 * v1 + 4.0 * v2 - v3;
+}
+
+// N consecutive BF16 values (N = 4 or a multiple of 8, address aligned to 2N bytes) as floats.
+template <int N>
+__device__ __forceinline__ void load_bf16(const bf16* p, float* out) {
+  static_assert(N == 4 || N % 8 == 0, "vector width");
+  if constexpr (N == 4) {
+    const uint2 r = *reinterpret_cast<const uint2*>(p);
+    const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&r.x));
+    const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&r.y));
+    out[0] = a.x; out[1] = a.y; out[2] = b.x; out[3] = b.y;
+  } else {
+#pragma unroll
+    for (int v = 0; v < N / 8; ++v) {
+      const uint4 r = reinterpret_cast<const uint4*>(p)[v];
+      const unsigned w[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w[j]));
+        out[8 * v + 2 * j] = f.x;
+        out[8 * v + 2 * j + 1] = f.y;
+      }
+    }
+  }
+}
+
 // y[co][p] = b[co] + sum_{kk, ci} W[co][ci][kk] x[ci][nb(p, kk)];  a = bf16(SiLU(y)) if ACT.
 // Each point is shared by G = (COUT / COP) * CIS adjacent lanes: a lane forms COP outputs over
 // CIN / CIS input channels, and lanes that split the input channels add their sums by shuffles.
 // (A point per thread would leave most SMs idle on the grids of these cells.)
-template <int CIN, int COUT, bool ACT, int COP, int CIS>
+// Layouts: channel-first x[ci][p], y[co][p], a[co][p] (training), or, with CL, channel-last
+// x[p][ci] and a[p][co] read and written with vector accesses, y not stored (prediction only).
+// PRED (COUT = 1): also vpred[p] = cubic(V0..V3)[p] + s3 * y[p], the network's potential prediction.
+template <int CIN, int COUT, bool ACT, int COP, int CIS, bool PRED = false, bool CL = false>
 __global__ void __launch_bounds__(256) k_nn_fwd(NNGrid g, const bf16* __restrict__ x,
                                                 const float* __restrict__ W, const float* __restrict__ b,
-                                                float* __restrict__ y, bf16* __restrict__ a) {
+                                                float* __restrict__ y, bf16* __restrict__ a,
+                                                NNPredict pr = NNPredict{}, const double* __restrict__ stats = nullptr) {
+  static_assert(!PRED || COUT == 1, "the prediction epilogue follows the single-channel layer");
   constexpr int GO = COUT / COP, G = GO * CIS, CIP = CIN / CIS;
   static_assert(GO * COP == COUT && CIP * CIS == CIN && 32 % G == 0, "lane split");
   __shared__ float Ws[27][CIN][COUT];
@@ -74,12 +107,21 @@ __global__ void __launch_bounds__(256) k_nn_fwd(NNGrid g, const bf16* __restrict
     for (int kk = 0; kk < 27; ++kk) {
       const int q = act ? nb_index(g, px, py, pz, kk % 3 - 1, (kk / 3) % 3 - 1, kk / 9 - 1) : -1;
       if (q < 0) continue;
+      if constexpr (CL) {
+        float xv[CIP];
+        load_bf16<CIP>(x + (size_t)q * CIN + cs * CIP, xv);
 #pragma unroll
-      for (int c = 0; c < CIP; ++c) {
-        const int ci = cs * CIP + c;
-        const float xv = __bfloat162float(x[(size_t)ci * g.npts + q]);
+        for (int c = 0; c < CIP; ++c)
 #pragma unroll
-        for (int o = 0; o < COP; ++o) acc[o] = fmaf(Ws[kk][ci][og * COP + o], xv, acc[o]);
+          for (int o = 0; o < COP; ++o) acc[o] = fmaf(Ws[kk][cs * CIP + c][og * COP + o], xv[c], acc[o]);
+      } else {
+#pragma unroll
+        for (int c = 0; c < CIP; ++c) {
+          const int ci = cs * CIP + c;
+          const float xv = __bfloat162float(x[(size_t)ci * g.npts + q]);
+#pragma unroll
+          for (int o = 0; o < COP; ++o) acc[o] = fmaf(Ws[kk][ci][og * COP + o], xv, acc[o]);
+        }
       }
     }
     if (CIS > 1) {
@@ -89,12 +131,23 @@ __global__ void __launch_bounds__(256) k_nn_fwd(NNGrid g, const bf16* __restrict
         for (int o = 0; o < COP; ++o) acc[o] += __shfl_xor_sync(0xffffffffu, acc[o], sft);
     }
     if (act && cs == 0) {
+      if constexpr (CL && ACT && COP == 4) {
+        const __nv_bfloat162 lo = __floats2bfloat162_rn(silu(acc[0]), silu(acc[1]));
+        const __nv_bfloat162 hi = __floats2bfloat162_rn(silu(acc[2]), silu(acc[3]));
+        uint2 r;
+        r.x = *reinterpret_cast<const unsigned*>(&lo);
+        r.y = *reinterpret_cast<const unsigned*>(&hi);
+        *reinterpret_cast<uint2*>(a + (size_t)p * COUT + og * COP) = r;
+      } else {
+        static_assert(!CL || !ACT || COP == 4, "channel-last activations are stored four at a time");
 #pragma unroll
-      for (int o = 0; o < COP; ++o) {
-        const int co = og * COP + o;
-        y[(size_t)co * g.npts + p] = acc[o];
-        if (ACT) a[(size_t)co * g.npts + p] = __float2bfloat16(silu(acc[o]));
+        for (int o = 0; o < COP; ++o) {
+          const int co = og * COP + o;
+          if (!CL) y[(size_t)co * g.npts + p] = acc[o];
+          if (ACT) a[(size_t)co * g.npts + p] = __float2bfloat16(silu(acc[o]));
+        }
       }
+      if (PRED) pr.vpred[p] = cubic(pr.V0[p], pr.V1[p], pr.V2[p], pr.V3[p]) + stats[2] * (double)acc[0];
     }
   }
 }
@@ -252,22 +305,22 @@ __global__ void __launch_bounds__(256) k_nn_stats(const double* __restrict__ V0,
   }
 }
 
-__device__ __forceinline__ double cubic(double v0, double v1, double v2, double v3) {
-  return 4.0 * v0 - 6.0 * v1 + 4.0 * v2 - v3;
-}
-
+// Network inputs x[c][p] (channel-first) or x[p][c] (cl = 1), c = scaled D1, D2, D3, V0 - mean.
 __global__ void k_nn_pack(const double* __restrict__ V0, const double* __restrict__ V1,
                           const double* __restrict__ V2, const double* __restrict__ V3,
                           const double* __restrict__ Vnext, const double* __restrict__ stats, int n,
-                          bf16* __restrict__ x, float* __restrict__ target) {
+                          int cl, bf16* __restrict__ x, float* __restrict__ target) {
   const double s1 = stats[0], s2 = stats[1], s3 = stats[2], m = stats[3], sv = stats[4];
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
     const double d1 = V0[p] - V1[p], d2 = V0[p] - 2.0 * V1[p] + V2[p];
     const double d3 = V0[p] - 3.0 * V1[p] + 3.0 * V2[p] - V3[p];
-    x[p] = __float2bfloat16((float)(d1 / s1));
-    x[(size_t)n + p] = __float2bfloat16((float)(d2 / s2));
-    x[2 * (size_t)n + p] = __float2bfloat16((float)(d3 / s3));
-    x[3 * (size_t)n + p] = __float2bfloat16((float)((V0[p] - m) / sv));
+    const bf16 c0 = __float2bfloat16((float)(d1 / s1)), c1 = __float2bfloat16((float)(d2 / s2));
+    const bf16 c2 = __float2bfloat16((float)(d3 / s3)), c3 = __float2bfloat16((float)((V0[p] - m) / sv));
+    if (cl) {
+      x[4 * (size_t)p] = c0; x[4 * (size_t)p + 1] = c1; x[4 * (size_t)p + 2] = c2; x[4 * (size_t)p + 3] = c3;
+    } else {
+      x[p] = c0; x[(size_t)n + p] = c1; x[2 * (size_t)n + p] = c2; x[3 * (size_t)n + p] = c3;
+    }
     if (Vnext) target[p] = (float)((Vnext[p] - cubic(V0[p], V1[p], V2[p], V3[p])) / s3);
   }
 }
@@ -312,9 +365,19 @@ int nn_part_blocks(int npts) { return (npts + PB - 1) / PB; }
 inline const bf16* B16(const unsigned short* p) { return reinterpret_cast<const bf16*>(p); }
 inline bf16* B16(unsigned short* p) { return reinterpret_cast<bf16*>(p); }
 
-cudaError_t nn_forward(const NNBuffers& B, const NNGrid& g, cudaStream_t s) {
+cudaError_t nn_forward(const NNBuffers& B, const NNGrid& g, cudaStream_t s, const NNPredict* pred) {
   // four lanes per point in every layer (4 outputs each; the last layer splits its 16 inputs)
+  // (the prediction reads channel-last inputs, see nn_inputs, and keeps its activations channel-last)
   const int nb = blocks_for(4 * g.npts);
+  if (pred) {
+    k_nn_fwd<4, 16, true, 4, 1, false, true><<<nb, 256, 0, s>>>(g, B16(B.x0), B.wq + kNNOff[0], B.wq + kNNOff[1],
+                                                                 nullptr, B16(B.a1));
+    k_nn_fwd<16, 16, true, 4, 1, false, true><<<nb, 256, 0, s>>>(g, B16(B.a1), B.wq + kNNOff[2], B.wq + kNNOff[3],
+                                                                  nullptr, B16(B.a2));
+    k_nn_fwd<16, 1, false, 1, 4, true, true><<<nb, 256, 0, s>>>(g, B16(B.a2), B.wq + kNNOff[4], B.wq + kNNOff[5],
+                                                                 B.out, nullptr, *pred, B.stats);
+    return cudaGetLastError();
+  }
   k_nn_fwd<4, 16, true, 4, 1><<<nb, 256, 0, s>>>(g, B16(B.x0), B.wq + kNNOff[0], B.wq + kNNOff[1], B.y1, B16(B.a1));
   k_nn_fwd<16, 16, true, 4, 1><<<nb, 256, 0, s>>>(g, B16(B.a1), B.wq + kNNOff[2], B.wq + kNNOff[3], B.y2, B16(B.a2));
   k_nn_fwd<16, 1, false, 1, 4><<<nb, 256, 0, s>>>(g, B16(B.a2), B.wq + kNNOff[4], B.wq + kNNOff[5], B.out, nullptr);
@@ -357,9 +420,11 @@ cudaError_t nn_round_weights(const NNBuffers& B, cudaStream_t s) {
 }
 
 cudaError_t nn_inputs(const NNBuffers& B, const NNGrid& g, const double* V0, const double* V1,
-                      const double* V2, const double* V3, const double* Vnext, cudaStream_t s) {
+                      const double* V2, const double* V3, const double* Vnext, cudaStream_t s,
+                      bool channel_last) {
   k_nn_stats<<<grid_sum_blocks(g.npts, 256), 256, 0, s>>>(V0, V1, V2, V3, g.npts, B.red, B.ticket, B.stats);
-  k_nn_pack<<<blocks_for(g.npts), 256, 0, s>>>(V0, V1, V2, V3, Vnext, B.stats, g.npts, B16(B.x0), B.target);
+  k_nn_pack<<<blocks_for(g.npts), 256, 0, s>>>(V0, V1, V2, V3, Vnext, B.stats, g.npts, channel_last ? 1 : 0,
+                                               B16(B.x0), B.target);
   return cudaGetLastError();
 }
 

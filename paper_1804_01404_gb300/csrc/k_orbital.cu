@@ -9,7 +9,15 @@
 //
 // Work split inside the CTA: a thread owns one (x, y) column segment and marches along z,
 // keeping the nine z-values u(z-4..z+4) of its column in registers; the 16 x/y neighbours come
-// from shared memory through offsets computed once per column.  Complex FP32 arithmetic uses the
+// from shared memory through offsets computed once per column.  Two buffer schemes:
+//   * two buffers (DBUF): a stage reads one shared-memory copy and writes the other (or a global
+//     scratch slice when two copies do not fit);
+//   * one buffer swept in place (IP, planes of up to kNTip points): one thread per column, all
+//     columns advance through z together, and the result of plane z replaces the input after a
+//     barrier, once every thread has read that input plane.  The input planes 0..3 that periodic
+//     columns still need at the end of the sweep (their images beyond the last plane) are kept in
+//     a small side buffer.  Half the shared memory lets two CTAs share an SM, so one CTA's loads,
+//     projections and barriers overlap the other's stencil work.  Complex FP32 arithmetic uses the
 // packed f32x2 instructions.  The nonlocal scatter runs as a separate pass over the grid points
 // that lie inside a projector sphere.  The last pass writes the orbital, accumulates the density
 // of Eq. (rho) (FP64 atomics; FP32 orbitals add into per-k FP32 partials folded in FP64) and, on
@@ -58,6 +66,7 @@ struct Smem {
   C* nxt;    // [nz * pstride] next vector (double-buffer mode)
   C* ph;     // [nsph] exp(i q.d)
   C* ec;     // [natom*4] E_p * dV * c_ap
+  C* sv;     // IP, periodic: [4][nx*ny] input planes 0..3 of the current stage
 };
 
 template <typename T>
@@ -72,8 +81,46 @@ inline size_t cell_smem_bytes(int nz, int pstride, int nsph, int natom, bool dbu
 // 128 registers per thread.
 template <typename T> constexpr int kNTof() { return sizeof(T) == 4 ? 800 : 512; }
 constexpr size_t kSmemLimit = 220 * 1024;
+// In-place sweep: at most kNTip columns (one thread each); FP32 CTAs are sized for two per SM
+// (72 registers per thread), FP64 CTAs for one.
+constexpr int kNTip = 448;
+template <typename T, bool IP> constexpr int kMaxThreads() { return IP ? kNTip : kNTof<T>(); }
+template <typename T, bool IP> constexpr int kMinBlocks() { return (IP && sizeof(T) == 4) ? 2 : 1; }
 
-// Projections of the shared-memory vector:  ec[a*4+p] = E_p dV sum_i beta_ip ph_i v(idx_i).
+template <typename T>
+inline size_t cell_smem_bytes_ip(int nx, int ny, int nz, int pstride, int nsph, int natom, bool periodic) {
+  using C = typename Cplx<T>::type;
+  return sizeof(C) * ((size_t)nz * pstride + nsph + 4 * (size_t)natom + (periodic ? 4 * (size_t)nx * ny : 0));
+}
+
+// Warp sums of N = 2^K values per lane with N - 1 + 5 - K shuffles instead of 5 N: at each of the
+// first K steps a lane keeps one half of its values and trades the other half with the partner lane
+// (lane ^ 16, then ^ 8, ...), the last 5 - K steps add a single value.  On return lane L holds the
+// warp total of value (L >> (5 - K)).
+template <int N, typename T>
+__device__ __forceinline__ T warp_split_sum(T* v) {
+  constexpr int K = (N >= 32) ? 5 : (N >= 16) ? 4 : (N >= 8) ? 3 : (N >= 4) ? 2 : (N >= 2) ? 1 : 0;
+  static_assert((1 << K) == N, "N must be a power of two up to 32");
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int st = 0; st < K; ++st) {
+    const int n = N >> st, o = 16 >> st;
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int j = 0; j < n / 2; ++j) {
+      const T send = up ? v[j] : v[j + n / 2];
+      const T keep = up ? v[j + n / 2] : v[j];
+      v[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  T r = v[0];
+#pragma unroll
+  for (int st = K; st < 5; ++st) r += __shfl_xor_sync(0xffffffffu, r, 16 >> st);
+  return r;
+}
+
+// Projections of the shared-memory vector:  ec[a*4+p] = E_p dV sum_i beta_ip ph_i v(idx_i), one warp
+// per atom.
 template <typename T>
 __device__ __forceinline__ void project(const OrbArgs<T>& a, const typename Cplx<T>::type* v,
                                         const typename Cplx<T>::type* ph,
@@ -94,13 +141,10 @@ __device__ __forceinline__ void project(const OrbArgs<T>& a, const typename Cplx
         acc[2 * p + 1] += b[p] * im;
       }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-      for (int j = 0; j < 8; ++j) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], o);
-    if (lane < 4) {
-      const T s = a.atomE[at * 4 + lane] * a.dV;
-      ec[at * 4 + lane] = C{acc[2 * lane] * s, acc[2 * lane + 1] * s};
+    const T tot = warp_split_sum<8>(acc);        // lane L: total of acc[L >> 2]
+    if ((lane & 3) == 0) {
+      const int j = lane >> 2, p = j >> 1;          // acc[2p]: Re, acc[2p+1]: Im of projector p
+      reinterpret_cast<T*>(ec)[2 * (at * 4 + p) + (j & 1)] = tot * (a.atomE[at * 4 + p] * a.dV);
     }
   }
 }
@@ -328,9 +372,9 @@ __device__ __forceinline__ void nonlocal_current(const OrbArgs<T>& a, const type
     __syncthreads();
     for (int job = warp; job < nb * nch; job += nw) {
       const int at = ab + job / nch, ch = job % nch;
-      T cb[8], bb[3][8];
+      T acc[32];                                  // [c, b_x, b_y, b_z][Re, Im of projector 0..3]
 #pragma unroll
-      for (int j = 0; j < 8; ++j) { cb[j] = 0; bb[0][j] = bb[1][j] = bb[2][j] = 0; }
+      for (int j = 0; j < 32; ++j) acc[j] = 0;
       for (int i = a.atom_off[at] + ch * 32 + lane; i < a.atom_off[at + 1]; i += 32 * nch) {
         const C u = v[a.sph_sidx[i]];
         const C f = ph[i];
@@ -339,31 +383,14 @@ __device__ __forceinline__ void nonlocal_current(const OrbArgs<T>& a, const type
 #pragma unroll
         for (int p = 0; p < 4; ++p) {
           const T b = a.sph_beta[i * 4 + p];
-          cb[2 * p] += b * re; cb[2 * p + 1] += b * im;
-          bb[0][2 * p] += d0 * b * re; bb[0][2 * p + 1] += d0 * b * im;
-          bb[1][2 * p] += d1 * b * re; bb[1][2 * p + 1] += d1 * b * im;
-          bb[2][2 * p] += d2 * b * re; bb[2][2 * p + 1] += d2 * b * im;
+          acc[2 * p] += b * re; acc[2 * p + 1] += b * im;
+          acc[8 + 2 * p] += d0 * b * re; acc[8 + 2 * p + 1] += d0 * b * im;
+          acc[16 + 2 * p] += d1 * b * re; acc[16 + 2 * p + 1] += d1 * b * im;
+          acc[24 + 2 * p] += d2 * b * re; acc[24 + 2 * p + 1] += d2 * b * im;
         }
       }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          cb[j] += __shfl_xor_sync(0xffffffffu, cb[j], o);
-          bb[0][j] += __shfl_xor_sync(0xffffffffu, bb[0][j], o);
-          bb[1][j] += __shfl_xor_sync(0xffffffffu, bb[1][j], o);
-          bb[2][j] += __shfl_xor_sync(0xffffffffu, bb[2][j], o);
-        }
-      if (lane == 0) {
-        T* pa = part + (at - ab) * 32;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          atomicAdd(&pa[j], cb[j]);
-          atomicAdd(&pa[8 + j], bb[0][j]);
-          atomicAdd(&pa[16 + j], bb[1][j]);
-          atomicAdd(&pa[24 + j], bb[2][j]);
-        }
-      }
+      const T tot = warp_split_sum<32>(acc);       // lane L: total of acc[L]
+      atomicAdd(&part[(at - ab) * 32 + lane], tot);
     }
     __syncthreads();
     if (threadIdx.x < nb) {
@@ -388,8 +415,10 @@ __device__ __forceinline__ void nonlocal_current(const OrbArgs<T>& a, const type
 // OBS (MODE 1): 0 none; 1 norm and current of the propagated orbital, in an extra pass after the
 // last stage; 2 norm and current of the input orbital, accumulated during the first stage from the
 // per-axis derivative sums that stage forms anyway (no extra pass).  MODE 2 always uses 1.
-template <typename T, int MODE, bool PER, bool DBUF, int OBS>
-__global__ void __launch_bounds__(kNTof<T>()) k_cell(OrbArgs<T> a, typename Cplx<T>::type* scratch) {
+template <typename T, int MODE, bool PER, bool DBUF, int OBS, bool IP>
+__global__ void __launch_bounds__(kMaxThreads<T, IP>(), kMinBlocks<T, IP>())
+    k_cell(OrbArgs<T> a, typename Cplx<T>::type* scratch) {
+  static_assert(!IP || (MODE == 1 && !DBUF), "the in-place sweep serves the Taylor stages with one buffer");
   using C = typename Cplx<T>::type;
   using M = CM<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -401,9 +430,10 @@ __global__ void __launch_bounds__(kNTof<T>()) k_cell(OrbArgs<T> a, typename Cplx
   const int vsz = a.nz * ps;
   Smem<T> L;
   L.v = reinterpret_cast<C*>(smem_raw);
-  L.nxt = L.v + vsz;
+  L.nxt = IP ? L.v : L.v + vsz;
   L.ph = L.v + (DBUF ? 2 * vsz : vsz);
   L.ec = L.ph + a.nsph;
+  L.sv = L.ec + 4 * a.natom;
   const int orb = blockIdx.x;
   const int cell = orb / (a.nk * a.norb);
   const int k = (orb - cell * a.nk * a.norb) / a.norb;
@@ -425,7 +455,7 @@ __global__ void __launch_bounds__(kNTof<T>()) k_cell(OrbArgs<T> a, typename Cplx
     const C u = (r < nxy) ? psi[z * nxy + r] : C{0, 0};
     L.v[i] = u;
     if (bk && r < nxy) bk[z * nxy + r] = u;
-    if (DBUF) L.nxt[i] = C{0, 0};
+    if (DBUF && !IP) L.nxt[i] = C{0, 0};
   }
   // wave vector of the observables: k + A'_obs (OBS 1: end of the step; OBS 2: its start)
   auto obs_q = [&](T qo[3]) {
@@ -461,44 +491,98 @@ __global__ void __launch_bounds__(kNTof<T>()) k_cell(OrbArgs<T> a, typename Cplx
     // its input (a separate instance of the loop, so the other stages compile as without them)
     auto local_pass = [&](auto acc_tag) {
       constexpr bool ACC = decltype(acc_tag)::value;
-#pragma unroll 1
-      for (int item = threadIdx.x; item < nitems; item += blockDim.x) {
-        const Column<T, PER> c = make_column<T, PER>(a, item);
+      if constexpr (IP) {
+        const int col = threadIdx.x;
+        const bool act = col < nxy;
+        const Column<T, PER> c = make_column<T, PER>(a, act ? col : 0);
         C w[9];
+        T vnext = T(0);
+        C pnext = C{0, 0};
+        if (act) {
 #pragma unroll
-        for (int j = 0; j < 9; ++j) w[j] = zload<T, PER>(a, L.v, c.z0 - 4 + j, c.col);
-        T vnext = Vc[c.z0 * nxy + c.col];
-        C pnext = (MODE == 1) ? psi[c.z0 * nxy + c.col] : C{0, 0};
+          for (int j = 0; j < 9; ++j) w[j] = zload<T, PER>(a, L.v, j - 4, col);
+          if (PER) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) L.sv[j * nxy + col] = w[4 + j];   // input planes 0..3
+          }
+          vnext = Vc[col];
+          pnext = psi[col];
+        }
 #pragma unroll 1
-        for (int z = c.z0; z < c.z1; ++z) {
+        for (int z = 0; z < a.nz; ++z) {
           const int zb = z * ps;
-          const int pg = z * nxy + c.col;
-          const T diag = diag0 + vnext;
-          const C pv = pnext;
-          if (z + 1 < c.z1) {                   // prefetch the next plane's V and psi
-            vnext = Vc[pg + nxy];
-            if (MODE == 1) pnext = psi[pg + nxy];
-          }
-          C Dd[3];
-          const C hv = local_h<T, PER, ACC && PER>(a, c, L.v, w, zb, diag, q, Dd);
-          if (ACC) {                            // |u|^2 and Im(conj(u) D1_a u)
-            const C u0 = w[4];
-            os[0] += u0.x * u0.x + u0.y * u0.y;
-            if (PER) {
-#pragma unroll
-              for (int d = 0; d < 3; ++d) os[1 + d] += u0.x * Dd[d].y - u0.y * Dd[d].x;
+          C r = C{0, 0};
+          if (act) {
+            const int pg = z * nxy + col;
+            const T diag = diag0 + vnext;
+            const C pv = pnext;
+            if (z + 1 < a.nz) {                 // prefetch the next plane's V and psi
+              vnext = Vc[pg + nxy];
+              pnext = psi[pg + nxy];
             }
-          }
-          C r;
-          if (MODE == 1) {
-            r = M::fma(coef, C{hv.y, -hv.x}, pv);   // psi + (-i coef) H v
-          } else {
-            r = hv;
-          }
-          if (DBUF) L.nxt[zb + c.col] = r; else gnxt[pg] = r;
+            C Dd[3];
+            const C hv = local_h<T, PER, ACC && PER>(a, c, L.v, w, zb, diag, q, Dd);
+            if (ACC) {
+              const C u0 = w[4];
+              os[0] += u0.x * u0.x + u0.y * u0.y;
+              if (PER) {
 #pragma unroll
-          for (int j = 0; j < 8; ++j) w[j] = w[j + 1];
-          w[8] = zload<T, PER>(a, L.v, z + 5, c.col);
+                for (int d = 0; d < 3; ++d) os[1 + d] += u0.x * Dd[d].y - u0.y * Dd[d].x;
+              }
+            }
+            r = M::fma(coef, C{hv.y, -hv.x}, pv);   // psi + (-i coef) H v
+#pragma unroll
+            for (int j = 0; j < 8; ++j) w[j] = w[j + 1];
+            // input plane z + 5: not yet replaced below nz; its periodic image beyond the last
+            // plane is one of the saved planes 0..3 (the value loaded at the last plane is unused)
+            const int zn = z + 5;
+            if (zn < a.nz) w[8] = L.v[zn * ps + col];
+            else if (PER && zn - a.nz < 4) w[8] = L.sv[(zn - a.nz) * nxy + col];
+            else w[8] = C{0, 0};
+          }
+          __syncthreads();                      // every thread has read input plane z
+          if (act) L.v[zb + col] = r;
+        }
+      } else {
+#pragma unroll 1
+        for (int item = threadIdx.x; item < nitems; item += blockDim.x) {
+          const Column<T, PER> c = make_column<T, PER>(a, item);
+          C w[9];
+#pragma unroll
+          for (int j = 0; j < 9; ++j) w[j] = zload<T, PER>(a, L.v, c.z0 - 4 + j, c.col);
+          T vnext = Vc[c.z0 * nxy + c.col];
+          C pnext = (MODE == 1) ? psi[c.z0 * nxy + c.col] : C{0, 0};
+#pragma unroll 1
+          for (int z = c.z0; z < c.z1; ++z) {
+            const int zb = z * ps;
+            const int pg = z * nxy + c.col;
+            const T diag = diag0 + vnext;
+            const C pv = pnext;
+            if (z + 1 < c.z1) {                   // prefetch the next plane's V and psi
+              vnext = Vc[pg + nxy];
+              if (MODE == 1) pnext = psi[pg + nxy];
+            }
+            C Dd[3];
+            const C hv = local_h<T, PER, ACC && PER>(a, c, L.v, w, zb, diag, q, Dd);
+            if (ACC) {                            // |u|^2 and Im(conj(u) D1_a u)
+              const C u0 = w[4];
+              os[0] += u0.x * u0.x + u0.y * u0.y;
+              if (PER) {
+#pragma unroll
+                for (int d = 0; d < 3; ++d) os[1 + d] += u0.x * Dd[d].y - u0.y * Dd[d].x;
+              }
+            }
+            C r;
+            if (MODE == 1) {
+              r = M::fma(coef, C{hv.y, -hv.x}, pv);   // psi + (-i coef) H v
+            } else {
+              r = hv;
+            }
+            if (DBUF) L.nxt[zb + c.col] = r; else gnxt[pg] = r;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) w[j] = w[j + 1];
+            w[8] = zload<T, PER>(a, L.v, z + 5, c.col);
+          }
         }
       }
     };
@@ -516,8 +600,8 @@ __global__ void __launch_bounds__(kNTof<T>()) k_cell(OrbArgs<T> a, typename Cplx
         const C nl = nonlocal_at<T>(a, s, L.ph, L.ec);
         const int pg = a.sp_pt[s];
         const int zz = pg / nxy;
-        const int pidx = DBUF ? pg + zz * (ps - nxy) : pg;
-        C* dst = DBUF ? L.nxt : gnxt;
+        const int pidx = (DBUF || IP) ? pg + zz * (ps - nxy) : pg;
+        C* dst = (DBUF || IP) ? L.nxt : gnxt;
         C r = dst[pidx];
         if (MODE == 1) r = M::fma(coef, C{nl.y, -nl.x}, r);
         else r = M::add(r, nl);
@@ -525,7 +609,7 @@ __global__ void __launch_bounds__(kNTof<T>()) k_cell(OrbArgs<T> a, typename Cplx
       }
       __syncthreads();
     }
-    if (MODE != 2) {
+    if (MODE != 2 && !IP) {
       if (DBUF) {
         C* t = L.v; L.v = L.nxt; L.nxt = t;
       } else {
@@ -543,8 +627,9 @@ __global__ void __launch_bounds__(kNTof<T>()) k_cell(OrbArgs<T> a, typename Cplx
   C* out = a.psi_out ? a.psi_out + (size_t)orb * a.npts : nullptr;
   constexpr bool FINAL_OBS = (OBS == 1);
 #pragma unroll 1
-  for (int item = threadIdx.x; item < nitems; item += blockDim.x) {
-    const Column<T, PER> c = make_column<T, PER>(a, item);
+  for (int item = threadIdx.x; item < (IP ? nxy : nitems); item += blockDim.x) {
+    Column<T, PER> c = make_column<T, PER>(a, item);
+    if (IP) { c.z0 = 0; c.z1 = a.nz; }           // whole columns
     C w[9];
     if (FINAL_OBS) {
 #pragma unroll
@@ -600,11 +685,15 @@ __global__ void __launch_bounds__(kNTof<T>()) k_cell(OrbArgs<T> a, typename Cplx
   reduce_obs<T>(os, qo, a.dV, s_jnl, red, a.obs + (size_t)orb * 8);
 }
 
-template <typename T, int MODE, bool PER, bool DBUF, int OBS>
+template <typename T, int MODE, bool PER, bool DBUF, int OBS, bool IP = false>
 cudaError_t launch_cell(const OrbArgs<T>& a, typename Cplx<T>::type* scratch, size_t smem, int nt,
                         cudaStream_t s) {
-  auto kern = k_cell<T, MODE, PER, DBUF, OBS>;
+  auto kern = k_cell<T, MODE, PER, DBUF, OBS, IP>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  // all of the unified L1 / shared storage as shared memory, so that as many CTAs as the
+  // shared-memory footprint allows are resident on an SM
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
   if (e != cudaSuccess) return e;
   kern<<<a.ncell * a.nk * a.norb, nt, smem, s>>>(a, scratch);
   return cudaGetLastError();
@@ -625,7 +714,21 @@ cudaError_t dispatch(const OrbArgs<T>& a, typename Cplx<T>::type* scratch, cudaS
               : launch_cell<T, MODE, false, false, OBS>(a, scratch, smem, nt, s);
 }
 
+// Taylor stages with the in-place sweep (cell_variant 1).
+template <typename T, int OBS>
+cudaError_t dispatch_ip(const OrbArgs<T>& a, cudaStream_t s) {
+  const size_t smem = cell_smem_bytes_ip<T>(a.nx, a.ny, a.nz, a.pstride, a.nsph, a.natom, a.periodic != 0);
+  const int nt = ((a.nx * a.ny + 31) / 32) * 32;
+  if (a.periodic) return launch_cell<T, 1, true, false, OBS, true>(a, nullptr, smem, nt, s);
+  return launch_cell<T, 1, false, false, OBS, true>(a, nullptr, smem, nt, s);
+}
+
 }  // namespace
+
+template <typename T>
+bool smem_orbital_ip_ok(int nx, int ny, int nz, int pstride, int nsph, int natom, int periodic) {
+  return nx * ny <= kNTip && cell_smem_bytes_ip<T>(nx, ny, nz, pstride, nsph, natom, periodic != 0) <= kSmemLimit;
+}
 
 template <typename T>
 bool smem_orbital_fits(int nz, int pstride, int nsph, int natom) {
@@ -651,12 +754,20 @@ cudaError_t launch_smem_orbital(const OrbArgs<T>& a, int mode, typename Cplx<T>:
                                 cudaStream_t s) {
   if (mode == 0) return dispatch<T, 0, 0>(a, scratch, s);
   if (mode == 1) {
+    if (a.cell_variant == 1) {
+      if (!smem_orbital_ip_ok<T>(a.nx, a.ny, a.nz, a.pstride, a.nsph, a.natom, a.periodic))
+        return cudaErrorInvalidValue;
+      if (!a.obs) return dispatch_ip<T, 0>(a, s);
+      return a.obs_at_start ? dispatch_ip<T, 2>(a, s) : dispatch_ip<T, 1>(a, s);
+    }
     if (!a.obs) return dispatch<T, 1, 0>(a, scratch, s);
     return a.obs_at_start ? dispatch<T, 1, 2>(a, scratch, s) : dispatch<T, 1, 1>(a, scratch, s);
   }
   return dispatch<T, 2, 1>(a, scratch, s);
 }
 
+template bool smem_orbital_ip_ok<float>(int, int, int, int, int, int, int);
+template bool smem_orbital_ip_ok<double>(int, int, int, int, int, int, int);
 template bool smem_orbital_fits<float>(int, int, int, int);
 template bool smem_orbital_fits<double>(int, int, int, int);
 template bool smem_orbital_needs_scratch<float>(int, int, int, int);

@@ -72,6 +72,8 @@ struct tdks_ctx {
   long long wait_limit = 1LL << 22;  // polls per device-side wait of the tile kernels
   int stop_after = -1;              // timeout test: planes the tile producer issues (-1: all)
   float tile_ms[2][kTileVariants] = {{-1.f, -1.f, -1.f}, {-1.f, -1.f, -1.f}};
+  int cell_variant = 0;          // Taylor launches of the cell kernels: 0 two buffers, 1 in-place sweep
+  float cell_ms[2] = {-1.f, -1.f};  // tuning time of one Taylor launch per variant (-1: not available)
   void *d_bufA = nullptr, *d_bufB = nullptr, *d_ec = nullptr;
   int* d_err = nullptr;
   bool have_rho0 = false, have_potential = false;
@@ -196,6 +198,7 @@ OrbArgs<T> make_args(const tdks_ctx* c, const void* in, void* out, const T* V, c
   a.rho = rho;
   a.kw = c->d_kw;
   a.write_out = write_out;
+  a.cell_variant = c->cell_variant;
   return a;
 }
 
@@ -507,6 +510,71 @@ tdks_status tune_tile(tdks_ctx* c) {
   return TDKS_OK;
 }
 
+bool cell_ip_ok(const tdks_ctx* c) {
+  const int* n = c->grid.n;
+  return !c->tiled &&
+         (is_f32(c) ? smem_orbital_ip_ok<float>(n[0], n[1], n[2], c->pstride, c->nsph, c->natom, c->grid.periodic)
+                    : smem_orbital_ip_ok<double>(n[0], n[1], n[2], c->pstride, c->nsph, c->natom, c->grid.periodic));
+}
+
+// Times one Taylor launch of each cell-kernel buffer scheme on zero orbitals -- up to 1216 of them
+// (eight waves of one CTA per SM) -- and keeps the faster scheme.  The launch is the corrector's:
+// four Horner stages with the per-orbital observables of the context's choice (input or output
+// state), no orbital or density output.
+tdks_status tune_cell(tdks_ctx* c) {
+  c->cell_variant = 0;
+  c->cell_ms[0] = c->cell_ms[1] = -1.f;
+  if (!cell_ip_ok(c)) return TDKS_OK;
+  const int nsub = std::min(c->ncell * c->nk * c->norb, 1216);
+  const size_t csz = is_f32(c) ? sizeof(float2) : sizeof(double2);
+  void* buf = nullptr;
+  TDKS_CUDA(cudaMalloc(&buf, csz * (size_t)nsub * c->npts));
+  cudaError_t err = cudaMemsetAsync(buf, 0, csz * (size_t)nsub * c->npts, c->stream);
+  if (err == cudaSuccess)
+    err = is_f32(c) ? cudaMemsetAsync(c->d_v32, 0, (size_t)c->npts * sizeof(float), c->stream)
+                    : cudaMemsetAsync(c->d_v64, 0, (size_t)c->npts * sizeof(double), c->stream);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (err == cudaSuccess) err = cudaEventCreate(&e0);
+  if (err == cudaSuccess) err = cudaEventCreate(&e1);
+  float best = 0.f;
+  for (int v = 0; v < 2 && err == cudaSuccess; ++v) {
+    auto run = [&]() -> cudaError_t {
+      if (is_f32(c)) {
+        auto a = make_args<float>(c, buf, buf, c->d_v32, nullptr, 0.02, nullptr, 0);
+        a.ncell = 1; a.nk = 1; a.norb = nsub; a.vstride = 0; a.Ap_cell = a.Ap_obs_cell = nullptr;
+        a.backup = nullptr;
+        a.obs = c->d_orb_obs;
+        a.obs_at_start = c->opt.obs_at_start;
+        a.cell_variant = v;
+        return launch_smem_orbital<float>(a, 1, static_cast<float2*>(c->d_scratch), c->stream);
+      }
+      auto a = make_args<double>(c, buf, buf, c->d_v64, nullptr, 0.02, nullptr, 0);
+      a.ncell = 1; a.nk = 1; a.norb = nsub; a.vstride = 0; a.Ap_cell = a.Ap_obs_cell = nullptr;
+      a.backup = nullptr;
+      a.obs = c->d_orb_obs;
+      a.obs_at_start = c->opt.obs_at_start;
+      a.cell_variant = v;
+      return launch_smem_orbital<double>(a, 1, static_cast<double2*>(c->d_scratch), c->stream);
+    };
+    err = run();
+    if (err == cudaSuccess) err = cudaEventRecord(e0, c->stream);
+    for (int r = 0; r < 2 && err == cudaSuccess; ++r) err = run();
+    if (err == cudaSuccess) err = cudaEventRecord(e1, c->stream);
+    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+    if (err != cudaSuccess) break;
+    c->cell_ms[v] = 0.5f * ms;
+    if (v == 0 || c->cell_ms[v] < best) { best = c->cell_ms[v]; c->cell_variant = v; }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaStreamSynchronize(c->stream);
+  cudaFree(buf);
+  if (err != cudaSuccess) return fail(TDKS_ECUDA, std::string("cell tuning: ") + cudaGetErrorString(err));
+  return TDKS_OK;
+}
+
 extern "C" {
 
 const char* tdks_last_error(void) { return g_err.c_str(); }
@@ -693,6 +761,7 @@ tdks_status tdks_init(const tdks_grid* grid, const tdks_cell* cell, const tdks_a
       return bail(fail(TDKS_ECUDA, "ghat"));
   }
   if ((s = tune_tile(c)) != TDKS_OK) return bail(s);
+  if ((s = tune_cell(c)) != TDKS_OK) return bail(s);
   if (cudaStreamSynchronize(c->stream) != cudaSuccess)
     return bail(fail(TDKS_ECUDA, std::string("init: ") + cudaGetErrorString(cudaGetLastError())));
   *out = c;
@@ -810,18 +879,21 @@ tdks_status predicted_step(tdks_ctx* c, void* u, const double Amid[3], const dou
   const bool net = c->pred_mode == TDKS_PRED_LEARNED;
   {
     Phase ph(c, 5);
-    if (net) {
-      TDKS_CUDA(nn_inputs(c->nn, g, hist_slot(c, 0), hist_slot(c, 1), hist_slot(c, 2), hist_slot(c, 3), nullptr, c->stream));
-      TDKS_CUDA(nn_forward(c->nn, g, c->stream));
+    if (net) {   // statistics, packing, three layers; the last one forms the prediction
+      const NNPredict pr{hist_slot(c, 0), hist_slot(c, 1), hist_slot(c, 2), hist_slot(c, 3), c->d_vpred};
+      TDKS_CUDA(nn_inputs(c->nn, g, hist_slot(c, 0), hist_slot(c, 1), hist_slot(c, 2), hist_slot(c, 3), nullptr,
+                          c->stream, true));
+      TDKS_CUDA(nn_forward(c->nn, g, c->stream, &pr));
       c->launches += 5;
+    } else {
+      TDKS_CUDA(nn_apply(c->nn, g, hist_slot(c, 0), hist_slot(c, 1), hist_slot(c, 2), hist_slot(c, 3), 1,
+                         c->d_vpred, c->stream));
+      c->launches += 1;
     }
-    TDKS_CUDA(nn_apply(c->nn, g, hist_slot(c, 0), hist_slot(c, 1), hist_slot(c, 2), hist_slot(c, 3),
-                       net ? 2 : 1, c->d_vpred, c->stream));
     // the shared-memory cell kernel writes the backup while it loads the orbitals; the tile path
     // copies it first
     if (c->tiled) TDKS_CUDA(cudaMemcpyAsync(c->d_backup, u, obytes, cudaMemcpyDeviceToDevice, c->stream));
     TDKS_CUDA(cudaMemsetAsync(c->d_rho, 0, gb, c->stream));
-    c->launches += 1;
   }
   TDKS_TRY(set_step_potential(c, 0.5, c->d_vpred, 0.5));
   c->cur_backup = c->tiled ? nullptr : c->d_backup;
@@ -1173,9 +1245,13 @@ tdks_status tdks_nn_predict(tdks_ctx* c, const double* vhist, double* vpred, int
   if (mode < 0 || mode > 2) return fail(TDKS_EINVAL, "mode must be 0 (linear), 1 (cubic) or 2 (network)");
   const NNGrid g = nn_grid(c);
   const size_t np = c->npts;
-  TDKS_CUDA(nn_inputs(c->nn, g, vhist, vhist + np, vhist + 2 * np, vhist + 3 * np, nullptr, c->stream));
-  if (mode == 2) TDKS_CUDA(nn_forward(c->nn, g, c->stream));
-  TDKS_CUDA(nn_apply(c->nn, g, vhist, vhist + np, vhist + 2 * np, vhist + 3 * np, mode, vpred, c->stream));
+  TDKS_CUDA(nn_inputs(c->nn, g, vhist, vhist + np, vhist + 2 * np, vhist + 3 * np, nullptr, c->stream, mode == 2));
+  if (mode == 2) {
+    const NNPredict pr{vhist, vhist + np, vhist + 2 * np, vhist + 3 * np, vpred};
+    TDKS_CUDA(nn_forward(c->nn, g, c->stream, &pr));
+  } else {
+    TDKS_CUDA(nn_apply(c->nn, g, vhist, vhist + np, vhist + 2 * np, vhist + 3 * np, mode, vpred, c->stream));
+  }
   return TDKS_OK;
 }
 
@@ -1236,6 +1312,18 @@ tdks_status tdks_tile_variant(tdks_ctx* c, int set, int* variant, float* tune_ms
   if (tune_ms)
     for (int m = 0; m < 2; ++m)
       for (int v = 0; v < kTileVariants; ++v) tune_ms[m * kTileVariants + v] = c->tile_ms[m][v];
+  return TDKS_OK;
+}
+
+tdks_status tdks_cell_variant(tdks_ctx* c, int set, int* variant, float* tune_ms) {
+  TDKS_TRY(check_ctx(c));
+  if (set < -1 || set > 1) return fail(TDKS_EINVAL, "cell variant outside -1..1");
+  if (c->tiled) return fail(TDKS_EUNSUPPORTED, "this context uses the tile kernels");
+  if (set == 1 && !cell_ip_ok(c))
+    return fail(TDKS_EUNSUPPORTED, "the in-place sweep needs nx * ny <= 448 and one orbital copy in shared memory");
+  if (set >= 0) c->cell_variant = set;
+  if (variant) *variant = c->cell_variant;
+  if (tune_ms) { tune_ms[0] = c->cell_ms[0]; tune_ms[1] = c->cell_ms[1]; }
   return TDKS_OK;
 }
 

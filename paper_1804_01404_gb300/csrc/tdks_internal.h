@@ -108,12 +108,14 @@ struct OrbArgs {
   long long vstride;        // offset of a cell's potential (0: one potential shared by all)
   const double* Ap_cell;    // nullable: [ncell][3] A' per cell, replaces Ap
   const double* Ap_obs_cell;// nullable: [ncell][3], replaces Ap_obs
+  int cell_variant;         // Taylor stages: 0 two buffers, 1 one buffer swept in place
 };
 
 // Orbital kernels (k_orbital.cu)
 // Shared-memory cell kernels.  mode 0: H u; 1: T4 (Horner) with optional density and fused
 // observables (a.obs); 2: observables of u (norm, current, <u|H|u> with a.V) into a.obs.
 // scratch = [norb_tot][npts] global buffer, needed only when smem_orbital_needs_scratch().
+// Mode 1 with a.cell_variant = 1 sweeps one shared-memory buffer in place (smem_orbital_ip_ok).
 template <typename T>
 cudaError_t launch_smem_orbital(const OrbArgs<T>& a, int mode, typename Cplx<T>::type* scratch,
                                 cudaStream_t s);
@@ -121,7 +123,8 @@ template <typename T>
 bool smem_orbital_fits(int nz, int pstride, int nsph, int natom);
 template <typename T>
 bool smem_orbital_needs_scratch(int nz, int pstride, int nsph, int natom);
-// threads per column (nseg) and planes per thread (zlen) for the cell kernels
+template <typename T>
+bool smem_orbital_ip_ok(int nx, int ny, int nz, int pstride, int nsph, int natom, int periodic);
 // column segments of the cell kernels; elem_bytes = bytes of one complex value (8: FP32, 16: FP64)
 void cell_split(int nx, int ny, int nz, int elem_bytes, int* nseg, int* zlen);
 
@@ -185,9 +188,18 @@ struct NNBuffers {
   unsigned* ticket;                               // grid_sum ticket (zero between launches)
 };
 int nn_part_blocks(int npts);
+// channel_last: inputs for nn_forward with a prediction epilogue (which reads them channel-last)
 cudaError_t nn_inputs(const NNBuffers& B, const NNGrid& g, const double* V0, const double* V1,
-                      const double* V2, const double* V3, const double* Vnext, cudaStream_t s);
-cudaError_t nn_forward(const NNBuffers& B, const NNGrid& g, cudaStream_t s);
+                      const double* V2, const double* V3, const double* Vnext, cudaStream_t s,
+                      bool channel_last = false);
+// Optional epilogue of the last layer: vpred = cubic(V0..V3) + s3 * out (the predictor's mode 2).
+// With it the layers run on channel-last inputs and activations (nn_inputs with channel_last) and
+// leave no pre-activations for a backward pass.
+struct NNPredict {
+  const double *V0, *V1, *V2, *V3;
+  double* vpred;
+};
+cudaError_t nn_forward(const NNBuffers& B, const NNGrid& g, cudaStream_t s, const NNPredict* pred = nullptr);
 cudaError_t nn_loss(const NNBuffers& B, const NNGrid& g, double* loss_acc, cudaStream_t s);
 cudaError_t nn_backward(const NNBuffers& B, const NNGrid& g, cudaStream_t s);   // grad +=
 cudaError_t nn_adam(const NNBuffers& B, float lr, int t, float gscale, cudaStream_t s);

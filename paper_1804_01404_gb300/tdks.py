@@ -113,6 +113,7 @@ def load_library(path: str = LIB_PATH):
         "tdks_stats_read": [vp, C.POINTER(Stats), i],
         "tdks_query": [vp, C.POINTER(i), C.POINTER(i), C.POINTER(i), C.POINTER(i), C.POINTER(i)],
         "tdks_tile_variant": [vp, i, C.POINTER(i), C.POINTER(C.c_float)],
+        "tdks_cell_variant": [vp, i, C.POINTER(i), C.POINTER(C.c_float)],
         "tdks_set_wait_test": [vp, C.c_longlong, i],
         "tdks_state_size": [vp, C.POINTER(C.c_size_t)],
         "tdks_ms_size": [vp, C.POINTER(i)],
@@ -319,6 +320,14 @@ class Context:
         ms = (C.c_float * 6)()
         _check(self.lib.tdks_tile_variant(self.ctx, int(set), v, ms))
         return [v[0], v[1]], [[float(x) for x in ms[:3]], [float(x) for x in ms[3:]]]
+
+    def cell_variant(self, set=-1):
+        """Buffer scheme of the cell kernels' Taylor launches (tdks_cell_variant): returns (scheme in
+        use, tuning ms [two buffers, in-place sweep])."""
+        v = C.c_int()
+        ms = (C.c_float * 2)()
+        _check(self.lib.tdks_cell_variant(self.ctx, int(set), C.byref(v), ms))
+        return v.value, [float(ms[0]), float(ms[1])]
 
     def get_state(self):
         """Checkpoint of the time-stepping state (tdks_get_state) as a numpy uint8 array."""
