@@ -19,6 +19,7 @@ namespace {
 
 constexpr int kFftThreads = 256;
 constexpr int kMaxRadices = 16;
+constexpr size_t kPlaneSmemLimit = 160 * 1024;   // xy-plane kernels: twiddles + two plane buffers
 
 struct FftPlanArgs {
   int nrad;
@@ -121,6 +122,32 @@ __device__ void butterfly_generic(const double2* __restrict__ src, double2* __re
   }
 }
 
+// Transforms nl lines of length n stored one after another in src (Stockham, ping-ponging between
+// src and dst); on return src holds the result.  All threads of the CTA take part.
+__device__ __forceinline__ void stockham_lines(double2*& src, double2*& dst, int n, int nl, const double2* tw,
+                                               const FftPlanArgs& plan, int dir) {
+  int Ns = 1;
+  for (int s = 0; s < plan.nrad; ++s) {
+    const int R = plan.rad[s];
+    const int nb = n / R;
+    for (int b = threadIdx.x; b < nl * nb; b += blockDim.x) {
+      const int j = b / nb, jb = b - j * nb;
+      const double2* sl = src + j * n;
+      double2* dl = dst + j * n;
+      switch (R) {
+        case 2: butterfly<2>(sl, dl, n, Ns, jb, tw, dir); break;
+        case 3: butterfly<3>(sl, dl, n, Ns, jb, tw, dir); break;
+        case 4: butterfly<4>(sl, dl, n, Ns, jb, tw, dir); break;
+        case 5: butterfly<5>(sl, dl, n, Ns, jb, tw, dir); break;
+        default: butterfly_generic(sl, dl, n, R, Ns, jb, tw, dir); break;
+      }
+    }
+    __syncthreads();
+    double2* t = src; src = dst; dst = t;
+    Ns *= R;
+  }
+}
+
 // Optional work fused into a line pass, so the Hartree + exchange solve takes five launches:
 //   load_real  (x pass, forward): lines are read from a real array [n2*batch][n1][n0], zero padded
 //              to the transform box, instead of from `data` (replaces a packing kernel);
@@ -195,29 +222,7 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_lines(double2* data, int n,
   __syncthreads();
   double2* src = b0;
   double2* dst = b1;
-  auto transform = [&](int d) {
-    int Ns = 1;
-    for (int s = 0; s < plan.nrad; ++s) {
-      const int R = plan.rad[s];
-      const int nb = n / R;
-      for (int b = threadIdx.x; b < nl * nb; b += blockDim.x) {
-        const int j = b / nb, jb = b - j * nb;
-        const double2* sl = src + j * n;
-        double2* dl = dst + j * n;
-        switch (R) {
-          case 2: butterfly<2>(sl, dl, n, Ns, jb, tw, d); break;
-          case 3: butterfly<3>(sl, dl, n, Ns, jb, tw, d); break;
-          case 4: butterfly<4>(sl, dl, n, Ns, jb, tw, d); break;
-          case 5: butterfly<5>(sl, dl, n, Ns, jb, tw, d); break;
-          default: butterfly_generic(sl, dl, n, R, Ns, jb, tw, d); break;
-        }
-      }
-      __syncthreads();
-      double2* t = src; src = dst; dst = t;
-      Ns *= R;
-    }
-  };
-  transform(dir);
+  stockham_lines(src, dst, n, nl, tw, plan, dir);
   if (hk.spectral) {
     for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
       const int j = idx / n, e = idx - j * n;
@@ -237,7 +242,7 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_lines(double2* data, int n,
       src[idx] = double2{v.x * f, v.y * f};
     }
     __syncthreads();
-    transform(-dir);
+    stockham_lines(src, dst, n, nl, tw, plan, -dir);
   }
   for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
     int j, e;
@@ -256,6 +261,67 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_lines(double2* data, int n,
       const long long l = l0 + j;
       const long long start = (l % cnt_lo) * s_lo + (l / cnt_lo) * s_hi;
       data[start + e * estride] = src[j * n + e];
+    }
+  }
+}
+
+// Periodic boxes whose xy-plane fits in shared memory: the x and y passes of the Hartree solve run
+// in one launch, one CTA per (z plane, cell), with the plane transposed in shared memory between
+// the two line sets.  Forward (FWD): the real density plane rho[cell][z] is transformed along x,
+// then y, and written to data.  Inverse: the plane of data is transformed back along y, then x, and
+// the epilogue writes vhxc = Re(value) + V_x(rho) (Slater exchange if xc).  Twiddle tables tw0
+// (length m0) and tw1 (length m1); shared memory: m0 + m1 twiddles and two m0 m1 buffers.
+template <bool FWD>
+__global__ void __launch_bounds__(kFftThreads) k_fft_planes(double2* data, int m0, int m1, int m2,
+                                                            const double2* __restrict__ tw0_g,
+                                                            const double2* __restrict__ tw1_g,
+                                                            FftPlanArgs plan0, FftPlanArgs plan1,
+                                                            const double* __restrict__ rho, int xc,
+                                                            double* __restrict__ vhxc) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int np = m0 * m1;
+  double2* tw0 = reinterpret_cast<double2*>(smem_raw);
+  double2* tw1 = tw0 + m0;
+  double2* b0 = tw1 + m1;
+  double2* b1 = b0 + np;
+  for (int t = threadIdx.x; t < m0; t += blockDim.x) tw0[t] = tw0_g[t];
+  for (int t = threadIdx.x; t < m1; t += blockDim.x) tw1[t] = tw1_g[t];
+  const long long plane = (long long)blockIdx.x * np;   // blockIdx.x = cell * m2 + z
+  double2* src = b0;
+  double2* dst = b1;
+  if (FWD) {
+    for (int i = threadIdx.x; i < np; i += blockDim.x) b0[i] = double2{rho[plane + i], 0.0};   // [y][x]
+    __syncthreads();
+    stockham_lines(src, dst, m0, m1, tw0, plan0, -1);                 // x lines
+    for (int i = threadIdx.x; i < np; i += blockDim.x) {              // [y][x] -> [x][y]
+      const int y = i / m0, x = i - y * m0;
+      dst[x * m1 + y] = src[i];
+    }
+    __syncthreads();
+    { double2* t = src; src = dst; dst = t; }
+    stockham_lines(src, dst, m1, m0, tw1, plan1, -1);                 // y lines
+    for (int i = threadIdx.x; i < np; i += blockDim.x) {              // [x][y] -> global [y][x]
+      const int y = i / m0, x = i - y * m0;
+      data[plane + i] = src[x * m1 + y];
+    }
+  } else {
+    for (int i = threadIdx.x; i < np; i += blockDim.x) {              // global [y][x] -> [x][y]
+      const int y = i / m0, x = i - y * m0;
+      b0[x * m1 + y] = data[plane + i];
+    }
+    __syncthreads();
+    stockham_lines(src, dst, m1, m0, tw1, plan1, +1);                 // y lines
+    for (int i = threadIdx.x; i < np; i += blockDim.x) {              // [x][y] -> [y][x]
+      const int y = i / m0, x = i - y * m0;
+      dst[i] = src[x * m1 + y];
+    }
+    __syncthreads();
+    { double2* t = src; src = dst; dst = t; }
+    stockham_lines(src, dst, m0, m1, tw0, plan0, +1);                 // x lines
+    for (int i = threadIdx.x; i < np; i += blockDim.x) {
+      double v = src[i].x;
+      if (xc) v -= cbrt(3.0 * fmax(rho[plane + i], 0.0) / kPi);     // Slater exchange
+      vhxc[plane + i] = v;
     }
   }
 }
@@ -594,16 +660,46 @@ cudaError_t launch_fft_axis_hooked(double2* data, const int dims[3], int axis, i
 
 // Hartree (periodic 4 pi / G^2, or Hockney with the kernel spectrum ghat) + exchange in five line
 // passes: x forward from the real density, y forward, z forward-multiply-inverse, y inverse, and
-// x inverse writing vhxc (see FftHooks).
+// x inverse writing vhxc (see FftHooks).  Periodic boxes whose xy-plane fits in shared memory take
+// three launches instead: xy planes forward, the z pass, xy planes inverse with the epilogue
+// (k_fft_planes).  *nlaunch (nullable) receives the number of launches.
 cudaError_t launch_hartree_xc_fused(double2* work, const int m[3], const int n[3], int batch, int periodic,
                                     const double h[3], const double* ghat, double gscale,
                                     double2* const tw[3], const int* const rad[3], const int nrad[3],
-                                    const double* rho, int xc, double* vhxc, cudaStream_t s) {
+                                    const double* rho, int xc, double* vhxc, cudaStream_t s, int* nlaunch) {
   FftHooks base;
   std::memset(&base, 0, sizeof(base));
   base.n0 = n[0]; base.n1 = n[1]; base.n2 = n[2];
   const int lo_x = periodic ? 0 : n[1], hi_xy = periodic ? 0 : n[2];
   cudaError_t e;
+  const size_t plane_smem = ((size_t)m[0] + m[1] + 2 * (size_t)m[0] * m[1]) * sizeof(double2);
+  if (periodic && plane_smem <= kPlaneSmemLimit && nrad[0] <= kMaxRadices && nrad[1] <= kMaxRadices) {
+    // three launches: xy planes forward, z forward-multiply-inverse, xy planes inverse + exchange
+    FftPlanArgs p0, p1;
+    p0.nrad = nrad[0];
+    p1.nrad = nrad[1];
+    for (int i = 0; i < nrad[0]; ++i) p0.rad[i] = rad[0][i];
+    for (int i = 0; i < nrad[1]; ++i) p1.rad[i] = rad[1][i];
+    const int grid = m[2] * batch;
+    if ((e = cudaFuncSetAttribute(k_fft_planes<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)plane_smem)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_fft_planes<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)plane_smem)) != cudaSuccess) return e;
+    k_fft_planes<true><<<grid, kFftThreads, plane_smem, s>>>(work, m[0], m[1], m[2], tw[0], tw[1], p0, p1, rho,
+                                                             0, nullptr);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    FftHooks h3 = base;
+    h3.spectral = 1;
+    for (int a = 0; a < 3; ++a) h3.L[a] = m[a] * h[a];
+    h3.inv_n = 1.0 / ((double)m[0] * m[1] * m[2]);
+    if ((e = launch_fft_axis_hooked(work, m, 2, -1, tw[2], rad[2], nrad[2], s, batch, 0, 0, &h3)) != cudaSuccess)
+      return e;
+    k_fft_planes<false><<<grid, kFftThreads, plane_smem, s>>>(work, m[0], m[1], m[2], tw[0], tw[1], p0, p1, rho,
+                                                              xc, vhxc);
+    if (nlaunch) *nlaunch = 3;
+    return cudaGetLastError();
+  }
+  if (nlaunch) *nlaunch = 5;
   FftHooks h1 = base;
   h1.load_real = 1;
   h1.rsrc = rho;

@@ -404,14 +404,16 @@ tdks_status hxc(tdks_ctx* c, const double* rho, double* vhxc) {
   const int ns[3] = {c->grid.n[0], c->grid.n[1], c->grid.n[2] * c->ncell};
   const int ms[3] = {c->m[0], c->m[1], c->m[2] * c->ncell};
   if (c->opt.hartree) {
-    // five line passes with the packing, the Poisson factor and the exchange epilogue fused in
+    // three (periodic xy planes in shared memory) or five line passes with the packing, the
+    // Poisson factor and the exchange epilogue fused in
     const double npad = (double)c->m[0] * c->m[1] * c->m[2];
     const int* rad[3] = {c->rad[0].data(), c->rad[1].data(), c->rad[2].data()};
     const int nrad[3] = {(int)c->rad[0].size(), (int)c->rad[1].size(), (int)c->rad[2].size()};
+    int nl = 0;
     TDKS_CUDA(launch_hartree_xc_fused(c->d_fft, c->m, c->grid.n, c->ncell, c->grid.periodic, c->grid.h,
                                       c->d_ghat, c->dV / npad, c->d_tw, rad, nrad, rho, c->opt.xc,
-                                      vhxc, c->stream));
-    c->launches += 5;
+                                      vhxc, c->stream, &nl));
+    c->launches += nl;
     return TDKS_OK;
   }
   c->launches += 1;

@@ -217,7 +217,8 @@ cudaError_t launch_residual(const double* Vnew, const double* Vpred, int n, doub
 cudaError_t launch_hartree_xc_fused(double2* work, const int m[3], const int n[3], int batch, int periodic,
                                     const double h[3], const double* ghat, double gscale,
                                     double2* const tw[3], const int* const rad[3], const int nrad[3],
-                                    const double* rho, int xc, double* vhxc, cudaStream_t s);
+                                    const double* rho, int xc, double* vhxc, cudaStream_t s,
+                                    int* nlaunch = nullptr);
 // batch = number of consecutive [dims2][dims1][dims0] arrays transformed together
 // lim_lo / lim_hi > 0: transform only the lines whose two other coordinates (lo: the faster of
 // them, hi: the slower, batch included for the last axis) are below the limits
