@@ -367,6 +367,7 @@ def gpu_arm(args, rank, world, local_rank):
     others = None
     if rank == 0 and not args.skip_workloads:
         others = workload_steps(dev)
+        others["absorption_peak"] = absorption_peak_check(dev)
 
     cpu = None
     if rank == 0 and not args.skip_cpu:
@@ -602,6 +603,49 @@ def workload_steps(dev, warmup=2, steps=5):
     return out
 
 
+def absorption_peak_check(dev, nsteps=1000, kappa=1e-3):
+    """Eq. (distribution) spectrum of a kicked isolated cluster (32^3 grid, h = 0.4, 8 atoms,
+    16 orbitals, impulse exp(i kappa z)) propagated on the GPU with FP64 orbitals and with FP32
+    orbitals (plain predictor-corrector both); the main absorption peak of each, located on a
+    0.001 eV grid with tdks_oscillator_strength, and their distance (criterion: 0.01 eV)."""
+    import torch
+    from paper_1804_01404_gb300 import tdks as T
+    from paper_1804_01404_gb300 import workloads as W
+    ev = 27.211386245988
+    s = W.isolated_cluster(n=32, natom=8, norb=16, radius=5.0, seed=2)
+    psi0 = W.initial_orbitals(s, 1)
+    res = {"workload": "isolated cluster 32^3 (h = 0.4), 8 atoms, 16 orbitals, kick 1e-3 along z, "
+                       f"{nsteps} predictor-corrector steps of dt = {s.dt}", "steps": nsteps}
+    peaks = {}
+    for prec in ("f64", "f32"):
+        ctx = T.Context(s, precision=prec)
+        u = torch.from_numpy(psi0.astype(np.complex128 if prec == "f64" else np.complex64)).to(dev)
+        ctx.kick(u, (0.0, 0.0, kappa))
+        ctx.update_potential(u)
+        d = [0.0]
+        tt = 0.0
+        torch.cuda.synchronize()
+        tic = time.perf_counter()
+        for _ in range(nsteps):
+            ctx.step(u, tt, s.dt)
+            tt += s.dt
+            d.append(ctx.read_step_observables()["dipole"][2])
+        res[f"{prec}_steps_per_s_host_synced"] = nsteps / (time.perf_counter() - tic)
+        ctx.check()
+        ctx.close()
+        d = np.array(d)
+        E = np.arange(0.0, 2.0, 0.005)
+        E0 = E[np.argmax(T.oscillator_strength(d, s.dt, kappa, E))]
+        Ef = np.arange(max(E0 - 0.01, 1e-6), E0 + 0.01, 0.001 / ev)
+        peaks[prec] = (float(Ef[np.argmax(T.oscillator_strength(d, s.dt, kappa, Ef))]), d)
+    res["peak_eV"] = {p: v[0] * ev for p, v in peaks.items()}
+    res["peak_shift_f32_vs_f64_eV"] = abs(peaks["f32"][0] - peaks["f64"][0]) * ev
+    d64, d32 = peaks["f64"][1], peaks["f32"][1]
+    res["dipole_rel_err_f32_vs_f64"] = float(np.max(np.abs(d32 - d64)) / np.max(np.abs(d64)))
+    res["resolution_eV"] = 2 * np.pi / (nsteps * s.dt) * ev
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -638,7 +682,10 @@ def main():
         import torch
         torch.cuda.set_device(local_rank)
         if rank == 0:
-            print(json.dumps({"other_workloads": workload_steps(torch.device("cuda", local_rank))}))
+            dev = torch.device("cuda", local_rank)
+            others = workload_steps(dev)
+            others["absorption_peak"] = absorption_peak_check(dev)
+            print(json.dumps({"other_workloads": others}))
         return 0
     if world > 1:
         import torch.distributed as dist

@@ -327,6 +327,30 @@ tdks_status tdks_set_wait_test(tdks_ctx* ctx, long long wait_limit, int stop_aft
 tdks_status tdks_hxc_noalloc(const tdks_grid* grid, const double* rho_dev, double* vhxc_dev,
                              int hartree, int xc, void* stream);
 
+/* Response analysis of a finished run (no context needed; FP64 on the GPU; host arrays in and out;
+ * synchronous on `stream`, a cudaStream_t or NULL for the legacy default stream; device scratch is
+ * allocated and freed inside the call).  Both transform a series x_i sampled at t_i = i dt,
+ * i = 0..nt-1, with the cubic mask f(s) = 1 - 3 s^2 + 2 s^3 of s = t_i / T, T = (nt - 1) dt:
+ *   F(w) = dt sum_i f(t_i / T) (x_i - xbar) exp(i w t_i).
+ * Errors: EINVAL for a null array, nt < 2, nw outside 1..2^24, dt <= 0, kappa or Ap0 zero, or (eps
+ * requested) a frequency <= 0; ENOMEM / ECUDA from the device. */
+
+/* Oscillator-strength distribution, Sec. 3.1 Eq. (distribution), in Hartree units (m = hbar = e = 1):
+ * dfdE[j] = -(2 E_j / (pi kappa)) Im F(E_j) for the dipole series d[nt] (one Cartesian component)
+ * after the kick exp(i kappa r_nu) of tdks_kick (field impulse F0 = -kappa; dividing by the kick
+ * strength makes the distribution positive and its integral over E the f-sum); xbar = 0. */
+tdks_status tdks_oscillator_strength(const double* d, int nt, double dt, double kappa, const double* E,
+                                     int nE, double* dfdE, void* stream);
+
+/* Conductivity and dielectric function, Sec. 4.1 Eq. (sigma_ft):
+ * sigma[2j], sigma[2j+1] = Re, Im of -(c / A0) F(w_j) = -F(w_j) / Ap0 for the current series I[nt]
+ * (one component) after the vector-potential step A'(t) = Ap0 theta(t) (A' = A/c, as in
+ * tdks_set_field); eps (nullable) = 1 + 4 pi i sigma / w in the same layout.  subtract_mean != 0
+ * first removes the mask-weighted mean xbar = sum f I / sum f, which makes sigma(0) = 0 exactly
+ * (the Sec. 4.1 example removes a small constant current for this reason); otherwise xbar = 0. */
+tdks_status tdks_conductivity(const double* I, int nt, double dt, double Ap0, const double* w, int nw,
+                              int subtract_mean, double* sigma, double* eps, void* stream);
+
 const char* tdks_last_error(void);
 int tdks_abi_version(void);
 void tdks_destroy(tdks_ctx* ctx);

@@ -22,6 +22,7 @@ What it computes (Hartree atomic units, hbar = m = e = 1, A' = A/c):
   isolated boxes with a zero-padded (Hockney) convolution.
 * Sec. 3.1 LDA: adiabatic local exchange (Slater exchange only in this build).
 * Sec. 3.1: dipole d = -int r (rho - rho0); Eq. (distribution): oscillator-strength spectrum.
+* Sec. 4.1, Eq. (sigma_ft): conductivity and dielectric function from the current after an A step.
 * Eq. (macro_current): macroscopic current including the nonlocal term.
 * Eq. (pulse), Eq. (impulsive_A): fields.
 * Eq. (Maxwell_ms): 1D wave equation driven by the cell currents.
@@ -32,7 +33,8 @@ notes; each is restated at the function that uses it.
 
 Parity status: every function here is pinned by the CPU tests against closed forms, brute
 force or invariants (plane-wave dispersion, dense eigendecomposition, Hockney direct sum,
-Gaussian/cosine charges, J = -dE/dA'/Omega, energy conservation, f-sum slope).  The full
+Gaussian/cosine charges, J = -dE/dA'/Omega, energy conservation, f-sum slope, the closed-form
+masked Fourier integral and the free-electron plasma limit of eps).  The full
 predictor-corrector step has no closed form: it is pinned only through those invariants.
 """
 from __future__ import annotations
@@ -430,7 +432,7 @@ def run(s, psi0, nsteps, pc=True, hartree_on=True, xc_on=True, record=True):
 
 
 # --------------------------------------------------------------------------------------------
-# analysis: Eq. (distribution), Eq. (Maxwell_ms)
+# analysis: Eq. (distribution), Eq. (sigma_ft), Eq. (Maxwell_ms)
 # --------------------------------------------------------------------------------------------
 def oscillator_strength(t, d, kappa, energies):
     """df/dE = -(2E/(pi kappa)) Im int_0^T f(t/T) d(t) exp(iEt) dt, f(x) = 1 - 3x^2 + 2x^3.
@@ -445,6 +447,33 @@ def oscillator_strength(t, d, kappa, energies):
     E = np.asarray(energies, np.float64)
     integ = (f * d)[None, :] * np.exp(1j * E[:, None] * t[None, :])
     return -(2.0 * E / (np.pi * kappa)) * np.imag(integ.sum(axis=1) * dt)
+
+
+def masked_transform(t, x, omegas, subtract_mean=False):
+    """F(w) = dt sum_i f(t_i/T) (x_i - xbar) exp(i w t_i), f(s) = 1 - 3s^2 + 2s^3, T = t[-1]: the
+    rectangle-rule form of the masked integrals of Eq. (distribution) and Eq. (sigma_ft).  With
+    subtract_mean, xbar = sum f x / sum f (the mean whose removal makes F(0) = 0, as the Sec. 4.1
+    example requires of sigma), else 0."""
+    t = np.asarray(t, np.float64)
+    x = np.asarray(x, np.float64)
+    T = t[-1]
+    dt = t[1] - t[0]
+    s = t / T
+    f = 1.0 - 3.0 * s ** 2 + 2.0 * s ** 3
+    xbar = np.sum(f * x) / np.sum(f) if subtract_mean else 0.0
+    w = np.asarray(omegas, np.float64)
+    return ((f * (x - xbar))[None, :] * np.exp(1j * w[:, None] * t[None, :])).sum(axis=1) * dt
+
+
+def conductivity(t, I, Ap0, omegas, subtract_mean=True):
+    """Eq. (sigma_ft): sigma(w) = -(c / A0) int_0^T e^{iwt} f(t/T) I(t) dt for a vector-potential step
+    A(t) = A0 theta(t); with A' = A/c the prefactor is -1/A'0.  Returns complex sigma."""
+    return -masked_transform(t, I, omegas, subtract_mean) / Ap0
+
+
+def dielectric(omegas, sigma):
+    """Sec. 4.1: eps(w) = 1 + 4 pi i sigma(w) / w."""
+    return 1.0 + 4.0 * np.pi * 1j * np.asarray(sigma) / np.asarray(omegas, np.float64)
 
 
 def mur_boundary(A_next, A_now, c_dt_dX):

@@ -1,0 +1,191 @@
+// Response analysis of a finished run, on the GPU: masked Fourier transforms of the time series
+// that the step observables give.
+//   * Eq. (distribution): the oscillator-strength distribution df/dE from the induced dipole after
+//     an impulsive kick of strength kappa;
+//   * Eq. (sigma_ft): the conductivity sigma(w) = -(c / A0) int_0^T e^{iwt} f(t/T) I(t) dt from the
+//     current after a vector-potential step A0 (here given as A'0 = A0 / c, the unit of the
+//     library's fields, so c / A0 = 1 / A'0), and eps(w) = 1 + 4 pi i sigma(w) / w; optionally
+//     with the mean current removed first (Sec. 4.1 example: sigma(0) = 0 for a gapped material).
+// Both use the cubic mask f(x) = 1 - 3x^2 + 2x^3 and the samples t_i = i dt, i = 0..n-1, T = t_{n-1},
+// summed with weight dt.  FP64 throughout.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <string>
+
+#include "../../include/tdks.h"
+#include "tdks_internal.h"
+
+namespace tdks {
+
+namespace {
+
+constexpr int kFtThreads = 256;
+constexpr double kPiR = 3.14159265358979323846;
+
+__device__ __forceinline__ double mask(double u) { return 1.0 - 3.0 * u * u + 2.0 * u * u * u; }
+
+// Sum of a pair over the CTA (fixed order); the result is valid in thread 0.
+__device__ __forceinline__ void block_sum2(double& a, double& b, double* red) {
+  red[threadIdx.x] = a;
+  red[kFtThreads + threadIdx.x] = b;
+  __syncthreads();
+  for (int o = kFtThreads / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      red[threadIdx.x] += red[threadIdx.x + o];
+      red[kFtThreads + threadIdx.x] += red[kFtThreads + threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  a = red[0];
+  b = red[kFtThreads];
+}
+
+// xbar = sum_i f(t_i/T) x_i / sum_i f(t_i/T): the mask-weighted mean, the one whose removal makes the
+// masked transform vanish at w = 0.  One CTA.
+__global__ void __launch_bounds__(kFtThreads) k_masked_mean(const double* __restrict__ x, int n, double* xbar) {
+  __shared__ double red[2 * kFtThreads];
+  const double T = (n - 1);
+  double s = 0.0, w = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double f = mask(n > 1 ? i / T : 0.0);
+    s += f * x[i];
+    w += f;
+  }
+  block_sum2(s, w, red);
+  if (threadIdx.x == 0) *xbar = (w != 0.0) ? s / w : 0.0;
+}
+
+// F(w_j) = dt sum_i f(t_i/T) (x_i - xbar) exp(i w_j t_i).  One CTA per frequency; thread k sums a
+// contiguous chunk of samples, starting from an exact phase factor and rotating it by exp(i w dt)
+// from sample to sample (at most n / 256 rotations, so the recurrence error stays near the
+// rounding of one product); the chunk sums are added in a fixed-order tree.
+__global__ void __launch_bounds__(kFtThreads) k_masked_ft(const double* __restrict__ x, int n, double dt,
+                                                         const double* __restrict__ xbar,
+                                                         const double* __restrict__ w, double2* __restrict__ F) {
+  __shared__ double red[2 * kFtThreads];
+  const double om = w[blockIdx.x];
+  const double mean = xbar ? *xbar : 0.0;
+  const int chunk = (n + kFtThreads - 1) / kFtThreads;
+  const int i0 = threadIdx.x * chunk, i1 = min(n, i0 + chunk);
+  double re = 0.0, im = 0.0;
+  if (i0 < i1) {
+    double s, c, rs, rc;
+    sincos(om * (i0 * dt), &s, &c);
+    sincos(om * dt, &rs, &rc);
+    for (int i = i0; i < i1; ++i) {
+      const double v = mask(n > 1 ? (double)i / (n - 1) : 0.0) * (x[i] - mean);
+      re += v * c;
+      im += v * s;
+      const double c2 = c * rc - s * rs;
+      s = s * rc + c * rs;
+      c = c2;
+    }
+  }
+  block_sum2(re, im, red);
+  if (threadIdx.x == 0) F[blockIdx.x] = double2{re * dt, im * dt};
+}
+
+// kind 0: out[j] = -(2 w_j / (pi kappa)) Im F_j                      (df/dE, Eq. distribution)
+// kind 1: out[2j..] = sigma_j = -F_j / A'0; eps[2j..] = 1 + 4 pi i sigma_j / w_j   (Eq. sigma_ft)
+__global__ void k_response_finish(const double2* __restrict__ F, const double* __restrict__ w, int nw, int kind,
+                                  double scale, double* __restrict__ out, double* __restrict__ eps) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nw) return;
+  const double2 f = F[j];
+  if (kind == 0) {
+    out[j] = -(2.0 * w[j] / (kPiR * scale)) * f.y;
+    return;
+  }
+  const double sr = -f.x / scale, si = -f.y / scale;
+  out[2 * j] = sr;
+  out[2 * j + 1] = si;
+  if (eps) {
+    eps[2 * j] = 1.0 - 4.0 * kPiR * si / w[j];
+    eps[2 * j + 1] = 4.0 * kPiR * sr / w[j];
+  }
+}
+
+tdks_status rfail(tdks_status s, const char* msg) {
+  set_last_error(msg);
+  return s;
+}
+
+// Host arrays in and out; device scratch for one call (synchronous on the stream).
+tdks_status masked_response(const double* x, int nt, double dt, const double* w, int nw, int subtract_mean,
+                            int kind, double scale, double* out, double* eps, void* stream) {
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t bx = sizeof(double) * (size_t)nt, bw = sizeof(double) * (size_t)nw;
+  const size_t bout = sizeof(double) * (size_t)nw * (kind == 0 ? 1 : 2);
+  double *dx = nullptr, *dw = nullptr, *dmean = nullptr, *dout = nullptr, *deps = nullptr;
+  double2* dF = nullptr;
+  cudaError_t e = cudaSuccess;
+  auto chk = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+  chk(cudaMalloc(&dx, bx));
+  chk(cudaMalloc(&dw, bw));
+  chk(cudaMalloc(&dmean, sizeof(double)));
+  chk(cudaMalloc(&dF, sizeof(double2) * (size_t)nw));
+  chk(cudaMalloc(&dout, bout));
+  if (eps) chk(cudaMalloc(&deps, bout));
+  if (e == cudaSuccess) {
+    chk(cudaMemcpyAsync(dx, x, bx, cudaMemcpyHostToDevice, s));
+    chk(cudaMemcpyAsync(dw, w, bw, cudaMemcpyHostToDevice, s));
+  }
+  if (e == cudaSuccess) {
+    if (subtract_mean) {
+      k_masked_mean<<<1, kFtThreads, 0, s>>>(dx, nt, dmean);
+      chk(cudaGetLastError());
+    }
+    k_masked_ft<<<nw, kFtThreads, 0, s>>>(dx, nt, dt, subtract_mean ? dmean : nullptr, dw, dF);
+    chk(cudaGetLastError());
+    k_response_finish<<<(nw + 127) / 128, 128, 0, s>>>(dF, dw, nw, kind, scale, dout, deps);
+    chk(cudaGetLastError());
+  }
+  if (e == cudaSuccess) chk(cudaMemcpyAsync(out, dout, bout, cudaMemcpyDeviceToHost, s));
+  if (e == cudaSuccess && eps) chk(cudaMemcpyAsync(eps, deps, bout, cudaMemcpyDeviceToHost, s));
+  if (e == cudaSuccess) chk(cudaStreamSynchronize(s));
+  cudaFree(dx);
+  cudaFree(dw);
+  cudaFree(dmean);
+  cudaFree(dF);
+  cudaFree(dout);
+  cudaFree(deps);
+  if (e != cudaSuccess) return rfail(e == cudaErrorMemoryAllocation ? TDKS_ENOMEM : TDKS_ECUDA,
+                                     (std::string("response analysis: ") + cudaGetErrorString(e)).c_str());
+  return TDKS_OK;
+}
+
+tdks_status check_series(const double* x, int nt, double dt, const double* w, int nw, const double* out) {
+  if (!x || !w || !out) return rfail(TDKS_EINVAL, "response analysis: null array");
+  if (nt < 2) return rfail(TDKS_EINVAL, "response analysis: need at least two samples");
+  if (nw < 1 || nw > (1 << 24)) return rfail(TDKS_EINVAL, "response analysis: frequency count outside 1..2^24");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return rfail(TDKS_EINVAL, "response analysis: dt must be positive");
+  return TDKS_OK;
+}
+
+}  // namespace
+
+}  // namespace tdks
+
+using tdks::check_series;
+using tdks::masked_response;
+using tdks::rfail;
+
+extern "C" tdks_status tdks_oscillator_strength(const double* d, int nt, double dt, double kappa, const double* E,
+                                                int nE, double* dfdE, void* stream) {
+  tdks_status st = check_series(d, nt, dt, E, nE, dfdE);
+  if (st != TDKS_OK) return st;
+  if (!(kappa != 0.0) || !std::isfinite(kappa)) return rfail(TDKS_EINVAL, "tdks_oscillator_strength: kappa must be nonzero");
+  return masked_response(d, nt, dt, E, nE, 0, 0, kappa, dfdE, nullptr, stream);
+}
+
+extern "C" tdks_status tdks_conductivity(const double* I, int nt, double dt, double Ap0, const double* w, int nw,
+                                         int subtract_mean, double* sigma, double* eps, void* stream) {
+  tdks_status st = check_series(I, nt, dt, w, nw, sigma);
+  if (st != TDKS_OK) return st;
+  if (!(Ap0 != 0.0) || !std::isfinite(Ap0)) return rfail(TDKS_EINVAL, "tdks_conductivity: Ap0 must be nonzero");
+  if (eps)
+    for (int j = 0; j < nw; ++j)
+      if (!(w[j] > 0.0)) return rfail(TDKS_EINVAL, "tdks_conductivity: eps needs every frequency > 0");
+  return masked_response(I, nt, dt, w, nw, subtract_mean ? 1 : 0, 1, Ap0, sigma, eps, stream);
+}

@@ -118,6 +118,10 @@ def load_library(path: str = LIB_PATH):
         "tdks_state_size": [vp, C.POINTER(C.c_size_t)],
         "tdks_ms_size": [vp, C.POINTER(i)],
         "tdks_probe_fp64": [C.POINTER(C.c_double)],
+        "tdks_oscillator_strength": [C.POINTER(C.c_double), i, d, d, C.POINTER(C.c_double), i,
+                                     C.POINTER(C.c_double), vp],
+        "tdks_conductivity": [C.POINTER(C.c_double), i, d, d, C.POINTER(C.c_double), i, i,
+                              C.POINTER(C.c_double), C.POINTER(C.c_double), vp],
         "tdks_get_state": [vp, vp, C.c_size_t],
         "tdks_set_state": [vp, vp, C.c_size_t],
     }
@@ -140,6 +144,40 @@ def probe_fp64():
     x = C.c_double()
     _check(lib.tdks_probe_fp64(C.byref(x)))
     return x.value
+
+
+def _dptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _stream_handle(stream):
+    return C.c_void_p(stream.cuda_stream if stream is not None else 0)
+
+
+def oscillator_strength(d, dt, kappa, E, stream=None):
+    """df/dE of a dipole series d[i] = d(i dt) after the kick exp(i kappa r) (tdks_oscillator_strength)."""
+    lib = load_library()
+    d = np.ascontiguousarray(d, np.float64)
+    E = np.ascontiguousarray(E, np.float64)
+    out = np.zeros(len(E))
+    _check(lib.tdks_oscillator_strength(_dptr(d), len(d), float(dt), float(kappa), _dptr(E), len(E), _dptr(out),
+                                        _stream_handle(stream)))
+    return out
+
+
+def conductivity(I, dt, Ap0, w, subtract_mean=True, stream=None):
+    """sigma(w) and eps(w) (complex arrays) of a current series I[i] = I(i dt) after the step
+    A'(t) = Ap0 theta(t) (tdks_conductivity).  eps is None unless every w > 0."""
+    lib = load_library()
+    I = np.ascontiguousarray(I, np.float64)
+    w = np.ascontiguousarray(w, np.float64)
+    sig = np.zeros(2 * len(w))
+    want_eps = bool(np.all(w > 0))
+    eps = np.zeros(2 * len(w)) if want_eps else None
+    _check(lib.tdks_conductivity(_dptr(I), len(I), float(dt), float(Ap0), _dptr(w), len(w), int(bool(subtract_mean)),
+                                 _dptr(sig), _dptr(eps) if want_eps else None, _stream_handle(stream)))
+    sigma = sig[0::2] + 1j * sig[1::2]
+    return sigma, (eps[0::2] + 1j * eps[1::2]) if want_eps else None
 
 
 def _check(status):

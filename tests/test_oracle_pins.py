@@ -491,3 +491,50 @@ def test_multiscale_without_coupling_is_independent_cells():
         ref, _, _ = O.pc_step(s, tabs, Vloc, psi0, v0, 0.0, 0.02, Ap=Amid)
         assert np.max(np.abs(cells[j][0] - ref)) < 1e-14
         assert abs(I_next[X] - O.current(s, tabs, ref, [0, 0, A_next[X] / O.C_LIGHT])[2]) < 1e-15
+
+
+def _masked_integral_closed_form(w, T):
+    """int_0^T e^{iwt} f(t/T) dt with f(s) = 1 - 3s^2 + 2s^3, by parts (f(1) = f'(0) = f'(1) = 0,
+    f(0) = 1, f''(0) = -6, f''(1) = 6, f''' = 12):
+    T [-1/(ia) + 6 (e^{ia} + 1)/(ia)^3 - 12 (e^{ia} - 1)/(ia)^4] with a = w T."""
+    a = 1j * w * T
+    return T * (-1.0 / a + 6.0 * (np.exp(a) + 1.0) / a ** 3 - 12.0 * (np.exp(a) - 1.0) / a ** 4)
+
+
+def test_masked_transform_closed_form():
+    """Eq. (sigma_ft) for a constant current I0: the rectangle-rule sum equals the closed-form masked
+    integral up to the O(dt) end term dt/2 (the mask vanishes at T)."""
+    T, dt, I0, Ap0 = 40.0, 0.005, 0.37, 2e-3
+    t = np.arange(0, int(round(T / dt)) + 1) * dt
+    w = np.array([0.05, 0.3, 1.1, 2.7])
+    sig = O.conductivity(t, np.full(len(t), I0), Ap0, w, subtract_mean=False)
+    ref = -(I0 / Ap0) * _masked_integral_closed_form(w, T)
+    assert np.max(np.abs(sig - ref - (-(I0 / Ap0) * dt / 2))) < 1e-6 * np.max(np.abs(ref))
+
+
+def test_dielectric_plasma_limit():
+    """A free-electron gas of density n under the step A'(t) = A'0: the current is -n A'0 (diamagnetic),
+    so sigma = n int e^{iwt} f dt -> i n / w and eps -> 1 - 4 pi n / w^2 = 1 - w_p^2 / w^2 once wT >> 1."""
+    n, Ap0, T, dt = 0.02, 1e-3, 400.0, 0.01
+    t = np.arange(0, int(round(T / dt)) + 1) * dt
+    w = np.array([0.6, 1.0, 2.0])
+    sig = O.conductivity(t, np.full(len(t), -n * Ap0), Ap0, w, subtract_mean=False)
+    eps = O.dielectric(w, sig)
+    # the sampled sum is the masked integral plus the Euler-Maclaurin end terms of e^{iwt} f(t/T):
+    # dt/2 g(0) + dt^2/12 (g'(T) - g'(0)) = dt/2 - i w dt^2 / 12
+    ref = 1.0 + 4.0 * np.pi * 1j / w * n * (_masked_integral_closed_form(w, T) + dt / 2 - 1j * w * dt ** 2 / 12)
+    assert np.max(np.abs(eps - ref)) < 1e-9
+    # and within the finite-T and end-term corrections of the plasma limit
+    assert np.max(np.abs(eps.real - (1.0 - 4.0 * np.pi * n / w ** 2))) < 5e-4
+    assert np.max(np.abs(eps.imag)) < 4.0 * np.pi * n * dt / 2 / w.min() * 1.01
+
+
+def test_conductivity_mean_removal():
+    """With the mask-weighted mean removed, sigma(0) = 0 exactly for any current history."""
+    rng = np.random.default_rng(4)
+    t = np.arange(0, 3001) * 0.02
+    I = 0.3 + rng.standard_normal(len(t)) * 1e-2 + 0.05 * np.sin(0.7 * t)
+    sig = O.conductivity(t, I, 1e-3, np.array([0.0, 0.5]), subtract_mean=True)
+    assert abs(sig[0]) < 1e-12 * np.max(np.abs(sig))
+    sig_raw = O.conductivity(t, I, 1e-3, np.array([0.0]), subtract_mean=False)
+    assert abs(sig_raw[0]) > 1e3 * abs(sig[0])
