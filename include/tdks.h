@@ -78,7 +78,12 @@ typedef struct { double E_s, E_p, r_cut, width; } tdks_projector;
 
 /* precision: TDKS_F64 (orbitals, stencil and all reductions in FP64) or TDKS_F32 (FP32 complex
  * orbitals and stencil; density, current, dipole, norms and the Poisson solve stay in FP64).
- * hartree, xc: include V_H and LDA exchange (1) or leave them out (0: linear propagation).
+ * hartree: include V_H (1) or leave it out (0).
+ * xc: adiabatic LDA of Sec. 3.1 -- 0 none, 1 Slater exchange, 2 exchange plus the Perdew-Zunger
+ *     correlation of the electron gas (eps_c = g / (1 + b1 sqrt(rs) + b2 rs) for rs >= 1, else
+ *     A ln rs + B + C rs ln rs + D rs, with g = -0.1423, b1 = 1.0529, b2 = 0.3334, A = 0.0311,
+ *     B = -0.048, C = 0.0020, D = -0.0116; V_c = eps_c - (rs/3) d eps_c / d rs).  hartree = xc = 0
+ *     gives linear propagation.
  * pc: predictor-corrector on (1) or a single Taylor step with V(t) (0).
  * ncell: number of independent copies of the system propagated together (0 or 1: one).  With
  * ncell > 1 (periodic grids only) orbitals are [ncell][nk][norb][nz][ny][nx] and every cell has its

@@ -20,7 +20,7 @@ What it computes (Hartree atomic units, hbar = m = e = 1, A' = A/c):
 * Eq. (rho): rho = 2 sum_p |psi_p|^2 (spin saturated), with k-weights for Bloch orbitals.
 * Eq. (TDKS): Hartree potential e^2 int rho(r')/|r-r'|; periodic cells solve it in G-space,
   isolated boxes with a zero-padded (Hockney) convolution.
-* Sec. 3.1 LDA: adiabatic local exchange (Slater exchange only in this build).
+* Sec. 3.1 LDA: adiabatic local exchange (Slater) and, as an option, the Perdew-Zunger correlation.
 * Sec. 3.1: dipole d = -int r (rho - rho0); Eq. (distribution): oscillator-strength spectrum.
 * Sec. 4.1, Eq. (sigma_ft): conductivity and dielectric function from the current after an A step.
 * Eq. (macro_current): macroscopic current including the nonlocal term.
@@ -290,12 +290,46 @@ def lda_x(rho):
     return vx, 0.75 * vx
 
 
+# Perdew-Zunger parametrisation of the correlation energy per electron of the unpolarised gas
+# (the LDA named in Sec. 3.1): eps_c(r_s) in two branches joined at r_s = 1.
+PZ_G, PZ_B1, PZ_B2 = -0.1423, 1.0529, 0.3334
+PZ_A, PZ_B, PZ_C, PZ_D = 0.0311, -0.048, 0.0020, -0.0116
+
+
+def pz_eps_c(rs):
+    """eps_c(r_s) = g / (1 + b1 sqrt(r_s) + b2 r_s) for r_s >= 1, A ln r_s + B + C r_s ln r_s + D r_s below."""
+    rs = np.asarray(rs, np.float64)
+    hi = PZ_G / (1.0 + PZ_B1 * np.sqrt(rs) + PZ_B2 * rs)
+    lo = PZ_A * np.log(rs) + PZ_B + PZ_C * rs * np.log(rs) + PZ_D * rs
+    return np.where(rs >= 1.0, hi, lo)
+
+
+def lda_c(rho):
+    """Correlation potential and energy density per electron: r_s = (3 / (4 pi rho))^(1/3),
+    V_c = d(rho eps_c)/d rho = eps_c - (r_s / 3) d eps_c / d r_s, with the derivative of each branch
+    written out; both are 0 where rho <= 0."""
+    r = np.asarray(rho, np.float64)
+    pos = r > 1e-30
+    rs = np.cbrt(3.0 / (4.0 * np.pi * np.where(pos, r, 1.0)))
+    eps = pz_eps_c(rs)
+    sq = np.sqrt(rs)
+    den = 1.0 + PZ_B1 * sq + PZ_B2 * rs
+    deps_hi = -PZ_G * (0.5 * PZ_B1 / sq + PZ_B2) / den ** 2
+    deps_lo = PZ_A / rs + PZ_C * (np.log(rs) + 1.0) + PZ_D
+    deps = np.where(rs >= 1.0, deps_hi, deps_lo)
+    vc = eps - rs / 3.0 * deps
+    return np.where(pos, vc, 0.0), np.where(pos, eps, 0.0)
+
+
 def hxc(s, rho, hartree_on=True, xc_on=True):
+    """V_H + V_xc; xc_on: 0/False none, 1/True Slater exchange, 2 exchange + PZ correlation."""
     v = np.zeros_like(rho)
     if hartree_on:
         v = v + hartree(s, rho)
     if xc_on:
         v = v + lda_x(rho)[0]
+    if xc_on == 2:
+        v = v + lda_c(rho)[0]
     return v
 
 
@@ -359,13 +393,15 @@ def band_energy(s, tabs, Vloc, psi, Ap):
 
 
 def total_energy(s, tabs, Vloc, psi, Ap, hartree_on=True, xc_on=True):
-    """E = band energy + 1/2 int rho V_H + int rho eps_x."""
+    """E = band energy + 1/2 int rho V_H + int rho eps_xc (eps_x, plus eps_c when xc_on == 2)."""
     rho = density(s, psi)
     e = band_energy(s, tabs, Vloc, psi, Ap)
     if hartree_on:
         e += 0.5 * np.sum(rho * hartree(s, rho)) * s.dV
     if xc_on:
         e += np.sum(rho * lda_x(rho)[1]) * s.dV
+    if xc_on == 2:
+        e += np.sum(rho * lda_c(rho)[1]) * s.dV
     return e
 
 

@@ -1,4 +1,4 @@
-// Grid kernels in FP64: FFT Poisson solve (periodic and zero-padded isolated), LDA exchange,
+// Grid kernels in FP64: FFT Poisson solve (periodic and zero-padded isolated), LDA (lda.cuh),
 // potential combination, density, dipole and current reductions, kick, local potential.
 //
 // FFT: batched 1D Stockham transforms in shared memory, one launch per axis, mixed radix
@@ -11,6 +11,7 @@
 
 #include "ff.cuh"
 #include "grid_sum.cuh"
+#include "lda.cuh"
 #include "tdks_internal.h"
 
 namespace tdks {
@@ -155,7 +156,7 @@ __device__ __forceinline__ void stockham_lines(double2*& src, double2*& dst, int
 //              factor of its wave vector (periodic: 4 pi / G^2 / N, G = 0 dropped; isolated: the
 //              Hockney spectrum ghat times gscale) and the line is transformed back in place;
 //   store_epi  (x pass, inverse): instead of writing the line back, the inside points n0 x n1 x n2
-//              get vhxc = Re(value) + V_x(rho), with V_x = -(3 rho / pi)^(1/3) if xc.
+//              get vhxc = Re(value) + V_xc(rho) (lda.cuh: xc = 1 exchange, 2 exchange + correlation).
 __device__ __forceinline__ double freq(int m, int n) { return (m <= (n - 1) / 2) ? m : m - n; }
 
 //   zero_from  (forward y and z passes of a padded box): elements e >= zero_from of every line are
@@ -254,7 +255,7 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_lines(double2* data, int n,
       if (x < hk.n0 && y < hk.n1 && zc < hk.n2) {
         const long long o = (((long long)cell * hk.n2 + zc) * hk.n1 + y) * hk.n0 + x;
         double v = src[j * n + e].x;
-        if (hk.xc) v -= cbrt(3.0 * fmax(hk.rho[o], 0.0) / kPi);   // Slater exchange
+        v += lda_vxc(hk.rho[o], hk.xc);
         hk.vhxc[o] = v;
       }
     } else {
@@ -269,7 +270,7 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_lines(double2* data, int n,
 // in one launch, one CTA per (z plane, cell), with the plane transposed in shared memory between
 // the two line sets.  Forward (FWD): the real density plane rho[cell][z] is transformed along x,
 // then y, and written to data.  Inverse: the plane of data is transformed back along y, then x, and
-// the epilogue writes vhxc = Re(value) + V_x(rho) (Slater exchange if xc).  Twiddle tables tw0
+// the epilogue writes vhxc = Re(value) + V_xc(rho) (lda.cuh).  Twiddle tables tw0
 // (length m0) and tw1 (length m1); shared memory: m0 + m1 twiddles and two m0 m1 buffers.
 template <bool FWD>
 __global__ void __launch_bounds__(kFftThreads) k_fft_planes(double2* data, int m0, int m1, int m2,
@@ -320,7 +321,7 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_planes(double2* data, int m
     stockham_lines(src, dst, m0, m1, tw0, plan0, +1);                 // x lines
     for (int i = threadIdx.x; i < np; i += blockDim.x) {
       double v = src[i].x;
-      if (xc) v -= cbrt(3.0 * fmax(rho[plane + i], 0.0) / kPi);     // Slater exchange
+      v += lda_vxc(rho[plane + i], xc);
       vhxc[plane + i] = v;
     }
   }
@@ -381,7 +382,7 @@ __global__ void k_hxc_epilogue(const double2* __restrict__ fft, int mx, int my,
     const int y = (int)(r % ny), z = (int)(r / ny);
     double v = 0.0;
     if (hartree) v += scale_h * fft[((long long)z * my + y) * mx + x].x;
-    if (xc) v -= cbrt(3.0 * fmax(rho[i], 0.0) / kPi);   // Slater exchange V_x = -(3 rho/pi)^(1/3)
+    v += lda_vxc(rho[i], xc);
     vhxc[i] = v;
   }
 }

@@ -610,6 +610,8 @@ tdks_status tdks_init(const tdks_grid* grid, const tdks_cell* cell, const tdks_a
   for (int k = 0; k < nk; ++k) wsum += kw[k];
   if (std::fabs(wsum - 1.0) > 1e-9) return fail(TDKS_EINVAL, "k-point weights must sum to 1");
   if (opts->obs_at_start != 0 && opts->obs_at_start != 1) return fail(TDKS_EINVAL, "obs_at_start must be 0 or 1");
+  if (opts->xc < 0 || opts->xc > 2) return fail(TDKS_EINVAL, "xc must be 0 (none), 1 (exchange) or 2 (exchange + correlation)");
+  if (opts->hartree != 0 && opts->hartree != 1) return fail(TDKS_EINVAL, "hartree must be 0 or 1");
 
   tdks_ctx* c = new tdks_ctx();
   c->grid = *grid;

@@ -64,6 +64,7 @@ extern "C" tdks_status tdks_hxc_noalloc(const tdks_grid* grid, const double* rho
                                         int hartree, int xc, void* stream) {
   using namespace tdks;
   if (!grid || !rho_dev || !vhxc_dev) return noalloc_fail(TDKS_EINVAL, "null grid, density or output");
+  if (xc < 0 || xc > 2) return noalloc_fail(TDKS_EINVAL, "tdks_hxc_noalloc: xc must be 0, 1 or 2");
   int m[3];
   int rad[3][16];
   int nrad[3];

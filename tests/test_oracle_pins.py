@@ -538,3 +538,47 @@ def test_conductivity_mean_removal():
     assert abs(sig[0]) < 1e-12 * np.max(np.abs(sig))
     sig_raw = O.conductivity(t, I, 1e-3, np.array([0.0]), subtract_mean=False)
     assert abs(sig_raw[0]) > 1e3 * abs(sig[0])
+
+
+# ---------------------------------------------------------------- LDA correlation (Perdew-Zunger)
+def test_pz_correlation_potential_is_the_density_derivative():
+    """V_c = d(rho eps_c)/d rho: the written-out branch derivatives against central differences of
+    rho eps_c(rho), on densities from r_s = 0.2 to r_s = 8 (both branches)."""
+    rs = np.array([0.2, 0.5, 0.9, 1.2, 2.0, 4.0, 8.0])
+    rho = 3.0 / (4.0 * np.pi * rs ** 3)
+    h = 1e-6 * rho
+    f = lambda r: r * O.lda_c(r)[1]
+    num = (f(rho + h) - f(rho - h)) / (2 * h)
+    vc, _ = O.lda_c(rho)
+    assert np.max(np.abs(vc - num)) < 1e-8
+
+
+def test_pz_branches_join_at_rs_1():
+    """The two branches of the parametrisation meet at r_s = 1 in eps_c and in V_c (to the 3e-5 of
+    the published constants): a wrong constant in either branch breaks this."""
+    rho1 = 3.0 / (4.0 * np.pi)
+    lo, hi = rho1 * (1 + 1e-9), rho1 * (1 - 1e-9)       # r_s just below and just above 1
+    vlo, elo = O.lda_c(np.array([lo]))
+    vhi, ehi = O.lda_c(np.array([hi]))
+    assert abs(elo[0] - ehi[0]) < 1e-4 and abs(vlo[0] - vhi[0]) < 1e-4
+    assert -0.07 < vlo[0] < -0.06 and -0.065 < elo[0] < -0.055
+
+
+def test_energy_conservation_with_correlation():
+    """As the exchange-only test, with exchange + correlation (xc = 2): the total-energy drift of the
+    predictor-corrector still falls at least as dt^2.  (This is an invariant of the whole step, not a
+    pin of V_c itself -- the correlation energy is too small a part of this drift; the derivative
+    test above pins V_c against eps_c.)"""
+    s = W.tiny(periodic=True, n=(8, 8, 8), natom=1, norb=2)
+    s.field = W.Field("none")
+    psi0 = W.initial_orbitals(s, 6)
+    tabs = O.projector_tables(s)
+    Vloc = O.local_potential(s)
+    Ap = np.zeros(3)
+    E0 = O.total_energy(s, tabs, Vloc, psi0, Ap, xc_on=2)
+    drifts = []
+    for dt, n in ((0.04, 10), (0.02, 20)):
+        s.dt = dt
+        psi, _, _ = O.run(s, psi0, n, record=False, xc_on=2)
+        drifts.append(abs(O.total_energy(s, tabs, Vloc, psi, Ap, xc_on=2) - E0))
+    assert drifts[1] < drifts[0] / 3.5, drifts
