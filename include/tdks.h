@@ -58,7 +58,7 @@ typedef enum {
 } tdks_status;
 
 enum { TDKS_F64 = 0, TDKS_F32 = 1 };
-enum { TDKS_FIELD_NONE = 0, TDKS_FIELD_STEP = 1, TDKS_FIELD_PULSE = 2 };
+enum { TDKS_FIELD_NONE = 0, TDKS_FIELD_STEP = 1, TDKS_FIELD_PULSE = 2, TDKS_FIELD_TABLE = 3 };
 
 /* Uniform grid (Sec. 2.1).  n = points per axis (x, y, z); h = spacing (bohr).
  * periodic = 1: periodic cuboid of side L = n h; coordinates r_j = j h.
@@ -122,9 +122,25 @@ tdks_status tdks_init(const tdks_grid* grid, const tdks_cell* cell,
 /* Spatially uniform field as A'(t) = A(t)/c.  kind = TDKS_FIELD_NONE: A' = 0.
  * TDKS_FIELD_STEP: A'(t) = A0 for t > 0 (impulsive kick in the velocity gauge, Eq. impulsive_A).
  * TDKS_FIELD_PULSE: A'(t) = A0 cos^2[pi (t - T/2)/T] sin[-omega (t - T/2) - 2 pi cep], 0 < t < T
- * (Eq. pulse with a real amplitude A0 already divided by c).  Isolated systems ignore the field. */
+ * (Eq. pulse with a real amplitude A0 already divided by c).  Isolated systems ignore the field.
+ * (TDKS_FIELD_TABLE is set with tdks_set_field_table.) */
 tdks_status tdks_set_field(tdks_ctx* ctx, int kind, const double A0[3], double omega,
                            double T, double cep);
+
+/* Pump-probe fields (Sec. 3.1: two successive pulses of the Eq. (pulse) form with a time delay):
+ * adds A'(t) += A0 cos^2[pi (t' - T/2)/T] sin[-omega (t' - T/2) - 2 pi cep] for 0 < t' = t - t_delay < T
+ * to a field set with kind TDKS_FIELD_PULSE (whose own pulse has delay 0); at most 8 pulses.
+ * Errors: EINVAL if the field is not of kind PULSE, A0 is NULL, T <= 0, t_delay is not finite or
+ * 8 pulses are set. */
+tdks_status tdks_add_pulse(tdks_ctx* ctx, const double A0[3], double omega, double T, double cep,
+                           double t_delay);
+
+/* A field given by a numerical table (Sec. 3.1), as samples of A'(t) = A(t)/c: Ap[3 i + a] is
+ * component a at t0 + i dt_table, i < nt; A' is linear between samples and equal to the first /
+ * last sample before / after the table (an E(t) table becomes one of A' = -int E dt).  The table is
+ * copied; it replaces the current field (kind TDKS_FIELD_TABLE).  Errors: EINVAL for a NULL table,
+ * nt outside 1..2^26, dt_table <= 0 or a non-finite value. */
+tdks_status tdks_set_field_table(tdks_ctx* ctx, const double* Ap, int nt, double t0, double dt_table);
 
 /* Isolated impulse (Sec. 3.1): u <- exp(i kappa . r) u for all orbitals, in place. */
 tdks_status tdks_kick(tdks_ctx* ctx, void* u_dev, const double kappa[3]);
@@ -290,7 +306,7 @@ tdks_status tdks_cell_variant(tdks_ctx* ctx, int set, int* variant, float* tune_
  *   V_Hxc(t), rho(t) and the reference density rho0 of every cell; the last four V_Hxc of the
  *   predictor history; the predictor mode, threshold, fallback count and network parameters; the
  *   multiscale field levels A^n, A^{n-1}, A^{n+1}, the cell currents and the grid geometry; the
- *   field settings (tdks_set_field).
+ *   field settings (tdks_set_field, tdks_add_pulse, tdks_set_field_table).
  * tdks_state_size gives the bytes; tdks_get_state writes them to host memory (synchronises);
  * tdks_set_state restores them into a context created for the same system and options (grid
  * points, cells, k-points, orbitals, precision, atoms, hartree/xc/pc), checked against the

@@ -336,19 +336,39 @@ def hxc(s, rho, hartree_on=True, xc_on=True):
 # --------------------------------------------------------------------------------------------
 # fields (Eq. pulse, Eq. impulsive_A)
 # --------------------------------------------------------------------------------------------
+def _pulse(A0, omega, T, cep, t):
+    """One pulse of Eq. (pulse): Im{A0 cos^2[pi(t-T/2)/T] e^{-i omega (t-T/2) - 2 pi i cep}}, 0 < t < T."""
+    if not (0.0 < t < T):
+        return np.zeros(3)
+    env = math.cos(math.pi * (t - T / 2.0) / T) ** 2
+    ph = -omega * (t - T / 2.0) - 2.0 * math.pi * cep
+    return np.asarray(A0, np.float64) * env * math.sin(ph)      # Im{A0 env e^{i ph}} for real A0
+
+
 def field_Aprime(f, t):
-    """A'(t) = A(t)/c as a 3-vector."""
+    """A'(t) = A(t)/c as a 3-vector.  Sec. 3.1 fields: the impulsive step (Eq. impulsive_A), the
+    pulse of Eq. (pulse) and successive delayed pulses (pump-probe, their sum), and a numerical
+    table (samples of A' at t0 + i dt, linear in between, the end samples outside)."""
     A0 = np.asarray(f.A0, np.float64)
     if f.kind == "none":
         return np.zeros(3)
     if f.kind == "step":
         return A0.copy() if t > 0.0 else np.zeros(3)
     if f.kind == "pulse":
-        if not (0.0 < t < f.T):
-            return np.zeros(3)
-        env = math.cos(math.pi * (t - f.T / 2.0) / f.T) ** 2
-        ph = -f.omega * (t - f.T / 2.0) - 2.0 * math.pi * f.cep
-        return A0 * env * math.sin(ph)      # Im{A0 env e^{i ph}} for real A0
+        a = _pulse(A0, f.omega, f.T, f.cep, t)
+        for (A1, w1, T1, c1, delay) in getattr(f, "more", ()):
+            a = a + _pulse(A1, w1, T1, c1, t - delay)
+        return a
+    if f.kind == "table":
+        tab = np.asarray(f.table, np.float64).reshape(-1, 3)
+        x = (t - f.t0) / f.dt_table
+        if len(tab) == 1 or x <= 0.0:
+            return tab[0].copy()
+        if x >= len(tab) - 1:
+            return tab[-1].copy()
+        i = int(math.floor(x))
+        w = x - i
+        return (1.0 - w) * tab[i] + w * tab[i + 1]
     raise ValueError(f.kind)
 
 

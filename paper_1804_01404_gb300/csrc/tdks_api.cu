@@ -36,6 +36,13 @@ void tdks::set_last_error(const char* msg) { g_err = msg; }
     if (s_ != TDKS_OK) return s_;           \
   } while (0)
 
+// One pulse of Eq. (pulse), delayed: A'(t) = A0 cos^2[pi (t' - T/2)/T] sin[-omega (t' - T/2) - 2 pi cep],
+// t' = t - delay, 0 < t' < T.
+struct PulseDef {
+  double A0[3], omega, T, cep, delay;
+};
+constexpr int kMaxPulses = 8;
+
 struct tdks_ctx {
   tdks_grid grid{};
   int npts = 0, nk = 0, norb = 0, ncell = 1;
@@ -51,7 +58,10 @@ struct tdks_ctx {
   cudaStream_t stream = nullptr;
   // field
   int field_kind = TDKS_FIELD_NONE;
-  double A0[3] = {0, 0, 0}, f_omega = 0, f_T = 0, f_cep = 0;
+  double A0[3] = {0, 0, 0};                 // TDKS_FIELD_STEP
+  std::vector<PulseDef> pulses;             // TDKS_FIELD_PULSE: A' is their sum
+  std::vector<double> ftable;               // TDKS_FIELD_TABLE: [nt][3] samples of A'
+  double tab_t0 = 0.0, tab_dt = 0.0;
   // projector tables
   int natom = 0, nsph = 0;
   int *d_atom_off = nullptr, *d_sph_idx = nullptr, *d_pt_off = nullptr, *d_pt_ent = nullptr,
@@ -138,10 +148,26 @@ void field_at(const tdks_ctx* c, double t, double out[3]) {
   if (c->field_kind == TDKS_FIELD_STEP) {
     if (t > 0.0) for (int a = 0; a < 3; ++a) out[a] = c->A0[a];
   } else if (c->field_kind == TDKS_FIELD_PULSE) {
-    if (t > 0.0 && t < c->f_T) {
-      const double env = std::cos(kPi * (t - 0.5 * c->f_T) / c->f_T);
-      const double s = std::sin(-c->f_omega * (t - 0.5 * c->f_T) - 2.0 * kPi * c->f_cep);
-      for (int a = 0; a < 3; ++a) out[a] = c->A0[a] * env * env * s;
+    for (const PulseDef& p : c->pulses) {
+      const double tt = t - p.delay;
+      if (tt > 0.0 && tt < p.T) {
+        const double env = std::cos(kPi * (tt - 0.5 * p.T) / p.T);
+        const double s = std::sin(-p.omega * (tt - 0.5 * p.T) - 2.0 * kPi * p.cep);
+        for (int a = 0; a < 3; ++a) out[a] += p.A0[a] * env * env * s;
+      }
+    }
+  } else if (c->field_kind == TDKS_FIELD_TABLE) {
+    // linear between the samples t0 + i dt, the end samples outside
+    const int nt = (int)(c->ftable.size() / 3);
+    const double x = (t - c->tab_t0) / c->tab_dt;
+    if (nt == 1 || x <= 0.0) {
+      for (int a = 0; a < 3; ++a) out[a] = c->ftable[a];
+    } else if (x >= nt - 1) {
+      for (int a = 0; a < 3; ++a) out[a] = c->ftable[3 * (nt - 1) + a];
+    } else {
+      const int i = (int)std::floor(x);
+      const double f = x - i;
+      for (int a = 0; a < 3; ++a) out[a] = (1.0 - f) * c->ftable[3 * i + a] + f * c->ftable[3 * (i + 1) + a];
     }
   }
 }
@@ -788,10 +814,45 @@ tdks_status tdks_set_field(tdks_ctx* c, int kind, const double A0[3], double ome
   if (kind != TDKS_FIELD_NONE && !A0) return fail(TDKS_EINVAL, "null A0");
   if (kind == TDKS_FIELD_PULSE && !(T > 0.0)) return fail(TDKS_EINVAL, "pulse duration must be positive");
   c->field_kind = kind;
-  for (int a = 0; a < 3; ++a) c->A0[a] = A0 ? A0[a] : 0.0;
-  c->f_omega = omega;
-  c->f_T = T;
-  c->f_cep = cep;
+  for (int a = 0; a < 3; ++a) c->A0[a] = (A0 && kind == TDKS_FIELD_STEP) ? A0[a] : 0.0;
+  c->pulses.clear();
+  c->ftable.clear();
+  if (kind == TDKS_FIELD_PULSE) {
+    PulseDef p;
+    for (int a = 0; a < 3; ++a) p.A0[a] = A0[a];
+    p.omega = omega; p.T = T; p.cep = cep; p.delay = 0.0;
+    c->pulses.push_back(p);
+  }
+  return TDKS_OK;
+}
+
+tdks_status tdks_add_pulse(tdks_ctx* c, const double A0[3], double omega, double T, double cep, double t_delay) {
+  TDKS_TRY(check_ctx(c));
+  if (c->field_kind != TDKS_FIELD_PULSE) return fail(TDKS_EINVAL, "tdks_add_pulse needs a field of kind TDKS_FIELD_PULSE");
+  if (!A0) return fail(TDKS_EINVAL, "null A0");
+  if (!(T > 0.0)) return fail(TDKS_EINVAL, "pulse duration must be positive");
+  if (!std::isfinite(t_delay)) return fail(TDKS_EINVAL, "pulse delay must be finite");
+  if ((int)c->pulses.size() >= kMaxPulses) return fail(TDKS_EINVAL, "at most 8 pulses");
+  PulseDef p;
+  for (int a = 0; a < 3; ++a) p.A0[a] = A0[a];
+  p.omega = omega; p.T = T; p.cep = cep; p.delay = t_delay;
+  c->pulses.push_back(p);
+  return TDKS_OK;
+}
+
+tdks_status tdks_set_field_table(tdks_ctx* c, const double* Ap, int nt, double t0, double dt_table) {
+  TDKS_TRY(check_ctx(c));
+  if (!Ap) return fail(TDKS_EINVAL, "null table");
+  if (nt < 1 || nt > (1 << 26)) return fail(TDKS_EINVAL, "table length outside 1..2^26");
+  if (!(dt_table > 0.0) || !std::isfinite(t0)) return fail(TDKS_EINVAL, "table spacing must be positive");
+  for (size_t i = 0; i < 3 * (size_t)nt; ++i)
+    if (!std::isfinite(Ap[i])) return fail(TDKS_EINVAL, "non-finite value in the field table");
+  c->field_kind = TDKS_FIELD_TABLE;
+  c->pulses.clear();
+  for (int a = 0; a < 3; ++a) c->A0[a] = 0.0;
+  c->ftable.assign(Ap, Ap + 3 * (size_t)nt);
+  c->tab_t0 = t0;
+  c->tab_dt = dt_table;
   return TDKS_OK;
 }
 
@@ -1342,7 +1403,7 @@ tdks_status tdks_set_wait_test(tdks_ctx* c, long long wait_limit, int stop_after
 // ------------------------------------------------------------------ checkpoint
 namespace {
 struct StateHeader {
-  char magic[8];            // "TDKSSTA1"
+  char magic[8];            // "TDKSSTA2"
   int npts, ncell, nk, norb, precision, natom, periodic;
   int hartree, xc, pc;
   int have_rho0, have_potential;
@@ -1350,7 +1411,11 @@ struct StateHeader {
   int pred_mode, nn_ready;
   double pred_thr, fallbacks, last_resid;
   int field_kind;
-  double A0[3], f_omega, f_T, f_cep;
+  double A0[3];
+  int npulse;
+  PulseDef pulse[kMaxPulses];
+  int ntable;                 // field table rows, stored after the arrays
+  double tab_t0, tab_dt;
   int ms_ready, nX, m0, ms_head;
   double dX;
 };
@@ -1360,6 +1425,7 @@ size_t state_bytes(const tdks_ctx* c) {
   size_t b = sizeof(StateHeader) + sizeof(double) * (3 * npc + 4 * (size_t)c->npts);
   if (c->nn_ready) b += sizeof(float) * kNNParams;
   if (c->ms_ready) b += sizeof(double) * 4 * (size_t)c->nX;
+  b += sizeof(double) * c->ftable.size();
   return b;
 }
 }  // namespace
@@ -1376,7 +1442,7 @@ tdks_status tdks_get_state(tdks_ctx* c, void* host, size_t bytes) {
   if (!host || bytes < state_bytes(c)) return fail(TDKS_EINVAL, "state buffer smaller than tdks_state_size");
   StateHeader h;
   std::memset(&h, 0, sizeof(h));
-  std::memcpy(h.magic, "TDKSSTA1", 8);
+  std::memcpy(h.magic, "TDKSSTA2", 8);
   h.npts = c->npts; h.ncell = c->ncell; h.nk = c->nk; h.norb = c->norb; h.precision = c->opt.precision;
   h.natom = c->natom; h.periodic = c->grid.periodic;
   h.hartree = c->opt.hartree; h.xc = c->opt.xc; h.pc = c->opt.pc;
@@ -1386,7 +1452,10 @@ tdks_status tdks_get_state(tdks_ctx* c, void* host, size_t bytes) {
   h.pred_thr = c->pred_thr; h.fallbacks = c->fallbacks; h.last_resid = c->last_resid;
   h.field_kind = c->field_kind;
   for (int a = 0; a < 3; ++a) h.A0[a] = c->A0[a];
-  h.f_omega = c->f_omega; h.f_T = c->f_T; h.f_cep = c->f_cep;
+  h.npulse = (int)c->pulses.size();
+  for (int i = 0; i < h.npulse; ++i) h.pulse[i] = c->pulses[i];
+  h.ntable = (int)(c->ftable.size() / 3);
+  h.tab_t0 = c->tab_t0; h.tab_dt = c->tab_dt;
   h.ms_ready = c->ms_ready; h.nX = c->nX; h.m0 = c->m0; h.ms_head = c->ms_head; h.dX = c->dX;
   unsigned char* o = static_cast<unsigned char*>(host);
   std::memcpy(o, &h, sizeof(h));
@@ -1406,6 +1475,7 @@ tdks_status tdks_get_state(tdks_ctx* c, void* host, size_t bytes) {
     for (int i = 0; i < 3; ++i) TDKS_CUDA(d2h(c->d_A[i], c->nX * sizeof(double)));
     TDKS_CUDA(d2h(c->d_I, c->nX * sizeof(double)));
   }
+  if (!c->ftable.empty()) std::memcpy(o, c->ftable.data(), sizeof(double) * c->ftable.size());
   TDKS_CUDA(cudaStreamSynchronize(c->stream));
   return TDKS_OK;
 }
@@ -1415,7 +1485,10 @@ tdks_status tdks_set_state(tdks_ctx* c, const void* host, size_t bytes) {
   if (!host || bytes < sizeof(StateHeader)) return fail(TDKS_EINVAL, "state buffer too small");
   StateHeader h;
   std::memcpy(&h, host, sizeof(h));
-  if (std::memcmp(h.magic, "TDKSSTA1", 8) != 0) return fail(TDKS_EINVAL, "not a tdks state (bad magic)");
+  if (std::memcmp(h.magic, "TDKSSTA2", 8) != 0) return fail(TDKS_EINVAL, "not a tdks state (bad magic)");
+  if (h.field_kind < TDKS_FIELD_NONE || h.field_kind > TDKS_FIELD_TABLE || h.npulse < 0 || h.npulse > kMaxPulses ||
+      h.ntable < 0 || (h.field_kind == TDKS_FIELD_TABLE && (h.ntable < 1 || !(h.tab_dt > 0.0))))
+    return fail(TDKS_EINVAL, "state holds an invalid field description");
   if (h.npts != c->npts || h.ncell != c->ncell || h.nk != c->nk || h.norb != c->norb ||
       h.precision != c->opt.precision || h.natom != c->natom || h.periodic != c->grid.periodic ||
       h.hartree != c->opt.hartree || h.xc != c->opt.xc || h.pc != c->opt.pc)
@@ -1434,6 +1507,7 @@ tdks_status tdks_set_state(tdks_ctx* c, const void* host, size_t bytes) {
   size_t need = sizeof(StateHeader) + sizeof(double) * (3 * npc + 4 * (size_t)c->npts);
   if (h.nn_ready) need += sizeof(float) * kNNParams;
   if (h.ms_ready) need += sizeof(double) * 4 * (size_t)h.nX;
+  need += sizeof(double) * 3 * (size_t)h.ntable;
   if (bytes < need) return fail(TDKS_EINVAL, "state buffer shorter than its header says");
   if (h.pred_mode != TDKS_PRED_PC) TDKS_TRY(tdks_set_predictor(c, h.pred_mode, h.pred_thr));
   else c->pred_mode = TDKS_PRED_PC;
@@ -1460,7 +1534,11 @@ tdks_status tdks_set_state(tdks_ctx* c, const void* host, size_t bytes) {
   c->pred_thr = h.pred_thr; c->fallbacks = h.fallbacks; c->last_resid = h.last_resid;
   c->field_kind = h.field_kind;
   for (int a = 0; a < 3; ++a) c->A0[a] = h.A0[a];
-  c->f_omega = h.f_omega; c->f_T = h.f_T; c->f_cep = h.f_cep;
+  c->pulses.assign(h.pulse, h.pulse + h.npulse);
+  c->ftable.resize(3 * (size_t)h.ntable);
+  if (h.ntable > 0) std::memcpy(c->ftable.data(), in, sizeof(double) * c->ftable.size());
+  in += sizeof(double) * c->ftable.size();
+  c->tab_t0 = h.tab_t0; c->tab_dt = h.tab_dt;
   c->ms_ready = h.ms_ready; c->nX = h.nX; c->m0 = h.m0; c->ms_head = h.ms_head; c->dX = h.dX;
   // the step potential follows from V_Hxc at the next step; the observables buffer is reset
   TDKS_CUDA(cudaMemsetAsync(c->d_step_obs, 0, 8 * sizeof(double) * c->ncell, c->stream));

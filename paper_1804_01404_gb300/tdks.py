@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libtdks.so")
 TDKS_F64, TDKS_F32 = 0, 1
 PRED_PC, PRED_EXTRAP, PRED_LEARNED = 0, 1, 2
 NN_NPARAMS = 9105
-FIELD_NONE, FIELD_STEP, FIELD_PULSE = 0, 1, 2
+FIELD_NONE, FIELD_STEP, FIELD_PULSE, FIELD_TABLE = 0, 1, 2, 3
 STATUS = {0: "TDKS_OK", 1: "TDKS_EINVAL", 2: "TDKS_ENOMEM", 3: "TDKS_ECUDA", 4: "TDKS_ETIMEOUT",
           5: "TDKS_ENONFINITE", 6: "TDKS_EUNSUPPORTED"}
 
@@ -91,6 +91,8 @@ def load_library(path: str = LIB_PATH):
                       C.POINTER(C.c_double), C.POINTER(C.c_double), i, i, C.POINTER(Options), vp,
                       C.POINTER(vp)],
         "tdks_set_field": [vp, i, _D3, d, d, d],
+        "tdks_add_pulse": [vp, _D3, d, d, d, d],
+        "tdks_set_field_table": [vp, C.POINTER(C.c_double), i, d, d],
         "tdks_kick": [vp, vp, _D3],
         "tdks_update_potential": [vp, vp],
         "tdks_hpsi": [vp, vp, vp, _D3],
@@ -235,9 +237,13 @@ class Context:
                              C.byref(opts), C.c_void_p(stream.cuda_stream), C.byref(ctx)))
         self.ctx = ctx
         f = getattr(system, "field", None)
-        if f is not None and f.kind != "none":
+        if f is not None and f.kind == "table":
+            self.set_field_table(f.table, f.t0, f.dt_table)
+        elif f is not None and f.kind != "none":
             kind = {"step": FIELD_STEP, "pulse": FIELD_PULSE}[f.kind]
             self.set_field(kind, f.A0, f.omega, f.T, f.cep)
+            for (A0, omega, T, cep, delay) in getattr(f, "more", ()):
+                self.add_pulse(A0, omega, T, cep, delay)
 
     def __del__(self):
         try:
@@ -253,6 +259,14 @@ class Context:
     # ---- calls (asynchronous on the context stream unless stated)
     def set_field(self, kind, A0, omega=0.0, T=0.0, cep=0.0):
         _check(self.lib.tdks_set_field(self.ctx, int(kind), _vec3(A0), float(omega), float(T), float(cep)))
+
+    def add_pulse(self, A0, omega, T, cep=0.0, delay=0.0):
+        _check(self.lib.tdks_add_pulse(self.ctx, _vec3(A0), float(omega), float(T), float(cep), float(delay)))
+
+    def set_field_table(self, table, t0, dt_table):
+        tab = np.ascontiguousarray(table, np.float64).reshape(-1, 3)
+        _check(self.lib.tdks_set_field_table(self.ctx, tab.ctypes.data_as(C.POINTER(C.c_double)), len(tab),
+                                             float(t0), float(dt_table)))
 
     def kick(self, u, kappa):
         _check(self.lib.tdks_kick(self.ctx, _ptr(u, self.cdtype), _vec3(kappa)))

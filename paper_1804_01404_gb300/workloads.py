@@ -45,13 +45,20 @@ class Field:
     kind = "none":  A' = 0.
     kind = "step":  A'(t) = A0 for t > 0 (impulsive kick in the velocity gauge, Eq. impulsive_A).
     kind = "pulse": A(t) = Im{A0 cos^2[pi(t-T/2)/T] exp[-i w (t-T/2) - 2 pi i cep]}, 0<t<T (Eq. pulse);
-                    A0 here is already divided by c.
+                    A0 here is already divided by c.  `more` adds delayed pulses of the same form,
+                    each (A0, omega, T, cep, delay), and A' is the sum (pump-probe).
+    kind = "table": A'(t) from samples table[i] = A'(t0 + i dt_table), linear in between, the end
+                    samples outside the table.
     """
     kind: str = "none"
     A0: tuple = (0.0, 0.0, 0.0)
     omega: float = 0.0
     T: float = 0.0
     cep: float = 0.0
+    more: tuple = ()
+    table: object = None
+    t0: float = 0.0
+    dt_table: float = 0.0
 
 
 @dataclass

@@ -582,3 +582,33 @@ def test_energy_conservation_with_correlation():
         psi, _, _ = O.run(s, psi0, n, record=False, xc_on=2)
         drifts.append(abs(O.total_energy(s, tabs, Vloc, psi, Ap, xc_on=2) - E0))
     assert drifts[1] < drifts[0] / 3.5, drifts
+
+
+# ---------------------------------------------------------------- fields: pump-probe and tables
+def test_pump_probe_field_is_the_sum_of_delayed_pulses():
+    """Two pulses with a delay: A'(t) equals the single pulse plus the same pulse shape started
+    at the delay, and vanishes outside both windows."""
+    p1 = W.Field("pulse", (0.0, 0.0, 2e-3), 0.057, 300.0, 0.0)
+    p2 = W.Field("pulse", (0.0, 1e-3, 0.0), 0.11, 150.0, 0.25)
+    both = W.Field("pulse", p1.A0, p1.omega, p1.T, p1.cep, more=((p2.A0, p2.omega, p2.T, p2.cep, 220.0),))
+    for t in (-1.0, 10.0, 150.0, 221.0, 299.0, 330.0, 369.9, 371.0):
+        ref = O.field_Aprime(p1, t) + O.field_Aprime(p2, t - 220.0)
+        assert np.array_equal(O.field_Aprime(both, t), ref), t
+    assert np.all(O.field_Aprime(both, 371.0) == 0.0) and np.all(O.field_Aprime(both, 0.0) == 0.0)
+    assert O.field_Aprime(both, 260.0)[1] != 0.0 and O.field_Aprime(both, 260.0)[2] != 0.0
+
+
+def test_field_table_interpolates_linearly():
+    """A table of the pulse sampled every 0.05 au reproduces the pulse to O(dt^2) (the linear
+    interpolant's error bound |A''| dt^2 / 8), hits every sample exactly, and is constant outside."""
+    p = W.pulse_field()
+    dtab = 0.05
+    ts = np.arange(0, int(p.T / dtab) + 1) * dtab
+    tab = np.array([O.field_Aprime(p, t) for t in ts])
+    f = W.Field("table", table=tab, t0=0.0, dt_table=dtab)
+    A0 = np.max(np.abs(p.A0))
+    app = A0 * (p.omega + 2 * np.pi / p.T) ** 2          # bound on |A''|
+    for t in np.linspace(1.0, p.T - 1.0, 97):
+        assert np.max(np.abs(O.field_Aprime(f, t) - O.field_Aprime(p, t))) <= app * dtab ** 2 / 8 * 1.001
+    assert np.array_equal(O.field_Aprime(f, ts[37]), tab[37])
+    assert np.array_equal(O.field_Aprime(f, -5.0), tab[0]) and np.array_equal(O.field_Aprime(f, p.T + 9.0), tab[-1])
