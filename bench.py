@@ -605,43 +605,66 @@ def workload_steps(dev, warmup=2, steps=5):
 
 def absorption_peak_check(dev, nsteps=1000, kappa=1e-3):
     """Eq. (distribution) spectrum of a kicked isolated cluster (32^3 grid, h = 0.4, 8 atoms,
-    16 orbitals, impulse exp(i kappa z)) propagated on the GPU with FP64 orbitals and with FP32
-    orbitals (plain predictor-corrector both); the main absorption peak of each, located on a
-    0.001 eV grid with tdks_oscillator_strength, and their distance (criterion: 0.01 eV)."""
+    16 orbitals, impulse exp(i kappa z)) propagated on the GPU three ways: FP64 orbitals with the
+    plain predictor-corrector (the reference), FP32 with the plain predictor-corrector, and FP32
+    with the learned predictor (network trained on the GPU on three other kicked initial states of
+    the same cluster, PC fallback at misfit > 1e-5).  The main absorption peak of each is located on
+    a 0.001 eV grid with tdks_oscillator_strength; criterion: FP32 peaks within 0.01 eV of FP64."""
     import torch
+    from paper_1804_01404_gb300 import learned as L
     from paper_1804_01404_gb300 import tdks as T
     from paper_1804_01404_gb300 import workloads as W
     ev = 27.211386245988
     s = W.isolated_cluster(n=32, natom=8, norb=16, radius=5.0, seed=2)
+    kick = (0.0, 0.0, kappa)
     psi0 = W.initial_orbitals(s, 1)
     res = {"workload": "isolated cluster 32^3 (h = 0.4), 8 atoms, 16 orbitals, kick 1e-3 along z, "
-                       f"{nsteps} predictor-corrector steps of dt = {s.dt}", "steps": nsteps}
+                       f"{nsteps} steps of dt = {s.dt}", "steps": nsteps}
+    tic = time.perf_counter()
+    trajs = [L.trajectory(s, W.initial_orbitals(s, seed), 300, "f32", kick=kick) for seed in (2, 3, 4)]
+    tctx = T.Context(s, precision="f32")
+    tctx.nn_init(1)
+    L.train(tctx, trajs, epochs=3, batch=8, lr=1e-3, seed=5)
+    params = tctx.nn_params()
+    tctx.close()
+    del trajs
+    res["training_s"] = time.perf_counter() - tic
     peaks = {}
-    for prec in ("f64", "f32"):
+    for name, prec, mode in (("f64_pc", "f64", T.PRED_PC), ("f32_pc", "f32", T.PRED_PC),
+                             ("f32_learned", "f32", T.PRED_LEARNED)):
         ctx = T.Context(s, precision=prec)
         u = torch.from_numpy(psi0.astype(np.complex128 if prec == "f64" else np.complex64)).to(dev)
-        ctx.kick(u, (0.0, 0.0, kappa))
+        ctx.kick(u, kick)
         ctx.update_potential(u)
+        if mode != T.PRED_PC:
+            ctx.nn_init(0)
+            ctx.nn_params(params)
+            ctx.set_predictor(mode, 1e-5)
         d = [0.0]
         tt = 0.0
         torch.cuda.synchronize()
         tic = time.perf_counter()
+        o = None
         for _ in range(nsteps):
             ctx.step(u, tt, s.dt)
             tt += s.dt
-            d.append(ctx.read_step_observables()["dipole"][2])
-        res[f"{prec}_steps_per_s_host_synced"] = nsteps / (time.perf_counter() - tic)
+            o = ctx.read_step_observables()
+            d.append(o["dipole"][2])
+        res[f"{name}_steps_per_s_host_synced"] = nsteps / (time.perf_counter() - tic)
+        if mode != T.PRED_PC:
+            res[f"{name}_fallbacks"] = o["fallbacks"]
         ctx.check()
         ctx.close()
         d = np.array(d)
         E = np.arange(0.0, 2.0, 0.005)
         E0 = E[np.argmax(T.oscillator_strength(d, s.dt, kappa, E))]
         Ef = np.arange(max(E0 - 0.01, 1e-6), E0 + 0.01, 0.001 / ev)
-        peaks[prec] = (float(Ef[np.argmax(T.oscillator_strength(d, s.dt, kappa, Ef))]), d)
+        peaks[name] = (float(Ef[np.argmax(T.oscillator_strength(d, s.dt, kappa, Ef))]), d)
     res["peak_eV"] = {p: v[0] * ev for p, v in peaks.items()}
-    res["peak_shift_f32_vs_f64_eV"] = abs(peaks["f32"][0] - peaks["f64"][0]) * ev
-    d64, d32 = peaks["f64"][1], peaks["f32"][1]
-    res["dipole_rel_err_f32_vs_f64"] = float(np.max(np.abs(d32 - d64)) / np.max(np.abs(d64)))
+    d64 = peaks["f64_pc"][1]
+    for name in ("f32_pc", "f32_learned"):
+        res[f"peak_shift_{name}_vs_f64_eV"] = abs(peaks[name][0] - peaks["f64_pc"][0]) * ev
+        res[f"dipole_rel_err_{name}_vs_f64"] = float(np.max(np.abs(peaks[name][1] - d64)) / np.max(np.abs(d64)))
     res["resolution_eV"] = 2 * np.pi / (nsteps * s.dt) * ev
     return res
 

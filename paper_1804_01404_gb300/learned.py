@@ -12,14 +12,16 @@ import time
 import numpy as np
 
 
-def trajectory(system, psi0, nsteps, precision="f32", t0=0.0):
+def trajectory(system, psi0, nsteps, precision="f32", t0=0.0, kick=None):
     """V_Hxc(t) for t = t0 .. t0 + nsteps dt along a plain predictor-corrector run, as a CUDA float64
-    tensor [nsteps + 1, nz, ny, nx]."""
+    tensor [nsteps + 1, nz, ny, nx].  kick: optional impulse exp(i kappa.r) applied first (tdks_kick)."""
     import torch
     from .tdks import Context
     ctx = Context(system, precision=precision)
     dt = torch.complex64 if precision == "f32" else torch.complex128
     u = torch.from_numpy(np.ascontiguousarray(psi0)).to("cuda", dt)
+    if kick is not None:
+        ctx.kick(u, kick)
     ctx.update_potential(u)
     out = torch.empty((nsteps + 1, system.n[2], system.n[1], system.n[0]), dtype=torch.float64, device="cuda")
     out[0] = ctx.grid_array(1)
