@@ -142,6 +142,11 @@ tdks_status tdks_add_pulse(tdks_ctx* ctx, const double A0[3], double omega, doub
  * nt outside 1..2^26, dt_table <= 0 or a non-finite value. */
 tdks_status tdks_set_field_table(tdks_ctx* ctx, const double* Ap, int nt, double t0, double dt_table);
 
+/* The context's field at time t (host values, no GPU work): Ap = A'(t) as tdks_step uses it, and
+ * E = -dA'/dt (the electric field, E = -(1/c) dA/dt) by a central difference with step
+ * h = 1e-6 max(1, |t|).  Either output may be NULL (not both).  Isolated systems report 0. */
+tdks_status tdks_field_at(tdks_ctx* ctx, double t, double Ap[3], double E[3]);
+
 /* Isolated impulse (Sec. 3.1): u <- exp(i kappa . r) u for all orbitals, in place. */
 tdks_status tdks_kick(tdks_ctx* ctx, void* u_dev, const double kappa[3]);
 
@@ -371,6 +376,15 @@ tdks_status tdks_oscillator_strength(const double* d, int nt, double dt, double 
  * (the Sec. 4.1 example removes a small constant current for this reason); otherwise xbar = 0. */
 tdks_status tdks_conductivity(const double* I, int nt, double dt, double Ap0, const double* w, int nw,
                               int subtract_mean, double* sigma, double* eps, void* stream);
+
+/* Work done by the field per unit volume, Sec. 4.1: W(t_i) = int_0^{t_i} I(t').E(t') dt' for samples
+ * I[3 i + a], E[3 i + a] at t_i = i dt (a cumulative trapezoid sum, W[0] = 0; host arrays, FP64 on the
+ * GPU, synchronous on `stream`).  This is the electronic excitation energy per volume
+ * (E_el(t) - E_el(0)) / Omega when the xc potential derives from an energy functional.  The sign is
+ * the one that makes the work of the field on the electrons positive with I of Eq. (macro_current)
+ * and E = -dA'/dt (the paper prints W = -int I.E dt', i.e. the opposite sign convention for one of
+ * them).  Errors: EINVAL for a null array, nt outside 1..2^26 or dt <= 0; ENOMEM / ECUDA. */
+tdks_status tdks_work(const double* I, const double* E, int nt, double dt, double* W, void* stream);
 
 const char* tdks_last_error(void);
 int tdks_abi_version(void);

@@ -22,7 +22,8 @@ What it computes (Hartree atomic units, hbar = m = e = 1, A' = A/c):
   isolated boxes with a zero-padded (Hockney) convolution.
 * Sec. 3.1 LDA: adiabatic local exchange (Slater) and, as an option, the Perdew-Zunger correlation.
 * Sec. 3.1: dipole d = -int r (rho - rho0); Eq. (distribution): oscillator-strength spectrum.
-* Sec. 4.1, Eq. (sigma_ft): conductivity and dielectric function from the current after an A step.
+* Sec. 4.1, Eq. (sigma_ft): conductivity and dielectric function from the current after an A step;
+  the work of the field W(t) = int I.E dt (excitation energy per volume).
 * Eq. (macro_current): macroscopic current including the nonlocal term.
 * Eq. (pulse), Eq. (impulsive_A): fields.
 * Eq. (Maxwell_ms): 1D wave equation driven by the cell currents.
@@ -530,6 +531,48 @@ def conductivity(t, I, Ap0, omegas, subtract_mean=True):
 def dielectric(omegas, sigma):
     """Sec. 4.1: eps(w) = 1 + 4 pi i sigma(w) / w."""
     return 1.0 + 4.0 * np.pi * 1j * np.asarray(sigma) / np.asarray(omegas, np.float64)
+
+
+def field_E(f, t):
+    """E(t) = -dA'/dt of field_Aprime: the pulse (and pulse trains) differentiated in closed form,
+    tables by their piecewise slope (the mean of both sides at a sample), a step gives 0 for t != 0."""
+    if f.kind in ("none", "step"):
+        return np.zeros(3)
+    if f.kind == "pulse":
+        def dpulse(A0, omega, T, cep, tt):
+            if not (0.0 < tt < T):
+                return np.zeros(3)
+            x = math.pi * (tt - T / 2.0) / T
+            ph = -omega * (tt - T / 2.0) - 2.0 * math.pi * cep
+            env = math.cos(x) ** 2
+            denv = -2.0 * math.cos(x) * math.sin(x) * math.pi / T
+            return np.asarray(A0, np.float64) * (denv * math.sin(ph) - env * omega * math.cos(ph))
+        g = dpulse(f.A0, f.omega, f.T, f.cep, t)
+        for (A1, w1, T1, c1, delay) in getattr(f, "more", ()):
+            g = g + dpulse(A1, w1, T1, c1, t - delay)
+        return -g
+    if f.kind == "table":
+        tab = np.asarray(f.table, np.float64).reshape(-1, 3)
+        x = (t - f.t0) / f.dt_table
+        if len(tab) == 1 or x < 0.0 or x > len(tab) - 1:
+            return np.zeros(3)
+        i = int(math.floor(x))
+        if x == i:                                    # at a sample: mean of the two slopes
+            lo = (tab[i] - tab[i - 1]) / f.dt_table if i > 0 else None
+            hi = (tab[i + 1] - tab[i]) / f.dt_table if i + 1 < len(tab) else None
+            sl = [v for v in (lo, hi) if v is not None]
+            return -sum(sl) / len(sl)
+        return -(tab[i + 1] - tab[i]) / f.dt_table
+    raise ValueError(f.kind)
+
+
+def work(t, J, E):
+    """Sec. 4.1: W(t) = int_0^t I.E dt' per unit volume by the trapezoid rule on the samples; with I
+    of Eq. (macro_current) and E = -dA'/dt this is (E_el(t) - E_el(0)) / Omega for an LDA energy
+    functional (the sign that makes the field's work on the electrons positive)."""
+    t = np.asarray(t, np.float64)
+    g = np.sum(np.asarray(J, np.float64) * np.asarray(E, np.float64), axis=1)
+    return np.concatenate([[0.0], np.cumsum(0.5 * (g[1:] + g[:-1]) * np.diff(t))])
 
 
 def mur_boundary(A_next, A_now, c_dt_dX):

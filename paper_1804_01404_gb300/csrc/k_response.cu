@@ -7,7 +7,11 @@
 //     library's fields, so c / A0 = 1 / A'0), and eps(w) = 1 + 4 pi i sigma(w) / w; optionally
 //     with the mean current removed first (Sec. 4.1 example: sigma(0) = 0 for a gapped material).
 // Both use the cubic mask f(x) = 1 - 3x^2 + 2x^3 and the samples t_i = i dt, i = 0..n-1, T = t_{n-1},
-// summed with weight dt.  FP64 throughout.
+// summed with weight dt.
+//   * Sec. 4.1: the work done by the field per unit volume, W(t) = int_0^t I(t').E(t') dt' (the
+//     electronic excitation energy per volume when the xc potential derives from an energy
+//     functional), as a cumulative trapezoid sum.
+// FP64 throughout.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -106,6 +110,35 @@ __global__ void k_response_finish(const double2* __restrict__ F, const double* _
   }
 }
 
+// W[0] = 0, W[i] = W[i-1] + dt/2 (g[i-1] + g[i]), g[i] = I[i].E[i] (3-vectors).  One CTA: thread k
+// owns a contiguous chunk of increments, the chunk totals are scanned in shared memory (fixed
+// order), and each thread then writes its chunk's running sums.
+constexpr int kScanThreads = 1024;
+__global__ void __launch_bounds__(kScanThreads) k_work(const double* __restrict__ I, const double* __restrict__ E,
+                                                       int n, double dt, double* __restrict__ W) {
+  __shared__ double tot[kScanThreads];
+  auto g = [&](int i) { return I[3 * i] * E[3 * i] + I[3 * i + 1] * E[3 * i + 1] + I[3 * i + 2] * E[3 * i + 2]; };
+  const int m = n - 1;                                  // increments 1..n-1
+  const int chunk = (m + kScanThreads - 1) / kScanThreads;
+  const int i0 = 1 + threadIdx.x * chunk, i1 = min(n, i0 + chunk);
+  double s = 0.0;
+  for (int i = i0; i < i1; ++i) s += 0.5 * dt * (g(i - 1) + g(i));
+  tot[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 1; o < kScanThreads; o <<= 1) {          // inclusive scan (Hillis-Steele)
+    const double add = threadIdx.x >= o ? tot[threadIdx.x - o] : 0.0;
+    __syncthreads();
+    tot[threadIdx.x] += add;
+    __syncthreads();
+  }
+  double run = threadIdx.x > 0 ? tot[threadIdx.x - 1] : 0.0;
+  if (threadIdx.x == 0) W[0] = 0.0;
+  for (int i = i0; i < i1; ++i) {
+    run += 0.5 * dt * (g(i - 1) + g(i));
+    W[i] = run;
+  }
+}
+
 tdks_status rfail(tdks_status s, const char* msg) {
   set_last_error(msg);
   return s;
@@ -168,6 +201,7 @@ tdks_status check_series(const double* x, int nt, double dt, const double* w, in
 }  // namespace tdks
 
 using tdks::check_series;
+using tdks::k_work;
 using tdks::masked_response;
 using tdks::rfail;
 
@@ -188,4 +222,34 @@ extern "C" tdks_status tdks_conductivity(const double* I, int nt, double dt, dou
     for (int j = 0; j < nw; ++j)
       if (!(w[j] > 0.0)) return rfail(TDKS_EINVAL, "tdks_conductivity: eps needs every frequency > 0");
   return masked_response(I, nt, dt, w, nw, subtract_mean ? 1 : 0, 1, Ap0, sigma, eps, stream);
+}
+
+extern "C" tdks_status tdks_work(const double* I, const double* E, int nt, double dt, double* W, void* stream) {
+  if (!I || !E || !W) return rfail(TDKS_EINVAL, "tdks_work: null array");
+  if (nt < 1 || nt > (1 << 26)) return rfail(TDKS_EINVAL, "tdks_work: nt outside 1..2^26");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return rfail(TDKS_EINVAL, "tdks_work: dt must be positive");
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t b3 = sizeof(double) * 3 * (size_t)nt, b1 = sizeof(double) * (size_t)nt;
+  double *dI = nullptr, *dE = nullptr, *dW = nullptr;
+  cudaError_t e = cudaSuccess;
+  auto chk = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+  chk(cudaMalloc(&dI, b3));
+  chk(cudaMalloc(&dE, b3));
+  chk(cudaMalloc(&dW, b1));
+  if (e == cudaSuccess) {
+    chk(cudaMemcpyAsync(dI, I, b3, cudaMemcpyHostToDevice, s));
+    chk(cudaMemcpyAsync(dE, E, b3, cudaMemcpyHostToDevice, s));
+  }
+  if (e == cudaSuccess) {
+    k_work<<<1, tdks::kScanThreads, 0, s>>>(dI, dE, nt, dt, dW);
+    chk(cudaGetLastError());
+  }
+  if (e == cudaSuccess) chk(cudaMemcpyAsync(W, dW, b1, cudaMemcpyDeviceToHost, s));
+  if (e == cudaSuccess) chk(cudaStreamSynchronize(s));
+  cudaFree(dI);
+  cudaFree(dE);
+  cudaFree(dW);
+  if (e != cudaSuccess) return rfail(e == cudaErrorMemoryAllocation ? TDKS_ENOMEM : TDKS_ECUDA,
+                                     (std::string("tdks_work: ") + cudaGetErrorString(e)).c_str());
+  return TDKS_OK;
 }

@@ -826,6 +826,21 @@ tdks_status tdks_set_field(tdks_ctx* c, int kind, const double A0[3], double ome
   return TDKS_OK;
 }
 
+tdks_status tdks_field_at(tdks_ctx* c, double t, double Ap[3], double E[3]) {
+  TDKS_TRY(check_ctx(c));
+  if (!Ap && !E) return fail(TDKS_EINVAL, "null outputs");
+  if (!std::isfinite(t)) return fail(TDKS_EINVAL, "t must be finite");
+  if (Ap) field_at(c, t, Ap);
+  if (E) {   // E = -dA'/dt by a central difference (h = 1e-6 max(1, |t|))
+    const double h = 1e-6 * std::max(1.0, std::fabs(t));
+    double ap[3], am[3];
+    field_at(c, t + h, ap);
+    field_at(c, t - h, am);
+    for (int a = 0; a < 3; ++a) E[a] = -(ap[a] - am[a]) / (2.0 * h);
+  }
+  return TDKS_OK;
+}
+
 tdks_status tdks_add_pulse(tdks_ctx* c, const double A0[3], double omega, double T, double cep, double t_delay) {
   TDKS_TRY(check_ctx(c));
   if (c->field_kind != TDKS_FIELD_PULSE) return fail(TDKS_EINVAL, "tdks_add_pulse needs a field of kind TDKS_FIELD_PULSE");

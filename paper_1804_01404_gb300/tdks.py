@@ -124,6 +124,8 @@ def load_library(path: str = LIB_PATH):
                                      C.POINTER(C.c_double), vp],
         "tdks_conductivity": [C.POINTER(C.c_double), i, d, d, C.POINTER(C.c_double), i, i,
                               C.POINTER(C.c_double), C.POINTER(C.c_double), vp],
+        "tdks_work": [C.POINTER(C.c_double), C.POINTER(C.c_double), i, d, C.POINTER(C.c_double), vp],
+        "tdks_field_at": [vp, d, C.POINTER(C.c_double), C.POINTER(C.c_double)],
         "tdks_get_state": [vp, vp, C.c_size_t],
         "tdks_set_state": [vp, vp, C.c_size_t],
     }
@@ -180,6 +182,18 @@ def conductivity(I, dt, Ap0, w, subtract_mean=True, stream=None):
                                  _dptr(sig), _dptr(eps) if want_eps else None, _stream_handle(stream)))
     sigma = sig[0::2] + 1j * sig[1::2]
     return sigma, (eps[0::2] + 1j * eps[1::2]) if want_eps else None
+
+
+def work(I, E, dt, stream=None):
+    """W(t_i) = int_0^t_i I.E dt' of sampled I[i][3], E[i][3] at t_i = i dt (tdks_work)."""
+    lib = load_library()
+    I = np.ascontiguousarray(I, np.float64).reshape(-1, 3)
+    E = np.ascontiguousarray(E, np.float64).reshape(-1, 3)
+    if len(I) != len(E):
+        raise ValueError("I and E need the same number of samples")
+    out = np.zeros(len(I))
+    _check(lib.tdks_work(_dptr(I), _dptr(E), len(I), float(dt), _dptr(out), _stream_handle(stream)))
+    return out
 
 
 def _check(status):
@@ -267,6 +281,13 @@ class Context:
         tab = np.ascontiguousarray(table, np.float64).reshape(-1, 3)
         _check(self.lib.tdks_set_field_table(self.ctx, tab.ctypes.data_as(C.POINTER(C.c_double)), len(tab),
                                              float(t0), float(dt_table)))
+
+    def field_at(self, t):
+        """(A'(t), E(t) = -dA'/dt) of the context's field (tdks_field_at)."""
+        ap = (C.c_double * 3)()
+        e = (C.c_double * 3)()
+        _check(self.lib.tdks_field_at(self.ctx, float(t), ap, e))
+        return np.array(ap[:]), np.array(e[:])
 
     def kick(self, u, kappa):
         _check(self.lib.tdks_kick(self.ctx, _ptr(u, self.cdtype), _vec3(kappa)))

@@ -134,3 +134,38 @@ def test_dielectric_function_of_a_kicked_cell(precision, tol):
     _, eps = T.conductivity(J, s.dt, Ap0, w, subtract_mean=True)
     eps_ref = O.dielectric(w, O.conductivity(t, Jref, Ap0, w, subtract_mean=True))
     assert _rel(eps - 1.0, eps_ref - 1.0) < 10 * tol
+
+
+def test_work_of_the_field():
+    """Sec. 4.1 work W(t) = int I.E dt: the GPU's FP64 current history and the context's field
+    (tdks_field_at) through tdks_work, against the oracle's current, closed-form E and work."""
+    from paper_1804_01404_gb300 import tdks as T
+    s = W.tiny(periodic=True, n=(6, 7, 8), natom=2, nk=2, norb=2)
+    s.field = W.Field("pulse", (0.0, 0.0, 0.05), 0.5, 6.0, 0.0, more=(((0.02, 0.0, 0.0), 0.8, 2.0, 0.0, 2.5),))
+    psi0 = W.initial_orbitals(s, 3)
+    n = 300
+    ctx = T.Context(s, precision="f64")
+    u = torch.from_numpy(psi0).cuda()
+    ctx.update_potential(u)
+    o0 = ctx.observables(u, ctx.field_at(0.0)[0])
+    J, E = [o0["J"]], [ctx.field_at(0.0)[1]]
+    tt = 0.0
+    for _ in range(n):
+        ctx.step(u, tt, s.dt)
+        tt += s.dt
+        J.append(ctx.read_step_observables()["J"])
+        Ap, Ef = ctx.field_at(tt)
+        assert np.max(np.abs(Ap - O.field_Aprime(s.field, tt))) < 1e-15
+        # central difference vs closed form; at a pulse onset (t = 2.5) the one-sided quadratic start
+        # of the envelope costs O(h |A''|) ~ 1e-7
+        assert np.max(np.abs(Ef - O.field_E(s.field, tt))) < 1e-6
+        E.append(Ef)
+    ctx.check()
+    ctx.close()
+    Wg = T.work(np.array(J), np.array(E), s.dt)
+    _, _, hist = O.run(s, psi0, n)
+    ts = np.arange(n + 1) * s.dt
+    Jref = np.concatenate([[O.current(s, O.projector_tables(s), psi0, np.zeros(3))], hist["J"]])
+    Wref = O.work(ts, Jref, np.array([O.field_E(s.field, t) for t in ts]))
+    assert _rel(Wg, Wref) < 1e-6
+    assert np.max(np.abs(Wref)) > 1e-6                       # the field does work
