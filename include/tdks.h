@@ -142,6 +142,20 @@ tdks_status tdks_add_pulse(tdks_ctx* ctx, const double A0[3], double omega, doub
  * nt outside 1..2^26, dt_table <= 0 or a non-finite value. */
 tdks_status tdks_set_field_table(tdks_ctx* ctx, const double* Ap, int nt, double t0, double dt_table);
 
+/* Longitudinal geometry (Sec. 4.1: in a thin film the vector potential is the external one plus the
+ * one induced by the surface polarisation): A'(t) = A'_ext(t) + A'_ind(t) with
+ * d^2 A'_ind / dt^2 = 4 pi J(t) (Gaussian units: E_ind = -4 pi P, dP/dt = J, E = -(1/c) dA/dt).  Each
+ * tdks_step first advances A'_ind by the leapfrog A^{n+1} = 2 A^n - A^{n-1} + 4 pi dt^2 J(t_n) (the
+ * first step from rest: A^1 = 2 pi dt^2 J(t_0)), on the device from the current the previous step
+ * left, then propagates with A' = A'_ext(t + dt/2) + (A^n + A^{n+1})/2 and forms J(t + dt) with
+ * A'_ext(t + dt) + A^{n+1}.  enable = 1 sets A'_ind = 0 and forms J(t0) of the orbitals u with
+ * A'_ext(t0); enable = 0 switches it off.  The paper gives no equation for the induced potential;
+ * this is the thin-film form of the works it cites.  Errors: EUNSUPPORTED unless the context has one
+ * periodic cell, obs_at_start = 0 and no multiscale grid; EINVAL for a NULL u or enable outside 0..1.
+ * tdks_longitudinal_read gives A'_ind at the end of the last step (synchronises). */
+tdks_status tdks_set_longitudinal(tdks_ctx* ctx, int enable, const void* u, double t0);
+tdks_status tdks_longitudinal_read(tdks_ctx* ctx, double A_ind[3]);
+
 /* The context's field at time t (host values, no GPU work): Ap = A'(t) as tdks_step uses it, and
  * E = -dA'/dt (the electric field, E = -(1/c) dA/dt) by a central difference with step
  * h = 1e-6 max(1, |t|).  Either output may be NULL (not both).  Isolated systems report 0. */
@@ -311,7 +325,8 @@ tdks_status tdks_cell_variant(tdks_ctx* ctx, int set, int* variant, float* tune_
  *   V_Hxc(t), rho(t) and the reference density rho0 of every cell; the last four V_Hxc of the
  *   predictor history; the predictor mode, threshold, fallback count and network parameters; the
  *   multiscale field levels A^n, A^{n-1}, A^{n+1}, the cell currents and the grid geometry; the
- *   field settings (tdks_set_field, tdks_add_pulse, tdks_set_field_table).
+ *   field settings (tdks_set_field, tdks_add_pulse, tdks_set_field_table) and the longitudinal
+ *   geometry's induced potential and current.
  * tdks_state_size gives the bytes; tdks_get_state writes them to host memory (synchronises);
  * tdks_set_state restores them into a context created for the same system and options (grid
  * points, cells, k-points, orbitals, precision, atoms, hartree/xc/pc), checked against the

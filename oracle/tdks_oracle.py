@@ -389,8 +389,10 @@ def current(s, tabs, psi, Ap):
         c = projections(s, tabs, q, u)
         for a in range(3):
             loc = np.real(np.sum(np.conj(u) * (-1j * d1(u, a, s) + q[a] * u))) * s.dV
-            b = projections(s, tabs, q, u, weight_by=a)
-            nl = np.sum(2.0 * np.array([t["E"] for t in tabs])[None] * np.imag(np.conj(b) * c))
+            nl = 0.0
+            if tabs:                                  # no atoms: no nonlocal current
+                b = projections(s, tabs, q, u, weight_by=a)
+                nl = np.sum(2.0 * np.array([t["E"] for t in tabs])[None] * np.imag(np.conj(b) * c))
             J[a] += s.kw[ik] * 2.0 * (loc + nl)
     return -J / cell_volume(s)
 
@@ -531,6 +533,33 @@ def conductivity(t, I, Ap0, omegas, subtract_mean=True):
 def dielectric(omegas, sigma):
     """Sec. 4.1: eps(w) = 1 + 4 pi i sigma(w) / w."""
     return 1.0 + 4.0 * np.pi * 1j * np.asarray(sigma) / np.asarray(omegas, np.float64)
+
+
+def longitudinal_run(s, psi0, nsteps, t0=0.0, hartree_on=True, xc_on=True):
+    """Longitudinal geometry (Sec. 4.1, thin film): A'(t) = A'_ext(t) + A'_ind(t) with
+    d^2 A'_ind/dt^2 = 4 pi J(t) (E_ind = -4 pi P, dP/dt = J, E = -dA'/dt).  Per step:
+    A^{n+1} = 2 A^n - A^{n-1} + 4 pi dt^2 J(t_n) (first step from rest, A^1 = 2 pi dt^2 J(t_0)), the
+    predictor-corrector step with A'_ext(t + dt/2) + (A^n + A^{n+1})/2, and J(t + dt) with
+    A'_ext(t + dt) + A^{n+1}.  Returns the orbitals and per-step records of J and A'_ind."""
+    tabs = projector_tables(s)
+    Vloc = local_potential(s)
+    psi = psi0.copy()
+    vhxc = hxc(s, density(s, psi), hartree_on, xc_on)
+    t = t0
+    J = current(s, tabs, psi, field_Aprime(s.field, t))
+    A_now, A_prev = np.zeros(3), None
+    hist = dict(J=[], A_ind=[])
+    for _ in range(nsteps):
+        src = 4.0 * np.pi * s.dt ** 2 * J
+        A_next = A_now + 0.5 * src if A_prev is None else 2.0 * A_now - A_prev + src
+        Amid = field_Aprime(s.field, t + 0.5 * s.dt) + 0.5 * (A_now + A_next)
+        psi, vhxc, _ = pc_step(s, tabs, Vloc, psi, vhxc, t, s.dt, True, hartree_on, xc_on, Ap=Amid)
+        t += s.dt
+        A_prev, A_now = A_now, A_next
+        J = current(s, tabs, psi, field_Aprime(s.field, t) + A_now)
+        hist["J"].append(J)
+        hist["A_ind"].append(A_now.copy())
+    return psi, {k: np.array(v) for k, v in hist.items()}
 
 
 def field_E(f, t):

@@ -844,9 +844,36 @@ __global__ void k_maxwell(const double* __restrict__ Ap, const double* __restric
   }
 }
 
+// Longitudinal geometry: d^2 A'_ind / dt^2 = 4 pi J, one leapfrog step per TDKS step from the current
+// J(t_n) in step_obs[0..2]; lg = {A_ind^n[3], A_ind^{n-1}[3]} is advanced in place.  The first step
+// starts from rest (zero A_ind and zero velocity: A^1 = A^0 + 2 pi dt^2 J).  The A' of the step's
+// Taylor stages (mid) and of its end (end) add the external field.
+__global__ void k_longitudinal(const double* __restrict__ step_obs, double* __restrict__ lg, int first, double dt,
+                               double3 ext_mid, double3 ext_end, double* __restrict__ mid, double* __restrict__ end) {
+  const int a = threadIdx.x;
+  if (a >= 3) return;
+  const double J = step_obs[a];
+  const double An = lg[a], Ap = lg[3 + a];
+  const double src = 4.0 * kPi * dt * dt * J;
+  const double Anext = first ? An + 0.5 * src : 2.0 * An - Ap + src;
+  lg[3 + a] = An;
+  lg[a] = Anext;
+  const double em = a == 0 ? ext_mid.x : (a == 1 ? ext_mid.y : ext_mid.z);
+  const double ee = a == 0 ? ext_end.x : (a == 1 ? ext_end.y : ext_end.z);
+  mid[a] = em + 0.5 * (An + Anext);
+  end[a] = ee + Anext;
+}
+
 __global__ void k_ms_current(const double* __restrict__ step_obs, int ncell, int m0, double* __restrict__ I) {
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += gridDim.x * blockDim.x)
     I[m0 + c] = step_obs[(size_t)c * 8 + 2];
+}
+
+cudaError_t launch_longitudinal(const double* step_obs, double* lg, int first, double dt, const double ext_mid[3],
+                                const double ext_end[3], double* ap_mid, double* ap_end, cudaStream_t s) {
+  k_longitudinal<<<1, 32, 0, s>>>(step_obs, lg, first, dt, make_double3(ext_mid[0], ext_mid[1], ext_mid[2]),
+                                  make_double3(ext_end[0], ext_end[1], ext_end[2]), ap_mid, ap_end);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_maxwell(const double* A_prev, const double* A_now, double* A_next, const double* I,

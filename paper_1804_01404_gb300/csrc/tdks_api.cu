@@ -62,6 +62,8 @@ struct tdks_ctx {
   std::vector<PulseDef> pulses;             // TDKS_FIELD_PULSE: A' is their sum
   std::vector<double> ftable;               // TDKS_FIELD_TABLE: [nt][3] samples of A'
   double tab_t0 = 0.0, tab_dt = 0.0;
+  int longitudinal = 0, lg_first = 1;       // longitudinal geometry (tdks_set_longitudinal)
+  double* d_lg = nullptr;                   // {A'_ind^n[3], A'_ind^{n-1}[3]}
   // projector tables
   int natom = 0, nsph = 0;
   int *d_atom_off = nullptr, *d_sph_idx = nullptr, *d_pt_off = nullptr, *d_pt_ent = nullptr,
@@ -841,6 +843,47 @@ tdks_status tdks_field_at(tdks_ctx* c, double t, double Ap[3], double E[3]) {
   return TDKS_OK;
 }
 
+tdks_status tdks_set_longitudinal(tdks_ctx* c, int enable, const void* u, double t0) {
+  TDKS_TRY(check_ctx(c));
+  if (enable != 0 && enable != 1) return fail(TDKS_EINVAL, "enable must be 0 or 1");
+  if (!enable) {
+    c->longitudinal = 0;
+    return TDKS_OK;
+  }
+  if (!c->grid.periodic || c->ncell != 1 || c->ms_ready)
+    return fail(TDKS_EUNSUPPORTED, "the longitudinal geometry needs one periodic cell outside the multiscale mode");
+  if (c->opt.obs_at_start) return fail(TDKS_EUNSUPPORTED, "the longitudinal geometry needs obs_at_start = 0");
+  if (!u) return fail(TDKS_EINVAL, "null orbitals");
+  if (!c->d_lg) TDKS_TRY(dalloc(c, &c->d_lg, 6));
+  if (!c->d_ap_mid) {
+    TDKS_TRY(dalloc(c, &c->d_ap_mid, 3 * (size_t)c->ncell));
+    TDKS_TRY(dalloc(c, &c->d_ap_end, 3 * (size_t)c->ncell));
+  }
+  TDKS_CUDA(cudaMemsetAsync(c->d_lg, 0, 6 * sizeof(double), c->stream));
+  double A[3];
+  field_at(c, t0, A);
+  // J(t0) of u (A'_ind = 0 at t0) into the step observables, where the first step reads it
+  TDKS_TRY(orbital_observables(c, u, A));
+  TDKS_CUDA(launch_reduce_current(c->d_orb_obs, c->nk, c->norb, c->d_kw, 1.0 / c->omega, 1, c->d_step_obs,
+                                  c->stream, c->ncell));
+  c->launches += 1;
+  c->lg_first = 1;
+  c->longitudinal = 1;
+  return TDKS_OK;
+}
+
+tdks_status tdks_longitudinal_read(tdks_ctx* c, double A_ind[3]) {
+  TDKS_TRY(check_ctx(c));
+  if (!A_ind) return fail(TDKS_EINVAL, "null output");
+  if (!c->d_lg) {
+    A_ind[0] = A_ind[1] = A_ind[2] = 0.0;
+    return TDKS_OK;
+  }
+  TDKS_CUDA(cudaMemcpyAsync(A_ind, c->d_lg, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  TDKS_CUDA(cudaStreamSynchronize(c->stream));
+  return TDKS_OK;
+}
+
 tdks_status tdks_add_pulse(tdks_ctx* c, const double A0[3], double omega, double T, double cep, double t_delay) {
   TDKS_TRY(check_ctx(c));
   if (c->field_kind != TDKS_FIELD_PULSE) return fail(TDKS_EINVAL, "tdks_add_pulse needs a field of kind TDKS_FIELD_PULSE");
@@ -1013,10 +1056,22 @@ tdks_status tdks_step(tdks_ctx* c, void* u, double t, double dt) {
                             c->d_partials, c->d_ticket, c->d_step_obs, c->stream));   // cell 0
     c->launches += 1;
   }
+  if (c->longitudinal) {   // A' = A'_ext + A'_ind, A'_ind advanced from J(t) on the device
+    Phase ph(c, 5);
+    TDKS_CUDA(launch_longitudinal(c->d_step_obs, c->d_lg, c->lg_first, dt, Amid, Aend, c->d_ap_mid, c->d_ap_end,
+                                  c->stream));
+    c->launches += 1;
+    c->lg_first = 0;
+    c->cur_ap_mid = c->d_ap_mid;
+    c->cur_ap_end = c->d_ap_end;
+  }
   bool done = false;
+  tdks_status st = TDKS_OK;
   if (c->pred_mode != TDKS_PRED_PC && c->hist_count >= 4 && (c->opt.hartree || c->opt.xc))
-    TDKS_TRY(predicted_step(c, u, Amid, Aobs, at_start, dt, &done));
-  if (!done) TDKS_TRY(pc_step(c, u, Amid, Aobs, at_start, dt));
+    st = predicted_step(c, u, Amid, Aobs, at_start, dt, &done);
+  if (st == TDKS_OK && !done) st = pc_step(c, u, Amid, Aobs, at_start, dt);
+  c->cur_ap_mid = c->cur_ap_end = nullptr;
+  TDKS_TRY(st);
   TDKS_TRY(hist_push(c, c->d_vhxc));
   Phase ph(c, 4);
   c->launches += c->grid.periodic ? 1 : 0;   // reduce_current
@@ -1036,6 +1091,7 @@ tdks_status tdks_step(tdks_ctx* c, void* u, double t, double dt) {
 
 tdks_status tdks_ms_init(tdks_ctx* c, int nX, int m0, double dX, const double* A_now, const double* A_prev) {
   TDKS_TRY(check_ctx(c));
+  if (c->longitudinal) return fail(TDKS_EUNSUPPORTED, "the multiscale mode and the longitudinal geometry exclude each other");
   if (!c->grid.periodic) return fail(TDKS_EINVAL, "the multiscale mode needs periodic cells");
   if (!A_now || !A_prev || nX < 3 || m0 < 1 || m0 + c->ncell > nX - 1 || !(dX > 0.0))
     return fail(TDKS_EINVAL, "need nX >= 3, 1 <= m0, m0 + ncell <= nX - 1, dX > 0 and both A levels");
@@ -1431,6 +1487,8 @@ struct StateHeader {
   PulseDef pulse[kMaxPulses];
   int ntable;                 // field table rows, stored after the arrays
   double tab_t0, tab_dt;
+  int longitudinal, lg_first;
+  double lg[6], lg_J[3];      // A'_ind levels and the current J(t_n) the next leapfrog step reads
   int ms_ready, nX, m0, ms_head;
   double dX;
 };
@@ -1471,6 +1529,12 @@ tdks_status tdks_get_state(tdks_ctx* c, void* host, size_t bytes) {
   for (int i = 0; i < h.npulse; ++i) h.pulse[i] = c->pulses[i];
   h.ntable = (int)(c->ftable.size() / 3);
   h.tab_t0 = c->tab_t0; h.tab_dt = c->tab_dt;
+  h.longitudinal = c->longitudinal; h.lg_first = c->lg_first;
+  if (c->d_lg) {
+    TDKS_CUDA(cudaMemcpyAsync(h.lg, c->d_lg, 6 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    TDKS_CUDA(cudaMemcpyAsync(h.lg_J, c->d_step_obs, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    TDKS_CUDA(cudaStreamSynchronize(c->stream));
+  }
   h.ms_ready = c->ms_ready; h.nX = c->nX; h.m0 = c->m0; h.ms_head = c->ms_head; h.dX = c->dX;
   unsigned char* o = static_cast<unsigned char*>(host);
   std::memcpy(o, &h, sizeof(h));
@@ -1554,9 +1618,22 @@ tdks_status tdks_set_state(tdks_ctx* c, const void* host, size_t bytes) {
   if (h.ntable > 0) std::memcpy(c->ftable.data(), in, sizeof(double) * c->ftable.size());
   in += sizeof(double) * c->ftable.size();
   c->tab_t0 = h.tab_t0; c->tab_dt = h.tab_dt;
+  if (h.longitudinal) {
+    if (!c->grid.periodic || c->ncell != 1 || c->opt.obs_at_start)
+      return fail(TDKS_EINVAL, "state holds the longitudinal geometry, which this context cannot use");
+    if (!c->d_lg) TDKS_TRY(dalloc(c, &c->d_lg, 6));
+    if (!c->d_ap_mid) {
+      TDKS_TRY(dalloc(c, &c->d_ap_mid, 3 * (size_t)c->ncell));
+      TDKS_TRY(dalloc(c, &c->d_ap_end, 3 * (size_t)c->ncell));
+    }
+    TDKS_CUDA(cudaMemcpyAsync(c->d_lg, h.lg, 6 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  }
+  c->longitudinal = h.longitudinal; c->lg_first = h.lg_first;
   c->ms_ready = h.ms_ready; c->nX = h.nX; c->m0 = h.m0; c->ms_head = h.ms_head; c->dX = h.dX;
   // the step potential follows from V_Hxc at the next step; the observables buffer is reset
   TDKS_CUDA(cudaMemsetAsync(c->d_step_obs, 0, 8 * sizeof(double) * c->ncell, c->stream));
+  if (h.longitudinal)   // the current the next leapfrog step of A'_ind reads
+    TDKS_CUDA(cudaMemcpyAsync(c->d_step_obs, h.lg_J, 3 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
   TDKS_CUDA(cudaStreamSynchronize(c->stream));
   return TDKS_OK;
 }

@@ -263,6 +263,9 @@ cudaError_t launch_reduce_current(const double* orb_obs, int nk, int norb, const
                                   double inv_omega, int periodic, double* out, cudaStream_t s,
                                   int ncell = 1);
 // 1D Maxwell leapfrog (Eq. Maxwell_ms) with Mur boundaries; A'(X) of the cells at t+dt/2 and t+dt
+// longitudinal geometry: one leapfrog step of A'_ind from J(t_n) = step_obs[0..2] (see k_grid.cu)
+cudaError_t launch_longitudinal(const double* step_obs, double* lg, int first, double dt, const double ext_mid[3],
+                                const double ext_end[3], double* ap_mid, double* ap_end, cudaStream_t s);
 cudaError_t launch_maxwell(const double* A_prev, const double* A_now, double* A_next, const double* I,
                            int nX, int m0, int ncell, double c_dt_dX, double src, double inv_c,
                            double* ap_mid, double* ap_end, cudaStream_t s);

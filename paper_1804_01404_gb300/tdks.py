@@ -126,6 +126,8 @@ def load_library(path: str = LIB_PATH):
                               C.POINTER(C.c_double), C.POINTER(C.c_double), vp],
         "tdks_work": [C.POINTER(C.c_double), C.POINTER(C.c_double), i, d, C.POINTER(C.c_double), vp],
         "tdks_field_at": [vp, d, C.POINTER(C.c_double), C.POINTER(C.c_double)],
+        "tdks_set_longitudinal": [vp, i, vp, d],
+        "tdks_longitudinal_read": [vp, C.POINTER(C.c_double)],
         "tdks_get_state": [vp, vp, C.c_size_t],
         "tdks_set_state": [vp, vp, C.c_size_t],
     }
@@ -281,6 +283,18 @@ class Context:
         tab = np.ascontiguousarray(table, np.float64).reshape(-1, 3)
         _check(self.lib.tdks_set_field_table(self.ctx, tab.ctypes.data_as(C.POINTER(C.c_double)), len(tab),
                                              float(t0), float(dt_table)))
+
+    def set_longitudinal(self, enable, u=None, t0=0.0):
+        """Longitudinal geometry on (A'_ind from d^2 A'_ind/dt^2 = 4 pi J, starting at rest with J of u
+        at t0) or off (tdks_set_longitudinal)."""
+        _check(self.lib.tdks_set_longitudinal(self.ctx, int(enable), _ptr(u, self.cdtype) if u is not None else None,
+                                              float(t0)))
+
+    def longitudinal_A(self):
+        """A'_ind at the end of the last step (tdks_longitudinal_read)."""
+        a = (C.c_double * 3)()
+        _check(self.lib.tdks_longitudinal_read(self.ctx, a))
+        return np.array(a[:])
 
     def field_at(self, t):
         """(A'(t), E(t) = -dA'/dt) of the context's field (tdks_field_at)."""

@@ -659,3 +659,39 @@ def test_work_equals_energy_gain_per_volume():
         gains.append(np.max(np.abs(gain)))
     assert errs[1] < errs[0] / 8, errs
     assert errs[1] < 0.01 * gains[1], (errs, gains)
+
+
+# ---------------------------------------------------------------- longitudinal geometry
+def _electron_gas(n=6, L=7.0):
+    """Uniform electron gas in a periodic box: no atoms, one doubly occupied plane wave at k = 0."""
+    s = W.tiny(periodic=True, n=(n, n, n), natom=0, nk=1, norb=1)
+    s.h = (L / n,) * 3
+    s.kpts = np.zeros((1, 3))
+    s.kw = np.ones(1)
+    psi = np.full((1, 1, n, n, n), 1.0 / math.sqrt(O.cell_volume(s)), complex)
+    return s, psi
+
+
+def test_longitudinal_plasma_oscillation():
+    """Free electrons (density n) after the A' step A0: J = -n A'_total exactly, so
+    A'_ind'' = -4 pi n (A0 + A'_ind) and the total field oscillates as A0 cos(w_p t), w_p^2 = 4 pi n --
+    the plasma oscillation of the thin-film (longitudinal) geometry.  The leapfrog's error is O(dt^2)."""
+    A0 = 1e-3
+    errs = []
+    for dt in (0.04, 0.02):
+        s, psi = _electron_gas()
+        s.field = W.Field("step", (0.0, 0.0, A0))
+        s.dt = dt
+        wp = math.sqrt(4.0 * math.pi * 2.0 / O.cell_volume(s))
+        nsteps = int(round(2.5 * (2 * math.pi / wp) / dt))   # two and a half periods
+        # start just after the step (A'_ext = A0 in J(t0); at t = 0 itself the step is still 0)
+        t0 = 1e-12
+        _, hist = O.longitudinal_run(s, psi, nsteps, t0=t0)
+        t = np.arange(1, nsteps + 1) * dt
+        Atot = A0 + hist["A_ind"][:, 2]
+        J = hist["J"][:, 2]
+        n_e = 2.0 / O.cell_volume(s)
+        # the diamagnetic current, up to the norm drift of the 4th-order propagator
+        assert np.max(np.abs(J + n_e * Atot)) < 1e-9 * A0 * n_e
+        errs.append(np.max(np.abs(Atot - A0 * np.cos(wp * t))))
+    assert errs[0] < 0.05 * A0 and 3.0 < errs[0] / errs[1] < 5.0, errs
