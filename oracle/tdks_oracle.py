@@ -535,6 +535,45 @@ def dielectric(omegas, sigma):
     return 1.0 + 4.0 * np.pi * 1j * np.asarray(sigma) / np.asarray(omegas, np.float64)
 
 
+def dense_hamiltonian(s, tabs, V, q):
+    """H_q as a dense npts x npts matrix, column j = hpsi of the j-th unit vector (tiny grids only)."""
+    N = s.npts
+    H = np.zeros((N, N), np.complex128)
+    for j in range(N):
+        e = np.zeros(N, np.complex128)
+        e[j] = 1.0
+        H[:, j] = hpsi(s, tabs, V, q, e.reshape(s.n[2], s.n[1], s.n[0])).ravel()
+    return H
+
+
+def ground_state(s, hartree_on=True, xc_on=True, mix=0.3, tol=1e-10, max_iter=400):
+    """Self-consistent ground state at A' = 0 (the static Kohn-Sham problem the paper's ground-state
+    step solves before the time evolution): diagonalise H_k[V_loc + V_Hxc] densely for every k,
+    occupy the lowest norb states (each normalised to sum |u|^2 dV = 1), form rho and V_Hxc[rho], and
+    mix the potential linearly, V_in <- V_in + mix (V_out - V_in), until ||V_out - V_in|| / ||V_out||
+    < tol.  Returns (psi [nk][norb][nz][ny][nx], eigenvalues [nk][norb], V_Hxc, iterations)."""
+    tabs = projector_tables(s)
+    Vloc = local_potential(s)
+    shape = (s.n[2], s.n[1], s.n[0])
+    zero = np.zeros(shape)
+    # the potential enters H_k only on the diagonal: build the rest once per k
+    H0 = [dense_hamiltonian(s, tabs, zero, np.asarray(s.kpts[k], np.float64)) for k in range(s.nk)]
+    vin = np.zeros(shape)
+    for it in range(1, max_iter + 1):
+        psi = np.zeros((s.nk, s.norb) + shape, np.complex128)
+        eig = np.zeros((s.nk, s.norb))
+        for k in range(s.nk):
+            E, U = np.linalg.eigh(H0[k] + np.diag((Vloc + vin).ravel()))
+            eig[k] = E[:s.norb]
+            psi[k] = (U[:, :s.norb].T / math.sqrt(s.dV)).reshape((s.norb,) + shape)
+        vout = hxc(s, density(s, psi), hartree_on, xc_on)
+        err = np.linalg.norm(vout - vin) / max(np.linalg.norm(vout), 1e-300)
+        if err < tol:
+            return psi, eig, vout, it
+        vin = vin + mix * (vout - vin)
+    return psi, eig, vout, max_iter
+
+
 def longitudinal_run(s, psi0, nsteps, t0=0.0, hartree_on=True, xc_on=True):
     """Longitudinal geometry (Sec. 4.1, thin film): A'(t) = A'_ext(t) + A'_ind(t) with
     d^2 A'_ind/dt^2 = 4 pi J(t) (E_ind = -4 pi P, dP/dt = J, E = -dA'/dt).  Per step:

@@ -695,3 +695,57 @@ def test_longitudinal_plasma_oscillation():
         assert np.max(np.abs(J + n_e * Atot)) < 1e-9 * A0 * n_e
         errs.append(np.max(np.abs(Atot - A0 * np.cos(wp * t))))
     assert errs[0] < 0.05 * A0 and 3.0 < errs[0] / errs[1] < 5.0, errs
+
+
+# ---------------------------------------------------------------- ground state (static SCF)
+def _loewdin(psi, dV):
+    """Orthonormalise the orbitals of each k-point: u'_i = sum_j (S^{-1/2})_{ji} u_j, S_ij = <u_i|u_j>."""
+    out = np.empty_like(psi)
+    for k in range(psi.shape[0]):
+        Q = psi[k].reshape(psi.shape[1], -1)
+        S = (Q.conj() @ Q.T) * dV
+        w, V = np.linalg.eigh(S)
+        X = V @ np.diag(w ** -0.5) @ V.conj().T
+        out[k] = (X.T @ Q).reshape(psi.shape[1:])
+    return out
+
+
+@pytest.mark.parametrize("periodic", [True, False])
+def test_ground_state_is_stationary(periodic):
+    """The self-consistent ground state does not evolve without a field: ten predictor-corrector steps
+    leave the density unchanged to 1e-8 (the SCF stops at a potential misfit of 1e-10; a random
+    orthonormal start moves the density at order 1)."""
+    s = W.tiny(periodic=periodic, n=(6, 6, 6), natom=1, nk=1, norb=2)
+    s.field = W.Field("none")
+    psi, eig, v, it = O.ground_state(s)
+    assert it < 400
+    tabs = O.projector_tables(s)
+    Vloc = O.local_potential(s)
+    rho0 = O.density(s, psi)
+    p, vh = psi.copy(), v
+    for _ in range(10):
+        p, vh, rho = O.pc_step(s, tabs, Vloc, p, vh, 0.0, 0.02)
+    assert np.max(np.abs(rho - rho0)) < 1e-8 * rho0.max()
+    q = W.initial_orbitals(s, 1)
+    p, vh = q.copy(), O.hxc(s, O.density(s, q))
+    for _ in range(10):
+        p, vh, rho = O.pc_step(s, tabs, Vloc, p, vh, 0.0, 0.02)
+    assert np.max(np.abs(rho - O.density(s, q))) > 1e-3 * O.density(s, q).max()
+
+
+def test_ground_state_is_an_energy_minimum():
+    """The total energy at the ground state rises quadratically under orthonormality-preserving
+    perturbations of the orbitals (eps and eps/2: ratio ~4), and the occupied eigenvalues lie below
+    the unoccupied ones."""
+    s = W.tiny(periodic=True, n=(6, 6, 6), natom=1, nk=1, norb=2)
+    s.field = W.Field("none")
+    psi, eig, v, _ = O.ground_state(s)
+    tabs = O.projector_tables(s)
+    Vloc = O.local_potential(s)
+    E0 = O.total_energy(s, tabs, Vloc, psi, np.zeros(3))
+    rng = np.random.default_rng(0)
+    d = rng.standard_normal(psi.shape) + 1j * rng.standard_normal(psi.shape)
+    rise = [O.total_energy(s, tabs, Vloc, _loewdin(psi + e * d, s.dV), np.zeros(3)) - E0 for e in (1e-2, 5e-3)]
+    assert rise[0] > 0 and rise[1] > 0 and 3.5 < rise[0] / rise[1] < 4.5, rise
+    full = np.linalg.eigvalsh(O.dense_hamiltonian(s, tabs, Vloc + v, np.asarray(s.kpts[0], np.float64)))
+    assert np.allclose(full[:2], eig[0], atol=1e-8)
