@@ -142,6 +142,25 @@ tdks_status tdks_add_pulse(tdks_ctx* ctx, const double A0[3], double omega, doub
  * nt outside 1..2^26, dt_table <= 0 or a non-finite value. */
 tdks_status tdks_set_field_table(tdks_ctx* ctx, const double* Ap, int nt, double t0, double dt_table);
 
+/* Ground state (the static Kohn-Sham problem solved before the time evolution; the paper's ground-
+ * state step uses Gram-Schmidt orthonormalisation): the lowest norb states of every k-point at A' = 0,
+ * self-consistent in V_Hxc, for the context's synthetic pseudo-atoms.  Each iteration takes an
+ * imaginary-time (steepest-descent) step in the subspace, orthonormalises by Cholesky (the
+ * Gram-Schmidt of the set) and mixes the potential linearly:
+ *   M = U^H H U dV,  W = U - tau (H U - U M),  U = W L^{-H} with W^H W dV = L L^H,
+ *   V_in <- V_in + mix (V_Hxc[rho(U)] - V_in).
+ * It stops when the subspace residual sqrt(sum ||H U - U M||^2 / (nk norb)) and the potential misfit
+ * ||V_Hxc[rho] - V_in|| / ||V_Hxc[rho]|| (checked every 10 iterations) are both below tol, or after
+ * max_iter.  u: caller's orbitals [nk][norb][nz][ny][nx] (the start; overwritten by an orthonormal
+ * basis of the occupied subspace -- the density and current depend on nothing else).  Afterwards
+ * V_Hxc(t) and rho0 are those of the ground state.  tau <= 0 picks 1 / (3.25 sum_a h_a^-2 + 4), below
+ * the stability bound of the step.  out[3] (nullable): iterations, final residual, band energy
+ * sum_k w_k sum_n 2 M_nn.  Synchronises every iteration (the small Cholesky runs on the host).
+ * Errors: EUNSUPPORTED for ncell > 1 or norb > 64; EINVAL for bad arguments or linearly dependent
+ * orbitals; ENOMEM. */
+tdks_status tdks_ground_state(tdks_ctx* ctx, void* u, int max_iter, double tol, double tau, double mix,
+                              double* out);
+
 /* Longitudinal geometry (Sec. 4.1: in a thin film the vector potential is the external one plus the
  * one induced by the surface polarisation): A'(t) = A'_ext(t) + A'_ind(t) with
  * d^2 A'_ind / dt^2 = 4 pi J(t) (Gaussian units: E_ind = -4 pi P, dP/dt = J, E = -(1/c) dA/dt).  Each

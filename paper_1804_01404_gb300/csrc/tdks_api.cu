@@ -843,6 +843,173 @@ tdks_status tdks_field_at(tdks_ctx* c, double t, double Ap[3], double E[3]) {
   return TDKS_OK;
 }
 
+namespace {
+// Cholesky S = L L^H of a Hermitian positive definite n x n matrix (row-major, double2) and
+// C = L^{-H} (upper triangular), so that the combinations W C of vectors with overlap S are
+// orthonormal (C^H S C = I).  False if S is not positive definite.
+bool cholesky_inverse_h(const double2* S, int n, double2* Cout) {
+  std::vector<double> Lr((size_t)n * n, 0.0), Li((size_t)n * n, 0.0), Xr((size_t)n * n, 0.0), Xi((size_t)n * n, 0.0);
+  for (int j = 0; j < n; ++j) {
+    double d = S[j * n + j].x;
+    for (int k = 0; k < j; ++k) d -= Lr[j * n + k] * Lr[j * n + k] + Li[j * n + k] * Li[j * n + k];
+    if (!(d > 0.0)) return false;
+    const double ljj = std::sqrt(d);
+    Lr[j * n + j] = ljj;
+    for (int i = j + 1; i < n; ++i) {
+      double re = S[i * n + j].x, im = S[i * n + j].y;
+      for (int k = 0; k < j; ++k) {   // - L_ik conj(L_jk)
+        re -= Lr[i * n + k] * Lr[j * n + k] + Li[i * n + k] * Li[j * n + k];
+        im -= Li[i * n + k] * Lr[j * n + k] - Lr[i * n + k] * Li[j * n + k];
+      }
+      Lr[i * n + j] = re / ljj;
+      Li[i * n + j] = im / ljj;
+    }
+  }
+  for (int j = 0; j < n; ++j) {          // X = L^{-1} by forward substitution, column by column
+    Xr[j * n + j] = 1.0 / Lr[j * n + j];
+    for (int i = j + 1; i < n; ++i) {
+      double re = 0.0, im = 0.0;
+      for (int k = j; k < i; ++k) {
+        re += Lr[i * n + k] * Xr[k * n + j] - Li[i * n + k] * Xi[k * n + j];
+        im += Lr[i * n + k] * Xi[k * n + j] + Li[i * n + k] * Xr[k * n + j];
+      }
+      Xr[i * n + j] = -re / Lr[i * n + i];
+      Xi[i * n + j] = -im / Lr[i * n + i];
+    }
+  }
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) Cout[i * n + j] = double2{Xr[j * n + i], -Xi[j * n + i]};   // C = X^H
+  return true;
+}
+}  // namespace
+
+tdks_status tdks_ground_state(tdks_ctx* c, void* u, int max_iter, double tol, double tau, double mix, double* out) {
+  TDKS_TRY(check_ctx(c));
+  if (!u) return fail(TDKS_EINVAL, "null orbitals");
+  if (c->ncell != 1) return fail(TDKS_EUNSUPPORTED, "tdks_ground_state needs ncell = 1");
+  if (c->norb > 64) return fail(TDKS_EUNSUPPORTED, "tdks_ground_state handles at most 64 orbitals per k-point");
+  if (max_iter < 1 || !(tol > 0.0) || !(mix > 0.0 && mix <= 1.0) || !std::isfinite(tau))
+    return fail(TDKS_EINVAL, "need max_iter >= 1, tol > 0, 0 < mix <= 1 and a finite tau");
+  if (tau <= 0.0) {   // below 2 / (largest eigenvalue): the FD kinetic symbol is at most 3.25 sum 1/h^2
+    double s = 0.0;
+    for (int a = 0; a < 3; ++a) s += 1.0 / (c->grid.h[a] * c->grid.h[a]);
+    tau = 1.0 / (3.25 * s + 4.0);
+  }
+  const int nk = c->nk, no = c->norb, np = c->npts;
+  const bool f32 = is_f32(c);
+  const size_t csz = f32 ? sizeof(float2) : sizeof(double2);
+  const size_t nob = (size_t)nk * no * np * csz, nmat = (size_t)nk * no * no;
+  void *HU = nullptr, *Wb = nullptr;
+  double2 *dM = nullptr, *dS = nullptr, *dC = nullptr;
+  double* d_vin = nullptr;
+  std::vector<double2> hM(nmat), hS(nmat), hC(nmat);
+  std::vector<double> hv((size_t)np), hvin((size_t)np);
+  cudaError_t e = cudaSuccess;
+  auto chk = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+  chk(cudaMalloc(&HU, nob));
+  chk(cudaMalloc(&Wb, nob));
+  chk(cudaMalloc(&dM, nmat * sizeof(double2)));
+  chk(cudaMalloc(&dS, nmat * sizeof(double2)));
+  chk(cudaMalloc(&dC, nmat * sizeof(double2)));
+  chk(cudaMalloc(&d_vin, (size_t)np * sizeof(double)));
+  auto cleanup = [&]() {
+    cudaStreamSynchronize(c->stream);
+    cudaFree(HU); cudaFree(Wb); cudaFree(dM); cudaFree(dS); cudaFree(dC); cudaFree(d_vin);
+  };
+  if (e != cudaSuccess) { cleanup(); return fail(TDKS_ENOMEM, "tdks_ground_state: device memory"); }
+  auto gram = [&](const void* A, const void* B, double2* o) {
+    return f32 ? launch_gram<float>((const float2*)A, (const float2*)B, nk, no, np, c->dV, o, c->stream)
+               : launch_gram<double>((const double2*)A, (const double2*)B, nk, no, np, c->dV, o, c->stream);
+  };
+  auto basis = [&](const void* U, const void* V, const double2* M, double a, double c0, double b, void* o) {
+    return f32 ? launch_basis<float>((const float2*)U, (const float2*)V, M, nk, no, np, a, c0, b, (float2*)o, c->stream)
+               : launch_basis<double>((const double2*)U, (const double2*)V, M, nk, no, np, a, c0, b, (double2*)o,
+                                      c->stream);
+  };
+  // dst = src C with C = L^{-H} of the overlap of src: an orthonormal basis of the same subspace
+  auto ortho = [&](const void* src, void* dst) -> tdks_status {
+    TDKS_CUDA(gram(src, src, dS));
+    TDKS_CUDA(cudaMemcpyAsync(hS.data(), dS, nmat * sizeof(double2), cudaMemcpyDeviceToHost, c->stream));
+    TDKS_CUDA(cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < nk; ++k)
+      if (!cholesky_inverse_h(&hS[(size_t)k * no * no], no, &hC[(size_t)k * no * no]))
+        return fail(TDKS_EINVAL, "tdks_ground_state: the orbitals are linearly dependent");
+    TDKS_CUDA(cudaMemcpyAsync(dC, hC.data(), nmat * sizeof(double2), cudaMemcpyHostToDevice, c->stream));
+    TDKS_CUDA(basis(src, nullptr, dC, 0.0, 0.0, 1.0, dst));
+    c->launches += 3;
+    return TDKS_OK;
+  };
+  auto run = [&]() -> tdks_status {
+    const double zeroA[3] = {0.0, 0.0, 0.0};
+    TDKS_TRY(ortho(u, Wb));
+    TDKS_CUDA(cudaMemcpyAsync(u, Wb, nob, cudaMemcpyDeviceToDevice, c->stream));
+    TDKS_TRY(density(c, u, c->d_rho));
+    TDKS_TRY(hxc(c, c->d_rho, c->d_vhxc));
+    TDKS_CUDA(cudaMemcpyAsync(d_vin, c->d_vhxc, (size_t)np * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    double resid = 0.0;
+    int it = 0;
+    for (it = 1; it <= max_iter; ++it) {
+      TDKS_TRY(set_step_potential(c, 1.0, nullptr, 0.0));
+      TDKS_TRY(orbital_kernel(c, 0, u, HU, zeroA, 0.0, nullptr, 1));            // H U
+      TDKS_CUDA(gram(u, HU, dM));                                               // M = U^H H U dV
+      TDKS_CUDA(basis(u, HU, dM, -tau, 1.0, tau, Wb));                          // W = U - tau (HU - U M)
+      const bool check = (it % 10 == 0) || it == max_iter;
+      if (check) {                                                              // R = HU - U M (in place)
+        TDKS_CUDA(basis(u, HU, dM, 1.0, 0.0, -1.0, HU));
+        TDKS_CUDA(gram(HU, HU, dS));
+        TDKS_CUDA(cudaMemcpyAsync(hS.data(), dS, nmat * sizeof(double2), cudaMemcpyDeviceToHost, c->stream));
+        TDKS_CUDA(cudaMemcpyAsync(hM.data(), dM, nmat * sizeof(double2), cudaMemcpyDeviceToHost, c->stream));
+      }
+      c->launches += check ? 5 : 3;
+      if (check) {
+        TDKS_CUDA(cudaStreamSynchronize(c->stream));
+        double r2 = 0.0;
+        for (int k = 0; k < nk; ++k)
+          for (int n = 0; n < no; ++n) r2 += hS[((size_t)k * no + n) * no + n].x;
+        resid = std::sqrt(r2 / (nk * no));
+      }
+      TDKS_TRY(ortho(Wb, u));                                                   // U = W L^{-H}
+      TDKS_TRY(density(c, u, c->d_rho));
+      TDKS_TRY(hxc(c, c->d_rho, c->d_vhxc));                                     // V_out
+      double dv = 0.0;
+      if (check) {
+        TDKS_CUDA(cudaMemcpyAsync(hv.data(), c->d_vhxc, (size_t)np * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        TDKS_CUDA(cudaMemcpyAsync(hvin.data(), d_vin, (size_t)np * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        TDKS_CUDA(cudaStreamSynchronize(c->stream));
+        double a2 = 0.0, b2 = 0.0;
+        for (int i = 0; i < np; ++i) { a2 += (hv[i] - hvin[i]) * (hv[i] - hvin[i]); b2 += hv[i] * hv[i]; }
+        dv = std::sqrt(a2 / std::max(b2, 1e-300));
+      }
+      TDKS_CUDA(launch_mix_potential(d_vin, c->d_vhxc, np, mix, c->stream));
+      c->launches += 1;
+      if (check && resid < tol && dv < tol) break;
+    }
+    // the ground state's own potential and reference density
+    TDKS_TRY(density(c, u, c->d_rho));
+    TDKS_TRY(hxc(c, c->d_rho, c->d_vhxc));
+    TDKS_CUDA(cudaMemcpyAsync(c->d_rho0, c->d_rho, (size_t)np * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    c->have_rho0 = true;
+    c->have_potential = true;
+    c->hist_count = 0;
+    TDKS_TRY(hist_push(c, c->d_vhxc));
+    if (out) {
+      std::vector<double> kw((size_t)nk);
+      TDKS_CUDA(cudaMemcpyAsync(kw.data(), c->d_kw, nk * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      TDKS_CUDA(cudaStreamSynchronize(c->stream));
+      double eb = 0.0;
+      for (int k = 0; k < nk; ++k)
+        for (int n = 0; n < no; ++n) eb += 2.0 * kw[k] * hM[((size_t)k * no + n) * no + n].x;
+      out[0] = std::min(it, max_iter);
+      out[1] = resid;
+      out[2] = eb;
+    }
+    return TDKS_OK;
+  };
+  const tdks_status st = run();
+  cleanup();
+  return st;
+}
+
 tdks_status tdks_set_longitudinal(tdks_ctx* c, int enable, const void* u, double t0) {
   TDKS_TRY(check_ctx(c));
   if (enable != 0 && enable != 1) return fail(TDKS_EINVAL, "enable must be 0 or 1");

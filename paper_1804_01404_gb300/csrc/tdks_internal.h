@@ -263,6 +263,17 @@ cudaError_t launch_reduce_current(const double* orb_obs, int nk, int norb, const
                                   double inv_omega, int periodic, double* out, cudaStream_t s,
                                   int ncell = 1);
 // 1D Maxwell leapfrog (Eq. Maxwell_ms) with Mur boundaries; A'(X) of the cells at t+dt/2 and t+dt
+// Ground-state subspace kernels (k_scf.cu): out[k][i][j] = dV sum conj(A_i) B_j;
+// out[k][j] = a V_j + c0 U_j + b sum_i U_i M[k][i][j]; vin <- vout <- vin + mix (vout - vin).
+template <typename T>
+cudaError_t launch_gram(const typename Cplx<T>::type* A, const typename Cplx<T>::type* B, int nk, int norb, int npts,
+                        double dV, double2* out, cudaStream_t s);
+template <typename T>
+cudaError_t launch_basis(const typename Cplx<T>::type* U, const typename Cplx<T>::type* V, const double2* M, int nk,
+                         int norb, int npts, double a, double c0, double b, typename Cplx<T>::type* out,
+                         cudaStream_t s);
+cudaError_t launch_mix_potential(double* vin, double* vout, long long n, double mix, cudaStream_t s);
+
 // longitudinal geometry: one leapfrog step of A'_ind from J(t_n) = step_obs[0..2] (see k_grid.cu)
 cudaError_t launch_longitudinal(const double* step_obs, double* lg, int first, double dt, const double ext_mid[3],
                                 const double ext_end[3], double* ap_mid, double* ap_end, cudaStream_t s);

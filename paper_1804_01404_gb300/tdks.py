@@ -127,6 +127,7 @@ def load_library(path: str = LIB_PATH):
         "tdks_work": [C.POINTER(C.c_double), C.POINTER(C.c_double), i, d, C.POINTER(C.c_double), vp],
         "tdks_field_at": [vp, d, C.POINTER(C.c_double), C.POINTER(C.c_double)],
         "tdks_set_longitudinal": [vp, i, vp, d],
+        "tdks_ground_state": [vp, vp, i, d, d, d, C.POINTER(C.c_double)],
         "tdks_longitudinal_read": [vp, C.POINTER(C.c_double)],
         "tdks_get_state": [vp, vp, C.c_size_t],
         "tdks_set_state": [vp, vp, C.c_size_t],
@@ -283,6 +284,14 @@ class Context:
         tab = np.ascontiguousarray(table, np.float64).reshape(-1, 3)
         _check(self.lib.tdks_set_field_table(self.ctx, tab.ctypes.data_as(C.POINTER(C.c_double)), len(tab),
                                              float(t0), float(dt_table)))
+
+    def ground_state(self, u, max_iter=5000, tol=1e-8, tau=0.0, mix=0.3):
+        """Self-consistent ground state into u (tdks_ground_state); returns (iterations, residual,
+        band energy)."""
+        out = (C.c_double * 3)()
+        _check(self.lib.tdks_ground_state(self.ctx, _ptr(u, self.cdtype), int(max_iter), float(tol), float(tau),
+                                          float(mix), out))
+        return int(out[0]), float(out[1]), float(out[2])
 
     def set_longitudinal(self, enable, u=None, t0=0.0):
         """Longitudinal geometry on (A'_ind from d^2 A'_ind/dt^2 = 4 pi J, starting at rest with J of u

@@ -1,0 +1,64 @@
+"""Ground state on the GPU (tdks_ground_state) against the oracle's dense self-consistent solution:
+the occupied subspace (overlap with the oracle's states), the density, the band energy, and
+stationarity of the result under the GPU's own time steps."""
+import numpy as np
+import pytest
+
+from oracle import tdks_oracle as O
+from paper_1804_01404_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def _systems():
+    a = W.tiny(periodic=True, n=(6, 6, 6), natom=1, nk=1, norb=2)
+    b = W.tiny(periodic=True, n=(6, 7, 5), natom=2, nk=2, norb=3)
+    c = W.tiny(periodic=False, n=(7, 6, 8), natom=2, norb=2)
+    for s in (a, b, c):
+        s.field = W.Field("none")
+    return {"periodic-1k": a, "periodic-2k": b, "isolated": c}
+
+
+SYSTEMS = _systems()
+
+
+@pytest.mark.parametrize("name", list(SYSTEMS))
+def test_ground_state_matches_oracle(name):
+    from paper_1804_01404_gb300.tdks import Context
+    s = SYSTEMS[name]
+    psi_ref, eig_ref, v_ref, _ = O.ground_state(s, tol=1e-11)
+    ctx = Context(s, precision="f64")
+    u = torch.from_numpy(W.initial_orbitals(s, 7)).cuda()
+    its, resid, eband = ctx.ground_state(u, max_iter=20000, tol=1e-9)
+    ctx.check()
+    assert resid < 1e-9 and its < 20000, (its, resid)
+    got = u.cpu().numpy()
+    for k in range(s.nk):          # same occupied subspace: the overlap matrix is unitary
+        Ov = (got[k].reshape(s.norb, -1).conj() @ psi_ref[k].reshape(s.norb, -1).T) * s.dV
+        assert np.max(np.abs(Ov.conj().T @ Ov - np.eye(s.norb))) < 1e-7
+    rho = ctx.grid_array(2).cpu().numpy()
+    rho_ref = O.density(s, psi_ref)
+    assert np.max(np.abs(rho - rho_ref)) < 1e-7 * rho_ref.max()
+    assert np.max(np.abs(ctx.grid_array(1).cpu().numpy() - v_ref)) < 1e-7 * np.max(np.abs(v_ref))
+    eb_ref = float(np.sum(2.0 * np.asarray(s.kw)[:, None] * eig_ref))
+    assert abs(eband - eb_ref) < 1e-7 * abs(eb_ref)
+    # stationary under the GPU's own predictor-corrector steps
+    t = 0.0
+    for _ in range(10):
+        ctx.step(u, t, s.dt)
+        t += s.dt
+    assert np.max(np.abs(ctx.grid_array(2).cpu().numpy() - rho)) < 1e-7 * rho.max()
+    ctx.close()
+
+
+def test_ground_state_argument_checks():
+    from paper_1804_01404_gb300.tdks import Context, TdksError
+    s = SYSTEMS["periodic-1k"]
+    ctx = Context(s, precision="f64")
+    u = torch.from_numpy(W.initial_orbitals(s, 1)).cuda()
+    with pytest.raises(TdksError):
+        ctx.ground_state(u, mix=1.5)
+    with pytest.raises(TdksError):
+        ctx.ground_state(torch.zeros_like(u))        # linearly dependent (zero) orbitals
+    ctx.close()
