@@ -161,6 +161,14 @@ tdks_status tdks_set_field_table(tdks_ctx* ctx, const double* Ap, int nt, double
 tdks_status tdks_ground_state(tdks_ctx* ctx, void* u, int max_iter, double tol, double tau, double mix,
                               double* out);
 
+/* Number density of excited electron-hole pairs (Sec. 4.2 example; the paper gives no formula):
+ * n_eh = (1 / Omega) sum_k w_k 2 (norb - sum_{m,n} |<phi_km|psi_kn> dV|^2), the occupied weight that has
+ * left the ground-state subspace spanned by u_gs (e.g. from tdks_ground_state; both [nk][norb][npts],
+ * device, the context's precision).  Projections on the ground-state orbitals of the same k; after the
+ * field has returned to zero this is the gauge-independent count.  Synchronises.  Isolated systems
+ * use Omega = the box volume.  Errors: EINVAL for NULL arguments; EUNSUPPORTED for ncell > 1. */
+tdks_status tdks_excited_pairs(tdks_ctx* ctx, const void* u, const void* u_gs, double* n_eh);
+
 /* Longitudinal geometry (Sec. 4.1: in a thin film the vector potential is the external one plus the
  * one induced by the surface polarisation): A'(t) = A'_ext(t) + A'_ind(t) with
  * d^2 A'_ind / dt^2 = 4 pi J(t) (Gaussian units: E_ind = -4 pi P, dP/dt = J, E = -(1/c) dA/dt).  Each

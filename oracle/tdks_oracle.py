@@ -574,6 +574,16 @@ def ground_state(s, hartree_on=True, xc_on=True, mix=0.3, tol=1e-10, max_iter=40
     return psi, eig, vout, max_iter
 
 
+def excited_pairs(s, psi, psi_gs):
+    """Number density of excited electron-hole pairs: (1/Omega) sum_k w_k 2 (norb - sum_{m,n}
+    |<phi_km|psi_kn>|^2), the occupied weight outside the ground-state subspace."""
+    n = 0.0
+    for k in range(s.nk):
+        O_ = psi_gs[k].reshape(s.norb, -1).conj() @ psi[k].reshape(s.norb, -1).T * s.dV
+        n += 2.0 * s.kw[k] * (s.norb - np.sum(np.abs(O_) ** 2))
+    return n / cell_volume(s)
+
+
 def longitudinal_run(s, psi0, nsteps, t0=0.0, hartree_on=True, xc_on=True):
     """Longitudinal geometry (Sec. 4.1, thin film): A'(t) = A'_ext(t) + A'_ind(t) with
     d^2 A'_ind/dt^2 = 4 pi J(t) (E_ind = -4 pi P, dP/dt = J, E = -dA'/dt).  Per step:

@@ -1010,6 +1010,38 @@ tdks_status tdks_ground_state(tdks_ctx* c, void* u, int max_iter, double tol, do
   return st;
 }
 
+tdks_status tdks_excited_pairs(tdks_ctx* c, const void* u, const void* u_gs, double* n_eh) {
+  TDKS_TRY(check_ctx(c));
+  if (!u || !u_gs || !n_eh) return fail(TDKS_EINVAL, "null argument");
+  if (c->ncell != 1) return fail(TDKS_EUNSUPPORTED, "tdks_excited_pairs needs ncell = 1");
+  const int nk = c->nk, no = c->norb;
+  const size_t nmat = (size_t)nk * no * no;
+  double2* dO = nullptr;
+  if (cudaMalloc(&dO, nmat * sizeof(double2)) != cudaSuccess) return fail(TDKS_ENOMEM, "tdks_excited_pairs: device memory");
+  std::vector<double2> hO(nmat);
+  std::vector<double> kw((size_t)nk);
+  cudaError_t e = is_f32(c)
+      ? launch_gram<float>((const float2*)u_gs, (const float2*)u, nk, no, c->npts, c->dV, dO, c->stream)
+      : launch_gram<double>((const double2*)u_gs, (const double2*)u, nk, no, c->npts, c->dV, dO, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hO.data(), dO, nmat * sizeof(double2), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(kw.data(), c->d_kw, nk * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  cudaFree(dO);
+  if (e != cudaSuccess) return fail(TDKS_ECUDA, std::string("tdks_excited_pairs: ") + cudaGetErrorString(e));
+  c->launches += 1;
+  double n = 0.0;
+  for (int k = 0; k < nk; ++k) {
+    double f2 = 0.0;     // sum_{m,n} |<phi_m|psi_n>|^2: the occupied weight kept in the ground-state subspace
+    for (size_t i = 0; i < (size_t)no * no; ++i) {
+      const double2 o = hO[(size_t)k * no * no + i];
+      f2 += o.x * o.x + o.y * o.y;
+    }
+    n += 2.0 * kw[k] * (no - f2);
+  }
+  *n_eh = n / c->omega;
+  return TDKS_OK;
+}
+
 tdks_status tdks_set_longitudinal(tdks_ctx* c, int enable, const void* u, double t0) {
   TDKS_TRY(check_ctx(c));
   if (enable != 0 && enable != 1) return fail(TDKS_EINVAL, "enable must be 0 or 1");

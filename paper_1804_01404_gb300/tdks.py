@@ -128,6 +128,7 @@ def load_library(path: str = LIB_PATH):
         "tdks_field_at": [vp, d, C.POINTER(C.c_double), C.POINTER(C.c_double)],
         "tdks_set_longitudinal": [vp, i, vp, d],
         "tdks_ground_state": [vp, vp, i, d, d, d, C.POINTER(C.c_double)],
+        "tdks_excited_pairs": [vp, vp, vp, C.POINTER(C.c_double)],
         "tdks_longitudinal_read": [vp, C.POINTER(C.c_double)],
         "tdks_get_state": [vp, vp, C.c_size_t],
         "tdks_set_state": [vp, vp, C.c_size_t],
@@ -292,6 +293,13 @@ class Context:
         _check(self.lib.tdks_ground_state(self.ctx, _ptr(u, self.cdtype), int(max_iter), float(tol), float(tau),
                                           float(mix), out))
         return int(out[0]), float(out[1]), float(out[2])
+
+    def excited_pairs(self, u, u_gs):
+        """Number density of excited electron-hole pairs of u relative to the ground-state orbitals u_gs
+        (tdks_excited_pairs)."""
+        n = C.c_double()
+        _check(self.lib.tdks_excited_pairs(self.ctx, _ptr(u, self.cdtype), _ptr(u_gs, self.cdtype), C.byref(n)))
+        return n.value
 
     def set_longitudinal(self, enable, u=None, t0=0.0):
         """Longitudinal geometry on (A'_ind from d^2 A'_ind/dt^2 = 4 pi J, starting at rest with J of u

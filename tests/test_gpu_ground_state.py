@@ -62,3 +62,25 @@ def test_ground_state_argument_checks():
     with pytest.raises(TdksError):
         ctx.ground_state(torch.zeros_like(u))        # linearly dependent (zero) orbitals
     ctx.close()
+
+
+def test_excited_pairs_after_a_pulse():
+    """From the GPU ground state, a pulse excites electron-hole pairs: tdks_excited_pairs against the
+    oracle's count on the same orbitals, zero before the pulse, positive after it."""
+    from paper_1804_01404_gb300.tdks import Context, FIELD_PULSE
+    s = SYSTEMS["periodic-2k"]
+    ctx = Context(s, precision="f64")
+    u = torch.from_numpy(W.initial_orbitals(s, 7)).cuda()
+    ctx.ground_state(u, max_iter=20000, tol=1e-9)
+    u_gs = u.clone()
+    assert abs(ctx.excited_pairs(u, u_gs)) < 1e-12
+    ctx.set_field(FIELD_PULSE, (0.0, 0.0, 0.2), 0.8, 3.0, 0.0)
+    t = 0.0
+    for _ in range(200):
+        ctx.step(u, t, s.dt)
+        t += s.dt
+    ctx.check()
+    n = ctx.excited_pairs(u, u_gs)
+    ref = O.excited_pairs(s, u.cpu().numpy(), u_gs.cpu().numpy())
+    assert abs(n - ref) < 1e-10 * abs(ref) and ref > 1e-8, (n, ref)
+    ctx.close()

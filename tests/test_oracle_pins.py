@@ -749,3 +749,24 @@ def test_ground_state_is_an_energy_minimum():
     assert rise[0] > 0 and rise[1] > 0 and 3.5 < rise[0] / rise[1] < 4.5, rise
     full = np.linalg.eigvalsh(O.dense_hamiltonian(s, tabs, Vloc + v, np.asarray(s.kpts[0], np.float64)))
     assert np.allclose(full[:2], eig[0], atol=1e-8)
+
+
+def test_excited_pairs_closed_form():
+    """Orbitals rotated by theta out of the ground-state subspace towards unoccupied eigenvectors:
+    n_eh = (1/Omega) sum_k w_k 2 sum_n sin^2(theta_n); a rotation inside the subspace counts 0."""
+    s = W.tiny(periodic=True, n=(6, 6, 6), natom=1, nk=1, norb=2)
+    s.field = W.Field("none")
+    psi, eig, v, _ = O.ground_state(s)
+    tabs = O.projector_tables(s)
+    E, U = np.linalg.eigh(O.dense_hamiltonian(s, tabs, O.local_potential(s) + v, np.asarray(s.kpts[0], np.float64)))
+    chi = (U[:, 2:4].T / math.sqrt(s.dV)).reshape((2,) + psi.shape[2:])     # two unoccupied states
+    th = np.array([0.3, 0.7])
+    rot = psi.copy()
+    for n in range(2):
+        rot[0, n] = np.cos(th[n]) * psi[0, n] + np.sin(th[n]) * chi[n]
+    ref = 2.0 * np.sum(np.sin(th) ** 2) / O.cell_volume(s)
+    assert abs(O.excited_pairs(s, rot, psi) - ref) < 1e-12 * ref
+    mixed = psi.copy()
+    c, sn = np.cos(0.4), np.sin(0.4)
+    mixed[0, 0], mixed[0, 1] = c * psi[0, 0] + sn * psi[0, 1], -sn * psi[0, 0] + c * psi[0, 1]
+    assert abs(O.excited_pairs(s, mixed, psi)) < 1e-12
