@@ -481,7 +481,11 @@ def hpsi_cluster(dev, reps=10, norb=256):
     res["update_potential_hartree_xc_ms"] = sx["ms"]["hartree_xc"] / max(1, sx["calls"]["hartree_xc"])
     variant, tune_ms = ctx.tile_variant()
     names = ["k_tile<float> (1 point/thread, 3 CTAs/SM)", "k_tile<float> (1 point/thread, 2 CTAs/SM) + L2 prefetch",
-             "k_tile4<8> (2x2 points/thread, 8 consumer warps) + L2 prefetch"]
+             "k_tile4<8> (2x2 points/thread, 8 consumer warps) + L2 prefetch",
+             "k_tile4<8, 1 row> (2x1 points/thread, 2 CTAs/SM) + L2 prefetch",
+             "k_tile4<4, 1 row> (2x1 points/thread, 4 CTAs/SM) + L2 prefetch",
+             "k_tile4<8, 1 row, TMA-staged V/psi> (2x1 points/thread, 2 CTAs/SM)",
+             "k_tile4<4, 1 row, TMA-staged V/psi> (2x1 points/thread, 4 CTAs/SM)"]
     res["stencil_variant"] = {"hpsi": names[variant[0]], "horner_stage": names[variant[1]]}
     # the tuner's timings of the stencil kernel alone (no projectors), 2 launches each at init:
     # H v moves 16 B per orbital-point, a Horner stage 24 B (reads v and psi, writes the result)

@@ -323,12 +323,16 @@ tdks_status tdks_query(const tdks_ctx* ctx, int* npts, int* nk, int* norb, int* 
  * and keeps the fastest for each of the two.
  * Variants (FP32): 0 = one grid point per thread, registers capped for 3 CTAs per SM, no L2 prefetch;
  * 1 = one point per thread, 2 CTAs per SM, TMA L2 prefetch of the planes 8 ahead; 2 = 2 x 2 points
- * per thread, 8 consumer warps, prefetch 8.  FP64: 0 and 1 (one CTA per SM, without / with prefetch).
- *   set       : -1 leaves the choice as it is; 0..2 forces that variant for both uses.
+ * per thread, 8 consumer warps, prefetch 8; 3 = 2 x 1 points per thread (one row), 8 consumer warps,
+ * 2 CTAs per SM, prefetch 8; 4 = the same with 4 consumer warps and 4 CTAs per SM; 5, 6 = 3, 4 with
+ * the potential (and for a Horner stage psi) of each plane delivered by TMA next to the orbital
+ * plane instead of loaded per thread (grids with nx divisible by 4).  FP64: 0 and 1 (one CTA per SM,
+ * without / with prefetch).
+ *   set       : -1 leaves the choice as it is; 0..6 forces that variant for both uses.
  *   variant   : receives the variants in use [H v, Horner stage] (may be NULL).
- *   tune_ms   : receives the 6 tuning times in ms [use][variant], -1 where not timed (may be NULL).
- * Errors: EUNSUPPORTED if the context does not use the tile kernels or the variant needs FP32;
- * EINVAL for set outside -1..2. */
+ *   tune_ms   : receives the 14 tuning times in ms [use][variant], -1 where not timed (may be NULL).
+ * Errors: EUNSUPPORTED if the context does not use the tile kernels or the variant does not apply
+ * (FP32 only; nx % 4 for 5 and 6); EINVAL for set outside -1..6. */
 tdks_status tdks_tile_variant(tdks_ctx* ctx, int set, int* variant, float* tune_ms);
 
 /* Buffer scheme of the shared-memory cell kernels for the Taylor propagator (Eq. taylor, Horner

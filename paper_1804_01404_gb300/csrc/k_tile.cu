@@ -20,6 +20,7 @@
 #include <cudaTypedefs.h>
 
 #include "tdks_internal.h"
+#include "warp_sum.cuh"
 
 namespace tdks {
 
@@ -79,6 +80,15 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                            unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2),
+        "r"(smem_u32(bar))
+      : "memory");
+}
+
 // L2 prefetch of one box of a tensor map (no shared memory, no completion to wait for).
 __device__ __forceinline__ void tma_prefetch_4d(const CUtensorMap* map, int c0, int c1, int c2, int c3) {
   asm volatile("cp.async.bulk.prefetch.tensor.4d.L2.global.tile [%0, {%1, %2, %3, %4}];"
@@ -97,12 +107,19 @@ __device__ __forceinline__ void tma_prefetch_4d(const CUtensorMap* map, int c0, 
 // limit: polls per wait (the drain at the end always uses the full kSpinLimit, so copies in flight
 // land before the CTA exits).  stop_after >= 0 issues only that many planes (the timeout test: the
 // consumers then wait for a plane that never comes and must give up).
+// Side planes (optional): with smap, slot j also receives the interior box of the potential (a 3D
+// map of floats) at plane j - 4, the plane whose stencil uses slot j as its centre, into sring; with
+// qmap, the interior box of the Horner base psi at the same plane into qring.  Both complete on the
+// slot's "full" barrier, so the stencil warps read V and psi from shared memory.
 template <typename C, int NSx, int SXx, int SYx>
 __device__ __forceinline__ void tile_producer(const CUtensorMap* map, const CUtensorMap* pmap, int pf,
                                               C* ring, unsigned long long* full,
                                               unsigned long long* empty, int* abort_flag, int* err,
                                               int x0, int y0, int orb, int nplanes, long long limit,
-                                              int stop_after) {
+                                              int stop_after, const CUtensorMap* smap = nullptr,
+                                              float* sring = nullptr, unsigned sbytes = 0,
+                                              const CUtensorMap* qmap = nullptr, C* qring = nullptr,
+                                              unsigned qbytes = 0) {
   constexpr int E = sizeof(C) / 8;
   constexpr unsigned kSlotBytes = SXx * SYx * sizeof(C);
   const int nz = nplanes - 8;
@@ -119,8 +136,10 @@ __device__ __forceinline__ void tile_producer(const CUtensorMap* map, const CUte
       const int zq = j + pf - NSx - 4;             // psi plane the consumers reach ~pf planes later
       if (pmap && zq >= 0 && zq < nz) tma_prefetch_4d(pmap, E * x0, y0, zq, orb);
     }
-    mbar_expect_tx(&full[slot], kSlotBytes);
+    mbar_expect_tx(&full[slot], kSlotBytes + (smap ? sbytes : 0u) + (qmap ? qbytes : 0u));
     tma_load_4d(ring + slot * SXx * SYx, map, E * (x0 - 4), y0 - 4, j - 4, orb, &full[slot]);
+    if (smap) tma_load_3d(sring + slot * (sbytes / sizeof(float)), smap, x0, y0, j - 4, &full[slot]);
+    if (qmap) tma_load_4d(qring + slot * (qbytes / sizeof(C)), qmap, E * x0, y0, j - 4, orb, &full[slot]);
     issued = j + 1;
   }
   if (!ok) {
@@ -285,12 +304,15 @@ __global__ void __launch_bounds__(NT, MINB) k_tile(const __grid_constant__ CUten
 // point and the instruction count roughly halves.  A warp covers 16 column pairs x 2 row pairs of
 // a 32 x (4 NCW) tile.  The z loop is unrolled by the window length 9, so the register window
 // rotates by renaming instead of moving values.
-template <int NCW>
+// ROWS = 1: the same with one row per thread (2 x 1 points, 104 B of shared memory per point and
+// about half the registers), a 32 x (2 NCW) tile.
+template <int NCW, int ROWS = 2>
 struct B4 {
-  static constexpr int TX = 32, TY = 4 * NCW, NS = 8;
+  static constexpr int TX = 32, TY = 2 * ROWS * NCW, NS = 8;
   static constexpr int SX = TX + 8, SY = TY + 8;
   static constexpr int NT = (NCW + 1) * 32;
-  static constexpr int MINB = NCW == 4 ? 2 : 1;   // resident CTAs per SM the register budget allows
+  // resident CTAs per SM the register budget allows
+  static constexpr int MINB = ROWS == 1 ? (NCW == 4 ? 4 : 2) : (NCW == 4 ? 2 : 1);
 };
 
 __device__ __forceinline__ float4 lds4(const float2* p) { return *reinterpret_cast<const float4*>(p); }
@@ -301,14 +323,19 @@ __device__ __forceinline__ float2 fma2s(float s, float2 a, float2 acc) {
   return __ffma2_rn(make_float2(s, s), a, acc);
 }
 
-template <int MODE, int NCW>
-__global__ void __launch_bounds__(B4<NCW>::NT, B4<NCW>::MINB) k_tile4(const __grid_constant__ CUtensorMap vmap,
-                                                      const __grid_constant__ CUtensorMap pmap,
-                                                      TileArgs<float> a) {
-  using G = B4<NCW>;
+// SV: the potential (and, for a Horner stage, psi) of each plane arrive by TMA beside the orbital
+// plane (side rings after the orbital ring) instead of as per-thread global loads.
+template <int MODE, int NCW, int ROWS = 2, bool SV = false>
+__global__ void __launch_bounds__(B4<NCW, ROWS>::NT, B4<NCW, ROWS>::MINB)
+    k_tile4(const __grid_constant__ CUtensorMap vmap, const __grid_constant__ CUtensorMap pmap,
+            const __grid_constant__ CUtensorMap potmap, TileArgs<float> a) {
+  using G = B4<NCW, ROWS>;
+  static_assert(ROWS == 1 || ROWS == 2, "one or two rows per thread");
   constexpr int TX = G::TX, TY = G::TY, NS = G::NS, SX = G::SX, SY = G::SY, SS = SX * SY;
   extern __shared__ unsigned char smem_raw[];
   float2* ring = reinterpret_cast<float2*>((reinterpret_cast<size_t>(smem_raw) + 127) & ~size_t(127));
+  float* sring = reinterpret_cast<float*>(ring + NS * SS);        // [NS][TY][TX] potential
+  float2* qring = reinterpret_cast<float2*>(sring + NS * TX * TY);  // [NS][TY][TX] psi (MODE 1)
   __shared__ __align__(8) unsigned long long full[NS], empty[NS];
   __shared__ int s_abort;
 
@@ -327,17 +354,22 @@ __global__ void __launch_bounds__(B4<NCW>::NT, B4<NCW>::MINB) k_tile4(const __gr
   }
   __syncthreads();
   if (warp == NCW) {
-    if (lane == 0)
+    if (lane == 0 && SV)
+      tile_producer<float2, NS, SX, SY>(&vmap, nullptr, a.prefetch, ring, full, empty, &s_abort, a.err, x0, y0,
+                                        orb, nz + 8, a.wait_limit, a.stop_after, &potmap, sring,
+                                        TX * TY * sizeof(float), MODE == 1 ? &pmap : nullptr, qring,
+                                        TX * TY * sizeof(float2));
+    else if (lane == 0)
       tile_producer<float2, NS, SX, SY>(&vmap, MODE == 1 ? &pmap : nullptr, a.prefetch, ring, full, empty,
                                         &s_abort, a.err, x0, y0, orb, nz + 8, a.wait_limit, a.stop_after);
     return;
   }
 
   const int lx = 2 * (lane & 15);                  // tile column of the pair (even)
-  const int ly = 4 * warp + 2 * (lane >> 4);       // first of the two tile rows
+  const int ly = 2 * ROWS * warp + ROWS * (lane >> 4);   // first of the thread's tile rows
   const int x = x0 + lx, y = y0 + ly;
   // nx is even, so both columns of a pair are inside together
-  const bool in0 = (x < a.nx) && (y < a.ny), in1 = (x < a.nx) && (y + 1 < a.ny);
+  const bool in0 = (x < a.nx) && (y < a.ny), in1 = ROWS == 2 && (x < a.nx) && (y + 1 < a.ny);
   const int o0 = (ly + 4) * SX + (lx + 4);         // slot offset of the row-0 pair (16-byte aligned)
   const int o1 = o0 + SX;
   const size_t plane = (size_t)a.nx * a.ny;
@@ -349,8 +381,12 @@ __global__ void __launch_bounds__(B4<NCW>::NT, B4<NCW>::MINB) k_tile4(const __gr
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
     if (!timeout && !mbar_wait(&full[j % NS], (j / NS) & 1, a.wait_limit)) timeout = true;
-    const float4 p0 = lds4(ring + (j % NS) * SS + o0), p1 = lds4(ring + (j % NS) * SS + o1);
-    w0a[j] = lo(p0); w0b[j] = hi(p0); w1a[j] = lo(p1); w1b[j] = hi(p1);
+    const float4 p0 = lds4(ring + (j % NS) * SS + o0);
+    w0a[j] = lo(p0); w0b[j] = hi(p0);
+    if (ROWS == 2) {
+      const float4 p1 = lds4(ring + (j % NS) * SS + o1);
+      w1a[j] = lo(p1); w1b[j] = hi(p1);
+    }
     if (j < 4) {
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[j % NS]);
@@ -364,11 +400,11 @@ __global__ void __launch_bounds__(B4<NCW>::NT, B4<NCW>::MINB) k_tile4(const __gr
   const float diag = a.diag, coef = a.coef;
   float2 vn0 = make_float2(0.f, 0.f), vn1 = vn0;
   float4 pn0 = make_float4(0.f, 0.f, 0.f, 0.f), pn1 = pn0;
-  if (in0) {
+  if (!SV && in0) {
     vn0 = *reinterpret_cast<const float2*>(a.V + v0);
     if (MODE == 1) pn0 = *reinterpret_cast<const float4*>(a.psi + g0);
   }
-  if (in1) {
+  if (!SV && in1) {
     vn1 = *reinterpret_cast<const float2*>(a.V + v0 + a.nx);
     if (MODE == 1) pn1 = *reinterpret_cast<const float4*>(a.psi + g0 + a.nx);
   }
@@ -385,13 +421,24 @@ __global__ void __launch_bounds__(B4<NCW>::NT, B4<NCW>::MINB) k_tile4(const __gr
       if (!mbar_wait(&full[jn % NS], (jn / NS) & 1, a.wait_limit)) { timeout = true; break; }
       {
         const float2* sn = ring + (jn % NS) * SS;
-        const float4 p0 = lds4(sn + o0), p1 = lds4(sn + o1);
-        w0a[rn] = lo(p0); w0b[rn] = hi(p0); w1a[rn] = lo(p1); w1b[rn] = hi(p1);
+        const float4 p0 = lds4(sn + o0);
+        w0a[rn] = lo(p0); w0b[rn] = hi(p0);
+        if (ROWS == 2) {
+          const float4 p1 = lds4(sn + o1);
+          w1a[rn] = lo(p1); w1b[rn] = hi(p1);
+        }
       }
       const float2* sc = ring + (jc % NS) * SS;
-      const float2 V0 = vn0, V1 = vn1;
-      const float4 P0 = pn0, P1 = pn1;
-      if (z + 1 < nz) {                            // prefetch the next plane's V and psi
+      float2 V0 = vn0, V1 = vn1;
+      float4 P0 = pn0, P1 = pn1;
+      if (SV) {                                    // this plane's V and psi from the side rings
+        V0 = *reinterpret_cast<const float2*>(sring + (jc % NS) * TX * TY + ly * TX + lx);
+        if (MODE == 1) P0 = *reinterpret_cast<const float4*>(qring + (jc % NS) * TX * TY + ly * TX + lx);
+        if (ROWS == 2) {
+          V1 = *reinterpret_cast<const float2*>(sring + (jc % NS) * TX * TY + (ly + 1) * TX + lx);
+          if (MODE == 1) P1 = *reinterpret_cast<const float4*>(qring + (jc % NS) * TX * TY + (ly + 1) * TX + lx);
+        }
+      } else if (z + 1 < nz) {                     // prefetch the next plane's V and psi
         const size_t dz = (size_t)(z + 1) * plane;
         if (in0) {
           vn0 = *reinterpret_cast<const float2*>(a.V + v0 + dz);
@@ -415,13 +462,24 @@ __global__ void __launch_bounds__(B4<NCW>::NT, B4<NCW>::MINB) k_tile4(const __gr
               W[(k + 1) % 9], W[(k + 7) % 9], W[k % 9], W[(k + 8) % 9])                          \
     S = __ffma2_rn(rz, Tz, fma2s(dv, W[rc], make_float2(0.f, 0.f)));                             \
   }
-      float2 S0a, S0b, S1a, S1b;
+      float2 S0a, S0b, S1a = make_float2(0.f, 0.f), S1b = S1a;
       TDKS_ZPART(S0a, diag + V0.x, w0a)
       TDKS_ZPART(S0b, diag + V0.y, w0b)
-      TDKS_ZPART(S1a, diag + V1.x, w1a)
-      TDKS_ZPART(S1b, diag + V1.y, w1b)
+      if (ROWS == 2) {
+        TDKS_ZPART(S1a, diag + V1.x, w1a)
+        TDKS_ZPART(S1b, diag + V1.y, w1b)
+      }
       asm volatile("" ::: "memory");
-      {
+      if (ROWS == 1) {
+        // y-neighbour pairs: rows ly-1 .. ly-4 and ly+1 .. ly+4
+        const float4 Ym1 = lds4(sc + o0 - SX), Ym2 = lds4(sc + o0 - 2 * SX), Ym3 = lds4(sc + o0 - 3 * SX), Ym4 = lds4(sc + o0 - 4 * SX);
+        const float4 Yp1 = lds4(sc + o0 + SX), Yp2 = lds4(sc + o0 + 2 * SX), Yp3 = lds4(sc + o0 + 3 * SX), Yp4 = lds4(sc + o0 + 4 * SX);
+        float2 T0a = make_float2(0.f, 0.f), T0b = T0a;
+        TDKS_AXIS(T0a, lo(Ym1), lo(Yp1), lo(Ym2), lo(Yp2), lo(Ym3), lo(Yp3), lo(Ym4), lo(Yp4))
+        TDKS_AXIS(T0b, hi(Ym1), hi(Yp1), hi(Ym2), hi(Yp2), hi(Ym3), hi(Yp3), hi(Ym4), hi(Yp4))
+        S0a = __ffma2_rn(ry, T0a, S0a);
+        S0b = __ffma2_rn(ry, T0b, S0b);
+      } else {
         // y-neighbour pairs: rows ly-1 .. ly-4 and ly+2 .. ly+5
         const float4 Ym1 = lds4(sc + o0 - SX), Ym2 = lds4(sc + o0 - 2 * SX), Ym3 = lds4(sc + o0 - 3 * SX), Ym4 = lds4(sc + o0 - 4 * SX);
         const float4 Yp1 = lds4(sc + o1 + SX), Yp2 = lds4(sc + o1 + 2 * SX), Yp3 = lds4(sc + o1 + 3 * SX), Yp4 = lds4(sc + o1 + 4 * SX);
@@ -442,7 +500,7 @@ __global__ void __launch_bounds__(B4<NCW>::NT, B4<NCW>::MINB) k_tile4(const __gr
         TDKS_AXIS(S0a, hi(Am1), w0b[rc], lo(Am1), lo(Ap1), hi(Am2), hi(Ap1), lo(Am2), lo(Ap2))
         TDKS_AXIS(S0b, w0a[rc], lo(Ap1), hi(Am1), hi(Ap1), lo(Am1), lo(Ap2), hi(Am2), hi(Ap2))
       }
-      {
+      if (ROWS == 2) {
         // row 1
         const float4 Am2 = lds4(sc + o1 - 4), Am1 = lds4(sc + o1 - 2), Ap1 = lds4(sc + o1 + 2), Ap2 = lds4(sc + o1 + 4);
         TDKS_AXIS(S1a, hi(Am1), w1b[rc], lo(Am1), lo(Ap1), hi(Am2), hi(Ap1), lo(Am2), lo(Ap2))
@@ -461,10 +519,10 @@ __global__ void __launch_bounds__(B4<NCW>::NT, B4<NCW>::MINB) k_tile4(const __gr
         const float2 r1a = __ffma2_rn(mc, make_float2(S1a.y, S1a.x), lo(P1));
         const float2 r1b = __ffma2_rn(mc, make_float2(S1b.y, S1b.x), hi(P1));
         if (in0) *reinterpret_cast<float4*>(a.out + o) = make_float4(r0a.x, r0a.y, r0b.x, r0b.y);
-        if (in1) *reinterpret_cast<float4*>(a.out + o + a.nx) = make_float4(r1a.x, r1a.y, r1b.x, r1b.y);
+        if (ROWS == 2 && in1) *reinterpret_cast<float4*>(a.out + o + a.nx) = make_float4(r1a.x, r1a.y, r1b.x, r1b.y);
       } else {
         if (in0) *reinterpret_cast<float4*>(a.out + o) = make_float4(S0a.x, S0a.y, S0b.x, S0b.y);
-        if (in1) *reinterpret_cast<float4*>(a.out + o + a.nx) = make_float4(S1a.x, S1a.y, S1b.x, S1b.y);
+        if (ROWS == 2 && in1) *reinterpret_cast<float4*>(a.out + o + a.nx) = make_float4(S1a.x, S1a.y, S1b.x, S1b.y);
       }
     }
   }
@@ -508,20 +566,15 @@ __global__ void __launch_bounds__(128) k_gproject(TileArgs<T> a, const typename 
         acc[o][2 * p + 1] += b[p] * x[o].y;
       }
   }
-#pragma unroll
-  for (int o = 0; o < OW; ++o) {
-#pragma unroll
-    for (int s = 16; s > 0; s >>= 1)
-#pragma unroll
-      for (int j = 0; j < 8; ++j) acc[o][j] += __shfl_xor_sync(0xffffffffu, acc[o][j], s);
-    if (lane < 4 && ob + o < a.norb_tot) {
-      const T sc = a.atomE[at * 4 + lane] * a.dV;
-      T re = acc[o][0], im = acc[o][1];           // select projector `lane` without dynamic indexing
-#pragma unroll
-      for (int p = 1; p < 4; ++p)
-        if (lane == p) { re = acc[o][2 * p]; im = acc[o][2 * p + 1]; }
-      a.ec[((size_t)(ob + o) * a.natom + at) * 4 + lane] = C{re * sc, im * sc};
-    }
+  // all OW x 8 sums at once: lane L receives acc[L / 8][L % 8] (Re of projector p on even L, Im on
+  // the odd partner)
+  static_assert(OW * 8 == 32, "one value per lane");
+  const T tot = warp_split_sum<32>(&acc[0][0]);
+  const T im = __shfl_xor_sync(0xffffffffu, tot, 1);
+  const int o = lane >> 3, p = (lane & 7) >> 1;
+  if ((lane & 1) == 0 && ob + o < a.norb_tot) {
+    const T sc = a.atomE[at * 4 + p] * a.dV;
+    a.ec[((size_t)(ob + o) * a.natom + at) * 4 + p] = C{tot * sc, im * sc};
   }
 }
 
@@ -584,16 +637,33 @@ bool encode_map(CUtensorMap* map, const void* base, int nx, int ny, int nz, int 
   return r == CUDA_SUCCESS;
 }
 
-template <int MODE, int NCW>
+// 3D map of the FP32 potential [nz][ny][nx] with an interior box bx x by (needs nx % 4 == 0).
+bool encode_pot_map(CUtensorMap* map, const float* V, int nx, int ny, int nz, int bx, int by) {
+  auto enc = get_encode();
+  if (!enc || nx % 4 != 0) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+  const cuuint64_t strides[2] = {(cuuint64_t)4 * nx, (cuuint64_t)4 * nx * ny};
+  const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(V), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int MODE, int NCW, int ROWS, bool SV>
 cudaError_t launch_tile4(const TileArgs<float>& a, const CUtensorMap& pmap, const void* vin, cudaStream_t s) {
-  using G = B4<NCW>;
-  CUtensorMap map;
+  using G = B4<NCW, ROWS>;
+  CUtensorMap map, potmap;
+  std::memset(&potmap, 0, sizeof(potmap));
   if (!encode_map<float>(&map, vin, a.nx, a.ny, a.nz, a.norb_tot, G::SX, G::SY)) return cudaErrorInvalidValue;
+  if (SV && !encode_pot_map(&potmap, a.V, a.nx, a.ny, a.nz, G::TX, G::TY)) return cudaErrorInvalidValue;
   const dim3 grid(((a.nx + G::TX - 1) / G::TX) * ((a.ny + G::TY - 1) / G::TY), a.norb_tot);
-  const size_t smem = (size_t)G::NS * G::SX * G::SY * sizeof(float2) + 128;
-  cudaError_t e = cudaFuncSetAttribute(k_tile4<MODE, NCW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  size_t smem = (size_t)G::NS * G::SX * G::SY * sizeof(float2) + 128;
+  if (SV) smem += (size_t)G::NS * G::TX * G::TY * (sizeof(float) + (MODE == 1 ? sizeof(float2) : 0));
+  cudaError_t e = cudaFuncSetAttribute(k_tile4<MODE, NCW, ROWS, SV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
   if (e != cudaSuccess) return e;
-  k_tile4<MODE, NCW><<<grid, G::NT, smem, s>>>(map, pmap, a);
+  k_tile4<MODE, NCW, ROWS, SV><<<grid, G::NT, smem, s>>>(map, pmap, potmap, a);
   return cudaGetLastError();
 }
 
@@ -618,6 +688,12 @@ cudaError_t launch_tile_plain(const TileArgs<T>& a, const CUtensorMap& pmap, con
 
 }  // namespace
 
+bool tile_variant_ok(int variant, int nx, int elem_bytes) {
+  if (elem_bytes == 16) return variant == 0 || variant == 1;
+  if (variant == 5 || variant == 6) return nx % 4 == 0;     // the potential's tensor-map rows
+  return variant >= 0 && variant < kTileVariants;
+}
+
 bool tile_supported(int nx, int ny, int nz, int elem_bytes) {
   // row stride must be a multiple of 16 bytes for the tensor map
   return ((size_t)nx * elem_bytes) % 16 == 0 && nz >= 1 && get_encode() != nullptr;
@@ -625,21 +701,36 @@ bool tile_supported(int nx, int ny, int nz, int elem_bytes) {
 
 // Variant table of the tile stencil (kernel, resident CTAs per SM the registers are capped for, L2
 // prefetch distance in planes).  FP32: 0 = k_tile, 3 CTAs, no prefetch; 1 = k_tile, 2 CTAs, 8;
-// 2 = k_tile4<8> (2 x 2 points per thread), 8.  FP64 (one CTA per SM, as the ring fills shared
-// memory): 0 = no prefetch, 1 = prefetch 8.
+// 2 = k_tile4<8> (2 x 2 points per thread), 8; 3 = k_tile4<8, 1 row> (2 x 1 points per thread,
+// 2 CTAs), 8; 4 = k_tile4<4, 1 row> (4 consumer warps, 4 CTAs), 8; 5, 6 = variants 3, 4 with V and psi
+// staged by TMA beside the orbital planes (nx % 4 == 0).  FP64 (one CTA per SM, as the ring fills
+// shared memory): 0 = no prefetch, 1 = prefetch 8.
 template <typename T>
 cudaError_t launch_tile_stage(const TileArgs<T>& a0, const void* vin, int mode, cudaStream_t s) {
   TileArgs<T> a = a0;
   a.prefetch = a.variant == 0 ? 0 : 8;
-  // psi map (interior box) for the L2 prefetch of the Horner base; unused in mode 0
+  // psi map (interior box): the L2 prefetch of the Horner base, or (variants 5, 6) its TMA loads;
+  // unused in mode 0
   CUtensorMap pmap;
   std::memset(&pmap, 0, sizeof(pmap));
   if (mode == 1 && a.prefetch > 0) {
-    const int by = sizeof(T) == 4 && a.variant == 2 ? B4<8>::TY : TY;
+    int by = TY;
+    if (sizeof(T) == 4 && a.variant == 2) by = B4<8>::TY;
+    if (sizeof(T) == 4 && (a.variant == 3 || a.variant == 5)) by = B4<8, 1>::TY;
+    if (sizeof(T) == 4 && (a.variant == 4 || a.variant == 6)) by = B4<4, 1>::TY;
     if (!encode_map<T>(&pmap, a.psi, a.nx, a.ny, a.nz, a.norb_tot, TX, by)) return cudaErrorInvalidValue;
   }
   if constexpr (sizeof(T) == 4) {
-    if (a.variant == 2) return mode == 1 ? launch_tile4<1, 8>(a, pmap, vin, s) : launch_tile4<0, 8>(a, pmap, vin, s);
+    if (a.variant == 2)
+      return mode == 1 ? launch_tile4<1, 8, 2, false>(a, pmap, vin, s) : launch_tile4<0, 8, 2, false>(a, pmap, vin, s);
+    if (a.variant == 3)
+      return mode == 1 ? launch_tile4<1, 8, 1, false>(a, pmap, vin, s) : launch_tile4<0, 8, 1, false>(a, pmap, vin, s);
+    if (a.variant == 4)
+      return mode == 1 ? launch_tile4<1, 4, 1, false>(a, pmap, vin, s) : launch_tile4<0, 4, 1, false>(a, pmap, vin, s);
+    if (a.variant == 5)
+      return mode == 1 ? launch_tile4<1, 8, 1, true>(a, pmap, vin, s) : launch_tile4<0, 8, 1, true>(a, pmap, vin, s);
+    if (a.variant == 6)
+      return mode == 1 ? launch_tile4<1, 4, 1, true>(a, pmap, vin, s) : launch_tile4<0, 4, 1, true>(a, pmap, vin, s);
     if (a.variant == 1) return launch_tile_plain<T, 2>(a, pmap, vin, mode, s);
     return launch_tile_plain<T, 3>(a, pmap, vin, mode, s);
   } else {

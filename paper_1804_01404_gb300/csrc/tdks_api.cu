@@ -83,8 +83,11 @@ struct tdks_ctx {
   int tile_variant[2] = {0, 0};  // stencil variant of the tiled path for H v / Horner stages
   long long wait_limit = 1LL << 22;  // polls per device-side wait of the tile kernels
   int stop_after = -1;              // timeout test: planes the tile producer issues (-1: all)
-  float tile_ms[2][kTileVariants] = {{-1.f, -1.f, -1.f}, {-1.f, -1.f, -1.f}};
+  float tile_ms[2][kTileVariants] = {{-1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f},
+                                     {-1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f}};
   int cell_variant = 0;          // Taylor launches of the cell kernels: 0 two buffers, 1 in-place sweep
+  cudaStream_t side = nullptr;   // tile path: the projections run here beside the stencil
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   float cell_ms[2] = {-1.f, -1.f};  // tuning time of one Taylor launch per variant (-1: not available)
   void *d_bufA = nullptr, *d_bufB = nullptr, *d_ec = nullptr;
   int* d_err = nullptr;
@@ -322,13 +325,24 @@ tdks_status tiled_kernel(tdks_ctx* c, int mode, const void* in, void* out, doubl
   using C = typename Cplx<T>::type;
   const T* V = sizeof(T) == 8 ? (const T*)c->d_v64 : (const T*)c->d_v32;
   TileArgs<T> a = make_tile_args<T>(c, V);
+  // the projections of the input (side stream) overlap the stencil (context stream); the scatter,
+  // which needs both, waits for the projections
+  auto project = [&](const C* v) -> cudaError_t {
+    cudaError_t e = cudaEventRecord(c->ev_fork, c->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->side, c->ev_fork, 0);
+    if (e == cudaSuccess) e = launch_tile_project<T>(a, v, c->side);
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev_join, c->side);
+    return e;
+  };
+  auto join = [&]() { return cudaStreamWaitEvent(c->stream, c->ev_join, 0); };
   if (mode == 0) {
     a.out = static_cast<C*>(out);
-    TDKS_CUDA(launch_tile_project<T>(a, static_cast<const C*>(in), c->stream));
+    TDKS_CUDA(project(static_cast<const C*>(in)));
     {
       Phase pk(c, 6);
       TDKS_CUDA(launch_tile_stage<T>(a, in, 0, c->stream));
     }
+    TDKS_CUDA(join());
     TDKS_CUDA(launch_tile_scatter<T>(a, a.out, 0, c->stream));
     c->launches += 3;
     return TDKS_OK;
@@ -344,11 +358,12 @@ tdks_status tiled_kernel(tdks_ctx* c, int mode, const void* in, void* out, doubl
   for (int st = 0; st < 4; ++st) {
     a.coef = (T)(dt / (4 - st));
     a.out = dst[st];
-    TDKS_CUDA(launch_tile_project<T>(a, v, c->stream));
+    TDKS_CUDA(project(v));
     {
       Phase pk(c, 6);
       TDKS_CUDA(launch_tile_stage<T>(a, v, 1, c->stream));
     }
+    TDKS_CUDA(join());
     TDKS_CUDA(launch_tile_scatter<T>(a, a.out, 1, c->stream));
     c->launches += 3;
     v = a.out;
@@ -500,9 +515,11 @@ tdks_status tune_tile(tdks_ctx* c) {
   TDKS_CUDA(cudaEventCreate(&e0));
   if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return fail(TDKS_ECUDA, "event"); }
   cudaError_t err = cudaSuccess;
+  const int eb = is_f32(c) ? 8 : 16;
   for (int mode = 0; mode < 2 && err == cudaSuccess; ++mode) {
-    float best = 0.f;
+    float best = -1.f;
     for (int v = 0; v < nvar && err == cudaSuccess; ++v) {
+      if (!tile_variant_ok(v, c->grid.n[0], eb)) continue;
       auto run = [&]() -> cudaError_t {
         if (is_f32(c)) {
           TileArgs<float> a = make_tile_args<float>(c, c->d_v32);
@@ -528,7 +545,7 @@ tdks_status tune_tile(tdks_ctx* c) {
       if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
       if (err != cudaSuccess) break;
       c->tile_ms[mode][v] = 0.5f * ms;
-      if (v == 0 || c->tile_ms[mode][v] < best) { best = c->tile_ms[mode][v]; c->tile_variant[mode] = v; }
+      if (best < 0.f || c->tile_ms[mode][v] < best) { best = c->tile_ms[mode][v]; c->tile_variant[mode] = v; }
     }
   }
   cudaEventDestroy(e0);
@@ -792,6 +809,12 @@ tdks_status tdks_init(const tdks_grid* grid, const tdks_cell* cell, const tdks_a
     if (launch_real_part(c->d_fft, c->d_ghat, nfft, 1.0, c->stream) != cudaSuccess)
       return bail(fail(TDKS_ECUDA, "ghat"));
   }
+  if (c->tiled) {
+    if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess)
+      return bail(fail(TDKS_ECUDA, "side stream for the projections"));
+  }
   if ((s = tune_tile(c)) != TDKS_OK) return bail(s);
   if ((s = tune_cell(c)) != TDKS_OK) return bail(s);
   if (cudaStreamSynchronize(c->stream) != cudaSuccess)
@@ -805,6 +828,9 @@ void tdks_destroy(tdks_ctx* c) {
   if (c->stream || !c->allocs.empty()) cudaStreamSynchronize(c->stream);
   for (auto& r : c->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->side) cudaStreamDestroy(c->side);
   for (void* p : c->allocs) cudaFree(p);
   if (c->h_resid) cudaFreeHost(c->h_resid);
   delete c;
@@ -1639,9 +1665,11 @@ tdks_status tdks_stats_read(tdks_ctx* c, tdks_stats* out, int reset) {
 
 tdks_status tdks_tile_variant(tdks_ctx* c, int set, int* variant, float* tune_ms) {
   TDKS_TRY(check_ctx(c));
-  if (set < -1 || set >= kTileVariants) return fail(TDKS_EINVAL, "tile variant outside -1..2");
+  if (set < -1 || set >= kTileVariants) return fail(TDKS_EINVAL, "tile variant outside -1..6");
   if (!c->tiled) return fail(TDKS_EUNSUPPORTED, "this context does not use the tile kernels");
-  if (set > 1 && !is_f32(c)) return fail(TDKS_EUNSUPPORTED, "tile variant 2 is FP32 only");
+  if (set > 1 && !is_f32(c)) return fail(TDKS_EUNSUPPORTED, "tile variants 2 to 6 are FP32 only");
+  if (set >= 0 && !tile_variant_ok(set, c->grid.n[0], is_f32(c) ? 8 : 16))
+    return fail(TDKS_EUNSUPPORTED, "tile variants 5 and 6 need nx divisible by 4");
   if (set >= 0) c->tile_variant[0] = c->tile_variant[1] = set;
   if (variant) { variant[0] = c->tile_variant[0]; variant[1] = c->tile_variant[1]; }
   if (tune_ms)

@@ -159,7 +159,9 @@ struct TileArgs {
   const int* ent_atom;
 };
 bool tile_supported(int nx, int ny, int nz, int elem_bytes);
-constexpr int kTileVariants = 3;
+constexpr int kTileVariants = 7;
+// whether a tile variant applies to rows of nx points of elem_bytes-byte complex values
+bool tile_variant_ok(int variant, int nx, int elem_bytes);
 // local part of one stage: mode 0 out = H_loc vin, mode 1 out = psi + (-i coef) H_loc vin
 template <typename T>
 cudaError_t launch_tile_stage(const TileArgs<T>& a, const void* vin, int mode, cudaStream_t s);

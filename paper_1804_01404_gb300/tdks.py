@@ -419,11 +419,11 @@ class Context:
 
     def tile_variant(self, set=-1):
         """Stencil variants of the tiled path (tdks_tile_variant): returns ([H v, Horner] variants,
-        tuning ms [[H v x 3], [Horner x 3]])."""
+        tuning ms [[H v x 7], [Horner x 7]])."""
         v = (C.c_int * 2)()
-        ms = (C.c_float * 6)()
+        ms = (C.c_float * 14)()
         _check(self.lib.tdks_tile_variant(self.ctx, int(set), v, ms))
-        return [v[0], v[1]], [[float(x) for x in ms[:3]], [float(x) for x in ms[3:]]]
+        return [v[0], v[1]], [[float(x) for x in ms[:7]], [float(x) for x in ms[7:]]]
 
     def cell_variant(self, set=-1):
         """Buffer scheme of the cell kernels' Taylor launches (tdks_cell_variant): returns (scheme in

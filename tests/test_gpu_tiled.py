@@ -104,15 +104,16 @@ def test_tiled_observables():
     assert abs(o["e_band"] - eb) < 1e-11 * abs(eb)
 
 
-@pytest.mark.parametrize("precision,variant", [("f32", 0), ("f32", 1), ("f32", 2), ("f64", 0), ("f64", 1)])
+@pytest.mark.parametrize("precision,variant", [("f32", 0), ("f32", 1), ("f32", 2), ("f32", 3), ("f32", 4), ("f32", 5),
+                                               ("f32", 6), ("f64", 0), ("f64", 1)])
 def test_tiled_variants_hpsi_and_taylor(precision, variant):
     """Every stencil variant (one point per thread for 3 CTAs per SM, or for 2 with L2 prefetch; FP32
-    2 x 2 blocks) against the oracle, on the anisotropic ragged grid (h differs per axis, so
+    2 x 2 and 2 x 1 blocks) against the oracle, on the anisotropic ragged grid (h differs per axis, so
     the per-axis coefficient ratios of the blocked variants are exercised)."""
     psi = W.initial_orbitals(S, 6)
     ctx = _ctx(S, precision)
     v, ms = ctx.tile_variant(variant)
-    nvar = 3 if precision == "f32" else 2
+    nvar = 7 if precision == "f32" else 2
     assert v == [variant, variant] and all(m > 0 for row in ms for m in row[:nvar])
     tol = 2e-5 if precision == "f32" else 1e-12
     ctx.update_potential(_dev(psi, precision))
@@ -138,7 +139,34 @@ def test_tile_variant_rules():
     with pytest.raises(TdksError):
         c64.tile_variant(2)
     with pytest.raises(TdksError):
-        _ctx(S, "f32").tile_variant(3)
+        c64.tile_variant(3)
+    with pytest.raises(TdksError):
+        _ctx(S, "f32").tile_variant(7)
+
+
+def test_staged_variants_need_nx_divisible_by_4():
+    """Variants 5 and 6 (potential rows as a tensor map of floats) apply only when nx % 4 == 0: on an
+    nx = 38 grid the tuner skips them and forcing one is refused; the others still run there."""
+    from paper_1804_01404_gb300.tdks import TdksError
+    s = W.isolated_cluster(n=24, natom=3, norb=2, radius=3.5, seed=5)
+    s.n = (38, 34, 30)                                    # too large for one orbital in shared memory
+    ctx = _ctx(s, "f32")
+    v, ms = ctx.tile_variant()
+    assert ms[0][5] == -1.0 and ms[0][6] == -1.0 and ms[1][5] == -1.0 and v[0] not in (5, 6)
+    assert all(m > 0 for m in ms[0][:5])
+    with pytest.raises(TdksError):
+        ctx.tile_variant(5)
+    psi = W.initial_orbitals(s, 2)
+    ud = _dev(psi, "f32")
+    ctx.update_potential(ud)
+    ctx.tile_variant(3)
+    hu = torch.empty_like(ud)
+    ctx.hpsi(ud, hu)
+    ctx.check()
+    tabs = O.projector_tables(s)
+    V = O.local_potential(s) + O.hxc(s, O.density(s, psi))
+    ref = O.hpsi(s, tabs, V, np.zeros(3), psi[0])
+    assert _rel(hu.cpu().numpy()[0].astype(np.complex128), ref) < 2e-5
 
 
 def test_wait_timeout_is_reported_and_context_recovers():
