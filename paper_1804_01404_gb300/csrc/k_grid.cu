@@ -175,6 +175,8 @@ struct FftHooks {
   double* vhxc;
   const double* rho;
   int xc;
+  int store_lim;                  // > 0: store only elements e < store_lim of each line
+  int herm;                       // 1: elements e > n/2 are conj(element n - e) (a real line's spectrum)
 };
 
 // data: 3D array [dims2][dims1][dims0]; transform lines along one axis.  Line l starts at
@@ -216,6 +218,9 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_lines(double2* data, int n,
       b0[j * n + e] = double2{v, 0.0};
     } else if (hk.zero_from > 0 && e >= hk.zero_from) {
       b0[j * n + e] = double2{0.0, 0.0};
+    } else if (hk.herm && e > n / 2) {
+      const double2 c = data[start + (long long)(n - e) * estride];
+      b0[j * n + e] = double2{c.x, -c.y};
     } else {
       b0[j * n + e] = data[start + e * estride];
     }
@@ -258,7 +263,7 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_lines(double2* data, int n,
         v += lda_vxc(hk.rho[o], hk.xc);
         hk.vhxc[o] = v;
       }
-    } else {
+    } else if (hk.store_lim <= 0 || e < hk.store_lim) {
       const long long l = l0 + j;
       const long long start = (l % cnt_lo) * s_lo + (l / cnt_lo) * s_hi;
       data[start + e * estride] = src[j * n + e];
@@ -615,7 +620,7 @@ int grid_for(long long n, int threads) {
 
 cudaError_t launch_fft_axis_hooked(double2* data, const int dims[3], int axis, int dir, const double2* tw,
                                    const int* radices, int nrad, cudaStream_t s, int batch, int lim_lo,
-                                   int lim_hi, const void* hooks);
+                                   int lim_hi, const void* hooks, int zx_lim = 0);
 
 cudaError_t launch_fft_axis(double2* data, const int dims[3], int axis, int dir, const double2* tw,
                             const int* radices, int nrad, cudaStream_t s, int batch, int lim_lo, int lim_hi) {
@@ -624,9 +629,10 @@ cudaError_t launch_fft_axis(double2* data, const int dims[3], int axis, int dir,
   return launch_fft_axis_hooked(data, dims, axis, dir, tw, radices, nrad, s, batch, lim_lo, lim_hi, &hk);
 }
 
+// zx_lim > 0 (z axis, batch 1): only the z lines of x < zx_lim, every y.
 cudaError_t launch_fft_axis_hooked(double2* data, const int dims[3], int axis, int dir, const double2* tw,
                                    const int* radices, int nrad, cudaStream_t s, int batch, int lim_lo,
-                                   int lim_hi, const void* hooks) {
+                                   int lim_hi, const void* hooks, int zx_lim) {
   const FftHooks& hk = *static_cast<const FftHooks*>(hooks);
   const int n = dims[axis];
   if (nrad > kMaxRadices) return cudaErrorInvalidValue;
@@ -638,6 +644,7 @@ cudaError_t launch_fft_axis_hooked(double2* data, const int dims[3], int axis, i
   const long long d01 = (long long)dims[0] * dims[1];
   if (axis == 0) { cnt_lo = dims[1]; cnt_hi = (long long)dims[2] * batch; s_lo = dims[0]; s_hi = d01; estride = 1; }
   else if (axis == 1) { cnt_lo = dims[0]; cnt_hi = (long long)dims[2] * batch; s_lo = 1; s_hi = d01; estride = dims[0]; }
+  else if (zx_lim > 0 && batch == 1) { cnt_lo = zx_lim; cnt_hi = dims[1]; s_lo = 1; s_hi = dims[0]; estride = d01; }
   else { cnt_lo = d01; cnt_hi = batch; s_lo = 1; s_hi = d01 * dims[2]; estride = d01; }
   // pruned transforms: only the lines with lo < lim_lo and hi < lim_hi (a zero-padded input, or
   // an output of which only a corner is used)
@@ -701,15 +708,21 @@ cudaError_t launch_hartree_xc_fused(double2* work, const int m[3], const int n[3
     return cudaGetLastError();
   }
   if (nlaunch) *nlaunch = 5;
+  // The density is real and the Poisson factor (4 pi / G^2, or the spectrum of the even Green's
+  // function) real and even, so every x line of the spectrum, after the y and z transforms in
+  // either direction, satisfies X(m0 - k) = conj(X(k)): the y and z passes only transform the
+  // x frequencies k <= m0/2, and the inverse x pass rebuilds the rest (one system per launch).
+  const int xh = batch == 1 ? m[0] / 2 + 1 : 0;
   FftHooks h1 = base;
   h1.load_real = 1;
   h1.rsrc = rho;
+  h1.store_lim = xh;
   if ((e = launch_fft_axis_hooked(work, m, 0, -1, tw[0], rad[0], nrad[0], s, batch, lo_x, hi_xy, &h1)) != cudaSuccess) return e;
   // the padded box (isolated) is written only where the density is: the forward y and z passes
   // read the rest as zeros
   FftHooks h2 = base;
   h2.zero_from = periodic ? 0 : n[1];
-  if ((e = launch_fft_axis_hooked(work, m, 1, -1, tw[1], rad[1], nrad[1], s, batch, 0, hi_xy, &h2)) != cudaSuccess) return e;
+  if ((e = launch_fft_axis_hooked(work, m, 1, -1, tw[1], rad[1], nrad[1], s, batch, xh, hi_xy, &h2)) != cudaSuccess) return e;
   FftHooks h3 = base;
   h3.zero_from = periodic ? 0 : n[2];
   h3.spectral = periodic ? 1 : 2;
@@ -717,9 +730,10 @@ cudaError_t launch_hartree_xc_fused(double2* work, const int m[3], const int n[3
   h3.inv_n = 1.0 / ((double)m[0] * m[1] * m[2]);
   h3.ghat = ghat;
   h3.gscale = gscale;
-  if ((e = launch_fft_axis_hooked(work, m, 2, -1, tw[2], rad[2], nrad[2], s, batch, 0, 0, &h3)) != cudaSuccess) return e;
-  if ((e = launch_fft_axis_hooked(work, m, 1, +1, tw[1], rad[1], nrad[1], s, batch, 0, hi_xy, &base)) != cudaSuccess) return e;
+  if ((e = launch_fft_axis_hooked(work, m, 2, -1, tw[2], rad[2], nrad[2], s, batch, 0, 0, &h3, xh)) != cudaSuccess) return e;
+  if ((e = launch_fft_axis_hooked(work, m, 1, +1, tw[1], rad[1], nrad[1], s, batch, xh, hi_xy, &base)) != cudaSuccess) return e;
   FftHooks h5 = base;
+  h5.herm = xh > 0 ? 1 : 0;
   h5.store_epi = 1;
   h5.vhxc = vhxc;
   h5.rho = rho;
