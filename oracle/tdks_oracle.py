@@ -21,6 +21,9 @@ What it computes (Hartree atomic units, hbar = m = e = 1, A' = A/c):
 * Eq. (TDKS): Hartree potential e^2 int rho(r')/|r-r'|; periodic cells solve it in G-space,
   isolated boxes with a zero-padded (Hockney) convolution.
 * Sec. 3.1 LDA: adiabatic local exchange (Slater) and, as an option, the Perdew-Zunger correlation.
+* Sec. 4.1 names the Becke-Johnson potential and its Tran-Blaha variant as xc options: TB-mBJ
+  exchange (published Becke-Roussel / Becke-Johnson / Tran-Blaha forms, restated) with the
+  kinetic energy density of the time-dependent orbitals, its current's share removed.
 * Sec. 3.1: dipole d = -int r (rho - rho0); Eq. (distribution): oscillator-strength spectrum.
 * Sec. 4.1, Eq. (sigma_ft): conductivity and dielectric function from the current after an A step;
   the work of the field W(t) = int I.E dt (excitation energy per volume).
@@ -35,7 +38,8 @@ notes; each is restated at the function that uses it.
 Parity status: every function here is pinned by the CPU tests against closed forms, brute
 force or invariants (plane-wave dispersion, dense eigendecomposition, Hockney direct sum,
 Gaussian/cosine charges, J = -dE/dA'/Omega, energy conservation, f-sum slope, the closed-form
-masked Fourier integral and the free-electron plasma limit of eps).  The full
+masked Fourier integral and the free-electron plasma limit of eps; for TB-mBJ the hydrogen
+Becke-Roussel hole, plane-wave kinetic densities and the uniform-gas correction term).  The full
 predictor-corrector step has no closed form: it is pinned only through those invariants.
 """
 from __future__ import annotations
@@ -322,15 +326,134 @@ def lda_c(rho):
     return np.where(pos, vc, 0.0), np.where(pos, eps, 0.0)
 
 
-def hxc(s, rho, hartree_on=True, xc_on=True):
-    """V_H + V_xc; xc_on: 0/False none, 1/True Slater exchange, 2 exchange + PZ correlation."""
+# Tran-Blaha modified Becke-Johnson exchange potential (TB-mBJ; Sec. 4.1 names the BJ potential and
+# its Tran-Blaha variant as options besides the LDA, without formulas).  The published forms
+# (Becke-Roussel 1989, Becke-Johnson 2006, Tran-Blaha 2009) are restated per spin; the system is
+# spin-unpolarised, so every per-spin density is half the total.  Parameters: gamma of the
+# Becke-Roussel hole curvature, alpha and beta (bohr^1/2) of c = alpha + beta sqrt(g).
+BR_GAMMA = 0.8
+MBJ_ALPHA, MBJ_BETA = -0.012, 1.023
+MBJ_RHO_MIN = 1e-10          # below this density the potential is set to zero (reading)
+
+
+def kinetic_density(s, psi, Ap=None):
+    """Kinetic energy density and paramagnetic current density of Bloch orbitals with
+    q = k + A' (Ap None: A' = 0), spin-saturated (factor 2) with k-weights:
+    tau = sum_k w_k sum_n 2 * 1/2 |(D1 + i q) u|^2,  j_a = sum_k w_k sum_n 2 Im(conj(u) (D1_a + i q_a) u),
+    rho = sum_k w_k sum_n 2 |u|^2.  Returns (rho, tau, j[3])."""
+    shape = psi.shape[-3:]
+    rho, tau = np.zeros(shape), np.zeros(shape)
+    j = np.zeros((3,) + shape)
+    for ik in range(s.nk):
+        q = np.asarray(s.kpts[ik], np.float64) + (np.zeros(3) if Ap is None else np.asarray(Ap, np.float64))
+        w = 2.0 * s.kw[ik]
+        u = psi[ik]
+        rho += w * np.sum(np.abs(u) ** 2, axis=0)
+        for a in range(3):
+            g = d1(u, a, s) + 1j * q[a] * u
+            tau += 0.5 * w * np.sum(np.abs(g) ** 2, axis=0)
+            j[a] += w * np.sum(np.imag(np.conj(u) * g), axis=0)
+    return rho, tau, j
+
+
+def tau_tilde(s, psi, Ap=None):
+    """tau - |j|^2 / (2 rho): the kinetic energy density with the current's share removed, the
+    time-dependent kinetic energy density the adiabatic TB-mBJ potential uses (reading).  A uniform
+    shift of q (any A') leaves it unchanged; it is >= 0 (Cauchy-Schwarz), 0 where rho = 0."""
+    rho, tau, j = kinetic_density(s, psi, Ap)
+    pos = rho > 0
+    jj = np.sum(j ** 2, axis=0)
+    return np.where(pos, np.maximum(tau - jj / (2.0 * np.where(pos, rho, 1.0)), 0.0), 0.0)
+
+
+def br_x(y):
+    """Root x of the Becke-Roussel equation x exp(-2x/3) / (x - 2) = y, elementwise.  The left side
+    falls monotonically on (0, 2) (from 0 to -inf) and on (2, inf) (from +inf to 0), so y < 0 has
+    its root in (0, 2), y > 0 in (2, inf), and y = +-inf gives x = 2."""
+    from scipy.optimize import brentq
+    y = np.asarray(y, np.float64)
+    out = np.empty(y.shape)
+    f = lambda x, yy: x * math.exp(-2.0 * x / 3.0) / (x - 2.0) - yy
+    for i, yy in np.ndenumerate(y):
+        if not np.isfinite(yy):
+            out[i] = 2.0
+        elif yy < 0:                              # f(0) = -y > 0
+            hi = 2.0 - 1e-15
+            out[i] = 2.0 if f(hi, yy) >= 0 else brentq(f, 0.0, hi, args=(yy,), xtol=1e-15, rtol=1e-15, maxiter=500)
+        else:                                     # f(2+) = +inf, f(inf) = -y < 0
+            lo, hi = 2.0 + 1e-15, 4.0
+            while f(hi, yy) > 0:
+                hi *= 2.0
+            out[i] = 2.0 if f(lo, yy) <= 0 else brentq(f, lo, hi, args=(yy,), xtol=1e-15, rtol=1e-15, maxiter=500)
+    return out
+
+
+def br_potential(rho_s, grad2_s, lap_s, D_s, gamma=BR_GAMMA):
+    """Becke-Roussel exchange potential of one spin channel: the exchange hole modelled as an
+    exponential exp(-a |r' - r - b|) normalised to -1, with the hole's curvature at r fixed by
+    Q = (lap rho - 2 gamma D) / 6, D = sum_i |grad psi_i|^2 - |grad rho|^2 / (4 rho) (the Fermi-hole
+    curvature, zero for one orbital).  x = a b solves x exp(-2x/3)/(x-2) = (2/3) pi^(2/3) rho^(5/3) / Q,
+    b = (x^3 exp(-x) / (8 pi rho))^(1/3), and the potential of the hole at its reference point is
+    v = -(1/b) (1 - exp(-x) - x exp(-x) / 2).  Inputs per spin: rho, |grad rho|^2, lap rho, D."""
+    rho_s = np.asarray(rho_s, np.float64)
+    Q = (np.asarray(lap_s, np.float64) - 2.0 * gamma * np.asarray(D_s, np.float64)) / 6.0
+    K = (2.0 / 3.0) * np.pi ** (2.0 / 3.0) * rho_s ** (5.0 / 3.0)
+    with np.errstate(divide="ignore"):
+        y = np.where(Q != 0, K / np.where(Q != 0, Q, 1.0), np.inf)
+    x = br_x(y)
+    b = np.cbrt(x ** 3 * np.exp(-x) / (8.0 * np.pi * rho_s))
+    return -(1.0 - np.exp(-x) - 0.5 * x * np.exp(-x)) / b
+
+
+def density_derivatives(s, rho):
+    """|grad rho|^2 and lap rho with the orbitals' 8th-order differences (periodic wrap or zero
+    outside the box)."""
+    g2 = sum(d1(rho, a, s) ** 2 for a in range(3))
+    return g2, sum(d2(rho, a, s) for a in range(3))
+
+
+def mbj_c(s, rho):
+    """c = alpha + beta sqrt(g), g = (1/Omega) int |grad rho| / rho over the cell (points with
+    rho <= MBJ_RHO_MIN add nothing; reading)."""
+    g2, _ = density_derivatives(s, rho)
+    pos = rho > MBJ_RHO_MIN
+    g = np.sum(np.where(pos, np.sqrt(g2) / np.where(pos, rho, 1.0), 0.0)) / rho.size
+    return MBJ_ALPHA + MBJ_BETA * math.sqrt(g)
+
+
+def mbj_x(s, rho, tau_t, c=None):
+    """TB-mBJ exchange potential, spin-unpolarised:
+    v_x = c v_BR + (3c - 2) (1/pi) sqrt(5/12) sqrt(2 t_s / rho_s) with rho_s = rho/2, t_s = tau_t/2
+    (tau_t in the (1/2) sum |grad psi|^2 convention) and v_BR of the spin channel, whose D is
+    2 t_s - |grad rho_s|^2 / (4 rho_s).  c None or <= 0: c from the density (mbj_c).  Zero where
+    rho <= MBJ_RHO_MIN.  Returns (v_x, c)."""
+    if c is None or c <= 0:
+        c = mbj_c(s, rho)
+    g2, lap = density_derivatives(s, rho)
+    pos = rho > MBJ_RHO_MIN
+    rs = np.where(pos, 0.5 * rho, 1.0)
+    ts = np.where(pos, 0.5 * np.asarray(tau_t, np.float64), 0.0)
+    gs2 = 0.25 * g2                               # |grad rho_s|^2
+    D = 2.0 * ts - gs2 / (4.0 * rs)
+    vbr = br_potential(rs, gs2, 0.5 * lap, D)
+    v = c * vbr + (3.0 * c - 2.0) / np.pi * math.sqrt(5.0 / 12.0) * np.sqrt(2.0 * ts / rs)
+    return np.where(pos, v, 0.0), c
+
+
+def hxc(s, rho, hartree_on=True, xc_on=True, psi=None, mbj_c=None):
+    """V_H + V_xc; xc_on: 0/False none, 1/True Slater exchange, 2 exchange + PZ correlation,
+    3 TB-mBJ exchange + PZ correlation (needs the orbitals psi that rho comes from; mbj_c fixes c)."""
     v = np.zeros_like(rho)
     if hartree_on:
         v = v + hartree(s, rho)
-    if xc_on:
+    if xc_on and xc_on != 3:
         v = v + lda_x(rho)[0]
-    if xc_on == 2:
+    if xc_on in (2, 3):
         v = v + lda_c(rho)[0]
+    if xc_on == 3:
+        if psi is None:
+            raise ValueError("xc 3 (TB-mBJ) needs the orbitals")
+        v = v + mbj_x(s, rho, tau_tilde(s, psi), mbj_c)[0]
     return v
 
 
@@ -443,23 +566,24 @@ def propagate_all(s, tabs, V, psi, Ap, dt):
     return out
 
 
-def pc_step(s, tabs, Vloc, psi, vhxc, t, dt, pc=True, hartree_on=True, xc_on=True, Ap=None):
+def pc_step(s, tabs, Vloc, psi, vhxc, t, dt, pc=True, hartree_on=True, xc_on=True, Ap=None, mbj_c=None):
     """One step t -> t + dt.
 
     Predictor: psi~ = T4[V_loc + V_Hxc(t)] psi(t); V~ = V_Hxc[rho(psi~)].
     Corrector: psi(t+dt) = T4[V_loc + (V_Hxc(t) + V~)/2] psi(t); V_Hxc(t+dt) = V_Hxc[rho(t+dt)].
     Both stages use A'(t + dt/2) (from s.field, or the given Ap).  With pc=False the step is
-    T4[V_loc + V_Hxc(t)] alone.  Returns (psi(t+dt), V_Hxc(t+dt), rho(t+dt))."""
+    T4[V_loc + V_Hxc(t)] alone.  V_Hxc of xc_on = 3 (TB-mBJ) takes the kinetic energy density of
+    the same orbitals as the density.  Returns (psi(t+dt), V_Hxc(t+dt), rho(t+dt))."""
     if Ap is None:
         Ap = field_Aprime(s.field, t + 0.5 * dt) if s.periodic else np.zeros(3)
     vmid = vhxc
     if pc:
         pred = propagate_all(s, tabs, Vloc + vhxc, psi, Ap, dt)
-        vpred = hxc(s, density(s, pred), hartree_on, xc_on)
+        vpred = hxc(s, density(s, pred), hartree_on, xc_on, pred, mbj_c)
         vmid = 0.5 * (vhxc + vpred)
     new = propagate_all(s, tabs, Vloc + vmid, psi, Ap, dt)
     rho = density(s, new)
-    return new, hxc(s, rho, hartree_on, xc_on), rho
+    return new, hxc(s, rho, hartree_on, xc_on, new, mbj_c), rho
 
 
 def apply_kick(s, psi, kappa):
@@ -470,17 +594,17 @@ def apply_kick(s, psi, kappa):
     return psi * ph
 
 
-def run(s, psi0, nsteps, pc=True, hartree_on=True, xc_on=True, record=True):
+def run(s, psi0, nsteps, pc=True, hartree_on=True, xc_on=True, record=True, mbj_c=None):
     """Propagate nsteps; returns final psi and per-step observables (t, J, dipole)."""
     tabs = projector_tables(s)
     Vloc = local_potential(s)
     psi = psi0.copy()
     rho0 = density(s, psi)
-    vhxc = hxc(s, rho0, hartree_on, xc_on)
+    vhxc = hxc(s, rho0, hartree_on, xc_on, psi, mbj_c)
     hist = dict(t=[], J=[], d=[])
     t = 0.0
     for _ in range(nsteps):
-        psi, vhxc, rho = pc_step(s, tabs, Vloc, psi, vhxc, t, s.dt, pc, hartree_on, xc_on)
+        psi, vhxc, rho = pc_step(s, tabs, Vloc, psi, vhxc, t, s.dt, pc, hartree_on, xc_on, mbj_c=mbj_c)
         t += s.dt
         if record:
             hist["t"].append(t)
@@ -546,7 +670,7 @@ def dense_hamiltonian(s, tabs, V, q):
     return H
 
 
-def ground_state(s, hartree_on=True, xc_on=True, mix=0.3, tol=1e-10, max_iter=400):
+def ground_state(s, hartree_on=True, xc_on=True, mix=0.3, tol=1e-10, max_iter=400, mbj_c=None):
     """Self-consistent ground state at A' = 0 (the static Kohn-Sham problem the paper's ground-state
     step solves before the time evolution): diagonalise H_k[V_loc + V_Hxc] densely for every k,
     occupy the lowest norb states (each normalised to sum |u|^2 dV = 1), form rho and V_Hxc[rho], and
@@ -566,7 +690,7 @@ def ground_state(s, hartree_on=True, xc_on=True, mix=0.3, tol=1e-10, max_iter=40
             E, U = np.linalg.eigh(H0[k] + np.diag((Vloc + vin).ravel()))
             eig[k] = E[:s.norb]
             psi[k] = (U[:, :s.norb].T / math.sqrt(s.dV)).reshape((s.norb,) + shape)
-        vout = hxc(s, density(s, psi), hartree_on, xc_on)
+        vout = hxc(s, density(s, psi), hartree_on, xc_on, psi, mbj_c)
         err = np.linalg.norm(vout - vin) / max(np.linalg.norm(vout), 1e-300)
         if err < tol:
             return psi, eig, vout, it
@@ -593,7 +717,7 @@ def longitudinal_run(s, psi0, nsteps, t0=0.0, hartree_on=True, xc_on=True):
     tabs = projector_tables(s)
     Vloc = local_potential(s)
     psi = psi0.copy()
-    vhxc = hxc(s, density(s, psi), hartree_on, xc_on)
+    vhxc = hxc(s, density(s, psi), hartree_on, xc_on, psi)
     t = t0
     J = current(s, tabs, psi, field_Aprime(s.field, t))
     A_now, A_prev = np.zeros(3), None
