@@ -83,7 +83,9 @@ typedef struct { double E_s, E_p, r_cut, width; } tdks_projector;
  *     correlation of the electron gas (eps_c = g / (1 + b1 sqrt(rs) + b2 rs) for rs >= 1, else
  *     A ln rs + B + C rs ln rs + D rs, with g = -0.1423, b1 = 1.0529, b2 = 0.3334, A = 0.0311,
  *     B = -0.048, C = 0.0020, D = -0.0116; V_c = eps_c - (rs/3) d eps_c / d rs).  hartree = xc = 0
- *     gives linear propagation.
+ *     gives linear propagation.  3: the Tran-Blaha modified Becke-Johnson exchange potential (Sec.
+ *     4.1 names it beside the LDA) plus the correlation of 2; see tdks_set_mbj.  xc = 3 needs
+ *     ncell <= 1 and keeps one more orbital array on the device (the predictor's orbitals).
  * pc: predictor-corrector on (1) or a single Taylor step with V(t) (0).
  * ncell: number of independent copies of the system propagated together (0 or 1: one).  With
  * ncell > 1 (periodic grids only) orbitals are [ncell][nk][norb][nz][ny][nx] and every cell has its
@@ -168,6 +170,23 @@ tdks_status tdks_ground_state(tdks_ctx* ctx, void* u, int max_iter, double tol, 
  * field has returned to zero this is the gauge-independent count.  Synchronises.  Isolated systems
  * use Omega = the box volume.  Errors: EINVAL for NULL arguments; EUNSUPPORTED for ncell > 1. */
 tdks_status tdks_excited_pairs(tdks_ctx* ctx, const void* u, const void* u_gs, double* n_eh);
+
+/* TB-mBJ exchange (xc = 3), the published Becke-Roussel / Becke-Johnson / Tran-Blaha forms per spin
+ * channel of the unpolarised system (rho_s = rho/2, t_s = tau~/2):
+ *   v_x = c v_BR + (3c - 2) (1/pi) sqrt(5/12) sqrt(2 t_s / rho_s),
+ *   v_BR = -(1/b)(1 - e^-x - x e^-x / 2),  b = (x^3 e^-x / (8 pi rho_s))^(1/3),
+ *   x e^(-2x/3) / (x - 2) = (2/3) pi^(2/3) rho_s^(5/3) / Q,  Q = (lap rho_s - 2 gamma D) / 6,
+ *   D = 2 t_s - |grad rho_s|^2 / (4 rho_s),  gamma = 0.8,
+ * with tau~ = tau - |j|^2 / (2 rho) the kinetic energy density of the orbitals whose density the
+ * potential is formed from (tau = sum_k w_k sum_n |(D1 + i k) u|^2, j = sum_k w_k sum_n 2 Im(conj(u)
+ * (D1 + i k) u); the current's share removed, so a uniform A' does not change it), derivatives by
+ * the 8th-order differences, no potential where rho <= 1e-10.  tdks_set_mbj: c > 0 fixes c; c <= 0
+ * (the default) forms c = -0.012 + 1.023 sqrt(g), g = (1/Omega) int |grad rho| / rho, from the
+ * density every time the potential is formed (three kernels per potential instead of two).  The
+ * setting is not part of a checkpoint.  tdks_mbj_c: the c of the last potential (synchronises).
+ * Errors: EUNSUPPORTED unless the context has xc = 3; EINVAL for a non-finite c or a NULL output. */
+tdks_status tdks_set_mbj(tdks_ctx* ctx, double c);
+tdks_status tdks_mbj_c(tdks_ctx* ctx, double* c);
 
 /* Longitudinal geometry (Sec. 4.1: in a thin film the vector potential is the external one plus the
  * one induced by the surface polarisation): A'(t) = A'_ext(t) + A'_ind(t) with

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtdks.so")
 SOURCES = ["tdks_api.cu", "k_orbital.cu", "k_tile.cu", "k_grid.cu", "k_nn.cu", "tdks_noalloc.cu", "k_probe.cu",
-           "k_response.cu", "k_scf.cu", "tables.cpp"]
+           "k_response.cu", "k_scf.cu", "k_mbj.cu", "tables.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1,0 +1,269 @@
+// TB-mBJ exchange potential (xc = 3; Sec. 4.1 names the Becke-Johnson potential and its
+// Tran-Blaha variant as options besides the LDA).  Published forms, per spin channel of the
+// spin-unpolarised system (rho_s = rho/2, t_s = tau~/2):
+//   D   = 2 t_s - |grad rho_s|^2 / (4 rho_s)              (curvature of the Fermi hole)
+//   Q   = (lap rho_s - 2 gamma D) / 6,  gamma = 0.8
+//   x   : x exp(-2x/3) / (x - 2) = (2/3) pi^(2/3) rho_s^(5/3) / Q      (Becke-Roussel hole)
+//   b   = (x^3 exp(-x) / (8 pi rho_s))^(1/3)
+//   v_BR = -(1/b) (1 - exp(-x) - x exp(-x) / 2)
+//   v_x = c v_BR + (3c - 2) (1/pi) sqrt(5/12) sqrt(2 t_s / rho_s)
+//   c   = alpha + beta sqrt(g), g = (1/Omega) int |grad rho| / rho,  alpha = -0.012, beta = 1.023
+// tau~ = tau - |j|^2 / (2 rho) is the kinetic energy density of the time-dependent orbitals with
+// the current's share removed (unchanged by a uniform A'), tau = sum_k w_k sum_n |(D1 + i k) u|^2,
+// j = sum_k w_k sum_n 2 Im(conj(u) (D1 + i k) u).  Derivatives are the 8th-order central
+// differences of the orbital stencil (periodic wrap, or zero outside an isolated box).  Points with
+// rho <= 1e-10 get no mBJ potential.
+//
+// Three launches: k_tau (partial sums of rho, tau, j over chunks of orbitals, one thread per grid
+// point), k_mbj_g (the cell average g and c, one grid_sum; skipped when c is fixed) and k_mbj_x
+// (folds the chunks, differentiates rho, solves the Becke-Roussel equation and adds v_x to V).
+#include <cuda_runtime.h>
+
+#include "grid_sum.cuh"
+#include "tdks_internal.h"
+
+namespace tdks {
+
+namespace {
+
+constexpr int kMbjThreads = 256;
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kRhoMin = 1e-10;
+constexpr double kGamma = 0.8, kAlpha = -0.012, kBeta = 1.023;
+
+struct Fd {   // the stencil's difference coefficients (kFD1, kFD2), passed by value
+  double d1[4], d2[5];
+};
+
+struct Nbr {   // linear indices of the 4 neighbours per side along each axis (-1: outside the box)
+  int p[3][4], m[3][4];
+};
+
+__device__ __forceinline__ Nbr neighbours(int ix, int iy, int iz, int nx, int ny, int nz, int periodic) {
+  Nbr b;
+  const int n[3] = {nx, ny, nz}, i[3] = {ix, iy, iz};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+#pragma unroll
+    for (int m = 1; m <= 4; ++m) {
+      int jp = i[a] + m, jm = i[a] - m;
+      bool op = true, om = true;
+      if (periodic) {
+        jp = jp >= n[a] ? jp - n[a] : jp;       // n >= 4: one wrap suffices
+        jm = jm < 0 ? jm + n[a] : jm;
+      } else {
+        op = jp < n[a];
+        om = jm >= 0;
+      }
+      int cp[3] = {ix, iy, iz}, cm[3] = {ix, iy, iz};
+      cp[a] = jp;
+      cm[a] = jm;
+      b.p[a][m - 1] = op ? (cp[2] * ny + cp[1]) * nx + cp[0] : -1;
+      b.m[a][m - 1] = om ? (cm[2] * ny + cm[1]) * nx + cm[0] : -1;
+    }
+  }
+  return b;
+}
+
+template <typename V>
+__device__ __forceinline__ V ld_or_zero(const V* f, int i) {
+  return i >= 0 ? f[i] : V{};
+}
+
+// part[(chunk * 5 + c) * npts + p], c = rho, tau, j_x, j_y, j_z, over the orbitals of one chunk.
+template <typename T>
+__global__ void __launch_bounds__(kMbjThreads) k_tau(const typename Cplx<T>::type* __restrict__ u, int nk, int norb,
+                                                    int nx, int ny, int nz, int periodic,
+                                                    const double* __restrict__ kpts, const double* __restrict__ kw,
+                                                    double hx, double hy, double hz, Fd fd, int ochunk,
+                                                    double* __restrict__ part) {
+  using C = typename Cplx<T>::type;
+  const int npts = nx * ny * nz;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= npts) return;
+  const int ix = p % nx, iy = (p / nx) % ny, iz = p / (nx * ny);
+  const Nbr nb = neighbours(ix, iy, iz, nx, ny, nz, periodic);
+  const double h[3] = {hx, hy, hz};
+  T d1[3][4];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int m = 0; m < 4; ++m) d1[a][m] = (T)(fd.d1[m] / h[a]);
+  const int o0 = blockIdx.y * ochunk, o1 = min(o0 + ochunk, nk * norb);
+  T acc[5] = {0, 0, 0, 0, 0};
+  for (int o = o0; o < o1; ++o) {
+    const int k = o / norb;
+    const T w = (T)(2.0 * kw[k]);
+    const C* f = u + (size_t)o * npts;
+    const C c0 = f[p];
+    acc[0] += w * (c0.x * c0.x + c0.y * c0.y);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const T q = (T)kpts[3 * k + a];
+      C g = C{-q * c0.y, q * c0.x};                                     // i q u
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const C fp = ld_or_zero(f, nb.p[a][m]), fm = ld_or_zero(f, nb.m[a][m]);
+        g.x += d1[a][m] * (fp.x - fm.x);
+        g.y += d1[a][m] * (fp.y - fm.y);
+      }
+      acc[1] += T(0.5) * w * (g.x * g.x + g.y * g.y);
+      acc[2 + a] += w * (c0.x * g.y - c0.y * g.x);                     // Im(conj(u) g)
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 5; ++c) part[((size_t)blockIdx.y * 5 + c) * npts + p] = (double)acc[c];
+}
+
+// |grad rho|^2 and lap rho at p by the 8th-order differences
+__device__ __forceinline__ void rho_derivs(const double* __restrict__ rho, const Nbr& nb, double r0,
+                                           const double h[3], const Fd& fd, double* g2, double* lap) {
+  double gg = 0.0, ll = 0.0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    double d = 0.0, s = fd.d2[0] * r0;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const double fp = ld_or_zero(rho, nb.p[a][m]), fm = ld_or_zero(rho, nb.m[a][m]);
+      d += fd.d1[m] * (fp - fm);
+      s += fd.d2[m + 1] * (fp + fm);
+    }
+    d /= h[a];
+    gg += d * d;
+    ll += s / (h[a] * h[a]);
+  }
+  *g2 = gg;
+  *lap = ll;
+}
+
+// c = alpha + beta sqrt(g) from the density (written by the last CTA)
+__global__ void __launch_bounds__(kMbjThreads) k_mbj_g(const double* __restrict__ rho, int nx, int ny, int nz,
+                                                      int periodic, double hx, double hy, double hz, Fd fd,
+                                                      double* partials, unsigned* ticket, double* c_out) {
+  __shared__ double tot[1];
+  const int npts = nx * ny * nz;
+  const double h[3] = {hx, hy, hz};
+  double v[1] = {0.0};
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npts; p += gridDim.x * blockDim.x) {
+    const double r0 = rho[p];
+    if (r0 > kRhoMin) {
+      const Nbr nb = neighbours(p % nx, (p / nx) % ny, p / (nx * ny), nx, ny, nz, periodic);
+      double g2, lap;
+      rho_derivs(rho, nb, r0, h, fd, &g2, &lap);
+      v[0] += sqrt(g2) / r0;
+    }
+  }
+  if (grid_sum<1>(v, partials, ticket, tot) && threadIdx.x == 0) *c_out = kAlpha + kBeta * sqrt(tot[0] / npts);
+}
+
+// H(x) = x exp(-2x/3) - y (x - 2): the Becke-Roussel equation times (x - 2), one root per branch
+__device__ __forceinline__ double br_h(double x, double y) { return x * exp(-2.0 * x / 3.0) - y * (x - 2.0); }
+
+// Root x of x exp(-2x/3)/(x-2) = y: y < 0 in (0, 2) (H(0) = 2y < 0 < H(2)), y > 0 in (2, hi)
+// (H(2) > 0 > H(hi)).  34 bisection steps, then up to four Newton steps kept inside the bracket.
+__device__ double br_root(double y) {
+  double neg, pos;                    // H(neg) < 0 < H(pos)
+  if (y < 0.0) {
+    neg = 0.0;
+    pos = 2.0;
+  } else {
+    pos = 2.0;
+    neg = 4.0;
+    while (br_h(neg, y) > 0.0 && neg < 4096.0) neg *= 2.0;   // exp(-2x/3) underflows long before 4096
+  }
+  for (int it = 0; it < 34; ++it) {
+    const double mid = 0.5 * (neg + pos);
+    if (br_h(mid, y) < 0.0) neg = mid; else pos = mid;
+  }
+  double x = 0.5 * (neg + pos);
+  const double lo = fmin(neg, pos), hi = fmax(neg, pos);
+  for (int it = 0; it < 4; ++it) {
+    const double e = exp(-2.0 * x / 3.0);
+    const double f = x * e - y * (x - 2.0), df = e * (1.0 - 2.0 * x / 3.0) - y;
+    if (df == 0.0) break;
+    const double xn = x - f / df;
+    if (!(xn > lo && xn < hi)) break;
+    x = xn;
+  }
+  return x;
+}
+
+// V[p] += v_x^mBJ(rho, grad rho, lap rho, tau~) with c = c_fixed (> 0) or *c_dev
+__global__ void __launch_bounds__(kMbjThreads) k_mbj_x(const double* __restrict__ rho, const double* __restrict__ part,
+                                                      int nchunk, int nx, int ny, int nz, int periodic, double hx,
+                                                      double hy, double hz, Fd fd, double c_fixed,
+                                                      const double* __restrict__ c_dev, double* __restrict__ V) {
+  const int npts = nx * ny * nz;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= npts) return;
+  const double r0 = rho[p];
+  if (!(r0 > kRhoMin)) return;
+  const double h[3] = {hx, hy, hz};
+  // tau~ from the orbitals' chunks (their own rho for the current's share), chunks in order
+  double s[5] = {0, 0, 0, 0, 0};
+  for (int ch = 0; ch < nchunk; ++ch)
+#pragma unroll
+    for (int c = 0; c < 5; ++c) s[c] += part[((size_t)ch * 5 + c) * npts + p];
+  double tt = 0.0;
+  if (s[0] > 0.0) tt = fmax(s[1] - (s[2] * s[2] + s[3] * s[3] + s[4] * s[4]) / (2.0 * s[0]), 0.0);
+  const Nbr nb = neighbours(p % nx, (p / nx) % ny, p / (nx * ny), nx, ny, nz, periodic);
+  double g2, lap;
+  rho_derivs(rho, nb, r0, h, fd, &g2, &lap);
+  const double c = c_fixed > 0.0 ? c_fixed : *c_dev;
+  const double rs = 0.5 * r0, ts = 0.5 * tt, gs2 = 0.25 * g2;
+  const double D = 2.0 * ts - gs2 / (4.0 * rs);
+  const double Q = (0.5 * lap - 2.0 * kGamma * D) / 6.0;
+  const double K = (2.0 / 3.0) * cbrt(kPi * kPi) * rs * cbrt(rs * rs);     // (2/3) pi^(2/3) rho_s^(5/3)
+  const double x = Q != 0.0 ? br_root(K / Q) : 2.0;
+  const double ex = exp(-x);
+  const double b = cbrt(x * x * x * ex / (8.0 * kPi * rs));
+  const double vbr = -(1.0 - ex - 0.5 * x * ex) / b;
+  V[p] += c * vbr + (3.0 * c - 2.0) / kPi * sqrt(5.0 / 12.0) * sqrt(2.0 * ts / rs);
+}
+
+}  // namespace
+
+int mbj_chunks(long long npts, int norb_tot) {
+  long long ch = (152LL * 4 * kMbjThreads + npts - 1) / npts;      // about 4 CTAs per SM
+  if (ch > norb_tot) ch = norb_tot;
+  return ch < 1 ? 1 : (int)ch;
+}
+
+template <typename T>
+cudaError_t launch_mbj(const typename Cplx<T>::type* u, int nk, int norb, const int n[3], int periodic,
+                       const double h[3], const double* kpts, const double* kw, const double* rho, double c_fixed,
+                       double* part, int nchunk, double* partials, unsigned* ticket, double* c_dev, double* V,
+                       cudaStream_t s, int* nlaunch) {
+  const int npts = n[0] * n[1] * n[2];
+  const int norb_tot = nk * norb;
+  const int ochunk = (norb_tot + nchunk - 1) / nchunk;
+  const int bx = (npts + kMbjThreads - 1) / kMbjThreads;
+  Fd fd;
+  for (int m = 0; m < 4; ++m) fd.d1[m] = kFD1[m];
+  for (int m = 0; m < 5; ++m) fd.d2[m] = kFD2[m];
+  k_tau<T><<<dim3(bx, nchunk), kMbjThreads, 0, s>>>(u, nk, norb, n[0], n[1], n[2], periodic, kpts, kw, h[0], h[1],
+                                                    h[2], fd, ochunk, part);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  int nl = 2;
+  if (!(c_fixed > 0.0)) {
+    k_mbj_g<<<grid_sum_blocks(npts, kMbjThreads), kMbjThreads, 0, s>>>(rho, n[0], n[1], n[2], periodic, h[0], h[1],
+                                                                      h[2], fd, partials, ticket, c_dev);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    nl = 3;
+  }
+  k_mbj_x<<<bx, kMbjThreads, 0, s>>>(rho, part, nchunk, n[0], n[1], n[2], periodic, h[0], h[1], h[2], fd, c_fixed,
+                                     c_dev, V);
+  if (nlaunch) *nlaunch = nl;
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_mbj<float>(const float2*, int, int, const int*, int, const double*, const double*,
+                                       const double*, const double*, double, double*, int, double*, unsigned*, double*,
+                                       double*, cudaStream_t, int*);
+template cudaError_t launch_mbj<double>(const double2*, int, int, const int*, int, const double*, const double*,
+                                        const double*, const double*, double, double*, int, double*, unsigned*,
+                                        double*, double*, cudaStream_t, int*);
+
+}  // namespace tdks

@@ -6,6 +6,7 @@
 //             eps_c = g / (1 + b1 sqrt(r_s) + b2 r_s)                 for r_s >= 1,
 //             eps_c = A ln r_s + B + C r_s ln r_s + D r_s              for r_s < 1,
 //           and V_c = d(rho eps_c)/d rho = eps_c - (r_s / 3) d eps_c / d r_s.
+//   xc = 3: the correlation of xc = 2 alone (the TB-mBJ exchange is added by its own kernel);
 //   xc = 0: nothing.
 #pragma once
 
@@ -16,8 +17,8 @@ namespace tdks {
 __device__ __forceinline__ double lda_vxc(double rho, int xc) {
   if (xc == 0) return 0.0;
   const double r = fmax(rho, 0.0);
-  double v = -cbrt(3.0 * r / 3.14159265358979323846);
-  if (xc == 2 && r > 1e-30) {
+  double v = xc == 3 ? 0.0 : -cbrt(3.0 * r / 3.14159265358979323846);
+  if ((xc == 2 || xc == 3) && r > 1e-30) {
     constexpr double g = -0.1423, b1 = 1.0529, b2 = 0.3334;
     constexpr double A = 0.0311, B = -0.048, C = 0.0020, D = -0.0116;
     const double rs = cbrt(3.0 / (4.0 * 3.14159265358979323846 * r));

@@ -63,6 +63,13 @@ struct tdks_ctx {
   std::vector<double> ftable;               // TDKS_FIELD_TABLE: [nt][3] samples of A'
   double tab_t0 = 0.0, tab_dt = 0.0;
   int longitudinal = 0, lg_first = 1;       // longitudinal geometry (tdks_set_longitudinal)
+  // TB-mBJ exchange (xc = 3): c fixed (> 0) or from the density; per-chunk kinetic-density sums;
+  // the predictor's orbitals (their kinetic energy density enters the predicted potential)
+  double mbj_c_fixed = 0.0;
+  double* d_mbj_c = nullptr;
+  double* d_mbj_part = nullptr;
+  int mbj_nchunk = 0;
+  void* d_porb = nullptr;
   double* d_lg = nullptr;                   // {A'_ind^n[3], A'_ind^{n-1}[3]}
   // projector tables
   int natom = 0, nsph = 0;
@@ -375,10 +382,11 @@ tdks_status tiled_kernel(tdks_ctx* c, int mode, const void* in, void* out, doubl
   return TDKS_OK;
 }
 
+// phase: profiling phase (-1: H u -> hpsi, a written Taylor result -> corrector, else predictor)
 tdks_status orbital_kernel(tdks_ctx* c, int mode, const void* in, void* out, const double Ap[3],
                            double dt, double* rho, int write_out, const double* Ap_obs = nullptr,
-                           bool obs_start = false) {
-  Phase ph(c, mode == 0 ? 2 : (write_out ? 1 : 0));
+                           bool obs_start = false, int phase = -1) {
+  Phase ph(c, phase >= 0 ? phase : (mode == 0 ? 2 : (write_out ? 1 : 0)));
   if (c->tiled)
     return is_f32(c) ? tiled_kernel<float>(c, mode, in, out, dt, rho, write_out)
                      : tiled_kernel<double>(c, mode, in, out, dt, rho, write_out);
@@ -440,8 +448,27 @@ tdks_status fft3d(tdks_ctx* c, int dir) {
   return TDKS_OK;
 }
 
-// vhxc = V_H[rho] + V_x[rho]
-tdks_status hxc(tdks_ctx* c, const double* rho, double* vhxc) {
+// vhxc = V_H[rho] + V_xc[rho]; u: the orbitals rho comes from (their kinetic energy density
+// enters the TB-mBJ exchange of xc = 3, added after the Hartree + correlation kernels)
+tdks_status hxc_lda(tdks_ctx* c, const double* rho, double* vhxc);
+tdks_status hxc(tdks_ctx* c, const double* rho, double* vhxc, const void* u) {
+  TDKS_TRY(hxc_lda(c, rho, vhxc));
+  if (c->opt.xc != 3) return TDKS_OK;
+  Phase ph(c, 3);
+  int nl = 0;
+  if (is_f32(c))
+    TDKS_CUDA(launch_mbj<float>(static_cast<const float2*>(u), c->nk, c->norb, c->grid.n, c->grid.periodic, c->grid.h,
+                                c->d_kpts, c->d_kw, rho, c->mbj_c_fixed, c->d_mbj_part, c->mbj_nchunk, c->d_partials,
+                                c->d_ticket, c->d_mbj_c, vhxc, c->stream, &nl));
+  else
+    TDKS_CUDA(launch_mbj<double>(static_cast<const double2*>(u), c->nk, c->norb, c->grid.n, c->grid.periodic,
+                                 c->grid.h, c->d_kpts, c->d_kw, rho, c->mbj_c_fixed, c->d_mbj_part, c->mbj_nchunk,
+                                 c->d_partials, c->d_ticket, c->d_mbj_c, vhxc, c->stream, &nl));
+  c->launches += nl;
+  return TDKS_OK;
+}
+
+tdks_status hxc_lda(tdks_ctx* c, const double* rho, double* vhxc) {
   Phase ph(c, 3);
   // a batch of periodic cells is handled as one grid stacked along z for the pointwise kernels
   const int ns[3] = {c->grid.n[0], c->grid.n[1], c->grid.n[2] * c->ncell};
@@ -655,7 +682,9 @@ tdks_status tdks_init(const tdks_grid* grid, const tdks_cell* cell, const tdks_a
   for (int k = 0; k < nk; ++k) wsum += kw[k];
   if (std::fabs(wsum - 1.0) > 1e-9) return fail(TDKS_EINVAL, "k-point weights must sum to 1");
   if (opts->obs_at_start != 0 && opts->obs_at_start != 1) return fail(TDKS_EINVAL, "obs_at_start must be 0 or 1");
-  if (opts->xc < 0 || opts->xc > 2) return fail(TDKS_EINVAL, "xc must be 0 (none), 1 (exchange) or 2 (exchange + correlation)");
+  if (opts->xc < 0 || opts->xc > 3)
+    return fail(TDKS_EINVAL, "xc must be 0 (none), 1 (exchange), 2 (exchange + correlation) or 3 (TB-mBJ exchange + correlation)");
+  if (opts->xc == 3 && opts->ncell > 1) return fail(TDKS_EUNSUPPORTED, "xc = 3 (TB-mBJ) needs ncell = 1");
   if (opts->hartree != 0 && opts->hartree != 1) return fail(TDKS_EINVAL, "hartree must be 0 or 1");
 
   tdks_ctx* c = new tdks_ctx();
@@ -755,6 +784,16 @@ tdks_status tdks_init(const tdks_grid* grid, const tdks_cell* cell, const tdks_a
     c->d_scratch = p;
   }
   if ((s = dalloc(c, &c->d_orb_obs, (size_t)c->ncell * nk * norb * 8)) != TDKS_OK) return bail(s);
+  if (opts->xc == 3) {
+    const size_t csz = is_f32(c) ? sizeof(float2) : sizeof(double2);
+    unsigned char* p = nullptr;
+    c->mbj_nchunk = mbj_chunks((long long)np, nk * norb);
+    if ((s = dalloc(c, &c->d_mbj_part, (size_t)c->mbj_nchunk * 5 * np)) != TDKS_OK) return bail(s);
+    if ((s = dalloc(c, &c->d_mbj_c, 1)) != TDKS_OK) return bail(s);
+    if ((s = dalloc(c, &p, csz * np * (size_t)nk * norb)) != TDKS_OK) return bail(s);
+    c->d_porb = p;
+    cudaMemsetAsync(c->d_mbj_c, 0, sizeof(double), c->stream);
+  }
   if ((s = dalloc(c, &c->d_step_obs, 8 * (size_t)c->ncell)) != TDKS_OK) return bail(s);
   c->red_blocks = 304;
   if ((s = dalloc(c, &c->d_partials, (size_t)c->red_blocks * 4)) != TDKS_OK) return bail(s);
@@ -970,7 +1009,7 @@ tdks_status tdks_ground_state(tdks_ctx* c, void* u, int max_iter, double tol, do
     TDKS_TRY(ortho(u, Wb));
     TDKS_CUDA(cudaMemcpyAsync(u, Wb, nob, cudaMemcpyDeviceToDevice, c->stream));
     TDKS_TRY(density(c, u, c->d_rho));
-    TDKS_TRY(hxc(c, c->d_rho, c->d_vhxc));
+    TDKS_TRY(hxc(c, c->d_rho, c->d_vhxc, u));
     TDKS_CUDA(cudaMemcpyAsync(d_vin, c->d_vhxc, (size_t)np * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     double resid = 0.0;
     int it = 0;
@@ -996,7 +1035,7 @@ tdks_status tdks_ground_state(tdks_ctx* c, void* u, int max_iter, double tol, do
       }
       TDKS_TRY(ortho(Wb, u));                                                   // U = W L^{-H}
       TDKS_TRY(density(c, u, c->d_rho));
-      TDKS_TRY(hxc(c, c->d_rho, c->d_vhxc));                                     // V_out
+      TDKS_TRY(hxc(c, c->d_rho, c->d_vhxc, u));                                  // V_out
       double dv = 0.0;
       if (check) {
         TDKS_CUDA(cudaMemcpyAsync(hv.data(), c->d_vhxc, (size_t)np * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -1012,7 +1051,7 @@ tdks_status tdks_ground_state(tdks_ctx* c, void* u, int max_iter, double tol, do
     }
     // the ground state's own potential and reference density
     TDKS_TRY(density(c, u, c->d_rho));
-    TDKS_TRY(hxc(c, c->d_rho, c->d_vhxc));
+    TDKS_TRY(hxc(c, c->d_rho, c->d_vhxc, u));
     TDKS_CUDA(cudaMemcpyAsync(c->d_rho0, c->d_rho, (size_t)np * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     c->have_rho0 = true;
     c->have_potential = true;
@@ -1065,6 +1104,28 @@ tdks_status tdks_excited_pairs(tdks_ctx* c, const void* u, const void* u_gs, dou
     n += 2.0 * kw[k] * (no - f2);
   }
   *n_eh = n / c->omega;
+  return TDKS_OK;
+}
+
+tdks_status tdks_set_mbj(tdks_ctx* c, double cval) {
+  TDKS_TRY(check_ctx(c));
+  if (c->opt.xc != 3) return fail(TDKS_EUNSUPPORTED, "tdks_set_mbj needs a context with xc = 3");
+  if (!std::isfinite(cval)) return fail(TDKS_EINVAL, "tdks_set_mbj: c must be finite");
+  c->mbj_c_fixed = cval > 0.0 ? cval : 0.0;
+  return TDKS_OK;
+}
+
+tdks_status tdks_mbj_c(tdks_ctx* c, double* cval) {
+  TDKS_TRY(check_ctx(c));
+  if (!cval) return fail(TDKS_EINVAL, "null output");
+  if (c->opt.xc != 3) return fail(TDKS_EUNSUPPORTED, "tdks_mbj_c needs a context with xc = 3");
+  if (c->mbj_c_fixed > 0.0) {
+    *cval = c->mbj_c_fixed;
+    return TDKS_OK;
+  }
+  TDKS_CUDA(cudaMemcpyAsync(c->h_resid, c->d_mbj_c, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  TDKS_CUDA(cudaStreamSynchronize(c->stream));
+  *cval = *c->h_resid;
   return TDKS_OK;
 }
 
@@ -1154,7 +1215,7 @@ tdks_status tdks_update_potential(tdks_ctx* c, const void* u) {
   TDKS_TRY(check_ctx(c));
   if (!u) return fail(TDKS_EINVAL, "null orbitals");
   TDKS_TRY(density(c, u, c->d_rho));
-  TDKS_TRY(hxc(c, c->d_rho, c->d_vhxc));
+  TDKS_TRY(hxc(c, c->d_rho, c->d_vhxc, u));
   if (!c->have_rho0) {
     TDKS_CUDA(cudaMemcpyAsync(c->d_rho0, c->d_rho, c->npts * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     c->have_rho0 = true;
@@ -1195,8 +1256,11 @@ tdks_status pc_step(tdks_ctx* c, void* u, const double Amid[3], const double* Ao
       Phase ph(c, 5);
       TDKS_CUDA(cudaMemsetAsync(c->d_rho_tmp, 0, gb, c->stream));
     }
-    TDKS_TRY(orbital_kernel(c, 1, u, u, Amid, dt, c->d_rho_tmp, 0, obs_start ? Aobs : nullptr, obs_start));
-    TDKS_TRY(hxc(c, c->d_rho_tmp, c->d_vpred));
+    // (TB-mBJ needs the predicted orbitals themselves: they are written to d_porb)
+    void* pout = c->d_porb ? c->d_porb : u;
+    TDKS_TRY(orbital_kernel(c, 1, u, pout, Amid, dt, c->d_rho_tmp, c->d_porb ? 1 : 0, obs_start ? Aobs : nullptr,
+                            obs_start, 0));
+    TDKS_TRY(hxc(c, c->d_rho_tmp, c->d_vpred, pout));
     // corrector: T4 with the mid-point potential
     TDKS_TRY(set_step_potential(c, 0.5, c->d_vpred, 0.5));
   } else {
@@ -1209,7 +1273,7 @@ tdks_status pc_step(tdks_ctx* c, void* u, const double Amid[3], const double* Ao
   // corrector; it also forms the per-orbital observables unless the predictor already did
   const bool corr_obs = !(pc && obs_start);
   TDKS_TRY(orbital_kernel(c, 1, u, u, Amid, dt, c->d_rho, 1, corr_obs ? Aobs : nullptr, obs_start));
-  TDKS_TRY(hxc(c, c->d_rho, c->d_vhxc));
+  TDKS_TRY(hxc(c, c->d_rho, c->d_vhxc, u));
   if (pc) {   // the PC's own misfit, for scale
     TDKS_CUDA(launch_residual(c->d_vhxc, c->d_vpred, c->npts * c->ncell, c->d_partials, c->d_ticket, c->d_resid, c->stream));
     c->launches += 1;
@@ -1248,7 +1312,7 @@ tdks_status predicted_step(tdks_ctx* c, void* u, const double Amid[3], const dou
   const tdks_status cs = orbital_kernel(c, 1, u, u, Amid, dt, c->d_rho, 1, Aobs, obs_start);
   c->cur_backup = nullptr;
   TDKS_TRY(cs);
-  TDKS_TRY(hxc(c, c->d_rho, c->d_vnew));
+  TDKS_TRY(hxc(c, c->d_rho, c->d_vnew, u));
   TDKS_CUDA(launch_residual(c->d_vnew, c->d_vpred, c->npts, c->d_partials, c->d_ticket, c->d_resid, c->stream));
   c->launches += 1;
   TDKS_CUDA(cudaMemcpyAsync(c->h_resid, c->d_resid, sizeof(double), cudaMemcpyDeviceToHost, c->stream));

@@ -276,6 +276,15 @@ cudaError_t launch_basis(const typename Cplx<T>::type* U, const typename Cplx<T>
                          cudaStream_t s);
 cudaError_t launch_mix_potential(double* vin, double* vout, long long n, double mix, cudaStream_t s);
 
+// TB-mBJ exchange (k_mbj.cu): V += v_x^mBJ[rho, tau~ of u]; c = c_fixed (> 0) or computed into *c_dev.
+// part: [nchunk][5][npts] doubles; partials / ticket: a grid_sum work area.  nlaunch: kernels launched.
+int mbj_chunks(long long npts, int norb_tot);
+template <typename T>
+cudaError_t launch_mbj(const typename Cplx<T>::type* u, int nk, int norb, const int n[3], int periodic,
+                       const double h[3], const double* kpts, const double* kw, const double* rho, double c_fixed,
+                       double* part, int nchunk, double* partials, unsigned* ticket, double* c_dev, double* V,
+                       cudaStream_t s, int* nlaunch);
+
 // longitudinal geometry: one leapfrog step of A'_ind from J(t_n) = step_obs[0..2] (see k_grid.cu)
 cudaError_t launch_longitudinal(const double* step_obs, double* lg, int first, double dt, const double ext_mid[3],
                                 const double ext_end[3], double* ap_mid, double* ap_end, cudaStream_t s);

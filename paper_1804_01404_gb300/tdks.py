@@ -130,6 +130,8 @@ def load_library(path: str = LIB_PATH):
         "tdks_ground_state": [vp, vp, i, d, d, d, C.POINTER(C.c_double)],
         "tdks_excited_pairs": [vp, vp, vp, C.POINTER(C.c_double)],
         "tdks_longitudinal_read": [vp, C.POINTER(C.c_double)],
+        "tdks_set_mbj": [vp, d],
+        "tdks_mbj_c": [vp, C.POINTER(C.c_double)],
         "tdks_get_state": [vp, vp, C.c_size_t],
         "tdks_set_state": [vp, vp, C.c_size_t],
     }
@@ -226,7 +228,7 @@ class Context:
     complex64 (f32), on the current CUDA device."""
 
     def __init__(self, system, precision="f64", hartree=True, xc=True, pc=True, stream=None, ncell=1,
-                 obs_at_start=False):
+                 obs_at_start=False, mbj_c=None):
         import torch
         lib = load_library()
         self.lib = lib
@@ -254,6 +256,8 @@ class Context:
                              kw.ctypes.data_as(C.POINTER(C.c_double)), len(kw), int(system.norb),
                              C.byref(opts), C.c_void_p(stream.cuda_stream), C.byref(ctx)))
         self.ctx = ctx
+        if mbj_c is not None:
+            self.set_mbj(mbj_c)
         f = getattr(system, "field", None)
         if f is not None and f.kind == "table":
             self.set_field_table(f.table, f.t0, f.dt_table)
@@ -306,6 +310,16 @@ class Context:
         at t0) or off (tdks_set_longitudinal)."""
         _check(self.lib.tdks_set_longitudinal(self.ctx, int(enable), _ptr(u, self.cdtype) if u is not None else None,
                                               float(t0)))
+
+    def set_mbj(self, c):
+        """TB-mBJ (xc = 3): c > 0 fixes c, c <= 0 forms it from the density (tdks_set_mbj)."""
+        _check(self.lib.tdks_set_mbj(self.ctx, float(c)))
+
+    def mbj_c(self):
+        """The c of the last TB-mBJ potential (tdks_mbj_c)."""
+        v = C.c_double()
+        _check(self.lib.tdks_mbj_c(self.ctx, C.byref(v)))
+        return v.value
 
     def longitudinal_A(self):
         """A'_ind at the end of the last step (tdks_longitudinal_read)."""

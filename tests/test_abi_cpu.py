@@ -45,7 +45,7 @@ def _init(lib, s, **kw):
     pr = T.ProjectorC(s.proj.E_s, s.proj.E_p, kw.get("r_cut", s.proj.r_cut), s.proj.width)
     kp = np.ascontiguousarray(np.asarray(s.kpts, np.float64).ravel())
     kwt = np.ascontiguousarray(np.asarray(kw.get("kw", s.kw), np.float64))
-    opts = T.Options(kw.get("precision", 0), 1, 1, 1, kw.get("ncell", 1), kw.get("obs_at_start", 0))
+    opts = T.Options(kw.get("precision", 0), 1, kw.get("xc", 1), 1, kw.get("ncell", 1), kw.get("obs_at_start", 0))
     ctx = C.c_void_p()
     st = lib.tdks_init(C.byref(g), C.byref(cell), atoms, len(s.atoms), C.byref(pr), 1,
                        kp.ctypes.data_as(C.POINTER(C.c_double)), kwt.ctypes.data_as(C.POINTER(C.c_double)),
@@ -63,12 +63,20 @@ def _init(lib, s, **kw):
     (dict(proj=5), "projector index"),
     (dict(ncell=-2), "ncell"),
     (dict(obs_at_start=3), "obs_at_start"),
+    (dict(xc=4), "xc must be"),
 ])
 def test_host_validation(lib, case, expect):
     s = W.tiny(periodic=True, n=(6, 6, 6), natom=1)
     st, msg = _init(lib, s, **case)
     assert st == 1, (st, msg)          # TDKS_EINVAL, returned before any device call
     assert expect in msg
+
+
+def test_mbj_needs_one_cell(lib):
+    """xc = 3 (TB-mBJ) with a batch of cells is refused before any device call (EUNSUPPORTED)."""
+    s = W.tiny(periodic=True, n=(6, 6, 6), natom=1)
+    st, msg = _init(lib, s, xc=3, ncell=2)
+    assert st == 6 and "TB-mBJ" in msg, (st, msg)
 
 
 def test_null_context_rejected(lib):

@@ -3,7 +3,7 @@
 The Hartree-exchange-correlation potential of a density on periodic and isolated grids (both
 Hartree paths: the three-launch plane solve and the five line passes), the allocation-free entry
 point with xc = 2, five predictor-corrector steps with correlation on, and the rejection of
-xc values outside 0..2."""
+xc values outside 0..3 (3 is TB-mBJ, tested on its own)."""
 import ctypes as C
 
 import numpy as np
@@ -91,5 +91,5 @@ def test_pc_steps_with_correlation(name):
 def test_xc_option_range():
     from paper_1804_01404_gb300.tdks import Context, TdksError
     with pytest.raises(TdksError) as e:
-        Context(SYSTEMS["periodic-16"], precision="f64", xc=3)
+        Context(SYSTEMS["periodic-16"], precision="f64", xc=4)
     assert "xc" in str(e.value)

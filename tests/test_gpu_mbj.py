@@ -1,0 +1,140 @@
+"""TB-mBJ exchange on the GPU (tdks_options.xc = 3, tdks_set_mbj) against the oracle.
+
+The potential of a set of orbitals (c fixed and c from the density; periodic with several
+k-points, a 16^3 cell with several orbital chunks, a ragged isolated box), predictor-corrector
+steps in FP64 and FP32 (the predictor's own orbitals feed the predicted potential), the tiled
+path of large isolated grids, the ground state with TB-mBJ, and the argument checks."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import tdks_oracle as O
+from paper_1804_01404_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def _systems():
+    a = W.tiny(periodic=True, n=(6, 7, 8), natom=2, nk=2, norb=2)
+    a.field = W.Field("pulse", (0.0, 0.0, 0.03), 0.4, 5.0, 0.0)
+    b = W.small_periodic()
+    c = W.tiny(periodic=False, n=(7, 9, 11), natom=2, norb=2)
+    return {"periodic-2k": a, "periodic-16": b, "isolated-ragged": c}
+
+
+SYSTEMS = _systems()
+
+
+def _dev(psi, precision="f64"):
+    return torch.from_numpy(np.ascontiguousarray(psi)).to(
+        "cuda", torch.complex128 if precision == "f64" else torch.complex64)
+
+
+@pytest.mark.parametrize("name", list(SYSTEMS))
+@pytest.mark.parametrize("cval", [None, 0.93])
+def test_mbj_potential(name, cval):
+    from paper_1804_01404_gb300.tdks import Context
+    s = SYSTEMS[name]
+    psi = W.initial_orbitals(s, 2)
+    ctx = Context(s, precision="f64", xc=3, mbj_c=cval)
+    ctx.update_potential(_dev(psi))
+    got = ctx.grid_array(1).cpu().numpy()
+    rho = O.density(s, psi)
+    ref = O.hxc(s, rho, True, 3, psi, cval)
+    assert np.max(np.abs(got - ref)) < 1e-10 * np.max(np.abs(ref))
+    # the mBJ exchange is really there: it differs from the LDA exchange by far more than the tolerance
+    assert np.max(np.abs(ref - O.hxc(s, rho, True, 2))) > 1e-2 * np.max(np.abs(ref))
+    c_ref = cval if cval is not None else O.mbj_c(s, rho)
+    assert abs(ctx.mbj_c() - c_ref) < 1e-12 * c_ref
+    ctx.close()
+
+
+@pytest.mark.parametrize("name", ["periodic-2k", "isolated-ragged"])
+@pytest.mark.parametrize("precision,tol", [("f64", 1e-10), ("f32", 1e-4)])
+def test_mbj_pc_steps(name, precision, tol):
+    from paper_1804_01404_gb300.tdks import Context
+    s = SYSTEMS[name]
+    psi0 = W.initial_orbitals(s, 3)
+    if not s.periodic:
+        psi0 = O.apply_kick(s, psi0, (0.0, 0.0, 0.05))
+    n = 4
+    ref, vref, _ = O.run(s, psi0, n, xc_on=3)
+    ctx = Context(s, precision=precision, xc=3)
+    u = _dev(psi0, precision)
+    ctx.update_potential(u)
+    t = 0.0
+    for _ in range(n):
+        ctx.step(u, t, s.dt)
+        t += s.dt
+    ctx.check()
+    got = u.cpu().numpy().astype(np.complex128)
+    assert np.linalg.norm(got - ref) < tol * np.linalg.norm(ref)
+    assert np.max(np.abs(ctx.grid_array(1).cpu().numpy() - vref)) < 10 * tol * np.max(np.abs(vref))
+    # the TB-mBJ run differs from the LDA one by far more than the tolerance
+    ref2, _, _ = O.run(s, psi0, n, xc_on=2)
+    assert np.linalg.norm(ref2 - ref) > 100 * tol * np.linalg.norm(ref)
+    ctx.close()
+
+
+def test_mbj_tiled_steps():
+    """Large isolated grid (tile kernels): the predictor's orbitals come from the tiled Horner
+    stages; two PC steps with c fixed against the oracle."""
+    from paper_1804_01404_gb300.tdks import Context
+    s = W.isolated_cluster(n=24, natom=5, norb=3, radius=3.5, seed=4)
+    s.n = (40, 30, 28)
+    s.h = (0.45, 0.5, 0.55)
+    psi0 = O.apply_kick(s, W.initial_orbitals(s, 3), (0.0, 0.0, 0.01))
+    ref, vref, _ = O.run(s, psi0, 2, xc_on=3, mbj_c=1.1)
+    ctx = Context(s, precision="f64", xc=3, mbj_c=1.1)
+    ctx.tile_variant()                               # raises unless the context uses the tile kernels
+    u = _dev(psi0)
+    ctx.update_potential(u)
+    t = 0.0
+    for _ in range(2):
+        ctx.step(u, t, s.dt)
+        t += s.dt
+    ctx.check()
+    got = u.cpu().numpy()
+    assert np.linalg.norm(got - ref) < 1e-10 * np.linalg.norm(ref)
+    assert np.max(np.abs(ctx.grid_array(1).cpu().numpy() - vref)) < 1e-9 * np.max(np.abs(vref))
+    ctx.close()
+
+
+def test_mbj_ground_state():
+    """The self-consistent ground state with TB-mBJ exchange (c from the density at every
+    iteration) against the oracle's dense SCF."""
+    from paper_1804_01404_gb300.tdks import Context
+    s = W.tiny(periodic=True, n=(6, 6, 6), natom=1, nk=1, norb=2)
+    s.field = W.Field("none")
+    psi_ref, eig_ref, v_ref, _ = O.ground_state(s, xc_on=3, tol=1e-11)
+    ctx = Context(s, precision="f64", xc=3)
+    u = _dev(W.initial_orbitals(s, 7))
+    its, resid, eband = ctx.ground_state(u, max_iter=20000, tol=1e-9)
+    ctx.check()
+    assert resid < 1e-9 and its < 20000, (its, resid)
+    rho_ref = O.density(s, psi_ref)
+    assert np.max(np.abs(ctx.grid_array(2).cpu().numpy() - rho_ref)) < 1e-7 * rho_ref.max()
+    assert np.max(np.abs(ctx.grid_array(1).cpu().numpy() - v_ref)) < 1e-7 * np.max(np.abs(v_ref))
+    eb_ref = float(np.sum(2.0 * np.asarray(s.kw)[:, None] * eig_ref))
+    assert abs(eband - eb_ref) < 1e-7 * abs(eb_ref)
+    ctx.close()
+
+
+def test_mbj_argument_checks():
+    from paper_1804_01404_gb300.tdks import Context, TdksError
+    s = SYSTEMS["periodic-2k"]
+    ctx = Context(s, precision="f64", xc=2)
+    with pytest.raises(TdksError) as e:
+        ctx.set_mbj(1.0)
+    assert e.value.status == 6                       # TDKS_EUNSUPPORTED
+    with pytest.raises(TdksError):
+        ctx.mbj_c()
+    ctx.close()
+    ctx = Context(s, precision="f64", xc=3)
+    with pytest.raises(TdksError) as e:
+        ctx.set_mbj(math.nan)
+    assert e.value.status == 1                       # TDKS_EINVAL
+    ctx.set_mbj(0.0)                                  # back to c from the density
+    ctx.close()
