@@ -604,6 +604,39 @@ def workload_steps(dev, warmup=2, steps=5):
     ctx.close()
     del u
     torch.cuda.empty_cache()
+
+    # TB-mBJ exchange on the diamond crystal: PC steps with the LDA and with TB-mBJ (c from the
+    # density), same orbitals; the difference of the hartree_xc phase is the mBJ kernels' cost
+    s = W.diamond_crystal()
+    u0 = smooth_random_orbitals((s.nk, s.norb, s.n[2], s.n[1], s.n[0]), s.dV, dev, seed=5)
+    res = {}
+    for xc in (2, 3):
+        u = u0.clone()
+        ctx = Context(s, precision="f32", xc=xc, obs_at_start=True)
+        ctx.update_potential(u)
+        tt = [0.0]
+
+        def pc_step():
+            ctx.step(u, tt[0], s.dt)
+            tt[0] += s.dt
+        ms, st = run(ctx, pc_step, f"diamond_xc{xc}_steps")
+        res[xc] = (ms, {k: v / steps for k, v in st["ms"].items()}, st["launches"] / steps)
+        ctx.close()
+        del u
+    opts = s.npts * s.nk * s.norb
+    mbj_ms = res[3][1].get("hartree_xc", 0.0) - res[2][1].get("hartree_xc", 0.0)
+    out["diamond_mbj"] = {
+        "workload": "diamond crystal 20^3, 8 atoms, 16 orbitals x 64 k, FP32 orbitals, predictor-corrector "
+                    "steps with LDA (xc = 2) and with TB-mBJ exchange (xc = 3, c from the density)",
+        "steps_timed": steps, "warmup": warmup,
+        "ms_per_step_lda": res[2][0], "ms_per_step_mbj": res[3][0],
+        "phase_ms_per_step_mbj": res[3][1], "launches_per_step_mbj": res[3][2],
+        "mbj_kernels_ms_per_step": mbj_ms,
+        "mbj_orbital_read_GBps": 2 * 8 * opts / max(mbj_ms * 1e-3, 1e-12) / 1e9,
+        "note": "two potentials per PC step; each reads every orbital once (8 B per orbital-point) in the "
+                "kinetic-density pass; the rate divides those bytes by the time of all three mBJ kernels"}
+    del u0
+    torch.cuda.empty_cache()
     return out
 
 
