@@ -698,6 +698,39 @@ def ground_state(s, hartree_on=True, xc_on=True, mix=0.3, tol=1e-10, max_iter=40
     return psi, eig, vout, max_iter
 
 
+def orbital_energies(s, tabs, V, psi, Ap=None):
+    """Orbital energies of the ground-state outputs (Sec. 2.1: discrete orbital energies of isolated
+    systems, energy bands of periodic ones): the Ritz values of H_q, q = k + A' (Ap None: A' = 0), in
+    the span of each k's orbitals -- the eigenvalues of M z = e S z with M_ij = <u_i|H_q|u_j>,
+    S_ij = <u_i|u_j> -- ascending, [nk][norb], and the Ritz vectors (the orbitals rotated into
+    S-orthonormal eigenvectors of the projected problem).  For eigenvectors of H_q the Ritz values are
+    their eigenvalues.  scipy.linalg.eigh solves the small generalised problem."""
+    from scipy.linalg import eigh
+    eps = np.zeros((s.nk, s.norb))
+    rot = np.empty_like(psi)
+    for ik in range(s.nk):
+        q = np.asarray(s.kpts[ik], np.float64) + (np.zeros(3) if Ap is None else np.asarray(Ap, np.float64))
+        U = psi[ik].reshape(s.norb, -1)
+        HU = hpsi(s, tabs, V, q, psi[ik]).reshape(s.norb, -1)
+        M = U.conj() @ HU.T * s.dV
+        S = U.conj() @ U.T * s.dV
+        e, Z = eigh(0.5 * (M + M.conj().T), 0.5 * (S + S.conj().T))
+        eps[ik] = e
+        rot[ik] = (Z.T @ U).reshape(psi[ik].shape)
+    return eps, rot
+
+
+def dos(eps, kw, E, sigma):
+    """Density of states (Sec. 2.1 ground-state outputs), spin-saturated, with a Gaussian of width
+    sigma for every level: D(E) = sum_k w_k sum_n 2 exp(-(E - e_nk)^2 / (2 sigma^2)) / (sigma sqrt(2 pi))."""
+    E = np.asarray(E, np.float64)
+    out = np.zeros_like(E)
+    for ik in range(len(kw)):
+        for e in np.asarray(eps[ik], np.float64):
+            out += 2.0 * kw[ik] * np.exp(-0.5 * ((E - e) / sigma) ** 2) / (sigma * math.sqrt(2.0 * np.pi))
+    return out
+
+
 def excited_pairs(s, psi, psi_gs):
     """Number density of excited electron-hole pairs: (1/Omega) sum_k w_k 2 (norb - sum_{m,n}
     |<phi_km|psi_kn>|^2), the occupied weight outside the ground-state subspace."""

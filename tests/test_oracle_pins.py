@@ -770,3 +770,47 @@ def test_excited_pairs_closed_form():
     c, sn = np.cos(0.4), np.sin(0.4)
     mixed[0, 0], mixed[0, 1] = c * psi[0, 0] + sn * psi[0, 1], -sn * psi[0, 0] + c * psi[0, 1]
     assert abs(O.excited_pairs(s, mixed, psi)) < 1e-12
+
+
+# ---------------------------------------------------------------- orbital energies and DOS
+def test_orbital_energies_of_mixed_plane_waves():
+    """V = 0, no projectors: any invertible (non-unitary) mixture of plane waves spans the same space,
+    so its Ritz values are the plane waves' closed-form eigenvalues, and the Ritz vectors are
+    orthonormal eigenvectors.  A dropped overlap matrix S (or a transposed mixing) fails this."""
+    s = _no_atoms(W.tiny(periodic=True, n=(8, 10, 12), norb=4, nk=1))
+    x, y, z = O.coords(s)
+    q = np.array([0.31, -0.17, 0.23])
+    s.kpts = q[None]
+    V = np.zeros((12, 10, 8))
+    waves, lams = [], []
+    for m in ((0, 0, 0), (1, 0, 0), (0, -1, 1), (2, 1, -1)):
+        G = [2 * np.pi * m[a] / (s.n[a] * s.h[a]) for a in range(3)]
+        waves.append(np.exp(1j * (G[0] * x[None, None, :] + G[1] * y[None, :, None] + G[2] * z[:, None, None])))
+        lam = 0.5 * q @ q
+        for a in range(3):
+            h = s.h[a]
+            lam += -(0.5 / h ** 2) * (O.FD2[0] + 2 * sum(O.FD2[k] * math.cos(k * G[a] * h) for k in range(1, 5)))
+            lam += q[a] * (2.0 / h) * sum(O.FD1[k - 1] * math.sin(k * G[a] * h) for k in range(1, 5))
+        lams.append(lam)
+    rng = np.random.default_rng(5)
+    mix = rng.normal(size=(4, 4)) + 1j * rng.normal(size=(4, 4)) + 3 * np.eye(4)
+    psi = np.einsum("ij,jzyx->izyx", mix, np.array(waves))[None]
+    eps, rot = O.orbital_energies(s, [], V, psi)
+    assert np.allclose(eps[0], np.sort(lams), rtol=1e-11, atol=1e-11)
+    R = rot[0].reshape(4, -1)
+    assert np.allclose(R.conj() @ R.T * s.dV, np.eye(4), atol=1e-11)
+    for n in range(4):
+        hu = O.hpsi(s, [], V, q, rot[0, n])
+        assert np.max(np.abs(hu - eps[0, n] * rot[0, n])) < 1e-10 * np.max(np.abs(rot[0, n]))
+
+
+def test_dos_integral_and_peak():
+    """The DOS integrates to the electron count 2 sum_k w_k norb, and an isolated level of weight w
+    peaks at 2 w / (sigma sqrt(2 pi))."""
+    eps = np.array([[-0.5, -0.2, 0.1], [-0.45, 0.0, 0.3]])
+    kw = np.array([0.25, 0.75])
+    E = np.linspace(-2.0, 2.0, 40001)
+    d = O.dos(eps, kw, E, 0.02)
+    assert abs(np.trapezoid(d, E) - 6.0) < 1e-9
+    one = O.dos(np.array([[0.7]]), np.array([1.0]), np.array([0.7]), 0.05)
+    assert abs(one[0] - 2.0 / (0.05 * math.sqrt(2 * math.pi))) < 1e-12
