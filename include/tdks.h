@@ -171,6 +171,18 @@ tdks_status tdks_ground_state(tdks_ctx* ctx, void* u, int max_iter, double tol, 
  * use Omega = the box volume.  Errors: EINVAL for NULL arguments; EUNSUPPORTED for ncell > 1. */
 tdks_status tdks_excited_pairs(tdks_ctx* ctx, const void* u, const void* u_gs, double* n_eh);
 
+/* Orbital energies (Sec. 2.1 ground-state outputs: discrete orbital energies of an isolated system,
+ * energy bands at the k-points of a periodic one): for every k, the Ritz values of
+ * H_q = T_q + V_loc + V_Hxc(t) + V_NL^q, q = k + Ap (Ap NULL: A' = 0), in the span of that k's orbitals
+ * u (device, [nk][norb][nz][ny][nx], need not be orthonormal) -- the eigenvalues e of
+ * M z = e S z, M_ij = <u_i|H_q|u_j> dV, S_ij = <u_i|u_j> dV (overlaps on the GPU, the norb x norb
+ * problem on the host: Cholesky of S, Jacobi rotations of L^{-1} M L^{-H}).  eps: host [nk][norb],
+ * ascending per k.  rotate = 1 also replaces u by the Ritz vectors (orthonormal, eigenvectors of the
+ * projected problem; after tdks_ground_state these are the Kohn-Sham orbitals).  Synchronises.
+ * Errors: EINVAL for NULL arguments, rotate outside 0..1, linearly dependent orbitals or no
+ * potential yet; EUNSUPPORTED for ncell > 1 or norb > 64. */
+tdks_status tdks_orbital_energies(tdks_ctx* ctx, void* u, const double Ap[3], int rotate, double* eps);
+
 /* TB-mBJ exchange (xc = 3), the published Becke-Roussel / Becke-Johnson / Tran-Blaha forms per spin
  * channel of the unpolarised system (rho_s = rho/2, t_s = tau~/2):
  *   v_x = c v_BR + (3c - 2) (1/pi) sqrt(5/12) sqrt(2 t_s / rho_s),
@@ -432,6 +444,14 @@ tdks_status tdks_hxc_noalloc(const tdks_grid* grid, const double* rho_dev, doubl
  * strength makes the distribution positive and its integral over E the f-sum); xbar = 0. */
 tdks_status tdks_oscillator_strength(const double* d, int nt, double dt, double kappa, const double* E,
                                      int nE, double* dfdE, void* stream);
+
+/* Density of states (Sec. 2.1 ground-state outputs), spin-saturated, each level broadened by a
+ * normalised Gaussian of width sigma: dos[j] = sum_k kw[k] sum_n 2 exp(-(E_j - eps[k][n])^2 /
+ * (2 sigma^2)) / (sigma sqrt(2 pi)).  eps: [nk][norb] (tdks_orbital_energies), kw[nk], E[nE]; host
+ * arrays, FP64 on the GPU, synchronous on `stream`.  Errors: EINVAL for a null array, nk * norb or nE
+ * outside 1..2^24, sigma <= 0. */
+tdks_status tdks_dos(const double* eps, int nk, int norb, const double* kw, const double* E, int nE, double sigma,
+                     double* dos, void* stream);
 
 /* Conductivity and dielectric function, Sec. 4.1 Eq. (sigma_ft):
  * sigma[2j], sigma[2j+1] = Re, Im of -(c / A0) F(w_j) = -F(w_j) / Ap0 for the current series I[nt]

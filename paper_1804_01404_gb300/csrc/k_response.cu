@@ -11,6 +11,8 @@
 //   * Sec. 4.1: the work done by the field per unit volume, W(t) = int_0^t I(t').E(t') dt' (the
 //     electronic excitation energy per volume when the xc potential derives from an energy
 //     functional), as a cumulative trapezoid sum.
+//   * Sec. 2.1 ground-state outputs: the density of states of a set of orbital energies, Gaussian
+//     broadened.
 // FP64 throughout.
 #include <cuda_runtime.h>
 
@@ -139,6 +141,25 @@ __global__ void __launch_bounds__(kScanThreads) k_work(const double* __restrict_
   }
 }
 
+// D(E_j) = sum_k w_k sum_n 2 g(E_j - e_nk), g the normalised Gaussian of width sigma; one thread per
+// energy, levels in fixed order.
+__global__ void k_dos(const double* __restrict__ eps, int nk, int norb, const double* __restrict__ kw,
+                      const double* __restrict__ E, int nE, double sigma, double* __restrict__ D) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nE) return;
+  const double e = E[j], inv = 1.0 / sigma, norm = 2.0 * inv / sqrt(2.0 * 3.14159265358979323846);
+  double acc = 0.0;
+  for (int k = 0; k < nk; ++k) {
+    double sk = 0.0;
+    for (int n = 0; n < norb; ++n) {
+      const double x = (e - eps[k * norb + n]) * inv;
+      sk += exp(-0.5 * x * x);
+    }
+    acc += kw[k] * sk;
+  }
+  D[j] = norm * acc;
+}
+
 tdks_status rfail(tdks_status s, const char* msg) {
   set_last_error(msg);
   return s;
@@ -201,6 +222,7 @@ tdks_status check_series(const double* x, int nt, double dt, const double* w, in
 }  // namespace tdks
 
 using tdks::check_series;
+using tdks::k_dos;
 using tdks::k_work;
 using tdks::masked_response;
 using tdks::rfail;
@@ -251,5 +273,40 @@ extern "C" tdks_status tdks_work(const double* I, const double* E, int nt, doubl
   cudaFree(dW);
   if (e != cudaSuccess) return rfail(e == cudaErrorMemoryAllocation ? TDKS_ENOMEM : TDKS_ECUDA,
                                      (std::string("tdks_work: ") + cudaGetErrorString(e)).c_str());
+  return TDKS_OK;
+}
+
+extern "C" tdks_status tdks_dos(const double* eps, int nk, int norb, const double* kw, const double* E, int nE,
+                                double sigma, double* dos, void* stream) {
+  if (!eps || !kw || !E || !dos) return rfail(TDKS_EINVAL, "tdks_dos: null array");
+  if (nk < 1 || norb < 1 || (long long)nk * norb > (1LL << 24)) return rfail(TDKS_EINVAL, "tdks_dos: nk * norb outside 1..2^24");
+  if (nE < 1 || nE > (1 << 24)) return rfail(TDKS_EINVAL, "tdks_dos: nE outside 1..2^24");
+  if (!(sigma > 0.0) || !std::isfinite(sigma)) return rfail(TDKS_EINVAL, "tdks_dos: sigma must be positive");
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t be = sizeof(double) * (size_t)nk * norb, bk = sizeof(double) * (size_t)nk, bE = sizeof(double) * (size_t)nE;
+  double *de = nullptr, *dk = nullptr, *dE = nullptr, *dD = nullptr;
+  cudaError_t e = cudaSuccess;
+  auto chk = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+  chk(cudaMalloc(&de, be));
+  chk(cudaMalloc(&dk, bk));
+  chk(cudaMalloc(&dE, bE));
+  chk(cudaMalloc(&dD, bE));
+  if (e == cudaSuccess) {
+    chk(cudaMemcpyAsync(de, eps, be, cudaMemcpyHostToDevice, s));
+    chk(cudaMemcpyAsync(dk, kw, bk, cudaMemcpyHostToDevice, s));
+    chk(cudaMemcpyAsync(dE, E, bE, cudaMemcpyHostToDevice, s));
+  }
+  if (e == cudaSuccess) {
+    k_dos<<<(nE + 255) / 256, 256, 0, s>>>(de, nk, norb, dk, dE, nE, sigma, dD);
+    chk(cudaGetLastError());
+  }
+  if (e == cudaSuccess) chk(cudaMemcpyAsync(dos, dD, bE, cudaMemcpyDeviceToHost, s));
+  if (e == cudaSuccess) chk(cudaStreamSynchronize(s));
+  cudaFree(de);
+  cudaFree(dk);
+  cudaFree(dE);
+  cudaFree(dD);
+  if (e != cudaSuccess) return rfail(e == cudaErrorMemoryAllocation ? TDKS_ENOMEM : TDKS_ECUDA,
+                                     (std::string("tdks_dos: ") + cudaGetErrorString(e)).c_str());
   return TDKS_OK;
 }

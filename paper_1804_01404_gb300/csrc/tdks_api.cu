@@ -8,6 +8,7 @@
 #include <string>
 #include <vector>
 
+#include "herm_eig.h"
 #include "tdks_internal.h"
 
 using namespace tdks;
@@ -1105,6 +1106,97 @@ tdks_status tdks_excited_pairs(tdks_ctx* c, const void* u, const void* u_gs, dou
   }
   *n_eh = n / c->omega;
   return TDKS_OK;
+}
+
+tdks_status tdks_orbital_energies(tdks_ctx* c, void* u, const double Ap[3], int rotate, double* eps) {
+  TDKS_TRY(check_ctx(c));
+  if (!u || !eps) return fail(TDKS_EINVAL, "null argument");
+  if (rotate != 0 && rotate != 1) return fail(TDKS_EINVAL, "rotate must be 0 or 1");
+  if (c->ncell != 1) return fail(TDKS_EUNSUPPORTED, "tdks_orbital_energies needs ncell = 1");
+  if (c->norb > 64) return fail(TDKS_EUNSUPPORTED, "tdks_orbital_energies handles at most 64 orbitals per k-point");
+  if (!c->have_potential) return fail(TDKS_EINVAL, "call tdks_update_potential or tdks_ground_state first");
+  const int nk = c->nk, no = c->norb, np = c->npts;
+  const bool f32 = is_f32(c);
+  const size_t nob = (size_t)nk * no * np * (f32 ? sizeof(float2) : sizeof(double2)), nmat = (size_t)nk * no * no;
+  const double zeroA[3] = {0.0, 0.0, 0.0};
+  void* HU = nullptr;
+  double2 *dM = nullptr, *dS = nullptr;
+  cudaError_t e = cudaSuccess;
+  auto chk = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+  chk(cudaMalloc(&HU, nob));
+  chk(cudaMalloc(&dM, nmat * sizeof(double2)));
+  chk(cudaMalloc(&dS, nmat * sizeof(double2)));
+  auto cleanup = [&]() {
+    cudaStreamSynchronize(c->stream);
+    cudaFree(HU); cudaFree(dM); cudaFree(dS);
+  };
+  if (e != cudaSuccess) { cleanup(); return fail(TDKS_ENOMEM, "tdks_orbital_energies: device memory"); }
+  auto run = [&]() -> tdks_status {
+    std::vector<double2> hM(nmat), hS(nmat), hX(nmat), hZ(nmat);
+    TDKS_TRY(set_step_potential(c, 1.0, nullptr, 0.0));
+    TDKS_TRY(orbital_kernel(c, 0, u, HU, Ap ? Ap : zeroA, 0.0, nullptr, 1));       // H_q u
+    if (f32) {
+      TDKS_CUDA(launch_gram<float>((const float2*)u, (const float2*)HU, nk, no, np, c->dV, dM, c->stream));
+      TDKS_CUDA(launch_gram<float>((const float2*)u, (const float2*)u, nk, no, np, c->dV, dS, c->stream));
+    } else {
+      TDKS_CUDA(launch_gram<double>((const double2*)u, (const double2*)HU, nk, no, np, c->dV, dM, c->stream));
+      TDKS_CUDA(launch_gram<double>((const double2*)u, (const double2*)u, nk, no, np, c->dV, dS, c->stream));
+    }
+    c->launches += 2;
+    TDKS_CUDA(cudaMemcpyAsync(hM.data(), dM, nmat * sizeof(double2), cudaMemcpyDeviceToHost, c->stream));
+    TDKS_CUDA(cudaMemcpyAsync(hS.data(), dS, nmat * sizeof(double2), cudaMemcpyDeviceToHost, c->stream));
+    TDKS_CUDA(cudaStreamSynchronize(c->stream));
+    using Zc = std::complex<double>;
+    for (int k = 0; k < nk; ++k) {
+      // S = L L^H, X = L^{-H}: the projected problem M z = e S z becomes A y = e y with A = X^H M X, z = X y
+      const size_t o = (size_t)k * no * no;
+      if (!cholesky_inverse_h(&hS[o], no, &hX[o]))
+        return fail(TDKS_EINVAL, "tdks_orbital_energies: the orbitals are linearly dependent");
+      std::vector<Zc> X((size_t)no * no), MX((size_t)no * no), A((size_t)no * no), Y;
+      for (size_t i = 0; i < (size_t)no * no; ++i) X[i] = Zc(hX[o + i].x, hX[o + i].y);
+      for (int i = 0; i < no; ++i)
+        for (int j = 0; j < no; ++j) {
+          Zc sacc = 0.0;
+          for (int l = 0; l < no; ++l) sacc += Zc(hM[o + (size_t)i * no + l].x, hM[o + (size_t)i * no + l].y) * X[(size_t)l * no + j];
+          MX[(size_t)i * no + j] = sacc;
+        }
+      for (int i = 0; i < no; ++i)
+        for (int j = 0; j < no; ++j) {
+          Zc sacc = 0.0;
+          for (int l = 0; l < no; ++l) sacc += std::conj(X[(size_t)l * no + i]) * MX[(size_t)l * no + j];
+          A[(size_t)i * no + j] = sacc;
+        }
+      for (int i = 0; i < no; ++i)                                               // symmetrise the rounding
+        for (int j = i + 1; j < no; ++j) {
+          const Zc m = 0.5 * (A[(size_t)i * no + j] + std::conj(A[(size_t)j * no + i]));
+          A[(size_t)i * no + j] = m;
+          A[(size_t)j * no + i] = std::conj(m);
+        }
+      std::vector<double> w;
+      herm_eig(A, no, w, Y);
+      for (int n = 0; n < no; ++n) eps[(size_t)k * no + n] = w[n];
+      for (int i = 0; i < no; ++i)                                               // Z = X Y
+        for (int j = 0; j < no; ++j) {
+          Zc sacc = 0.0;
+          for (int l = 0; l < no; ++l) sacc += X[(size_t)i * no + l] * Y[(size_t)l * no + j];
+          hZ[o + (size_t)i * no + j] = double2{sacc.real(), sacc.imag()};
+        }
+    }
+    if (rotate) {   // u_j <- sum_i u_i Z_ij through the work buffer
+      TDKS_CUDA(cudaMemcpyAsync(dM, hZ.data(), nmat * sizeof(double2), cudaMemcpyHostToDevice, c->stream));
+      if (f32)
+        TDKS_CUDA(launch_basis<float>((const float2*)u, nullptr, dM, nk, no, np, 0.0, 0.0, 1.0, (float2*)HU, c->stream));
+      else
+        TDKS_CUDA(launch_basis<double>((const double2*)u, nullptr, dM, nk, no, np, 0.0, 0.0, 1.0, (double2*)HU,
+                                       c->stream));
+      TDKS_CUDA(cudaMemcpyAsync(u, HU, nob, cudaMemcpyDeviceToDevice, c->stream));
+      c->launches += 1;
+    }
+    return TDKS_OK;
+  };
+  const tdks_status st = run();
+  cleanup();
+  return st;
 }
 
 tdks_status tdks_set_mbj(tdks_ctx* c, double cval) {

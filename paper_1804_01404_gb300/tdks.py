@@ -125,12 +125,15 @@ def load_library(path: str = LIB_PATH):
         "tdks_conductivity": [C.POINTER(C.c_double), i, d, d, C.POINTER(C.c_double), i, i,
                               C.POINTER(C.c_double), C.POINTER(C.c_double), vp],
         "tdks_work": [C.POINTER(C.c_double), C.POINTER(C.c_double), i, d, C.POINTER(C.c_double), vp],
+        "tdks_dos": [C.POINTER(C.c_double), i, i, C.POINTER(C.c_double), C.POINTER(C.c_double), i, d,
+                     C.POINTER(C.c_double), vp],
         "tdks_field_at": [vp, d, C.POINTER(C.c_double), C.POINTER(C.c_double)],
         "tdks_set_longitudinal": [vp, i, vp, d],
         "tdks_ground_state": [vp, vp, i, d, d, d, C.POINTER(C.c_double)],
         "tdks_excited_pairs": [vp, vp, vp, C.POINTER(C.c_double)],
         "tdks_longitudinal_read": [vp, C.POINTER(C.c_double)],
         "tdks_set_mbj": [vp, d],
+        "tdks_orbital_energies": [vp, vp, C.POINTER(C.c_double), i, C.POINTER(C.c_double)],
         "tdks_mbj_c": [vp, C.POINTER(C.c_double)],
         "tdks_get_state": [vp, vp, C.c_size_t],
         "tdks_set_state": [vp, vp, C.c_size_t],
@@ -199,6 +202,21 @@ def work(I, E, dt, stream=None):
         raise ValueError("I and E need the same number of samples")
     out = np.zeros(len(I))
     _check(lib.tdks_work(_dptr(I), _dptr(E), len(I), float(dt), _dptr(out), _stream_handle(stream)))
+    return out
+
+
+def dos(eps, kw, E, sigma, stream=None):
+    """Gaussian-broadened, spin-saturated density of states of orbital energies eps[nk][norb] with
+    k-weights kw at energies E (tdks_dos)."""
+    lib = load_library()
+    eps = np.ascontiguousarray(eps, np.float64)
+    kw = np.ascontiguousarray(kw, np.float64)
+    E = np.ascontiguousarray(E, np.float64)
+    if eps.ndim != 2 or eps.shape[0] != len(kw):
+        raise ValueError("eps must be [nk][norb] with nk = len(kw)")
+    out = np.zeros(len(E))
+    _check(lib.tdks_dos(_dptr(eps), eps.shape[0], eps.shape[1], _dptr(kw), _dptr(E), len(E), float(sigma), _dptr(out),
+                        _stream_handle(stream)))
     return out
 
 
@@ -310,6 +328,15 @@ class Context:
         at t0) or off (tdks_set_longitudinal)."""
         _check(self.lib.tdks_set_longitudinal(self.ctx, int(enable), _ptr(u, self.cdtype) if u is not None else None,
                                               float(t0)))
+
+    def orbital_energies(self, u, Ap=None, rotate=False):
+        """Ritz values of H_q in the span of each k's orbitals, ascending, numpy [nk, norb]; rotate=True
+        also turns u into the Ritz vectors (tdks_orbital_energies)."""
+        eps = np.zeros((len(self.system.kw), self.system.norb))
+        ap = (C.c_double * 3)(*Ap) if Ap is not None else None
+        _check(self.lib.tdks_orbital_energies(self.ctx, _ptr(u, self.cdtype), ap, int(bool(rotate)),
+                                              eps.ctypes.data_as(C.POINTER(C.c_double))))
+        return eps
 
     def set_mbj(self, c):
         """TB-mBJ (xc = 3): c > 0 fixes c, c <= 0 forms it from the density (tdks_set_mbj)."""

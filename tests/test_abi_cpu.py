@@ -79,6 +79,15 @@ def test_mbj_needs_one_cell(lib):
     assert st == 6 and "TB-mBJ" in msg, (st, msg)
 
 
+def test_dos_argument_checks(lib):
+    """tdks_dos rejects a non-positive width and empty arrays before any device call."""
+    d = np.zeros(3)
+    p = d.ctypes.data_as(C.POINTER(C.c_double))
+    assert lib.tdks_dos(p, 1, 3, p, p, 3, 0.0, p, None) == 1
+    assert lib.tdks_dos(p, 0, 3, p, p, 3, 0.1, p, None) == 1
+    assert lib.tdks_dos(None, 1, 3, p, p, 3, 0.1, p, None) == 1
+
+
 def test_null_context_rejected(lib):
     assert lib.tdks_hpsi(None, None, None, (C.c_double * 3)()) == 1
     assert lib.tdks_step(None, None, 0.0, 0.02) == 1

@@ -1,6 +1,7 @@
 """Ground state on the GPU (tdks_ground_state) against the oracle's dense self-consistent solution:
 the occupied subspace (overlap with the oracle's states), the density, the band energy, and
-stationarity of the result under the GPU's own time steps."""
+stationarity of the result under the GPU's own time steps; the orbital energies (Ritz values and
+vectors, tdks_orbital_energies) and the density of states (tdks_dos)."""
 import numpy as np
 import pytest
 
@@ -83,4 +84,53 @@ def test_excited_pairs_after_a_pulse():
     n = ctx.excited_pairs(u, u_gs)
     ref = O.excited_pairs(s, u.cpu().numpy(), u_gs.cpu().numpy())
     assert abs(n - ref) < 1e-10 * abs(ref) and ref > 1e-8, (n, ref)
+    ctx.close()
+
+
+@pytest.mark.parametrize("name", ["periodic-2k", "isolated"])
+def test_orbital_energies_and_dos_of_the_ground_state(name):
+    """tdks_orbital_energies of the GPU ground state: the Ritz values equal the oracle's occupied
+    eigenvalues, the rotated orbitals are eigenvectors of the GPU's own H (H u = e u), and tdks_dos
+    of those energies equals the oracle's DOS."""
+    from paper_1804_01404_gb300 import tdks as T
+    s = SYSTEMS[name]
+    _, eig_ref, _, _ = O.ground_state(s, tol=1e-11)
+    ctx = T.Context(s, precision="f64")
+    u = torch.from_numpy(W.initial_orbitals(s, 7)).cuda()
+    ctx.ground_state(u, max_iter=20000, tol=1e-9)
+    eps = ctx.orbital_energies(u, rotate=True)
+    assert np.max(np.abs(eps - eig_ref)) < 1e-7 * np.max(np.abs(eig_ref))
+    hu = torch.empty_like(u)
+    ctx.hpsi(u, hu)
+    ctx.check()
+    for k in range(s.nk):
+        for n in range(s.norb):
+            r = (hu[k, n] - eps[k, n] * u[k, n]).abs().max().item()
+            assert r < 1e-6 * u[k, n].abs().max().item(), (k, n, r)
+    E = np.linspace(eps.min() - 0.5, eps.max() + 0.5, 777)
+    d = T.dos(eps, s.kw, E, 0.03)
+    assert np.max(np.abs(d - O.dos(eps, s.kw, E, 0.03))) < 1e-12 * np.max(d)
+    ctx.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("f64", 1e-10), ("f32", 2e-5)])
+def test_ritz_values_of_random_orbitals(precision, tol):
+    """Ritz values of non-orthonormal random orbitals under V_loc + V_Hxc and a nonzero A', against
+    the oracle's generalised eigenproblem; without rotation u is left unchanged."""
+    from paper_1804_01404_gb300.tdks import Context
+    s = W.tiny(periodic=True, n=(6, 7, 8), natom=2, nk=2, norb=3)
+    psi = W.initial_orbitals(s, 3)
+    psi = psi + 0.3 * np.roll(psi, 1, axis=1) * (1 + 0.5j)            # not orthonormal
+    Ap = np.array([0.05, -0.02, 0.04])
+    ctx = Context(s, precision=precision)
+    u = torch.from_numpy(psi).to("cuda", torch.complex128 if precision == "f64" else torch.complex64)
+    ctx.update_potential(u)
+    before = u.clone()
+    eps = ctx.orbital_energies(u, Ap=Ap)
+    assert torch.equal(u, before)
+    ctx.check()
+    got_psi = u.cpu().numpy().astype(np.complex128)
+    V = O.local_potential(s) + O.hxc(s, O.density(s, got_psi))
+    ref, _ = O.orbital_energies(s, O.projector_tables(s), V, got_psi, Ap)
+    assert np.max(np.abs(eps - ref)) < tol * np.max(np.abs(ref))
     ctx.close()
