@@ -514,18 +514,17 @@ def smooth_random_orbitals(shape, dV, dev, seed, passes=3):
     return (u / nrm).contiguous()
 
 
-def workload_steps(dev, warmup=2, steps=5):
+def workload_steps(dev, warmup=2, steps=5, which=("cluster", "multiscale", "mbj")):
     """Full steps of the two large workloads, timed over a few steps (CUDA events on the context
     stream) after warm-up:
       * isolated cluster: 96^3 grid (h = 0.4), 128 atoms, 256 orbitals, FP32, impulse kick,
         predictor-corrector with Hockney Hartree, tiled TMA stencil;
       * multiscale: 256 microscopic cells (16^3, 8 atoms, 16 orbitals x 8 k) on a 1D Maxwell grid
-        (dX = 250 bohr), one coupled step = TDKS PC step of every cell + current + Maxwell update.
+        (dX = 250 bohr), one coupled step = TDKS PC step of every cell + current + Maxwell update;
+      * TB-mBJ: PC steps of the diamond crystal with the LDA and with TB-mBJ exchange.
     "effective hpsi GB/s" = 2 Taylor steps x 4 H applications x 16 B per orbital-point / step time
     (the unfused-equivalent stream; it exceeds the HBM peak when orbitals stay on chip)."""
     import torch
-    from paper_1804_01404_gb300 import workloads as W
-    from paper_1804_01404_gb300.tdks import Context
     stream = torch.cuda.current_stream()
     out = {}
 
@@ -548,6 +547,20 @@ def workload_steps(dev, warmup=2, steps=5):
         ctx.check()
         return e0.elapsed_time(e1) / steps, st
 
+    if "cluster" in which:
+        out.update(_cluster_steps(dev, run, steps, warmup))
+    if "multiscale" in which:
+        out.update(_multiscale_steps(dev, run, steps, warmup))
+    if "mbj" in which:
+        out.update(_mbj_steps(dev, run, steps, warmup))
+    return out
+
+
+def _cluster_steps(dev, run, steps, warmup):
+    import torch
+    from paper_1804_01404_gb300 import workloads as W
+    from paper_1804_01404_gb300.tdks import Context
+    out = {}
     # isolated cluster
     s = W.isolated_cluster()
     u = smooth_random_orbitals((s.nk, s.norb, s.n[2], s.n[1], s.n[0]), s.dV, dev, seed=11)
@@ -572,7 +585,14 @@ def workload_steps(dev, warmup=2, steps=5):
     ctx.close()
     del u
     torch.cuda.empty_cache()
+    return out
 
+
+def _multiscale_steps(dev, run, steps, warmup):
+    import torch
+    from paper_1804_01404_gb300 import workloads as W
+    from paper_1804_01404_gb300.tdks import Context
+    out = {}
     # batched multiscale cells
     s = W.multiscale_cell()
     ncell, m0, dX = 256, 4, 250.0
@@ -604,7 +624,14 @@ def workload_steps(dev, warmup=2, steps=5):
     ctx.close()
     del u
     torch.cuda.empty_cache()
+    return out
 
+
+def _mbj_steps(dev, run, steps, warmup):
+    import torch
+    from paper_1804_01404_gb300 import workloads as W
+    from paper_1804_01404_gb300.tdks import Context
+    out = {}
     # TB-mBJ exchange on the diamond crystal: PC steps with the LDA and with TB-mBJ (c from the
     # density), same orbitals; the difference of the hartree_xc phase is the mBJ kernels' cost
     s = W.diamond_crystal()
@@ -717,9 +744,10 @@ def main():
     ap.add_argument("--skip-hpsi", action="store_true")
     ap.add_argument("--skip-workloads", action="store_true",
                     help="skip the few-step timings of the isolated cluster and multiscale workloads")
-    ap.add_argument("--only", default="", choices=["", "hpsi", "workloads"],
+    ap.add_argument("--only", default="", choices=["", "hpsi", "workloads", "mbj"],
                     help="hpsi: only the tdks_hpsi measurement on the isolated cluster (profiling); "
-                         "workloads: only the cluster and multiscale step timings")
+                         "workloads: only the cluster, multiscale and TB-mBJ step timings; mbj: only the "
+                         "TB-mBJ step timing of the diamond crystal")
     ap.add_argument("--hpsi-norb", type=int, default=256)
     ap.add_argument("--hpsi-reps", type=int, default=10)
     ap.add_argument("--cpu-steps", type=int, default=8)
@@ -737,6 +765,12 @@ def main():
         if rank == 0:
             print(json.dumps({"hpsi_cluster": hpsi_cluster(torch.device("cuda", local_rank),
                                                            reps=args.hpsi_reps, norb=args.hpsi_norb)}))
+        return 0
+    if args.only == "mbj":
+        import torch
+        torch.cuda.set_device(local_rank)
+        if rank == 0:
+            print(json.dumps({"other_workloads": workload_steps(torch.device("cuda", local_rank), which=("mbj",))}))
         return 0
     if args.only == "workloads":
         import torch
