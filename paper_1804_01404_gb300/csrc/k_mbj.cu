@@ -26,13 +26,19 @@ namespace tdks {
 
 namespace {
 
-constexpr int kMbjThreads = 256;
+constexpr int kMbjThreads = 128;          // k_tau, k_mbj_g
+constexpr int kBrThreads = 64;            // k_mbj_x: FP64-bound per SM, so spread over as many SMs as possible
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kRhoMin = 1e-10;
 constexpr double kGamma = 0.8, kAlpha = -0.012, kBeta = 1.023;
 
 struct Fd {   // the stencil's difference coefficients (kFD1, kFD2), passed by value
   double d1[4], d2[5];
+};
+
+template <typename T>
+struct D1h {  // first-derivative coefficients FD1[m] / h_a in the orbitals' precision, formed on the host
+  T c[3][4];
 };
 
 struct Nbr {   // linear indices of the 4 neighbours per side along each axis (-1: outside the box)
@@ -75,41 +81,46 @@ template <typename T>
 __global__ void __launch_bounds__(kMbjThreads) k_tau(const typename Cplx<T>::type* __restrict__ u, int nk, int norb,
                                                     int nx, int ny, int nz, int periodic,
                                                     const double* __restrict__ kpts, const double* __restrict__ kw,
-                                                    double hx, double hy, double hz, Fd fd, int ochunk,
-                                                    double* __restrict__ part) {
+                                                    D1h<T> d1, int ochunk, double* __restrict__ part) {
   using C = typename Cplx<T>::type;
   const int npts = nx * ny * nz;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= npts) return;
   const int ix = p % nx, iy = (p / nx) % ny, iz = p / (nx * ny);
   const Nbr nb = neighbours(ix, iy, iz, nx, ny, nz, periodic);
-  const double h[3] = {hx, hy, hz};
-  T d1[3][4];
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int m = 0; m < 4; ++m) d1[a][m] = (T)(fd.d1[m] / h[a]);
   const int o0 = blockIdx.y * ochunk, o1 = min(o0 + ochunk, nk * norb);
   T acc[5] = {0, 0, 0, 0, 0};
-  for (int o = o0; o < o1; ++o) {
+  // the orbitals of one k at a time: unweighted sums over them, weighted once per k (the weight and
+  // wave vector are converted once per k -- FP64 -> FP32 conversions run on the slow FP64 pipe), and
+  // a branch-free inner loop whose loads the compiler can overlap across orbitals
+  for (int o = o0; o < o1;) {
     const int k = o / norb;
-    const T w = (T)(2.0 * kw[k]);
-    const C* f = u + (size_t)o * npts;
-    const C c0 = f[p];
-    acc[0] += w * (c0.x * c0.x + c0.y * c0.y);
+    const int oe = min(o1, (k + 1) * norb);
+    const T q[3] = {(T)kpts[3 * k], (T)kpts[3 * k + 1], (T)kpts[3 * k + 2]};
+    T sk[5] = {0, 0, 0, 0, 0};
+#pragma unroll 2
+    for (; o < oe; ++o) {
+      const C* f = u + (size_t)o * npts;
+      const C c0 = f[p];
+      sk[0] += c0.x * c0.x + c0.y * c0.y;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const T q = (T)kpts[3 * k + a];
-      C g = C{-q * c0.y, q * c0.x};                                     // i q u
+      for (int a = 0; a < 3; ++a) {
+        C g = C{-q[a] * c0.y, q[a] * c0.x};                             // i q u
 #pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        const C fp = ld_or_zero(f, nb.p[a][m]), fm = ld_or_zero(f, nb.m[a][m]);
-        g.x += d1[a][m] * (fp.x - fm.x);
-        g.y += d1[a][m] * (fp.y - fm.y);
+        for (int m = 0; m < 4; ++m) {
+          const C fp = ld_or_zero(f, nb.p[a][m]), fm = ld_or_zero(f, nb.m[a][m]);
+          g.x += d1.c[a][m] * (fp.x - fm.x);
+          g.y += d1.c[a][m] * (fp.y - fm.y);
+        }
+        sk[1] += g.x * g.x + g.y * g.y;
+        sk[2 + a] += c0.x * g.y - c0.y * g.x;                           // Im(conj(u) g)
       }
-      acc[1] += T(0.5) * w * (g.x * g.x + g.y * g.y);
-      acc[2 + a] += w * (c0.x * g.y - c0.y * g.x);                     // Im(conj(u) g)
     }
+    const T w = (T)(2.0 * kw[k]);
+    acc[0] += w * sk[0];
+    acc[1] += T(0.5) * w * sk[1];
+#pragma unroll
+    for (int c = 2; c < 5; ++c) acc[c] += w * sk[c];
   }
 #pragma unroll
   for (int c = 0; c < 5; ++c) part[((size_t)blockIdx.y * 5 + c) * npts + p] = (double)acc[c];
@@ -159,37 +170,68 @@ __global__ void __launch_bounds__(kMbjThreads) k_mbj_g(const double* __restrict_
 // H(x) = x exp(-2x/3) - y (x - 2): the Becke-Roussel equation times (x - 2), one root per branch
 __device__ __forceinline__ double br_h(double x, double y) { return x * exp(-2.0 * x / 3.0) - y * (x - 2.0); }
 
+__device__ __forceinline__ float br_hf(float x, float y) { return x * __expf(-2.0f * x / 3.0f) - y * (x - 2.0f); }
+
 // Root x of x exp(-2x/3)/(x-2) = y: y < 0 in (0, 2) (H(0) = 2y < 0 < H(2)), y > 0 in (2, hi)
-// (H(2) > 0 > H(hi)).  34 bisection steps, then up to four Newton steps kept inside the bracket.
+// (H(2) > 0 > H(hi)).  The bracket is narrowed by bisection in FP32 (26 steps; FP64 arithmetic runs
+// at a small fraction of the FP32 rate on this GPU) and widened by a relative 1e-5 to cover the
+// FP32 rounding of H; FP64 Newton steps kept inside it then reach full precision.  Where y is
+// outside the FP32 range, or the widened bracket does not keep the signs of H, the bisection runs
+// in FP64 (34 steps) on the whole branch.
 __device__ double br_root(double y) {
-  double neg, pos;                    // H(neg) < 0 < H(pos)
-  if (y < 0.0) {
-    neg = 0.0;
-    pos = 2.0;
-  } else {
-    pos = 2.0;
-    neg = 4.0;
-    while (br_h(neg, y) > 0.0 && neg < 4096.0) neg *= 2.0;   // exp(-2x/3) underflows long before 4096
+  double neg = 0.0, pos = 0.0;        // H(neg) < 0 < H(pos)
+  bool have = false;
+  const double ay = fabs(y);
+  if (ay > 1e-30 && ay < 1e30) {
+    const float yf = (float)y;
+    float nf, pf;
+    if (yf < 0.0f) {
+      nf = 0.0f;
+      pf = 2.0f;
+    } else {
+      pf = 2.0f;
+      nf = 4.0f;
+      while (br_hf(nf, yf) > 0.0f && nf < 256.0f) nf *= 2.0f;   // y > 1e-30: the root is below 160
+    }
+    for (int it = 0; it < 26; ++it) {
+      const float mid = 0.5f * (nf + pf);
+      if (br_hf(mid, yf) < 0.0f) nf = mid; else pf = mid;
+    }
+    const double a = fmin((double)nf, (double)pf), b = fmax((double)nf, (double)pf);
+    const double pad = 1e-5 * b;
+    neg = y < 0.0 ? fmax(a - pad, 0.0) : b + pad;
+    pos = y < 0.0 ? fmin(b + pad, 2.0) : fmax(a - pad, 2.0);
+    have = br_h(neg, y) < 0.0 && br_h(pos, y) > 0.0;
   }
-  for (int it = 0; it < 34; ++it) {
-    const double mid = 0.5 * (neg + pos);
-    if (br_h(mid, y) < 0.0) neg = mid; else pos = mid;
+  if (!have) {
+    if (y < 0.0) {
+      neg = 0.0;
+      pos = 2.0;
+    } else {
+      pos = 2.0;
+      neg = 4.0;
+      while (br_h(neg, y) > 0.0 && neg < 4096.0) neg *= 2.0;   // exp(-2x/3) underflows long before 4096
+    }
+    for (int it = 0; it < 34; ++it) {
+      const double mid = 0.5 * (neg + pos);
+      if (br_h(mid, y) < 0.0) neg = mid; else pos = mid;
+    }
   }
   double x = 0.5 * (neg + pos);
   const double lo = fmin(neg, pos), hi = fmax(neg, pos);
-  for (int it = 0; it < 4; ++it) {
+  for (int it = 0; it < 5; ++it) {   // Newton, kept inside [lo, hi] (the root may sit at an end, x = 2)
     const double e = exp(-2.0 * x / 3.0);
     const double f = x * e - y * (x - 2.0), df = e * (1.0 - 2.0 * x / 3.0) - y;
     if (df == 0.0) break;
     const double xn = x - f / df;
-    if (!(xn > lo && xn < hi)) break;
+    if (!(xn >= lo && xn <= hi)) break;
     x = xn;
   }
   return x;
 }
 
 // V[p] += v_x^mBJ(rho, grad rho, lap rho, tau~) with c = c_fixed (> 0) or *c_dev
-__global__ void __launch_bounds__(kMbjThreads) k_mbj_x(const double* __restrict__ rho, const double* __restrict__ part,
+__global__ void __launch_bounds__(kBrThreads) k_mbj_x(const double* __restrict__ rho, const double* __restrict__ part,
                                                       int nchunk, int nx, int ny, int nz, int periodic, double hx,
                                                       double hy, double hz, Fd fd, double c_fixed,
                                                       const double* __restrict__ c_dev, double* __restrict__ V) {
@@ -223,8 +265,10 @@ __global__ void __launch_bounds__(kMbjThreads) k_mbj_x(const double* __restrict_
 
 }  // namespace
 
+// chunks of orbitals for k_tau: about 6 CTAs of points x chunks per SM in one wave
 int mbj_chunks(long long npts, int norb_tot) {
-  long long ch = (152LL * 4 * kMbjThreads + npts - 1) / npts;      // about 4 CTAs per SM
+  const long long bx = (npts + kMbjThreads - 1) / kMbjThreads;
+  long long ch = (152LL * 6) / bx;
   if (ch > norb_tot) ch = norb_tot;
   return ch < 1 ? 1 : (int)ch;
 }
@@ -241,8 +285,11 @@ cudaError_t launch_mbj(const typename Cplx<T>::type* u, int nk, int norb, const 
   Fd fd;
   for (int m = 0; m < 4; ++m) fd.d1[m] = kFD1[m];
   for (int m = 0; m < 5; ++m) fd.d2[m] = kFD2[m];
-  k_tau<T><<<dim3(bx, nchunk), kMbjThreads, 0, s>>>(u, nk, norb, n[0], n[1], n[2], periodic, kpts, kw, h[0], h[1],
-                                                    h[2], fd, ochunk, part);
+  D1h<T> d1;
+  for (int a = 0; a < 3; ++a)
+    for (int m = 0; m < 4; ++m) d1.c[a][m] = (T)(kFD1[m] / h[a]);
+  k_tau<T><<<dim3(bx, nchunk), kMbjThreads, 0, s>>>(u, nk, norb, n[0], n[1], n[2], periodic, kpts, kw, d1, ochunk,
+                                                    part);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   int nl = 2;
@@ -253,8 +300,8 @@ cudaError_t launch_mbj(const typename Cplx<T>::type* u, int nk, int norb, const 
     if (e != cudaSuccess) return e;
     nl = 3;
   }
-  k_mbj_x<<<bx, kMbjThreads, 0, s>>>(rho, part, nchunk, n[0], n[1], n[2], periodic, h[0], h[1], h[2], fd, c_fixed,
-                                     c_dev, V);
+  k_mbj_x<<<(npts + kBrThreads - 1) / kBrThreads, kBrThreads, 0, s>>>(rho, part, nchunk, n[0], n[1], n[2], periodic,
+                                                                    h[0], h[1], h[2], fd, c_fixed, c_dev, V);
   if (nlaunch) *nlaunch = nl;
   return cudaGetLastError();
 }
