@@ -265,10 +265,11 @@ __global__ void __launch_bounds__(kBrThreads) k_mbj_x(const double* __restrict__
 
 }  // namespace
 
-// chunks of orbitals for k_tau: about 6 CTAs of points x chunks per SM in one wave
+// chunks of orbitals for k_tau: one wave of about 8 CTAs of points x chunks per SM (the register
+// limit of the FP32 kernel, 64 registers x 128 threads)
 int mbj_chunks(long long npts, int norb_tot) {
   const long long bx = (npts + kMbjThreads - 1) / kMbjThreads;
-  long long ch = (152LL * 6) / bx;
+  long long ch = (152LL * 8) / bx;
   if (ch > norb_tot) ch = norb_tot;
   return ch < 1 ? 1 : (int)ch;
 }

@@ -2,8 +2,9 @@
 
 The potential of a set of orbitals (c fixed and c from the density; periodic with several
 k-points, a 16^3 cell with several orbital chunks, a ragged isolated box), predictor-corrector
-steps in FP64 and FP32 (the predictor's own orbitals feed the predicted potential), the tiled
-path of large isolated grids, the ground state with TB-mBJ, and the argument checks."""
+steps in FP64 and FP32 (the predictor's own orbitals feed the predicted potential), predicted
+steps with the extrapolated potential, the tiled path of large isolated grids, the ground state with
+TB-mBJ, and the argument checks."""
 import math
 
 import numpy as np
@@ -137,4 +138,43 @@ def test_mbj_argument_checks():
         ctx.set_mbj(math.nan)
     assert e.value.status == 1                       # TDKS_EINVAL
     ctx.set_mbj(0.0)                                  # back to c from the density
+    ctx.close()
+
+
+def test_mbj_extrapolated_predictor_steps():
+    """Predicted steps with TB-mBJ (cubic extrapolation of V_Hxc, every prediction accepted): the
+    corrector's potential comes from the propagated orbitals' own kinetic energy density.  Against an
+    oracle loop of the same scheme (plain PC while the history fills, then the predicted step)."""
+    from oracle import nn_oracle as N
+    from paper_1804_01404_gb300 import tdks as T
+    s = SYSTEMS["periodic-2k"]
+    psi0 = W.initial_orbitals(s, 5)
+    n = 7
+    tabs, Vloc = O.projector_tables(s), O.local_potential(s)
+    psi = psi0.copy()
+    v = O.hxc(s, O.density(s, psi), True, 3, psi)
+    hist = [v]
+    for i in range(n):
+        t = i * s.dt
+        if len(hist) >= 4:
+            vt = N.cubic_extrapolation(hist[-1], hist[-2], hist[-3], hist[-4])
+            Ap = O.field_Aprime(s.field, t + 0.5 * s.dt)
+            psi = O.propagate_all(s, tabs, Vloc + 0.5 * (v + vt), psi, Ap, s.dt)
+            v = O.hxc(s, O.density(s, psi), True, 3, psi)
+        else:
+            psi, v, _ = O.pc_step(s, tabs, Vloc, psi, v, t, s.dt, xc_on=3)
+        hist.append(v)
+    ctx = T.Context(s, precision="f64", xc=3)
+    u = _dev(psi0)
+    ctx.update_potential(u)
+    ctx.set_predictor(T.PRED_EXTRAP, 1.0)
+    t = 0.0
+    for _ in range(n):
+        ctx.step(u, t, s.dt)
+        t += s.dt
+    ctx.check()
+    assert ctx.read_step_observables()["fallbacks"] == 0
+    got = u.cpu().numpy()
+    assert np.linalg.norm(got - psi) < 1e-10 * np.linalg.norm(psi)
+    assert np.max(np.abs(ctx.grid_array(1).cpu().numpy() - v)) < 1e-9 * np.max(np.abs(v))
     ctx.close()
