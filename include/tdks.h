@@ -417,7 +417,8 @@ tdks_status tdks_set_wait_test(tdks_ctx* ctx, long long wait_limit, int stop_aft
 /* Hartree + exchange potential of a density without allocating device memory.
  * For callers that cannot call cudaMalloc -- code running while a CUDA graph is captured, hosts whose
  * device memory belongs to a pool they do not control, loops that must never allocate -- this
- * computes vhxc = V_H[rho] + V_x[rho] (hartree / xc select the terms, as in tdks_options) for a
+ * computes vhxc = V_H[rho] + V_xc[rho] (hartree / xc select the terms, as in tdks_options; xc = 3,
+ * TB-mBJ, needs the orbitals and returns TDKS_EINVAL here) for a
  * periodic or isolated grid with the same kernels as tdks_update_potential, using a fixed work area
  * built into the library (6 MiB of device memory per GPU that loads the library, held until the
  * process exits) instead of context buffers.  rho_dev and vhxc_dev are caller-owned device arrays
