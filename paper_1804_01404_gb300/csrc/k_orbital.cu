@@ -664,11 +664,30 @@ template <typename T, int MODE, bool PER, bool DBUF, int OBS, bool IP = false>
 cudaError_t launch_cell(const OrbArgs<T>& a, typename Cplx<T>::type* scratch, size_t smem, int nt,
                         cudaStream_t s) {
   auto kern = k_cell<T, MODE, PER, DBUF, OBS, IP>;
+  // Shared-memory carveout: just enough shared memory for the CTAs that can be resident (registers,
+  // threads and the footprint allow), the rest of the unified storage left as L1 for the reads that
+  // stay global (the input orbital of every stage, the potential, the projector tables).  Computed
+  // once per kernel and launch shape.
+  static size_t last_smem = 0;
+  static int last_nt = 0, carve = -1;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  // all of the unified L1 / shared storage as shared memory, so that as many CTAs as the
-  // shared-memory footprint allows are resident on an SM
-  e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+  if (carve < 0 || last_smem != smem || last_nt != nt) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+    int nb = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, nt, smem);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, kern);
+    if (e != cudaSuccess) return e;
+    const size_t per_sm = 228 * 1024, need = (size_t)(nb > 0 ? nb : 1) * (smem + fa.sharedSizeBytes + 1024);
+    int pct = (int)((need * 100 + per_sm - 1) / per_sm);
+    carve = pct > 100 ? 100 : pct;
+    last_smem = smem;
+    last_nt = nt;
+  }
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, carve);
   if (e != cudaSuccess) return e;
   kern<<<a.ncell * a.nk * a.norb, nt, smem, s>>>(a, scratch);
   return cudaGetLastError();
