@@ -1,6 +1,11 @@
-// Eigen-decomposition of a small Hermitian matrix on the host by cyclic Jacobi rotations (used for
-// the norb x norb projected Hamiltonians of the Ritz rotation).
+// Dense linear algebra of the small norb x norb matrices, on the host (the overlaps and projected
+// Hamiltonians of the ground-state iteration and of the Ritz rotation).  Row-major, complex.
 //
+// cholesky_inverse_h: Cholesky S = L L^H of a Hermitian positive definite n x n matrix and
+// C = L^{-H} (upper triangular), so that the combinations W C of vectors with overlap S are
+// orthonormal (C^H S C = I).  False if S is not positive definite.
+//
+// herm_eig: eigen-decomposition of a Hermitian matrix by cyclic Jacobi rotations,
 // A = Y diag(w) Y^H with w ascending and Y unitary.  Each rotation zeroes one off-diagonal pair
 // (p, q): the phase of a_pq is moved into column q (D = diag(1, e^{-i phi}) turns the 2 x 2 block
 // into the real symmetric [[a, r], [r, b]], r = |a_pq|), then the real Jacobi rotation with
@@ -15,6 +20,41 @@
 #include <vector>
 
 namespace tdks {
+
+inline bool cholesky_inverse_h(const std::complex<double>* S, int n, std::complex<double>* Cout) {
+  std::vector<double> Lr((size_t)n * n, 0.0), Li((size_t)n * n, 0.0), Xr((size_t)n * n, 0.0), Xi((size_t)n * n, 0.0);
+  for (int j = 0; j < n; ++j) {
+    double d = S[j * n + j].real();
+    for (int k = 0; k < j; ++k) d -= Lr[j * n + k] * Lr[j * n + k] + Li[j * n + k] * Li[j * n + k];
+    if (!(d > 0.0)) return false;
+    const double ljj = std::sqrt(d);
+    Lr[j * n + j] = ljj;
+    for (int i = j + 1; i < n; ++i) {
+      double re = S[i * n + j].real(), im = S[i * n + j].imag();
+      for (int k = 0; k < j; ++k) {   // - L_ik conj(L_jk)
+        re -= Lr[i * n + k] * Lr[j * n + k] + Li[i * n + k] * Li[j * n + k];
+        im -= Li[i * n + k] * Lr[j * n + k] - Lr[i * n + k] * Li[j * n + k];
+      }
+      Lr[i * n + j] = re / ljj;
+      Li[i * n + j] = im / ljj;
+    }
+  }
+  for (int j = 0; j < n; ++j) {          // X = L^{-1} by forward substitution, column by column
+    Xr[j * n + j] = 1.0 / Lr[j * n + j];
+    for (int i = j + 1; i < n; ++i) {
+      double re = 0.0, im = 0.0;
+      for (int k = j; k < i; ++k) {
+        re += Lr[i * n + k] * Xr[k * n + j] - Li[i * n + k] * Xi[k * n + j];
+        im += Lr[i * n + k] * Xi[k * n + j] + Li[i * n + k] * Xr[k * n + j];
+      }
+      Xr[i * n + j] = -re / Lr[i * n + i];
+      Xi[i * n + j] = -im / Lr[i * n + i];
+    }
+  }
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) Cout[i * n + j] = std::complex<double>(Xr[j * n + i], -Xi[j * n + i]);   // C = X^H
+  return true;
+}
 
 inline void herm_eig(std::vector<std::complex<double>> A, int n, std::vector<double>& w,
                      std::vector<std::complex<double>>& Y) {

@@ -8,7 +8,7 @@
 #include <string>
 #include <vector>
 
-#include "herm_eig.h"
+#include "host_linalg.h"
 #include "tdks_internal.h"
 
 using namespace tdks;
@@ -910,41 +910,12 @@ tdks_status tdks_field_at(tdks_ctx* c, double t, double Ap[3], double E[3]) {
 }
 
 namespace {
-// Cholesky S = L L^H of a Hermitian positive definite n x n matrix (row-major, double2) and
-// C = L^{-H} (upper triangular), so that the combinations W C of vectors with overlap S are
-// orthonormal (C^H S C = I).  False if S is not positive definite.
+// cholesky_inverse_h (host_linalg.h) on the double2 matrices the Gram kernels write
 bool cholesky_inverse_h(const double2* S, int n, double2* Cout) {
-  std::vector<double> Lr((size_t)n * n, 0.0), Li((size_t)n * n, 0.0), Xr((size_t)n * n, 0.0), Xi((size_t)n * n, 0.0);
-  for (int j = 0; j < n; ++j) {
-    double d = S[j * n + j].x;
-    for (int k = 0; k < j; ++k) d -= Lr[j * n + k] * Lr[j * n + k] + Li[j * n + k] * Li[j * n + k];
-    if (!(d > 0.0)) return false;
-    const double ljj = std::sqrt(d);
-    Lr[j * n + j] = ljj;
-    for (int i = j + 1; i < n; ++i) {
-      double re = S[i * n + j].x, im = S[i * n + j].y;
-      for (int k = 0; k < j; ++k) {   // - L_ik conj(L_jk)
-        re -= Lr[i * n + k] * Lr[j * n + k] + Li[i * n + k] * Li[j * n + k];
-        im -= Li[i * n + k] * Lr[j * n + k] - Lr[i * n + k] * Li[j * n + k];
-      }
-      Lr[i * n + j] = re / ljj;
-      Li[i * n + j] = im / ljj;
-    }
-  }
-  for (int j = 0; j < n; ++j) {          // X = L^{-1} by forward substitution, column by column
-    Xr[j * n + j] = 1.0 / Lr[j * n + j];
-    for (int i = j + 1; i < n; ++i) {
-      double re = 0.0, im = 0.0;
-      for (int k = j; k < i; ++k) {
-        re += Lr[i * n + k] * Xr[k * n + j] - Li[i * n + k] * Xi[k * n + j];
-        im += Lr[i * n + k] * Xi[k * n + j] + Li[i * n + k] * Xr[k * n + j];
-      }
-      Xr[i * n + j] = -re / Lr[i * n + i];
-      Xi[i * n + j] = -im / Lr[i * n + i];
-    }
-  }
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j < n; ++j) Cout[i * n + j] = double2{Xr[j * n + i], -Xi[j * n + i]};   // C = X^H
+  std::vector<std::complex<double>> a((size_t)n * n), c((size_t)n * n);
+  for (size_t i = 0; i < a.size(); ++i) a[i] = std::complex<double>(S[i].x, S[i].y);
+  if (!tdks::cholesky_inverse_h(a.data(), n, c.data())) return false;
+  for (size_t i = 0; i < c.size(); ++i) Cout[i] = double2{c[i].real(), c[i].imag()};
   return true;
 }
 }  // namespace
