@@ -178,3 +178,33 @@ def test_mbj_extrapolated_predictor_steps():
     assert np.linalg.norm(got - psi) < 1e-10 * np.linalg.norm(psi)
     assert np.max(np.abs(ctx.grid_array(1).cpu().numpy() - v)) < 1e-9 * np.max(np.abs(v))
     ctx.close()
+
+
+@pytest.mark.parametrize("precision,tol,ctol", [("f64", 1e-5, 1e-6), ("f32", 3e-2, 2e-3)])
+def test_mbj_plane_wave_edge_case(precision, tol, ctol):
+    """The degenerate case of the Becke-Roussel equation: one plane wave gives a uniform density and
+    tau - |j|^2/(2 rho) = 0, so Q = 0 up to rounding and the root is x = 2; g = 0 gives c = alpha.
+    The GPU potential against the closed form -alpha (1 - 2 e^-2)(pi e^2 rho/2)^(1/3) plus the PZ
+    correlation.  Tolerances: the square roots of g and t_s lift the rounding of their vanishing
+    arguments to ~1e-8 in FP64; FP32 orbitals leave ~1e-7 relative noise in rho and tau, lifted to
+    ~1e-2 of the potential (the FP32 case checks that the degenerate root stays finite and near
+    the closed form)."""
+    from paper_1804_01404_gb300.tdks import Context
+    s = W.tiny(periodic=True, n=(8, 9, 10), natom=0, nk=1, norb=1)
+    s.h = (0.5, 0.45, 0.4)
+    s.kpts = np.zeros((1, 3))
+    s.kw = np.ones(1)
+    x, y, z = O.coords(s)
+    L = [s.n[a] * s.h[a] for a in range(3)]
+    u = np.exp(1j * (2 * np.pi / L[0] * x[None, None, :] + 4 * np.pi / L[1] * y[None, :, None] + 0 * z[:, None, None]))
+    psi = (u / math.sqrt(O.cell_volume(s)))[None, None]
+    ctx = Context(s, precision=precision, hartree=False, xc=3)
+    ctx.update_potential(_dev(psi, precision))
+    got = ctx.grid_array(1).cpu().numpy()
+    rho = O.density(s, psi)
+    rs = rho.mean() / 2
+    exact = 0.012 * (1 - 2 * math.exp(-2.0)) * (math.pi * math.e ** 2 * rs) ** (1 / 3) + O.lda_c(rho)[0]
+    assert np.all(np.isfinite(got))
+    assert np.max(np.abs(got - exact)) < tol * np.max(np.abs(exact))
+    assert abs(ctx.mbj_c() - (-0.012)) < ctol
+    ctx.close()

@@ -155,3 +155,26 @@ def test_mbj_two_electron_exponential_is_the_hydrogen_form():
     sel = (r > 0.6) & (r < 1.4)
     assert sel.sum() > 1000
     assert np.max(np.abs(v[sel] - exact[sel]) / np.abs(exact[sel])) < 2e-4
+
+
+def test_mbj_of_a_plane_wave_is_the_x2_closed_form():
+    """One plane-wave orbital: rho is uniform (no gradient or Laplacian on the grid) and
+    tau - |j|^2/(2 rho) = 0, so D = Q = 0, the Becke-Roussel root is x = 2 (the limit of the equation
+    at Q -> 0), b = (8 e^-2 / (8 pi rho_s))^(1/3), the correction term vanishes and g = 0 gives
+    c = alpha.  End to end through hxc: V_x = c v_BR = -alpha (1 - 2 e^-2) (pi e^2 rho_s)^(1/3).  The
+    square roots of g and of t_s lift the rounding of the vanishing terms (~1e-16) to ~1e-8, which
+    sets the tolerances."""
+    n, h = (8, 9, 10), (0.5, 0.45, 0.4)
+    s = _periodic(n, h)
+    x, y, z = O.coords(s)
+    L = [n[a] * h[a] for a in range(3)]
+    G = [2 * np.pi / L[0], 2 * np.pi * 2 / L[1], 0.0]
+    u = np.exp(1j * (G[0] * x[None, None, :] + G[1] * y[None, :, None] + G[2] * z[:, None, None]))
+    u /= math.sqrt(O.cell_volume(s))
+    psi = u[None, None]
+    rho = O.density(s, psi)
+    v = O.hxc(s, rho, False, 3, psi) - O.lda_c(rho)[0]
+    rs = rho.mean() / 2
+    vbr = -(1 - 2 * math.exp(-2.0)) * (math.pi * math.e ** 2 * rs) ** (1 / 3)
+    assert abs(O.mbj_c(s, rho) - (-0.012)) < 1e-7
+    assert np.allclose(v, -0.012 * vbr, rtol=1e-5, atol=0)
