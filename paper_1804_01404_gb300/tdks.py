@@ -128,6 +128,7 @@ def load_library(path: str = LIB_PATH):
         "tdks_dos": [C.POINTER(C.c_double), i, i, C.POINTER(C.c_double), C.POINTER(C.c_double), i, d,
                      C.POINTER(C.c_double), vp],
         "tdks_field_at": [vp, d, C.POINTER(C.c_double), C.POINTER(C.c_double)],
+        "tdks_hxc_noalloc": [C.POINTER(Grid), vp, vp, i, i, vp],
         "tdks_set_longitudinal": [vp, i, vp, d],
         "tdks_ground_state": [vp, vp, i, d, d, d, C.POINTER(C.c_double)],
         "tdks_excited_pairs": [vp, vp, vp, C.POINTER(C.c_double)],
@@ -203,6 +204,19 @@ def work(I, E, dt, stream=None):
     out = np.zeros(len(I))
     _check(lib.tdks_work(_dptr(I), _dptr(E), len(I), float(dt), _dptr(out), _stream_handle(stream)))
     return out
+
+
+def hxc_noalloc(system, rho, out, hartree=True, xc=1, stream=None):
+    """V_H + V_xc of a density into out without allocating device memory (tdks_hxc_noalloc); rho and
+    out are CUDA float64 tensors [nz, ny, nx] of the system's grid; asynchronous on `stream`."""
+    import torch
+    lib = load_library()
+    for t in (rho, out):
+        if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous():
+            raise ValueError("rho and out must be contiguous CUDA float64 tensors")
+    g = Grid((C.c_int * 3)(*system.n), (C.c_double * 3)(*system.h), 1 if system.periodic else 0)
+    _check(lib.tdks_hxc_noalloc(C.byref(g), C.c_void_p(rho.data_ptr()), C.c_void_p(out.data_ptr()), int(hartree),
+                                int(xc), _stream_handle(stream)))
 
 
 def dos(eps, kw, E, sigma, stream=None):

@@ -88,6 +88,15 @@ def test_dos_argument_checks(lib):
     assert lib.tdks_dos(None, 1, 3, p, p, 3, 0.1, p, None) == 1
 
 
+def test_binding_declares_every_symbol(lib):
+    """The Python binding gives argument types to every function the header declares."""
+    from paper_1804_01404_gb300 import tdks as T
+    src = open(T.__file__).read()
+    missing = [n for n in declared_symbols() if f'"{n}"' not in src and f"lib.{n}" not in src]
+    assert not missing, missing
+    assert lib.tdks_hxc_noalloc(None, None, None, 1, 1, None) == 1         # EINVAL before any device call
+
+
 def test_null_context_rejected(lib):
     assert lib.tdks_hpsi(None, None, None, (C.c_double * 3)()) == 1
     assert lib.tdks_step(None, None, 0.0, 0.02) == 1
