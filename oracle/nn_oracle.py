@@ -141,6 +141,32 @@ def predict(params, V0, V1, V2, V3, periodic):
     return cubic_extrapolation(V0, V1, V2, V3) + s3 * out
 
 
+def bf16(x):
+    """Round to the nearest bfloat16 (8-bit significand, ties to even), returned as float64.  The
+    network stores its weights, inputs and activations in this format and accumulates in FP32; the
+    rounding is done on the FP32 value, as a device does when it narrows FP32 to BF16."""
+    f = np.asarray(x, np.float64).astype(np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def forward_bf16(params, x, periodic):
+    """The forward pass at the network's storage precision: weights, biases, inputs and the two
+    hidden activations rounded to BF16, every sum in FP64 (the device sums in FP32; the difference
+    is its accumulation rounding and, rarely, a BF16 rounding decision that it flips)."""
+    W1, b1, W2, b2, W3, b3 = unpack(bf16(params))
+    a1 = bf16(silu(conv(bf16(x), W1, b1, periodic)))
+    a2 = bf16(silu(conv(a1, W2, b2, periodic)))
+    return conv(a2, W3, b3, periodic)[0]
+
+
+def predict_bf16(params, V0, V1, V2, V3, periodic):
+    """V~(t+dt) of the network as stored (forward_bf16), the scales and the cubic in FP64."""
+    x, s3 = inputs(V0, V1, V2, V3)
+    return cubic_extrapolation(V0, V1, V2, V3) + s3 * forward_bf16(params, x, periodic)
+
+
 def target(V0, V1, V2, V3, Vnext, s3):
     return (Vnext - cubic_extrapolation(V0, V1, V2, V3)) / s3
 

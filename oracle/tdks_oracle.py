@@ -586,6 +586,73 @@ def pc_step(s, tabs, Vloc, psi, vhxc, t, dt, pc=True, hartree_on=True, xc_on=Tru
     return new, hxc(s, rho, hartree_on, xc_on, new, mbj_c), rho
 
 
+def misfit(vnew, vpred):
+    """Self-consistency misfit of a predicted potential: ||V_Hxc(t+dt) - V~||_2 / ||V_Hxc(t+dt)||_2
+    (the reading of the "density residual" that decides whether a predicted step is kept)."""
+    return float(np.linalg.norm(vnew - vpred) / np.linalg.norm(vnew))
+
+
+def predicted_step(s, tabs, Vloc, psi, vhxc, vpred, t, dt, threshold, hartree_on=True, xc_on=True,
+                   Ap=None, mbj_c=None):
+    """One step with a predicted potential V~(t+dt) in place of the predictor half-step of the
+    predictor-corrector scheme (Program summary):
+
+        corrector  psi(t+dt) = T4[V_loc + (V_Hxc(t) + V~)/2] psi(t),  A'(t + dt/2),
+                   V_Hxc(t+dt) = V_Hxc[rho(t+dt)],
+        misfit     r = ||V_Hxc(t+dt) - V~|| / ||V_Hxc(t+dt)||.
+
+    If r exceeds the threshold (or is not finite) the step is discarded and redone from psi(t) by
+    the plain predictor-corrector step, which also supplies the returned misfit of its own
+    predictor.  Returns (psi(t+dt), V_Hxc(t+dt), rho(t+dt), r of the predicted V~, accepted)."""
+    if Ap is None:
+        Ap = field_Aprime(s.field, t + 0.5 * dt) if s.periodic else np.zeros(3)
+    new = propagate_all(s, tabs, Vloc + 0.5 * (vhxc + vpred), psi, Ap, dt)
+    rho = density(s, new)
+    vnew = hxc(s, rho, hartree_on, xc_on, new, mbj_c)
+    r = misfit(vnew, vpred)
+    if np.isfinite(r) and r <= threshold:
+        return new, vnew, rho, r, True
+    new, vnew, rho = pc_step(s, tabs, Vloc, psi, vhxc, t, dt, True, hartree_on, xc_on, Ap, mbj_c)
+    return new, vnew, rho, r, False
+
+
+def run_predicted(s, psi0, nsteps, predictor, threshold, hartree_on=True, xc_on=True, t0=0.0, mbj_c=None):
+    """Propagate nsteps with predicted steps.  The history holds the last four V_Hxc (starting from
+    V_Hxc[rho(psi0)]); while it has fewer than four the step is the plain predictor-corrector step.
+    predictor(V0, V1, V2, V3) -> V~(t+dt) from V_Hxc(t), V_Hxc(t-dt), V_Hxc(t-2dt), V_Hxc(t-3dt).
+    Returns the final psi, V_Hxc and per-step records: t, J(t+dt) (with A'(t+dt)), dipole of
+    rho(t+dt), the misfit of the prediction (nan for plain steps) and the number of rejected
+    predictions."""
+    tabs = projector_tables(s)
+    Vloc = local_potential(s)
+    psi = psi0.copy()
+    rho0 = density(s, psi)
+    vhxc = hxc(s, rho0, hartree_on, xc_on, psi, mbj_c)
+    hist = [vhxc]
+    rec = dict(t=[], J=[], d=[], misfit=[])
+    rejected = 0
+    t = t0
+    for _ in range(nsteps):
+        if len(hist) >= 4:
+            vpred = predictor(hist[-1], hist[-2], hist[-3], hist[-4])
+            psi, vhxc, rho, r, ok = predicted_step(s, tabs, Vloc, psi, vhxc, vpred, t, s.dt, threshold,
+                                                   hartree_on, xc_on, mbj_c=mbj_c)
+            rejected += 0 if ok else 1
+        else:
+            psi, vhxc, rho = pc_step(s, tabs, Vloc, psi, vhxc, t, s.dt, True, hartree_on, xc_on, mbj_c=mbj_c)
+            r = np.nan
+        hist = (hist + [vhxc])[-4:]
+        t += s.dt
+        Ap = field_Aprime(s.field, t) if s.periodic else np.zeros(3)
+        rec["t"].append(t)
+        rec["J"].append(current(s, tabs, psi, Ap) if s.periodic else np.zeros(3))
+        rec["d"].append(dipole(s, rho, rho0))
+        rec["misfit"].append(r)
+    out = {k: np.array(v) for k, v in rec.items()}
+    out["rejected"] = rejected
+    return psi, vhxc, out
+
+
 def apply_kick(s, psi, kappa):
     """Isolated impulse (Sec. 3.1): psi(0+) = exp(i kappa . r) phi."""
     x, y, z = coords(s)
