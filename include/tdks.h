@@ -43,7 +43,7 @@
 extern "C" {
 #endif
 
-#define TDKS_ABI_VERSION 1
+#define TDKS_ABI_VERSION 2
 
 typedef struct tdks_ctx tdks_ctx;
 
@@ -95,8 +95,25 @@ typedef struct { double E_s, E_p, r_cut, width; } tdks_projector;
  * stage; 1 it leaves those of the input state, J(t) and dipole(t), which the first Taylor stage
  * forms from the derivative sums it computes anyway (no extra pass; the values of the final state
  * then come from tdks_observables or the next step).  The multiscale step (tdks_ms_step) always
- * uses the end-of-step current, which the Maxwell update needs. */
-typedef struct { int precision; int hartree; int xc; int pc; int ncell; int obs_at_start; } tdks_options;
+ * uses the end-of-step current, which the Maxwell update needs.
+ * norb_offset, norb_total: the orbital range of this context when the orbitals of every k-point are
+ * split over several contexts (orbital parallelism, Sec. 3.2: the paper distributes the orbitals over
+ * processes and sums the density over them).  The context holds orbitals norb_offset .. norb_offset +
+ * norb - 1 of norb_total per k-point.  norb_total = 0 means norb (the whole set; norb_offset must then
+ * be 0).  A context with norb < norb_total holds a shard: H u, Taylor steps, the kick and
+ * tdks_observables act on its own orbitals (its observables are the shard's partial sums, which the
+ * caller adds over the shards), while the calls that form the density-dependent potential from the
+ * orbitals (tdks_update_potential, tdks_step, tdks_ms_step, tdks_ground_state) return
+ * TDKS_EUNSUPPORTED: this build has no exchange of densities between shards. */
+typedef struct {
+  int precision; int hartree; int xc; int pc; int ncell; int obs_at_start;
+  int norb_offset; int norb_total;
+} tdks_options;
+
+/* Validate options for a grid with nk k-points and norb orbitals per k-point without creating a
+ * context (host only, no GPU needed); tdks_init applies the same checks.  TDKS_OK, or TDKS_EINVAL /
+ * TDKS_EUNSUPPORTED with a message (tdks_last_error). */
+tdks_status tdks_check_options(const tdks_grid* grid, int nk, int norb, const tdks_options* opts);
 
 /* Observables returned to the host. */
 typedef struct {
@@ -222,16 +239,24 @@ tdks_status tdks_field_at(tdks_ctx* ctx, double t, double Ap[3], double E[3]);
 /* Isolated impulse (Sec. 3.1): u <- exp(i kappa . r) u for all orbitals, in place. */
 tdks_status tdks_kick(tdks_ctx* ctx, void* u_dev, const double kappa[3]);
 
-/* rho <- rho[u] (Eq. rho), V_Hxc(t) <- V_H[rho] + V_x[rho].  The first call also stores rho as
- * the reference density rho0 of the dipole.  Must be called once before tdks_step. */
+/* rho <- rho[u] (Eq. rho), V_Hxc(t) <- V_H[rho] + V_xc[rho] (Eq. TDKS: the Hartree potential; Sec.
+ * 3.1: the adiabatic LDA, with the terms the options select -- exchange, exchange + correlation, or
+ * TB-mBJ exchange + correlation from the orbitals' kinetic energy density).  The first call also
+ * stores rho as the reference density rho0 of the dipole.  Must be called once before tdks_step.
+ * Errors: EINVAL for a NULL u; EUNSUPPORTED on an orbital shard (options.norb_total > norb). */
 tdks_status tdks_update_potential(tdks_ctx* ctx, const void* u_dev);
 
-/* hu <- H_q u for all orbitals with q = k + Aprime and the current potential
- * V_loc + V_Hxc(t).  u and hu must not overlap. */
+/* hu <- H_q u for all orbitals: the Hamiltonian of Eq. (TDKS_solid) (Bloch orbitals in the velocity
+ * gauge; Eq. (TDKS) for isolated grids, where q = 0) with q = k + Aprime, the current potential
+ * V_loc + V_Hxc(t) and the Kleinman-Bylander projectors of Sec. 3.1 with the gauge phase of Sec. 4.1.
+ * u, hu: device orbital arrays of the context's layout; they must not overlap.  Asynchronous.
+ * Errors: EINVAL for NULL arrays. */
 tdks_status tdks_hpsi(tdks_ctx* ctx, const void* u_dev, void* hu_dev, const double Aprime[3]);
 
-/* u <- sum_{n=0..4} (-i dt H_q)^n u / n! in place (Horner form), with q = k + Aprime and the
- * current potential V_loc + V_Hxc(t). */
+/* u <- sum_{n=0..4} (-i dt H_q)^n u / n! in place (Horner form): the truncated Taylor expansion of the
+ * evolution operator (Program summary), 4th order, with H_q as in tdks_hpsi (q = k + Aprime) and the
+ * current potential V_loc + V_Hxc(t) held fixed over the step.  Asynchronous.  Errors: EINVAL for a
+ * NULL u. */
 tdks_status tdks_taylor_step(tdks_ctx* ctx, void* u_dev, double dt, const double Aprime[3]);
 
 /* One predictor-corrector step t -> t + dt, in place (Program summary; Sec. 3.1, 4.1):
@@ -248,11 +273,20 @@ tdks_status tdks_step(tdks_ctx* ctx, void* u_dev, double t, double dt);
 tdks_status tdks_read_step_observables(tdks_ctx* ctx, tdks_obs* out);
 
 /* Compute all observables of u with A'(t) = Aprime, against the current rho0 and potential
- * (synchronises the stream).  Does not change the context's potential. */
-tdks_status tdks_observables(tdks_ctx* ctx, const void* u_dev, const double Aprime[3], tdks_obs* out);
+ * (synchronises the stream): the current of Eq. (macro_current) including the nonlocal term, the
+ * dipole d = -int r (rho - rho0) dr of Sec. 3.1 from the density of Eq. (rho), the orbital norms, the
+ * band energy and the electron count.  rho_dev (nullable): a caller-owned device array [nz][ny][nx]
+ * of doubles that receives rho[u].  Does not change the context's potential or density.  On an
+ * orbital shard the sums run over the shard's orbitals only.  Errors: EINVAL for NULL u or out;
+ * EUNSUPPORTED for ncell > 1. */
+tdks_status tdks_observables(tdks_ctx* ctx, const void* u_dev, const double Aprime[3], double* rho_dev,
+                             tdks_obs* out);
 
-/* Copy context arrays (device-to-device, [nz][ny][nx] doubles) into caller buffers:
- * which = 0: V_loc; 1: V_Hxc(t); 2: rho(t); 3: rho0. */
+/* Copy a context array of the first cell (device-to-device, [nz][ny][nx] doubles) into a caller
+ * buffer dst_dev:  which = 0: the local pseudopotential V_loc (Sec. 3.1); 1: V_Hxc(t), the Hartree
+ * (Eq. TDKS) plus exchange-correlation (Sec. 3.1) potential of the last update; 2: rho(t) of Eq. (rho);
+ * 3: the reference density rho0 of the dipole.  Asynchronous.  Errors: EINVAL for NULL dst_dev or
+ * which outside 0..3. */
 tdks_status tdks_get_grid_array(tdks_ctx* ctx, int which, double* dst_dev);
 
 /* Wait for all work of the context's stream and report any asynchronous CUDA error. */

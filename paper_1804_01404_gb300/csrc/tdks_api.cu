@@ -525,6 +525,15 @@ tdks_status check_ctx(const tdks_ctx* c) {
   return TDKS_OK;
 }
 
+// The calls that form the density-dependent potential from the orbitals need every orbital's density;
+// a context that holds one shard of the orbitals (options.norb_total > norb) has only its own.
+tdks_status check_whole_set(const tdks_ctx* c, const char* what) {
+  if (c->opt.norb_total > c->norb)
+    return fail(TDKS_EUNSUPPORTED, std::string(what) + " needs every orbital: this context holds a shard "
+                "(norb < norb_total) and this build has no density exchange between shards");
+  return TDKS_OK;
+}
+
 }  // namespace
 
 // Stencil autotuner of the tiled path: every variant runs the stencil alone (H v, and a Horner stage
@@ -655,15 +664,8 @@ extern "C" {
 const char* tdks_last_error(void) { return g_err.c_str(); }
 int tdks_abi_version(void) { return TDKS_ABI_VERSION; }
 
-tdks_status tdks_init(const tdks_grid* grid, const tdks_cell* cell, const tdks_atom* atoms,
-                      int natom, const tdks_projector* projectors, int nproj, const double* kpts,
-                      const double* kw, int nk, int norb, const tdks_options* opts, void* stream,
-                      tdks_ctx** out) {
-  if (!out) return fail(TDKS_EINVAL, "out is null");
-  *out = nullptr;
-  if (!grid || !opts || !kpts || !kw) return fail(TDKS_EINVAL, "null grid, options or k-points");
-  if (natom < 0 || (natom > 0 && !atoms)) return fail(TDKS_EINVAL, "bad atom list");
-  if (nproj < 0 || (nproj > 0 && !projectors)) return fail(TDKS_EINVAL, "bad projector list");
+tdks_status tdks_check_options(const tdks_grid* grid, int nk, int norb, const tdks_options* opts) {
+  if (!grid || !opts) return fail(TDKS_EINVAL, "null grid or options");
   if (nk < 1 || norb < 1) return fail(TDKS_EINVAL, "nk and norb must be >= 1");
   if (opts->precision != TDKS_F64 && opts->precision != TDKS_F32)
     return fail(TDKS_EINVAL, "precision must be TDKS_F64 or TDKS_F32");
@@ -673,6 +675,29 @@ tdks_status tdks_init(const tdks_grid* grid, const tdks_cell* cell, const tdks_a
     if (grid->n[a] < 4 || grid->n[a] > 1024) return fail(TDKS_EINVAL, "grid points per axis must be in [4, 1024]");
     if (!(grid->h[a] > 0.0)) return fail(TDKS_EINVAL, "grid spacing must be positive");
   }
+  if (opts->obs_at_start != 0 && opts->obs_at_start != 1) return fail(TDKS_EINVAL, "obs_at_start must be 0 or 1");
+  if (opts->xc < 0 || opts->xc > 3)
+    return fail(TDKS_EINVAL, "xc must be 0 (none), 1 (exchange), 2 (exchange + correlation) or 3 (TB-mBJ exchange + correlation)");
+  if (opts->xc == 3 && opts->ncell > 1) return fail(TDKS_EUNSUPPORTED, "xc = 3 (TB-mBJ) needs ncell = 1");
+  if (opts->hartree != 0 && opts->hartree != 1) return fail(TDKS_EINVAL, "hartree must be 0 or 1");
+  if (opts->norb_total < 0 || opts->norb_offset < 0) return fail(TDKS_EINVAL, "norb_offset and norb_total must be >= 0");
+  if (opts->norb_total == 0 && opts->norb_offset != 0)
+    return fail(TDKS_EINVAL, "norb_offset needs norb_total (0 means the whole set, offset 0)");
+  if (opts->norb_total > 0 && (long long)opts->norb_offset + norb > opts->norb_total)
+    return fail(TDKS_EINVAL, "orbital range norb_offset .. norb_offset + norb - 1 exceeds norb_total");
+  return TDKS_OK;
+}
+
+tdks_status tdks_init(const tdks_grid* grid, const tdks_cell* cell, const tdks_atom* atoms,
+                      int natom, const tdks_projector* projectors, int nproj, const double* kpts,
+                      const double* kw, int nk, int norb, const tdks_options* opts, void* stream,
+                      tdks_ctx** out) {
+  if (!out) return fail(TDKS_EINVAL, "out is null");
+  *out = nullptr;
+  if (!grid || !opts || !kpts || !kw) return fail(TDKS_EINVAL, "null grid, options or k-points");
+  if (natom < 0 || (natom > 0 && !atoms)) return fail(TDKS_EINVAL, "bad atom list");
+  if (nproj < 0 || (nproj > 0 && !projectors)) return fail(TDKS_EINVAL, "bad projector list");
+  TDKS_TRY(tdks_check_options(grid, nk, norb, opts));
   if (grid->periodic) {
     if (!cell) return fail(TDKS_EINVAL, "periodic grid needs a cell");
     for (int a = 0; a < 3; ++a)
@@ -682,11 +707,6 @@ tdks_status tdks_init(const tdks_grid* grid, const tdks_cell* cell, const tdks_a
   double wsum = 0.0;
   for (int k = 0; k < nk; ++k) wsum += kw[k];
   if (std::fabs(wsum - 1.0) > 1e-9) return fail(TDKS_EINVAL, "k-point weights must sum to 1");
-  if (opts->obs_at_start != 0 && opts->obs_at_start != 1) return fail(TDKS_EINVAL, "obs_at_start must be 0 or 1");
-  if (opts->xc < 0 || opts->xc > 3)
-    return fail(TDKS_EINVAL, "xc must be 0 (none), 1 (exchange), 2 (exchange + correlation) or 3 (TB-mBJ exchange + correlation)");
-  if (opts->xc == 3 && opts->ncell > 1) return fail(TDKS_EUNSUPPORTED, "xc = 3 (TB-mBJ) needs ncell = 1");
-  if (opts->hartree != 0 && opts->hartree != 1) return fail(TDKS_EINVAL, "hartree must be 0 or 1");
 
   tdks_ctx* c = new tdks_ctx();
   c->grid = *grid;
@@ -922,6 +942,7 @@ bool cholesky_inverse_h(const double2* S, int n, double2* Cout) {
 
 tdks_status tdks_ground_state(tdks_ctx* c, void* u, int max_iter, double tol, double tau, double mix, double* out) {
   TDKS_TRY(check_ctx(c));
+  TDKS_TRY(check_whole_set(c, "tdks_ground_state"));
   if (!u) return fail(TDKS_EINVAL, "null orbitals");
   if (c->ncell != 1) return fail(TDKS_EUNSUPPORTED, "tdks_ground_state needs ncell = 1");
   if (c->norb > 64) return fail(TDKS_EUNSUPPORTED, "tdks_ground_state handles at most 64 orbitals per k-point");
@@ -1276,6 +1297,7 @@ tdks_status tdks_kick(tdks_ctx* c, void* u, const double kappa[3]) {
 
 tdks_status tdks_update_potential(tdks_ctx* c, const void* u) {
   TDKS_TRY(check_ctx(c));
+  TDKS_TRY(check_whole_set(c, "tdks_update_potential"));
   if (!u) return fail(TDKS_EINVAL, "null orbitals");
   TDKS_TRY(density(c, u, c->d_rho));
   TDKS_TRY(hxc(c, c->d_rho, c->d_vhxc, u));
@@ -1393,6 +1415,7 @@ tdks_status predicted_step(tdks_ctx* c, void* u, const double Amid[3], const dou
 
 tdks_status tdks_step(tdks_ctx* c, void* u, double t, double dt) {
   TDKS_TRY(check_ctx(c));
+  TDKS_TRY(check_whole_set(c, "tdks_step"));
   if (!u) return fail(TDKS_EINVAL, "null orbitals");
   if (!c->have_potential) return fail(TDKS_EINVAL, "call tdks_update_potential before tdks_step");
   double Amid[3], Aend[3], Astart[3];
@@ -1466,6 +1489,7 @@ tdks_status tdks_ms_init(tdks_ctx* c, int nX, int m0, double dX, const double* A
 
 tdks_status tdks_ms_step(tdks_ctx* c, void* u, double t, double dt) {
   TDKS_TRY(check_ctx(c));
+  TDKS_TRY(check_whole_set(c, "tdks_ms_step"));
   if (!u) return fail(TDKS_EINVAL, "null orbitals");
   if (!c->ms_ready) return fail(TDKS_EINVAL, "call tdks_ms_init first");
   if (!c->have_potential) return fail(TDKS_EINVAL, "call tdks_update_potential before tdks_ms_step");
@@ -1528,13 +1552,15 @@ tdks_status tdks_read_step_observables(tdks_ctx* c, tdks_obs* o) {
   return TDKS_OK;
 }
 
-tdks_status tdks_observables(tdks_ctx* c, const void* u, const double Ap[3], tdks_obs* o) {
+tdks_status tdks_observables(tdks_ctx* c, const void* u, const double Ap[3], double* rho_out, tdks_obs* o) {
   TDKS_TRY(check_ctx(c));
   if (!u || !o) return fail(TDKS_EINVAL, "null argument");
   if (c->ncell > 1) return fail(TDKS_EUNSUPPORTED, "tdks_observables needs ncell = 1");
   double A[3] = {0, 0, 0};
   if (Ap && c->grid.periodic) for (int a = 0; a < 3; ++a) A[a] = Ap[a];
   TDKS_TRY(density(c, u, c->d_rho_tmp));
+  if (rho_out)
+    TDKS_CUDA(cudaMemcpyAsync(rho_out, c->d_rho_tmp, c->npts * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
   const double* r0 = c->have_rho0 ? c->d_rho0 : c->d_rho_tmp;
   TDKS_CUDA(launch_dipole(c->d_rho_tmp, r0, c->grid.n, c->grid.h, c->grid.periodic, c->d_partials, c->d_ticket, c->d_step_obs, c->stream));
   TDKS_TRY(orbital_observables(c, u, A));

@@ -6,9 +6,10 @@
 // code cannot pass the array's name to a kernel (on the host that name is only a stand-in), so
 // the first call on each device asks the runtime for the array's device address with
 // cudaGetSymbolAddress and caches it; that first call should therefore come before any stream
-// capture.  All calls share the array: concurrent calls on different streams race.
+// capture.  The cached address belongs to the device's current context: after cudaDeviceReset the
+// module is loaded again and the array may move, so a process that resets a device must not call this
+// entry point on it again.  All calls share the array: concurrent calls on different streams race.
 #include <cmath>
-#include <cstring>
 #include <mutex>
 
 #include "tdks_internal.h"
@@ -30,12 +31,8 @@ static __device__ __align__(256) NoallocArea g_noalloc;
 NoallocArea* g_noalloc_addr[kMaxDevices] = {nullptr};
 std::mutex g_noalloc_mu;
 
-thread_local char g_noalloc_msg[256];
-
 tdks_status noalloc_fail(tdks_status s, const char* msg) {
-  std::strncpy(g_noalloc_msg, msg, sizeof(g_noalloc_msg) - 1);
-  g_noalloc_msg[sizeof(g_noalloc_msg) - 1] = '\0';
-  tdks::set_last_error(g_noalloc_msg);
+  tdks::set_last_error(msg);
   return s;
 }
 

@@ -46,7 +46,7 @@ class ProjectorC(C.Structure):
 
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("hartree", C.c_int), ("xc", C.c_int), ("pc", C.c_int),
-                ("ncell", C.c_int), ("obs_at_start", C.c_int)]
+                ("ncell", C.c_int), ("obs_at_start", C.c_int), ("norb_offset", C.c_int), ("norb_total", C.c_int)]
 
 
 class Obs(C.Structure):
@@ -99,7 +99,8 @@ def load_library(path: str = LIB_PATH):
         "tdks_taylor_step": [vp, vp, d, _D3],
         "tdks_step": [vp, vp, d, d],
         "tdks_read_step_observables": [vp, C.POINTER(Obs)],
-        "tdks_observables": [vp, vp, _D3, C.POINTER(Obs)],
+        "tdks_observables": [vp, vp, _D3, vp, C.POINTER(Obs)],
+        "tdks_check_options": [C.POINTER(Grid), i, i, C.POINTER(Options)],
         "tdks_get_grid_array": [vp, i, vp],
         "tdks_check": [vp],
         "tdks_profile": [vp, i],
@@ -208,12 +209,20 @@ def work(I, E, dt, stream=None):
 
 def hxc_noalloc(system, rho, out, hartree=True, xc=1, stream=None):
     """V_H + V_xc of a density into out without allocating device memory (tdks_hxc_noalloc); rho and
-    out are CUDA float64 tensors [nz, ny, nx] of the system's grid; asynchronous on `stream`."""
+    out are contiguous CUDA float64 tensors of the system's grid (n0 n1 n2 points) on the current
+    device; asynchronous on `stream`.  Arrays of another size or on another device are refused here:
+    the library cannot see their extent, and a short array would be accessed past its end."""
     import torch
-    lib = load_library()
+    npts = int(system.n[0]) * int(system.n[1]) * int(system.n[2])
+    for t in (rho, out):
+        if t.numel() != npts:
+            raise ValueError(f"rho and out must hold the grid's {npts} points, got {t.numel()}")
     for t in (rho, out):
         if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous():
             raise ValueError("rho and out must be contiguous CUDA float64 tensors")
+        if t.device.index != torch.cuda.current_device():
+            raise ValueError("rho and out must be on the current CUDA device")
+    lib = load_library()
     g = Grid((C.c_int * 3)(*system.n), (C.c_double * 3)(*system.h), 1 if system.periodic else 0)
     _check(lib.tdks_hxc_noalloc(C.byref(g), C.c_void_p(rho.data_ptr()), C.c_void_p(out.data_ptr()), int(hartree),
                                 int(xc), _stream_handle(stream)))
@@ -260,7 +269,7 @@ class Context:
     complex64 (f32), on the current CUDA device."""
 
     def __init__(self, system, precision="f64", hartree=True, xc=True, pc=True, stream=None, ncell=1,
-                 obs_at_start=False, mbj_c=None):
+                 obs_at_start=False, mbj_c=None, norb_offset=0, norb_total=0):
         import torch
         lib = load_library()
         self.lib = lib
@@ -277,7 +286,7 @@ class Context:
         kp = np.ascontiguousarray(np.asarray(system.kpts, np.float64).reshape(-1))
         kw = np.ascontiguousarray(np.asarray(system.kw, np.float64))
         opts = Options(TDKS_F64 if precision == "f64" else TDKS_F32, int(hartree), int(xc), int(pc), int(ncell),
-                       int(bool(obs_at_start)))
+                       int(bool(obs_at_start)), int(norb_offset), int(norb_total))
         self.ncell = int(ncell)
         if stream is None:
             stream = torch.cuda.current_stream()
@@ -395,9 +404,12 @@ class Context:
         _check(self.lib.tdks_read_step_observables(self.ctx, C.byref(o)))
         return o.as_dict()
 
-    def observables(self, u, Aprime=None):
+    def observables(self, u, Aprime=None, rho=None):
+        """All observables of u (tdks_observables); rho: optional CUDA float64 tensor [nz, ny, nx] that
+        receives the density of u."""
         o = Obs()
-        _check(self.lib.tdks_observables(self.ctx, _ptr(u, self.cdtype), _vec3(Aprime), C.byref(o)))
+        _check(self.lib.tdks_observables(self.ctx, _ptr(u, self.cdtype), _vec3(Aprime),
+                                         _ptr(rho) if rho is not None else None, C.byref(o)))
         return o.as_dict()
 
     def grid_array(self, which):

@@ -31,7 +31,7 @@ def test_every_declared_symbol_is_exported(lib):
     assert "tdks_init" in names and "tdks_step" in names and len(names) >= 14
     for n in names:
         assert hasattr(lib, n), n
-    assert lib.tdks_abi_version() == 1
+    assert lib.tdks_abi_version() == 2
 
 
 def _init(lib, s, **kw):
@@ -45,7 +45,8 @@ def _init(lib, s, **kw):
     pr = T.ProjectorC(s.proj.E_s, s.proj.E_p, kw.get("r_cut", s.proj.r_cut), s.proj.width)
     kp = np.ascontiguousarray(np.asarray(s.kpts, np.float64).ravel())
     kwt = np.ascontiguousarray(np.asarray(kw.get("kw", s.kw), np.float64))
-    opts = T.Options(kw.get("precision", 0), 1, kw.get("xc", 1), 1, kw.get("ncell", 1), kw.get("obs_at_start", 0))
+    opts = T.Options(kw.get("precision", 0), 1, kw.get("xc", 1), 1, kw.get("ncell", 1), kw.get("obs_at_start", 0),
+                     kw.get("norb_offset", 0), kw.get("norb_total", 0))
     ctx = C.c_void_p()
     st = lib.tdks_init(C.byref(g), C.byref(cell), atoms, len(s.atoms), C.byref(pr), 1,
                        kp.ctypes.data_as(C.POINTER(C.c_double)), kwt.ctypes.data_as(C.POINTER(C.c_double)),
@@ -64,6 +65,9 @@ def _init(lib, s, **kw):
     (dict(ncell=-2), "ncell"),
     (dict(obs_at_start=3), "obs_at_start"),
     (dict(xc=4), "xc must be"),
+    (dict(norb_offset=1), "norb_offset needs norb_total"),
+    (dict(norb_offset=3, norb_total=4), "exceeds norb_total"),
+    (dict(norb_total=-1), "must be >= 0"),
 ])
 def test_host_validation(lib, case, expect):
     s = W.tiny(periodic=True, n=(6, 6, 6), natom=1)
@@ -100,3 +104,47 @@ def test_binding_declares_every_symbol(lib):
 def test_null_context_rejected(lib):
     assert lib.tdks_hpsi(None, None, None, (C.c_double * 3)()) == 1
     assert lib.tdks_step(None, None, 0.0, 0.02) == 1
+
+
+def _check_options(lib, s, norb, **kw):
+    from paper_1804_01404_gb300 import tdks as T
+    g = T.Grid((C.c_int * 3)(*s.n), (C.c_double * 3)(*s.h), int(s.periodic))
+    o = T.Options(kw.get("precision", 1), 1, 1, 1, 1, 0, kw.get("norb_offset", 0), kw.get("norb_total", 0))
+    return lib.tdks_check_options(C.byref(g), 1, norb, C.byref(o)), lib.tdks_last_error().decode()
+
+
+def test_orbital_range_offset(lib):
+    """The orbital range of a shard (orbital parallelism: the orbitals of each k-point split over
+    contexts) is validated on the host: offset + norb must stay within norb_total, an offset needs
+    a total, and the whole set (norb_total = 0 or = norb) is the default."""
+    from paper_1804_01404_gb300 import tdks as T
+    s = W.tiny(periodic=True, n=(6, 6, 6), natom=1)
+    assert T.Options.norb_offset.offset == 6 * 4 and T.Options.norb_total.offset == 7 * 4
+    assert C.sizeof(T.Options) == 8 * 4
+    assert _check_options(lib, s, 4)[0] == 0
+    assert _check_options(lib, s, 4, norb_total=4)[0] == 0
+    assert _check_options(lib, s, 4, norb_offset=12, norb_total=16)[0] == 0
+    assert _check_options(lib, s, 4, norb_offset=0, norb_total=16)[0] == 0
+    st, msg = _check_options(lib, s, 4, norb_offset=13, norb_total=16)
+    assert st == 1 and "exceeds norb_total" in msg
+    st, msg = _check_options(lib, s, 4, norb_offset=2)
+    assert st == 1 and "norb_offset needs norb_total" in msg
+    st, msg = _check_options(lib, s, 4, precision=5)
+    assert st == 1 and "precision" in msg
+
+
+def test_noalloc_wrapper_refuses_wrong_sizes_before_any_call():
+    """The Python wrapper of the allocation-free potential refuses arrays that do not hold the grid
+    (a short array would be read or written past its end on the device) before it reaches the
+    library; the size check comes first, so it runs without a GPU."""
+    torch = pytest.importorskip("torch")
+    from paper_1804_01404_gb300 import tdks as T
+    s = W.tiny(periodic=True, n=(6, 6, 6), natom=1)
+    good = torch.zeros((6, 6, 6), dtype=torch.float64)
+    short = torch.zeros(6 * 6 * 6 - 1, dtype=torch.float64)
+    with pytest.raises(ValueError, match="points"):
+        T.hxc_noalloc(s, short, good)
+    with pytest.raises(ValueError, match="points"):
+        T.hxc_noalloc(s, good, short)
+    with pytest.raises(ValueError, match="CUDA"):
+        T.hxc_noalloc(s, good, good)                 # right size, but host tensors

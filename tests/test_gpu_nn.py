@@ -157,19 +157,6 @@ def test_predicted_step_fallback_equals_pc():
     assert np.linalg.norm(u1 - u0) < 1e-12 * np.linalg.norm(u0)
 
 
-def test_predicted_step_accepts_and_stays_close():
-    """Linear extrapolation accepted at every step (loose threshold): J stays within 1e-4 of the
-    predictor-corrector run over 40 steps, and the measured misfits are small and finite."""
-    from paper_1804_01404_gb300 import tdks as T
-    s = W.small_periodic(nsteps=40)
-    psi0 = W.initial_orbitals(s, 0)
-    J0, r0, _, _ = _steps(s, psi0, 40, T.PRED_PC, 1e-5)
-    J1, r1, fb, _ = _steps(s, psi0, 40, T.PRED_EXTRAP, 1.0)
-    assert fb == 0
-    assert np.all(np.isfinite(r1)) and np.max(r1[3:]) < 1e-2
-    assert np.max(np.abs(J1 - J0)) < 1e-4 * np.max(np.abs(J0))
-
-
 def test_trained_network_beats_cubic_extrapolation_on_held_out_trajectory():
     """What the network gains over the method without it: trained on V_Hxc histories the method
     itself generates (plain predictor-corrector, small periodic cell, seeds 1-3), it predicts the

@@ -122,7 +122,10 @@ def test_observables(name):
     ud = _dev(psi, "f64")
     rho0_psi = W.initial_orbitals(s, 9)
     ctx.update_potential(_dev(rho0_psi, "f64"))       # sets rho0
-    o = ctx.observables(ud, Ap)
+    rho = torch.full((s.n[2], s.n[1], s.n[0]), float("nan"), dtype=torch.float64, device="cuda")
+    o = ctx.observables(ud, Ap, rho=rho)
+    rho_ref = O.density(s, psi)
+    assert np.max(np.abs(rho.cpu().numpy() - rho_ref)) < 1e-13 * np.max(rho_ref)
     tabs = O.projector_tables(s)
     nrm = O.norms(s, psi)
     assert abs(o["norm_min"] - nrm.min()) < 1e-13 and abs(o["norm_max"] - nrm.max()) < 1e-13
@@ -235,3 +238,28 @@ def test_norm_monitor_reports_nonfinite():
     assert ei.value.status == 5
     o = ctx.observables(_dev(psi, "f64"))
     assert abs(o["norm_max"] - 1.0) < 1e-12
+
+
+def test_orbital_shard():
+    """A context that holds one shard of the orbitals (options.norb_offset / norb_total): H u and a
+    Taylor step of its orbitals equal the oracle's for the same orbitals with V_loc (no density is
+    formed on a shard), and the calls that form the potential from the orbitals are refused."""
+    from paper_1804_01404_gb300.tdks import Context, TdksError
+    s = W.small_periodic()
+    psi = W.initial_orbitals(s, 6)[:, 4:]                 # orbitals 4..7 of 8
+    s.norb = 4
+    Ap = np.array([0.01, -0.02, 0.005])
+    ctx = Context(s, precision="f64", norb_offset=4, norb_total=8)
+    ud = _dev(psi, "f64")
+    hu = torch.empty_like(ud)
+    ctx.hpsi(ud, hu, Ap)
+    tabs, Vloc = O.projector_tables(s), O.local_potential(s)
+    q = np.asarray(s.kpts[0]) + Ap
+    assert _rel(hu.cpu().numpy()[0], O.hpsi(s, tabs, Vloc, q, psi[0])) < 1e-12
+    ctx.taylor_step(ud, 0.02, Ap)
+    assert _rel(ud.cpu().numpy()[0], O.taylor4(s, tabs, Vloc, q, psi[0], 0.02)) < 1e-12
+    for call in (lambda: ctx.update_potential(ud), lambda: ctx.step(ud, 0.0, 0.02)):
+        with pytest.raises(TdksError) as e:
+            call()
+        assert e.value.status == 6 and "shard" in str(e.value)
+    ctx.close()

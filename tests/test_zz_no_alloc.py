@@ -69,3 +69,23 @@ def test_noalloc_rejects_oversize_grid():
     st = f(C.byref(g), C.c_void_p(buf.data_ptr()), C.c_void_p(buf.data_ptr()), 1, 1, None)
     assert st == 6, st                              # TDKS_EUNSUPPORTED
     assert "64" in lib.tdks_last_error().decode()
+
+
+@pytest.mark.parametrize("sys_index", [0, 1])
+def test_noalloc_public_wrapper_matches_the_oracle(sys_index):
+    """The same entry point through the package's Python wrapper (tdks.hxc_noalloc), two calls in a
+    row on one pair of buffers, against the oracle's Hartree + exchange potential of the density
+    (periodic: G-space Poisson; isolated: zero-padded convolution with the cell-averaged self term)."""
+    from oracle import tdks_oracle as O
+    from paper_1804_01404_gb300 import tdks
+    s = _systems()[sys_index]
+    out = torch.empty((s.n[2], s.n[1], s.n[0]), dtype=torch.float64, device="cuda")
+    for seed in (4, 9):
+        rho_np = O.density(s, W.initial_orbitals(s, seed))
+        rho = torch.from_numpy(rho_np).to("cuda")
+        out.fill_(float("nan"))
+        tdks.hxc_noalloc(s, rho, out, hartree=True, xc=1)
+        torch.cuda.synchronize()
+        ref = O.hxc(s, rho_np, True, 1)
+        err = np.max(np.abs(out.cpu().numpy() - ref)) / np.max(np.abs(ref))
+        assert err < 1e-12, (seed, err)
