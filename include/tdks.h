@@ -437,6 +437,11 @@ tdks_status tdks_set_state(tdks_ctx* ctx, const void* host_buf, size_t bytes);
  * device; no context needed).  No counterpart in the paper. */
 tdks_status tdks_probe_fp64(double* tflops);
 
+/* Measured FP32 FMA throughput of the current device in TFLOP/s (an FMA counts 2): the higher of
+ * scalar FMA chains and packed two-lane (f32x2) FMA chains on every SM, for the roofline of the FP32
+ * cell kernels (synchronises the device; no context needed).  No counterpart in the paper. */
+tdks_status tdks_probe_fp32(double* tflops);
+
 /* Test hook of the device-side timeout path (no counterpart in the paper).  The tile kernels of large
  * isolated grids wait on shared-memory barriers for their TMA plane copies; every wait gives up after
  * a number of polls, sets the context's error word and the kernel returns (tdks_check then reports

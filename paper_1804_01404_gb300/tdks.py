@@ -121,6 +121,7 @@ def load_library(path: str = LIB_PATH):
         "tdks_state_size": [vp, C.POINTER(C.c_size_t)],
         "tdks_ms_size": [vp, C.POINTER(i)],
         "tdks_probe_fp64": [C.POINTER(C.c_double)],
+        "tdks_probe_fp32": [C.POINTER(C.c_double)],
         "tdks_oscillator_strength": [C.POINTER(C.c_double), i, d, d, C.POINTER(C.c_double), i,
                                      C.POINTER(C.c_double), vp],
         "tdks_conductivity": [C.POINTER(C.c_double), i, d, d, C.POINTER(C.c_double), i, i,
@@ -158,6 +159,14 @@ def probe_fp64():
     lib = load_library()
     x = C.c_double()
     _check(lib.tdks_probe_fp64(C.byref(x)))
+    return x.value
+
+
+def probe_fp32():
+    """Measured FP32 FMA throughput of the current CUDA device, TFLOP/s (tdks_probe_fp32)."""
+    lib = load_library()
+    x = C.c_double()
+    _check(lib.tdks_probe_fp32(C.byref(x)))
     return x.value
 
 
