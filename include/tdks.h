@@ -318,8 +318,11 @@ tdks_status tdks_ms_size(const tdks_ctx* ctx, int* nX);
  * In the two predicted modes a step runs one Taylor propagation with (V_Hxc(t) + V~)/2, forms
  * V_Hxc(t+dt) and the misfit r = ||V_Hxc(t+dt) - V~|| / ||V_Hxc(t+dt)||; if r > threshold the step is
  * undone and redone with the plain predictor-corrector (fallback).  Predicted steps need the last
- * four potentials: the first three steps after tdks_update_potential always use the PC.  These
- * modes read r on the host every step (one stream synchronisation per step). */
+ * four potentials: the first three steps after tdks_update_potential always use the PC.  The decision
+ * is taken on the device: the step ends with a CUDA graph (built on the first predicted step, and again
+ * when the orbital array, dt or the threshold change) whose decision kernel keeps V_Hxc(t+dt) or counts
+ * a fallback and triggers a conditional node holding the restore and the plain step, so tdks_step does
+ * not wait for the GPU.  The fallback count is read by tdks_read_step_observables. */
 enum { TDKS_PRED_PC = 0, TDKS_PRED_EXTRAP = 1, TDKS_PRED_LEARNED = 2 };
 tdks_status tdks_set_predictor(tdks_ctx* ctx, int mode, double threshold);
 

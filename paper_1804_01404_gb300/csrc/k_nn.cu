@@ -353,6 +353,30 @@ __global__ void __launch_bounds__(256) k_residual(const double* __restrict__ Vne
   if (threadIdx.x == 0) *res = sqrt(tot[0] / fmax(tot[1], 1e-300));
 }
 
+// Accept or reject a predicted potential on the device: every thread reads the misfit the residual
+// kernel left, and if it is finite and within the threshold copies V_Hxc(t+dt) of the predicted step
+// into the step potential; thread 0 of block 0 otherwise counts a fallback and sets the graph's
+// conditional handle, which runs the conditional body (the restore and the plain predictor-corrector
+// step).  One thread sets the handle, so there are no racing calls.
+__global__ void __launch_bounds__(256) k_decide(const double* __restrict__ res, double thr,
+                                                const double* __restrict__ vnew, double* __restrict__ vhxc,
+                                                int n, double* fb, cudaGraphConditionalHandle handle) {
+  const double r = *res;
+  const bool ok = (r <= thr) && (r == r) && (r < 1e300);   // finite and within the threshold
+  if (ok)
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) vhxc[p] = vnew[p];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (!ok) *fb += 1.0;
+    cudaGraphSetConditional(handle, ok ? 0u : 1u);
+  }
+}
+
+__global__ void k_store6(double* dst, double a0, double a1, double a2, double a3, double a4, double a5) {
+  if (threadIdx.x == 0) {
+    dst[0] = a0; dst[1] = a1; dst[2] = a2; dst[3] = a3; dst[4] = a4; dst[5] = a5;
+  }
+}
+
 int blocks_for(int n) {
   int b = (n + 255) / 256;
   return b > 152 * 8 ? 152 * 8 : (b < 1 ? 1 : b);
@@ -431,6 +455,25 @@ cudaError_t nn_inputs(const NNBuffers& B, const NNGrid& g, const double* V0, con
 cudaError_t nn_apply(const NNBuffers& B, const NNGrid& g, const double* V0, const double* V1,
                      const double* V2, const double* V3, int mode, double* vpred, cudaStream_t s) {
   k_nn_apply<<<blocks_for(g.npts), 256, 0, s>>>(V0, V1, V2, V3, B.out, B.stats, g.npts, mode, vpred);
+  return cudaGetLastError();
+}
+
+cudaError_t add_decide_node(cudaGraph_t g, cudaGraphNode_t* node, const double* res, double thr, const double* vnew,
+                            double* vhxc, int n, double* fb, cudaGraphConditionalHandle handle) {
+  void* args[] = {(void*)&res, (void*)&thr, (void*)&vnew, (void*)&vhxc, (void*)&n, (void*)&fb, (void*)&handle};
+  cudaKernelNodeParams kp{};
+  kp.func = (void*)k_decide;
+  int nb = (n + 255) / 256;
+  kp.gridDim = dim3(nb < 1 ? 1 : (nb > 152 ? 152 : nb));
+  kp.blockDim = dim3(256);
+  kp.sharedMemBytes = 0;
+  kp.kernelParams = args;
+  kp.extra = nullptr;
+  return cudaGraphAddKernelNode(node, g, nullptr, 0, &kp);
+}
+
+cudaError_t launch_store6(double* dst, const double v[6], cudaStream_t s) {
+  k_store6<<<1, 32, 0, s>>>(dst, v[0], v[1], v[2], v[3], v[4], v[5]);
   return cudaGetLastError();
 }
 

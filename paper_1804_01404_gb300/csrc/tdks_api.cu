@@ -124,6 +124,21 @@ struct tdks_ctx {
   void* d_backup = nullptr;      // orbitals at t (predicted steps)
   void* cur_backup = nullptr;    // set while the corrector of a predicted step writes the backup
   double fallbacks = 0, last_resid = 0;
+  // device-side acceptance of predicted steps: a CUDA graph of the decision kernel and a conditional
+  // node whose body restores the orbitals and runs the plain predictor-corrector step (captured once
+  // per orbital array and step settings); the fallback count lives on the device
+  struct FallbackGraph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    const void* u = nullptr;
+    double dt = 0, thr = 0, mbj_c = 0;
+    int lg = -1, has_obs = -1, obs_start = -1, cell_variant = -1, tile0 = -1, tile1 = -1;
+    long long body_launches = 0;
+  } fg;
+  cudaStream_t cap = nullptr;    // private stream the fallback body is captured on
+  double* d_apf = nullptr;       // [6] A'(t+dt/2) and A' of the observables, read by the fallback body
+  double* d_fb = nullptr;        // fallback count (device)
+  double fb_seen = 0;            // fallbacks already added to the launch count
   bool nn_ready = false;
   NNBuffers nn{};
   int nn_step = 0;
@@ -783,6 +798,9 @@ tdks_status tdks_init(const tdks_grid* grid, const tdks_cell* cell, const tdks_a
   if ((s = dalloc(c, &c->d_vhist, 4 * np)) != TDKS_OK) return bail(s);
   if ((s = dalloc(c, &c->d_vnew, npc)) != TDKS_OK) return bail(s);
   if ((s = dalloc(c, &c->d_resid, 2)) != TDKS_OK) return bail(s);
+  if ((s = dalloc(c, &c->d_apf, 6)) != TDKS_OK) return bail(s);
+  if ((s = dalloc(c, &c->d_fb, 1)) != TDKS_OK) return bail(s);
+  if (cudaMemsetAsync(c->d_fb, 0, sizeof(double), c->stream) != cudaSuccess) return bail(fail(TDKS_ECUDA, "memset"));
   if (cudaMallocHost((void**)&c->h_resid, sizeof(double)) != cudaSuccess) return bail(fail(TDKS_ENOMEM, "pinned"));
   if (is_f32(c) && !c->tiled)
     if ((s = dalloc(c, &c->d_rho32, npc * (size_t)nk)) != TDKS_OK) return bail(s);
@@ -893,6 +911,9 @@ void tdks_destroy(tdks_ctx* c) {
   if (c->side) cudaStreamDestroy(c->side);
   for (void* p : c->allocs) cudaFree(p);
   if (c->h_resid) cudaFreeHost(c->h_resid);
+  if (c->fg.exec) cudaGraphExecDestroy(c->fg.exec);
+  if (c->fg.graph) cudaGraphDestroy(c->fg.graph);
+  if (c->cap) cudaStreamDestroy(c->cap);
   delete c;
 }
 
@@ -1366,14 +1387,90 @@ tdks_status pc_step(tdks_ctx* c, void* u, const double Amid[3], const double* Ao
   return TDKS_OK;
 }
 
-// One step with a predicted V~(t+dt) in place of the predictor half-step.  Returns accepted = false
-// (and u restored) when the misfit exceeds the threshold.
-tdks_status predicted_step(tdks_ctx* c, void* u, const double Amid[3], const double* Aobs, bool obs_start,
-                           double dt, bool* accepted) {
+// The fallback of a predicted step as a CUDA graph: the decision node (k_decide: accept V_Hxc(t+dt) or
+// count a fallback) and a conditional node whose body, taken only on rejection, copies the saved
+// orbitals back and runs the plain predictor-corrector step.  The body reads the vector potentials from
+// device memory (d_apf, or the longitudinal geometry's d_ap_mid / d_ap_end), so one graph serves every
+// step with the same orbital array and settings; it is rebuilt when one of them changes.
+static tdks_status ensure_fallback_graph(tdks_ctx* c, void* u, double dt, bool has_obs, bool obs_start) {
+  auto& f = c->fg;
+  const int lg = c->longitudinal ? 1 : 0;
+  if (f.exec && f.u == u && f.dt == dt && f.thr == c->pred_thr && f.lg == lg && f.has_obs == (int)has_obs &&
+      f.obs_start == (int)obs_start && f.cell_variant == c->cell_variant && f.tile0 == c->tile_variant[0] &&
+      f.tile1 == c->tile_variant[1] && f.mbj_c == c->mbj_c_fixed)
+    return TDKS_OK;
+  if (f.exec) { cudaGraphExecDestroy(f.exec); f.exec = nullptr; }
+  if (f.graph) { cudaGraphDestroy(f.graph); f.graph = nullptr; }
+  if (!c->cap) TDKS_CUDA(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+  // the body's launches must follow the work already queued on the context stream: the graph is
+  // launched on that stream, so only the capture itself happens on the private one
+  TDKS_CUDA(cudaGraphCreate(&f.graph, 0));
+  cudaGraphConditionalHandle handle;
+  TDKS_CUDA(cudaGraphConditionalHandleCreate(&handle, f.graph, 0, cudaGraphCondAssignDefault));
+  cudaGraphNode_t dn, cn;
+  TDKS_CUDA(add_decide_node(f.graph, &dn, c->d_resid, c->pred_thr, c->d_vnew, c->d_vhxc, c->npts, c->d_fb, handle));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = handle;
+  cp.conditional.type = cudaGraphCondTypeIf;
+  cp.conditional.size = 1;
+  TDKS_CUDA(cudaGraphAddNode(&cn, f.graph, &dn, nullptr, 1, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+
+  // capture the body: the stream, the vector potentials and the bookkeeping are switched for the
+  // capture and restored afterwards (profiling events cannot sit in a conditional body)
+  const cudaStream_t main = c->stream;
+  const bool prof = c->profiling;
+  const long long launches0 = c->launches;
+  long long calls0[TDKS_NPHASE];
+  std::memcpy(calls0, c->calls, sizeof(calls0));
+  const double* apm = c->cur_ap_mid;
+  const double* ape = c->cur_ap_end;
+  c->stream = c->cap;
+  c->profiling = false;
+  c->cur_ap_mid = lg ? c->d_ap_mid : c->d_apf;
+  c->cur_ap_end = lg ? c->d_ap_end : c->d_apf + 3;
+  const size_t obytes = (size_t)c->nk * c->norb * c->npts * (is_f32(c) ? sizeof(float2) : sizeof(double2));
+  const double zero[3] = {0.0, 0.0, 0.0};
+  tdks_status st = TDKS_OK;
+  cudaError_t e = cudaStreamBeginCaptureToGraph(c->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) {
+    e = cudaMemcpyAsync(u, c->d_backup, obytes, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess) st = pc_step(c, u, zero, has_obs ? zero : nullptr, obs_start, dt);
+    cudaGraph_t out = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(c->stream, &out);
+    if (e == cudaSuccess) e = e2;
+  }
+  f.body_launches = c->launches - launches0;
+  c->launches = launches0;
+  std::memcpy(c->calls, calls0, sizeof(calls0));
+  c->stream = main;
+  c->profiling = prof;
+  c->cur_ap_mid = apm;
+  c->cur_ap_end = ape;
+  if (e != cudaSuccess || st != TDKS_OK) {
+    cudaGetLastError();
+    cudaGraphDestroy(f.graph);
+    f.graph = nullptr;
+    if (st != TDKS_OK) return st;
+    return fail(TDKS_ECUDA, std::string("capture of the fallback step: ") + cudaGetErrorString(e));
+  }
+  TDKS_CUDA(cudaGraphInstantiate(&f.exec, f.graph, 0));
+  f.u = u; f.dt = dt; f.thr = c->pred_thr; f.lg = lg; f.has_obs = has_obs; f.obs_start = obs_start;
+  f.cell_variant = c->cell_variant; f.tile0 = c->tile_variant[0]; f.tile1 = c->tile_variant[1];
+  f.mbj_c = c->mbj_c_fixed;
+  return TDKS_OK;
+}
+
+// One step with a predicted V~(t+dt) in place of the predictor half-step.  The misfit is judged on the
+// device (fallback graph): no host synchronisation.
+static tdks_status predicted_step(tdks_ctx* c, void* u, const double Amid[3], const double* Aobs, bool obs_start,
+                           double dt) {
   const size_t gb = c->npts * sizeof(double);
   const size_t obytes = (size_t)c->nk * c->norb * c->npts * (is_f32(c) ? sizeof(float2) : sizeof(double2));
   const NNGrid g = nn_grid(c);
   const bool net = c->pred_mode == TDKS_PRED_LEARNED;
+  TDKS_TRY(ensure_fallback_graph(c, u, dt, Aobs != nullptr, obs_start));
   {
     Phase ph(c, 5);
     if (net) {   // statistics, packing, three layers; the last one forms the prediction
@@ -1391,6 +1488,11 @@ tdks_status predicted_step(tdks_ctx* c, void* u, const double Amid[3], const dou
     // copies it first
     if (c->tiled) TDKS_CUDA(cudaMemcpyAsync(c->d_backup, u, obytes, cudaMemcpyDeviceToDevice, c->stream));
     TDKS_CUDA(cudaMemsetAsync(c->d_rho, 0, gb, c->stream));
+    if (!c->longitudinal) {   // the fallback body's vector potentials
+      const double v[6] = {Amid[0], Amid[1], Amid[2], Aobs ? Aobs[0] : 0.0, Aobs ? Aobs[1] : 0.0, Aobs ? Aobs[2] : 0.0};
+      TDKS_CUDA(launch_store6(c->d_apf, v, c->stream));
+      c->launches += 1;
+    }
   }
   TDKS_TRY(set_step_potential(c, 0.5, c->d_vpred, 0.5));
   c->cur_backup = c->tiled ? nullptr : c->d_backup;
@@ -1399,17 +1501,11 @@ tdks_status predicted_step(tdks_ctx* c, void* u, const double Amid[3], const dou
   TDKS_TRY(cs);
   TDKS_TRY(hxc(c, c->d_rho, c->d_vnew, u));
   TDKS_CUDA(launch_residual(c->d_vnew, c->d_vpred, c->npts, c->d_partials, c->d_ticket, c->d_resid, c->stream));
-  c->launches += 1;
-  TDKS_CUDA(cudaMemcpyAsync(c->h_resid, c->d_resid, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-  TDKS_CUDA(cudaStreamSynchronize(c->stream));
-  c->last_resid = *c->h_resid;
-  *accepted = std::isfinite(c->last_resid) && c->last_resid <= c->pred_thr;
-  if (*accepted) {
-    TDKS_CUDA(cudaMemcpyAsync(c->d_vhxc, c->d_vnew, gb, cudaMemcpyDeviceToDevice, c->stream));
-  } else {
-    TDKS_CUDA(cudaMemcpyAsync(u, c->d_backup, obytes, cudaMemcpyDeviceToDevice, c->stream));
-    c->fallbacks += 1;
+  {
+    Phase ph(c, 5);
+    TDKS_CUDA(cudaGraphLaunch(c->fg.exec, c->stream));
   }
+  c->launches += 2;
   return TDKS_OK;
 }
 
@@ -1440,11 +1536,11 @@ tdks_status tdks_step(tdks_ctx* c, void* u, double t, double dt) {
     c->cur_ap_mid = c->d_ap_mid;
     c->cur_ap_end = c->d_ap_end;
   }
-  bool done = false;
   tdks_status st = TDKS_OK;
   if (c->pred_mode != TDKS_PRED_PC && c->hist_count >= 4 && (c->opt.hartree || c->opt.xc))
-    st = predicted_step(c, u, Amid, Aobs, at_start, dt, &done);
-  if (st == TDKS_OK && !done) st = pc_step(c, u, Amid, Aobs, at_start, dt);
+    st = predicted_step(c, u, Amid, Aobs, at_start, dt);
+  else
+    st = pc_step(c, u, Amid, Aobs, at_start, dt);
   c->cur_ap_mid = c->cur_ap_end = nullptr;
   TDKS_TRY(st);
   TDKS_TRY(hist_push(c, c->d_vhxc));
@@ -1537,13 +1633,25 @@ tdks_status tdks_ms_read(tdks_ctx* c, double* A_host, double* I_host) {
 }
 
 
+// Read the device fallback count (synchronises the stream); the launches of the fallback bodies that
+// ran since the last read join the launch count.
+static tdks_status sync_fallbacks(tdks_ctx* c) {
+  double fb = 0.0;
+  TDKS_CUDA(cudaMemcpyAsync(&fb, c->d_fb, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  TDKS_CUDA(cudaStreamSynchronize(c->stream));
+  if (fb > c->fb_seen) c->launches += (long long)(fb - c->fb_seen) * c->fg.body_launches;
+  c->fb_seen = fb;
+  c->fallbacks = fb;
+  return TDKS_OK;
+}
+
 tdks_status tdks_read_step_observables(tdks_ctx* c, tdks_obs* o) {
   TDKS_TRY(check_ctx(c));
   if (!o) return fail(TDKS_EINVAL, "null output");
   double h[8], r = 0.0;
   TDKS_CUDA(cudaMemcpyAsync(h, c->d_step_obs, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
   TDKS_CUDA(cudaMemcpyAsync(&r, c->d_resid, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-  TDKS_CUDA(cudaStreamSynchronize(c->stream));
+  TDKS_TRY(sync_fallbacks(c));
   std::memset(o, 0, sizeof(*o));
   for (int a = 0; a < 3; ++a) { o->J[a] = h[a]; o->dipole[a] = h[3 + a]; }
   o->n_elec = h[6];
@@ -1798,7 +1906,7 @@ tdks_status tdks_profile(tdks_ctx* c, int enable) {
 tdks_status tdks_stats_read(tdks_ctx* c, tdks_stats* out, int reset) {
   TDKS_TRY(check_ctx(c));
   if (!out) return fail(TDKS_EINVAL, "null output");
-  TDKS_CUDA(cudaStreamSynchronize(c->stream));
+  TDKS_TRY(sync_fallbacks(c));
   for (auto& r : c->recs) {
     float ms = 0.0f;
     TDKS_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
@@ -1893,6 +2001,7 @@ tdks_status tdks_state_size(const tdks_ctx* c, size_t* bytes) {
 tdks_status tdks_get_state(tdks_ctx* c, void* host, size_t bytes) {
   TDKS_TRY(check_ctx(c));
   if (!host || bytes < state_bytes(c)) return fail(TDKS_EINVAL, "state buffer smaller than tdks_state_size");
+  TDKS_TRY(sync_fallbacks(c));
   StateHeader h;
   std::memset(&h, 0, sizeof(h));
   std::memcpy(h.magic, "TDKSSTA2", 8);
@@ -1991,6 +2100,8 @@ tdks_status tdks_set_state(tdks_ctx* c, const void* host, size_t bytes) {
   c->have_rho0 = h.have_rho0; c->have_potential = h.have_potential;
   c->hist_head = h.hist_head; c->hist_count = h.hist_count;
   c->pred_thr = h.pred_thr; c->fallbacks = h.fallbacks; c->last_resid = h.last_resid;
+  c->fb_seen = h.fallbacks;
+  TDKS_CUDA(cudaMemcpyAsync(c->d_fb, &c->fallbacks, sizeof(double), cudaMemcpyHostToDevice, c->stream));
   c->field_kind = h.field_kind;
   for (int a = 0; a < 3; ++a) c->A0[a] = h.A0[a];
   c->pulses.assign(h.pulse, h.pulse + h.npulse);

@@ -212,6 +212,12 @@ cudaError_t nn_apply(const NNBuffers& B, const NNGrid& g, const double* V0, cons
 // partials: [304][2] doubles, ticket: one unsigned that is zero between launches (grid_sum)
 cudaError_t launch_residual(const double* Vnew, const double* Vpred, int n, double* partials, unsigned* ticket,
                             double* res, cudaStream_t s);
+// Graph node of the device-side acceptance of a predicted potential: vhxc <- vnew if *res <= thr (finite),
+// else *fb += 1 and the conditional `handle` is set to 1 (0 when accepted).
+cudaError_t add_decide_node(cudaGraph_t g, cudaGraphNode_t* node, const double* res, double thr, const double* vnew,
+                            double* vhxc, int n, double* fb, cudaGraphConditionalHandle handle);
+// dst[0..5] <- v[0..5] (six doubles passed by value, so the host buffer may change right after the call)
+cudaError_t launch_store6(double* dst, const double v[6], cudaStream_t s);
 
 // Grid kernels (k_grid.cu)
 // Hartree + exchange in five fused FFT line passes: vhxc = V_H[rho] (+ V_x[rho] if xc).  work: the
