@@ -377,6 +377,236 @@ __global__ void k_store6(double* dst, double a0, double a1, double a2, double a3
   }
 }
 
+// ---------------------------------------------------------------------------------------------
+// The whole prediction in one cooperative launch: statistics, input packing and the three layers are
+// phases separated by grid barriers (every CTA is resident, so a CTA waits only for the others to
+// finish the phase before).  Layer 2 (16 -> 16 channels, the bulk of the work) is an implicit GEMM on
+// the tensor cores: a warp takes 16 grid points, and for each of the 27 taps multiplies the 16 x 16
+// BF16 matrix of its points' neighbour activations by the tap's 16 x 16 BF16 weight matrix with
+// mma.sync (m16n8k16, two n-halves), accumulating in FP32.  Layers 1 and 3 (4 -> 16 and 16 -> 1) are
+// small and run on the CUDA cores.  Arithmetic per value is that of k_nn_stats, k_nn_pack and k_nn_fwd.
+// ---------------------------------------------------------------------------------------------
+constexpr int kFusedThreads = 256;
+constexpr int kFusedMaxBlocks = 304;   // partials of the statistics: [304][5]
+
+struct FusedArgs {
+  NNGrid g;
+  const double *V0, *V1, *V2, *V3;
+  double* vpred;
+  const float *W1, *b1, *W2, *b2, *W3, *b3;   // BF16-rounded parameters, FP32 containers
+  bf16 *x0, *a1, *a2;        // channel-last [npts][4], [npts][16], [npts][16]
+  double* stats;             // out: s1, s2, s3, mean V0, s_V
+  double* part;              // [gridDim.x][5]
+  unsigned* bar;             // grid-barrier counter, zero at launch
+  int* err;                  // TDKS_ETIMEOUT if a barrier wait gives up
+  long long limit;           // polls per barrier wait
+};
+
+// Grid barrier number k (targets k * gridDim.x arrivals) with a bounded wait: false (and *err set) if
+// the other CTAs did not all arrive within the poll limit.
+__device__ __forceinline__ bool fused_barrier(const FusedArgs& A, unsigned k, int* ok_s) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(A.bar, 1u);
+    const unsigned target = k * gridDim.x;
+    long long it = 0;
+    unsigned v = *(volatile unsigned*)A.bar;
+    while (v < target && ++it < A.limit) {
+      __nanosleep(40);
+      v = *(volatile unsigned*)A.bar;
+    }
+    __threadfence();
+    *ok_s = v >= target;
+    if (!*ok_s) atomicExch(A.err, 4);            // TDKS_ETIMEOUT
+  }
+  __syncthreads();
+  return *ok_s != 0;
+}
+
+__device__ __forceinline__ unsigned pack_bf16x2(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const unsigned*>(&v);
+}
+
+__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__global__ void __launch_bounds__(kFusedThreads) k_nn_predict(FusedArgs A) {
+  __shared__ float W1s[27][4][16];
+  __shared__ float W3s[27][16];
+  __shared__ float b1s[16], b2s[16], b3s;
+  __shared__ uint2 Bf[27][2][32];      // layer-2 weights as mma B fragments [tap][n-half][lane]
+  __shared__ double red[5][8];
+  __shared__ double st[5];
+  __shared__ int ok_s;
+  const NNGrid& g = A.g;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const long long nthr = (long long)gridDim.x * blockDim.x;
+  const long long gtid = (long long)blockIdx.x * blockDim.x + tid;
+  // weights (read through their BF16 rounding, as stored)
+  const float* W1 = A.W1;
+  const float* W2 = A.W2;
+  const float* W3 = A.W3;
+  for (int i = tid; i < 16 * 4 * 27; i += blockDim.x) {
+    const int co = i / (4 * 27), r = i % (4 * 27), ci = r / 27, kk = r % 27;
+    W1s[kk][ci][co] = W1[i];
+  }
+  for (int i = tid; i < 16 * 27; i += blockDim.x) W3s[i % 27][i / 27] = W3[i];
+  if (tid < 16) { b1s[tid] = A.b1[tid]; b2s[tid] = A.b2[tid]; }
+  if (tid == 0) b3s = A.b3[0];
+  for (int i = tid; i < 27 * 2 * 32; i += blockDim.x) {
+    const int kk = i / 64, h = (i / 32) % 2, l = i % 32;
+    const int n = 8 * h + (l >> 2), k0 = 2 * (l & 3);
+    auto w = [&](int ci) { return W2[(n * 16 + ci) * 27 + kk]; };
+    Bf[kk][h][l] = make_uint2(pack_bf16x2(w(k0), w(k0 + 1)), pack_bf16x2(w(k0 + 8), w(k0 + 9)));
+  }
+
+  // phase 1: statistics of the backward differences (FP64), per-CTA partials
+  {
+    double acc[5] = {0, 0, 0, 0, 0};
+    for (long long p = gtid; p < g.npts; p += nthr) {
+      const double v0 = A.V0[p], v1 = A.V1[p], v2 = A.V2[p], v3 = A.V3[p];
+      const double d1 = v0 - v1, d2 = d1 - (v1 - v2), d3 = d2 - ((v1 - v2) - (v2 - v3));
+      acc[0] += d1 * d1; acc[1] += d2 * d2; acc[2] += d3 * d3; acc[3] += v0; acc[4] += v0 * v0;
+    }
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+      double x = acc[j];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      if (lane == 0) red[j][warp] = x;
+    }
+    __syncthreads();
+    if (tid < 5) {
+      double x = 0;
+      for (int w = 0; w < kFusedThreads / 32; ++w) x += red[tid][w];
+      A.part[(size_t)blockIdx.x * 5 + tid] = x;
+    }
+  }
+  if (!fused_barrier(A, 1, &ok_s)) return;
+  if (warp < 5) {       // totals in a fixed order: lane l sums CTAs l, l + 32, ..., then a shuffle tree
+    double x = 0;
+    for (unsigned b = lane; b < gridDim.x; b += 32) x += __ldcg(&A.part[(size_t)b * 5 + warp]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) st[warp] = x;
+  }
+  __syncthreads();
+  double s1, s2, s3, mean, sv;
+  {
+    const double n = (double)g.npts;
+    mean = st[3] / n;
+    const double fl = 1e-13 * sqrt(st[4] / n) + 1e-300;
+    s1 = fmax(sqrt(st[0] / n), fl);
+    s2 = fmax(sqrt(st[1] / n), fl);
+    s3 = fmax(sqrt(st[2] / n), fl);
+    sv = fmax(sqrt(fmax(st[4] / n - mean * mean, 0.0)), fl);
+    if (blockIdx.x == 0 && tid == 0) {
+      A.stats[0] = s1; A.stats[1] = s2; A.stats[2] = s3; A.stats[3] = mean; A.stats[4] = sv;
+    }
+  }
+  // phase 2: the four input channels of every point (BF16, channel-last)
+  for (long long p = gtid; p < g.npts; p += nthr) {
+    const double v0 = A.V0[p], v1 = A.V1[p], v2 = A.V2[p], v3 = A.V3[p];
+    const double d1 = v0 - v1, d2 = v0 - 2.0 * v1 + v2, d3 = v0 - 3.0 * v1 + 3.0 * v2 - v3;
+    uint2 r;
+    r.x = *reinterpret_cast<const unsigned*>(&(const __nv_bfloat162&)make_bfloat162(
+        __float2bfloat16((float)(d1 / s1)), __float2bfloat16((float)(d2 / s2))));
+    r.y = *reinterpret_cast<const unsigned*>(&(const __nv_bfloat162&)make_bfloat162(
+        __float2bfloat16((float)(d3 / s3)), __float2bfloat16((float)((v0 - mean) / sv))));
+    *reinterpret_cast<uint2*>(A.x0 + 4 * p) = r;
+  }
+  if (!fused_barrier(A, 2, &ok_s)) return;
+  // phase 3: layer 1 (4 -> 16), four lanes per point, four outputs each
+  for (long long t = gtid; t < 4LL * g.npts; t += nthr) {
+    const int p = (int)(t >> 2), og = (int)(t & 3);
+    int px, py, pz;
+    coords(g, p, px, py, pz);
+    float acc[4];
+#pragma unroll
+    for (int o = 0; o < 4; ++o) acc[o] = b1s[og * 4 + o];
+    for (int kk = 0; kk < 27; ++kk) {
+      const int q = nb_index(g, px, py, pz, kk % 3 - 1, (kk / 3) % 3 - 1, kk / 9 - 1);
+      if (q < 0) continue;
+      float xv[4];
+      load_bf16<4>(A.x0 + 4 * (size_t)q, xv);
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int o = 0; o < 4; ++o) acc[o] = fmaf(W1s[kk][c][og * 4 + o], xv[c], acc[o]);
+    }
+    uint2 r;
+    r.x = pack_bf16x2(silu(acc[0]), silu(acc[1]));
+    r.y = pack_bf16x2(silu(acc[2]), silu(acc[3]));
+    *reinterpret_cast<uint2*>(A.a1 + 16 * (size_t)p + 4 * og) = r;
+  }
+  if (!fused_barrier(A, 3, &ok_s)) return;
+  // phase 4: layer 2 (16 -> 16) on the tensor cores, 16 points per warp
+  {
+    const int grp = lane >> 2, tq = lane & 3;
+    const int ntile = (g.npts + 15) / 16;
+    const int nwarp = gridDim.x * (blockDim.x / 32);
+    const unsigned* a1w = reinterpret_cast<const unsigned*>(A.a1);   // 8 words per point
+    for (int tile = blockIdx.x * (blockDim.x / 32) + warp; tile < ntile; tile += nwarp) {
+      const int r0 = tile * 16 + grp, r1 = r0 + 8;
+      const bool v0ok = r0 < g.npts, v1ok = r1 < g.npts;
+      int x0, y0, z0, x1, y1, z1;
+      coords(g, v0ok ? r0 : 0, x0, y0, z0);
+      coords(g, v1ok ? r1 : 0, x1, y1, z1);
+      float d[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+      for (int kk = 0; kk < 27; ++kk) {
+        const int dx = kk % 3 - 1, dy = (kk / 3) % 3 - 1, dz = kk / 9 - 1;
+        const int q0 = v0ok ? nb_index(g, x0, y0, z0, dx, dy, dz) : -1;
+        const int q1 = v1ok ? nb_index(g, x1, y1, z1, dx, dy, dz) : -1;
+        unsigned a[4];
+        a[0] = q0 >= 0 ? a1w[8 * (size_t)q0 + tq] : 0u;
+        a[1] = q1 >= 0 ? a1w[8 * (size_t)q1 + tq] : 0u;
+        a[2] = q0 >= 0 ? a1w[8 * (size_t)q0 + tq + 4] : 0u;
+        a[3] = q1 >= 0 ? a1w[8 * (size_t)q1 + tq + 4] : 0u;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const uint2 b = Bf[kk][h][lane];
+          mma_bf16_16816(d[h], a, b.x, b.y);
+        }
+      }
+      unsigned* a2w = reinterpret_cast<unsigned*>(A.a2);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int c0 = 8 * h + 2 * tq;
+        if (v0ok) a2w[8 * (size_t)r0 + 4 * h + tq] = pack_bf16x2(silu(d[h][0] + b2s[c0]), silu(d[h][1] + b2s[c0 + 1]));
+        if (v1ok) a2w[8 * (size_t)r1 + 4 * h + tq] = pack_bf16x2(silu(d[h][2] + b2s[c0]), silu(d[h][3] + b2s[c0 + 1]));
+      }
+    }
+  }
+  if (!fused_barrier(A, 4, &ok_s)) return;
+  // phase 5: layer 3 (16 -> 1), four lanes per point splitting the channels, and the prediction
+  for (long long t0 = (long long)blockIdx.x * blockDim.x; t0 < 4LL * g.npts; t0 += nthr) {
+    const long long t = t0 + tid;                  // every lane of the warp takes part in the shuffles
+    const bool act = t < 4LL * g.npts;
+    const int p = act ? (int)(t >> 2) : 0, cs = (int)(t & 3);
+    int px, py, pz;
+    coords(g, p, px, py, pz);
+    float acc = (cs == 0) ? b3s : 0.f;
+    for (int kk = 0; kk < 27; ++kk) {
+      const int q = act ? nb_index(g, px, py, pz, kk % 3 - 1, (kk / 3) % 3 - 1, kk / 9 - 1) : -1;
+      if (q < 0) continue;
+      float xv[4];
+      load_bf16<4>(A.a2 + 16 * (size_t)q + 4 * cs, xv);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc = fmaf(W3s[kk][4 * cs + c], xv[c], acc);
+    }
+    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+    if (act && cs == 0) A.vpred[p] = cubic(A.V0[p], A.V1[p], A.V2[p], A.V3[p]) + s3 * (double)acc;
+  }
+}
+
 int blocks_for(int n) {
   int b = (n + 255) / 256;
   return b > 152 * 8 ? 152 * 8 : (b < 1 ? 1 : b);
@@ -456,6 +686,30 @@ cudaError_t nn_apply(const NNBuffers& B, const NNGrid& g, const double* V0, cons
                      const double* V2, const double* V3, int mode, double* vpred, cudaStream_t s) {
   k_nn_apply<<<blocks_for(g.npts), 256, 0, s>>>(V0, V1, V2, V3, B.out, B.stats, g.npts, mode, vpred);
   return cudaGetLastError();
+}
+
+cudaError_t nn_predict_fused(const NNBuffers& B, const NNGrid& g, const NNPredict& pr, long long wait_limit,
+                             cudaStream_t s) {
+  static int nsm = 0, occ = 0;
+  if (nsm == 0) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_nn_predict, kFusedThreads, 0);
+    if (e != cudaSuccess) { nsm = 0; return e; }
+  }
+  long long want = (4LL * g.npts + kFusedThreads - 1) / kFusedThreads;
+  long long nb = (long long)nsm * occ;
+  if (nb > kFusedMaxBlocks) nb = kFusedMaxBlocks;
+  if (nb > want) nb = want;
+  if (nb < 1) nb = 1;
+  cudaError_t e = cudaMemsetAsync(B.bar, 0, sizeof(unsigned), s);
+  if (e != cudaSuccess) return e;
+  FusedArgs A{g, pr.V0, pr.V1, pr.V2, pr.V3, pr.vpred,
+              B.wq + kNNOff[0], B.wq + kNNOff[1], B.wq + kNNOff[2], B.wq + kNNOff[3], B.wq + kNNOff[4], B.wq + kNNOff[5],
+              B16(B.x0), B16(B.a1), B16(B.a2), B.stats, B.red, B.bar, B.err, wait_limit};
+  void* args[] = {&A};
+  return cudaLaunchCooperativeKernel((const void*)k_nn_predict, dim3((unsigned)nb), dim3(kFusedThreads), args, 0, s);
 }
 
 cudaError_t add_decide_node(cudaGraph_t g, cudaGraphNode_t* node, const double* res, double thr, const double* vnew,

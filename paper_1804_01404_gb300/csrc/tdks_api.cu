@@ -1473,12 +1473,10 @@ static tdks_status predicted_step(tdks_ctx* c, void* u, const double Amid[3], co
   TDKS_TRY(ensure_fallback_graph(c, u, dt, Aobs != nullptr, obs_start));
   {
     Phase ph(c, 5);
-    if (net) {   // statistics, packing, three layers; the last one forms the prediction
+    if (net) {   // statistics, packing and the three layers in one cooperative launch
       const NNPredict pr{hist_slot(c, 0), hist_slot(c, 1), hist_slot(c, 2), hist_slot(c, 3), c->d_vpred};
-      TDKS_CUDA(nn_inputs(c->nn, g, hist_slot(c, 0), hist_slot(c, 1), hist_slot(c, 2), hist_slot(c, 3), nullptr,
-                          c->stream, true));
-      TDKS_CUDA(nn_forward(c->nn, g, c->stream, &pr));
-      c->launches += 5;
+      TDKS_CUDA(nn_predict_fused(c->nn, g, pr, c->wait_limit, c->stream));
+      c->launches += 1;
     } else {
       TDKS_CUDA(nn_apply(c->nn, g, hist_slot(c, 0), hist_slot(c, 1), hist_slot(c, 2), hist_slot(c, 3), 1,
                          c->d_vpred, c->stream));
@@ -1789,7 +1787,9 @@ tdks_status tdks_nn_init(tdks_ctx* c, unsigned long long seed) {
     TDKS_TRY(dalloc(c, &B.loss, 1));
     TDKS_TRY(dalloc(c, &B.red, 304 * 5));
     TDKS_TRY(dalloc(c, &B.ticket, 1));
+    TDKS_TRY(dalloc(c, &B.bar, 1));
     TDKS_CUDA(cudaMemsetAsync(B.ticket, 0, sizeof(unsigned), c->stream));
+    B.err = c->d_err;
   }
   std::vector<float> p(kNNParams, 0.0f);
   const int fan[3] = {4 * 27, 16 * 27, 16 * 27};
@@ -1867,12 +1867,14 @@ tdks_status tdks_nn_predict(tdks_ctx* c, const double* vhist, double* vpred, int
   if (mode < 0 || mode > 2) return fail(TDKS_EINVAL, "mode must be 0 (linear), 1 (cubic) or 2 (network)");
   const NNGrid g = nn_grid(c);
   const size_t np = c->npts;
-  TDKS_CUDA(nn_inputs(c->nn, g, vhist, vhist + np, vhist + 2 * np, vhist + 3 * np, nullptr, c->stream, mode == 2));
   if (mode == 2) {
     const NNPredict pr{vhist, vhist + np, vhist + 2 * np, vhist + 3 * np, vpred};
-    TDKS_CUDA(nn_forward(c->nn, g, c->stream, &pr));
+    TDKS_CUDA(nn_predict_fused(c->nn, g, pr, c->wait_limit, c->stream));
+    c->launches += 1;
   } else {
+    TDKS_CUDA(nn_inputs(c->nn, g, vhist, vhist + np, vhist + 2 * np, vhist + 3 * np, nullptr, c->stream, false));
     TDKS_CUDA(nn_apply(c->nn, g, vhist, vhist + np, vhist + 2 * np, vhist + 3 * np, mode, vpred, c->stream));
+    c->launches += 3;
   }
   return TDKS_OK;
 }

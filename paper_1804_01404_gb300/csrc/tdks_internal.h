@@ -188,6 +188,8 @@ struct NNBuffers {
   double* loss;                                   // accumulator
   double* red;                                    // [304][5] grid_sum partials of the statistics
   unsigned* ticket;                               // grid_sum ticket (zero between launches)
+  unsigned* bar;                                  // grid-barrier counter of the fused prediction
+  int* err;                                       // context error word (TDKS_ETIMEOUT of a barrier wait)
 };
 int nn_part_blocks(int npts);
 // channel_last: inputs for nn_forward with a prediction epilogue (which reads them channel-last)
@@ -202,6 +204,11 @@ struct NNPredict {
   double* vpred;
 };
 cudaError_t nn_forward(const NNBuffers& B, const NNGrid& g, cudaStream_t s, const NNPredict* pred = nullptr);
+// The prediction V~ = cubic + s3 * NN in one cooperative launch (statistics, inputs and three layers
+// separated by grid barriers whose waits give up after wait_limit polls and set *B.err).  Same values
+// as nn_inputs + nn_forward(pred) up to the FP32 summation order of the tensor-core layer.
+cudaError_t nn_predict_fused(const NNBuffers& B, const NNGrid& g, const NNPredict& pr, long long wait_limit,
+                             cudaStream_t s);
 cudaError_t nn_loss(const NNBuffers& B, const NNGrid& g, double* loss_acc, cudaStream_t s);
 cudaError_t nn_backward(const NNBuffers& B, const NNGrid& g, cudaStream_t s);   // grad +=
 cudaError_t nn_adam(const NNBuffers& B, float lr, int t, float gscale, cudaStream_t s);
