@@ -326,6 +326,14 @@ tdks_status tdks_ms_size(const tdks_ctx* ctx, int* nX);
 enum { TDKS_PRED_PC = 0, TDKS_PRED_EXTRAP = 1, TDKS_PRED_LEARNED = 2 };
 tdks_status tdks_set_predictor(tdks_ctx* ctx, int mode, double threshold);
 
+/* How predicted steps are issued (no counterpart in the paper).  enable = 1 (default): as the CUDA graph
+ * described above (one per slot of the four-potential history, so that the graph's buffers are fixed),
+ * with the decision on the device.  enable = 0: the same kernels launched one by one on the stream, the
+ * misfit copied to the host and the fallback enqueued from there (one synchronisation per step; every
+ * kernel appears as its own launch to profilers, which do not time the kernel nodes of graphs that hold
+ * conditional nodes).  Both give the same results.  Errors: EINVAL for enable outside 0..1. */
+tdks_status tdks_set_step_graph(tdks_ctx* ctx, int enable);
+
 /* ---- Learned potential predictor ------------------------------------------------------------
  * A 3-layer 3D convolutional network (4 -> 16 -> 16 -> 1 channels, 3^3 kernels with bias, SiLU,
  * circular padding for periodic grids, zero padding for isolated ones) with BF16 weights and

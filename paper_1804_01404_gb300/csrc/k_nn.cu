@@ -393,7 +393,7 @@ struct FusedArgs {
   NNGrid g;
   const double *V0, *V1, *V2, *V3;
   double* vpred;
-  const float *W1, *b1, *W2, *b2, *W3, *b3;   // BF16-rounded parameters, FP32 containers
+  const uint4* wpack;        // FusedWeights image of the BF16-rounded parameters
   bf16 *x0, *a1, *a2;        // channel-last [npts][4], [npts][16], [npts][16]
   double* stats;             // out: s1, s2, s3, mean V0, s_V
   double* part;              // [gridDim.x][5]
@@ -437,11 +437,58 @@ __device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const unsigned (&a
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-__global__ void __launch_bounds__(kFusedThreads) k_nn_predict(FusedArgs A) {
-  __shared__ float W1s[27][4][16];
-  __shared__ float W3s[27][16];
-  __shared__ float b1s[16], b2s[16], b3s;
-  __shared__ uint2 Bf[27][2][32];      // layer-2 weights as mma B fragments [tap][n-half][lane]
+// Neighbour indices of the 27 taps (the layer loops are fully unrolled so that every neighbour's load
+// is issued before the arithmetic that uses it; these layers are bound by load latency).
+__device__ __forceinline__ void tap_index(const NNGrid& g, int x, int y, int z, bool valid, int (&q)[27]) {
+#pragma unroll
+  for (int kk = 0; kk < 27; ++kk)
+    q[kk] = valid ? nb_index(g, x, y, z, kk % 3 - 1, (kk / 3) % 3 - 1, kk / 9 - 1) : -1;
+}
+
+// The weights as the prediction kernel holds them in shared memory, laid out once per parameter update
+// (k_nn_pack_weights) so that every CTA copies them with a few 16-byte loads per thread.
+struct alignas(16) FusedWeights {
+  float W1s[27][4][16];
+  float W3s[27][16];
+  float b1s[16], b2s[16];
+  float b3s[4];
+  uint2 Bf[27][2][32];      // layer-2 weights as mma B fragments [tap][n-half][lane]
+};
+static_assert(sizeof(FusedWeights) % 16 == 0, "copied as uint4");
+constexpr int kFusedWeightVecs = sizeof(FusedWeights) / 16;
+
+static_assert(kNNOff[1] == 1728 && kNNOff[2] == 1744 && kNNOff[3] == 8656 && kNNOff[4] == 8672 && kNNOff[5] == 9104,
+              "parameter offsets used by k_nn_pack_weights");
+__global__ void k_nn_pack_weights(const float* __restrict__ wq, FusedWeights* __restrict__ out) {
+  const float* W1 = wq + 0;
+  const float* W2 = wq + 1744;
+  const float* W3 = wq + 8672;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 16 * 4 * 27; i += gridDim.x * blockDim.x) {
+    const int co = i / (4 * 27), r = i % (4 * 27), ci = r / 27, kk = r % 27;
+    out->W1s[kk][ci][co] = W1[i];
+  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 16 * 27; i += gridDim.x * blockDim.x)
+    out->W3s[i % 27][i / 27] = W3[i];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 16; i += gridDim.x * blockDim.x) {
+    out->b1s[i] = wq[1728 + i];
+    out->b2s[i] = wq[8656 + i];
+    if (i < 4) out->b3s[i] = (i == 0) ? wq[9104] : 0.f;
+  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 27 * 2 * 32; i += gridDim.x * blockDim.x) {
+    const int kk = i / 64, h = (i / 32) % 2, l = i % 32;
+    const int n = 8 * h + (l >> 2), k0 = 2 * (l & 3);
+    auto w = [&](int ci) { return W2[(n * 16 + ci) * 27 + kk]; };
+    out->Bf[kk][h][l] = make_uint2(pack_bf16x2(w(k0), w(k0 + 1)), pack_bf16x2(w(k0 + 8), w(k0 + 9)));
+  }
+}
+
+__global__ void __launch_bounds__(kFusedThreads, 1) k_nn_predict(FusedArgs A) {
+  __shared__ FusedWeights Ws;
+  float (&W1s)[27][4][16] = Ws.W1s;
+  float (&W3s)[27][16] = Ws.W3s;
+  float (&b1s)[16] = Ws.b1s;
+  float (&b2s)[16] = Ws.b2s;
+  uint2 (&Bf)[27][2][32] = Ws.Bf;
   __shared__ double red[5][8];
   __shared__ double st[5];
   __shared__ int ok_s;
@@ -449,23 +496,24 @@ __global__ void __launch_bounds__(kFusedThreads) k_nn_predict(FusedArgs A) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const long long nthr = (long long)gridDim.x * blockDim.x;
   const long long gtid = (long long)blockIdx.x * blockDim.x + tid;
-  // weights (read through their BF16 rounding, as stored)
-  const float* W1 = A.W1;
-  const float* W2 = A.W2;
-  const float* W3 = A.W3;
-  for (int i = tid; i < 16 * 4 * 27; i += blockDim.x) {
-    const int co = i / (4 * 27), r = i % (4 * 27), ci = r / 27, kk = r % 27;
-    W1s[kk][ci][co] = W1[i];
+  // weights (read through their BF16 rounding, as stored): the packed image, all loads in flight at once
+  {
+    constexpr int PER = (kFusedWeightVecs + kFusedThreads - 1) / kFusedThreads;
+    uint4 tmp[PER];
+    uint4* dst = reinterpret_cast<uint4*>(&Ws);
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+      const int i = tid + j * kFusedThreads;
+      if (i < kFusedWeightVecs) tmp[j] = __ldg(A.wpack + i);
+    }
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+      const int i = tid + j * kFusedThreads;
+      if (i < kFusedWeightVecs) dst[i] = tmp[j];
+    }
   }
-  for (int i = tid; i < 16 * 27; i += blockDim.x) W3s[i % 27][i / 27] = W3[i];
-  if (tid < 16) { b1s[tid] = A.b1[tid]; b2s[tid] = A.b2[tid]; }
-  if (tid == 0) b3s = A.b3[0];
-  for (int i = tid; i < 27 * 2 * 32; i += blockDim.x) {
-    const int kk = i / 64, h = (i / 32) % 2, l = i % 32;
-    const int n = 8 * h + (l >> 2), k0 = 2 * (l & 3);
-    auto w = [&](int ci) { return W2[(n * 16 + ci) * 27 + kk]; };
-    Bf[kk][h][l] = make_uint2(pack_bf16x2(w(k0), w(k0 + 1)), pack_bf16x2(w(k0 + 8), w(k0 + 9)));
-  }
+  __syncthreads();
+  const float b3s = Ws.b3s[0];
 
   // phase 1: statistics of the backward differences (FP64), per-CTA partials
   {
@@ -528,14 +576,20 @@ __global__ void __launch_bounds__(kFusedThreads) k_nn_predict(FusedArgs A) {
     const int p = (int)(t >> 2), og = (int)(t & 3);
     int px, py, pz;
     coords(g, p, px, py, pz);
+    int q[27];
+    tap_index(g, px, py, pz, true, q);
+    uint2 raw[27];
+#pragma unroll
+    for (int kk = 0; kk < 27; ++kk)
+      raw[kk] = q[kk] >= 0 ? *reinterpret_cast<const uint2*>(A.x0 + 4 * (size_t)q[kk]) : make_uint2(0u, 0u);
     float acc[4];
 #pragma unroll
     for (int o = 0; o < 4; ++o) acc[o] = b1s[og * 4 + o];
+#pragma unroll
     for (int kk = 0; kk < 27; ++kk) {
-      const int q = nb_index(g, px, py, pz, kk % 3 - 1, (kk / 3) % 3 - 1, kk / 9 - 1);
-      if (q < 0) continue;
-      float xv[4];
-      load_bf16<4>(A.x0 + 4 * (size_t)q, xv);
+      const float2 lo = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&raw[kk].x));
+      const float2 hi = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&raw[kk].y));
+      const float xv[4] = {lo.x, lo.y, hi.x, hi.y};
 #pragma unroll
       for (int c = 0; c < 4; ++c)
 #pragma unroll
@@ -560,20 +614,28 @@ __global__ void __launch_bounds__(kFusedThreads) k_nn_predict(FusedArgs A) {
       coords(g, v0ok ? r0 : 0, x0, y0, z0);
       coords(g, v1ok ? r1 : 0, x1, y1, z1);
       float d[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
-      for (int kk = 0; kk < 27; ++kk) {
-        const int dx = kk % 3 - 1, dy = (kk / 3) % 3 - 1, dz = kk / 9 - 1;
-        const int q0 = v0ok ? nb_index(g, x0, y0, z0, dx, dy, dz) : -1;
-        const int q1 = v1ok ? nb_index(g, x1, y1, z1, dx, dy, dz) : -1;
-        unsigned a[4];
-        a[0] = q0 >= 0 ? a1w[8 * (size_t)q0 + tq] : 0u;
-        a[1] = q1 >= 0 ? a1w[8 * (size_t)q1 + tq] : 0u;
-        a[2] = q0 >= 0 ? a1w[8 * (size_t)q0 + tq + 4] : 0u;
-        a[3] = q1 >= 0 ? a1w[8 * (size_t)q1 + tq + 4] : 0u;
+      int q0[27], q1[27];
+      tap_index(g, x0, y0, z0, v0ok, q0);
+      tap_index(g, x1, y1, z1, v1ok, q1);
+      // the taps in three batches of nine: the batch's 36 words are loaded before its 18 MMAs
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const uint2 b = Bf[kk][h][lane];
-          mma_bf16_16816(d[h], a, b.x, b.y);
+      for (int k0 = 0; k0 < 27; k0 += 9) {
+        unsigned a[9][4];
+#pragma unroll
+        for (int j = 0; j < 9; ++j) {
+          const int kk = k0 + j;
+          a[j][0] = q0[kk] >= 0 ? a1w[8 * (size_t)q0[kk] + tq] : 0u;
+          a[j][1] = q1[kk] >= 0 ? a1w[8 * (size_t)q1[kk] + tq] : 0u;
+          a[j][2] = q0[kk] >= 0 ? a1w[8 * (size_t)q0[kk] + tq + 4] : 0u;
+          a[j][3] = q1[kk] >= 0 ? a1w[8 * (size_t)q1[kk] + tq + 4] : 0u;
         }
+#pragma unroll
+        for (int j = 0; j < 9; ++j)
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const uint2 b = Bf[k0 + j][h][lane];
+            mma_bf16_16816(d[h], a[j], b.x, b.y);
+          }
       }
       unsigned* a2w = reinterpret_cast<unsigned*>(A.a2);
 #pragma unroll
@@ -592,14 +654,21 @@ __global__ void __launch_bounds__(kFusedThreads) k_nn_predict(FusedArgs A) {
     const int p = act ? (int)(t >> 2) : 0, cs = (int)(t & 3);
     int px, py, pz;
     coords(g, p, px, py, pz);
-    float acc = (cs == 0) ? b3s : 0.f;
-    for (int kk = 0; kk < 27; ++kk) {
-      const int q = act ? nb_index(g, px, py, pz, kk % 3 - 1, (kk / 3) % 3 - 1, kk / 9 - 1) : -1;
-      if (q < 0) continue;
-      float xv[4];
-      load_bf16<4>(A.a2 + 16 * (size_t)q + 4 * cs, xv);
+    int q[27];
+    tap_index(g, px, py, pz, act, q);
+    uint2 raw[27];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) acc = fmaf(W3s[kk][4 * cs + c], xv[c], acc);
+    for (int kk = 0; kk < 27; ++kk)
+      raw[kk] = q[kk] >= 0 ? *reinterpret_cast<const uint2*>(A.a2 + 16 * (size_t)q[kk] + 4 * cs) : make_uint2(0u, 0u);
+    float acc = (cs == 0) ? b3s : 0.f;
+#pragma unroll
+    for (int kk = 0; kk < 27; ++kk) {
+      const float2 lo = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&raw[kk].x));
+      const float2 hi = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&raw[kk].y));
+      acc = fmaf(W3s[kk][4 * cs], lo.x, acc);
+      acc = fmaf(W3s[kk][4 * cs + 1], lo.y, acc);
+      acc = fmaf(W3s[kk][4 * cs + 2], hi.x, acc);
+      acc = fmaf(W3s[kk][4 * cs + 3], hi.y, acc);
     }
     acc += __shfl_xor_sync(0xffffffffu, acc, 1);
     acc += __shfl_xor_sync(0xffffffffu, acc, 2);
@@ -665,13 +734,17 @@ cudaError_t nn_adam(const NNBuffers& B, float lr, int t, float gscale, cudaStrea
   const float c1 = 1.0f - powf(b1, (float)t), c2 = 1.0f - powf(b2, (float)t);
   k_nn_adam<<<blocks_for(kNNParams), 256, 0, s>>>(B.params, B.grad, B.m, B.v, B.wq, kNNParams, lr, b1, b2,
                                                    1e-8f, c1, c2, gscale);
+  k_nn_pack_weights<<<8, 256, 0, s>>>(B.wq, reinterpret_cast<FusedWeights*>(B.wpack));
   return cudaGetLastError();
 }
 
 cudaError_t nn_round_weights(const NNBuffers& B, cudaStream_t s) {
   k_nn_round<<<blocks_for(kNNParams), 256, 0, s>>>(B.params, B.wq, kNNParams);
+  k_nn_pack_weights<<<8, 256, 0, s>>>(B.wq, reinterpret_cast<FusedWeights*>(B.wpack));
   return cudaGetLastError();
 }
+
+size_t nn_wpack_bytes() { return sizeof(FusedWeights); }
 
 cudaError_t nn_inputs(const NNBuffers& B, const NNGrid& g, const double* V0, const double* V1,
                       const double* V2, const double* V3, const double* Vnext, cudaStream_t s,
@@ -705,25 +778,18 @@ cudaError_t nn_predict_fused(const NNBuffers& B, const NNGrid& g, const NNPredic
   if (nb < 1) nb = 1;
   cudaError_t e = cudaMemsetAsync(B.bar, 0, sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
-  FusedArgs A{g, pr.V0, pr.V1, pr.V2, pr.V3, pr.vpred,
-              B.wq + kNNOff[0], B.wq + kNNOff[1], B.wq + kNNOff[2], B.wq + kNNOff[3], B.wq + kNNOff[4], B.wq + kNNOff[5],
+  FusedArgs A{g, pr.V0, pr.V1, pr.V2, pr.V3, pr.vpred, B.wpack,
               B16(B.x0), B16(B.a1), B16(B.a2), B.stats, B.red, B.bar, B.err, wait_limit};
   void* args[] = {&A};
   return cudaLaunchCooperativeKernel((const void*)k_nn_predict, dim3((unsigned)nb), dim3(kFusedThreads), args, 0, s);
 }
 
-cudaError_t add_decide_node(cudaGraph_t g, cudaGraphNode_t* node, const double* res, double thr, const double* vnew,
-                            double* vhxc, int n, double* fb, cudaGraphConditionalHandle handle) {
-  void* args[] = {(void*)&res, (void*)&thr, (void*)&vnew, (void*)&vhxc, (void*)&n, (void*)&fb, (void*)&handle};
-  cudaKernelNodeParams kp{};
-  kp.func = (void*)k_decide;
+cudaError_t launch_decide(const double* res, double thr, const double* vnew, double* vhxc, int n, double* fb,
+                         cudaGraphConditionalHandle handle, cudaStream_t s) {
   int nb = (n + 255) / 256;
-  kp.gridDim = dim3(nb < 1 ? 1 : (nb > 152 ? 152 : nb));
-  kp.blockDim = dim3(256);
-  kp.sharedMemBytes = 0;
-  kp.kernelParams = args;
-  kp.extra = nullptr;
-  return cudaGraphAddKernelNode(node, g, nullptr, 0, &kp);
+  nb = nb < 1 ? 1 : (nb > 152 ? 152 : nb);
+  k_decide<<<nb, 256, 0, s>>>(res, thr, vnew, vhxc, n, fb, handle);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_store6(double* dst, const double v[6], cudaStream_t s) {

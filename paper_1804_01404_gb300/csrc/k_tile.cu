@@ -578,6 +578,85 @@ __global__ void __launch_bounds__(128) k_gproject(TileArgs<T> a, const typename 
   }
 }
 
+// FP32 projections as a batched dense contraction on the tensor cores.  For one atom the projections of
+// all orbitals are the matrix product C = U B: U [orbitals x sphere points] holds the orbitals' values at
+// the atom's sphere points (real and imaginary parts as two matrices), B [sphere points x 4] the real
+// projectors.  A warp takes 16 orbitals and walks the sphere points in steps of 8 with
+// mma.sync m16n8k8 TF32 (the four projectors padded to n = 8), FP32 accumulation.  Each operand is
+// split into a TF32 head and a TF32 tail (x = hi + lo, both exact in FP32) and the product is formed
+// as hi*hi + hi*lo + lo*hi, which keeps the sum at FP32 accuracy (three TF32 products per step).
+// Fragments (PTX ISA, m16n8k8 .tf32): A a0 (row g, col t), a1 (g+8, t), a2 (g, t+4), a3 (g+8, t+4);
+// B b0 (row t, col g), b1 (t+4, g); C c0 (g, 2t), c1 (g, 2t+1), c2 (g+8, 2t), c3 (g+8, 2t+1), with
+// g = lane / 4 and t = lane % 4.  Rows are orbitals, columns of B and C are projectors.
+constexpr int kPW = 4;      // warps per CTA (16 orbitals each)
+
+__device__ __forceinline__ unsigned tf32_rna(float x) {
+  unsigned r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void split_tf32(float x, unsigned& hi, unsigned& lo) {
+  hi = tf32_rna(x);
+  lo = tf32_rna(x - __uint_as_float(hi));
+}
+
+__device__ __forceinline__ void mma_tf32_1688(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__global__ void __launch_bounds__(32 * kPW) k_gproject_mma(TileArgs<float> a, const float2* __restrict__ v) {
+  const int at = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  const int ob = (blockIdx.y * kPW + warp) * 16;
+  if (ob >= a.norb_tot) return;
+  const int i0 = a.atom_off[at], i1 = a.atom_off[at + 1];
+  const bool r0 = ob + g < a.norb_tot, r1 = ob + g + 8 < a.norb_tot;
+  const float2* u0 = v + (size_t)(r0 ? ob + g : 0) * a.npts;
+  const float2* u1 = v + (size_t)(r1 ? ob + g + 8 : 0) * a.npts;
+  float dre[4] = {0, 0, 0, 0}, dim[4] = {0, 0, 0, 0};
+  for (int k0 = i0; k0 < i1; k0 += 8) {
+    const int ia = k0 + t, ib = k0 + t + 4;
+    const bool va = ia < i1, vb = ib < i1;
+    const int xa = va ? a.sph_idx[ia] : 0, xb = vb ? a.sph_idx[ib] : 0;
+    const float2 z = make_float2(0.f, 0.f);
+    const float2 p0a = (va && r0) ? u0[xa] : z, p1a = (va && r1) ? u1[xa] : z;
+    const float2 p0b = (vb && r0) ? u0[xb] : z, p1b = (vb && r1) ? u1[xb] : z;
+    const float ba = (va && g < 4) ? a.sph_beta[4 * ia + g] : 0.f;
+    const float bb = (vb && g < 4) ? a.sph_beta[4 * ib + g] : 0.f;
+    unsigned bh0, bl0, bh1, bl1;
+    split_tf32(ba, bh0, bl0);
+    split_tf32(bb, bh1, bl1);
+    unsigned ah[4], al[4];
+    // real parts
+    split_tf32(p0a.x, ah[0], al[0]); split_tf32(p1a.x, ah[1], al[1]);
+    split_tf32(p0b.x, ah[2], al[2]); split_tf32(p1b.x, ah[3], al[3]);
+    mma_tf32_1688(dre, al, bh0, bh1);
+    mma_tf32_1688(dre, ah, bl0, bl1);
+    mma_tf32_1688(dre, ah, bh0, bh1);
+    // imaginary parts
+    split_tf32(p0a.y, ah[0], al[0]); split_tf32(p1a.y, ah[1], al[1]);
+    split_tf32(p0b.y, ah[2], al[2]); split_tf32(p1b.y, ah[3], al[3]);
+    mma_tf32_1688(dim, al, bh0, bh1);
+    mma_tf32_1688(dim, ah, bl0, bl1);
+    mma_tf32_1688(dim, ah, bh0, bh1);
+  }
+  if (t < 2) {             // columns 2t, 2t+1 are projectors 0..3
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int p = 2 * t + j;
+      const float sc = a.atomE[at * 4 + p] * a.dV;
+      if (r0) a.ec[((size_t)(ob + g) * a.natom + at) * 4 + p] = make_float2(dre[j] * sc, dim[j] * sc);
+      if (r1) a.ec[((size_t)(ob + g + 8) * a.natom + at) * 4 + p] = make_float2(dre[2 + j] * sc, dim[2 + j] * sc);
+    }
+  }
+}
+
 // out[p] += f * V_NL v at sphere points, f = 1 (H) or -i coef (Horner stage); one thread per
 // (sphere point, orbital).
 template <typename T, int MODE>
@@ -741,8 +820,13 @@ cudaError_t launch_tile_stage(const TileArgs<T>& a0, const void* vin, int mode, 
 template <typename T>
 cudaError_t launch_tile_project(const TileArgs<T>& a, const typename Cplx<T>::type* v, cudaStream_t s) {
   if (a.natom == 0) return cudaSuccess;
-  const dim3 grid(a.natom, (a.norb_tot + kOB - 1) / kOB);
-  k_gproject<T><<<grid, 128, 0, s>>>(a, v);
+  if constexpr (sizeof(T) == 4) {      // FP32: tensor cores (3xTF32)
+    const dim3 grid(a.natom, (a.norb_tot + 16 * kPW - 1) / (16 * kPW));
+    k_gproject_mma<<<grid, 32 * kPW, 0, s>>>(a, v);
+  } else {
+    const dim3 grid(a.natom, (a.norb_tot + kOB - 1) / kOB);
+    k_gproject<T><<<grid, 128, 0, s>>>(a, v);
+  }
   return cudaGetLastError();
 }
 

@@ -124,19 +124,35 @@ struct tdks_ctx {
   void* d_backup = nullptr;      // orbitals at t (predicted steps)
   void* cur_backup = nullptr;    // set while the corrector of a predicted step writes the backup
   double fallbacks = 0, last_resid = 0;
-  // device-side acceptance of predicted steps: a CUDA graph of the decision kernel and a conditional
-  // node whose body restores the orbitals and runs the plain predictor-corrector step (captured once
-  // per orbital array and step settings); the fallback count lives on the device
-  struct FallbackGraph {
+  // Predicted steps run as one CUDA graph per slot of the potential history ring (the slot sets which
+  // buffers hold V_Hxc(t .. t-3dt)): prediction, corrector, Hartree-exchange, misfit, the decision
+  // kernel and a conditional node whose body restores the orbitals and runs the plain
+  // predictor-corrector step, then the history update and the observables.  The vector potentials
+  // come from device memory, so a graph serves every step with the same orbital array and settings.
+  struct Rec { int phase; cudaEvent_t a, b; };
+  struct StepGraph {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    std::vector<Rec> recs;       // phase events recorded by the graph (profiling on)
+    long long launches = 0;      // launches of one execution without the fallback body
+    long long calls[TDKS_NPHASE] = {0};
+    bool pending = false;        // recs hold times of an execution not yet added to ms[]
+  } sg[4];
+  struct StepKey {
     const void* u = nullptr;
     double dt = 0, thr = 0, mbj_c = 0;
-    int lg = -1, has_obs = -1, obs_start = -1, cell_variant = -1, tile0 = -1, tile1 = -1;
-    long long body_launches = 0;
-  } fg;
-  cudaStream_t cap = nullptr;    // private stream the fallback body is captured on
-  double* d_apf = nullptr;       // [6] A'(t+dt/2) and A' of the observables, read by the fallback body
+    int mode = -1, lg = -1, has_obs = -1, obs_start = -1, cell_variant = -1, tile0 = -1, tile1 = -1, prof = -1;
+    bool operator==(const StepKey& o) const {
+      return u == o.u && dt == o.dt && thr == o.thr && mbj_c == o.mbj_c && mode == o.mode && lg == o.lg &&
+             has_obs == o.has_obs && obs_start == o.obs_start && cell_variant == o.cell_variant && tile0 == o.tile0 &&
+             tile1 == o.tile1 && prof == o.prof;
+    }
+  } sg_key;
+  long long body_launches = 0;   // launches of the fallback body
+  int step_graph = 1;            // predicted steps as step graphs (1) or stream launches with a host decision (0)
+  std::vector<Rec>* cap_recs = nullptr;   // set while a step graph is captured with profiling on
+  cudaStream_t cap = nullptr, cap2 = nullptr;   // private streams the graphs are captured on
+  double* d_apf = nullptr;       // [6] A'(t+dt/2) and A' of the observables, read by the step graph
   double* d_fb = nullptr;        // fallback count (device)
   double fb_seen = 0;            // fallbacks already added to the launch count
   bool nn_ready = false;
@@ -147,7 +163,6 @@ struct tdks_ctx {
   long long launches = 0;
   long long calls[TDKS_NPHASE] = {0};
   double ms[TDKS_NPHASE] = {0};
-  struct Rec { int phase; cudaEvent_t a, b; };
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> event_pool;
 };
@@ -291,14 +306,19 @@ struct Phase {
   cudaEvent_t a = nullptr;
   Phase(tdks_ctx* c_, int p) : c(c_), phase(p) {
     c->calls[p] += 1;
-    if (c->profiling && (a = take_event(c)) != nullptr) cudaEventRecord(a, c->stream);
+    if (c->profiling && (a = take_event(c)) != nullptr) record(a);
   }
   ~Phase() {
     if (!a) return;
     cudaEvent_t b = take_event(c);
     if (!b) { c->event_pool.push_back(a); return; }
-    cudaEventRecord(b, c->stream);
-    c->recs.push_back({phase, a, b});
+    record(b);
+    (c->cap_recs ? *c->cap_recs : c->recs).push_back({phase, a, b});
+  }
+  // while a step graph is captured the event becomes an event-record node of the graph
+  void record(cudaEvent_t e) {
+    if (c->cap_recs) cudaEventRecordWithFlags(e, c->stream, cudaEventRecordExternal);
+    else cudaEventRecord(e, c->stream);
   }
 };
 
@@ -911,9 +931,13 @@ void tdks_destroy(tdks_ctx* c) {
   if (c->side) cudaStreamDestroy(c->side);
   for (void* p : c->allocs) cudaFree(p);
   if (c->h_resid) cudaFreeHost(c->h_resid);
-  if (c->fg.exec) cudaGraphExecDestroy(c->fg.exec);
-  if (c->fg.graph) cudaGraphDestroy(c->fg.graph);
+  for (auto& g : c->sg) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (g.graph) cudaGraphDestroy(g.graph);
+    for (auto& r : g.recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+  }
   if (c->cap) cudaStreamDestroy(c->cap);
+  if (c->cap2) cudaStreamDestroy(c->cap2);
   delete c;
 }
 
@@ -1387,93 +1411,29 @@ tdks_status pc_step(tdks_ctx* c, void* u, const double Amid[3], const double* Ao
   return TDKS_OK;
 }
 
-// The fallback of a predicted step as a CUDA graph: the decision node (k_decide: accept V_Hxc(t+dt) or
-// count a fallback) and a conditional node whose body, taken only on rejection, copies the saved
-// orbitals back and runs the plain predictor-corrector step.  The body reads the vector potentials from
-// device memory (d_apf, or the longitudinal geometry's d_ap_mid / d_ap_end), so one graph serves every
-// step with the same orbital array and settings; it is rebuilt when one of them changes.
-static tdks_status ensure_fallback_graph(tdks_ctx* c, void* u, double dt, bool has_obs, bool obs_start) {
-  auto& f = c->fg;
-  const int lg = c->longitudinal ? 1 : 0;
-  if (f.exec && f.u == u && f.dt == dt && f.thr == c->pred_thr && f.lg == lg && f.has_obs == (int)has_obs &&
-      f.obs_start == (int)obs_start && f.cell_variant == c->cell_variant && f.tile0 == c->tile_variant[0] &&
-      f.tile1 == c->tile_variant[1] && f.mbj_c == c->mbj_c_fixed)
-    return TDKS_OK;
-  if (f.exec) { cudaGraphExecDestroy(f.exec); f.exec = nullptr; }
-  if (f.graph) { cudaGraphDestroy(f.graph); f.graph = nullptr; }
-  if (!c->cap) TDKS_CUDA(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
-  // the body's launches must follow the work already queued on the context stream: the graph is
-  // launched on that stream, so only the capture itself happens on the private one
-  TDKS_CUDA(cudaGraphCreate(&f.graph, 0));
-  cudaGraphConditionalHandle handle;
-  TDKS_CUDA(cudaGraphConditionalHandleCreate(&handle, f.graph, 0, cudaGraphCondAssignDefault));
-  cudaGraphNode_t dn, cn;
-  TDKS_CUDA(add_decide_node(f.graph, &dn, c->d_resid, c->pred_thr, c->d_vnew, c->d_vhxc, c->npts, c->d_fb, handle));
-  cudaGraphNodeParams cp = {};
-  cp.type = cudaGraphNodeTypeConditional;
-  cp.conditional.handle = handle;
-  cp.conditional.type = cudaGraphCondTypeIf;
-  cp.conditional.size = 1;
-  TDKS_CUDA(cudaGraphAddNode(&cn, f.graph, &dn, nullptr, 1, &cp));
-  cudaGraph_t body = cp.conditional.phGraph_out[0];
-
-  // capture the body: the stream, the vector potentials and the bookkeeping are switched for the
-  // capture and restored afterwards (profiling events cannot sit in a conditional body)
-  const cudaStream_t main = c->stream;
-  const bool prof = c->profiling;
-  const long long launches0 = c->launches;
-  long long calls0[TDKS_NPHASE];
-  std::memcpy(calls0, c->calls, sizeof(calls0));
-  const double* apm = c->cur_ap_mid;
-  const double* ape = c->cur_ap_end;
-  c->stream = c->cap;
-  c->profiling = false;
-  c->cur_ap_mid = lg ? c->d_ap_mid : c->d_apf;
-  c->cur_ap_end = lg ? c->d_ap_end : c->d_apf + 3;
-  const size_t obytes = (size_t)c->nk * c->norb * c->npts * (is_f32(c) ? sizeof(float2) : sizeof(double2));
-  const double zero[3] = {0.0, 0.0, 0.0};
-  tdks_status st = TDKS_OK;
-  cudaError_t e = cudaStreamBeginCaptureToGraph(c->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
-  if (e == cudaSuccess) {
-    e = cudaMemcpyAsync(u, c->d_backup, obytes, cudaMemcpyDeviceToDevice, c->stream);
-    if (e == cudaSuccess) st = pc_step(c, u, zero, has_obs ? zero : nullptr, obs_start, dt);
-    cudaGraph_t out = nullptr;
-    const cudaError_t e2 = cudaStreamEndCapture(c->stream, &out);
-    if (e == cudaSuccess) e = e2;
-  }
-  f.body_launches = c->launches - launches0;
-  c->launches = launches0;
-  std::memcpy(c->calls, calls0, sizeof(calls0));
-  c->stream = main;
-  c->profiling = prof;
-  c->cur_ap_mid = apm;
-  c->cur_ap_end = ape;
-  if (e != cudaSuccess || st != TDKS_OK) {
-    cudaGetLastError();
-    cudaGraphDestroy(f.graph);
-    f.graph = nullptr;
-    if (st != TDKS_OK) return st;
-    return fail(TDKS_ECUDA, std::string("capture of the fallback step: ") + cudaGetErrorString(e));
-  }
-  TDKS_CUDA(cudaGraphInstantiate(&f.exec, f.graph, 0));
-  f.u = u; f.dt = dt; f.thr = c->pred_thr; f.lg = lg; f.has_obs = has_obs; f.obs_start = obs_start;
-  f.cell_variant = c->cell_variant; f.tile0 = c->tile_variant[0]; f.tile1 = c->tile_variant[1];
-  f.mbj_c = c->mbj_c_fixed;
+// Read the device fallback count (synchronises the stream); the launches of the fallback bodies that
+// ran since the last read join the launch count.
+static tdks_status sync_fallbacks(tdks_ctx* c) {
+  double fb = 0.0;
+  TDKS_CUDA(cudaMemcpyAsync(&fb, c->d_fb, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  TDKS_CUDA(cudaStreamSynchronize(c->stream));
+  if (fb > c->fb_seen) c->launches += (long long)(fb - c->fb_seen) * c->body_launches;
+  c->fb_seen = fb;
+  c->fallbacks = fb;
   return TDKS_OK;
 }
 
-// One step with a predicted V~(t+dt) in place of the predictor half-step.  The misfit is judged on the
-// device (fallback graph): no host synchronisation.
-static tdks_status predicted_step(tdks_ctx* c, void* u, const double Amid[3], const double* Aobs, bool obs_start,
-                           double dt) {
+// Predicted step, main path (inside a step-graph capture): the prediction of V~(t+dt) from the
+// history (the network or the cubic), the corrector T4[V_loc + (V_Hxc(t) + V~)/2] with its density,
+// V_Hxc(t+dt) into d_vnew and the misfit into d_resid.
+static tdks_status predicted_main(tdks_ctx* c, void* u, const double Amid[3], double dt, const double* Aobs,
+                                  bool obs_start) {
   const size_t gb = c->npts * sizeof(double);
   const size_t obytes = (size_t)c->nk * c->norb * c->npts * (is_f32(c) ? sizeof(float2) : sizeof(double2));
   const NNGrid g = nn_grid(c);
-  const bool net = c->pred_mode == TDKS_PRED_LEARNED;
-  TDKS_TRY(ensure_fallback_graph(c, u, dt, Aobs != nullptr, obs_start));
   {
     Phase ph(c, 5);
-    if (net) {   // statistics, packing and the three layers in one cooperative launch
+    if (c->pred_mode == TDKS_PRED_LEARNED) {   // statistics, inputs and the three layers: one launch
       const NNPredict pr{hist_slot(c, 0), hist_slot(c, 1), hist_slot(c, 2), hist_slot(c, 3), c->d_vpred};
       TDKS_CUDA(nn_predict_fused(c->nn, g, pr, c->wait_limit, c->stream));
       c->launches += 1;
@@ -1486,11 +1446,6 @@ static tdks_status predicted_step(tdks_ctx* c, void* u, const double Amid[3], co
     // copies it first
     if (c->tiled) TDKS_CUDA(cudaMemcpyAsync(c->d_backup, u, obytes, cudaMemcpyDeviceToDevice, c->stream));
     TDKS_CUDA(cudaMemsetAsync(c->d_rho, 0, gb, c->stream));
-    if (!c->longitudinal) {   // the fallback body's vector potentials
-      const double v[6] = {Amid[0], Amid[1], Amid[2], Aobs ? Aobs[0] : 0.0, Aobs ? Aobs[1] : 0.0, Aobs ? Aobs[2] : 0.0};
-      TDKS_CUDA(launch_store6(c->d_apf, v, c->stream));
-      c->launches += 1;
-    }
   }
   TDKS_TRY(set_step_potential(c, 0.5, c->d_vpred, 0.5));
   c->cur_backup = c->tiled ? nullptr : c->d_backup;
@@ -1499,11 +1454,198 @@ static tdks_status predicted_step(tdks_ctx* c, void* u, const double Amid[3], co
   TDKS_TRY(cs);
   TDKS_TRY(hxc(c, c->d_rho, c->d_vnew, u));
   TDKS_CUDA(launch_residual(c->d_vnew, c->d_vpred, c->npts, c->d_partials, c->d_ticket, c->d_resid, c->stream));
-  {
-    Phase ph(c, 5);
-    TDKS_CUDA(cudaGraphLaunch(c->fg.exec, c->stream));
+  c->launches += 1;
+  return TDKS_OK;
+}
+
+// The rest of the step graph after the conditional fallback: V_Hxc(t+dt) into the history slot the
+// next step reads as V0, J and the dipole.
+static tdks_status step_tail(tdks_ctx* c, bool at_start) {
+  double* next0 = c->d_vhist + (size_t)((c->hist_head + 1) % 4) * c->npts;
+  TDKS_CUDA(cudaMemcpyAsync(next0, c->d_vhxc, c->npts * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  Phase ph(c, 4);
+  if (c->grid.periodic) {
+    TDKS_CUDA(launch_reduce_current(c->d_orb_obs, c->nk, c->norb, c->d_kw, 1.0 / c->omega, 1, c->d_step_obs,
+                                    c->stream, c->ncell));
+    c->launches += 1;
+  } else {
+    TDKS_CUDA(cudaMemsetAsync(c->d_step_obs, 0, 3 * sizeof(double), c->stream));
   }
-  c->launches += 2;
+  if (!at_start) {
+    TDKS_CUDA(launch_dipole(c->d_rho, c->d_rho0, c->grid.n, c->grid.h, c->grid.periodic, c->d_partials, c->d_ticket,
+                            c->d_step_obs, c->stream));
+    c->launches += 1;
+  }
+  return TDKS_OK;
+}
+
+// Add the step-graph timings of the last execution of slot v to the phase times.
+static tdks_status collect_step_graph(tdks_ctx* c, int v) {
+  auto& g = c->sg[v];
+  if (!g.pending) return TDKS_OK;
+  for (auto& r : g.recs) {
+    float ms = 0.f;
+    TDKS_CUDA(cudaEventSynchronize(r.b));
+    TDKS_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
+    c->ms[r.phase] += ms;
+  }
+  g.pending = false;
+  return TDKS_OK;
+}
+
+static void drop_step_graphs(tdks_ctx* c) {
+  cudaStreamSynchronize(c->stream);
+  for (int v = 0; v < 4; ++v) {
+    auto& g = c->sg[v];
+    collect_step_graph(c, v);
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (g.graph) cudaGraphDestroy(g.graph);
+    for (auto& r : g.recs) { c->event_pool.push_back(r.a); c->event_pool.push_back(r.b); }
+    g = tdks_ctx::StepGraph{};
+  }
+}
+
+// Capture the step graph of history slot v = c->hist_head (see tdks_ctx::StepGraph).
+static tdks_status build_step_graph(tdks_ctx* c, void* u, double dt, const double* Aobs, bool obs_start) {
+  auto& g = c->sg[c->hist_head];
+  if (!c->cap) TDKS_CUDA(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+  if (!c->cap2) TDKS_CUDA(cudaStreamCreateWithFlags(&c->cap2, cudaStreamNonBlocking));
+  const cudaStream_t main = c->stream;
+  const bool prof = c->profiling;
+  const long long launches0 = c->launches;
+  long long calls0[TDKS_NPHASE];
+  std::memcpy(calls0, c->calls, sizeof(calls0));
+  const size_t obytes = (size_t)c->nk * c->norb * c->npts * (is_f32(c) ? sizeof(float2) : sizeof(double2));
+  const double zero[3] = {0.0, 0.0, 0.0};
+  c->cur_ap_mid = c->longitudinal ? c->d_ap_mid : c->d_apf;
+  c->cur_ap_end = c->longitudinal ? c->d_ap_end : c->d_apf + 3;
+  c->stream = c->cap;
+  c->cap_recs = prof ? &g.recs : nullptr;
+  long long body0 = 0, body1 = 0;
+  tdks_status st = TDKS_OK;
+  cudaError_t e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) {
+    st = predicted_main(c, u, zero, dt, Aobs, obs_start);   // the kernels read A' from the device pointers
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    cudaStreamCaptureStatus cst;
+    cudaGraphConditionalHandle handle;
+    cudaGraphNode_t cn = nullptr;
+    cudaGraph_t body = nullptr;
+    if (st == TDKS_OK) e = cudaStreamGetCaptureInfo(c->cap, &cst, nullptr, &cg, nullptr, nullptr, nullptr);
+    if (st == TDKS_OK && e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&handle, cg, 0, cudaGraphCondAssignDefault);
+    if (st == TDKS_OK && e == cudaSuccess) {
+      Phase ph(c, 5);
+      e = launch_decide(c->d_resid, c->pred_thr, c->d_vnew, c->d_vhxc, c->npts, c->d_fb, handle, c->stream);
+      c->launches += 1;
+    }
+    if (st == TDKS_OK && e == cudaSuccess) e = cudaStreamGetCaptureInfo(c->cap, &cst, nullptr, &cg, &deps, nullptr, &ndeps);
+    if (st == TDKS_OK && e == cudaSuccess) {
+      cudaGraphNodeParams cp = {};
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = handle;
+      cp.conditional.type = cudaGraphCondTypeIf;
+      cp.conditional.size = 1;
+      e = cudaGraphAddNode(&cn, cg, deps, nullptr, ndeps, &cp);
+      if (e == cudaSuccess) body = cp.conditional.phGraph_out[0];
+    }
+    if (st == TDKS_OK && e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(c->cap, &cn, nullptr, 1, cudaStreamSetCaptureDependencies);
+    if (st == TDKS_OK && e == cudaSuccess) {
+      // the fallback body: restore the orbitals, plain predictor-corrector (no profiling events: a
+      // conditional body holds kernels, copies and memsets only)
+      c->stream = c->cap2;
+      c->cap_recs = nullptr;
+      c->profiling = false;
+      body0 = c->launches;
+      e = cudaStreamBeginCaptureToGraph(c->cap2, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+      if (e == cudaSuccess) {
+        e = cudaMemcpyAsync(u, c->d_backup, obytes, cudaMemcpyDeviceToDevice, c->stream);
+        if (e == cudaSuccess) st = pc_step(c, u, zero, Aobs ? zero : nullptr, obs_start, dt);
+        const cudaError_t e2 = cudaStreamEndCapture(c->cap2, &body);
+        if (e == cudaSuccess) e = e2;
+      }
+      body1 = c->launches;
+      c->stream = c->cap;
+      c->cap_recs = prof ? &g.recs : nullptr;
+      c->profiling = prof;
+    }
+    if (st == TDKS_OK && e == cudaSuccess) st = step_tail(c, obs_start);
+    const cudaError_t e2 = cudaStreamEndCapture(c->cap, &g.graph);
+    if (e == cudaSuccess) e = e2;
+  }
+  c->body_launches = body1 - body0;
+  g.launches = c->launches - launches0 - c->body_launches;
+  for (int p = 0; p < TDKS_NPHASE; ++p) g.calls[p] = c->calls[p] - calls0[p];
+  c->launches = launches0;
+  std::memcpy(c->calls, calls0, sizeof(calls0));
+  c->stream = main;
+  c->profiling = prof;
+  c->cap_recs = nullptr;
+  c->cur_ap_mid = c->cur_ap_end = nullptr;
+  if (e == cudaSuccess && st == TDKS_OK) e = cudaGraphInstantiate(&g.exec, g.graph, 0);
+  if (e != cudaSuccess || st != TDKS_OK) {
+    cudaGetLastError();
+    if (g.graph) cudaGraphDestroy(g.graph);
+    for (auto& r : g.recs) { c->event_pool.push_back(r.a); c->event_pool.push_back(r.b); }
+    g = tdks_ctx::StepGraph{};
+    if (st != TDKS_OK) return st;
+    return fail(TDKS_ECUDA, std::string("capture of the predicted step: ") + cudaGetErrorString(e));
+  }
+  return TDKS_OK;
+}
+
+// A predicted step without the step graph (tdks_set_step_graph(ctx, 0)): the same launches on the
+// stream, the misfit read on the host (one synchronisation) and the fallback enqueued from the host.
+// The caller adds the history update and the observables.
+static tdks_status predicted_step_host(tdks_ctx* c, void* u, const double Amid[3], const double* Aobs,
+                                       bool obs_start, double dt) {
+  TDKS_TRY(predicted_main(c, u, Amid, dt, Aobs, obs_start));
+  double r = 0.0;
+  TDKS_CUDA(cudaMemcpyAsync(&r, c->d_resid, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  TDKS_CUDA(cudaStreamSynchronize(c->stream));
+  const size_t gb = c->npts * sizeof(double);
+  if (std::isfinite(r) && r <= c->pred_thr) {
+    TDKS_CUDA(cudaMemcpyAsync(c->d_vhxc, c->d_vnew, gb, cudaMemcpyDeviceToDevice, c->stream));
+    return TDKS_OK;
+  }
+  const size_t obytes = (size_t)c->nk * c->norb * c->npts * (is_f32(c) ? sizeof(float2) : sizeof(double2));
+  TDKS_CUDA(cudaMemcpyAsync(u, c->d_backup, obytes, cudaMemcpyDeviceToDevice, c->stream));
+  TDKS_TRY(sync_fallbacks(c));
+  c->fallbacks += 1.0;
+  c->fb_seen = c->fallbacks;
+  TDKS_CUDA(cudaMemcpy(c->d_fb, &c->fallbacks, sizeof(double), cudaMemcpyHostToDevice));
+  return pc_step(c, u, Amid, Aobs, obs_start, dt);
+}
+
+// One predicted step: the vector potentials to the device, then the step graph of the current history
+// slot (built on first use).  No host synchronisation.
+static tdks_status predicted_step(tdks_ctx* c, void* u, const double Amid[3], const double* Aobs, bool obs_start,
+                                  double dt) {
+  tdks_ctx::StepKey key;
+  key.u = u; key.dt = dt; key.thr = c->pred_thr; key.mbj_c = c->mbj_c_fixed; key.mode = c->pred_mode;
+  key.lg = c->longitudinal ? 1 : 0; key.has_obs = Aobs ? 1 : 0; key.obs_start = obs_start ? 1 : 0;
+  key.cell_variant = c->cell_variant; key.tile0 = c->tile_variant[0]; key.tile1 = c->tile_variant[1];
+  key.prof = c->profiling ? 1 : 0;
+  if (!(key == c->sg_key)) {
+    drop_step_graphs(c);
+    c->sg_key = key;
+  }
+  if (!c->longitudinal) {
+    Phase ph(c, 5);
+    const double v[6] = {Amid[0], Amid[1], Amid[2], Aobs ? Aobs[0] : 0.0, Aobs ? Aobs[1] : 0.0, Aobs ? Aobs[2] : 0.0};
+    TDKS_CUDA(launch_store6(c->d_apf, v, c->stream));
+    c->launches += 1;
+  }
+  const int v = c->hist_head;
+  auto& g = c->sg[v];
+  if (!g.exec) TDKS_TRY(build_step_graph(c, u, dt, Aobs, obs_start));
+  TDKS_TRY(collect_step_graph(c, v));
+  TDKS_CUDA(cudaGraphLaunch(g.exec, c->stream));
+  g.pending = c->profiling;
+  c->launches += g.launches;
+  for (int p = 0; p < TDKS_NPHASE; ++p) c->calls[p] += g.calls[p];
+  c->hist_head = (v + 1) % 4;
   return TDKS_OK;
 }
 
@@ -1534,11 +1676,14 @@ tdks_status tdks_step(tdks_ctx* c, void* u, double t, double dt) {
     c->cur_ap_mid = c->d_ap_mid;
     c->cur_ap_end = c->d_ap_end;
   }
-  tdks_status st = TDKS_OK;
-  if (c->pred_mode != TDKS_PRED_PC && c->hist_count >= 4 && (c->opt.hartree || c->opt.xc))
-    st = predicted_step(c, u, Amid, Aobs, at_start, dt);
-  else
-    st = pc_step(c, u, Amid, Aobs, at_start, dt);
+  const bool predicted = c->pred_mode != TDKS_PRED_PC && c->hist_count >= 4 && (c->opt.hartree || c->opt.xc);
+  if (predicted && c->step_graph) {
+    const tdks_status st = predicted_step(c, u, Amid, Aobs, at_start, dt);   // history, J and dipole inside
+    c->cur_ap_mid = c->cur_ap_end = nullptr;
+    return st;
+  }
+  const tdks_status st = predicted ? predicted_step_host(c, u, Amid, Aobs, at_start, dt)
+                                   : pc_step(c, u, Amid, Aobs, at_start, dt);
   c->cur_ap_mid = c->cur_ap_end = nullptr;
   TDKS_TRY(st);
   TDKS_TRY(hist_push(c, c->d_vhxc));
@@ -1631,18 +1776,6 @@ tdks_status tdks_ms_read(tdks_ctx* c, double* A_host, double* I_host) {
 }
 
 
-// Read the device fallback count (synchronises the stream); the launches of the fallback bodies that
-// ran since the last read join the launch count.
-static tdks_status sync_fallbacks(tdks_ctx* c) {
-  double fb = 0.0;
-  TDKS_CUDA(cudaMemcpyAsync(&fb, c->d_fb, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-  TDKS_CUDA(cudaStreamSynchronize(c->stream));
-  if (fb > c->fb_seen) c->launches += (long long)(fb - c->fb_seen) * c->fg.body_launches;
-  c->fb_seen = fb;
-  c->fallbacks = fb;
-  return TDKS_OK;
-}
-
 tdks_status tdks_read_step_observables(tdks_ctx* c, tdks_obs* o) {
   TDKS_TRY(check_ctx(c));
   if (!o) return fail(TDKS_EINVAL, "null output");
@@ -1732,6 +1865,14 @@ tdks_status tdks_check(tdks_ctx* c) {
   return TDKS_OK;
 }
 
+tdks_status tdks_set_step_graph(tdks_ctx* c, int enable) {
+  TDKS_TRY(check_ctx(c));
+  if (enable != 0 && enable != 1) return fail(TDKS_EINVAL, "enable must be 0 or 1");
+  if (!enable) drop_step_graphs(c);
+  c->step_graph = enable;
+  return TDKS_OK;
+}
+
 tdks_status tdks_set_predictor(tdks_ctx* c, int mode, double threshold) {
   TDKS_TRY(check_ctx(c));
   if (mode < TDKS_PRED_PC || mode > TDKS_PRED_LEARNED) return fail(TDKS_EINVAL, "unknown predictor mode");
@@ -1788,6 +1929,7 @@ tdks_status tdks_nn_init(tdks_ctx* c, unsigned long long seed) {
     TDKS_TRY(dalloc(c, &B.red, 304 * 5));
     TDKS_TRY(dalloc(c, &B.ticket, 1));
     TDKS_TRY(dalloc(c, &B.bar, 1));
+    TDKS_TRY(dalloc(c, &B.wpack, nn_wpack_bytes() / sizeof(uint4)));
     TDKS_CUDA(cudaMemsetAsync(B.ticket, 0, sizeof(unsigned), c->stream));
     B.err = c->d_err;
   }
@@ -1909,6 +2051,7 @@ tdks_status tdks_stats_read(tdks_ctx* c, tdks_stats* out, int reset) {
   TDKS_TRY(check_ctx(c));
   if (!out) return fail(TDKS_EINVAL, "null output");
   TDKS_TRY(sync_fallbacks(c));
+  for (int v = 0; v < 4; ++v) TDKS_TRY(collect_step_graph(c, v));
   for (auto& r : c->recs) {
     float ms = 0.0f;
     TDKS_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));

@@ -189,6 +189,7 @@ struct NNBuffers {
   double* red;                                    // [304][5] grid_sum partials of the statistics
   unsigned* ticket;                               // grid_sum ticket (zero between launches)
   unsigned* bar;                                  // grid-barrier counter of the fused prediction
+  uint4* wpack;                                   // shared-memory image of the prediction's weights
   int* err;                                       // context error word (TDKS_ETIMEOUT of a barrier wait)
 };
 int nn_part_blocks(int npts);
@@ -213,16 +214,18 @@ cudaError_t nn_loss(const NNBuffers& B, const NNGrid& g, double* loss_acc, cudaS
 cudaError_t nn_backward(const NNBuffers& B, const NNGrid& g, cudaStream_t s);   // grad +=
 cudaError_t nn_adam(const NNBuffers& B, float lr, int t, float gscale, cudaStream_t s);
 cudaError_t nn_round_weights(const NNBuffers& B, cudaStream_t s);
+size_t nn_wpack_bytes();   // size of NNBuffers::wpack
 // vpred: mode 0 = 2 V0 - V1, 1 = cubic 4 V0 - 6 V1 + 4 V2 - V3, 2 = cubic + s3 * out
 cudaError_t nn_apply(const NNBuffers& B, const NNGrid& g, const double* V0, const double* V1,
                      const double* V2, const double* V3, int mode, double* vpred, cudaStream_t s);
 // partials: [304][2] doubles, ticket: one unsigned that is zero between launches (grid_sum)
 cudaError_t launch_residual(const double* Vnew, const double* Vpred, int n, double* partials, unsigned* ticket,
                             double* res, cudaStream_t s);
-// Graph node of the device-side acceptance of a predicted potential: vhxc <- vnew if *res <= thr (finite),
-// else *fb += 1 and the conditional `handle` is set to 1 (0 when accepted).
-cudaError_t add_decide_node(cudaGraph_t g, cudaGraphNode_t* node, const double* res, double thr, const double* vnew,
-                            double* vhxc, int n, double* fb, cudaGraphConditionalHandle handle);
+// Device-side acceptance of a predicted potential (a kernel inside a captured graph that owns `handle`):
+// vhxc <- vnew if *res <= thr (finite), else *fb += 1 and the conditional `handle` is set to 1 (0 when
+// accepted).
+cudaError_t launch_decide(const double* res, double thr, const double* vnew, double* vhxc, int n, double* fb,
+                          cudaGraphConditionalHandle handle, cudaStream_t s);
 // dst[0..5] <- v[0..5] (six doubles passed by value, so the host buffer may change right after the call)
 cudaError_t launch_store6(double* dst, const double v[6], cudaStream_t s);
 

@@ -105,6 +105,7 @@ def load_library(path: str = LIB_PATH):
         "tdks_check": [vp],
         "tdks_profile": [vp, i],
         "tdks_set_predictor": [vp, i, d],
+        "tdks_set_step_graph": [vp, i],
         "tdks_ms_init": [vp, i, i, d, C.POINTER(C.c_double), C.POINTER(C.c_double)],
         "tdks_ms_step": [vp, vp, d, d],
         "tdks_ms_read": [vp, C.POINTER(C.c_double), C.POINTER(C.c_double)],
@@ -453,6 +454,11 @@ class Context:
     # ---- predictor and learned network
     def set_predictor(self, mode, threshold=1e-5):
         _check(self.lib.tdks_set_predictor(self.ctx, int(mode), float(threshold)))
+
+    def set_step_graph(self, enable=True):
+        """Predicted steps as CUDA graphs with the decision on the device (default) or as stream launches
+        with the decision on the host (tdks_set_step_graph)."""
+        _check(self.lib.tdks_set_step_graph(self.ctx, int(bool(enable))))
 
     def nn_init(self, seed=0):
         _check(self.lib.tdks_nn_init(self.ctx, int(seed)))
