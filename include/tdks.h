@@ -383,7 +383,9 @@ typedef struct {
   double ms[TDKS_NPHASE];
 } tdks_stats;
 
-/* enable = 1 starts recording phase events, 0 stops. */
+/* enable = 1 starts recording phase events, 2 records only the pair around the orbital stencil kernel
+ * launches (phase 6; the other phases are counted but not timed, which keeps the event overhead of a
+ * step small), 0 stops.  Errors: EINVAL for enable outside 0..2. */
 tdks_status tdks_profile(tdks_ctx* ctx, int enable);
 
 /* Sum the recorded phase times (synchronises the stream); reset = 1 clears counters and times. */

@@ -397,7 +397,8 @@ struct FusedArgs {
   bf16 *x0, *a1, *a2;        // channel-last [npts][4], [npts][16], [npts][16]
   double* stats;             // out: s1, s2, s3, mean V0, s_V
   double* part;              // [gridDim.x][5]
-  unsigned* bar;             // grid-barrier counter, zero at launch
+  double inv_n;              // 1 / points
+  unsigned* bar;             // [2] grid-barrier counter and exit counter, zero at launch (the kernel resets them)
   int* err;                  // TDKS_ETIMEOUT if a barrier wait gives up
   long long limit;           // polls per barrier wait
 };
@@ -412,10 +413,7 @@ __device__ __forceinline__ bool fused_barrier(const FusedArgs& A, unsigned k, in
     const unsigned target = k * gridDim.x;
     long long it = 0;
     unsigned v = *(volatile unsigned*)A.bar;
-    while (v < target && ++it < A.limit) {
-      __nanosleep(40);
-      v = *(volatile unsigned*)A.bar;
-    }
+    while (v < target && ++it < A.limit) v = *(volatile unsigned*)A.bar;
     __threadfence();
     *ok_s = v >= target;
     if (!*ok_s) atomicExch(A.err, 4);            // TDKS_ETIMEOUT
@@ -439,10 +437,45 @@ __device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const unsigned (&a
 
 // Neighbour indices of the 27 taps (the layer loops are fully unrolled so that every neighbour's load
 // is issued before the arithmetic that uses it; these layers are bound by load latency).
+// Built from the three wrapped (or, outside an isolated box, invalid) coordinates per axis; an invalid
+// coordinate contributes a large negative offset, so every neighbour it touches gets q < 0.
 __device__ __forceinline__ void tap_index(const NNGrid& g, int x, int y, int z, bool valid, int (&q)[27]) {
+  constexpr int kOut = -(1 << 29);
+  int xo[3], yo[3], zo[3];
 #pragma unroll
-  for (int kk = 0; kk < 27; ++kk)
-    q[kk] = valid ? nb_index(g, x, y, z, kk % 3 - 1, (kk / 3) % 3 - 1, kk / 9 - 1) : -1;
+  for (int d = 0; d < 3; ++d) {
+    int xx = x + d - 1, yy = y + d - 1, zz = z + d - 1;
+    if (g.periodic) {
+      xx += (xx < 0) ? g.nx : 0; xx -= (xx >= g.nx) ? g.nx : 0;
+      yy += (yy < 0) ? g.ny : 0; yy -= (yy >= g.ny) ? g.ny : 0;
+      zz += (zz < 0) ? g.nz : 0; zz -= (zz >= g.nz) ? g.nz : 0;
+    }
+    xo[d] = (xx >= 0 && xx < g.nx) ? xx : kOut;
+    yo[d] = (yy >= 0 && yy < g.ny) ? yy * g.nx : kOut;
+    zo[d] = (zz >= 0 && zz < g.nz) ? zz * g.nx * g.ny : kOut;
+  }
+#pragma unroll
+  for (int kk = 0; kk < 27; ++kk) {
+    const int v = zo[kk / 9] + yo[(kk / 3) % 3] + xo[kk % 3];
+    q[kk] = (valid && v >= 0) ? v : -1;
+  }
+}
+
+// sqrt(a) and 1 / sqrt(a) of a normal, positive a to FP64 accuracy without the FP64 square-root and
+// division sequences (slow on this GPU): an FP32 reciprocal square root refined by two Newton steps
+// y <- y (3 - a y^2) / 2, whose error squares at each step (about 1e-7, 1e-14, 1e-28).  Arguments
+// outside the FP32 range take the exact route.
+__device__ __forceinline__ void sqrt_and_rsqrt(double a, double& s, double& r) {
+  if (a > 1e-30 && a < 1e30) {
+    double y = (double)rsqrtf((float)a);
+    y = y * (1.5 - 0.5 * a * y * y);
+    y = y * (1.5 - 0.5 * a * y * y);
+    r = y;
+    s = a * y;
+  } else {
+    s = sqrt(a);
+    r = 1.0 / s;
+  }
 }
 
 // The weights as the prediction kernel holds them in shared memory, laid out once per parameter update
@@ -539,25 +572,40 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_nn_predict(FusedArgs A) {
   }
   if (!fused_barrier(A, 1, &ok_s)) return;
   if (warp < 5) {       // totals in a fixed order: lane l sums CTAs l, l + 32, ..., then a shuffle tree
+    double xs[kFusedMaxBlocks / 32 + 1];
+#pragma unroll
+    for (int j = 0; j <= kFusedMaxBlocks / 32; ++j) {   // every load in flight at once
+      const unsigned b = lane + 32u * j;
+      xs[j] = b < gridDim.x ? __ldcg(&A.part[(size_t)b * 5 + warp]) : 0.0;
+    }
     double x = 0;
-    for (unsigned b = lane; b < gridDim.x; b += 32) x += __ldcg(&A.part[(size_t)b * 5 + warp]);
+#pragma unroll
+    for (int j = 0; j <= kFusedMaxBlocks / 32; ++j) x += xs[j];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
     if (lane == 0) st[warp] = x;
   }
   __syncthreads();
-  double s1, s2, s3, mean, sv;
-  {
-    const double n = (double)g.npts;
-    mean = st[3] / n;
-    const double fl = 1e-13 * sqrt(st[4] / n) + 1e-300;
-    s1 = fmax(sqrt(st[0] / n), fl);
-    s2 = fmax(sqrt(st[1] / n), fl);
-    s3 = fmax(sqrt(st[2] / n), fl);
-    sv = fmax(sqrt(fmax(st[4] / n - mean * mean, 0.0)), fl);
-    if (blockIdx.x == 0 && tid == 0) {
-      A.stats[0] = s1; A.stats[1] = s2; A.stats[2] = s3; A.stats[3] = mean; A.stats[4] = sv;
-    }
+  // the four scales s_j = max(rms_j, floor) and their reciprocals, one thread each (an FP32 seed and
+  // Newton steps; FP64 square roots and divisions are slow on this GPU)
+  __shared__ double sc[9];
+  if (tid < 4) {
+    const double mean = st[3] * A.inv_n;
+    double s0, r0;
+    sqrt_and_rsqrt(st[4] * A.inv_n, s0, r0);                       // rms(V0)
+    const double fl = 1e-13 * s0 + 1e-300;
+    const double a = (tid < 3) ? st[tid] * A.inv_n : fmax(st[4] * A.inv_n - mean * mean, 0.0);
+    double sj = 0.0, rj = 0.0;
+    if (a > 0.0) sqrt_and_rsqrt(a, sj, rj);
+    if (!(sj >= fl)) { sj = fl; rj = 1.0 / fl; }                    // floored (degenerate history)
+    sc[2 * tid] = sj;
+    sc[2 * tid + 1] = rj;
+    if (tid == 0) sc[8] = mean;
+  }
+  __syncthreads();
+  const double r1 = sc[1], r2 = sc[3], r3 = sc[5], rv = sc[7], s3 = sc[4], mean = sc[8];
+  if (blockIdx.x == 0 && tid == 0) {
+    A.stats[0] = sc[0]; A.stats[1] = sc[2]; A.stats[2] = sc[4]; A.stats[3] = mean; A.stats[4] = sc[6];
   }
   // phase 2: the four input channels of every point (BF16, channel-last)
   for (long long p = gtid; p < g.npts; p += nthr) {
@@ -565,9 +613,9 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_nn_predict(FusedArgs A) {
     const double d1 = v0 - v1, d2 = v0 - 2.0 * v1 + v2, d3 = v0 - 3.0 * v1 + 3.0 * v2 - v3;
     uint2 r;
     r.x = *reinterpret_cast<const unsigned*>(&(const __nv_bfloat162&)make_bfloat162(
-        __float2bfloat16((float)(d1 / s1)), __float2bfloat16((float)(d2 / s2))));
+        __float2bfloat16((float)(d1 * r1)), __float2bfloat16((float)(d2 * r2))));
     r.y = *reinterpret_cast<const unsigned*>(&(const __nv_bfloat162&)make_bfloat162(
-        __float2bfloat16((float)(d3 / s3)), __float2bfloat16((float)((v0 - mean) / sv))));
+        __float2bfloat16((float)(d3 * r3)), __float2bfloat16((float)((v0 - mean) * rv))));
     *reinterpret_cast<uint2*>(A.x0 + 4 * p) = r;
   }
   if (!fused_barrier(A, 2, &ok_s)) return;
@@ -601,52 +649,50 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_nn_predict(FusedArgs A) {
     *reinterpret_cast<uint2*>(A.a1 + 16 * (size_t)p + 4 * og) = r;
   }
   if (!fused_barrier(A, 3, &ok_s)) return;
-  // phase 4: layer 2 (16 -> 16) on the tensor cores, 16 points per warp
+  // phase 4: layer 2 (16 -> 16) on the tensor cores: a warp task is 16 points and one half (8) of the
+  // output channels, so that the tasks cover every warp of the grid
   {
     const int grp = lane >> 2, tq = lane & 3;
-    const int ntile = (g.npts + 15) / 16;
+    const int ntask = 2 * ((g.npts + 15) / 16);
     const int nwarp = gridDim.x * (blockDim.x / 32);
     const unsigned* a1w = reinterpret_cast<const unsigned*>(A.a1);   // 8 words per point
-    for (int tile = blockIdx.x * (blockDim.x / 32) + warp; tile < ntile; tile += nwarp) {
+    unsigned* a2w = reinterpret_cast<unsigned*>(A.a2);
+    for (int task = blockIdx.x * (blockDim.x / 32) + warp; task < ntask; task += nwarp) {
+      const int tile = task >> 1, h = task & 1;
       const int r0 = tile * 16 + grp, r1 = r0 + 8;
       const bool v0ok = r0 < g.npts, v1ok = r1 < g.npts;
       int x0, y0, z0, x1, y1, z1;
       coords(g, v0ok ? r0 : 0, x0, y0, z0);
       coords(g, v1ok ? r1 : 0, x1, y1, z1);
-      float d[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+      float d[4] = {0, 0, 0, 0};
       int q0[27], q1[27];
       tap_index(g, x0, y0, z0, v0ok, q0);
       tap_index(g, x1, y1, z1, v1ok, q1);
-      // the taps in three batches of nine: the batch's 36 words are loaded before its 18 MMAs
+      unsigned a[27][4];                      // every tap's words loaded before the 27 MMAs
 #pragma unroll
-      for (int k0 = 0; k0 < 27; k0 += 9) {
-        unsigned a[9][4];
-#pragma unroll
-        for (int j = 0; j < 9; ++j) {
-          const int kk = k0 + j;
-          a[j][0] = q0[kk] >= 0 ? a1w[8 * (size_t)q0[kk] + tq] : 0u;
-          a[j][1] = q1[kk] >= 0 ? a1w[8 * (size_t)q1[kk] + tq] : 0u;
-          a[j][2] = q0[kk] >= 0 ? a1w[8 * (size_t)q0[kk] + tq + 4] : 0u;
-          a[j][3] = q1[kk] >= 0 ? a1w[8 * (size_t)q1[kk] + tq + 4] : 0u;
-        }
-#pragma unroll
-        for (int j = 0; j < 9; ++j)
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const uint2 b = Bf[k0 + j][h][lane];
-            mma_bf16_16816(d[h], a[j], b.x, b.y);
-          }
+      for (int kk = 0; kk < 27; ++kk) {
+        a[kk][0] = q0[kk] >= 0 ? a1w[8 * (size_t)q0[kk] + tq] : 0u;
+        a[kk][1] = q1[kk] >= 0 ? a1w[8 * (size_t)q1[kk] + tq] : 0u;
+        a[kk][2] = q0[kk] >= 0 ? a1w[8 * (size_t)q0[kk] + tq + 4] : 0u;
+        a[kk][3] = q1[kk] >= 0 ? a1w[8 * (size_t)q1[kk] + tq + 4] : 0u;
       }
-      unsigned* a2w = reinterpret_cast<unsigned*>(A.a2);
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int c0 = 8 * h + 2 * tq;
-        if (v0ok) a2w[8 * (size_t)r0 + 4 * h + tq] = pack_bf16x2(silu(d[h][0] + b2s[c0]), silu(d[h][1] + b2s[c0 + 1]));
-        if (v1ok) a2w[8 * (size_t)r1 + 4 * h + tq] = pack_bf16x2(silu(d[h][2] + b2s[c0]), silu(d[h][3] + b2s[c0 + 1]));
+      for (int kk = 0; kk < 27; ++kk) {
+        const uint2 b = Bf[kk][h][lane];
+        mma_bf16_16816(d, a[kk], b.x, b.y);
       }
+      const int c0 = 8 * h + 2 * tq;
+      if (v0ok) a2w[8 * (size_t)r0 + 4 * h + tq] = pack_bf16x2(silu(d[0] + b2s[c0]), silu(d[1] + b2s[c0 + 1]));
+      if (v1ok) a2w[8 * (size_t)r1 + 4 * h + tq] = pack_bf16x2(silu(d[2] + b2s[c0]), silu(d[3] + b2s[c0 + 1]));
     }
   }
   if (!fused_barrier(A, 4, &ok_s)) return;
+  // every CTA is past the last barrier (none polls the counter any more): the last CTA to get here
+  // resets both counters for the next launch
+  if (tid == 0 && atomicAdd(A.bar + 1, 1u) == gridDim.x - 1) {
+    atomicExch(A.bar, 0u);
+    atomicExch(A.bar + 1, 0u);
+  }
   // phase 5: layer 3 (16 -> 1), four lanes per point splitting the channels, and the prediction
   for (long long t0 = (long long)blockIdx.x * blockDim.x; t0 < 4LL * g.npts; t0 += nthr) {
     const long long t = t0 + tid;                  // every lane of the warp takes part in the shuffles
@@ -776,10 +822,8 @@ cudaError_t nn_predict_fused(const NNBuffers& B, const NNGrid& g, const NNPredic
   if (nb > kFusedMaxBlocks) nb = kFusedMaxBlocks;
   if (nb > want) nb = want;
   if (nb < 1) nb = 1;
-  cudaError_t e = cudaMemsetAsync(B.bar, 0, sizeof(unsigned), s);
-  if (e != cudaSuccess) return e;
   FusedArgs A{g, pr.V0, pr.V1, pr.V2, pr.V3, pr.vpred, B.wpack,
-              B16(B.x0), B16(B.a1), B16(B.a2), B.stats, B.red, B.bar, B.err, wait_limit};
+              B16(B.x0), B16(B.a1), B16(B.a2), B.stats, B.red, 1.0 / (double)g.npts, B.bar, B.err, wait_limit};
   void* args[] = {&A};
   return cudaLaunchCooperativeKernel((const void*)k_nn_predict, dim3((unsigned)nb), dim3(kFusedThreads), args, 0, s);
 }

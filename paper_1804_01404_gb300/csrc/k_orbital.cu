@@ -24,6 +24,8 @@
 // request, the norm and the current of Eq. (macro_current).
 #include <cuda_runtime.h>
 
+#include <cstdint>
+
 #include <type_traits>
 
 #include "ff.cuh"
@@ -425,12 +427,38 @@ __global__ void __launch_bounds__(kMaxThreads<T, IP>(), kMinBlocks<T, IP>())
   // load the orbital (pad elements zero), phases; a predicted step also keeps a copy of its input
   // (the fallback restores it), written here while the values pass through
   C* bk = a.backup ? a.backup + (size_t)orb * a.npts : nullptr;
-  for (int i = threadIdx.x; i < vsz; i += blockDim.x) {
-    const int z = i / ps, r = i - z * ps;
-    const C u = (r < nxy) ? psi[z * nxy + r] : C{0, 0};
-    L.v[i] = u;
-    if (bk && r < nxy) bk[z * nxy + r] = u;
-    if (DBUF && !IP) L.nxt[i] = C{0, 0};
+  if (PER && ps == nxy && ((vsz * sizeof(C)) & 15) == 0 && ((reinterpret_cast<uintptr_t>(psi) & 15) == 0)) {
+    // a contiguous orbital: 16-byte copies, eight per thread in flight at once (a plain loop waits
+    // for each load before the next); the next buffer needs no clearing (every point is written)
+    const int nv = vsz * (int)sizeof(C) / 16;
+    const uint4* src = reinterpret_cast<const uint4*>(psi);
+    uint4* dst = reinterpret_cast<uint4*>(L.v);
+    uint4* bkv = reinterpret_cast<uint4*>(bk);
+    constexpr int U = 8;
+    for (int base = threadIdx.x; base < nv; base += U * blockDim.x) {
+      uint4 t[U];
+#pragma unroll
+      for (int j = 0; j < U; ++j) {
+        const int i = base + j * blockDim.x;
+        if (i < nv) t[j] = __ldg(src + i);
+      }
+#pragma unroll
+      for (int j = 0; j < U; ++j) {
+        const int i = base + j * blockDim.x;
+        if (i < nv) {
+          dst[i] = t[j];
+          if (bkv) bkv[i] = t[j];
+        }
+      }
+    }
+  } else {
+    for (int i = threadIdx.x; i < vsz; i += blockDim.x) {
+      const int z = i / ps, r = i - z * ps;
+      const C u = (r < nxy) ? psi[z * nxy + r] : C{0, 0};
+      L.v[i] = u;
+      if (bk && r < nxy) bk[z * nxy + r] = u;
+      if (DBUF && !IP) L.nxt[i] = C{0, 0};
+    }
   }
   // wave vector of the observables: k + A'_obs (OBS 1: end of the step; OBS 2: its start)
   auto obs_q = [&](T qo[3]) {

@@ -581,14 +581,15 @@ __global__ void __launch_bounds__(128) k_gproject(TileArgs<T> a, const typename 
 // FP32 projections as a batched dense contraction on the tensor cores.  For one atom the projections of
 // all orbitals are the matrix product C = U B: U [orbitals x sphere points] holds the orbitals' values at
 // the atom's sphere points (real and imaginary parts as two matrices), B [sphere points x 4] the real
-// projectors.  A warp takes 16 orbitals and walks the sphere points in steps of 8 with
-// mma.sync m16n8k8 TF32 (the four projectors padded to n = 8), FP32 accumulation.  Each operand is
+// projectors.  A CTA takes 16 orbitals; its warps walk interleaved steps of 8 sphere points with
+// mma.sync m16n8k8 TF32 (the four projectors padded to n = 8), FP32 accumulation, and their partial
+// products are added in shared memory in a fixed order.  Each operand is
 // split into a TF32 head and a TF32 tail (x = hi + lo, both exact in FP32) and the product is formed
 // as hi*hi + hi*lo + lo*hi, which keeps the sum at FP32 accuracy (three TF32 products per step).
 // Fragments (PTX ISA, m16n8k8 .tf32): A a0 (row g, col t), a1 (g+8, t), a2 (g, t+4), a3 (g+8, t+4);
 // B b0 (row t, col g), b1 (t+4, g); C c0 (g, 2t), c1 (g, 2t+1), c2 (g+8, 2t), c3 (g+8, 2t+1), with
 // g = lane / 4 and t = lane % 4.  Rows are orbitals, columns of B and C are projectors.
-constexpr int kPW = 4;      // warps per CTA (16 orbitals each)
+constexpr int kPW = 4;      // warps per CTA: the same 16 orbitals, each warp a quarter of the sphere points
 
 __device__ __forceinline__ unsigned tf32_rna(float x) {
   unsigned r;
@@ -610,17 +611,17 @@ __device__ __forceinline__ void mma_tf32_1688(float (&d)[4], const unsigned (&a)
 }
 
 __global__ void __launch_bounds__(32 * kPW) k_gproject_mma(TileArgs<float> a, const float2* __restrict__ v) {
+  __shared__ float part[kPW][32][8];
   const int at = blockIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane >> 2, t = lane & 3;
-  const int ob = (blockIdx.y * kPW + warp) * 16;
-  if (ob >= a.norb_tot) return;
+  const int ob = blockIdx.y * 16;
   const int i0 = a.atom_off[at], i1 = a.atom_off[at + 1];
   const bool r0 = ob + g < a.norb_tot, r1 = ob + g + 8 < a.norb_tot;
   const float2* u0 = v + (size_t)(r0 ? ob + g : 0) * a.npts;
   const float2* u1 = v + (size_t)(r1 ? ob + g + 8 : 0) * a.npts;
   float dre[4] = {0, 0, 0, 0}, dim[4] = {0, 0, 0, 0};
-  for (int k0 = i0; k0 < i1; k0 += 8) {
+  for (int k0 = i0 + 8 * warp; k0 < i1; k0 += 8 * kPW) {
     const int ia = k0 + t, ib = k0 + t + 4;
     const bool va = ia < i1, vb = ib < i1;
     const int xa = va ? a.sph_idx[ia] : 0, xb = vb ? a.sph_idx[ib] : 0;
@@ -646,14 +647,21 @@ __global__ void __launch_bounds__(32 * kPW) k_gproject_mma(TileArgs<float> a, co
     mma_tf32_1688(dim, ah, bl0, bl1);
     mma_tf32_1688(dim, ah, bh0, bh1);
   }
-  if (t < 2) {             // columns 2t, 2t+1 are projectors 0..3
+  // the warps' partial products meet in shared memory (fixed order)
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const int p = 2 * t + j;
-      const float sc = a.atomE[at * 4 + p] * a.dV;
-      if (r0) a.ec[((size_t)(ob + g) * a.natom + at) * 4 + p] = make_float2(dre[j] * sc, dim[j] * sc);
-      if (r1) a.ec[((size_t)(ob + g + 8) * a.natom + at) * 4 + p] = make_float2(dre[2 + j] * sc, dim[2 + j] * sc);
-    }
+  for (int j = 0; j < 4; ++j) { part[warp][lane][j] = dre[j]; part[warp][lane][4 + j] = dim[j]; }
+  __syncthreads();
+  if (warp != 0 || t >= 2) return;        // columns 2t, 2t+1 are projectors 0..3
+#pragma unroll
+  for (int w = 1; w < kPW; ++w)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) { dre[j] += part[w][lane][j]; dim[j] += part[w][lane][4 + j]; }
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const int p = 2 * t + j;
+    const float sc = a.atomE[at * 4 + p] * a.dV;
+    if (r0) a.ec[((size_t)(ob + g) * a.natom + at) * 4 + p] = make_float2(dre[j] * sc, dim[j] * sc);
+    if (r1) a.ec[((size_t)(ob + g + 8) * a.natom + at) * 4 + p] = make_float2(dre[2 + j] * sc, dim[2 + j] * sc);
   }
 }
 
@@ -821,7 +829,7 @@ template <typename T>
 cudaError_t launch_tile_project(const TileArgs<T>& a, const typename Cplx<T>::type* v, cudaStream_t s) {
   if (a.natom == 0) return cudaSuccess;
   if constexpr (sizeof(T) == 4) {      // FP32: tensor cores (3xTF32)
-    const dim3 grid(a.natom, (a.norb_tot + 16 * kPW - 1) / (16 * kPW));
+    const dim3 grid(a.natom, (a.norb_tot + 15) / 16);
     k_gproject_mma<<<grid, 32 * kPW, 0, s>>>(a, v);
   } else {
     const dim3 grid(a.natom, (a.norb_tot + kOB - 1) / kOB);

@@ -120,7 +120,7 @@ struct tdks_ctx {
   double pred_thr = 1e-5;
   double* d_vnew = nullptr;      // V_Hxc(t+dt) of a predicted step before acceptance
   double* d_resid = nullptr;     // device residual
-  double* h_resid = nullptr;     // pinned host copy
+  double* h_resid = nullptr;     // pinned host buffer [16] (step observables, misfit, fallbacks; c of TB-mBJ)
   void* d_backup = nullptr;      // orbitals at t (predicted steps)
   void* cur_backup = nullptr;    // set while the corrector of a predicted step writes the backup
   double fallbacks = 0, last_resid = 0;
@@ -149,9 +149,12 @@ struct tdks_ctx {
     }
   } sg_key;
   long long body_launches = 0;   // launches of the fallback body
+  long long body_calls[TDKS_NPHASE] = {0};   // phase calls of the fallback body
   int step_graph = 1;            // predicted steps as step graphs (1) or stream launches with a host decision (0)
   std::vector<Rec>* cap_recs = nullptr;   // set while a step graph is captured with profiling on
   cudaStream_t cap = nullptr, cap2 = nullptr;   // private streams the graphs are captured on
+  cudaStream_t side2 = nullptr;      // side stream of the tile path inside a fallback body
+  cudaStream_t body_side = nullptr;  // set to side2 while a fallback body is captured
   double* d_apf = nullptr;       // [6] A'(t+dt/2) and A' of the observables, read by the step graph
   double* d_fb = nullptr;        // fallback count (device)
   double fb_seen = 0;            // fallbacks already added to the launch count
@@ -160,6 +163,7 @@ struct tdks_ctx {
   int nn_step = 0;
   // profiling
   bool profiling = false;
+  bool prof_stencil_only = false;   // record events around the orbital stencil kernel launches only
   long long launches = 0;
   long long calls[TDKS_NPHASE] = {0};
   double ms[TDKS_NPHASE] = {0};
@@ -306,7 +310,7 @@ struct Phase {
   cudaEvent_t a = nullptr;
   Phase(tdks_ctx* c_, int p) : c(c_), phase(p) {
     c->calls[p] += 1;
-    if (c->profiling && (a = take_event(c)) != nullptr) record(a);
+    if (c->profiling && (!c->prof_stencil_only || p == 6) && (a = take_event(c)) != nullptr) record(a);
   }
   ~Phase() {
     if (!a) return;
@@ -370,11 +374,14 @@ tdks_status tiled_kernel(tdks_ctx* c, int mode, const void* in, void* out, doubl
   TileArgs<T> a = make_tile_args<T>(c, V);
   // the projections of the input (side stream) overlap the stencil (context stream); the scatter,
   // which needs both, waits for the projections
+  // (while the fallback body of a step graph is captured, the side stream of the enclosing capture
+  // is still part of that capture, so the body forks to a second one)
+  cudaStream_t side = c->body_side ? c->body_side : c->side;
   auto project = [&](const C* v) -> cudaError_t {
     cudaError_t e = cudaEventRecord(c->ev_fork, c->stream);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->side, c->ev_fork, 0);
-    if (e == cudaSuccess) e = launch_tile_project<T>(a, v, c->side);
-    if (e == cudaSuccess) e = cudaEventRecord(c->ev_join, c->side);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(side, c->ev_fork, 0);
+    if (e == cudaSuccess) e = launch_tile_project<T>(a, v, side);
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev_join, side);
     return e;
   };
   auto join = [&]() { return cudaStreamWaitEvent(c->stream, c->ev_join, 0); };
@@ -817,11 +824,15 @@ tdks_status tdks_init(const tdks_grid* grid, const tdks_cell* cell, const tdks_a
   if ((s = dalloc(c, &c->d_err, 1)) != TDKS_OK) return bail(s);
   if ((s = dalloc(c, &c->d_vhist, 4 * np)) != TDKS_OK) return bail(s);
   if ((s = dalloc(c, &c->d_vnew, npc)) != TDKS_OK) return bail(s);
-  if ((s = dalloc(c, &c->d_resid, 2)) != TDKS_OK) return bail(s);
+  // the step observables of every cell, then the misfit (2) and the fallback count: one block, so that
+  // tdks_read_step_observables of a single cell is one copy into pinned memory
+  if ((s = dalloc(c, &c->d_step_obs, 8 * (size_t)c->ncell + 4)) != TDKS_OK) return bail(s);
+  c->d_resid = c->d_step_obs + 8 * (size_t)c->ncell;
+  c->d_fb = c->d_resid + 2;
+  if (cudaMemsetAsync(c->d_step_obs, 0, (8 * (size_t)c->ncell + 4) * sizeof(double), c->stream) != cudaSuccess)
+    return bail(fail(TDKS_ECUDA, "memset"));
   if ((s = dalloc(c, &c->d_apf, 6)) != TDKS_OK) return bail(s);
-  if ((s = dalloc(c, &c->d_fb, 1)) != TDKS_OK) return bail(s);
-  if (cudaMemsetAsync(c->d_fb, 0, sizeof(double), c->stream) != cudaSuccess) return bail(fail(TDKS_ECUDA, "memset"));
-  if (cudaMallocHost((void**)&c->h_resid, sizeof(double)) != cudaSuccess) return bail(fail(TDKS_ENOMEM, "pinned"));
+  if (cudaMallocHost((void**)&c->h_resid, 16 * sizeof(double)) != cudaSuccess) return bail(fail(TDKS_ENOMEM, "pinned"));
   if (is_f32(c) && !c->tiled)
     if ((s = dalloc(c, &c->d_rho32, npc * (size_t)nk)) != TDKS_OK) return bail(s);
   cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
@@ -853,12 +864,10 @@ tdks_status tdks_init(const tdks_grid* grid, const tdks_cell* cell, const tdks_a
     c->d_porb = p;
     cudaMemsetAsync(c->d_mbj_c, 0, sizeof(double), c->stream);
   }
-  if ((s = dalloc(c, &c->d_step_obs, 8 * (size_t)c->ncell)) != TDKS_OK) return bail(s);
   c->red_blocks = 304;
   if ((s = dalloc(c, &c->d_partials, (size_t)c->red_blocks * 4)) != TDKS_OK) return bail(s);
   if ((s = dalloc(c, &c->d_ticket, 1)) != TDKS_OK) return bail(s);
   cudaMemsetAsync(c->d_ticket, 0, sizeof(unsigned), c->stream);
-  cudaMemsetAsync(c->d_step_obs, 0, 8 * sizeof(double) * c->ncell, c->stream);
 
   // FFT set-up: periodic transforms are n^3, isolated ones (2n)^3 (zero padding)
   for (int a = 0; a < 3; ++a) {
@@ -938,6 +947,7 @@ void tdks_destroy(tdks_ctx* c) {
   }
   if (c->cap) cudaStreamDestroy(c->cap);
   if (c->cap2) cudaStreamDestroy(c->cap2);
+  if (c->side2) cudaStreamDestroy(c->side2);
   delete c;
 }
 
@@ -1417,7 +1427,11 @@ static tdks_status sync_fallbacks(tdks_ctx* c) {
   double fb = 0.0;
   TDKS_CUDA(cudaMemcpyAsync(&fb, c->d_fb, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   TDKS_CUDA(cudaStreamSynchronize(c->stream));
-  if (fb > c->fb_seen) c->launches += (long long)(fb - c->fb_seen) * c->body_launches;
+  if (fb > c->fb_seen) {
+    const long long n = (long long)(fb - c->fb_seen);
+    c->launches += n * c->body_launches;
+    for (int p = 0; p < TDKS_NPHASE; ++p) c->calls[p] += n * c->body_calls[p];
+  }
   c->fb_seen = fb;
   c->fallbacks = fb;
   return TDKS_OK;
@@ -1510,6 +1524,7 @@ static tdks_status build_step_graph(tdks_ctx* c, void* u, double dt, const doubl
   auto& g = c->sg[c->hist_head];
   if (!c->cap) TDKS_CUDA(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
   if (!c->cap2) TDKS_CUDA(cudaStreamCreateWithFlags(&c->cap2, cudaStreamNonBlocking));
+  if (c->tiled && !c->side2) TDKS_CUDA(cudaStreamCreateWithFlags(&c->side2, cudaStreamNonBlocking));
   const cudaStream_t main = c->stream;
   const bool prof = c->profiling;
   const long long launches0 = c->launches;
@@ -1555,9 +1570,12 @@ static tdks_status build_step_graph(tdks_ctx* c, void* u, double dt, const doubl
       // the fallback body: restore the orbitals, plain predictor-corrector (no profiling events: a
       // conditional body holds kernels, copies and memsets only)
       c->stream = c->cap2;
+      c->body_side = c->side2;
       c->cap_recs = nullptr;
       c->profiling = false;
       body0 = c->launches;
+      long long bc0[TDKS_NPHASE];
+      std::memcpy(bc0, c->calls, sizeof(bc0));
       e = cudaStreamBeginCaptureToGraph(c->cap2, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
       if (e == cudaSuccess) {
         e = cudaMemcpyAsync(u, c->d_backup, obytes, cudaMemcpyDeviceToDevice, c->stream);
@@ -1566,7 +1584,9 @@ static tdks_status build_step_graph(tdks_ctx* c, void* u, double dt, const doubl
         if (e == cudaSuccess) e = e2;
       }
       body1 = c->launches;
+      for (int p = 0; p < TDKS_NPHASE; ++p) c->body_calls[p] = c->calls[p] - bc0[p];
       c->stream = c->cap;
+      c->body_side = nullptr;
       c->cap_recs = prof ? &g.recs : nullptr;
       c->profiling = prof;
     }
@@ -1576,7 +1596,7 @@ static tdks_status build_step_graph(tdks_ctx* c, void* u, double dt, const doubl
   }
   c->body_launches = body1 - body0;
   g.launches = c->launches - launches0 - c->body_launches;
-  for (int p = 0; p < TDKS_NPHASE; ++p) g.calls[p] = c->calls[p] - calls0[p];
+  for (int p = 0; p < TDKS_NPHASE; ++p) g.calls[p] = c->calls[p] - calls0[p] - c->body_calls[p];
   c->launches = launches0;
   std::memcpy(c->calls, calls0, sizeof(calls0));
   c->stream = main;
@@ -1626,7 +1646,7 @@ static tdks_status predicted_step(tdks_ctx* c, void* u, const double Amid[3], co
   key.u = u; key.dt = dt; key.thr = c->pred_thr; key.mbj_c = c->mbj_c_fixed; key.mode = c->pred_mode;
   key.lg = c->longitudinal ? 1 : 0; key.has_obs = Aobs ? 1 : 0; key.obs_start = obs_start ? 1 : 0;
   key.cell_variant = c->cell_variant; key.tile0 = c->tile_variant[0]; key.tile1 = c->tile_variant[1];
-  key.prof = c->profiling ? 1 : 0;
+  key.prof = c->profiling ? (c->prof_stencil_only ? 2 : 1) : 0;
   if (!(key == c->sg_key)) {
     drop_step_graphs(c);
     c->sg_key = key;
@@ -1779,10 +1799,23 @@ tdks_status tdks_ms_read(tdks_ctx* c, double* A_host, double* I_host) {
 tdks_status tdks_read_step_observables(tdks_ctx* c, tdks_obs* o) {
   TDKS_TRY(check_ctx(c));
   if (!o) return fail(TDKS_EINVAL, "null output");
-  double h[8], r = 0.0;
-  TDKS_CUDA(cudaMemcpyAsync(h, c->d_step_obs, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
-  TDKS_CUDA(cudaMemcpyAsync(&r, c->d_resid, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-  TDKS_TRY(sync_fallbacks(c));
+  double* h = c->h_resid;
+  if (c->ncell == 1) {       // J, dipole, N, misfit, fallback count: one copy
+    TDKS_CUDA(cudaMemcpyAsync(h, c->d_step_obs, 11 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  } else {
+    TDKS_CUDA(cudaMemcpyAsync(h, c->d_step_obs, 8 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    TDKS_CUDA(cudaMemcpyAsync(h + 8, c->d_resid, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  }
+  TDKS_CUDA(cudaStreamSynchronize(c->stream));
+  const double r = h[8];
+  const double fb = h[10];
+  if (fb > c->fb_seen) {
+    const long long n = (long long)(fb - c->fb_seen);
+    c->launches += n * c->body_launches;
+    for (int p = 0; p < TDKS_NPHASE; ++p) c->calls[p] += n * c->body_calls[p];
+  }
+  c->fb_seen = fb;
+  c->fallbacks = fb;
   std::memset(o, 0, sizeof(*o));
   for (int a = 0; a < 3; ++a) { o->J[a] = h[a]; o->dipole[a] = h[3 + a]; }
   o->n_elec = h[6];
@@ -1860,6 +1893,8 @@ tdks_status tdks_check(tdks_ctx* c) {
   TDKS_CUDA(cudaMemcpy(&err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
   if (err != 0) {
     cudaMemset(c->d_err, 0, sizeof(int));
+    // a prediction whose grid barrier gave up left its counters behind
+    if (c->nn_ready) cudaMemset(c->nn.bar, 0, 2 * sizeof(unsigned));
     return fail((tdks_status)err, "a device-side wait timed out (kernel gave up and returned)");
   }
   return TDKS_OK;
@@ -1928,7 +1963,8 @@ tdks_status tdks_nn_init(tdks_ctx* c, unsigned long long seed) {
     TDKS_TRY(dalloc(c, &B.loss, 1));
     TDKS_TRY(dalloc(c, &B.red, 304 * 5));
     TDKS_TRY(dalloc(c, &B.ticket, 1));
-    TDKS_TRY(dalloc(c, &B.bar, 1));
+    TDKS_TRY(dalloc(c, &B.bar, 2));
+    TDKS_CUDA(cudaMemsetAsync(B.bar, 0, 2 * sizeof(unsigned), c->stream));
     TDKS_TRY(dalloc(c, &B.wpack, nn_wpack_bytes() / sizeof(uint4)));
     TDKS_CUDA(cudaMemsetAsync(B.ticket, 0, sizeof(unsigned), c->stream));
     B.err = c->d_err;
@@ -2043,7 +2079,9 @@ tdks_status tdks_nn_gradient(tdks_ctx* c, const double* vhist, const double* vne
 
 tdks_status tdks_profile(tdks_ctx* c, int enable) {
   TDKS_TRY(check_ctx(c));
+  if (enable < 0 || enable > 2) return fail(TDKS_EINVAL, "enable must be 0, 1 or 2");
   c->profiling = enable != 0;
+  c->prof_stencil_only = enable == 2;
   return TDKS_OK;
 }
 

@@ -188,7 +188,7 @@ struct NNBuffers {
   double* loss;                                   // accumulator
   double* red;                                    // [304][5] grid_sum partials of the statistics
   unsigned* ticket;                               // grid_sum ticket (zero between launches)
-  unsigned* bar;                                  // grid-barrier counter of the fused prediction
+  unsigned* bar;                                  // [2] grid-barrier counters of the fused prediction (zero between launches)
   uint4* wpack;                                   // shared-memory image of the prediction's weights
   int* err;                                       // context error word (TDKS_ETIMEOUT of a barrier wait)
 };

@@ -489,6 +489,8 @@ class Context:
         return loss.value, g
 
     def profile(self, enable=True):
+        """Phase timing on (True or 1: every phase; 2: the orbital stencil kernel only) or off
+        (tdks_profile)."""
         _check(self.lib.tdks_profile(self.ctx, int(enable)))
 
     def stats(self, reset=False):

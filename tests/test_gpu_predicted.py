@@ -128,3 +128,42 @@ def test_learned_steps_with_rejections_match_the_oracle():
     assert np.linalg.norm(g["psi"] - psi) < 1e-10 * np.linalg.norm(psi)
     assert _rel(g["J"], rec["J"]) < 1e-10
     assert _rel(g["d"], rec["d"]) < 1e-10
+
+
+def _tile_system():
+    s = W.isolated_cluster(n=24, natom=5, norb=3, radius=3.5, seed=4)
+    s.n = (40, 30, 28)                      # does not fit the shared-memory cell kernels: tile path
+    s.h = (0.45, 0.5, 0.55)
+    return s
+
+
+@pytest.mark.parametrize("graph", [True, False])
+@pytest.mark.parametrize("threshold", [1.0, 1e-300])
+def test_predicted_steps_on_the_tile_path(graph, threshold):
+    """Cubic-extrapolation steps on a large isolated grid (TMA tile kernels, projections on a side
+    stream), every prediction kept (threshold 1) or every one rejected (the fallback body, which forks
+    its own side stream inside the step graph), as a step graph and as stream launches, FP64, against
+    the oracle's predicted run."""
+    from paper_1804_01404_gb300 import tdks as T
+    s = _tile_system()
+    n = 7
+    psi0 = O.apply_kick(s, W.initial_orbitals(s, 2), (0.0, 0.0, 0.01))
+    psi, v, rec = O.run_predicted(s, psi0, n, N.cubic_extrapolation, threshold)
+    assert rec["rejected"] == (0 if threshold == 1.0 else n - 3)
+    ctx = T.Context(s, precision="f64")
+    u = torch.from_numpy(psi0).to("cuda")
+    ctx.update_potential(u)
+    ctx.set_predictor(T.PRED_EXTRAP, threshold)
+    ctx.set_step_graph(graph)
+    d = []
+    t = 0.0
+    for _ in range(n):
+        ctx.step(u, t, s.dt)
+        t += s.dt
+        d.append(ctx.read_step_observables()["dipole"])
+    ctx.check()
+    assert ctx.read_step_observables()["fallbacks"] == rec["rejected"]
+    got = u.cpu().numpy()
+    assert np.linalg.norm(got - psi) < 1e-10 * np.linalg.norm(psi)
+    assert _rel(np.array(d), rec["d"]) < 1e-10
+    ctx.close()
