@@ -163,21 +163,22 @@ tdks_status tdks_set_field_table(tdks_ctx* ctx, const double* Ap, int nt, double
 
 /* Ground state (the static Kohn-Sham problem solved before the time evolution; the paper's ground-
  * state step uses Gram-Schmidt orthonormalisation): the lowest norb states of every k-point at A' = 0,
- * self-consistent in V_Hxc, for the context's synthetic pseudo-atoms.  Each iteration takes an
- * imaginary-time (steepest-descent) step in the subspace, orthonormalises by Cholesky (the
- * Gram-Schmidt of the set) and mixes the potential linearly:
- *   M = U^H H U dV,  W = U - tau (H U - U M),  U = W L^{-H} with W^H W dV = L L^H,
- *   V_in <- V_in + mix (V_Hxc[rho(U)] - V_in).
- * It stops when the subspace residual sqrt(sum ||H U - U M||^2 / (nk norb)) and the potential misfit
- * ||V_Hxc[rho] - V_in|| / ||V_Hxc[rho]|| (checked every 10 iterations) are both below tol, or after
- * max_iter.  u: caller's orbitals [nk][norb][nz][ny][nx] (the start; overwritten by an orthonormal
- * basis of the occupied subspace -- the density and current depend on nothing else).  Afterwards
- * V_Hxc(t) and rho0 are those of the ground state.  tau <= 0 picks 1 / (3.25 sum_a h_a^-2 + 4), below
- * the stability bound of the step.  out[3] (nullable): iterations, final residual, band energy
- * sum_k w_k sum_n 2 M_nn.  Synchronises every iteration (the small Cholesky runs on the host).
- * Errors: EUNSUPPORTED for ncell > 1 or norb > 64; EINVAL for bad arguments or linearly dependent
- * orbitals; ENOMEM. */
-tdks_status tdks_ground_state(tdks_ctx* ctx, void* u, int max_iter, double tol, double tau, double mix,
+ * self-consistent in V_Hxc, for the context's synthetic pseudo-atoms.  Chebyshev-filtered subspace
+ * iteration on a block of nb = norb + max(4, norb/4) states per k-point: each iteration filters the
+ * block with the Chebyshev polynomial of the given degree that damps the spectrum between the block's
+ * highest Ritz value and an upper bound of H (the FD kinetic symbol, the largest potential and a
+ * Gershgorin bound of the projectors), orthonormalises it (Cholesky: the Gram-Schmidt of the set),
+ * takes the Rayleigh-Ritz rotation (norb x norb problems on the host), puts the lowest norb Ritz vectors
+ * into u, and mixes the potential linearly, V_in <- V_in + mix (V_Hxc[rho(u)] - V_in).
+ * It stops when the residual sqrt(sum_occupied ||H u - e u||^2 / (nk norb)) and the potential misfit
+ * ||V_Hxc[rho] - V_in|| / ||V_Hxc[rho]|| are both below tol, or after max_iter iterations.
+ * u: caller's orbitals [nk][norb][nz][ny][nx] (the start; overwritten by the occupied Ritz vectors,
+ * orthonormal).  Afterwards V_Hxc(t) and rho0 are those of the ground state.  degree <= 0 picks 10.
+ * out[3] (nullable): iterations, final residual, band energy sum_k w_k sum_n 2 e_kn.  Allocates its
+ * work blocks and a context of nb orbitals per k-point for the duration of the call; synchronises every
+ * iteration.  Errors: EUNSUPPORTED for ncell > 1, norb > 64 or an orbital shard; EINVAL for bad
+ * arguments or linearly dependent orbitals; ENOMEM. */
+tdks_status tdks_ground_state(tdks_ctx* ctx, void* u, int max_iter, double tol, double degree, double mix,
                               double* out);
 
 /* Number density of excited electron-hole pairs (Sec. 4.2 example; the paper gives no formula):

@@ -70,6 +70,25 @@ __global__ void k_basis(const typename Cplx<T>::type* __restrict__ U, const type
   }
 }
 
+// out = a A + b B + g C, elementwise over n complex values (C unread when g = 0): one step of the
+// Chebyshev filter's three-term recurrence
+template <typename T>
+__global__ void k_lincomb3(const typename Cplx<T>::type* __restrict__ A, const typename Cplx<T>::type* __restrict__ B,
+                           const typename Cplx<T>::type* __restrict__ Cv, double a, double b, double g, long long n,
+                           typename Cplx<T>::type* __restrict__ out) {
+  using C = typename Cplx<T>::type;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const C x = A[i], y = B[i];
+    double re = a * (double)x.x + b * (double)y.x, im = a * (double)x.y + b * (double)y.y;
+    if (g != 0.0) {
+      const C z = Cv[i];
+      re += g * (double)z.x;
+      im += g * (double)z.y;
+    }
+    out[i] = C{(T)re, (T)im};
+  }
+}
+
 // vin <- vin + mix (vout - vin); vout <- vin (the mixed potential becomes the current V_Hxc)
 __global__ void k_mix_potential(double* __restrict__ vin, double* __restrict__ vout, long long n, double mix) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -97,6 +116,20 @@ cudaError_t launch_basis(const typename Cplx<T>::type* U, const typename Cplx<T>
   k_basis<T><<<dim3(bx, nk), 256, 0, s>>>(U, V, M, norb, npts, a, c0, b, out);
   return cudaGetLastError();
 }
+
+template <typename T>
+cudaError_t launch_lincomb3(const typename Cplx<T>::type* A, const typename Cplx<T>::type* B,
+                            const typename Cplx<T>::type* Cv, double a, double b, double g, long long n,
+                            typename Cplx<T>::type* out, cudaStream_t s) {
+  long long bl = (n + 255) / 256;
+  if (bl > 152 * 16) bl = 152 * 16;
+  k_lincomb3<T><<<(int)(bl < 1 ? 1 : bl), 256, 0, s>>>(A, B, Cv, a, b, g, n, out);
+  return cudaGetLastError();
+}
+template cudaError_t launch_lincomb3<float>(const float2*, const float2*, const float2*, double, double, double,
+                                            long long, float2*, cudaStream_t);
+template cudaError_t launch_lincomb3<double>(const double2*, const double2*, const double2*, double, double, double,
+                                             long long, double2*, cudaStream_t);
 
 cudaError_t launch_mix_potential(double* vin, double* vout, long long n, double mix, cudaStream_t s) {
   long long b = (n + 255) / 256;

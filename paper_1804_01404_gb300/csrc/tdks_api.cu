@@ -24,6 +24,17 @@ tdks_status fail(tdks_status s, const std::string& msg) {
 
 void tdks::set_last_error(const char* msg) { g_err = msg; }
 
+namespace {
+// seeded uniform numbers (splitmix64) for initial network parameters and buffer states
+unsigned long long splitmix64(unsigned long long& x) {
+  unsigned long long z = (x += 0x9E3779B97F4A7C15ULL);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+double uniform01(unsigned long long& x) { return (splitmix64(x) >> 11) * (1.0 / 9007199254740992.0); }
+}  // namespace
+
 #define TDKS_CUDA(call)                                                                    \
   do {                                                                                     \
     cudaError_t e_ = (call);                                                               \
@@ -46,6 +57,10 @@ constexpr int kMaxPulses = 8;
 
 struct tdks_ctx {
   tdks_grid grid{};
+  tdks_cell cell_in{};
+  std::vector<tdks_atom> atoms_in;
+  std::vector<tdks_projector> proj_in;
+  double vnl_bound = 0.0;        // upper bound of ||V_NL|| (Gershgorin on the projector overlaps)
   int npts = 0, nk = 0, norb = 0, ncell = 1;
   // multiscale: A(X) at three time levels (ring), cell currents I(X), per-cell A'
   int nX = 0, m0 = 0, ms_head = 0;
@@ -769,6 +784,29 @@ tdks_status tdks_init(const tdks_grid* grid, const tdks_cell* cell, const tdks_a
   std::string err;
   if (!build_projector_tables(*grid, atoms, natom, projectors, nproj, T, err))
     return bail(fail(TDKS_EINVAL, err));
+  // the set-up inputs (the ground-state solver builds a sibling context with a larger orbital block)
+  if (cell) c->cell_in = *cell;
+  if (natom > 0) c->atoms_in.assign(atoms, atoms + natom);
+  if (nproj > 0) c->proj_in.assign(projectors, projectors + nproj);
+  // bound on the norm of the nonlocal operator: max |E_p| times the largest row sum of |<beta_i|beta_j>|
+  // (Gershgorin), the overlaps bounded pointwise through the point -> entries table
+  {
+    std::vector<double> row((size_t)T.natom * 4, 0.0);
+    double emax = 0.0;
+    for (double e : T.E) emax = std::max(emax, std::fabs(e));
+    for (size_t pt = 0; pt + 1 < T.pt_off.size(); ++pt)
+      for (int e1 = T.pt_off[pt]; e1 < T.pt_off[pt + 1]; ++e1)
+        for (int e2 = T.pt_off[pt]; e2 < T.pt_off[pt + 1]; ++e2) {
+          const int i = T.pt_ent[e1], j = T.pt_ent[e2];
+          double bj = 0.0;
+          for (int q = 0; q < 4; ++q) bj += std::fabs(T.beta[4 * (size_t)j + q]);
+          for (int p = 0; p < 4; ++p)
+            row[(size_t)T.ent_atom[i] * 4 + p] += std::fabs(T.beta[4 * (size_t)i + p]) * bj * c->dV;
+        }
+    double rmax = 0.0;
+    for (double r : row) rmax = std::max(rmax, r);
+    c->vnl_bound = emax * rmax;
+  }
   c->natom = T.natom;
   c->nsph = (int)T.idx.size();
   c->nsp = (int)T.sp_pt.size();
@@ -995,107 +1033,255 @@ bool cholesky_inverse_h(const double2* S, int n, double2* Cout) {
 }
 }  // namespace
 
-tdks_status tdks_ground_state(tdks_ctx* c, void* u, int max_iter, double tol, double tau, double mix, double* out) {
+tdks_status tdks_ground_state(tdks_ctx* c, void* u, int max_iter, double tol, double degree, double mix,
+                              double* out) {
   TDKS_TRY(check_ctx(c));
   TDKS_TRY(check_whole_set(c, "tdks_ground_state"));
   if (!u) return fail(TDKS_EINVAL, "null orbitals");
   if (c->ncell != 1) return fail(TDKS_EUNSUPPORTED, "tdks_ground_state needs ncell = 1");
   if (c->norb > 64) return fail(TDKS_EUNSUPPORTED, "tdks_ground_state handles at most 64 orbitals per k-point");
-  if (max_iter < 1 || !(tol > 0.0) || !(mix > 0.0 && mix <= 1.0) || !std::isfinite(tau))
-    return fail(TDKS_EINVAL, "need max_iter >= 1, tol > 0, 0 < mix <= 1 and a finite tau");
-  if (tau <= 0.0) {   // below 2 / (largest eigenvalue): the FD kinetic symbol is at most 3.25 sum 1/h^2
-    double s = 0.0;
-    for (int a = 0; a < 3; ++a) s += 1.0 / (c->grid.h[a] * c->grid.h[a]);
-    tau = 1.0 / (3.25 * s + 4.0);
-  }
+  if (max_iter < 1 || !(tol > 0.0) || !(mix > 0.0 && mix <= 1.0) || !std::isfinite(degree))
+    return fail(TDKS_EINVAL, "need max_iter >= 1, tol > 0, 0 < mix <= 1 and a finite filter degree");
+  const int m = degree > 0.0 ? std::max(2, std::min(60, (int)std::lround(degree))) : 10;
   const int nk = c->nk, no = c->norb, np = c->npts;
+  const int nb = std::min(no + std::max(4, (no + 3) / 4), np);      // the block: occupied + buffer states
   const bool f32 = is_f32(c);
   const size_t csz = f32 ? sizeof(float2) : sizeof(double2);
-  const size_t nob = (size_t)nk * no * np * csz, nmat = (size_t)nk * no * no;
-  void *HU = nullptr, *Wb = nullptr;
-  double2 *dM = nullptr, *dS = nullptr, *dC = nullptr;
+  const size_t nblk = (size_t)nk * nb * np;                          // complex values of one block
+  const size_t nmat = (size_t)nk * nb * nb;
+  using Z = std::complex<double>;
+  std::vector<Z> hM(nmat), hC(nmat);
+  std::vector<double> hv((size_t)np), hvin((size_t)np), hvl((size_t)np), eig((size_t)nk * nb, 0.0);
+  void* Bf[4] = {nullptr, nullptr, nullptr, nullptr};
+  double2 *dM = nullptr, *dC = nullptr;
   double* d_vin = nullptr;
-  std::vector<double2> hM(nmat), hS(nmat), hC(nmat);
-  std::vector<double> hv((size_t)np), hvin((size_t)np);
+  tdks_ctx* sib = nullptr;
   cudaError_t e = cudaSuccess;
   auto chk = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
-  chk(cudaMalloc(&HU, nob));
-  chk(cudaMalloc(&Wb, nob));
+  for (auto& b : Bf) chk(cudaMalloc(&b, nblk * csz));
   chk(cudaMalloc(&dM, nmat * sizeof(double2)));
-  chk(cudaMalloc(&dS, nmat * sizeof(double2)));
   chk(cudaMalloc(&dC, nmat * sizeof(double2)));
   chk(cudaMalloc(&d_vin, (size_t)np * sizeof(double)));
   auto cleanup = [&]() {
     cudaStreamSynchronize(c->stream);
-    cudaFree(HU); cudaFree(Wb); cudaFree(dM); cudaFree(dS); cudaFree(dC); cudaFree(d_vin);
+    for (auto& b : Bf) cudaFree(b);
+    cudaFree(dM); cudaFree(dC); cudaFree(d_vin);
+    if (sib) tdks_destroy(sib);
   };
   if (e != cudaSuccess) { cleanup(); return fail(TDKS_ENOMEM, "tdks_ground_state: device memory"); }
+  // a context of the same system with nb orbitals per k-point applies H to the block
+  {
+    tdks_options o2 = c->opt;
+    o2.hartree = 0; o2.xc = 0; o2.pc = 0; o2.ncell = 1; o2.obs_at_start = 0; o2.norb_offset = 0; o2.norb_total = 0;
+    const tdks_status st = tdks_init(&c->grid, &c->cell_in, c->atoms_in.empty() ? nullptr : c->atoms_in.data(),
+                                     (int)c->atoms_in.size(), c->proj_in.empty() ? nullptr : c->proj_in.data(),
+                                     (int)c->proj_in.size(), c->kpts.data(), c->kw.data(), nk, nb, &o2, c->stream, &sib);
+    if (st != TDKS_OK) { cleanup(); return st; }
+  }
+  const double zeroA[3] = {0.0, 0.0, 0.0};
+  auto H = [&](const void* in, void* o) -> tdks_status {                   // o = H in, the block
+    TDKS_TRY(set_step_potential(sib, 1.0, nullptr, 0.0));
+    return orbital_kernel(sib, 0, in, o, zeroA, 0.0, nullptr, 1);
+  };
   auto gram = [&](const void* A, const void* B, double2* o) {
-    return f32 ? launch_gram<float>((const float2*)A, (const float2*)B, nk, no, np, c->dV, o, c->stream)
-               : launch_gram<double>((const double2*)A, (const double2*)B, nk, no, np, c->dV, o, c->stream);
+    return f32 ? launch_gram<float>((const float2*)A, (const float2*)B, nk, nb, np, c->dV, o, c->stream)
+               : launch_gram<double>((const double2*)A, (const double2*)B, nk, nb, np, c->dV, o, c->stream);
   };
   auto basis = [&](const void* U, const void* V, const double2* M, double a, double c0, double b, void* o) {
-    return f32 ? launch_basis<float>((const float2*)U, (const float2*)V, M, nk, no, np, a, c0, b, (float2*)o, c->stream)
-               : launch_basis<double>((const double2*)U, (const double2*)V, M, nk, no, np, a, c0, b, (double2*)o,
+    return f32 ? launch_basis<float>((const float2*)U, (const float2*)V, M, nk, nb, np, a, c0, b, (float2*)o, c->stream)
+               : launch_basis<double>((const double2*)U, (const double2*)V, M, nk, nb, np, a, c0, b, (double2*)o,
                                       c->stream);
   };
-  // dst = src C with C = L^{-H} of the overlap of src: an orthonormal basis of the same subspace
+  auto lincomb = [&](const void* A, const void* B, const void* C3, double a, double b, double g, void* o) {
+    return f32 ? launch_lincomb3<float>((const float2*)A, (const float2*)B, (const float2*)C3, a, b, g,
+                                        (long long)nblk, (float2*)o, c->stream)
+               : launch_lincomb3<double>((const double2*)A, (const double2*)B, (const double2*)C3, a, b, g,
+                                         (long long)nblk, (double2*)o, c->stream);
+  };
+  auto vec = [&](void* base, int k, int n) {        // start of vector n of k-point k in a block
+    return static_cast<unsigned char*>(base) + (((size_t)k * nb + n) * np) * csz;
+  };
+  // orthonormal block: dst = src L^{-H} with src^H src dV = L L^H
   auto ortho = [&](const void* src, void* dst) -> tdks_status {
-    TDKS_CUDA(gram(src, src, dS));
-    TDKS_CUDA(cudaMemcpyAsync(hS.data(), dS, nmat * sizeof(double2), cudaMemcpyDeviceToHost, c->stream));
+    TDKS_CUDA(gram(src, src, dM));
+    TDKS_CUDA(cudaMemcpyAsync(hM.data(), dM, nmat * sizeof(double2), cudaMemcpyDeviceToHost, c->stream));
     TDKS_CUDA(cudaStreamSynchronize(c->stream));
     for (int k = 0; k < nk; ++k)
-      if (!cholesky_inverse_h(&hS[(size_t)k * no * no], no, &hC[(size_t)k * no * no]))
+      if (!cholesky_inverse_h(&hM[(size_t)k * nb * nb], nb, &hC[(size_t)k * nb * nb]))
         return fail(TDKS_EINVAL, "tdks_ground_state: the orbitals are linearly dependent");
     TDKS_CUDA(cudaMemcpyAsync(dC, hC.data(), nmat * sizeof(double2), cudaMemcpyHostToDevice, c->stream));
     TDKS_CUDA(basis(src, nullptr, dC, 0.0, 0.0, 1.0, dst));
+    c->launches += 2;
+    return TDKS_OK;
+  };
+  // Rayleigh-Ritz of the orthonormal block X (HX its H image, W a work block): the eigenpairs of the
+  // projected H per k (host Jacobi), X and HX rotated into Ritz vectors, eig their values
+  auto ritz = [&](void*& X, void*& HX, void*& W) -> tdks_status {
+    TDKS_TRY(H(X, HX));
+    TDKS_CUDA(gram(X, HX, dM));
+    TDKS_CUDA(cudaMemcpyAsync(hM.data(), dM, nmat * sizeof(double2), cudaMemcpyDeviceToHost, c->stream));
+    TDKS_CUDA(cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < nk; ++k) {
+      std::vector<Z> A(hM.begin() + (size_t)k * nb * nb, hM.begin() + (size_t)(k + 1) * nb * nb), Y;
+      for (int i2 = 0; i2 < nb; ++i2)                  // the projected H is Hermitian up to rounding
+        for (int j2 = 0; j2 < i2; ++j2) {
+          const Z h = 0.5 * (A[(size_t)i2 * nb + j2] + std::conj(A[(size_t)j2 * nb + i2]));
+          A[(size_t)i2 * nb + j2] = h;
+          A[(size_t)j2 * nb + i2] = std::conj(h);
+        }
+      std::vector<double> w;
+      herm_eig(A, nb, w, Y);
+      for (int n = 0; n < nb; ++n) eig[(size_t)k * nb + n] = w[n];
+      std::copy(Y.begin(), Y.end(), hC.begin() + (size_t)k * nb * nb);
+    }
+    TDKS_CUDA(cudaMemcpyAsync(dC, hC.data(), nmat * sizeof(double2), cudaMemcpyHostToDevice, c->stream));
+    TDKS_CUDA(basis(X, nullptr, dC, 0.0, 0.0, 1.0, W));
+    std::swap(X, W);
+    TDKS_CUDA(basis(HX, nullptr, dC, 0.0, 0.0, 1.0, W));
+    std::swap(HX, W);
     c->launches += 3;
     return TDKS_OK;
   };
-  auto run = [&]() -> tdks_status {
-    const double zeroA[3] = {0.0, 0.0, 0.0};
-    TDKS_TRY(ortho(u, Wb));
-    TDKS_CUDA(cudaMemcpyAsync(u, Wb, nob, cudaMemcpyDeviceToDevice, c->stream));
+  // the input orbitals must be independent: their own overlap
+  {
+    std::vector<Z> S((size_t)nk * no * no), Cn((size_t)nk * no * no);
+    const tdks_status st = [&]() -> tdks_status {
+      TDKS_CUDA(f32 ? launch_gram<float>((const float2*)u, (const float2*)u, nk, no, np, c->dV, dM, c->stream)
+                    : launch_gram<double>((const double2*)u, (const double2*)u, nk, no, np, c->dV, dM, c->stream));
+      TDKS_CUDA(cudaMemcpyAsync(S.data(), dM, S.size() * sizeof(double2), cudaMemcpyDeviceToHost, c->stream));
+      TDKS_CUDA(cudaStreamSynchronize(c->stream));
+      for (int k = 0; k < nk; ++k)
+        if (!cholesky_inverse_h(&S[(size_t)k * no * no], no, &Cn[(size_t)k * no * no]))
+          return fail(TDKS_EINVAL, "tdks_ground_state: the orbitals are linearly dependent");
+      return TDKS_OK;
+    }();
+    if (st != TDKS_OK) { cleanup(); return st; }
+  }
+  auto free_blocks = [&](const void* X, const void* HX, void* (&fr)[2]) {   // the two blocks not in use
+    int n = 0;
+    for (void* bb : Bf)
+      if (bb != X && bb != HX && n < 2) fr[n++] = bb;
+  };
+  auto solve = [&]() -> tdks_status {
+    void* X = Bf[0];
+    void* HX = Bf[1];
+    void* P = Bf[2];
+    // initial block in P: the input orbitals, then seeded random buffer states; orthonormalised into X
+    {
+      std::vector<unsigned char> hb((size_t)(nb - no) * np * csz);
+      unsigned long long sd = 0x243F6A8885A308D3ULL;
+      for (size_t i2 = 0; i2 < (size_t)(nb - no) * np; ++i2) {
+        const double re = 2.0 * uniform01(sd) - 1.0, im = 2.0 * uniform01(sd) - 1.0;
+        if (f32) reinterpret_cast<float2*>(hb.data())[i2] = float2{(float)re, (float)im};
+        else reinterpret_cast<double2*>(hb.data())[i2] = double2{re, im};
+      }
+      for (int k = 0; k < nk; ++k) {
+        TDKS_CUDA(cudaMemcpyAsync(vec(P, k, 0), static_cast<unsigned char*>(u) + (size_t)k * no * np * csz,
+                                  (size_t)no * np * csz, cudaMemcpyDeviceToDevice, c->stream));
+        TDKS_CUDA(cudaMemcpyAsync(vec(P, k, no), hb.data(), hb.size(), cudaMemcpyHostToDevice, c->stream));
+      }
+      TDKS_CUDA(cudaStreamSynchronize(c->stream));
+    }
+    TDKS_TRY(ortho(P, X));
+    // the potential of the input density
     TDKS_TRY(density(c, u, c->d_rho));
     TDKS_TRY(hxc(c, c->d_rho, c->d_vhxc, u));
     TDKS_CUDA(cudaMemcpyAsync(d_vin, c->d_vhxc, (size_t)np * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    TDKS_CUDA(cudaMemcpyAsync(sib->d_vhxc, c->d_vhxc, (size_t)np * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    TDKS_TRY(ritz(X, HX, P));
+    // upper bound of the spectrum: the FD kinetic symbol (its largest value per axis 3.26 / h^2, the
+    // first-derivative term at most 2.09 |q| / h, plus |q|^2 / 2), the largest potential, ||V_NL||
+    double kin = 0.0;
+    for (int k = 0; k < nk; ++k) {
+      double kk = 0.0, q2 = 0.0;
+      for (int a = 0; a < 3; ++a) {
+        const double q = c->kpts[3 * k + a], h = c->grid.h[a];
+        kk += 3.26 / (h * h) + 2.09 * std::fabs(q) / h;
+        q2 += q * q;
+      }
+      kin = std::max(kin, kk + 0.5 * q2);
+    }
+    TDKS_CUDA(cudaMemcpyAsync(hvl.data(), c->d_vloc, (size_t)np * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     double resid = 0.0;
     int it = 0;
     for (it = 1; it <= max_iter; ++it) {
-      TDKS_TRY(set_step_potential(c, 1.0, nullptr, 0.0));
-      TDKS_TRY(orbital_kernel(c, 0, u, HU, zeroA, 0.0, nullptr, 1));            // H U
-      TDKS_CUDA(gram(u, HU, dM));                                               // M = U^H H U dV
-      TDKS_CUDA(basis(u, HU, dM, -tau, 1.0, tau, Wb));                          // W = U - tau (HU - U M)
-      const bool check = (it % 10 == 0) || it == max_iter;
-      if (check) {                                                              // R = HU - U M (in place)
-        TDKS_CUDA(basis(u, HU, dM, 1.0, 0.0, -1.0, HU));
-        TDKS_CUDA(gram(HU, HU, dS));
-        TDKS_CUDA(cudaMemcpyAsync(hS.data(), dS, nmat * sizeof(double2), cudaMemcpyDeviceToHost, c->stream));
-        TDKS_CUDA(cudaMemcpyAsync(hM.data(), dM, nmat * sizeof(double2), cudaMemcpyDeviceToHost, c->stream));
+      // bounds of the filter: damp [a, b] (a = the block's highest Ritz value), normalised at the lowest
+      TDKS_CUDA(cudaMemcpyAsync(hv.data(), sib->d_vhxc, (size_t)np * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      TDKS_CUDA(cudaStreamSynchronize(c->stream));
+      double vmax = -1e300;
+      for (int i2 = 0; i2 < np; ++i2) vmax = std::max(vmax, hvl[i2] + hv[i2]);
+      double elo = 1e300, ehi = -1e300;
+      for (int k = 0; k < nk; ++k) {
+        elo = std::min(elo, eig[(size_t)k * nb]);
+        ehi = std::max(ehi, eig[(size_t)k * nb + nb - 1]);
       }
-      c->launches += check ? 5 : 3;
-      if (check) {
+      const double b = kin + vmax + c->vnl_bound;
+      const double a = ehi;
+      if (!(b > a && a > elo)) return fail(TDKS_ECUDA, "tdks_ground_state: inconsistent spectral bounds");
+      const double ee = 0.5 * (b - a), cc = 0.5 * (b + a);
+      double sig = ee / (elo - cc);
+      const double sig1 = sig;
+      // Chebyshev filter of degree m (three-term recurrence, scaled so the lowest end stays of order 1):
+      // Y1 = (H - cc) X sig1 / ee;  Y_{j+1} = 2 sig' / ee (H - cc) Y_j - sig sig' Y_{j-1}.  The buffers
+      // rotate over the four blocks; HX (needed only by the first term) then holds H Y_j.
+      void* fr[2];
+      free_blocks(X, HX, fr);
+      void* prev = X;
+      void* cur = fr[0];
+      void* nxt = fr[1];
+      TDKS_CUDA(lincomb(HX, X, nullptr, sig1 / ee, -cc * sig1 / ee, 0.0, cur));
+      c->launches += 1;
+      for (int jj = 2; jj <= m; ++jj) {
+        const double sig2 = 1.0 / (2.0 / sig1 - sig);
+        TDKS_TRY(H(cur, HX));
+        TDKS_CUDA(lincomb(HX, cur, prev, 2.0 * sig2 / ee, -2.0 * cc * sig2 / ee, -sig * sig2, nxt));
+        c->launches += 1;
+        void* t = prev;
+        prev = cur;
+        cur = nxt;
+        nxt = t;
+        sig = sig2;
+      }
+      // orthonormalise the filtered block into a free block, then Rayleigh-Ritz
+      X = (prev != cur) ? prev : nxt;
+      TDKS_TRY(ortho(cur, X));
+      free_blocks(X, HX, fr);
+      P = fr[0];
+      TDKS_TRY(ritz(X, HX, P));
+      free_blocks(X, HX, fr);
+      P = fr[0];
+      // residual of the occupied Ritz pairs, R = HX - X diag(e)
+      {
+        std::vector<Z> D(nmat, Z(0.0, 0.0));
+        for (int k = 0; k < nk; ++k)
+          for (int n = 0; n < nb; ++n) D[(size_t)k * nb * nb + (size_t)n * nb + n] = eig[(size_t)k * nb + n];
+        TDKS_CUDA(cudaMemcpyAsync(dC, D.data(), nmat * sizeof(double2), cudaMemcpyHostToDevice, c->stream));
+        TDKS_CUDA(basis(X, HX, dC, 1.0, 0.0, -1.0, P));
+        TDKS_CUDA(gram(P, P, dM));
+        TDKS_CUDA(cudaMemcpyAsync(hM.data(), dM, nmat * sizeof(double2), cudaMemcpyDeviceToHost, c->stream));
         TDKS_CUDA(cudaStreamSynchronize(c->stream));
         double r2 = 0.0;
         for (int k = 0; k < nk; ++k)
-          for (int n = 0; n < no; ++n) r2 += hS[((size_t)k * no + n) * no + n].x;
+          for (int n = 0; n < no; ++n) r2 += hM[(size_t)k * nb * nb + (size_t)n * nb + n].real();
         resid = std::sqrt(r2 / (nk * no));
+        c->launches += 2;
       }
-      TDKS_TRY(ortho(Wb, u));                                                   // U = W L^{-H}
+      // the occupied states into u, their density and potential, mixing
+      for (int k = 0; k < nk; ++k)
+        TDKS_CUDA(cudaMemcpyAsync(static_cast<unsigned char*>(u) + (size_t)k * no * np * csz, vec(X, k, 0),
+                                  (size_t)no * np * csz, cudaMemcpyDeviceToDevice, c->stream));
       TDKS_TRY(density(c, u, c->d_rho));
-      TDKS_TRY(hxc(c, c->d_rho, c->d_vhxc, u));                                  // V_out
-      double dv = 0.0;
-      if (check) {
-        TDKS_CUDA(cudaMemcpyAsync(hv.data(), c->d_vhxc, (size_t)np * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-        TDKS_CUDA(cudaMemcpyAsync(hvin.data(), d_vin, (size_t)np * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-        TDKS_CUDA(cudaStreamSynchronize(c->stream));
-        double a2 = 0.0, b2 = 0.0;
-        for (int i = 0; i < np; ++i) { a2 += (hv[i] - hvin[i]) * (hv[i] - hvin[i]); b2 += hv[i] * hv[i]; }
-        dv = std::sqrt(a2 / std::max(b2, 1e-300));
-      }
+      TDKS_TRY(hxc(c, c->d_rho, c->d_vhxc, u));                                   // V_out
+      TDKS_CUDA(cudaMemcpyAsync(hv.data(), c->d_vhxc, (size_t)np * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      TDKS_CUDA(cudaMemcpyAsync(hvin.data(), d_vin, (size_t)np * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      TDKS_CUDA(cudaStreamSynchronize(c->stream));
+      double a2 = 0.0, b2 = 0.0;
+      for (int i2 = 0; i2 < np; ++i2) { a2 += (hv[i2] - hvin[i2]) * (hv[i2] - hvin[i2]); b2 += hv[i2] * hv[i2]; }
+      const double dv = std::sqrt(a2 / std::max(b2, 1e-300));
+      if (resid < tol && dv < tol) break;
       TDKS_CUDA(launch_mix_potential(d_vin, c->d_vhxc, np, mix, c->stream));
+      TDKS_CUDA(cudaMemcpyAsync(sib->d_vhxc, c->d_vhxc, (size_t)np * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
       c->launches += 1;
-      if (check && resid < tol && dv < tol) break;
     }
     // the ground state's own potential and reference density
     TDKS_TRY(density(c, u, c->d_rho));
@@ -1106,19 +1292,16 @@ tdks_status tdks_ground_state(tdks_ctx* c, void* u, int max_iter, double tol, do
     c->hist_count = 0;
     TDKS_TRY(hist_push(c, c->d_vhxc));
     if (out) {
-      std::vector<double> kw((size_t)nk);
-      TDKS_CUDA(cudaMemcpyAsync(kw.data(), c->d_kw, nk * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-      TDKS_CUDA(cudaStreamSynchronize(c->stream));
       double eb = 0.0;
       for (int k = 0; k < nk; ++k)
-        for (int n = 0; n < no; ++n) eb += 2.0 * kw[k] * hM[((size_t)k * no + n) * no + n].x;
+        for (int n = 0; n < no; ++n) eb += 2.0 * c->kw[k] * eig[(size_t)k * nb + n];
       out[0] = std::min(it, max_iter);
       out[1] = resid;
       out[2] = eb;
     }
     return TDKS_OK;
   };
-  const tdks_status st = run();
+  const tdks_status st = solve();
   cleanup();
   return st;
 }
@@ -1928,15 +2111,6 @@ tdks_status tdks_set_predictor(tdks_ctx* c, int mode, double threshold) {
   return TDKS_OK;
 }
 
-namespace {
-unsigned long long splitmix64(unsigned long long& x) {
-  unsigned long long z = (x += 0x9E3779B97F4A7C15ULL);
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
-  return z ^ (z >> 31);
-}
-double uniform01(unsigned long long& x) { return (splitmix64(x) >> 11) * (1.0 / 9007199254740992.0); }
-}  // namespace
 
 tdks_status tdks_nn_init(tdks_ctx* c, unsigned long long seed) {
   TDKS_TRY(check_ctx(c));

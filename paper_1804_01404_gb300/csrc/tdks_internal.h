@@ -291,6 +291,11 @@ cudaError_t launch_basis(const typename Cplx<T>::type* U, const typename Cplx<T>
                          int norb, int npts, double a, double c0, double b, typename Cplx<T>::type* out,
                          cudaStream_t s);
 cudaError_t launch_mix_potential(double* vin, double* vout, long long n, double mix, cudaStream_t s);
+// out = a A + b B + g C over n complex values (Cv may be NULL when g = 0)
+template <typename T>
+cudaError_t launch_lincomb3(const typename Cplx<T>::type* A, const typename Cplx<T>::type* B,
+                            const typename Cplx<T>::type* Cv, double a, double b, double g, long long n,
+                            typename Cplx<T>::type* out, cudaStream_t s);
 
 // TB-mBJ exchange (k_mbj.cu): V += v_x^mBJ[rho, tau~ of u]; c = c_fixed (> 0) or computed into *c_dev.
 // part: [nchunk][5][npts] doubles; partials / ticket: a grid_sum work area.  nlaunch: kernels launched.

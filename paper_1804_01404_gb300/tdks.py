@@ -341,11 +341,11 @@ class Context:
         _check(self.lib.tdks_set_field_table(self.ctx, tab.ctypes.data_as(C.POINTER(C.c_double)), len(tab),
                                              float(t0), float(dt_table)))
 
-    def ground_state(self, u, max_iter=5000, tol=1e-8, tau=0.0, mix=0.3):
-        """Self-consistent ground state into u (tdks_ground_state); returns (iterations, residual,
-        band energy)."""
+    def ground_state(self, u, max_iter=500, tol=1e-8, degree=0, mix=0.3):
+        """Self-consistent ground state into u (tdks_ground_state, Chebyshev-filtered subspace iteration
+        of the given filter degree, 0: 10); returns (iterations, residual, band energy)."""
         out = (C.c_double * 3)()
-        _check(self.lib.tdks_ground_state(self.ctx, _ptr(u, self.cdtype), int(max_iter), float(tol), float(tau),
+        _check(self.lib.tdks_ground_state(self.ctx, _ptr(u, self.cdtype), int(max_iter), float(tol), float(degree),
                                           float(mix), out))
         return int(out[0]), float(out[1]), float(out[2])
 
