@@ -415,6 +415,12 @@ def gpu_arm(args, rank, world, local_rank):
     host_in = u2.cpu().pin_memory()
     state = ctx2.get_state()
     host_out = torch.empty_like(host_in).pin_memory()
+    # every step's observables go to one of two pinned host blocks (tdks_copy_step_observables) and
+    # are unpacked on the host after the next step is queued, so the stream never waits for the host
+    ring = [torch.zeros(T.STEP_OBS_DOUBLES, dtype=torch.float64).pin_memory() for _ in range(2)]
+    evs = [torch.cuda.Event() for _ in range(2)]
+    cstream = ctx2.stream
+    obs_read = []
     u2.zero_()
     torch.cuda.synchronize()
     tic = time.perf_counter()
@@ -422,19 +428,27 @@ def gpu_arm(args, rank, world, local_rank):
     ctx2.set_state(state)
     for i in range(args.steps):
         ctx2.step(u2, tt, s.dt)
-        ctx2.read_step_observables()
+        ctx2.copy_step_observables(ring[i % 2])
+        evs[i % 2].record(cstream)
+        if i > 0:
+            evs[(i - 1) % 2].synchronize()
+            obs_read.append(ctx2.unpack_step_observables(ring[(i - 1) % 2]))
         tt += s.dt
     host_out.copy_(u2, non_blocking=True)
+    evs[(args.steps - 1) % 2].synchronize()
+    obs_read.append(ctx2.unpack_step_observables(ring[(args.steps - 1) % 2]))
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - tic
+    assert len(obs_read) == args.steps and all(np.isfinite(o["J"]).all() for o in obs_read)
     psi_bytes = psi0.nbytes
     state_bytes = len(state)
     e2e = {"value": world * args.steps / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": (psi_bytes + state_bytes) / args.steps,
-           "d2h_bytes_per_step": psi_bytes / args.steps + 10 * 8,
+           "d2h_bytes_per_step": psi_bytes / args.steps + T.STEP_OBS_DOUBLES * 8,
            "note": "a run resumed from host memory: psi and the context state of a checkpoint uploaded, psi "
-                   "downloaded once per K steps; J, dipole and the predictor misfit read back every step "
-                   "(synchronising); context and step graphs set up by a warm-up run before the timed region"}
+                   "downloaded once per K steps; J, dipole, misfit and fallback count of every step copied "
+                   "to pinned host memory and unpacked on the host one step later (the next step is queued "
+                   "first); context and step graphs set up by a warm-up run before the timed region"}
     ctx2.close()
 
     hpsi = None
@@ -609,6 +623,9 @@ def summary(line):
            "hpsi_cluster_frac_of_measured_hbm": g(line, "hpsi_cluster", "frac_of_measured_hbm"),
            "hpsi_cluster_stencil_frac_of_measured_hbm": g(line, "hpsi_cluster", "stencil_kernel_frac_of_measured_hbm"),
            "hpsi_cluster_ms": g(line, "hpsi_cluster", "ms_per_hpsi_phase"),
+           "taylor_step_cluster_frac_of_measured_hbm": g(line, "hpsi_cluster", "taylor_step", "frac_of_measured_hbm"),
+           "taylor_stage_stencil_frac_of_measured_hbm": g(line, "hpsi_cluster", "taylor_step",
+                                                          "stencil_stage_frac_of_measured_hbm"),
            "J_rel_err_vs_f64": line.get("J_rel_err_vs_f64"),
            "cpu_oracle_steps_per_s": g(line, "cpu_baseline", "value"), "cpu_cores": g(line, "cpu_baseline", "cores")}
     for name in ("learned", "cubic", "pc"):
@@ -708,6 +725,32 @@ def hpsi_cluster(dev, reps=10, norb=256):
            "stencil_kernel_ms": s_ms, "stencil_kernel_GBps": nbytes / (s_ms * 1e-3) / 1e9,
            "stencil_kernel_frac_of_measured_hbm": nbytes / (s_ms * 1e-3) / 1e9 / pk["hbm_gbs"],
            "stencil_kernel_traffic": measured_traffic("k_tile_f32_mode0")}
+    # the Taylor step of the same orbitals: four Horner stages v <- psi + (-i dt/m) H v, each the
+    # fused stencil (reads v and psi, writes the new v: 24 B per orbital-point) with the projections
+    # on the side stream and the nonlocal scatter -- hpsi as the propagator applies it
+    for _ in range(2):
+        ctx.taylor_step(u, s.dt)
+    torch.cuda.synchronize()
+    ctx.stats(reset=True)
+    ctx.profile(2)
+    e0.record(stream)
+    for _ in range(reps):
+        ctx.taylor_step(u, s.dt)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sts = ctx.stats(reset=True)
+    ctx.profile(False)
+    ctx.check()
+    tms = e0.elapsed_time(e1) / reps
+    stage_ms = sts["ms"]["stencil_kernel"] / max(1, sts["calls"]["stencil_kernel"])
+    tbytes = 4 * 1.5 * nbytes
+    res["taylor_step"] = {
+        "ms": tms, "bytes_per_step": tbytes, "GBps": tbytes / (tms * 1e-3) / 1e9,
+        "frac_of_measured_hbm": tbytes / (tms * 1e-3) / 1e9 / pk["hbm_gbs"],
+        "stencil_stage_ms": stage_ms, "stencil_stage_GBps": 1.5 * nbytes / (stage_ms * 1e-3) / 1e9,
+        "stencil_stage_frac_of_measured_hbm": 1.5 * nbytes / (stage_ms * 1e-3) / 1e9 / pk["hbm_gbs"],
+        "note": "4 Horner stages, 24 B per orbital-point each (read v and psi, write the new v); whole step "
+                "with projections and scatters, and the fused stencil kernel of one stage alone"}
     # density + Hockney Poisson (192^3 FFTs, FP64) + LDA exchange of the same orbitals
     ctx.stats(reset=True)
     for _ in range(3):

@@ -29,7 +29,8 @@
  *     allocated in tdks_init and released in tdks_destroy.
  *   - Every call is enqueued on the CUDA stream given to tdks_init and returns without waiting,
  *     except calls that return host values (tdks_observables, tdks_read_step_observables,
- *     tdks_check), which synchronise that stream.
+ *     tdks_check), which synchronise that stream (tdks_copy_step_observables is their
+ *     asynchronous counterpart).
  *   - A context is not thread-safe; use one context per host thread.
  *   - Errors are returned as tdks_status codes; tdks_last_error() gives a message (thread-local).
  *     No call throws across the ABI.
@@ -272,6 +273,21 @@ tdks_status tdks_step(tdks_ctx* ctx, void* u_dev, double t, double dt);
 /* Copy the observables written by the last tdks_step to the host (synchronises the stream).
  * J, dipole, n_elec, residual and fallbacks are filled; the other fields are set to 0. */
 tdks_status tdks_read_step_observables(tdks_ctx* ctx, tdks_obs* out);
+
+/* The same read without waiting, for callers that keep the stream busy while they read: enqueue on
+ * the context stream the copy of the step-observable block of the last tdks_step (first cell) into
+ * host_dst, TDKS_STEP_OBS_DOUBLES doubles owned by the caller:
+ *   [0..2] J, [3..5] dipole, [6] n_elec, [7] 0, [8] misfit of the predicted potential, [9] 0,
+ *   [10] fallbacks so far.
+ * host_dst must be page-locked for the copy to run asynchronously (pageable memory makes the CUDA
+ * runtime copy synchronously).  The block is valid once the stream has passed the copy (an event
+ * recorded after it, or any synchronising call); tdks_unpack_step_observables then fills a
+ * tdks_obs from it, exactly as tdks_read_step_observables would have.  Unpack blocks in the order
+ * they were copied (the fallback count feeds the context's launch counters).
+ * Errors: EINVAL for a NULL buffer or output. */
+#define TDKS_STEP_OBS_DOUBLES 11
+tdks_status tdks_copy_step_observables(tdks_ctx* ctx, double* host_dst);
+tdks_status tdks_unpack_step_observables(tdks_ctx* ctx, const double* host_src, tdks_obs* out);
 
 /* Compute all observables of u with A'(t) = Aprime, against the current rho0 and potential
  * (synchronises the stream): the current of Eq. (macro_current) including the nonlocal term, the

@@ -1979,31 +1979,60 @@ tdks_status tdks_ms_read(tdks_ctx* c, double* A_host, double* I_host) {
 }
 
 
-tdks_status tdks_read_step_observables(tdks_ctx* c, tdks_obs* o) {
-  TDKS_TRY(check_ctx(c));
-  if (!o) return fail(TDKS_EINVAL, "null output");
-  double* h = c->h_resid;
-  if (c->ncell == 1) {       // J, dipole, N, misfit, fallback count: one copy
-    TDKS_CUDA(cudaMemcpyAsync(h, c->d_step_obs, 11 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-  } else {
-    TDKS_CUDA(cudaMemcpyAsync(h, c->d_step_obs, 8 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    TDKS_CUDA(cudaMemcpyAsync(h + 8, c->d_resid, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-  }
-  TDKS_CUDA(cudaStreamSynchronize(c->stream));
-  const double r = h[8];
+namespace {
+
+// Enqueue the copy of the step-observable block of the first cell (J[3], dipole[3], n_elec, 0,
+// misfit, 0, fallback count) into h on the context stream.
+cudaError_t copy_step_obs(tdks_ctx* c, double* h) {
+  if (c->ncell == 1)         // J, dipole, N, misfit, fallback count: one copy
+    return cudaMemcpyAsync(h, c->d_step_obs, TDKS_STEP_OBS_DOUBLES * sizeof(double), cudaMemcpyDeviceToHost,
+                           c->stream);
+  cudaError_t e = cudaMemcpyAsync(h, c->d_step_obs, 8 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h + 8, c->d_resid, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  return e;
+}
+
+// Fill o from a copied block; fallbacks seen for the first time add the launches and phase calls of
+// the predictor-corrector body they ran to the context's counters.
+void unpack_step_obs(tdks_ctx* c, const double* h, tdks_obs* o) {
   const double fb = h[10];
   if (fb > c->fb_seen) {
     const long long n = (long long)(fb - c->fb_seen);
     c->launches += n * c->body_launches;
     for (int p = 0; p < TDKS_NPHASE; ++p) c->calls[p] += n * c->body_calls[p];
+    c->fb_seen = fb;
   }
-  c->fb_seen = fb;
-  c->fallbacks = fb;
+  if (fb > c->fallbacks) c->fallbacks = fb;
   std::memset(o, 0, sizeof(*o));
   for (int a = 0; a < 3; ++a) { o->J[a] = h[a]; o->dipole[a] = h[3 + a]; }
   o->n_elec = h[6];
-  o->residual = r;
-  o->fallbacks = c->fallbacks;
+  o->residual = h[8];
+  o->fallbacks = fb;
+}
+
+}  // namespace
+
+tdks_status tdks_read_step_observables(tdks_ctx* c, tdks_obs* o) {
+  TDKS_TRY(check_ctx(c));
+  if (!o) return fail(TDKS_EINVAL, "null output");
+  TDKS_CUDA(copy_step_obs(c, c->h_resid));
+  TDKS_CUDA(cudaStreamSynchronize(c->stream));
+  unpack_step_obs(c, c->h_resid, o);
+  return TDKS_OK;
+}
+
+tdks_status tdks_copy_step_observables(tdks_ctx* c, double* host_dst) {
+  TDKS_TRY(check_ctx(c));
+  if (!host_dst) return fail(TDKS_EINVAL, "null host buffer");
+  TDKS_CUDA(copy_step_obs(c, host_dst));
+  return TDKS_OK;
+}
+
+tdks_status tdks_unpack_step_observables(tdks_ctx* c, const double* host_src, tdks_obs* o) {
+  TDKS_TRY(check_ctx(c));
+  if (!host_src || !o) return fail(TDKS_EINVAL, "null argument");
+  unpack_step_obs(c, host_src, o);
   return TDKS_OK;
 }
 

@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(HERE, "libtdks.so")
 
 TDKS_F64, TDKS_F32 = 0, 1
 PRED_PC, PRED_EXTRAP, PRED_LEARNED = 0, 1, 2
+STEP_OBS_DOUBLES = 11        # doubles of one step-observable block (tdks_copy_step_observables)
 NN_NPARAMS = 9105
 FIELD_NONE, FIELD_STEP, FIELD_PULSE, FIELD_TABLE = 0, 1, 2, 3
 STATUS = {0: "TDKS_OK", 1: "TDKS_EINVAL", 2: "TDKS_ENOMEM", 3: "TDKS_ECUDA", 4: "TDKS_ETIMEOUT",
@@ -99,6 +100,8 @@ def load_library(path: str = LIB_PATH):
         "tdks_taylor_step": [vp, vp, d, _D3],
         "tdks_step": [vp, vp, d, d],
         "tdks_read_step_observables": [vp, C.POINTER(Obs)],
+        "tdks_copy_step_observables": [vp, vp],
+        "tdks_unpack_step_observables": [vp, vp, C.POINTER(Obs)],
         "tdks_observables": [vp, vp, _D3, vp, C.POINTER(Obs)],
         "tdks_check_options": [C.POINTER(Grid), i, i, C.POINTER(Options)],
         "tdks_get_grid_array": [vp, i, vp],
@@ -271,6 +274,14 @@ def _ptr(t, dtype=None):
     return C.c_void_p(t.data_ptr())
 
 
+def _host_obs_ptr(t):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.device.type == "cpu" and t.is_contiguous()
+            and t.dtype == torch.float64 and t.numel() >= STEP_OBS_DOUBLES):
+        raise ValueError(f"expected a contiguous CPU float64 tensor of >= {STEP_OBS_DOUBLES} values")
+    return C.c_void_p(t.data_ptr())
+
+
 class Context:
     """One propagation context (libtdks tdks_ctx) for a system description.
 
@@ -412,6 +423,18 @@ class Context:
     def read_step_observables(self):
         o = Obs()
         _check(self.lib.tdks_read_step_observables(self.ctx, C.byref(o)))
+        return o.as_dict()
+
+    def copy_step_observables(self, host_buf):
+        """Enqueue the copy of the last step's observable block (STEP_OBS_DOUBLES doubles) into
+        host_buf, a page-locked CPU float64 tensor, without waiting (tdks_copy_step_observables)."""
+        _check(self.lib.tdks_copy_step_observables(self.ctx, _host_obs_ptr(host_buf)))
+
+    def unpack_step_observables(self, host_buf):
+        """The observables of a block copied by copy_step_observables, once the stream has passed the
+        copy (tdks_unpack_step_observables)."""
+        o = Obs()
+        _check(self.lib.tdks_unpack_step_observables(self.ctx, _host_obs_ptr(host_buf), C.byref(o)))
         return o.as_dict()
 
     def observables(self, u, Aprime=None, rho=None):

@@ -55,7 +55,10 @@ def _oracle(name, threshold):
     return _ORACLE[key]
 
 
-def _gpu(name, threshold, precision):
+def _gpu(name, threshold, precision, pipelined=False):
+    """pipelined: read every step's observables as an application that keeps the stream busy does --
+    tdks_copy_step_observables into one of two pinned host blocks, unpacked after the next step has
+    been queued."""
     from paper_1804_01404_gb300 import tdks as T
     s = W.small_periodic(nsteps=NSTEPS)
     psi0 = W.initial_orbitals(s, 0)
@@ -66,14 +69,33 @@ def _gpu(name, threshold, precision):
     ctx.nn_params(_params())
     ctx.set_predictor(T.PRED_LEARNED if name == "learned" else T.PRED_EXTRAP, threshold)
     J, d, r = [], [], []
+    ring = [torch.zeros(T.STEP_OBS_DOUBLES, dtype=torch.float64).pin_memory() for _ in range(2)]
+    evs = [torch.cuda.Event() for _ in range(2)]
     t = 0.0
-    for _ in range(NSTEPS):
-        ctx.step(u, t, s.dt)
-        t += s.dt
-        o = ctx.read_step_observables()
+
+    def take(o):
         J.append(o["J"])
         d.append(o["dipole"])
         r.append(o["residual"])
+
+    for i in range(NSTEPS):
+        ctx.step(u, t, s.dt)
+        t += s.dt
+        if not pipelined:
+            o = ctx.read_step_observables()
+            take(o)
+            continue
+        ctx.copy_step_observables(ring[i % 2])
+        evs[i % 2].record(ctx.stream)
+        if i > 0:
+            evs[(i - 1) % 2].synchronize()
+            take(ctx.unpack_step_observables(ring[(i - 1) % 2]))
+    if pipelined:
+        evs[(NSTEPS - 1) % 2].synchronize()
+        o = ctx.unpack_step_observables(ring[(NSTEPS - 1) % 2])
+        take(o)
+        o2 = ctx.read_step_observables()
+        assert np.array_equal(o2["J"], o["J"]) and o2["fallbacks"] == o["fallbacks"]
     ctx.check()
     out = dict(J=np.array(J), d=np.array(d), misfit=np.array(r), fallbacks=o["fallbacks"],
                psi=u.cpu().numpy().astype(np.complex128), v=ctx.grid_array(1).cpu().numpy())
@@ -128,6 +150,24 @@ def test_learned_steps_with_rejections_match_the_oracle():
     assert np.linalg.norm(g["psi"] - psi) < 1e-10 * np.linalg.norm(psi)
     assert _rel(g["J"], rec["J"]) < 1e-10
     assert _rel(g["d"], rec["d"]) < 1e-10
+
+
+def test_pipelined_reads_of_learned_steps_with_rejections_match_the_oracle():
+    """The same run with every step's observables copied without waiting and unpacked one step later
+    (tdks_copy_step_observables / tdks_unpack_step_observables): the values and the fallback count of
+    every step are those of the oracle run."""
+    _, _, free = _oracle("learned", 1.0)
+    m = np.sort(free["misfit"][3:])
+    gaps = np.log(m[1:] / m[:-1])
+    j = int(np.argmax(gaps[len(m) // 4: 3 * len(m) // 4])) + len(m) // 4
+    thr = float(np.sqrt(m[j] * m[j + 1]))
+    psi, v, rec = _oracle("learned", thr)
+    g = _gpu("learned", thr, "f64", pipelined=True)
+    assert 0 < rec["rejected"] and g["fallbacks"] == rec["rejected"]
+    assert len(g["J"]) == NSTEPS
+    assert _rel(g["J"], rec["J"]) < 1e-10
+    assert _rel(g["d"], rec["d"]) < 1e-10
+    assert np.linalg.norm(g["psi"] - psi) < 1e-10 * np.linalg.norm(psi)
 
 
 def _tile_system():
