@@ -654,7 +654,8 @@ def cell_scheme(v):
     (tdks_cell_variant), with the tuning times of one Taylor launch of each."""
     if v is None:
         return None
-    names = ["two shared-memory copies", "one copy swept in place"]
+    names = ["two shared-memory copies", "one copy swept in place",
+             "two shared-memory copies, grid size built in (column segments unrolled)"]
     return {"in_use": names[v[0]], "tune_ms": {n: (t if t > 0 else None) for n, t in zip(names, v[1])}}
 
 

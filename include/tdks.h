@@ -44,7 +44,7 @@
 extern "C" {
 #endif
 
-#define TDKS_ABI_VERSION 2
+#define TDKS_ABI_VERSION 3
 
 typedef struct tdks_ctx tdks_ctx;
 
@@ -434,15 +434,17 @@ tdks_status tdks_tile_variant(tdks_ctx* ctx, int set, int* variant, float* tune_
  * form; no counterpart in the paper).  0 = two orbital copies in shared memory (or a global scratch
  * slice when two do not fit), one stage reading one and writing the other; 1 = one copy swept in
  * place plane by plane, one thread per (x, y) column, for planes of at most 448 points -- half the
- * shared memory, so two FP32 CTAs share an SM.  The arithmetic per grid point and per projection is
- * the same in both; the norm and current sums of an orbital are split over the CTA's warps and may
- * add in another order.  At tdks_init a cell context on which scheme 1 applies times one Taylor launch of each on
- * zeroed orbitals and keeps the faster.
- *   set       : -1 leaves the choice as it is; 0 or 1 forces that scheme.
+ * shared memory, so two FP32 CTAs share an SM; 2 = scheme 0 compiled for a fixed grid size (the
+ * periodic 20^3 and 16^3 grids), each thread's column segment unrolled over its planes.  The
+ * arithmetic per grid point and per projection is the same in all three; the norm and current sums
+ * of an orbital are split over the CTA's warps and may add in another order.  At tdks_init a cell
+ * context on which scheme 1 or 2 applies times one Taylor launch of each scheme that applies on
+ * zeroed orbitals and keeps the fastest.
+ *   set       : -1 leaves the choice as it is; 0, 1 or 2 forces that scheme.
  *   variant   : receives the scheme in use (may be NULL).
- *   tune_ms   : receives the 2 tuning times in ms, -1 where not timed (may be NULL).
- * Errors: EUNSUPPORTED if the context uses the tile kernels, or set = 1 where scheme 1 does not
- * apply; EINVAL for set outside -1..1. */
+ *   tune_ms   : receives the 3 tuning times in ms, -1 where not timed (may be NULL).
+ * Errors: EUNSUPPORTED if the context uses the tile kernels, or set = 1 or 2 where that scheme does
+ * not apply; EINVAL for set outside -1..2. */
 tdks_status tdks_cell_variant(tdks_ctx* ctx, int set, int* variant, float* tune_ms);
 
 /* Checkpoint and restart of the time stepping (no counterpart in the paper's formulation; the

@@ -176,30 +176,28 @@ __device__ __forceinline__ typename Cplx<T>::type zload(const OrbArgs<T>& a,
   return v[zz * a.pstride + col];
 }
 
-// Local part of (H v) at (x, y, z) of a column: diag*v + S + (-i) q.D, z-neighbours from window w.
+// Local part of (H v) at one point: diag*v + S + (-i) q.D.  nb(j) gives the in-plane neighbours
+// (j = 2(m-1): x+m, 2(m-1)+1: x-m, 8 + 2(m-1): y+m, 8 + 2(m-1)+1: y-m), wz(j) the z-values
+// u(z-4+j), j = 0..8.
 // WD (periodic cells): also return the per-axis first-derivative sums D1_a v in Dout[3], with one
 // accumulator per axis.  Otherwise each neighbour distance m uses one Laplacian and one derivative
 // coefficient, the axes entering through the fixed ratios (c2y = ry c2x, d1y = ty d1x, ...):
 //   S += c2x[m] (X_m + ry Y_m + rz Z_m),  q.D += d1x[m] (q_x X'_m + ty q_y Y'_m + tz q_z Z'_m)
 // (X_m: x+m plus x-m values, X'_m: their difference), which halves the coefficient registers.
-template <typename T, bool PER, bool WD>
-__device__ __forceinline__ typename Cplx<T>::type local_h(const OrbArgs<T>& a,
-                                                          const Column<T, PER>& c,
-                                                          const typename Cplx<T>::type* v,
-                                                          const typename Cplx<T>::type* w, int zb,
-                                                          T diag, const T* q,
-                                                          typename Cplx<T>::type* Dout) {
+template <typename T, bool PER, bool WD, typename NB, typename WZ>
+__device__ __forceinline__ typename Cplx<T>::type local_h_at(const OrbArgs<T>& a, NB nb, WZ wz, T diag,
+                                                             const T* q, typename Cplx<T>::type* Dout) {
   using C = typename Cplx<T>::type;
   using M = CM<T>;
   if (WD) {
     // independent accumulators per axis keep the FMA chains short
-    C Sx = M::fma(diag, w[4], C{0, 0}), Sy = C{0, 0}, Sz = C{0, 0};
+    C Sx = M::fma(diag, wz(4), C{0, 0}), Sy = C{0, 0}, Sz = C{0, 0};
     C Dx = C{0, 0}, Dy = C{0, 0}, Dz = C{0, 0};
 #pragma unroll
     for (int m = 1; m <= 4; ++m) {
-      const C xp = v[zb + c.ix[2 * (m - 1)]], xm = v[zb + c.ix[2 * (m - 1) + 1]];
-      const C yp = v[zb + c.iy[2 * (m - 1)]], ym = v[zb + c.iy[2 * (m - 1) + 1]];
-      const C zp = w[4 + m], zm = w[4 - m];
+      const C xp = nb(2 * (m - 1)), xm = nb(2 * (m - 1) + 1);
+      const C yp = nb(8 + 2 * (m - 1)), ym = nb(8 + 2 * (m - 1) + 1);
+      const C zp = wz(4 + m), zm = wz(4 - m);
       Sx = M::fma(a.c2x[m], M::add(xp, xm), Sx);
       Sy = M::fma(a.c2y[m], M::add(yp, ym), Sy);
       Sz = M::fma(a.c2z[m], M::add(zp, zm), Sz);
@@ -212,14 +210,14 @@ __device__ __forceinline__ typename Cplx<T>::type local_h(const OrbArgs<T>& a,
     Dout[0] = Dx; Dout[1] = Dy; Dout[2] = Dz;
     return C{S.x + D.y, S.y - D.x};   // + (-i) q.D
   }
-  C S = M::fma(diag, w[4], C{0, 0});
+  C S = M::fma(diag, wz(4), C{0, 0});
   C D = C{0, 0};
   const T qy = q[1] * a.ty, qz = q[2] * a.tz;
 #pragma unroll
   for (int m = 1; m <= 4; ++m) {
-    const C xp = v[zb + c.ix[2 * (m - 1)]], xm = v[zb + c.ix[2 * (m - 1) + 1]];
-    const C yp = v[zb + c.iy[2 * (m - 1)]], ym = v[zb + c.iy[2 * (m - 1) + 1]];
-    const C zp = w[4 + m], zm = w[4 - m];
+    const C xp = nb(2 * (m - 1)), xm = nb(2 * (m - 1) + 1);
+    const C yp = nb(8 + 2 * (m - 1)), ym = nb(8 + 2 * (m - 1) + 1);
+    const C zp = wz(4 + m), zm = wz(4 - m);
     S = M::fma(a.c2x[m], M::fma(a.rz, M::add(zp, zm), M::fma(a.ry, M::add(yp, ym), M::add(xp, xm))), S);
     if (PER)
       D = M::fma(a.d1x[m - 1],
@@ -227,6 +225,121 @@ __device__ __forceinline__ typename Cplx<T>::type local_h(const OrbArgs<T>& a,
   }
   if (PER) S = C{S.x + D.y, S.y - D.x};   // + (-i) q.D
   return S;
+}
+
+// local_h_at for a column: in-plane neighbours at the column's precomputed offsets in plane zb,
+// z-values from the window w.
+template <typename T, bool PER, bool WD>
+__device__ __forceinline__ typename Cplx<T>::type local_h(const OrbArgs<T>& a,
+                                                          const Column<T, PER>& c,
+                                                          const typename Cplx<T>::type* v,
+                                                          const typename Cplx<T>::type* w, int zb,
+                                                          T diag, const T* q,
+                                                          typename Cplx<T>::type* Dout) {
+  return local_h_at<T, PER, WD>(
+      a, [&](int j) { return v[zb + (j < 8 ? c.ix[j] : c.iy[j - 8])]; }, [&](int j) { return w[j]; }, diag, q,
+      Dout);
+}
+
+// ------------------------------------------------------------------ fixed cell geometries
+// Periodic cells whose size is a template parameter (GEOM 1: 20^3, GEOM 2: 16^3; 0: any size).  A
+// thread's column segment is unrolled over its ZL planes: the z window rotates by renaming registers,
+// and every shared-memory access of the segment is one of 18 per-thread base addresses plus a
+// compile-time plane offset, so the loads and stores need no address arithmetic.
+template <int GEOM> struct Geom;
+template <> struct Geom<1> { static constexpr int NX = 20, NY = 20, NZ = 20; };
+template <> struct Geom<2> { static constexpr int NX = 16, NY = 16, NZ = 16; };
+
+// the column split of cell_split for this geometry
+template <typename T, int GEOM>
+struct GeomT {
+  static constexpr int NX = Geom<GEOM>::NX, NY = Geom<GEOM>::NY, NZ = Geom<GEOM>::NZ, NXY = NX * NY;
+  static constexpr int S0 = kNTof<T>() / NXY;
+  static constexpr int S = S0 < 1 ? 1 : (S0 > NZ ? NZ : S0);
+  static constexpr int ZL = (NZ + S - 1) / S;
+  static constexpr int NSEG = (NZ + ZL - 1) / ZL;
+};
+
+__device__ __forceinline__ float2 lds_c(unsigned addr, float) {
+  float2 r;
+  asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(r.x), "=f"(r.y) : "r"(addr));
+  return r;
+}
+__device__ __forceinline__ double2 lds_c(unsigned addr, double) {
+  double2 r;
+  asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(r.x), "=d"(r.y) : "r"(addr));
+  return r;
+}
+__device__ __forceinline__ void sts_c(unsigned addr, float2 v) {
+  asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(v.x), "f"(v.y));
+}
+__device__ __forceinline__ void sts_c(unsigned addr, double2 v) {
+  asm volatile("st.shared.v2.f64 [%0], {%1, %2};" ::"r"(addr), "d"(v.x), "d"(v.y));
+}
+
+// One column segment of a Taylor stage (MODE 1: psi + (-i coef) H v) or of H v (MODE 0) for a fixed
+// geometry: reads the shared-memory vector at byte address sv, writes the next one at sn.  ACC: also
+// add |u|^2 and Im(conj(u) D1_a u) of the input to os (the first stage of OBS 2).
+template <typename T, int GEOM, int MODE, bool ACC>
+__device__ __forceinline__ void fixed_column(const OrbArgs<T>& a, int item, unsigned sv, unsigned sn,
+                                             const T* __restrict__ Vc,
+                                             const typename Cplx<T>::type* __restrict__ psi, T diag0,
+                                             const T* q, T coef, T os[5]) {
+  using C = typename Cplx<T>::type;
+  using M = CM<T>;
+  using G = GeomT<T, GEOM>;
+  constexpr int NX = G::NX, NY = G::NY, NZ = G::NZ, NXY = G::NXY, ZL = G::ZL;
+  constexpr bool RAGGED = (NZ % ZL) != 0;
+  constexpr unsigned CB = sizeof(C), PB = NXY * sizeof(C);   // bytes per point, per plane
+  const int col = item % NXY, seg = item / NXY;
+  const int y = col / NX, x = col - y * NX;
+  const int z0 = seg * ZL;
+  const unsigned p0 = (unsigned)(z0 * NXY) * CB;
+  unsigned nbA[16];                                  // plane z0: x+-m, y+-m (periodic images)
+#pragma unroll
+  for (int m = 1; m <= 4; ++m) {
+    const int xp = x + m - (x + m >= NX ? NX : 0), xm = x - m + (x - m < 0 ? NX : 0);
+    const int yp = y + m - (y + m >= NY ? NY : 0), ym = y - m + (y - m < 0 ? NY : 0);
+    nbA[2 * (m - 1)] = sv + p0 + (unsigned)(y * NX + xp) * CB;
+    nbA[2 * (m - 1) + 1] = sv + p0 + (unsigned)(y * NX + xm) * CB;
+    nbA[8 + 2 * (m - 1)] = sv + p0 + (unsigned)(yp * NX + x) * CB;
+    nbA[8 + 2 * (m - 1) + 1] = sv + p0 + (unsigned)(ym * NX + x) * CB;
+  }
+  const unsigned cA = sv + p0 + (unsigned)col * CB, oA = sn + p0 + (unsigned)col * CB;
+  C w[9];                                            // plane z0 + k - 4 + j in w[(k + j) % 9]
+#pragma unroll
+  for (int j = 0; j < 9; ++j) {
+    int zz = z0 - 4 + j;
+    zz += zz < 0 ? NZ : 0;
+    zz -= zz >= NZ ? NZ : 0;
+    w[j] = lds_c(sv + (unsigned)(zz * NXY + col) * CB, T());
+  }
+  const T* Vp = Vc + z0 * NXY + col;
+  const C* Pp = psi + z0 * NXY + col;
+  const int len = NZ - z0;
+#pragma unroll
+  for (int k = 0; k < ZL; ++k) {
+    if (RAGGED && k >= len) break;
+    const T diag = diag0 + Vp[k * NXY];
+    C Dd[3];
+    const C hv = local_h_at<T, true, ACC>(
+        a, [&](int j) { return lds_c(nbA[j] + (unsigned)k * PB, T()); }, [&](int j) { return w[(k + j) % 9]; },
+        diag, q, Dd);
+    if (ACC) {                                       // |u|^2 and Im(conj(u) D1_a u)
+      const C u0 = w[(k + 4) % 9];
+      os[0] += u0.x * u0.x + u0.y * u0.y;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) os[1 + d] += u0.x * Dd[d].y - u0.y * Dd[d].x;
+    }
+    C r;
+    if (MODE == 1) r = M::fma(coef, C{hv.y, -hv.x}, Pp[k * NXY]);   // psi + (-i coef) H v
+    else r = hv;
+    sts_c(oA + (unsigned)k * PB, r);
+    if (k < ZL - 1) {                                // plane z + 5 replaces plane z - 4
+      const bool wrap = z0 + k + 5 >= NZ;
+      w[k % 9] = lds_c(cA + (unsigned)(k + 5) * PB - (wrap ? (unsigned)NZ * PB : 0u), T());
+    }
+  }
 }
 
 // Nonlocal value at sphere point s: sum over its entries of conj(ph_i) sum_p beta_ip ec_ap.
@@ -392,10 +505,11 @@ __device__ __forceinline__ void nonlocal_current(const OrbArgs<T>& a, const type
 // OBS (MODE 1): 0 none; 1 norm and current of the propagated orbital, in an extra pass after the
 // last stage; 2 norm and current of the input orbital, accumulated during the first stage from the
 // per-axis derivative sums that stage forms anyway (no extra pass).  MODE 2 always uses 1.
-template <typename T, int MODE, bool PER, bool DBUF, int OBS, bool IP>
+template <typename T, int MODE, bool PER, bool DBUF, int OBS, bool IP, int GEOM = 0>
 __global__ void __launch_bounds__(kMaxThreads<T, IP>(), kMinBlocks<T, IP>())
     k_cell(OrbArgs<T> a, typename Cplx<T>::type* scratch) {
   static_assert(!IP || (MODE == 1 && !DBUF), "the in-place sweep serves the Taylor stages with one buffer");
+  static_assert(GEOM == 0 || (PER && DBUF && !IP && MODE != 2), "fixed geometries: periodic, two copies");
   using C = typename Cplx<T>::type;
   using M = CM<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -546,6 +660,11 @@ __global__ void __launch_bounds__(kMaxThreads<T, IP>(), kMinBlocks<T, IP>())
           __syncthreads();                      // every thread has read input plane z
           if (act) L.v[zb + col] = r;
         }
+      } else if constexpr (GEOM != 0) {
+        const unsigned sv = (unsigned)__cvta_generic_to_shared(L.v), sn = (unsigned)__cvta_generic_to_shared(L.nxt);
+#pragma unroll 1
+        for (int item = threadIdx.x; item < nitems; item += blockDim.x)
+          fixed_column<T, GEOM, MODE, ACC && PER>(a, item, sv, sn, Vc, psi, diag0, q, coef, os);
       } else {
 #pragma unroll 1
         for (int item = threadIdx.x; item < nitems; item += blockDim.x) {
@@ -688,10 +807,10 @@ __global__ void __launch_bounds__(kMaxThreads<T, IP>(), kMinBlocks<T, IP>())
   reduce_obs<T>(os, qo, a.dV, s_jnl, red, a.obs + (size_t)orb * 8);
 }
 
-template <typename T, int MODE, bool PER, bool DBUF, int OBS, bool IP = false>
+template <typename T, int MODE, bool PER, bool DBUF, int OBS, bool IP = false, int GEOM = 0>
 cudaError_t launch_cell(const OrbArgs<T>& a, typename Cplx<T>::type* scratch, size_t smem, int nt,
                         cudaStream_t s) {
-  auto kern = k_cell<T, MODE, PER, DBUF, OBS, IP>;
+  auto kern = k_cell<T, MODE, PER, DBUF, OBS, IP, GEOM>;
   // Shared-memory carveout: just enough shared memory for the CTAs that can be resident (registers,
   // threads and the footprint allow), the rest of the unified storage left as L1 for the reads that
   // stay global (the input orbital of every stage, the potential, the projector tables).  Computed
@@ -734,6 +853,36 @@ cudaError_t dispatch(const OrbArgs<T>& a, typename Cplx<T>::type* scratch, cudaS
                 : launch_cell<T, MODE, true, false, OBS>(a, scratch, smem, nt, s);
   return dbuf ? launch_cell<T, MODE, false, true, OBS>(a, scratch, smem, nt, s)
               : launch_cell<T, MODE, false, false, OBS>(a, scratch, smem, nt, s);
+}
+
+// The built-in geometry (1 or 2) of a's grid for the Taylor stages of cell_variant 2, or 0: periodic,
+// planes unpadded, two shared-memory copies, the column split of cell_split.
+template <typename T, int GEOM>
+bool geom_is(const OrbArgs<T>& a) {
+  using G = GeomT<T, GEOM>;
+  return a.periodic && a.nx == G::NX && a.ny == G::NY && a.nz == G::NZ && a.pstride == G::NXY &&
+         a.zlen == G::ZL && a.nseg == G::NSEG &&
+         cell_smem_bytes<T>(a.nz, a.pstride, a.nsph, a.natom, true) <= kSmemLimit;
+}
+
+template <typename T>
+int cell_geom(const OrbArgs<T>& a) {
+  if (geom_is<T, 1>(a)) return 1;
+  if (geom_is<T, 2>(a)) return 2;
+  return 0;
+}
+
+// Taylor stages with a built-in geometry (cell_variant 2).
+template <typename T, int OBS>
+cudaError_t dispatch_geom(const OrbArgs<T>& a, cudaStream_t s) {
+  const int g = cell_geom<T>(a);
+  if (g == 0) return cudaErrorInvalidValue;
+  const size_t smem = cell_smem_bytes<T>(a.nz, a.pstride, a.nsph, a.natom, true);
+  const int items = a.nx * a.ny * a.nseg;
+  int nt = ((items + 31) / 32) * 32;
+  if (nt > kNTof<T>()) nt = kNTof<T>();
+  return g == 1 ? launch_cell<T, 1, true, true, OBS, false, 1>(a, nullptr, smem, nt, s)
+                : launch_cell<T, 1, true, true, OBS, false, 2>(a, nullptr, smem, nt, s);
 }
 
 // Taylor stages with the in-place sweep (cell_variant 1).
@@ -782,12 +931,26 @@ cudaError_t launch_smem_orbital(const OrbArgs<T>& a, int mode, typename Cplx<T>:
       if (!a.obs) return dispatch_ip<T, 0>(a, s);
       return a.obs_at_start ? dispatch_ip<T, 2>(a, s) : dispatch_ip<T, 1>(a, s);
     }
+    if (a.cell_variant == 2) {
+      if (!a.obs) return dispatch_geom<T, 0>(a, s);
+      return a.obs_at_start ? dispatch_geom<T, 2>(a, s) : dispatch_geom<T, 1>(a, s);
+    }
     if (!a.obs) return dispatch<T, 1, 0>(a, scratch, s);
     return a.obs_at_start ? dispatch<T, 1, 2>(a, scratch, s) : dispatch<T, 1, 1>(a, scratch, s);
   }
   return dispatch<T, 2, 1>(a, scratch, s);
 }
 
+template <typename T>
+bool smem_orbital_geom_ok(int nx, int ny, int nz, int pstride, int nsph, int natom, int periodic, int nseg, int zlen) {
+  OrbArgs<T> a{};
+  a.nx = nx; a.ny = ny; a.nz = nz; a.pstride = pstride; a.nsph = nsph; a.natom = natom;
+  a.periodic = periodic; a.nseg = nseg; a.zlen = zlen;
+  return cell_geom<T>(a) != 0;
+}
+
+template bool smem_orbital_geom_ok<float>(int, int, int, int, int, int, int, int, int);
+template bool smem_orbital_geom_ok<double>(int, int, int, int, int, int, int, int, int);
 template bool smem_orbital_ip_ok<float>(int, int, int, int, int, int, int);
 template bool smem_orbital_ip_ok<double>(int, int, int, int, int, int, int);
 template bool smem_orbital_fits<float>(int, int, int, int);

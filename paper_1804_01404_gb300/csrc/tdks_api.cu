@@ -108,10 +108,11 @@ struct tdks_ctx {
   int stop_after = -1;              // timeout test: planes the tile producer issues (-1: all)
   float tile_ms[2][kTileVariants] = {{-1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f},
                                      {-1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f}};
-  int cell_variant = 0;          // Taylor launches of the cell kernels: 0 two buffers, 1 in-place sweep
+  int cell_variant = 0;          // Taylor launches of the cell kernels: 0 two buffers, 1 in-place sweep,
+                                 // 2 two buffers with the grid size built in
   cudaStream_t side = nullptr;   // tile path: the projections run here beside the stencil
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-  float cell_ms[2] = {-1.f, -1.f};  // tuning time of one Taylor launch per variant (-1: not available)
+  float cell_ms[3] = {-1.f, -1.f, -1.f};  // tuning time of one Taylor launch per variant (-1: not available)
   void *d_bufA = nullptr, *d_bufB = nullptr, *d_ec = nullptr;
   int* d_err = nullptr;
   bool have_rho0 = false, have_potential = false;
@@ -658,14 +659,27 @@ bool cell_ip_ok(const tdks_ctx* c) {
                     : smem_orbital_ip_ok<double>(n[0], n[1], n[2], c->pstride, c->nsph, c->natom, c->grid.periodic));
 }
 
-// Times one Taylor launch of each cell-kernel buffer scheme on zero orbitals -- up to 1216 of them
-// (eight waves of one CTA per SM) -- and keeps the faster scheme.  The launch is the corrector's:
+bool cell_geom_ok(const tdks_ctx* c) {
+  const int* n = c->grid.n;
+  return !c->tiled &&
+         (is_f32(c) ? smem_orbital_geom_ok<float>(n[0], n[1], n[2], c->pstride, c->nsph, c->natom, c->grid.periodic,
+                                                  c->nseg, c->zlen)
+                    : smem_orbital_geom_ok<double>(n[0], n[1], n[2], c->pstride, c->nsph, c->natom,
+                                                   c->grid.periodic, c->nseg, c->zlen));
+}
+
+bool cell_variant_ok(const tdks_ctx* c, int v) {
+  return v == 0 ? !c->tiled : (v == 1 ? cell_ip_ok(c) : cell_geom_ok(c));
+}
+
+// Times one Taylor launch of each cell-kernel scheme that applies on zero orbitals -- up to 1216 of
+// them (eight waves of one CTA per SM) -- and keeps the fastest.  The launch is the corrector's:
 // four Horner stages with the per-orbital observables of the context's choice (input or output
 // state), no orbital or density output.
 tdks_status tune_cell(tdks_ctx* c) {
   c->cell_variant = 0;
-  c->cell_ms[0] = c->cell_ms[1] = -1.f;
-  if (!cell_ip_ok(c)) return TDKS_OK;
+  c->cell_ms[0] = c->cell_ms[1] = c->cell_ms[2] = -1.f;
+  if (!cell_ip_ok(c) && !cell_geom_ok(c)) return TDKS_OK;
   const int nsub = std::min(c->ncell * c->nk * c->norb, 1216);
   const size_t csz = is_f32(c) ? sizeof(float2) : sizeof(double2);
   void* buf = nullptr;
@@ -678,7 +692,8 @@ tdks_status tune_cell(tdks_ctx* c) {
   if (err == cudaSuccess) err = cudaEventCreate(&e0);
   if (err == cudaSuccess) err = cudaEventCreate(&e1);
   float best = 0.f;
-  for (int v = 0; v < 2 && err == cudaSuccess; ++v) {
+  for (int v = 0; v < 3 && err == cudaSuccess; ++v) {
+    if (!cell_variant_ok(c, v)) continue;
     auto run = [&]() -> cudaError_t {
       if (is_f32(c)) {
         auto a = make_args<float>(c, buf, buf, c->d_v32, nullptr, 0.02, nullptr, 0);
@@ -2327,13 +2342,17 @@ tdks_status tdks_tile_variant(tdks_ctx* c, int set, int* variant, float* tune_ms
 
 tdks_status tdks_cell_variant(tdks_ctx* c, int set, int* variant, float* tune_ms) {
   TDKS_TRY(check_ctx(c));
-  if (set < -1 || set > 1) return fail(TDKS_EINVAL, "cell variant outside -1..1");
+  if (set < -1 || set > 2) return fail(TDKS_EINVAL, "cell variant outside -1..2");
   if (c->tiled) return fail(TDKS_EUNSUPPORTED, "this context uses the tile kernels");
   if (set == 1 && !cell_ip_ok(c))
     return fail(TDKS_EUNSUPPORTED, "the in-place sweep needs nx * ny <= 448 and one orbital copy in shared memory");
+  if (set == 2 && !cell_geom_ok(c))
+    return fail(TDKS_EUNSUPPORTED, "the built-in geometries are the periodic 20^3 and 16^3 grids with two "
+                                   "orbital copies in shared memory");
   if (set >= 0) c->cell_variant = set;
   if (variant) *variant = c->cell_variant;
-  if (tune_ms) { tune_ms[0] = c->cell_ms[0]; tune_ms[1] = c->cell_ms[1]; }
+  if (tune_ms)
+    for (int v = 0; v < 3; ++v) tune_ms[v] = c->cell_ms[v];
   return TDKS_OK;
 }
 

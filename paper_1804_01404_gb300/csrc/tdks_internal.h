@@ -108,7 +108,8 @@ struct OrbArgs {
   long long vstride;        // offset of a cell's potential (0: one potential shared by all)
   const double* Ap_cell;    // nullable: [ncell][3] A' per cell, replaces Ap
   const double* Ap_obs_cell;// nullable: [ncell][3], replaces Ap_obs
-  int cell_variant;         // Taylor stages: 0 two buffers, 1 one buffer swept in place
+  int cell_variant;         // Taylor stages: 0 two buffers, 1 one buffer swept in place, 2 two
+                            // buffers with the grid size fixed at compile time (smem_orbital_geom_ok)
 };
 
 // Orbital kernels (k_orbital.cu)
@@ -125,6 +126,10 @@ template <typename T>
 bool smem_orbital_needs_scratch(int nz, int pstride, int nsph, int natom);
 template <typename T>
 bool smem_orbital_ip_ok(int nx, int ny, int nz, int pstride, int nsph, int natom, int periodic);
+// Mode 1 with a.cell_variant = 2: a periodic grid of a size built into the kernels (20^3, 16^3)
+template <typename T>
+bool smem_orbital_geom_ok(int nx, int ny, int nz, int pstride, int nsph, int natom, int periodic, int nseg,
+                          int zlen);
 // column segments of the cell kernels; elem_bytes = bytes of one complex value (8: FP32, 16: FP64)
 void cell_split(int nx, int ny, int nz, int elem_bytes, int* nseg, int* zlen);
 

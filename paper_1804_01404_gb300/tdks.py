@@ -534,11 +534,11 @@ class Context:
 
     def cell_variant(self, set=-1):
         """Buffer scheme of the cell kernels' Taylor launches (tdks_cell_variant): returns (scheme in
-        use, tuning ms [two buffers, in-place sweep])."""
+        use, tuning ms [two buffers, in-place sweep, two buffers with the grid size built in])."""
         v = C.c_int()
-        ms = (C.c_float * 2)()
+        ms = (C.c_float * 3)()
         _check(self.lib.tdks_cell_variant(self.ctx, int(set), C.byref(v), ms))
-        return v.value, [float(ms[0]), float(ms[1])]
+        return v.value, [float(x) for x in ms]
 
     def get_state(self):
         """Checkpoint of the time-stepping state (tdks_get_state) as a numpy uint8 array."""

@@ -1,5 +1,6 @@
-"""The two buffer schemes of the shared-memory cell kernels' Taylor launches (tdks_cell_variant):
-0 = two orbital copies, 1 = one copy swept in place plane by plane.
+"""The buffer schemes of the shared-memory cell kernels' Taylor launches (tdks_cell_variant):
+0 = two orbital copies, 1 = one copy swept in place plane by plane, 2 = scheme 0 compiled for the
+periodic 20^3 and 16^3 grids (column segments unrolled over their planes).
 
 Each scheme is checked against the oracle's 4th-order Taylor step (Eq. taylor) and predictor-corrector
 steps, on periodic and isolated grids, in FP64 and FP32, including the smallest allowed z extent
@@ -151,19 +152,98 @@ def test_multiscale_in_place_scheme(precision, tol):
 
 def test_scheme_selection_and_errors():
     from paper_1804_01404_gb300.tdks import Context, TdksError
-    s = SYSTEMS["diamond-2k"]
+    s = SYSTEMS["diamond-2k"]                       # periodic 20^3: all three schemes apply
     ctx = Context(s, precision="f32")
     v, ms = ctx.cell_variant()
-    assert v in (0, 1) and ms[0] > 0 and ms[1] > 0      # both timed at init; the faster is kept
+    assert v in (0, 1, 2) and min(ms) > 0          # all timed at init; the fastest is kept
     assert ms[v] == min(ms)
     with pytest.raises(TdksError):
+        ctx.cell_variant(3)
+    ctx.close()
+    t = SYSTEMS["tiny-periodic"]                    # 6 x 7 x 5: no built-in geometry
+    ctx = Context(t, precision="f64")
+    v, ms = ctx.cell_variant()
+    assert v in (0, 1) and ms[2] == -1.0
+    with pytest.raises(TdksError) as ei:
         ctx.cell_variant(2)
+    assert "built-in" in str(ei.value)
     ctx.close()
     big = W.isolated_cluster(n=22, natom=4, norb=2, radius=3.8)      # 22 x 22 = 484 columns
     ctx = Context(big, precision="f32")
     v, ms = ctx.cell_variant()
-    assert v == 0 and ms == [-1.0, -1.0]
+    assert v == 0 and ms == [-1.0, -1.0, -1.0]
     with pytest.raises(TdksError) as ei:
         ctx.cell_variant(1)
     assert "in-place" in str(ei.value)
     ctx.close()
+
+
+GEOM_SYSTEMS = {"diamond-20^3": SYSTEMS["diamond-2k"], "periodic-16^3": W.small_periodic()}
+
+
+@pytest.mark.parametrize("name,precision,tol", [("diamond-20^3", "f32", 2e-5), ("periodic-16^3", "f32", 2e-5),
+                                                ("periodic-16^3", "f64", 1e-12)])
+def test_taylor_step_built_in_geometry(name, precision, tol):
+    """Scheme 2 on the built-in grids (FP32 at 16^3: column segments of 6, 6 and 4 planes) against
+    the oracle's Taylor step, and against scheme 0, whose arithmetic it repeats point by point.  (Two
+    FP64 copies of a 20^3 orbital do not fit in shared memory: scheme 2 is refused there.)"""
+    from paper_1804_01404_gb300.tdks import Context, TdksError
+    s = GEOM_SYSTEMS[name]
+    if name == "diamond-20^3":
+        c64 = Context(s, precision="f64")
+        assert c64.cell_variant()[1][2] == -1.0
+        with pytest.raises(TdksError):
+            c64.cell_variant(2)
+        c64.close()
+    psi = W.initial_orbitals(s, 4)
+    Ap = np.array([0.02, -0.01, 0.015])
+    tabs = O.projector_tables(s)
+    V = O.local_potential(s) + O.hxc(s, O.density(s, psi))
+    out = []
+    for scheme in (0, 2):
+        ctx = Context(s, precision=precision)
+        ctx.cell_variant(scheme)
+        assert ctx.cell_variant()[0] == scheme
+        u = _dev(psi, precision)
+        ctx.update_potential(u)
+        ctx.taylor_step(u, 0.02, Ap)
+        ctx.check()
+        got = u.cpu().numpy()
+        out.append(got)
+        for k in range(s.nk):
+            ref = O.taylor4(s, tabs, V, np.asarray(s.kpts[k]) + Ap, psi[k], 0.02)
+            assert _rel(got[k].astype(np.complex128), ref) < tol, (scheme, k)
+        ctx.close()
+    assert _rel(out[1].astype(np.complex128), out[0].astype(np.complex128)) < (1e-14 if precision == "f64" else 1e-6)
+
+
+@pytest.mark.parametrize("at_start", [False, True])
+def test_pc_steps_built_in_geometry(at_start):
+    """Five predictor-corrector steps (FP64) of the small periodic cell with scheme 2: orbitals, J(t)
+    and d(t) against the oracle, with the observables from the end-of-step pass or from the first
+    stage."""
+    from paper_1804_01404_gb300.tdks import Context
+    s = GEOM_SYSTEMS["periodic-16^3"]
+    psi0 = W.initial_orbitals(s, 5)
+    n = 5
+    ref, _, hist = O.run(s, psi0, n)
+    ctx = Context(s, precision="f64", obs_at_start=at_start)
+    ctx.cell_variant(2)
+    u = _dev(psi0, "f64")
+    ctx.update_potential(u)
+    J, d = [], []
+    t = 0.0
+    for _ in range(n):
+        ctx.step(u, t, s.dt)
+        t += s.dt
+        o = ctx.read_step_observables()
+        J.append(o["J"])
+        d.append(o["dipole"])
+    ctx.check()
+    J, d = np.array(J), np.array(d)
+    assert _rel(u.cpu().numpy(), ref) < 1e-11
+    Jref, dref = hist["J"], hist["d"]
+    if at_start:       # step n reports the state it started from: the oracle's record of step n-1
+        J, Jref, d, dref = J[1:], Jref[:-1], d[1:], dref[:-1]
+    assert np.max(np.abs(d - dref)) <= 1e-10 * max(np.max(np.abs(dref)), 1e-30)
+    assert np.max(np.abs(J - Jref)) < 1e-10 * np.max(np.abs(Jref))
