@@ -73,7 +73,7 @@ struct Smem {
 };
 
 template <typename T>
-inline size_t cell_smem_bytes(int nz, int pstride, int nsph, int natom, bool dbuf) {
+__host__ __device__ inline size_t cell_smem_bytes(int nz, int pstride, int nsph, int natom, bool dbuf) {
   using C = typename Cplx<T>::type;
   const size_t vsz = (size_t)nz * pstride;
   return sizeof(C) * (vsz * (dbuf ? 2 : 1) + nsph + 4 * (size_t)natom);
@@ -89,6 +89,17 @@ constexpr size_t kSmemLimit = 220 * 1024;
 constexpr int kNTip = 448;
 template <typename T, bool IP> constexpr int kMaxThreads() { return IP ? kNTip : kNTof<T>(); }
 template <typename T, bool IP> constexpr int kMinBlocks() { return (IP && sizeof(T) == 4) ? 2 : 1; }
+
+// Fixed geometries also hold the projector tables of the sphere entries in shared memory: beta_ip
+// (4 values, 16-byte aligned) and the point index with the atom in its upper 16 bits.
+template <typename T>
+__host__ __device__ inline size_t geom_table_offset(int nz, int pstride, int nsph, int natom) {
+  return (cell_smem_bytes<T>(nz, pstride, nsph, natom, true) + 15) & ~size_t(15);
+}
+template <typename T>
+inline size_t cell_smem_bytes_geom(int nz, int pstride, int nsph, int natom) {
+  return geom_table_offset<T>(nz, pstride, nsph, natom) + (size_t)nsph * (4 * sizeof(T) + sizeof(int));
+}
 
 template <typename T>
 inline size_t cell_smem_bytes_ip(int nx, int ny, int nz, int pstride, int nsph, int natom, bool periodic) {
@@ -239,6 +250,64 @@ __device__ __forceinline__ typename Cplx<T>::type local_h(const OrbArgs<T>& a,
   return local_h_at<T, PER, WD>(
       a, [&](int j) { return v[zb + (j < 8 ? c.ix[j] : c.iy[j - 8])]; }, [&](int j) { return w[j]; }, diag, q,
       Dout);
+}
+
+// Projections from the shared-memory tables (fixed geometries): as project(), with beta_ip and the
+// point index of entry i read from tbeta[4i..4i+3] and tidx[i] & 0xffff.
+template <typename T>
+__device__ __forceinline__ void project_tab(const OrbArgs<T>& a, const typename Cplx<T>::type* v,
+                                            const typename Cplx<T>::type* ph, const int* tidx,
+                                            const T* tbeta, typename Cplx<T>::type* ec) {
+  using C = typename Cplx<T>::type;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int at = warp; at < a.natom; at += nw) {
+    T acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const int e1 = a.atom_off[at + 1];
+    for (int i = a.atom_off[at] + lane; i < e1; i += 32) {
+      const C u = v[tidx[i] & 0xffff];
+      const C f = ph[i];
+      const T re = u.x * f.x - u.y * f.y, im = u.x * f.y + u.y * f.x;
+      const T* b = tbeta + 4 * i;
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        acc[2 * p] += b[p] * re;
+        acc[2 * p + 1] += b[p] * im;
+      }
+    }
+    const T tot = warp_split_sum<8>(acc);        // lane L: total of acc[L >> 2]
+    if ((lane & 3) == 0) {
+      const int j = lane >> 2, p = j >> 1;
+      reinterpret_cast<T*>(ec)[2 * (at * 4 + p) + (j & 1)] = tot * (a.atomE[at * 4 + p] * a.dV);
+    }
+  }
+}
+
+// Nonlocal scatter from the shared-memory tables, one sphere entry per thread: entry i of atom a adds
+// conj(ph_i) sum_p beta_ip ec_ap (MODE 0), or -i coef times that (a Horner stage), to the next vector
+// at its point.  Points inside several spheres receive one shared-memory atomic add per entry.
+template <typename T, int MODE>
+__device__ __forceinline__ void scatter_tab(const OrbArgs<T>& a, const typename Cplx<T>::type* ph,
+                                            const typename Cplx<T>::type* ec, const int* tidx,
+                                            const T* tbeta, typename Cplx<T>::type* nxt, T coef) {
+  using C = typename Cplx<T>::type;
+  for (int i = threadIdx.x; i < a.nsph; i += blockDim.x) {
+    const int pk = tidx[i];
+    const int at = pk >> 16;
+    const T* b = tbeta + 4 * i;
+    T sr = 0, si = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const C cc = ec[at * 4 + q];
+      sr += b[q] * cc.x;
+      si += b[q] * cc.y;
+    }
+    const C f = ph[i];
+    C nl = C{sr * f.x + si * f.y, si * f.x - sr * f.y};
+    if (MODE == 1) nl = C{coef * nl.y, -coef * nl.x};
+    C* dst = nxt + (pk & 0xffff);
+    atomicAdd(&dst->x, nl.x);
+    atomicAdd(&dst->y, nl.y);
+  }
 }
 
 // ------------------------------------------------------------------ fixed cell geometries
@@ -525,6 +594,9 @@ __global__ void __launch_bounds__(kMaxThreads<T, IP>(), kMinBlocks<T, IP>())
   L.ph = L.v + (DBUF ? 2 * vsz : vsz);
   L.ec = L.ph + a.nsph;
   L.sv = L.ec + 4 * a.natom;
+  // fixed geometries: projector tables in shared memory (loaded below)
+  T* tbeta = reinterpret_cast<T*>(smem_raw + geom_table_offset<T>(a.nz, ps, a.nsph, a.natom));
+  int* tidx = reinterpret_cast<int*>(tbeta + 4 * (size_t)a.nsph);
   const int orb = blockIdx.x;
   const int cell = orb / (a.nk * a.norb);
   const int k = (orb - cell * a.nk * a.norb) / a.norb;
@@ -574,6 +646,13 @@ __global__ void __launch_bounds__(kMaxThreads<T, IP>(), kMinBlocks<T, IP>())
       if (DBUF && !IP) L.nxt[i] = C{0, 0};
     }
   }
+  if constexpr (GEOM != 0) {
+    for (int i = threadIdx.x; i < a.nsph; i += blockDim.x) {
+      tidx[i] = a.sph_sidx[i] | (a.ent_atom[i] << 16);
+#pragma unroll
+      for (int p = 0; p < 4; ++p) tbeta[4 * i + p] = a.sph_beta[4 * i + p];
+    }
+  }
   // wave vector of the observables: k + A'_obs (OBS 1: end of the step; OBS 2: its start)
   auto obs_q = [&](T qo[3]) {
     qo[0] = q[0]; qo[1] = q[1]; qo[2] = q[2];
@@ -599,7 +678,11 @@ __global__ void __launch_bounds__(kMaxThreads<T, IP>(), kMinBlocks<T, IP>())
   T os[5] = {0, 0, 0, 0, 0};
 #pragma unroll 1
   for (int st = 0; st < NSTAGE; ++st) {
-    if (a.natom > 0) {
+    if constexpr (GEOM != 0) {
+      // the projection only reads the current vector; the scatter that reads ec waits for the
+      // barrier after the local pass
+      if (a.natom > 0) project_tab<T>(a, L.v, L.ph, tidx, tbeta, L.ec);
+    } else if (a.natom > 0) {
       project<T>(a, L.v, L.ph, L.ec);
       __syncthreads();
     }
@@ -717,7 +800,10 @@ __global__ void __launch_bounds__(kMaxThreads<T, IP>(), kMinBlocks<T, IP>())
     }
     __syncthreads();
     // nonlocal scatter at sphere points
-    if (a.natom > 0) {
+    if (GEOM != 0 && a.natom > 0) {
+      scatter_tab<T, MODE>(a, L.ph, L.ec, tidx, tbeta, L.nxt, coef);
+      __syncthreads();
+    } else if (a.natom > 0) {
       for (int s = threadIdx.x; s < a.nsp; s += blockDim.x) {
         const C nl = nonlocal_at<T>(a, s, L.ph, L.ec);
         const int pg = a.sp_pt[s];
@@ -861,8 +947,8 @@ template <typename T, int GEOM>
 bool geom_is(const OrbArgs<T>& a) {
   using G = GeomT<T, GEOM>;
   return a.periodic && a.nx == G::NX && a.ny == G::NY && a.nz == G::NZ && a.pstride == G::NXY &&
-         a.zlen == G::ZL && a.nseg == G::NSEG &&
-         cell_smem_bytes<T>(a.nz, a.pstride, a.nsph, a.natom, true) <= kSmemLimit;
+         a.zlen == G::ZL && a.nseg == G::NSEG && a.natom < 32768 &&
+         cell_smem_bytes_geom<T>(a.nz, a.pstride, a.nsph, a.natom) <= kSmemLimit;
 }
 
 template <typename T>
@@ -877,7 +963,7 @@ template <typename T, int OBS>
 cudaError_t dispatch_geom(const OrbArgs<T>& a, cudaStream_t s) {
   const int g = cell_geom<T>(a);
   if (g == 0) return cudaErrorInvalidValue;
-  const size_t smem = cell_smem_bytes<T>(a.nz, a.pstride, a.nsph, a.natom, true);
+  const size_t smem = cell_smem_bytes_geom<T>(a.nz, a.pstride, a.nsph, a.natom);
   const int items = a.nx * a.ny * a.nseg;
   int nt = ((items + 31) / 32) * 32;
   if (nt > kNTof<T>()) nt = kNTof<T>();
