@@ -87,7 +87,11 @@ constexpr size_t kSmemLimit = 220 * 1024;
 // In-place sweep: at most kNTip columns (one thread each); FP32 CTAs are sized for two per SM
 // (72 registers per thread), FP64 CTAs for one.
 constexpr int kNTip = 448;
-template <typename T, bool IP> constexpr int kMaxThreads() { return IP ? kNTip : kNTof<T>(); }
+// FP32 fixed geometries (GEOM != 0): two x-adjacent points per thread, at most kNTpair threads.
+constexpr int kNTpair = 416;
+template <typename T, bool IP, int GEOM = 0> constexpr int kMaxThreads() {
+  return IP ? kNTip : ((GEOM != 0 && sizeof(T) == 4) ? kNTpair : kNTof<T>());
+}
 template <typename T, bool IP> constexpr int kMinBlocks() { return (IP && sizeof(T) == 4) ? 2 : 1; }
 
 // Fixed geometries also hold the projector tables of the sphere entries in shared memory: beta_ip
@@ -411,6 +415,122 @@ __device__ __forceinline__ void fixed_column(const OrbArgs<T>& a, int item, unsi
   }
 }
 
+// FP32 fixed geometries: a thread owns two x-adjacent points (x even) of a column segment.  The
+// points of a row pair are one 16-byte shared-memory load, so the 16 x-neighbours of the two points
+// come from four loads and their 16 y-neighbours from eight: 13 loads per two points with the z
+// window, against 17 per point for one point per thread.
+template <int GEOM>
+struct GeomP {
+  static constexpr int NX = Geom<GEOM>::NX, NY = Geom<GEOM>::NY, NZ = Geom<GEOM>::NZ, NXY = NX * NY;
+  static constexpr int NP = NXY / 2;                       // point pairs per plane
+  static constexpr int S0 = kNTpair / NP;
+  static constexpr int S = S0 < 1 ? 1 : (S0 > NZ ? NZ : S0);
+  static constexpr int ZL = (NZ + S - 1) / S;
+  static constexpr int NSEG = (NZ + ZL - 1) / ZL;
+  static_assert(NX % 2 == 0, "point pairs need an even nx");
+};
+
+__device__ __forceinline__ float4 lds_c2(unsigned addr) {
+  float4 r;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w) : "r"(addr));
+  return r;
+}
+__device__ __forceinline__ void sts_c2(unsigned addr, float4 v) {
+  asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w));
+}
+__device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
+
+template <int GEOM, int MODE, bool ACC>
+__device__ __forceinline__ void fixed_pair(const OrbArgs<float>& a, int item, unsigned sv, unsigned sn,
+                                           const float* __restrict__ Vc, const float2* __restrict__ psi,
+                                           float diag0, const float* q, float coef, float os[5]) {
+  using M = CM<float>;
+  using G = GeomP<GEOM>;
+  constexpr int NX = G::NX, NY = G::NY, NZ = G::NZ, NXY = G::NXY, ZL = G::ZL;
+  constexpr bool RAGGED = (NZ % ZL) != 0;
+  constexpr unsigned CB = sizeof(float2), PB = NXY * sizeof(float2);
+  const int pi = item % G::NP, seg = item / G::NP;
+  const int col = 2 * pi;
+  const int y = col / NX, x = col - y * NX;          // x even
+  const int z0 = seg * ZL;
+  const unsigned p0 = sv + (unsigned)(z0 * NXY) * CB;
+  auto wx = [](int v) { return v < 0 ? v + NX : (v >= NX ? v - NX : v); };
+  auto wy = [](int v) { return v < 0 ? v + NY : (v >= NY ? v - NY : v); };
+  // pairs (x-4, x-3), (x-2, x-1), (x+2, x+3), (x+4, x+5) of row y; the pair (x, x+1) of rows y +- m
+  const unsigned xa0 = p0 + (unsigned)(y * NX + wx(x - 4)) * CB, xa1 = p0 + (unsigned)(y * NX + wx(x - 2)) * CB;
+  const unsigned xa2 = p0 + (unsigned)(y * NX + wx(x + 2)) * CB, xa3 = p0 + (unsigned)(y * NX + wx(x + 4)) * CB;
+  unsigned ya[8];
+#pragma unroll
+  for (int m = 1; m <= 4; ++m) {
+    ya[2 * (m - 1)] = p0 + (unsigned)(wy(y + m) * NX + x) * CB;
+    ya[2 * (m - 1) + 1] = p0 + (unsigned)(wy(y - m) * NX + x) * CB;
+  }
+  const unsigned cA = p0 + (unsigned)col * CB, oA = sn + (unsigned)(z0 * NXY + col) * CB;
+  float4 w[9];                                       // plane z0 + k - 4 + j in w[(k + j) % 9]
+#pragma unroll
+  for (int j = 0; j < 9; ++j) {
+    int zz = z0 - 4 + j;
+    zz += zz < 0 ? NZ : 0;
+    zz -= zz >= NZ ? NZ : 0;
+    w[j] = lds_c2(sv + (unsigned)(zz * NXY + col) * CB);
+  }
+  const float* Vp = Vc + z0 * NXY + col;
+  const float2* Pp = psi + z0 * NXY + col;
+  const int len = NZ - z0;
+#pragma unroll
+  for (int k = 0; k < ZL; ++k) {
+    if (RAGGED && k >= len) break;
+    const unsigned ko = (unsigned)k * PB;
+    const float4 XM4 = lds_c2(xa0 + ko), XM2 = lds_c2(xa1 + ko), XP2 = lds_c2(xa2 + ko), XP4 = lds_c2(xa3 + ko);
+    float4 Y[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) Y[j] = lds_c2(ya[j] + ko);
+    const float4 Wc = w[(k + 4) % 9];
+    const float2 Vv = *reinterpret_cast<const float2*>(Vp + k * NXY);
+    // in-plane neighbours of point A (x) and B (x + 1), in local_h_at's order
+    auto nbA = [&](int j) -> float2 {
+      switch (j) {
+        case 0: return hi2(Wc);  case 1: return hi2(XM2); case 2: return lo2(XP2); case 3: return lo2(XM2);
+        case 4: return hi2(XP2); case 5: return hi2(XM4); case 6: return lo2(XP4); case 7: return lo2(XM4);
+        default: return lo2(Y[j - 8]);
+      }
+    };
+    auto nbB = [&](int j) -> float2 {
+      switch (j) {
+        case 0: return lo2(XP2); case 1: return lo2(Wc);  case 2: return hi2(XP2); case 3: return hi2(XM2);
+        case 4: return lo2(XP4); case 5: return lo2(XM2); case 6: return hi2(XP4); case 7: return hi2(XM4);
+        default: return hi2(Y[j - 8]);
+      }
+    };
+    float2 DdA[3], DdB[3];
+    const float2 hA = local_h_at<float, true, ACC>(a, nbA, [&](int j) { return lo2(w[(k + j) % 9]); },
+                                                   diag0 + Vv.x, q, DdA);
+    const float2 hB = local_h_at<float, true, ACC>(a, nbB, [&](int j) { return hi2(w[(k + j) % 9]); },
+                                                   diag0 + Vv.y, q, DdB);
+    if (ACC) {                                       // |u|^2 and Im(conj(u) D1_a u) of both points
+      const float2 uA = lo2(Wc), uB = hi2(Wc);
+      os[0] += uA.x * uA.x + uA.y * uA.y;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) os[1 + d] += uA.x * DdA[d].y - uA.y * DdA[d].x;
+      os[0] += uB.x * uB.x + uB.y * uB.y;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) os[1 + d] += uB.x * DdB[d].y - uB.y * DdB[d].x;
+    }
+    float2 rA = hA, rB = hB;
+    if (MODE == 1) {                                 // psi + (-i coef) H v
+      const float4 P = *reinterpret_cast<const float4*>(Pp + k * NXY);
+      rA = M::fma(coef, make_float2(hA.y, -hA.x), lo2(P));
+      rB = M::fma(coef, make_float2(hB.y, -hB.x), hi2(P));
+    }
+    sts_c2(oA + ko, make_float4(rA.x, rA.y, rB.x, rB.y));
+    if (k < ZL - 1) {                                // plane z + 5 replaces plane z - 4
+      const bool wrap = z0 + k + 5 >= NZ;
+      w[k % 9] = lds_c2(cA + (unsigned)(k + 5) * PB - (wrap ? (unsigned)NZ * PB : 0u));
+    }
+  }
+}
+
 // Nonlocal value at sphere point s: sum over its entries of conj(ph_i) sum_p beta_ip ec_ap.
 template <typename T>
 __device__ __forceinline__ typename Cplx<T>::type nonlocal_at(const OrbArgs<T>& a, int s,
@@ -575,7 +695,7 @@ __device__ __forceinline__ void nonlocal_current(const OrbArgs<T>& a, const type
 // last stage; 2 norm and current of the input orbital, accumulated during the first stage from the
 // per-axis derivative sums that stage forms anyway (no extra pass).  MODE 2 always uses 1.
 template <typename T, int MODE, bool PER, bool DBUF, int OBS, bool IP, int GEOM = 0>
-__global__ void __launch_bounds__(kMaxThreads<T, IP>(), kMinBlocks<T, IP>())
+__global__ void __launch_bounds__(kMaxThreads<T, IP, GEOM>(), kMinBlocks<T, IP>())
     k_cell(OrbArgs<T> a, typename Cplx<T>::type* scratch) {
   static_assert(!IP || (MODE == 1 && !DBUF), "the in-place sweep serves the Taylor stages with one buffer");
   static_assert(GEOM == 0 || (PER && DBUF && !IP && MODE != 2), "fixed geometries: periodic, two copies");
@@ -745,9 +865,16 @@ __global__ void __launch_bounds__(kMaxThreads<T, IP>(), kMinBlocks<T, IP>())
         }
       } else if constexpr (GEOM != 0) {
         const unsigned sv = (unsigned)__cvta_generic_to_shared(L.v), sn = (unsigned)__cvta_generic_to_shared(L.nxt);
+        if constexpr (sizeof(T) == 4) {
+          constexpr int npair_items = GeomP<GEOM>::NP * GeomP<GEOM>::NSEG;
 #pragma unroll 1
-        for (int item = threadIdx.x; item < nitems; item += blockDim.x)
-          fixed_column<T, GEOM, MODE, ACC && PER>(a, item, sv, sn, Vc, psi, diag0, q, coef, os);
+          for (int item = threadIdx.x; item < npair_items; item += blockDim.x)
+            fixed_pair<GEOM, MODE, ACC && PER>(a, item, sv, sn, Vc, psi, diag0, q, coef, os);
+        } else {
+#pragma unroll 1
+          for (int item = threadIdx.x; item < nitems; item += blockDim.x)
+            fixed_column<T, GEOM, MODE, ACC && PER>(a, item, sv, sn, Vc, psi, diag0, q, coef, os);
+        }
       } else {
 #pragma unroll 1
         for (int item = threadIdx.x; item < nitems; item += blockDim.x) {
@@ -964,9 +1091,11 @@ cudaError_t dispatch_geom(const OrbArgs<T>& a, cudaStream_t s) {
   const int g = cell_geom<T>(a);
   if (g == 0) return cudaErrorInvalidValue;
   const size_t smem = cell_smem_bytes_geom<T>(a.nz, a.pstride, a.nsph, a.natom);
-  const int items = a.nx * a.ny * a.nseg;
+  const int items = sizeof(T) == 4 ? (g == 1 ? GeomP<1>::NP * GeomP<1>::NSEG : GeomP<2>::NP * GeomP<2>::NSEG)
+                                   : a.nx * a.ny * a.nseg;
   int nt = ((items + 31) / 32) * 32;
-  if (nt > kNTof<T>()) nt = kNTof<T>();
+  const int ntmax = sizeof(T) == 4 ? kNTpair : kNTof<T>();
+  if (nt > ntmax) nt = ntmax;
   return g == 1 ? launch_cell<T, 1, true, true, OBS, false, 1>(a, nullptr, smem, nt, s)
                 : launch_cell<T, 1, true, true, OBS, false, 2>(a, nullptr, smem, nt, s);
 }
