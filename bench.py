@@ -767,6 +767,10 @@ def hpsi_cluster(dev, reps=10, norb=256):
              "k_tile4<8, 1 row, TMA-staged V/psi> (2x1 points/thread, 2 CTAs/SM)",
              "k_tile4<4, 1 row, TMA-staged V/psi> (2x1 points/thread, 4 CTAs/SM)"]
     res["stencil_variant"] = {"hpsi": names[variant[0]], "horner_stage": names[variant[1]]}
+    pv, pms = ctx.project_variant()
+    res["projection_schedule"] = {"in_use": f"{2 << pv} warps per CTA",
+                                  "tune_ms": {f"{2 << v} warps per CTA": t for v, t in enumerate(pms)},
+                                  "kernel": "k_gproject_mma (mma.sync m16n8k8 TF32, 3xTF32 split)"}
     # the tuner's timings of the stencil kernel alone (no projectors), 2 launches each at init:
     # H v moves 16 B per orbital-point, a Horner stage 24 B (reads v and psi, writes the result)
     res["stencil_only_GBps"] = {

@@ -316,7 +316,12 @@ tdks_status tdks_check(tdks_ctx* ctx);
  * the cells' currents I(X, t), first-order Mur absorbing boundaries at both ends; then every cell
  * takes one tdks_step-like predictor-corrector step with its own A'(t+dt/2) = (A(X,t)+A(X,t+dt))/(2c)
  * along z (Eq. TDKS_ms), and its current density J_z at t+dt (with A(X,t+dt)) becomes I(X, t+dt).
- * A_now, A_prev (host, [nX]): A at t = 0 and t = -dt (set the incident pulse here). */
+ * A_now, A_prev (host, [nX]): A at t = 0 and t = -dt (set the incident pulse here).
+ * From the second tdks_ms_step after tdks_ms_init (or tdks_set_state) on, the step is one launch of a
+ * CUDA graph holding all of its kernels (one graph per rotation of the three A levels, rebuilt when the
+ * orbital array, dt or the kernel variants change; tdks_set_step_graph(ctx, 0) launches the kernels one
+ * by one instead).  No host value enters the step after its first call: every cell's A' comes from the
+ * device. */
 tdks_status tdks_ms_init(tdks_ctx* ctx, int nX, int m0, double dX, const double* A_now,
                          const double* A_prev);
 tdks_status tdks_ms_step(tdks_ctx* ctx, void* u_dev, double t, double dt);
@@ -343,12 +348,14 @@ tdks_status tdks_ms_size(const tdks_ctx* ctx, int* nX);
 enum { TDKS_PRED_PC = 0, TDKS_PRED_EXTRAP = 1, TDKS_PRED_LEARNED = 2 };
 tdks_status tdks_set_predictor(tdks_ctx* ctx, int mode, double threshold);
 
-/* How predicted steps are issued (no counterpart in the paper).  enable = 1 (default): as the CUDA graph
- * described above (one per slot of the four-potential history, so that the graph's buffers are fixed),
- * with the decision on the device.  enable = 0: the same kernels launched one by one on the stream, the
- * misfit copied to the host and the fallback enqueued from there (one synchronisation per step; every
- * kernel appears as its own launch to profilers, which do not time the kernel nodes of graphs that hold
- * conditional nodes).  Both give the same results.  Errors: EINVAL for enable outside 0..1. */
+/* How predicted steps and multiscale steps are issued (no counterpart in the paper).  enable = 1
+ * (default): as the CUDA graphs described above (for predicted steps one per slot of the four-potential
+ * history, so that the graph's buffers are fixed, with the decision on the device; for multiscale steps
+ * one per rotation of the A levels).  enable = 0: the same kernels launched one by one on the stream;
+ * a predicted step then copies the misfit to the host and enqueues the fallback from there (one
+ * synchronisation per step; every kernel appears as its own launch to profilers, which do not time the
+ * kernel nodes of graphs that hold conditional nodes).  Both give the same results.  Errors: EINVAL for
+ * enable outside 0..1. */
 tdks_status tdks_set_step_graph(tdks_ctx* ctx, int enable);
 
 /* ---- Learned potential predictor ------------------------------------------------------------
@@ -429,6 +436,19 @@ tdks_status tdks_query(const tdks_ctx* ctx, int* npts, int* nk, int* norb, int* 
  * Errors: EUNSUPPORTED if the context does not use the tile kernels or the variant does not apply
  * (FP32 only; nx % 4 for 5 and 6); EINVAL for set outside -1..6. */
 tdks_status tdks_tile_variant(tdks_ctx* ctx, int set, int* variant, float* tune_ms);
+
+/* Schedule of the FP32 projections of large grids (the batched contraction [orbitals x sphere points]
+ * x [sphere points x 4] of the Kleinman-Bylander projections, Sec. 3.1, on the tensor cores; no
+ * counterpart in the paper).  A CTA takes one atom and 16 orbitals; its warps take interleaved steps
+ * of 8 sphere points: 0 = 2 warps, 1 = 4 warps, 2 = 8 warps per CTA.  At tdks_init a context that
+ * uses the tile kernels in FP32 times the three on its own orbital count (zeroed orbitals) and keeps
+ * the fastest.  The sums are the same products added in another grouping.
+ *   set       : -1 leaves the choice as it is; 0..2 forces that schedule.
+ *   variant   : receives the schedule in use (may be NULL).
+ *   tune_ms   : receives the 3 tuning times in ms, -1 where not timed (may be NULL).
+ * Errors: EUNSUPPORTED if the context does not use the FP32 tile kernels; EINVAL for set outside
+ * -1..2. */
+tdks_status tdks_project_variant(tdks_ctx* ctx, int set, int* variant, float* tune_ms);
 
 /* Buffer scheme of the shared-memory cell kernels for the Taylor propagator (Eq. taylor, Horner
  * form; no counterpart in the paper).  0 = two orbital copies in shared memory (or a global scratch

@@ -531,6 +531,87 @@ __device__ __forceinline__ void fixed_pair(const OrbArgs<float>& a, int item, un
   }
 }
 
+// Final pass of an FP32 fixed geometry over one column-pair segment of the propagated vector at
+// shared-memory address sv: writes the orbital (out, nullable), adds 2 |u|^2 to the per-k density
+// partial rho32 (nullable), and with OBS adds |u|^2 and Im(conj(u) D1_a u) (a = x, y, z) to os.
+template <int GEOM, bool OBS>
+__device__ __forceinline__ void fixed_final_pair(const OrbArgs<float>& a, int item, unsigned sv,
+                                                 float2* __restrict__ out, float* __restrict__ rho32,
+                                                 float os[5]) {
+  using M = CM<float>;
+  using G = GeomP<GEOM>;
+  constexpr int NX = G::NX, NY = G::NY, NZ = G::NZ, NXY = G::NXY, ZL = G::ZL;
+  constexpr bool RAGGED = (NZ % ZL) != 0;
+  constexpr unsigned CB = sizeof(float2), PB = NXY * sizeof(float2);
+  const int pi = item % G::NP, seg = item / G::NP;
+  const int col = 2 * pi;
+  const int y = col / NX, x = col - y * NX;
+  const int z0 = seg * ZL;
+  const unsigned p0 = sv + (unsigned)(z0 * NXY) * CB;
+  auto wx = [](int v) { return v < 0 ? v + NX : (v >= NX ? v - NX : v); };
+  auto wy = [](int v) { return v < 0 ? v + NY : (v >= NY ? v - NY : v); };
+  const unsigned cA = p0 + (unsigned)col * CB;
+  unsigned xa0 = 0, xa1 = 0, xa2 = 0, xa3 = 0, ya[8];
+  float4 w[9];
+  if (OBS) {
+    xa0 = p0 + (unsigned)(y * NX + wx(x - 4)) * CB; xa1 = p0 + (unsigned)(y * NX + wx(x - 2)) * CB;
+    xa2 = p0 + (unsigned)(y * NX + wx(x + 2)) * CB; xa3 = p0 + (unsigned)(y * NX + wx(x + 4)) * CB;
+#pragma unroll
+    for (int m = 1; m <= 4; ++m) {
+      ya[2 * (m - 1)] = p0 + (unsigned)(wy(y + m) * NX + x) * CB;
+      ya[2 * (m - 1) + 1] = p0 + (unsigned)(wy(y - m) * NX + x) * CB;
+    }
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+      int zz = z0 - 4 + j;
+      zz += zz < 0 ? NZ : 0;
+      zz -= zz >= NZ ? NZ : 0;
+      w[j] = lds_c2(sv + (unsigned)(zz * NXY + col) * CB);
+    }
+  }
+  const int len = NZ - z0;
+#pragma unroll
+  for (int k = 0; k < ZL; ++k) {
+    if (RAGGED && k >= len) break;
+    const unsigned ko = (unsigned)k * PB;
+    const float4 Wc = OBS ? w[(k + 4) % 9] : lds_c2(cA + ko);
+    const int pg = (z0 + k) * NXY + col;
+    if (out) *reinterpret_cast<float4*>(out + pg) = Wc;
+    const float2 rA = lo2(Wc), rB = hi2(Wc);
+    const float rrA = rA.x * rA.x + rA.y * rA.y, rrB = rB.x * rB.x + rB.y * rB.y;
+    if (rho32) {
+      atomicAdd(rho32 + pg, 2.0f * rrA);
+      atomicAdd(rho32 + pg + 1, 2.0f * rrB);
+    }
+    if (OBS) {
+      const float4 XM4 = lds_c2(xa0 + ko), XM2 = lds_c2(xa1 + ko), XP2 = lds_c2(xa2 + ko), XP4 = lds_c2(xa3 + ko);
+      float4 Y[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) Y[j] = lds_c2(ya[j] + ko);
+      // x +- m of point A (x) and B (x + 1), as in fixed_pair
+      const float2 axp[4] = {hi2(Wc), lo2(XP2), hi2(XP2), lo2(XP4)}, axm[4] = {hi2(XM2), lo2(XM2), hi2(XM4), lo2(XM4)};
+      const float2 bxp[4] = {lo2(XP2), hi2(XP2), lo2(XP4), hi2(XP4)}, bxm[4] = {lo2(Wc), hi2(XM2), lo2(XM2), hi2(XM4)};
+      float2 dA[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}}, dB[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll
+      for (int m = 1; m <= 4; ++m) {
+        dA[0] = M::fma(a.d1x[m - 1], M::sub(axp[m - 1], axm[m - 1]), dA[0]);
+        dB[0] = M::fma(a.d1x[m - 1], M::sub(bxp[m - 1], bxm[m - 1]), dB[0]);
+        dA[1] = M::fma(a.d1y[m - 1], M::sub(lo2(Y[2 * (m - 1)]), lo2(Y[2 * (m - 1) + 1])), dA[1]);
+        dB[1] = M::fma(a.d1y[m - 1], M::sub(hi2(Y[2 * (m - 1)]), hi2(Y[2 * (m - 1) + 1])), dB[1]);
+        dA[2] = M::fma(a.d1z[m - 1], M::sub(lo2(w[(k + 4 + m) % 9]), lo2(w[(k + 4 - m) % 9])), dA[2]);
+        dB[2] = M::fma(a.d1z[m - 1], M::sub(hi2(w[(k + 4 + m) % 9]), hi2(w[(k + 4 - m) % 9])), dB[2]);
+      }
+      os[0] += rrA + rrB;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) os[1 + d] += (rA.x * dA[d].y - rA.y * dA[d].x) + (rB.x * dB[d].y - rB.y * dB[d].x);
+      if (k < ZL - 1) {
+        const bool wrap = z0 + k + 5 >= NZ;
+        w[k % 9] = lds_c2(cA + (unsigned)(k + 5) * PB - (wrap ? (unsigned)NZ * PB : 0u));
+      }
+    }
+  }
+}
+
 // Nonlocal value at sphere point s: sum over its entries of conj(ph_i) sum_p beta_ip ec_ap.
 template <typename T>
 __device__ __forceinline__ typename Cplx<T>::type nonlocal_at(const OrbArgs<T>& a, int s,
@@ -576,6 +657,10 @@ template <> struct Acc<float> {
   using type = FF;
   static __device__ __forceinline__ FF zero() { return FF{0.f, 0.f}; }
   static __device__ __forceinline__ FF add(FF a, float x) { return ff_add(a, FF{x, 0.f}); }
+  static __device__ __forceinline__ FF addv(FF a, FF b) { return ff_add(a, b); }
+  // a float-float in one double slot of a shared array
+  static __device__ __forceinline__ void store(double* r, int i, FF a) { reinterpret_cast<FF*>(r)[i] = a; }
+  static __device__ __forceinline__ FF load(const double* r, int i) { return reinterpret_cast<const FF*>(r)[i]; }
   static __device__ __forceinline__ FF warp_sum(FF a) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) a = ff_add(a, ff_shfl_xor(a, o));
@@ -591,6 +676,9 @@ template <> struct Acc<double> {
   using type = double;
   static __device__ __forceinline__ double zero() { return 0.0; }
   static __device__ __forceinline__ double add(double a, double x) { return a + x; }
+  static __device__ __forceinline__ double addv(double a, double b) { return a + b; }
+  static __device__ __forceinline__ void store(double* r, int i, double a) { r[i] = a; }
+  static __device__ __forceinline__ double load(const double* r, int i) { return r[i]; }
   static __device__ __forceinline__ double warp_sum(double a) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
@@ -602,8 +690,9 @@ template <> struct Acc<double> {
 
 // Per-orbital observables from per-thread partial sums v = {sum |u|^2, sum Im(conj(u) D1_a u) (a = x,
 // y, z), sum Re(conj(u) (H u))}: warp sums in the accumulator type, one barrier, then thread j < 8 adds
-// the warps' sums in FP64 and writes out[j] = {norm, J_loc[3], J_nl[3], e} with
-// J_loc_a = (sum Im(conj(u) D1_a u) + qo_a sum |u|^2) dV and J_nl from s_jnl.
+// the warps' sums in the accumulator type (float-float for FP32 orbitals: a chain of dependent FP64
+// adds would wait on the narrow FP64 pipe at every step) and writes out[j] = {norm, J_loc[3], J_nl[3],
+// e} with J_loc_a = (sum Im(conj(u) D1_a u) + qo_a sum |u|^2) dV and J_nl from s_jnl.
 // red: [8][32] shared doubles.
 template <typename T>
 __device__ __forceinline__ void reduce_obs(const T v[5], const T qo[3], double dV, const double* s_jnl,
@@ -615,15 +704,19 @@ __device__ __forceinline__ void reduce_obs(const T v[5], const T qo[3], double d
   __syncthreads();                                 // red and s_jnl complete, red free
   if (lane == 0) {
 #pragma unroll
-    for (int j = 0; j < 5; ++j) red[j * 32 + warp] = Acc<T>::to_double(x[j]);
+    for (int j = 0; j < 5; ++j) Acc<T>::store(red, j * 32 + warp, x[j]);
   }
   __syncthreads();
   if (threadIdx.x < 8) {
     const int j = threadIdx.x;
-    double t[2] = {0, 0};
+    typename Acc<T>::type s0 = Acc<T>::zero(), s1 = Acc<T>::zero();
     const int src = (j == 7) ? 4 : (j < 4 ? j : -1);
     if (src >= 0)
-      for (int w = 0; w < nw; ++w) { t[0] += red[src * 32 + w]; t[1] += red[w]; }
+      for (int w = 0; w < nw; ++w) {
+        s0 = Acc<T>::addv(s0, Acc<T>::load(red, src * 32 + w));
+        s1 = Acc<T>::addv(s1, Acc<T>::load(red, w));
+      }
+    const double t[2] = {Acc<T>::to_double(s0), Acc<T>::to_double(s1)};
     double r;
     if (j == 0 || j == 7) r = t[0] * dV;
     else if (j < 4) r = (t[0] + (double)qo[j - 1] * t[1]) * dV;
@@ -637,11 +730,13 @@ __device__ __forceinline__ void reduce_obs(const T v[5], const T qo[3], double d
 // one atom's sphere points (atoms in batches of kNLBatch, each split over the warps), partial sums
 // meet in shared memory (part: [kNLBatch][32] of T), and thread a of the batch forms the products
 // of atom a and adds it to s_jnl[3] (shared; zeroed by the caller).
+// TAB: the point indices and beta_ip come from the shared-memory tables of the fixed geometries.
 constexpr int kNLBatch = 16;
-template <typename T>
+template <typename T, bool TAB = false>
 __device__ __forceinline__ void nonlocal_current(const OrbArgs<T>& a, const typename Cplx<T>::type* v,
                                                  const typename Cplx<T>::type* ph, T* part,
-                                                 double* s_jnl) {
+                                                 double* s_jnl, const int* tidx = nullptr,
+                                                 const T* tbeta = nullptr) {
   using C = typename Cplx<T>::type;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int ab = 0; ab < a.natom; ab += kNLBatch) {
@@ -655,13 +750,13 @@ __device__ __forceinline__ void nonlocal_current(const OrbArgs<T>& a, const type
 #pragma unroll
       for (int j = 0; j < 32; ++j) acc[j] = 0;
       for (int i = a.atom_off[at] + ch * 32 + lane; i < a.atom_off[at + 1]; i += 32 * nch) {
-        const C u = v[a.sph_sidx[i]];
+        const C u = v[TAB ? (tidx[i] & 0xffff) : a.sph_sidx[i]];
         const C f = ph[i];
         const T re = u.x * f.x - u.y * f.y, im = u.x * f.y + u.y * f.x;
         const T d0 = a.sph_d[3 * i], d1 = a.sph_d[3 * i + 1], d2 = a.sph_d[3 * i + 2];
 #pragma unroll
         for (int p = 0; p < 4; ++p) {
-          const T b = a.sph_beta[i * 4 + p];
+          const T b = TAB ? tbeta[i * 4 + p] : a.sph_beta[i * 4 + p];
           acc[2 * p] += b * re; acc[2 * p + 1] += b * im;
           acc[8 + 2 * p] += d0 * b * re; acc[8 + 2 * p + 1] += d0 * b * im;
           acc[16 + 2 * p] += d1 * b * re; acc[16 + 2 * p + 1] += d1 * b * im;
@@ -677,11 +772,15 @@ __device__ __forceinline__ void nonlocal_current(const OrbArgs<T>& a, const type
       const T* pa = part + threadIdx.x * 32;
       const double dv2 = (double)a.dV * (double)a.dV;
       for (int d = 0; d < 3; ++d) {
-        double sacc = 0;
-        for (int p = 0; p < 4; ++p)
-          sacc += 2.0 * (double)a.atomE[at * 4 + p] *
-                  ((double)pa[8 + 8 * d + 2 * p] * pa[2 * p + 1] - (double)pa[8 + 8 * d + 2 * p + 1] * pa[2 * p]);
-        atomicAdd(&s_jnl[d], sacc * dv2);
+        // the products in the orbitals' precision (the sums in pa are of that precision already): for
+        // FP32 orbitals no dependent FP64 chain on the narrow FP64 pipe
+        T sacc = 0;
+        for (int p = 0; p < 4; ++p) {
+          const T br = pa[8 + 8 * d + 2 * p], bi = pa[8 + 8 * d + 2 * p + 1];
+          const T im = fma(br, pa[2 * p + 1], -(bi * pa[2 * p]));   // Im(conj(b) c)
+          sacc = fma(T(2) * a.atomE[at * 4 + p], im, sacc);
+        }
+        atomicAdd(&s_jnl[d], (double)sacc * dv2);
       }
     }
     __syncthreads();
@@ -786,8 +885,9 @@ __global__ void __launch_bounds__(kMaxThreads<T, IP, GEOM>(), kMinBlocks<T, IP>(
     T qo[3];
     obs_q(qo);
     set_phases<T>(a, L.ph, qo);
-    __syncthreads();
-    nonlocal_current<T>(a, L.v, L.ph, nl_part, s_jnl);
+    __syncthreads();                               // also completes the table load
+    if constexpr (GEOM != 0) nonlocal_current<T, true>(a, L.v, L.ph, nl_part, s_jnl, tidx, tbeta);
+    else nonlocal_current<T>(a, L.v, L.ph, nl_part, s_jnl);
   }
   set_phases<T>(a, L.ph, q);
   __syncthreads();
@@ -961,6 +1061,15 @@ __global__ void __launch_bounds__(kMaxThreads<T, IP, GEOM>(), kMinBlocks<T, IP>(
   const double wk = 2.0 * a.kw[k];
   C* out = a.psi_out ? a.psi_out + (size_t)orb * a.npts : nullptr;
   constexpr bool FINAL_OBS = (OBS == 1);
+  if constexpr (GEOM != 0 && sizeof(T) == 4) {
+    const unsigned sv = (unsigned)__cvta_generic_to_shared(L.v);
+    float2* o = (MODE == 0 || (MODE == 1 && a.write_out)) ? out : nullptr;
+    float* r32 = (MODE == 1 && a.rho32) ? a.rho32 + ((size_t)cell * a.nk + k) * a.npts : nullptr;
+    constexpr int npair_items = GeomP<GEOM>::NP * GeomP<GEOM>::NSEG;
+#pragma unroll 1
+    for (int item = threadIdx.x; item < npair_items; item += blockDim.x)
+      fixed_final_pair<GEOM, FINAL_OBS>(a, item, sv, o, r32, os);
+  } else
 #pragma unroll 1
   for (int item = threadIdx.x; item < (IP ? nxy : nitems); item += blockDim.x) {
     Column<T, PER> c = make_column<T, PER>(a, item);
@@ -1015,7 +1124,8 @@ __global__ void __launch_bounds__(kMaxThreads<T, IP, GEOM>(), kMinBlocks<T, IP>(
     __syncthreads();
     set_phases<T>(a, L.ph, qo);
     __syncthreads();
-    nonlocal_current<T>(a, L.v, L.ph, nl_part, s_jnl);
+    if constexpr (GEOM != 0) nonlocal_current<T, true>(a, L.v, L.ph, nl_part, s_jnl, tidx, tbeta);
+    else nonlocal_current<T>(a, L.v, L.ph, nl_part, s_jnl);
   }
   reduce_obs<T>(os, qo, a.dV, s_jnl, red, a.obs + (size_t)orb * 8);
 }

@@ -589,7 +589,8 @@ __global__ void __launch_bounds__(128) k_gproject(TileArgs<T> a, const typename 
 // Fragments (PTX ISA, m16n8k8 .tf32): A a0 (row g, col t), a1 (g+8, t), a2 (g, t+4), a3 (g+8, t+4);
 // B b0 (row t, col g), b1 (t+4, g); C c0 (g, 2t), c1 (g, 2t+1), c2 (g+8, 2t), c3 (g+8, 2t+1), with
 // g = lane / 4 and t = lane % 4.  Rows are orbitals, columns of B and C are projectors.
-constexpr int kPW = 4;      // warps per CTA: the same 16 orbitals, each warp a quarter of the sphere points
+// kPW (template parameter): warps per CTA, all on the same 16 orbitals, each on every kPW-th step of
+// 8 sphere points; the context's tuner picks 2, 4 or 8 (TileArgs::proj_variant 0, 1, 2).
 
 __device__ __forceinline__ unsigned tf32_rna(float x) {
   unsigned r;
@@ -610,6 +611,7 @@ __device__ __forceinline__ void mma_tf32_1688(float (&d)[4], const unsigned (&a)
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
+template <int kPW>
 __global__ void __launch_bounds__(32 * kPW) k_gproject_mma(TileArgs<float> a, const float2* __restrict__ v) {
   __shared__ float part[kPW][32][8];
   const int at = blockIdx.x;
@@ -828,9 +830,11 @@ cudaError_t launch_tile_stage(const TileArgs<T>& a0, const void* vin, int mode, 
 template <typename T>
 cudaError_t launch_tile_project(const TileArgs<T>& a, const typename Cplx<T>::type* v, cudaStream_t s) {
   if (a.natom == 0) return cudaSuccess;
-  if constexpr (sizeof(T) == 4) {      // FP32: tensor cores (3xTF32)
-    const dim3 grid(a.natom, (a.norb_tot + 15) / 16);
-    k_gproject_mma<<<grid, 32 * kPW, 0, s>>>(a, v);
+  if constexpr (sizeof(T) == 4) {      // FP32: tensor cores (3xTF32); the schedule of the projection
+    const dim3 grid(a.natom, (a.norb_tot + 15) / 16);   // tuner: 2, 4 or 8 warps per CTA
+    if (a.proj_variant == 0) k_gproject_mma<2><<<grid, 64, 0, s>>>(a, v);
+    else if (a.proj_variant == 2) k_gproject_mma<8><<<grid, 256, 0, s>>>(a, v);
+    else k_gproject_mma<4><<<grid, 128, 0, s>>>(a, v);
   } else {
     const dim3 grid(a.natom, (a.norb_tot + kOB - 1) / kOB);
     k_gproject<T><<<grid, 128, 0, s>>>(a, v);

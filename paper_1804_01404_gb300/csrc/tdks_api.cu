@@ -104,6 +104,8 @@ struct tdks_ctx {
   // large isolated grids (tile kernels): two Horner buffers and the projection coefficients
   bool tiled = false;
   int tile_variant[2] = {0, 0};  // stencil variant of the tiled path for H v / Horner stages
+  int proj_variant = 1;          // FP32 projection schedule of the tiled path (2, 4, 8 warps per CTA)
+  float proj_ms[kProjVariants] = {-1.f, -1.f, -1.f};   // its tuning times (-1: not timed)
   long long wait_limit = 1LL << 22;  // polls per device-side wait of the tile kernels
   int stop_after = -1;              // timeout test: planes the tile producer issues (-1: all)
   float tile_ms[2][kTileVariants] = {{-1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f},
@@ -158,12 +160,26 @@ struct tdks_ctx {
     const void* u = nullptr;
     double dt = 0, thr = 0, mbj_c = 0;
     int mode = -1, lg = -1, has_obs = -1, obs_start = -1, cell_variant = -1, tile0 = -1, tile1 = -1, prof = -1;
+    int proj = -1;
     bool operator==(const StepKey& o) const {
       return u == o.u && dt == o.dt && thr == o.thr && mbj_c == o.mbj_c && mode == o.mode && lg == o.lg &&
              has_obs == o.has_obs && obs_start == o.obs_start && cell_variant == o.cell_variant && tile0 == o.tile0 &&
-             tile1 == o.tile1 && prof == o.prof;
+             tile1 == o.tile1 && prof == o.prof && proj == o.proj;
     }
   } sg_key;
+  // multiscale steps as graphs, one per rotation of the three A levels (c->ms_head), built from the
+  // second tdks_ms_step on (the first runs on the stream)
+  StepGraph msg[3];
+  struct MsKey {
+    const void* u = nullptr;
+    double dt = 0, mbj_c = 0;
+    int cell_variant = -1, tile0 = -1, tile1 = -1, prof = -1;
+    bool operator==(const MsKey& o) const {
+      return u == o.u && dt == o.dt && mbj_c == o.mbj_c && cell_variant == o.cell_variant && tile0 == o.tile0 &&
+             tile1 == o.tile1 && prof == o.prof;
+    }
+  } msg_key;
+  long long ms_steps = 0;        // multiscale steps since tdks_ms_init / tdks_set_state
   long long body_launches = 0;   // launches of the fallback body
   long long body_calls[TDKS_NPHASE] = {0};   // phase calls of the fallback body
   int step_graph = 1;            // predicted steps as step graphs (1) or stream launches with a host decision (0)
@@ -368,6 +384,7 @@ TileArgs<T> make_tile_args(const tdks_ctx* c, const T* V) {
   a.ry = (T)((c->grid.h[0] * c->grid.h[0]) / (c->grid.h[1] * c->grid.h[1]));
   a.rz = (T)((c->grid.h[0] * c->grid.h[0]) / (c->grid.h[2] * c->grid.h[2]));
   a.variant = c->tile_variant[0];
+  a.proj_variant = c->proj_variant;
   a.wait_limit = c->wait_limit;
   a.stop_after = c->stop_after;
   a.err = c->d_err;
@@ -641,6 +658,25 @@ tdks_status tune_tile(tdks_ctx* c) {
       if (err != cudaSuccess) break;
       c->tile_ms[mode][v] = 0.5f * ms;
       if (best < 0.f || c->tile_ms[mode][v] < best) { best = c->tile_ms[mode][v]; c->tile_variant[mode] = v; }
+    }
+  }
+  // the schedule of the FP32 tensor-core projection: 2, 4 or 8 warps per CTA over the sphere points
+  if (is_f32(c) && c->natom > 0) {
+    float best = -1.f;
+    for (int v = 0; v < kProjVariants && err == cudaSuccess; ++v) {
+      TileArgs<float> a = make_tile_args<float>(c, c->d_v32);
+      a.proj_variant = v;
+      err = launch_tile_project<float>(a, static_cast<const float2*>(c->d_bufA), c->stream);
+      if (err == cudaSuccess) err = cudaEventRecord(e0, c->stream);
+      for (int r = 0; r < 3 && err == cudaSuccess; ++r)
+        err = launch_tile_project<float>(a, static_cast<const float2*>(c->d_bufA), c->stream);
+      if (err == cudaSuccess) err = cudaEventRecord(e1, c->stream);
+      if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+      if (err != cudaSuccess) break;
+      c->proj_ms[v] = ms / 3.f;
+      if (best < 0.f || c->proj_ms[v] < best) { best = c->proj_ms[v]; c->proj_variant = v; }
     }
   }
   cudaEventDestroy(e0);
@@ -993,7 +1029,8 @@ void tdks_destroy(tdks_ctx* c) {
   if (c->side) cudaStreamDestroy(c->side);
   for (void* p : c->allocs) cudaFree(p);
   if (c->h_resid) cudaFreeHost(c->h_resid);
-  for (auto& g : c->sg) {
+  for (auto* gs : {&c->sg[0], &c->sg[1], &c->sg[2], &c->sg[3], &c->msg[0], &c->msg[1], &c->msg[2]}) {
+    auto& g = *gs;
     if (g.exec) cudaGraphExecDestroy(g.exec);
     if (g.graph) cudaGraphDestroy(g.graph);
     for (auto& r : g.recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
@@ -1692,8 +1729,7 @@ static tdks_status step_tail(tdks_ctx* c, bool at_start) {
 }
 
 // Add the step-graph timings of the last execution of slot v to the phase times.
-static tdks_status collect_step_graph(tdks_ctx* c, int v) {
-  auto& g = c->sg[v];
+static tdks_status collect_graph(tdks_ctx* c, tdks_ctx::StepGraph& g) {
   if (!g.pending) return TDKS_OK;
   for (auto& r : g.recs) {
     float ms = 0.f;
@@ -1705,16 +1741,24 @@ static tdks_status collect_step_graph(tdks_ctx* c, int v) {
   return TDKS_OK;
 }
 
+static tdks_status collect_step_graph(tdks_ctx* c, int v) { return collect_graph(c, c->sg[v]); }
+
+static void drop_graph(tdks_ctx* c, tdks_ctx::StepGraph& g) {
+  collect_graph(c, g);
+  if (g.exec) cudaGraphExecDestroy(g.exec);
+  if (g.graph) cudaGraphDestroy(g.graph);
+  for (auto& r : g.recs) { c->event_pool.push_back(r.a); c->event_pool.push_back(r.b); }
+  g = tdks_ctx::StepGraph{};
+}
+
 static void drop_step_graphs(tdks_ctx* c) {
   cudaStreamSynchronize(c->stream);
-  for (int v = 0; v < 4; ++v) {
-    auto& g = c->sg[v];
-    collect_step_graph(c, v);
-    if (g.exec) cudaGraphExecDestroy(g.exec);
-    if (g.graph) cudaGraphDestroy(g.graph);
-    for (auto& r : g.recs) { c->event_pool.push_back(r.a); c->event_pool.push_back(r.b); }
-    g = tdks_ctx::StepGraph{};
-  }
+  for (int v = 0; v < 4; ++v) drop_graph(c, c->sg[v]);
+}
+
+static void drop_ms_graphs(tdks_ctx* c) {
+  cudaStreamSynchronize(c->stream);
+  for (int v = 0; v < 3; ++v) drop_graph(c, c->msg[v]);
 }
 
 // Capture the step graph of history slot v = c->hist_head (see tdks_ctx::StepGraph).
@@ -1845,6 +1889,7 @@ static tdks_status predicted_step(tdks_ctx* c, void* u, const double Amid[3], co
   key.lg = c->longitudinal ? 1 : 0; key.has_obs = Aobs ? 1 : 0; key.obs_start = obs_start ? 1 : 0;
   key.cell_variant = c->cell_variant; key.tile0 = c->tile_variant[0]; key.tile1 = c->tile_variant[1];
   key.prof = c->profiling ? (c->prof_stencil_only ? 2 : 1) : 0;
+  key.proj = c->proj_variant;
   if (!(key == c->sg_key)) {
     drop_step_graphs(c);
     c->sg_key = key;
@@ -1935,6 +1980,8 @@ tdks_status tdks_ms_init(tdks_ctx* c, int nX, int m0, double dX, const double* A
       TDKS_TRY(dalloc(c, &c->d_ap_end, 3 * (size_t)c->ncell));
     }
   }
+  drop_ms_graphs(c);
+  c->ms_steps = 0;
   c->nX = nX; c->m0 = m0; c->dX = dX; c->ms_head = 0;
   TDKS_CUDA(cudaMemcpyAsync(c->d_A[0], A_now, nX * sizeof(double), cudaMemcpyHostToDevice, c->stream));
   TDKS_CUDA(cudaMemcpyAsync(c->d_A[2], A_prev, nX * sizeof(double), cudaMemcpyHostToDevice, c->stream));
@@ -1944,13 +1991,10 @@ tdks_status tdks_ms_init(tdks_ctx* c, int nX, int m0, double dX, const double* A
   return TDKS_OK;
 }
 
-tdks_status tdks_ms_step(tdks_ctx* c, void* u, double t, double dt) {
-  TDKS_TRY(check_ctx(c));
-  TDKS_TRY(check_whole_set(c, "tdks_ms_step"));
-  if (!u) return fail(TDKS_EINVAL, "null orbitals");
-  if (!c->ms_ready) return fail(TDKS_EINVAL, "call tdks_ms_init first");
-  if (!c->have_potential) return fail(TDKS_EINVAL, "call tdks_update_potential before tdks_ms_step");
-  (void)t;
+// One coupled multiscale step on c->stream: the Maxwell update of the macroscopic grid (A' of every
+// cell at the half and full step), the predictor-corrector step of all cells with their own A', and
+// the currents back to the grid.  Reads the three A levels selected by c->ms_head.
+static tdks_status ms_step_body(tdks_ctx* c, void* u, double dt) {
   const double cl = 137.035999084;
   const int h = c->ms_head;
   double* Aprev = c->d_A[(h + 2) % 3];
@@ -1973,6 +2017,73 @@ tdks_status tdks_ms_step(tdks_ctx* c, void* u, double t, double dt) {
                                   c->d_step_obs, c->stream, c->ncell));
   TDKS_CUDA(launch_ms_current(c->d_step_obs, c->ncell, c->m0, c->d_I, c->stream));
   c->launches += 2;
+  return TDKS_OK;
+}
+
+// Capture ms_step_body for the current c->ms_head into c->msg[c->ms_head].
+static tdks_status build_ms_graph(tdks_ctx* c, void* u, double dt) {
+  auto& g = c->msg[c->ms_head];
+  if (!c->cap) TDKS_CUDA(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+  const cudaStream_t main = c->stream;
+  const long long launches0 = c->launches;
+  long long calls0[TDKS_NPHASE];
+  std::memcpy(calls0, c->calls, sizeof(calls0));
+  c->stream = c->cap;
+  c->cap_recs = c->profiling ? &g.recs : nullptr;
+  tdks_status st = TDKS_OK;
+  cudaError_t e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) {
+    st = ms_step_body(c, u, dt);
+    const cudaError_t e2 = cudaStreamEndCapture(c->cap, &g.graph);
+    if (e == cudaSuccess) e = e2;
+  }
+  g.launches = c->launches - launches0;
+  for (int p = 0; p < TDKS_NPHASE; ++p) g.calls[p] = c->calls[p] - calls0[p];
+  c->launches = launches0;
+  std::memcpy(c->calls, calls0, sizeof(calls0));
+  c->stream = main;
+  c->cap_recs = nullptr;
+  if (e == cudaSuccess && st == TDKS_OK) e = cudaGraphInstantiate(&g.exec, g.graph, 0);
+  if (e != cudaSuccess || st != TDKS_OK) {
+    cudaGetLastError();
+    if (g.graph) cudaGraphDestroy(g.graph);
+    for (auto& r : g.recs) { c->event_pool.push_back(r.a); c->event_pool.push_back(r.b); }
+    g = tdks_ctx::StepGraph{};
+    if (st != TDKS_OK) return st;
+    return fail(TDKS_ECUDA, std::string("capture of the multiscale step: ") + cudaGetErrorString(e));
+  }
+  return TDKS_OK;
+}
+
+tdks_status tdks_ms_step(tdks_ctx* c, void* u, double t, double dt) {
+  TDKS_TRY(check_ctx(c));
+  TDKS_TRY(check_whole_set(c, "tdks_ms_step"));
+  if (!u) return fail(TDKS_EINVAL, "null orbitals");
+  if (!c->ms_ready) return fail(TDKS_EINVAL, "call tdks_ms_init first");
+  if (!c->have_potential) return fail(TDKS_EINVAL, "call tdks_update_potential before tdks_ms_step");
+  (void)t;
+  const int h = c->ms_head;
+  if (c->step_graph && c->ms_steps > 0) {
+    // a replay of the step's graph: one launch, no host work between the kernels
+    tdks_ctx::MsKey key;
+    key.u = u; key.dt = dt; key.mbj_c = c->mbj_c_fixed; key.cell_variant = c->cell_variant;
+    key.tile0 = c->tile_variant[0]; key.tile1 = c->tile_variant[1];
+    key.prof = c->profiling ? (c->prof_stencil_only ? 2 : 1) : 0;
+    if (!(key == c->msg_key)) {
+      drop_ms_graphs(c);
+      c->msg_key = key;
+    }
+    auto& g = c->msg[h];
+    if (!g.exec) TDKS_TRY(build_ms_graph(c, u, dt));
+    TDKS_TRY(collect_graph(c, g));
+    TDKS_CUDA(cudaGraphLaunch(g.exec, c->stream));
+    g.pending = c->profiling;
+    c->launches += g.launches;
+    for (int p = 0; p < TDKS_NPHASE; ++p) c->calls[p] += g.calls[p];
+  } else {
+    TDKS_TRY(ms_step_body(c, u, dt));
+  }
+  c->ms_steps += 1;
   c->ms_head = (h + 1) % 3;
   return TDKS_OK;
 }
@@ -2130,7 +2241,10 @@ tdks_status tdks_check(tdks_ctx* c) {
 tdks_status tdks_set_step_graph(tdks_ctx* c, int enable) {
   TDKS_TRY(check_ctx(c));
   if (enable != 0 && enable != 1) return fail(TDKS_EINVAL, "enable must be 0 or 1");
-  if (!enable) drop_step_graphs(c);
+  if (!enable) {
+    drop_step_graphs(c);
+    drop_ms_graphs(c);
+  }
   c->step_graph = enable;
   return TDKS_OK;
 }
@@ -2308,6 +2422,7 @@ tdks_status tdks_stats_read(tdks_ctx* c, tdks_stats* out, int reset) {
   if (!out) return fail(TDKS_EINVAL, "null output");
   TDKS_TRY(sync_fallbacks(c));
   for (int v = 0; v < 4; ++v) TDKS_TRY(collect_step_graph(c, v));
+  for (int v = 0; v < 3; ++v) TDKS_TRY(collect_graph(c, c->msg[v]));
   for (auto& r : c->recs) {
     float ms = 0.0f;
     TDKS_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
@@ -2322,6 +2437,18 @@ tdks_status tdks_stats_read(tdks_ctx* c, tdks_stats* out, int reset) {
     c->launches = 0;
     for (int p = 0; p < TDKS_NPHASE; ++p) { c->calls[p] = 0; c->ms[p] = 0.0; }
   }
+  return TDKS_OK;
+}
+
+tdks_status tdks_project_variant(tdks_ctx* c, int set, int* variant, float* tune_ms) {
+  TDKS_TRY(check_ctx(c));
+  if (set < -1 || set >= kProjVariants) return fail(TDKS_EINVAL, "projection schedule outside -1..2");
+  if (!c->tiled || !is_f32(c))
+    return fail(TDKS_EUNSUPPORTED, "the projection schedules belong to the FP32 tile kernels");
+  if (set >= 0) c->proj_variant = set;
+  if (variant) *variant = c->proj_variant;
+  if (tune_ms)
+    for (int v = 0; v < kProjVariants; ++v) tune_ms[v] = c->proj_ms[v];
   return TDKS_OK;
 }
 
@@ -2526,6 +2653,8 @@ tdks_status tdks_set_state(tdks_ctx* c, const void* host, size_t bytes) {
   }
   c->longitudinal = h.longitudinal; c->lg_first = h.lg_first;
   c->ms_ready = h.ms_ready; c->nX = h.nX; c->m0 = h.m0; c->ms_head = h.ms_head; c->dX = h.dX;
+  drop_ms_graphs(c);
+  c->ms_steps = 0;
   // the step potential follows from V_Hxc at the next step; the observables buffer is reset
   TDKS_CUDA(cudaMemsetAsync(c->d_step_obs, 0, 8 * sizeof(double) * c->ncell, c->stream));
   if (h.longitudinal)   // the current the next leapfrog step of A'_ind reads

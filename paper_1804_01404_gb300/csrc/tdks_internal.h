@@ -149,6 +149,7 @@ struct TileArgs {
   long long wait_limit;     // polls per mbarrier wait before giving up (TDKS_ETIMEOUT)
   int stop_after;           // >= 0: the producer issues only this many planes (timeout test)
   int variant;              // stencil variant (kernel + L2 prefetch), see launch_tile_stage
+  int proj_variant;         // FP32 projection schedule: 0, 1, 2 = 2, 4, 8 warps per CTA
   int prefetch;             // L2 prefetch distance in planes (set by launch_tile_stage)
   // projectors (q = 0)
   int natom, nsp;
@@ -165,6 +166,7 @@ struct TileArgs {
 };
 bool tile_supported(int nx, int ny, int nz, int elem_bytes);
 constexpr int kTileVariants = 7;
+constexpr int kProjVariants = 3;
 // whether a tile variant applies to rows of nx points of elem_bytes-byte complex values
 bool tile_variant_ok(int variant, int nx, int elem_bytes);
 // local part of one stage: mode 0 out = H_loc vin, mode 1 out = psi + (-i coef) H_loc vin

@@ -121,6 +121,7 @@ def load_library(path: str = LIB_PATH):
         "tdks_query": [vp, C.POINTER(i), C.POINTER(i), C.POINTER(i), C.POINTER(i), C.POINTER(i)],
         "tdks_tile_variant": [vp, i, C.POINTER(i), C.POINTER(C.c_float)],
         "tdks_cell_variant": [vp, i, C.POINTER(i), C.POINTER(C.c_float)],
+        "tdks_project_variant": [vp, i, C.POINTER(i), C.POINTER(C.c_float)],
         "tdks_set_wait_test": [vp, C.c_longlong, i],
         "tdks_state_size": [vp, C.POINTER(C.c_size_t)],
         "tdks_ms_size": [vp, C.POINTER(i)],
@@ -479,8 +480,8 @@ class Context:
         _check(self.lib.tdks_set_predictor(self.ctx, int(mode), float(threshold)))
 
     def set_step_graph(self, enable=True):
-        """Predicted steps as CUDA graphs with the decision on the device (default) or as stream launches
-        with the decision on the host (tdks_set_step_graph)."""
+        """Predicted and multiscale steps as CUDA graphs (default; a predicted step decides on the device)
+        or as stream launches (a predicted step decides on the host) (tdks_set_step_graph)."""
         _check(self.lib.tdks_set_step_graph(self.ctx, int(bool(enable))))
 
     def nn_init(self, seed=0):
@@ -531,6 +532,14 @@ class Context:
         ms = (C.c_float * 14)()
         _check(self.lib.tdks_tile_variant(self.ctx, int(set), v, ms))
         return [v[0], v[1]], [[float(x) for x in ms[:7]], [float(x) for x in ms[7:]]]
+
+    def project_variant(self, set=-1):
+        """Schedule of the FP32 tensor-core projections of the tile path (tdks_project_variant): returns
+        (schedule in use, tuning ms [2, 4, 8 warps per CTA])."""
+        v = C.c_int()
+        ms = (C.c_float * 3)()
+        _check(self.lib.tdks_project_variant(self.ctx, int(set), C.byref(v), ms))
+        return v.value, [float(x) for x in ms]
 
     def cell_variant(self, set=-1):
         """Buffer scheme of the cell kernels' Taylor launches (tdks_cell_variant): returns (scheme in

@@ -217,19 +217,20 @@ def test_taylor_step_built_in_geometry(name, precision, tol):
     assert _rel(out[1].astype(np.complex128), out[0].astype(np.complex128)) < (1e-14 if precision == "f64" else 1e-6)
 
 
+@pytest.mark.parametrize("precision,tol_u,tol_o", [("f64", 1e-11, 1e-10), ("f32", 2e-5, 1e-4)])
 @pytest.mark.parametrize("at_start", [False, True])
-def test_pc_steps_built_in_geometry(at_start):
-    """Five predictor-corrector steps (FP64) of the small periodic cell with scheme 2: orbitals, J(t)
-    and d(t) against the oracle, with the observables from the end-of-step pass or from the first
-    stage."""
+def test_pc_steps_built_in_geometry(at_start, precision, tol_u, tol_o):
+    """Five predictor-corrector steps of the small periodic cell with scheme 2: orbitals, J(t) and
+    d(t) against the oracle, with the observables from the end-of-step pass or from the first stage
+    (FP32: two points per thread in the stages and in the final pass)."""
     from paper_1804_01404_gb300.tdks import Context
     s = GEOM_SYSTEMS["periodic-16^3"]
     psi0 = W.initial_orbitals(s, 5)
     n = 5
     ref, _, hist = O.run(s, psi0, n)
-    ctx = Context(s, precision="f64", obs_at_start=at_start)
+    ctx = Context(s, precision=precision, obs_at_start=at_start)
     ctx.cell_variant(2)
-    u = _dev(psi0, "f64")
+    u = _dev(psi0, precision)
     ctx.update_potential(u)
     J, d = [], []
     t = 0.0
@@ -241,9 +242,9 @@ def test_pc_steps_built_in_geometry(at_start):
         d.append(o["dipole"])
     ctx.check()
     J, d = np.array(J), np.array(d)
-    assert _rel(u.cpu().numpy(), ref) < 1e-11
+    assert _rel(u.cpu().numpy().astype(np.complex128), ref) < tol_u
     Jref, dref = hist["J"], hist["d"]
     if at_start:       # step n reports the state it started from: the oracle's record of step n-1
         J, Jref, d, dref = J[1:], Jref[:-1], d[1:], dref[:-1]
-    assert np.max(np.abs(d - dref)) <= 1e-10 * max(np.max(np.abs(dref)), 1e-30)
-    assert np.max(np.abs(J - Jref)) < 1e-10 * np.max(np.abs(Jref))
+    assert np.max(np.abs(d - dref)) <= tol_o * max(np.max(np.abs(dref)), 1e-30)
+    assert np.max(np.abs(J - Jref)) < tol_o * np.max(np.abs(Jref))

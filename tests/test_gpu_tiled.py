@@ -132,6 +132,37 @@ def test_tiled_variants_hpsi_and_taylor(precision, variant):
         assert _rel(ud.cpu().numpy()[b].astype(np.complex128), ref) < tol
 
 
+@pytest.mark.parametrize("schedule", [0, 1, 2])
+def test_projection_schedules(schedule):
+    """The three schedules of the FP32 tensor-core projection (2, 4, 8 warps per CTA over the sphere
+    points) give H u and a Taylor step within the FP32 bound of the oracle; all three are timed at
+    init and the fastest is kept; FP64 contexts (CUDA-core projection) refuse the call."""
+    from paper_1804_01404_gb300.tdks import TdksError
+    psi = W.initial_orbitals(S, 7)
+    ctx = _ctx(S, "f32")
+    v0, ms = ctx.project_variant()
+    assert min(ms) > 0 and ms[v0] == min(ms)
+    assert ctx.project_variant(schedule)[0] == schedule
+    ctx.update_potential(_dev(psi, "f32"))
+    ud = _dev(psi, "f32")
+    hu = torch.empty_like(ud)
+    ctx.hpsi(ud, hu)
+    tabs = O.projector_tables(S)
+    V = O.local_potential(S) + O.hxc(S, O.density(S, psi))
+    for b in range(psi.shape[0]):
+        ref = O.hpsi(S, tabs, V, np.zeros(3), psi[b])
+        assert _rel(hu.cpu().numpy()[b].astype(np.complex128), ref) < 2e-5
+    ctx.taylor_step(ud, 0.02)
+    ctx.check()
+    for b in range(psi.shape[0]):
+        ref = O.taylor4(S, tabs, V, np.zeros(3), psi[b], 0.02)
+        assert _rel(ud.cpu().numpy()[b].astype(np.complex128), ref) < 2e-5
+    with pytest.raises(TdksError):
+        ctx.project_variant(3)
+    with pytest.raises(TdksError):
+        _ctx(S, "f64").project_variant()
+
+
 def test_tile_variant_rules():
     from paper_1804_01404_gb300.tdks import TdksError
     c64 = _ctx(S, "f64")
