@@ -1,11 +1,13 @@
 // Sums over a whole grid of CTAs in one launch.
 //
-// FP64 arithmetic runs at a small fraction of the FP32 rate on this GPU, so a reduction that does
-// its FP64 additions in a single CTA is bound by that one SM.  grid_sum spreads them: every CTA
-// reduces its threads' values (warp shuffles, then one warp), writes them to partials[blockIdx.x],
-// and the CTA that finishes last (an atomic ticket, after a memory fence) adds all CTAs' partials in
-// CTA order -- so the total does not depend on the order in which CTAs ran -- and resets the
-// ticket for the next launch.
+// FP64 arithmetic runs at a small fraction of the FP32 rate on this GPU, and a chain of dependent FP64
+// additions waits on the narrow FP64 pipe at every link, so a reduction keeps its chains short:
+// every CTA reduces its threads' values (warp shuffles, then one thread per value over the warps),
+// writes them to partials[blockIdx.x], and the CTA that finishes last (an atomic ticket, after a
+// memory fence) loads all CTAs' partials at once -- thread t takes CTAs t, t + blockDim.x, ... -- and
+// reduces them the same way.  The grouping of the additions depends only on CTA and thread indices,
+// so the total does not depend on the order in which CTAs ran.  The last CTA resets the ticket for
+// the next launch.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -40,9 +42,18 @@ __device__ __forceinline__ bool grid_sum(const double (&v)[NV], double* partials
   __syncthreads();
   if (!last) return false;
   __threadfence();
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+    double x = 0;
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) x += __ldcg(&partials[(size_t)b * NV + j]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) red[j][warp] = x;
+  }
+  __syncthreads();
   if (threadIdx.x < NV) {
     double x = 0;
-    for (unsigned b = 0; b < gridDim.x; ++b) x += __ldcg(&partials[(size_t)b * NV + threadIdx.x]);
+    for (int w = 0; w < nw; ++w) x += red[threadIdx.x][w];
     tot[threadIdx.x] = x;
   }
   if (threadIdx.x == 0) *ticket = 0u;

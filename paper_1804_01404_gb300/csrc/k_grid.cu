@@ -534,7 +534,8 @@ __global__ void __launch_bounds__(256) k_reduce_current(const double* __restrict
   const double* ob = obs + (size_t)blockIdx.x * tot * 8;   // this block's cell
   out += blockIdx.x * 8;
   if (periodic)
-    for (int o = threadIdx.x; o < tot; o += blockDim.x) {
+#pragma unroll 4
+    for (int o = threadIdx.x; o < tot; o += blockDim.x) {   // unrolled: the loads of 4 orbitals in flight
       const double w = 2.0 * kw[o / norb];
       for (int d = 0; d < 3; ++d) acc[d] += w * (ob[(size_t)o * 8 + 1 + d] + ob[(size_t)o * 8 + 4 + d]);
     }
