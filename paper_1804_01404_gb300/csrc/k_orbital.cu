@@ -83,6 +83,10 @@ __host__ __device__ inline size_t cell_smem_bytes(int nz, int pstride, int nsph,
 // warps-per-scheduler count caps registers at 72), 16 warps for FP64 so that its wider values get
 // 128 registers per thread.
 template <typename T> constexpr int kNTof() { return sizeof(T) == 4 ? 800 : 512; }
+// Column segments: about one per thread in FP32; two per thread in FP64, whose CTA of 16 warps then
+// spreads the FP64 work evenly over the four schedulers of the SM (one segment per column of a
+// 20 x 20 plane leaves one scheduler 3.5 warps of work and the others 3).
+template <typename T> constexpr int kSegThreads() { return sizeof(T) == 4 ? kNTof<T>() : 2 * kNTof<T>(); }
 constexpr size_t kSmemLimit = 220 * 1024;
 // In-place sweep: at most kNTip columns (one thread each); FP32 CTAs are sized for two per SM
 // (72 registers per thread), FP64 CTAs for one.
@@ -199,11 +203,31 @@ __device__ __forceinline__ typename Cplx<T>::type zload(const OrbArgs<T>& a,
 // coefficient, the axes entering through the fixed ratios (c2y = ry c2x, d1y = ty d1x, ...):
 //   S += c2x[m] (X_m + ry Y_m + rz Z_m),  q.D += d1x[m] (q_x X'_m + ty q_y Y'_m + tz q_z Z'_m)
 // (X_m: x+m plus x-m values, X'_m: their difference), which halves the coefficient registers.
-template <typename T, bool PER, bool WD, typename NB, typename WZ>
+// FMA64 (FP64, periodic, without the per-axis sums): each neighbour pair of axis a and distance m
+// enters as S += c2_a[m] (u+ + u-) - i (q_a d1_a[m]) (u+ - u-), two adds and four FMAs, which leaves
+// 100 FP64 instructions per point instead of 113 (the FP64 pipe bounds these kernels).
+template <typename T, bool PER, bool WD, typename NB, typename WZ, bool FMA64 = true>
 __device__ __forceinline__ typename Cplx<T>::type local_h_at(const OrbArgs<T>& a, NB nb, WZ wz, T diag,
                                                              const T* q, typename Cplx<T>::type* Dout) {
   using C = typename Cplx<T>::type;
   using M = CM<T>;
+  if constexpr (FMA64 && sizeof(T) == 8 && PER && !WD) {
+    C S = M::fma(diag, wz(4), C{0, 0});
+#pragma unroll
+    for (int m = 1; m <= 4; ++m) {
+#pragma unroll
+      for (int ax = 0; ax < 3; ++ax) {
+        const C up = ax == 0 ? nb(2 * (m - 1)) : (ax == 1 ? nb(8 + 2 * (m - 1)) : wz(4 + m));
+        const C um = ax == 0 ? nb(2 * (m - 1) + 1) : (ax == 1 ? nb(8 + 2 * (m - 1) + 1) : wz(4 - m));
+        const T c2 = ax == 0 ? a.c2x[m] : (ax == 1 ? a.c2y[m] : a.c2z[m]);
+        const T b = q[ax] * (ax == 0 ? a.d1x[m - 1] : (ax == 1 ? a.d1y[m - 1] : a.d1z[m - 1]));
+        const T sr = up.x + um.x, si = up.y + um.y, dr = up.x - um.x, di = up.y - um.y;
+        S.x = fma(b, di, fma(c2, sr, S.x));
+        S.y = fma(-b, dr, fma(c2, si, S.y));
+      }
+    }
+    return S;
+  }
   if (WD) {
     // independent accumulators per axis keep the FMA chains short
     C Sx = M::fma(diag, wz(4), C{0, 0}), Sy = C{0, 0}, Sz = C{0, 0};
@@ -244,16 +268,16 @@ __device__ __forceinline__ typename Cplx<T>::type local_h_at(const OrbArgs<T>& a
 
 // local_h_at for a column: in-plane neighbours at the column's precomputed offsets in plane zb,
 // z-values from the window w.
-template <typename T, bool PER, bool WD>
+template <typename T, bool PER, bool WD, bool FMA64 = true>
 __device__ __forceinline__ typename Cplx<T>::type local_h(const OrbArgs<T>& a,
                                                           const Column<T, PER>& c,
                                                           const typename Cplx<T>::type* v,
                                                           const typename Cplx<T>::type* w, int zb,
                                                           T diag, const T* q,
                                                           typename Cplx<T>::type* Dout) {
-  return local_h_at<T, PER, WD>(
-      a, [&](int j) { return v[zb + (j < 8 ? c.ix[j] : c.iy[j - 8])]; }, [&](int j) { return w[j]; }, diag, q,
-      Dout);
+  auto nb = [&](int j) { return v[zb + (j < 8 ? c.ix[j] : c.iy[j - 8])]; };
+  auto wz = [&](int j) { return w[j]; };
+  return local_h_at<T, PER, WD, decltype(nb), decltype(wz), FMA64>(a, nb, wz, diag, q, Dout);
 }
 
 // Projections from the shared-memory tables (fixed geometries): as project(), with beta_ip and the
@@ -327,7 +351,7 @@ template <> struct Geom<2> { static constexpr int NX = 16, NY = 16, NZ = 16; };
 template <typename T, int GEOM>
 struct GeomT {
   static constexpr int NX = Geom<GEOM>::NX, NY = Geom<GEOM>::NY, NZ = Geom<GEOM>::NZ, NXY = NX * NY;
-  static constexpr int S0 = kNTof<T>() / NXY;
+  static constexpr int S0 = kSegThreads<T>() / NXY;
   static constexpr int S = S0 < 1 ? 1 : (S0 > NZ ? NZ : S0);
   static constexpr int ZL = (NZ + S - 1) / S;
   static constexpr int NSEG = (NZ + ZL - 1) / ZL;
@@ -941,7 +965,8 @@ __global__ void __launch_bounds__(kMaxThreads<T, IP, GEOM>(), kMinBlocks<T, IP>(
               pnext = psi[pg + nxy];
             }
             C Dd[3];
-            const C hv = local_h<T, PER, ACC && PER>(a, c, L.v, w, zb, diag, q, Dd);
+            // (the in-place sweep keeps the separate Laplacian and derivative sums: fewer registers)
+            const C hv = local_h<T, PER, ACC && PER, false>(a, c, L.v, w, zb, diag, q, Dd);
             if (ACC) {
               const C u0 = w[4];
               os[0] += u0.x * u0.x + u0.y * u0.y;
@@ -1238,7 +1263,7 @@ bool smem_orbital_needs_scratch(int nz, int pstride, int nsph, int natom) {
 
 void cell_split(int nx, int ny, int nz, int elem_bytes, int* nseg, int* zlen) {
   const int ncol = nx * ny;
-  int s = (elem_bytes == 8 ? kNTof<float>() : kNTof<double>()) / ncol;
+  int s = (elem_bytes == 8 ? kSegThreads<float>() : kSegThreads<double>()) / ncol;
   if (s < 1) s = 1;
   if (s > nz) s = nz;
   *zlen = (nz + s - 1) / s;
