@@ -393,6 +393,9 @@ struct FusedArgs {
   NNGrid g;
   const double *V0, *V1, *V2, *V3;
   double* vpred;
+  const double *vloc, *vhxc; // optional: the corrector's step potential from V~ (see NNPredict)
+  double* vstep64;
+  float* vstep32;
   const uint4* wpack;        // FusedWeights image of the BF16-rounded parameters
   bf16 *x0, *a1, *a2;        // channel-last [npts][4], [npts][16], [npts][16]
   double* stats;             // out: s1, s2, s3, mean V0, s_V
@@ -718,7 +721,17 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_nn_predict(FusedArgs A) {
     }
     acc += __shfl_xor_sync(0xffffffffu, acc, 1);
     acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-    if (act && cs == 0) A.vpred[p] = cubic(A.V0[p], A.V1[p], A.V2[p], A.V3[p]) + s3 * (double)acc;
+    if (act && cs == 0) {
+      const double vp = cubic(A.V0[p], A.V1[p], A.V2[p], A.V3[p]) + s3 * (double)acc;
+      A.vpred[p] = vp;
+      if (A.vstep64) {                             // V_loc + (V_Hxc(t) + V~)/2, as k_combine forms it
+        double v = A.vloc[p];
+        v += 0.5 * A.vhxc[p];
+        v += 0.5 * vp;
+        A.vstep64[p] = v;
+        if (A.vstep32) A.vstep32[p] = (float)v;
+      }
+    }
   }
 }
 
@@ -822,7 +835,7 @@ cudaError_t nn_predict_fused(const NNBuffers& B, const NNGrid& g, const NNPredic
   if (nb > kFusedMaxBlocks) nb = kFusedMaxBlocks;
   if (nb > want) nb = want;
   if (nb < 1) nb = 1;
-  FusedArgs A{g, pr.V0, pr.V1, pr.V2, pr.V3, pr.vpred, B.wpack,
+  FusedArgs A{g, pr.V0, pr.V1, pr.V2, pr.V3, pr.vpred, pr.vloc, pr.vhxc, pr.vstep64, pr.vstep32, B.wpack,
               B16(B.x0), B16(B.a1), B16(B.a2), B.stats, B.red, 1.0 / (double)g.npts, B.bar, B.err, wait_limit};
   void* args[] = {&A};
   return cudaLaunchCooperativeKernel((const void*)k_nn_predict, dim3((unsigned)nb), dim3(kFusedThreads), args, 0, s);

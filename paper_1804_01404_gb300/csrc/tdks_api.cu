@@ -359,6 +359,10 @@ struct Phase {
 };
 
 // V used by the next orbital kernel: V_loc + a * V_Hxc + b * V_pred
+// Whether the density of an orbital kernel is written whole (FP32 cell kernels: per-k partials folded
+// into rho) rather than accumulated into a zeroed rho (FP64 atomics, the tile path).
+bool rho_overwritten(const tdks_ctx* c) { return is_f32(c) && !c->tiled; }
+
 tdks_status set_step_potential(tdks_ctx* c, double a, const double* v2, double b) {
   Phase ph(c, 5);
   TDKS_CUDA(launch_combine_potential(c->d_vloc, c->d_vhxc, a, v2, b, c->d_v64,
@@ -470,7 +474,8 @@ tdks_status orbital_kernel(tdks_ctx* c, int mode, const void* in, void* out, con
   if (is_f32(c)) {
     auto a = make_args<float>(c, in, out, c->d_v32, Ap, dt, rho, write_out);
     if (rho) {
-      // per-k FP32 partial densities, folded into rho in FP64 afterwards
+      // per-k FP32 partial densities, folded into rho in FP64 afterwards (a memset here costs less
+      // in a step than zeroing them in the fold kernel, measured)
       TDKS_CUDA(cudaMemsetAsync(c->d_rho32, 0, sizeof(float) * (size_t)c->ncell * c->nk * c->npts, c->stream));
       a.rho = nullptr;
       a.rho32 = c->d_rho32;
@@ -1627,7 +1632,7 @@ tdks_status pc_step(tdks_ctx* c, void* u, const double Amid[3], const double* Ao
   if (pc) {
     // predictor: T4 with V(t); only its density is kept
     TDKS_TRY(set_step_potential(c, 1.0, nullptr, 0.0));
-    {
+    if (!rho_overwritten(c)) {
       Phase ph(c, 5);
       TDKS_CUDA(cudaMemsetAsync(c->d_rho_tmp, 0, gb, c->stream));
     }
@@ -1641,7 +1646,7 @@ tdks_status pc_step(tdks_ctx* c, void* u, const double Amid[3], const double* Ao
   } else {
     TDKS_TRY(set_step_potential(c, 1.0, nullptr, 0.0));
   }
-  {
+  if (!rho_overwritten(c)) {
     Phase ph(c, 5);
     TDKS_CUDA(cudaMemsetAsync(c->d_rho, 0, gb, c->stream));
   }
@@ -1680,12 +1685,17 @@ static tdks_status predicted_main(tdks_ctx* c, void* u, const double Amid[3], do
   const size_t gb = c->npts * sizeof(double);
   const size_t obytes = (size_t)c->nk * c->norb * c->npts * (is_f32(c) ? sizeof(float2) : sizeof(double2));
   const NNGrid g = nn_grid(c);
+  bool step_pot_done = false;
   {
     Phase ph(c, 5);
     if (c->pred_mode == TDKS_PRED_LEARNED) {   // statistics, inputs and the three layers: one launch
-      const NNPredict pr{hist_slot(c, 0), hist_slot(c, 1), hist_slot(c, 2), hist_slot(c, 3), c->d_vpred};
+      NNPredict pr{hist_slot(c, 0), hist_slot(c, 1), hist_slot(c, 2), hist_slot(c, 3), c->d_vpred};
+      if (c->ncell == 1) {   // the corrector's step potential too (what set_step_potential forms)
+        pr.vloc = c->d_vloc; pr.vhxc = c->d_vhxc; pr.vstep64 = c->d_v64; pr.vstep32 = is_f32(c) ? c->d_v32 : nullptr;
+      }
       TDKS_CUDA(nn_predict_fused(c->nn, g, pr, c->wait_limit, c->stream));
       c->launches += 1;
+      step_pot_done = c->ncell == 1;
     } else {
       TDKS_CUDA(nn_apply(c->nn, g, hist_slot(c, 0), hist_slot(c, 1), hist_slot(c, 2), hist_slot(c, 3), 1,
                          c->d_vpred, c->stream));
@@ -1694,9 +1704,9 @@ static tdks_status predicted_main(tdks_ctx* c, void* u, const double Amid[3], do
     // the shared-memory cell kernel writes the backup while it loads the orbitals; the tile path
     // copies it first
     if (c->tiled) TDKS_CUDA(cudaMemcpyAsync(c->d_backup, u, obytes, cudaMemcpyDeviceToDevice, c->stream));
-    TDKS_CUDA(cudaMemsetAsync(c->d_rho, 0, gb, c->stream));
+    if (!rho_overwritten(c)) TDKS_CUDA(cudaMemsetAsync(c->d_rho, 0, gb, c->stream));
   }
-  TDKS_TRY(set_step_potential(c, 0.5, c->d_vpred, 0.5));
+  if (!step_pot_done) TDKS_TRY(set_step_potential(c, 0.5, c->d_vpred, 0.5));
   c->cur_backup = c->tiled ? nullptr : c->d_backup;
   const tdks_status cs = orbital_kernel(c, 1, u, u, Amid, dt, c->d_rho, 1, Aobs, obs_start);
   c->cur_backup = nullptr;

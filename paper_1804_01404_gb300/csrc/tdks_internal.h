@@ -210,6 +210,12 @@ cudaError_t nn_inputs(const NNBuffers& B, const NNGrid& g, const double* V0, con
 struct NNPredict {
   const double *V0, *V1, *V2, *V3;
   double* vpred;
+  // optional (nn_predict_fused): also the corrector's step potential V_loc + (V_Hxc(t) + V~)/2 into
+  // vstep64 and, if not null, its FP32 copy vstep32
+  const double* vloc = nullptr;
+  const double* vhxc = nullptr;
+  double* vstep64 = nullptr;
+  float* vstep32 = nullptr;
 };
 cudaError_t nn_forward(const NNBuffers& B, const NNGrid& g, cudaStream_t s, const NNPredict* pred = nullptr);
 // The prediction V~ = cubic + s3 * NN in one cooperative launch (statistics, inputs and three layers
