@@ -99,7 +99,8 @@ template <typename T, bool IP, int GEOM = 0> constexpr int kMaxThreads() {
 template <typename T, bool IP> constexpr int kMinBlocks() { return (IP && sizeof(T) == 4) ? 2 : 1; }
 
 // Fixed geometries also hold the projector tables of the sphere entries in shared memory: beta_ip
-// (4 values, 16-byte aligned) and the point index with the atom in its upper 16 bits.
+// (4 values, 16-byte aligned) and the point index with the atom in bits 16..30 and, in the sign bit,
+// whether the point lies inside more than one sphere.
 template <typename T>
 __host__ __device__ inline size_t geom_table_offset(int nz, int pstride, int nsph, int natom) {
   return (cell_smem_bytes<T>(nz, pstride, nsph, natom, true) + 15) & ~size_t(15);
@@ -312,7 +313,8 @@ __device__ __forceinline__ void project_tab(const OrbArgs<T>& a, const typename 
 
 // Nonlocal scatter from the shared-memory tables, one sphere entry per thread: entry i of atom a adds
 // conj(ph_i) sum_p beta_ip ec_ap (MODE 0), or -i coef times that (a Horner stage), to the next vector
-// at its point.  Points inside several spheres receive one shared-memory atomic add per entry.
+// at its point.  A point inside one sphere only (tidx >= 0) is updated by a plain read-modify-write;
+// a point inside several (the sign bit of tidx set) receives one shared-memory atomic add per entry.
 template <typename T, int MODE>
 __device__ __forceinline__ void scatter_tab(const OrbArgs<T>& a, const typename Cplx<T>::type* ph,
                                             const typename Cplx<T>::type* ec, const int* tidx,
@@ -320,7 +322,7 @@ __device__ __forceinline__ void scatter_tab(const OrbArgs<T>& a, const typename 
   using C = typename Cplx<T>::type;
   for (int i = threadIdx.x; i < a.nsph; i += blockDim.x) {
     const int pk = tidx[i];
-    const int at = pk >> 16;
+    const int at = (pk >> 16) & 0x7fff;
     const T* b = tbeta + 4 * i;
     T sr = 0, si = 0;
 #pragma unroll
@@ -333,8 +335,15 @@ __device__ __forceinline__ void scatter_tab(const OrbArgs<T>& a, const typename 
     C nl = C{sr * f.x + si * f.y, si * f.x - sr * f.y};
     if (MODE == 1) nl = C{coef * nl.y, -coef * nl.x};
     C* dst = nxt + (pk & 0xffff);
-    atomicAdd(&dst->x, nl.x);
-    atomicAdd(&dst->y, nl.y);
+    if (pk < 0) {
+      atomicAdd(&dst->x, nl.x);
+      atomicAdd(&dst->y, nl.y);
+    } else {
+      C r = *dst;
+      r.x += nl.x;
+      r.y += nl.y;
+      *dst = r;
+    }
   }
 }
 
@@ -891,7 +900,9 @@ __global__ void __launch_bounds__(kMaxThreads<T, IP, GEOM>(), kMinBlocks<T, IP>(
   }
   if constexpr (GEOM != 0) {
     for (int i = threadIdx.x; i < a.nsph; i += blockDim.x) {
-      tidx[i] = a.sph_sidx[i] | (a.ent_atom[i] << 16);
+      const int pg = a.sph_idx[i];                 // periodic cells: the same as the shared-memory index
+      const bool several = a.pt_off[pg + 1] - a.pt_off[pg] > 1;
+      tidx[i] = a.sph_sidx[i] | (a.ent_atom[i] << 16) | (several ? (int)0x80000000u : 0);
 #pragma unroll
       for (int p = 0; p < 4; ++p) tbeta[4 * i + p] = a.sph_beta[4 * i + p];
     }
