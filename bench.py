@@ -655,7 +655,8 @@ def cell_scheme(v):
     if v is None:
         return None
     names = ["two shared-memory copies", "one copy swept in place",
-             "two shared-memory copies, grid size built in (column segments unrolled)"]
+             "two shared-memory copies, grid size built in (column segments unrolled)",
+             "one copy swept in place, grid size built in (two CTAs per SM)"]
     return {"in_use": names[v[0]], "tune_ms": {n: (t if t > 0 else None) for n, t in zip(names, v[1])}}
 
 

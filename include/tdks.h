@@ -44,7 +44,7 @@
 extern "C" {
 #endif
 
-#define TDKS_ABI_VERSION 3
+#define TDKS_ABI_VERSION 4
 
 typedef struct tdks_ctx tdks_ctx;
 
@@ -455,16 +455,17 @@ tdks_status tdks_project_variant(tdks_ctx* ctx, int set, int* variant, float* tu
  * slice when two do not fit), one stage reading one and writing the other; 1 = one copy swept in
  * place plane by plane, one thread per (x, y) column, for planes of at most 448 points -- half the
  * shared memory, so two FP32 CTAs share an SM; 2 = scheme 0 compiled for a fixed grid size (the
- * periodic 20^3 and 16^3 grids), each thread's column segment unrolled over its planes.  The
- * arithmetic per grid point and per projection is the same in all three; the norm and current sums
- * of an orbital are split over the CTA's warps and may add in another order.  At tdks_init a cell
- * context on which scheme 1 or 2 applies times one Taylor launch of each scheme that applies on
- * zeroed orbitals and keeps the fastest.
- *   set       : -1 leaves the choice as it is; 0, 1 or 2 forces that scheme.
+ * periodic 20^3 and 16^3 grids), each thread's column segment unrolled over its planes (FP32: two
+ * x-adjacent points per thread); 3 = scheme 1 compiled for those grids with two points per thread
+ * (FP32 only).  The arithmetic per grid point and per projection is the same in all four; the norm and
+ * current sums of an orbital are split over the CTA's warps and may add in another order.  At
+ * tdks_init a cell context on which scheme 1, 2 or 3 applies times one Taylor launch of each scheme
+ * that applies on zeroed orbitals and keeps the fastest.
+ *   set       : -1 leaves the choice as it is; 0..3 forces that scheme.
  *   variant   : receives the scheme in use (may be NULL).
- *   tune_ms   : receives the 3 tuning times in ms, -1 where not timed (may be NULL).
- * Errors: EUNSUPPORTED if the context uses the tile kernels, or set = 1 or 2 where that scheme does
- * not apply; EINVAL for set outside -1..2. */
+ *   tune_ms   : receives the 4 tuning times in ms, -1 where not timed (may be NULL).
+ * Errors: EUNSUPPORTED if the context uses the tile kernels, or set = 1, 2 or 3 where that scheme
+ * does not apply; EINVAL for set outside -1..3. */
 tdks_status tdks_cell_variant(tdks_ctx* ctx, int set, int* variant, float* tune_ms);
 
 /* Checkpoint and restart of the time stepping (no counterpart in the paper's formulation; the

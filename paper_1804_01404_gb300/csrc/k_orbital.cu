@@ -93,8 +93,11 @@ constexpr size_t kSmemLimit = 220 * 1024;
 constexpr int kNTip = 448;
 // FP32 fixed geometries (GEOM != 0): two x-adjacent points per thread, at most kNTpair threads.
 constexpr int kNTpair = 416;
+// ... and with one copy swept in place (scheme 3): one thread per column pair, at most kNTpairIP, two
+// CTAs per SM.
+constexpr int kNTpairIP = 224;
 template <typename T, bool IP, int GEOM = 0> constexpr int kMaxThreads() {
-  return IP ? kNTip : ((GEOM != 0 && sizeof(T) == 4) ? kNTpair : kNTof<T>());
+  return (GEOM != 0 && sizeof(T) == 4) ? (IP ? kNTpairIP : kNTpair) : (IP ? kNTip : kNTof<T>());
 }
 template <typename T, bool IP> constexpr int kMinBlocks() { return (IP && sizeof(T) == 4) ? 2 : 1; }
 
@@ -102,18 +105,22 @@ template <typename T, bool IP> constexpr int kMinBlocks() { return (IP && sizeof
 // (4 values, 16-byte aligned) and the point index with the atom in bits 16..30 and, in the sign bit,
 // whether the point lies inside more than one sphere.
 template <typename T>
-__host__ __device__ inline size_t geom_table_offset(int nz, int pstride, int nsph, int natom) {
-  return (cell_smem_bytes<T>(nz, pstride, nsph, natom, true) + 15) & ~size_t(15);
-}
-template <typename T>
-inline size_t cell_smem_bytes_geom(int nz, int pstride, int nsph, int natom) {
-  return geom_table_offset<T>(nz, pstride, nsph, natom) + (size_t)nsph * (4 * sizeof(T) + sizeof(int));
-}
-
-template <typename T>
-inline size_t cell_smem_bytes_ip(int nx, int ny, int nz, int pstride, int nsph, int natom, bool periodic) {
+__host__ __device__ inline size_t cell_smem_bytes_ip(int nx, int ny, int nz, int pstride, int nsph, int natom,
+                                                     bool periodic) {
   using C = typename Cplx<T>::type;
   return sizeof(C) * ((size_t)nz * pstride + nsph + 4 * (size_t)natom + (periodic ? 4 * (size_t)nx * ny : 0));
+}
+// ip: after the layout of the in-place sweep (one copy and the saved planes) instead of two copies
+template <typename T>
+__host__ __device__ inline size_t geom_table_offset(int nx, int ny, int nz, int pstride, int nsph, int natom,
+                                                    bool ip) {
+  const size_t base = ip ? cell_smem_bytes_ip<T>(nx, ny, nz, pstride, nsph, natom, true)
+                         : cell_smem_bytes<T>(nz, pstride, nsph, natom, true);
+  return (base + 15) & ~size_t(15);
+}
+template <typename T>
+inline size_t cell_smem_bytes_geom(int nx, int ny, int nz, int pstride, int nsph, int natom, bool ip) {
+  return geom_table_offset<T>(nx, ny, nz, pstride, nsph, natom, ip) + (size_t)nsph * (4 * sizeof(T) + sizeof(int));
 }
 
 // Projections of the shared-memory vector:  ec[a*4+p] = E_p dV sum_i beta_ip ph_i v(idx_i), one warp
@@ -564,6 +571,99 @@ __device__ __forceinline__ void fixed_pair(const OrbArgs<float>& a, int item, un
   }
 }
 
+// One Taylor stage of an FP32 fixed geometry with one copy swept in place (scheme 3): a thread owns
+// the column pair pi (x = 2 pi mod nx even) over all planes, and all threads advance through z
+// together; the result of plane z replaces the input after a barrier, once every thread has read that
+// input plane as a neighbour plane.  The z window keeps the input values of planes z-4 .. z+4 in
+// registers (loaded before they are replaced); the input planes 0..3, which the last planes need as
+// their periodic images, are kept in the side buffer at ssv.  Inactive threads (act = false) take
+// part in the barriers only.
+template <int GEOM, bool ACC>
+__device__ __forceinline__ void fixed_ip_pair(const OrbArgs<float>& a, int pi, bool act, unsigned sv, unsigned ssv,
+                                              const float* __restrict__ Vc, const float2* __restrict__ psi,
+                                              float diag0, const float* q, float coef, float os[5]) {
+  using M = CM<float>;
+  using G = GeomP<GEOM>;
+  constexpr int NX = G::NX, NY = G::NY, NZ = G::NZ, NXY = G::NXY;
+  constexpr unsigned CB = sizeof(float2), PB = NXY * sizeof(float2);
+  const int col = act ? 2 * pi : 0;
+  const int y = col / NX, x = col - y * NX;
+  auto wx = [](int v) { return v < 0 ? v + NX : (v >= NX ? v - NX : v); };
+  auto wy = [](int v) { return v < 0 ? v + NY : (v >= NY ? v - NY : v); };
+  const unsigned xa0 = sv + (unsigned)(y * NX + wx(x - 4)) * CB, xa1 = sv + (unsigned)(y * NX + wx(x - 2)) * CB;
+  const unsigned xa2 = sv + (unsigned)(y * NX + wx(x + 2)) * CB, xa3 = sv + (unsigned)(y * NX + wx(x + 4)) * CB;
+  unsigned ya[8];
+#pragma unroll
+  for (int m = 1; m <= 4; ++m) {
+    ya[2 * (m - 1)] = sv + (unsigned)(wy(y + m) * NX + x) * CB;
+    ya[2 * (m - 1) + 1] = sv + (unsigned)(wy(y - m) * NX + x) * CB;
+  }
+  const unsigned cA = sv + (unsigned)col * CB, sA = ssv + (unsigned)col * CB;
+  float4 w[9];                                       // plane z - 4 + j in w[(z + j) % 9]
+  if (act) {
+#pragma unroll
+    for (int j = 0; j < 9; ++j) w[j] = lds_c2(cA + (unsigned)((j - 4 + NZ) % NZ) * PB);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {                  // input planes 0..3 (8-byte accesses: the side
+      sts_c(sA + (unsigned)j * PB, lo2(w[4 + j])); // buffer is only 8-byte aligned)
+      sts_c(sA + (unsigned)j * PB + CB, hi2(w[4 + j]));
+    }
+  }
+#pragma unroll
+  for (int z = 0; z < NZ; ++z) {
+    float4 rr = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (act) {
+      const unsigned ko = (unsigned)z * PB;
+      const float4 XM4 = lds_c2(xa0 + ko), XM2 = lds_c2(xa1 + ko), XP2 = lds_c2(xa2 + ko), XP4 = lds_c2(xa3 + ko);
+      float4 Y[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) Y[j] = lds_c2(ya[j] + ko);
+      const float4 Wc = w[(z + 4) % 9];
+      const float2 Vv = *reinterpret_cast<const float2*>(Vc + z * NXY + col);
+      auto nbA = [&](int j) -> float2 {
+        switch (j) {
+          case 0: return hi2(Wc);  case 1: return hi2(XM2); case 2: return lo2(XP2); case 3: return lo2(XM2);
+          case 4: return hi2(XP2); case 5: return hi2(XM4); case 6: return lo2(XP4); case 7: return lo2(XM4);
+          default: return lo2(Y[j - 8]);
+        }
+      };
+      auto nbB = [&](int j) -> float2 {
+        switch (j) {
+          case 0: return lo2(XP2); case 1: return lo2(Wc);  case 2: return hi2(XP2); case 3: return hi2(XM2);
+          case 4: return lo2(XP4); case 5: return lo2(XM2); case 6: return hi2(XP4); case 7: return hi2(XM4);
+          default: return hi2(Y[j - 8]);
+        }
+      };
+      float2 DdA[3], DdB[3];
+      const float2 hA = local_h_at<float, true, ACC>(a, nbA, [&](int j) { return lo2(w[(z + j) % 9]); },
+                                                     diag0 + Vv.x, q, DdA);
+      const float2 hB = local_h_at<float, true, ACC>(a, nbB, [&](int j) { return hi2(w[(z + j) % 9]); },
+                                                     diag0 + Vv.y, q, DdB);
+      if (ACC) {
+        const float2 uA = lo2(Wc), uB = hi2(Wc);
+        os[0] += uA.x * uA.x + uA.y * uA.y;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) os[1 + d] += uA.x * DdA[d].y - uA.y * DdA[d].x;
+        os[0] += uB.x * uB.x + uB.y * uB.y;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) os[1 + d] += uB.x * DdB[d].y - uB.y * DdB[d].x;
+      }
+      const float4 P = *reinterpret_cast<const float4*>(psi + z * NXY + col);
+      const float2 rA = M::fma(coef, make_float2(hA.y, -hA.x), lo2(P));   // psi + (-i coef) H v
+      const float2 rB = M::fma(coef, make_float2(hB.y, -hB.x), hi2(P));
+      rr = make_float4(rA.x, rA.y, rB.x, rB.y);
+      // input plane z + 5: not yet replaced below nz; beyond, one of the saved planes 0..3
+      if (z + 5 < NZ) w[z % 9] = lds_c2(cA + (unsigned)(z + 5) * PB);
+      else if (z + 5 - NZ < 4) {
+        const float2 l = lds_c(sA + (unsigned)(z + 5 - NZ) * PB, 0.f), h = lds_c(sA + (unsigned)(z + 5 - NZ) * PB + CB, 0.f);
+        w[z % 9] = make_float4(l.x, l.y, h.x, h.y);
+      }
+    }
+    __syncthreads();                                 // every thread has read input plane z
+    if (act) sts_c2(cA + (unsigned)z * PB, rr);
+  }
+}
+
 // Final pass of an FP32 fixed geometry over one column-pair segment of the propagated vector at
 // shared-memory address sv: writes the orbital (out, nullable), adds 2 |u|^2 to the per-k density
 // partial rho32 (nullable), and with OBS adds |u|^2 and Im(conj(u) D1_a u) (a = x, y, z) to os.
@@ -830,7 +930,8 @@ template <typename T, int MODE, bool PER, bool DBUF, int OBS, bool IP, int GEOM 
 __global__ void __launch_bounds__(kMaxThreads<T, IP, GEOM>(), kMinBlocks<T, IP>())
     k_cell(OrbArgs<T> a, typename Cplx<T>::type* scratch) {
   static_assert(!IP || (MODE == 1 && !DBUF), "the in-place sweep serves the Taylor stages with one buffer");
-  static_assert(GEOM == 0 || (PER && DBUF && !IP && MODE != 2), "fixed geometries: periodic, two copies");
+  static_assert(GEOM == 0 || (PER && (DBUF || IP) && MODE != 2), "fixed geometries: periodic, two copies or in place");
+  static_assert(!(GEOM != 0 && IP) || sizeof(T) == 4, "the fixed in-place sweep is FP32");
   using C = typename Cplx<T>::type;
   using M = CM<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -847,7 +948,7 @@ __global__ void __launch_bounds__(kMaxThreads<T, IP, GEOM>(), kMinBlocks<T, IP>(
   L.ec = L.ph + a.nsph;
   L.sv = L.ec + 4 * a.natom;
   // fixed geometries: projector tables in shared memory (loaded below)
-  T* tbeta = reinterpret_cast<T*>(smem_raw + geom_table_offset<T>(a.nz, ps, a.nsph, a.natom));
+  T* tbeta = reinterpret_cast<T*>(smem_raw + geom_table_offset<T>(a.nx, a.ny, a.nz, ps, a.nsph, a.natom, IP));
   int* tidx = reinterpret_cast<int*>(tbeta + 4 * (size_t)a.nsph);
   const int orb = blockIdx.x;
   const int cell = orb / (a.nk * a.norb);
@@ -935,8 +1036,9 @@ __global__ void __launch_bounds__(kMaxThreads<T, IP, GEOM>(), kMinBlocks<T, IP>(
   for (int st = 0; st < NSTAGE; ++st) {
     if constexpr (GEOM != 0) {
       // the projection only reads the current vector; the scatter that reads ec waits for the
-      // barrier after the local pass
+      // barrier after the local pass (the in-place sweep replaces the vector: it waits here)
       if (a.natom > 0) project_tab<T>(a, L.v, L.ph, tidx, tbeta, L.ec);
+      if (IP) __syncthreads();
     } else if (a.natom > 0) {
       project<T>(a, L.v, L.ph, L.ec);
       __syncthreads();
@@ -946,7 +1048,11 @@ __global__ void __launch_bounds__(kMaxThreads<T, IP, GEOM>(), kMinBlocks<T, IP>(
     // its input (a separate instance of the loop, so the other stages compile as without them)
     auto local_pass = [&](auto acc_tag) {
       constexpr bool ACC = decltype(acc_tag)::value;
-      if constexpr (IP) {
+      if constexpr (IP && GEOM != 0) {
+        const unsigned sv = (unsigned)__cvta_generic_to_shared(L.v), ssv = (unsigned)__cvta_generic_to_shared(L.sv);
+        const int pi = threadIdx.x;
+        fixed_ip_pair<GEOM, ACC && PER>(a, pi, pi < GeomP<GEOM>::NP, sv, ssv, Vc, psi, diag0, q, coef, os);
+      } else if constexpr (IP) {
         const int col = threadIdx.x;
         const bool act = col < nxy;
         const Column<T, PER> c = make_column<T, PER>(a, act ? col : 0);
@@ -1221,7 +1327,7 @@ bool geom_is(const OrbArgs<T>& a) {
   using G = GeomT<T, GEOM>;
   return a.periodic && a.nx == G::NX && a.ny == G::NY && a.nz == G::NZ && a.pstride == G::NXY &&
          a.zlen == G::ZL && a.nseg == G::NSEG && a.natom < 32768 &&
-         cell_smem_bytes_geom<T>(a.nz, a.pstride, a.nsph, a.natom) <= kSmemLimit;
+         cell_smem_bytes_geom<T>(a.nx, a.ny, a.nz, a.pstride, a.nsph, a.natom, false) <= kSmemLimit;
 }
 
 template <typename T>
@@ -1236,7 +1342,7 @@ template <typename T, int OBS>
 cudaError_t dispatch_geom(const OrbArgs<T>& a, cudaStream_t s) {
   const int g = cell_geom<T>(a);
   if (g == 0) return cudaErrorInvalidValue;
-  const size_t smem = cell_smem_bytes_geom<T>(a.nz, a.pstride, a.nsph, a.natom);
+  const size_t smem = cell_smem_bytes_geom<T>(a.nx, a.ny, a.nz, a.pstride, a.nsph, a.natom, false);
   const int items = sizeof(T) == 4 ? (g == 1 ? GeomP<1>::NP * GeomP<1>::NSEG : GeomP<2>::NP * GeomP<2>::NSEG)
                                    : a.nx * a.ny * a.nseg;
   int nt = ((items + 31) / 32) * 32;
@@ -1244,6 +1350,24 @@ cudaError_t dispatch_geom(const OrbArgs<T>& a, cudaStream_t s) {
   if (nt > ntmax) nt = ntmax;
   return g == 1 ? launch_cell<T, 1, true, true, OBS, false, 1>(a, nullptr, smem, nt, s)
                 : launch_cell<T, 1, true, true, OBS, false, 2>(a, nullptr, smem, nt, s);
+}
+
+// Taylor stages of an FP32 built-in geometry swept in place, two points per thread (cell_variant 3).
+template <typename T, int OBS>
+cudaError_t dispatch_geom_ip(const OrbArgs<T>& a, cudaStream_t s) {
+  if constexpr (sizeof(T) != 4) {
+    return cudaErrorInvalidValue;
+  } else {
+    const int g = cell_geom<T>(a);
+    if (g == 0) return cudaErrorInvalidValue;
+    const size_t smem = cell_smem_bytes_geom<T>(a.nx, a.ny, a.nz, a.pstride, a.nsph, a.natom, true);
+    if (smem > kSmemLimit) return cudaErrorInvalidValue;
+    const int np = g == 1 ? GeomP<1>::NP : GeomP<2>::NP;
+    const int nt = ((np + 31) / 32) * 32;
+    if (nt > kNTpairIP) return cudaErrorInvalidValue;
+    return g == 1 ? launch_cell<T, 1, true, false, OBS, true, 1>(a, nullptr, smem, nt, s)
+                  : launch_cell<T, 1, true, false, OBS, true, 2>(a, nullptr, smem, nt, s);
+  }
 }
 
 // Taylor stages with the in-place sweep (cell_variant 1).
@@ -1296,6 +1420,10 @@ cudaError_t launch_smem_orbital(const OrbArgs<T>& a, int mode, typename Cplx<T>:
       if (!a.obs) return dispatch_geom<T, 0>(a, s);
       return a.obs_at_start ? dispatch_geom<T, 2>(a, s) : dispatch_geom<T, 1>(a, s);
     }
+    if (a.cell_variant == 3) {
+      if (!a.obs) return dispatch_geom_ip<T, 0>(a, s);
+      return a.obs_at_start ? dispatch_geom_ip<T, 2>(a, s) : dispatch_geom_ip<T, 1>(a, s);
+    }
     if (!a.obs) return dispatch<T, 1, 0>(a, scratch, s);
     return a.obs_at_start ? dispatch<T, 1, 2>(a, scratch, s) : dispatch<T, 1, 1>(a, scratch, s);
   }
@@ -1310,6 +1438,15 @@ bool smem_orbital_geom_ok(int nx, int ny, int nz, int pstride, int nsph, int nat
   return cell_geom<T>(a) != 0;
 }
 
+template <typename T>
+bool smem_orbital_geom_ip_ok(int nx, int ny, int nz, int pstride, int nsph, int natom, int periodic, int nseg,
+                             int zlen) {
+  if (sizeof(T) != 4 || !smem_orbital_geom_ok<T>(nx, ny, nz, pstride, nsph, natom, periodic, nseg, zlen)) return false;
+  return cell_smem_bytes_geom<T>(nx, ny, nz, pstride, nsph, natom, true) <= kSmemLimit;
+}
+
+template bool smem_orbital_geom_ip_ok<float>(int, int, int, int, int, int, int, int, int);
+template bool smem_orbital_geom_ip_ok<double>(int, int, int, int, int, int, int, int, int);
 template bool smem_orbital_geom_ok<float>(int, int, int, int, int, int, int, int, int);
 template bool smem_orbital_geom_ok<double>(int, int, int, int, int, int, int, int, int);
 template bool smem_orbital_ip_ok<float>(int, int, int, int, int, int, int);

@@ -111,10 +111,10 @@ struct tdks_ctx {
   float tile_ms[2][kTileVariants] = {{-1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f},
                                      {-1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f}};
   int cell_variant = 0;          // Taylor launches of the cell kernels: 0 two buffers, 1 in-place sweep,
-                                 // 2 two buffers with the grid size built in
+                                 // 2 two buffers with the grid size built in, 3 in-place sweep with it
   cudaStream_t side = nullptr;   // tile path: the projections run here beside the stencil
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-  float cell_ms[3] = {-1.f, -1.f, -1.f};  // tuning time of one Taylor launch per variant (-1: not available)
+  float cell_ms[4] = {-1.f, -1.f, -1.f, -1.f};  // tuning time of one Taylor launch per variant (-1: not available)
   void *d_bufA = nullptr, *d_bufB = nullptr, *d_ec = nullptr;
   int* d_err = nullptr;
   bool have_rho0 = false, have_potential = false;
@@ -709,8 +709,20 @@ bool cell_geom_ok(const tdks_ctx* c) {
                                                    c->grid.periodic, c->nseg, c->zlen));
 }
 
+bool cell_geom_ip_ok(const tdks_ctx* c) {
+  const int* n = c->grid.n;
+  return !c->tiled && is_f32(c) &&
+         smem_orbital_geom_ip_ok<float>(n[0], n[1], n[2], c->pstride, c->nsph, c->natom, c->grid.periodic, c->nseg,
+                                        c->zlen);
+}
+
 bool cell_variant_ok(const tdks_ctx* c, int v) {
-  return v == 0 ? !c->tiled : (v == 1 ? cell_ip_ok(c) : cell_geom_ok(c));
+  switch (v) {
+    case 0: return !c->tiled;
+    case 1: return cell_ip_ok(c);
+    case 2: return cell_geom_ok(c);
+    default: return cell_geom_ip_ok(c);
+  }
 }
 
 // Times one Taylor launch of each cell-kernel scheme that applies on zero orbitals -- up to 1216 of
@@ -719,7 +731,7 @@ bool cell_variant_ok(const tdks_ctx* c, int v) {
 // state), no orbital or density output.
 tdks_status tune_cell(tdks_ctx* c) {
   c->cell_variant = 0;
-  c->cell_ms[0] = c->cell_ms[1] = c->cell_ms[2] = -1.f;
+  c->cell_ms[0] = c->cell_ms[1] = c->cell_ms[2] = c->cell_ms[3] = -1.f;
   if (!cell_ip_ok(c) && !cell_geom_ok(c)) return TDKS_OK;
   const int nsub = std::min(c->ncell * c->nk * c->norb, 1216);
   const size_t csz = is_f32(c) ? sizeof(float2) : sizeof(double2);
@@ -733,7 +745,7 @@ tdks_status tune_cell(tdks_ctx* c) {
   if (err == cudaSuccess) err = cudaEventCreate(&e0);
   if (err == cudaSuccess) err = cudaEventCreate(&e1);
   float best = 0.f;
-  for (int v = 0; v < 3 && err == cudaSuccess; ++v) {
+  for (int v = 0; v < 4 && err == cudaSuccess; ++v) {
     if (!cell_variant_ok(c, v)) continue;
     auto run = [&]() -> cudaError_t {
       if (is_f32(c)) {
@@ -2479,17 +2491,20 @@ tdks_status tdks_tile_variant(tdks_ctx* c, int set, int* variant, float* tune_ms
 
 tdks_status tdks_cell_variant(tdks_ctx* c, int set, int* variant, float* tune_ms) {
   TDKS_TRY(check_ctx(c));
-  if (set < -1 || set > 2) return fail(TDKS_EINVAL, "cell variant outside -1..2");
+  if (set < -1 || set > 3) return fail(TDKS_EINVAL, "cell variant outside -1..3");
   if (c->tiled) return fail(TDKS_EUNSUPPORTED, "this context uses the tile kernels");
   if (set == 1 && !cell_ip_ok(c))
     return fail(TDKS_EUNSUPPORTED, "the in-place sweep needs nx * ny <= 448 and one orbital copy in shared memory");
   if (set == 2 && !cell_geom_ok(c))
     return fail(TDKS_EUNSUPPORTED, "the built-in geometries are the periodic 20^3 and 16^3 grids with two "
                                    "orbital copies in shared memory");
+  if (set == 3 && !cell_geom_ip_ok(c))
+    return fail(TDKS_EUNSUPPORTED, "the built-in geometries swept in place are the periodic 20^3 and 16^3 grids "
+                                   "with FP32 orbitals");
   if (set >= 0) c->cell_variant = set;
   if (variant) *variant = c->cell_variant;
   if (tune_ms)
-    for (int v = 0; v < 3; ++v) tune_ms[v] = c->cell_ms[v];
+    for (int v = 0; v < 4; ++v) tune_ms[v] = c->cell_ms[v];
   return TDKS_OK;
 }
 

@@ -109,7 +109,8 @@ struct OrbArgs {
   const double* Ap_cell;    // nullable: [ncell][3] A' per cell, replaces Ap
   const double* Ap_obs_cell;// nullable: [ncell][3], replaces Ap_obs
   int cell_variant;         // Taylor stages: 0 two buffers, 1 one buffer swept in place, 2 two
-                            // buffers with the grid size fixed at compile time (smem_orbital_geom_ok)
+                            // buffers with the grid size fixed at compile time (smem_orbital_geom_ok),
+                            // 3 one buffer swept in place with the grid size fixed (FP32)
 };
 
 // Orbital kernels (k_orbital.cu)
@@ -130,6 +131,10 @@ bool smem_orbital_ip_ok(int nx, int ny, int nz, int pstride, int nsph, int natom
 template <typename T>
 bool smem_orbital_geom_ok(int nx, int ny, int nz, int pstride, int nsph, int natom, int periodic, int nseg,
                           int zlen);
+// Mode 1 with a.cell_variant = 3: the same grids swept in place, FP32 (two CTAs per SM)
+template <typename T>
+bool smem_orbital_geom_ip_ok(int nx, int ny, int nz, int pstride, int nsph, int natom, int periodic, int nseg,
+                             int zlen);
 // column segments of the cell kernels; elem_bytes = bytes of one complex value (8: FP32, 16: FP64)
 void cell_split(int nx, int ny, int nz, int elem_bytes, int* nseg, int* zlen);
 

@@ -543,9 +543,10 @@ class Context:
 
     def cell_variant(self, set=-1):
         """Buffer scheme of the cell kernels' Taylor launches (tdks_cell_variant): returns (scheme in
-        use, tuning ms [two buffers, in-place sweep, two buffers with the grid size built in])."""
+        use, tuning ms [two buffers, in-place sweep, two buffers with the grid size built in, in-place
+        sweep with the grid size built in])."""
         v = C.c_int()
-        ms = (C.c_float * 3)()
+        ms = (C.c_float * 4)()
         _check(self.lib.tdks_cell_variant(self.ctx, int(set), C.byref(v), ms))
         return v.value, [float(x) for x in ms]
 

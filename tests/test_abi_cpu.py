@@ -31,7 +31,7 @@ def test_every_declared_symbol_is_exported(lib):
     assert "tdks_init" in names and "tdks_step" in names and len(names) >= 14
     for n in names:
         assert hasattr(lib, n), n
-    assert lib.tdks_abi_version() == 3
+    assert lib.tdks_abi_version() == 4
 
 
 def _init(lib, s, **kw):

@@ -1,6 +1,7 @@
 """The buffer schemes of the shared-memory cell kernels' Taylor launches (tdks_cell_variant):
 0 = two orbital copies, 1 = one copy swept in place plane by plane, 2 = scheme 0 compiled for the
-periodic 20^3 and 16^3 grids (column segments unrolled over their planes).
+periodic 20^3 and 16^3 grids (column segments unrolled over their planes), 3 = scheme 1 compiled for
+those grids (FP32, two points per thread).
 
 Each scheme is checked against the oracle's 4th-order Taylor step (Eq. taylor) and predictor-corrector
 steps, on periodic and isolated grids, in FP64 and FP32, including the smallest allowed z extent
@@ -152,18 +153,23 @@ def test_multiscale_in_place_scheme(precision, tol):
 
 def test_scheme_selection_and_errors():
     from paper_1804_01404_gb300.tdks import Context, TdksError
-    s = SYSTEMS["diamond-2k"]                       # periodic 20^3: all three schemes apply
+    s = SYSTEMS["diamond-2k"]                       # periodic 20^3: all four schemes apply in FP32
     ctx = Context(s, precision="f32")
     v, ms = ctx.cell_variant()
-    assert v in (0, 1, 2) and min(ms) > 0          # all timed at init; the fastest is kept
+    assert v in (0, 1, 2, 3) and min(ms) > 0       # all timed at init; the fastest is kept
     assert ms[v] == min(ms)
     with pytest.raises(TdksError):
-        ctx.cell_variant(3)
+        ctx.cell_variant(4)
     ctx.close()
+    c64 = Context(s, precision="f64")               # FP64: no scheme 3 (nor 2: two copies do not fit)
+    assert c64.cell_variant()[1][3] == -1.0
+    with pytest.raises(TdksError):
+        c64.cell_variant(3)
+    c64.close()
     t = SYSTEMS["tiny-periodic"]                    # 6 x 7 x 5: no built-in geometry
     ctx = Context(t, precision="f64")
     v, ms = ctx.cell_variant()
-    assert v in (0, 1) and ms[2] == -1.0
+    assert v in (0, 1) and ms[2] == -1.0 and ms[3] == -1.0
     with pytest.raises(TdksError) as ei:
         ctx.cell_variant(2)
     assert "built-in" in str(ei.value)
@@ -171,7 +177,7 @@ def test_scheme_selection_and_errors():
     big = W.isolated_cluster(n=22, natom=4, norb=2, radius=3.8)      # 22 x 22 = 484 columns
     ctx = Context(big, precision="f32")
     v, ms = ctx.cell_variant()
-    assert v == 0 and ms == [-1.0, -1.0, -1.0]
+    assert v == 0 and ms == [-1.0, -1.0, -1.0, -1.0]
     with pytest.raises(TdksError) as ei:
         ctx.cell_variant(1)
     assert "in-place" in str(ei.value)
@@ -184,9 +190,9 @@ GEOM_SYSTEMS = {"diamond-20^3": SYSTEMS["diamond-2k"], "periodic-16^3": W.small_
 @pytest.mark.parametrize("name,precision,tol", [("diamond-20^3", "f32", 2e-5), ("periodic-16^3", "f32", 2e-5),
                                                 ("periodic-16^3", "f64", 1e-12)])
 def test_taylor_step_built_in_geometry(name, precision, tol):
-    """Scheme 2 on the built-in grids (FP32 at 16^3: column segments of 6, 6 and 4 planes) against
-    the oracle's Taylor step, and against scheme 0, whose arithmetic it repeats point by point.  (Two
-    FP64 copies of a 20^3 orbital do not fit in shared memory: scheme 2 is refused there.)"""
+    """Schemes 2 and 3 (FP32) on the built-in grids against the oracle's Taylor step, and against
+    scheme 0, whose arithmetic they repeat point by point.  (Two FP64 copies of a 20^3 orbital do not
+    fit in shared memory: scheme 2 is refused there.)"""
     from paper_1804_01404_gb300.tdks import Context, TdksError
     s = GEOM_SYSTEMS[name]
     if name == "diamond-20^3":
@@ -200,7 +206,8 @@ def test_taylor_step_built_in_geometry(name, precision, tol):
     tabs = O.projector_tables(s)
     V = O.local_potential(s) + O.hxc(s, O.density(s, psi))
     out = []
-    for scheme in (0, 2):
+    schemes = (0, 2, 3) if precision == "f32" else (0, 2)
+    for scheme in schemes:
         ctx = Context(s, precision=precision)
         ctx.cell_variant(scheme)
         assert ctx.cell_variant()[0] == scheme
@@ -214,12 +221,14 @@ def test_taylor_step_built_in_geometry(name, precision, tol):
             ref = O.taylor4(s, tabs, V, np.asarray(s.kpts[k]) + Ap, psi[k], 0.02)
             assert _rel(got[k].astype(np.complex128), ref) < tol, (scheme, k)
         ctx.close()
-    assert _rel(out[1].astype(np.complex128), out[0].astype(np.complex128)) < (1e-14 if precision == "f64" else 1e-6)
+    for o in out[1:]:
+        assert _rel(o.astype(np.complex128), out[0].astype(np.complex128)) < (1e-14 if precision == "f64" else 1e-6)
 
 
-@pytest.mark.parametrize("precision,tol_u,tol_o", [("f64", 1e-11, 1e-10), ("f32", 2e-5, 1e-4)])
+@pytest.mark.parametrize("precision,tol_u,tol_o,scheme", [("f64", 1e-11, 1e-10, 2), ("f32", 2e-5, 1e-4, 2),
+                                                          ("f32", 2e-5, 1e-4, 3)])
 @pytest.mark.parametrize("at_start", [False, True])
-def test_pc_steps_built_in_geometry(at_start, precision, tol_u, tol_o):
+def test_pc_steps_built_in_geometry(at_start, precision, tol_u, tol_o, scheme):
     """Five predictor-corrector steps of the small periodic cell with scheme 2: orbitals, J(t) and
     d(t) against the oracle, with the observables from the end-of-step pass or from the first stage
     (FP32: two points per thread in the stages and in the final pass)."""
@@ -229,7 +238,7 @@ def test_pc_steps_built_in_geometry(at_start, precision, tol_u, tol_o):
     n = 5
     ref, _, hist = O.run(s, psi0, n)
     ctx = Context(s, precision=precision, obs_at_start=at_start)
-    ctx.cell_variant(2)
+    ctx.cell_variant(scheme)
     u = _dev(psi0, precision)
     ctx.update_potential(u)
     J, d = [], []
