@@ -507,8 +507,8 @@ tdks_status tdks_probe_fp32(double* tflops);
 tdks_status tdks_set_wait_test(tdks_ctx* ctx, long long wait_limit, int stop_after);
 
 /* Hartree + exchange potential of a density without allocating device memory.
- * For callers that cannot call cudaMalloc -- code running while a CUDA graph is captured, hosts whose
- * device memory belongs to a pool they do not control, loops that must never allocate -- this
+ * For callers that cannot call cudaMalloc -- hosts whose device memory belongs to a pool they do not
+ * control, loops that must never allocate -- this
  * computes vhxc = V_H[rho] + V_xc[rho] (hartree / xc select the terms, as in tdks_options; xc = 3,
  * TB-mBJ, needs the orbitals and returns TDKS_EINVAL here) for a
  * periodic or isolated grid with the same kernels as tdks_update_potential, using a fixed work area
@@ -517,8 +517,8 @@ tdks_status tdks_set_wait_test(tdks_ctx* ctx, long long wait_limit, int stop_aft
  * [nz][ny][nx] of doubles; stream is a cudaStream_t (NULL = legacy default stream); the call is
  * asynchronous.  Limit: FFT length <= 64 per axis (periodic n <= 64, isolated n <= 32) with prime
  * factors <= 31 and at most 64^3 FFT points; larger grids return TDKS_EUNSUPPORTED.  The first call
- * on each device looks up the work area's device address; make that first call before any stream
- * capture.  All calls share the one work area, so calls that overlap on the GPU race.  The paper
+ * on each device looks up the work area's device address.  All calls share the one work area, so
+ * calls that overlap on the GPU race.  The paper
  * has no counterpart: this is an interface variant of the Hartree/exchange step. */
 tdks_status tdks_hxc_noalloc(const tdks_grid* grid, const double* rho_dev, double* vhxc_dev,
                              int hartree, int xc, void* stream);

@@ -5,10 +5,10 @@
 // cudaMalloc.  Every GPU that loads the library holds the array until the process exits.  Host
 // code cannot pass the array's name to a kernel (on the host that name is only a stand-in), so
 // the first call on each device asks the runtime for the array's device address with
-// cudaGetSymbolAddress and caches it; that first call should therefore come before any stream
-// capture.  The cached address belongs to the device's current context: after cudaDeviceReset the
-// module is loaded again and the array may move, so a process that resets a device must not call this
-// entry point on it again.  All calls share the array: concurrent calls on different streams race.
+// cudaGetSymbolAddress and caches it.  The cached address belongs to the device's current context:
+// after cudaDeviceReset the module is loaded again and the array may move, so a process that resets
+// a device must not call this entry point on it again.  All calls share the array: concurrent calls
+// on different streams race.
 #include <cmath>
 #include <mutex>
 

@@ -1,8 +1,7 @@
 """tdks_hxc_noalloc, the entry point for callers that cannot allocate device memory.
 
-Some callers cannot call cudaMalloc: code that runs while a CUDA graph is being captured (an
-allocation breaks or synchronises the capture), host programs whose device memory is handed out
-by a pool they do not own, and latency-critical loops that must never allocate.  For them the
+Some callers cannot call cudaMalloc: host programs whose device memory is handed out by a pool they
+do not own, and latency-critical loops that must never allocate.  For them the
 library computes the Hartree + exchange potential of a density in a fixed device work area that
 is part of the library image (at most 64^3 FFT points).
 
