@@ -15,7 +15,7 @@
 // rho <= 1e-10 get no mBJ potential.
 //
 // Three launches: k_tau (partial sums of rho, tau, j over chunks of orbitals, one thread per grid
-// point), k_mbj_g (the cell average g and c, one grid_sum; skipped when c is fixed) and k_mbj_x
+// point; k_tau_pair: one thread per two x-adjacent points of FP32 grids with an even nx), k_mbj_g (the cell average g and c, one grid_sum; skipped when c is fixed) and k_mbj_x
 // (folds the chunks, differentiates rho, solves the Becke-Roussel equation and adds v_x to V).
 #include <cuda_runtime.h>
 
@@ -124,6 +124,110 @@ __global__ void __launch_bounds__(kMbjThreads) k_tau(const typename Cplx<T>::typ
   }
 #pragma unroll
   for (int c = 0; c < 5; ++c) part[((size_t)blockIdx.y * 5 + c) * npts + p] = (double)acc[c];
+}
+
+// k_tau for FP32 grids with an even nx: a thread takes two x-adjacent points (x even).  The orbital
+// values of a point pair are one 16-byte load, so the values the two points need -- their centres,
+// x +- 1..4 of both, and y +- 1..4 and z +- 1..4 of the pair -- are 21 loads instead of 50.  With an
+// even nx a neighbour pair is wholly inside or wholly outside an isolated box.  Same sums as k_tau.
+__device__ __forceinline__ float4 ld4_or_zero(const float2* f, int i) {
+  return i >= 0 ? __ldg(reinterpret_cast<const float4*>(f + i)) : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+__global__ void __launch_bounds__(kMbjThreads) k_tau_pair(const float2* __restrict__ u, int nk, int norb, int nx,
+                                                         int ny, int nz, int periodic,
+                                                         const double* __restrict__ kpts,
+                                                         const double* __restrict__ kw, D1h<float> d1, int ochunk,
+                                                         double* __restrict__ part) {
+  const int npts = nx * ny * nz, nxh = nx / 2;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= npts / 2) return;
+  const int ix = 2 * (t % nxh), iy = (t / nxh) % ny, iz = t / (nxh * ny);
+  const int p = (iz * ny + iy) * nx + ix;
+  int ox[4], oy[8], oz[8];                         // neighbour pairs (-1: outside the box)
+  const int dxs[4] = {-4, -2, 2, 4};
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    int jx = ix + dxs[j];
+    bool in = true;
+    if (periodic) jx = jx < 0 ? jx + nx : (jx >= nx ? jx - nx : jx);
+    else in = jx >= 0 && jx < nx;
+    ox[j] = in ? (iz * ny + iy) * nx + jx : -1;
+  }
+#pragma unroll
+  for (int m = 1; m <= 4; ++m) {
+#pragma unroll
+    for (int sgn = 0; sgn < 2; ++sgn) {
+      int jy = sgn == 0 ? iy + m : iy - m, jz = sgn == 0 ? iz + m : iz - m;
+      bool iny = true, inz = true;
+      if (periodic) {
+        jy = jy < 0 ? jy + ny : (jy >= ny ? jy - ny : jy);
+        jz = jz < 0 ? jz + nz : (jz >= nz ? jz - nz : jz);
+      } else {
+        iny = jy >= 0 && jy < ny;
+        inz = jz >= 0 && jz < nz;
+      }
+      oy[2 * (m - 1) + sgn] = iny ? (iz * ny + jy) * nx + ix : -1;
+      oz[2 * (m - 1) + sgn] = inz ? (jz * ny + iy) * nx + ix : -1;
+    }
+  }
+  const int o0 = blockIdx.y * ochunk, o1 = min(o0 + ochunk, nk * norb);
+  float acc[2][5] = {{0, 0, 0, 0, 0}, {0, 0, 0, 0, 0}};
+  for (int o = o0; o < o1;) {
+    const int k = o / norb;
+    const int oe = min(o1, (k + 1) * norb);
+    const float q[3] = {(float)kpts[3 * k], (float)kpts[3 * k + 1], (float)kpts[3 * k + 2]};
+    float sk[2][5] = {{0, 0, 0, 0, 0}, {0, 0, 0, 0, 0}};
+#pragma unroll 1
+    for (; o < oe; ++o) {
+      const float2* f = u + (size_t)o * npts;
+      const float4 c = __ldg(reinterpret_cast<const float4*>(f + p));
+      float4 X[4], Y[8], Z[8];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) X[j] = ld4_or_zero(f, ox[j]);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) { Y[j] = ld4_or_zero(f, oy[j]); Z[j] = ld4_or_zero(f, oz[j]); }
+      // x +- m of point A (x) and B (x + 1), m = 1..4
+      const float2 lo_c = make_float2(c.x, c.y), hi_c = make_float2(c.z, c.w);
+      auto lo = [](float4 v) { return make_float2(v.x, v.y); };
+      auto hi = [](float4 v) { return make_float2(v.z, v.w); };
+      const float2 axp[4] = {hi_c, lo(X[2]), hi(X[2]), lo(X[3])}, axm[4] = {hi(X[1]), lo(X[1]), hi(X[0]), lo(X[0])};
+      const float2 bxp[4] = {lo(X[2]), hi(X[2]), lo(X[3]), hi(X[3])}, bxm[4] = {lo_c, hi(X[1]), lo(X[1]), hi(X[0])};
+#pragma unroll
+      for (int pt = 0; pt < 2; ++pt) {
+        const float2 c0 = pt == 0 ? lo_c : hi_c;
+        sk[pt][0] += c0.x * c0.x + c0.y * c0.y;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          float2 g = make_float2(-q[a] * c0.y, q[a] * c0.x);            // i q u
+#pragma unroll
+          for (int m = 0; m < 4; ++m) {
+            float2 fp, fm;
+            if (a == 0) { fp = pt == 0 ? axp[m] : bxp[m]; fm = pt == 0 ? axm[m] : bxm[m]; }
+            else if (a == 1) { fp = pt == 0 ? lo(Y[2 * m]) : hi(Y[2 * m]); fm = pt == 0 ? lo(Y[2 * m + 1]) : hi(Y[2 * m + 1]); }
+            else { fp = pt == 0 ? lo(Z[2 * m]) : hi(Z[2 * m]); fm = pt == 0 ? lo(Z[2 * m + 1]) : hi(Z[2 * m + 1]); }
+            g.x += d1.c[a][m] * (fp.x - fm.x);
+            g.y += d1.c[a][m] * (fp.y - fm.y);
+          }
+          sk[pt][1] += g.x * g.x + g.y * g.y;
+          sk[pt][2 + a] += c0.x * g.y - c0.y * g.x;                    // Im(conj(u) g)
+        }
+      }
+    }
+    const float w = (float)(2.0 * kw[k]);
+#pragma unroll
+    for (int pt = 0; pt < 2; ++pt) {
+      acc[pt][0] += w * sk[pt][0];
+      acc[pt][1] += 0.5f * w * sk[pt][1];
+#pragma unroll
+      for (int cc = 2; cc < 5; ++cc) acc[pt][cc] += w * sk[pt][cc];
+    }
+  }
+#pragma unroll
+  for (int cc = 0; cc < 5; ++cc) {
+    part[((size_t)blockIdx.y * 5 + cc) * npts + p] = (double)acc[0][cc];
+    part[((size_t)blockIdx.y * 5 + cc) * npts + p + 1] = (double)acc[1][cc];
+  }
 }
 
 // |grad rho|^2 and lap rho at p by the 8th-order differences
@@ -289,8 +393,19 @@ cudaError_t launch_mbj(const typename Cplx<T>::type* u, int nk, int norb, const 
   D1h<T> d1;
   for (int a = 0; a < 3; ++a)
     for (int m = 0; m < 4; ++m) d1.c[a][m] = (T)(kFD1[m] / h[a]);
-  k_tau<T><<<dim3(bx, nchunk), kMbjThreads, 0, s>>>(u, nk, norb, n[0], n[1], n[2], periodic, kpts, kw, d1, ochunk,
-                                                    part);
+  if constexpr (sizeof(T) == 4) {
+    if (n[0] % 2 == 0) {
+      const int bx2 = (npts / 2 + kMbjThreads - 1) / kMbjThreads;
+      k_tau_pair<<<dim3(bx2, nchunk), kMbjThreads, 0, s>>>(u, nk, norb, n[0], n[1], n[2], periodic, kpts, kw, d1,
+                                                          ochunk, part);
+    } else {
+      k_tau<T><<<dim3(bx, nchunk), kMbjThreads, 0, s>>>(u, nk, norb, n[0], n[1], n[2], periodic, kpts, kw, d1, ochunk,
+                                                        part);
+    }
+  } else {
+    k_tau<T><<<dim3(bx, nchunk), kMbjThreads, 0, s>>>(u, nk, norb, n[0], n[1], n[2], periodic, kpts, kw, d1, ochunk,
+                                                      part);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   int nl = 2;

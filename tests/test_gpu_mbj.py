@@ -22,7 +22,8 @@ def _systems():
     a.field = W.Field("pulse", (0.0, 0.0, 0.03), 0.4, 5.0, 0.0)
     b = W.small_periodic()
     c = W.tiny(periodic=False, n=(7, 9, 11), natom=2, norb=2)
-    return {"periodic-2k": a, "periodic-16": b, "isolated-ragged": c}
+    d = W.tiny(periodic=False, n=(8, 9, 10), natom=2, norb=2)    # even nx: the paired FP32 kinetic sums
+    return {"periodic-2k": a, "periodic-16": b, "isolated-ragged": c, "isolated-even": d}
 
 
 SYSTEMS = _systems()
@@ -52,7 +53,7 @@ def test_mbj_potential(name, cval):
     ctx.close()
 
 
-@pytest.mark.parametrize("name", ["periodic-2k", "isolated-ragged"])
+@pytest.mark.parametrize("name", ["periodic-2k", "isolated-ragged", "isolated-even"])
 @pytest.mark.parametrize("precision,tol", [("f64", 1e-10), ("f32", 1e-4)])
 def test_mbj_pc_steps(name, precision, tol):
     from paper_1804_01404_gb300.tdks import Context
