@@ -273,7 +273,9 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_lines(double2* data, int n,
 
 // Periodic boxes whose xy-plane fits in shared memory: the x and y passes of the Hartree solve run
 // in one launch, one CTA per (z plane, cell), with the plane transposed in shared memory between
-// the two line sets.  Forward (FWD): the real density plane rho[cell][z] is transformed along x,
+// the two line sets.  xh < m0: only the x frequencies kx < xh (kx <= m0/2) go through the y (and z)
+// passes: the density is real and the Poisson factor real and even, so after the inverse z and y
+// passes every x line satisfies X(m0 - kx) = conj(X(kx)), and the inverse x pass rebuilds the rest.  Forward (FWD): the real density plane rho[cell][z] is transformed along x,
 // then y, and written to data.  Inverse: the plane of data is transformed back along y, then x, and
 // the epilogue writes vhxc = Re(value) + V_xc(rho) (lda.cuh).  Twiddle tables tw0
 // (length m0) and tw1 (length m1); shared memory: m0 + m1 twiddles and two m0 m1 buffers.
@@ -283,7 +285,7 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_planes(double2* data, int m
                                                             const double2* __restrict__ tw1_g,
                                                             FftPlanArgs plan0, FftPlanArgs plan1,
                                                             const double* __restrict__ rho, int xc,
-                                                            double* __restrict__ vhxc) {
+                                                            double* __restrict__ vhxc, int xh) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int np = m0 * m1;
   double2* tw0 = reinterpret_cast<double2*>(smem_raw);
@@ -299,27 +301,32 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_planes(double2* data, int m
     for (int i = threadIdx.x; i < np; i += blockDim.x) b0[i] = double2{rho[plane + i], 0.0};   // [y][x]
     __syncthreads();
     stockham_lines(src, dst, m0, m1, tw0, plan0, -1);                 // x lines
-    for (int i = threadIdx.x; i < np; i += blockDim.x) {              // [y][x] -> [x][y]
-      const int y = i / m0, x = i - y * m0;
-      dst[x * m1 + y] = src[i];
+    for (int i = threadIdx.x; i < xh * m1; i += blockDim.x) {         // [y][x] -> [x][y], x < xh
+      const int x = i / m1, y = i - x * m1;
+      dst[x * m1 + y] = src[y * m0 + x];
     }
     __syncthreads();
     { double2* t = src; src = dst; dst = t; }
-    stockham_lines(src, dst, m1, m0, tw1, plan1, -1);                 // y lines
-    for (int i = threadIdx.x; i < np; i += blockDim.x) {              // [x][y] -> global [y][x]
-      const int y = i / m0, x = i - y * m0;
-      data[plane + i] = src[x * m1 + y];
+    stockham_lines(src, dst, m1, xh, tw1, plan1, -1);                 // y lines
+    for (int i = threadIdx.x; i < xh * m1; i += blockDim.x) {         // [x][y] -> global [y][x]
+      const int y = i / xh, x = i - y * xh;
+      data[plane + (long long)y * m0 + x] = src[x * m1 + y];
     }
   } else {
-    for (int i = threadIdx.x; i < np; i += blockDim.x) {              // global [y][x] -> [x][y]
-      const int y = i / m0, x = i - y * m0;
-      b0[x * m1 + y] = data[plane + i];
+    for (int i = threadIdx.x; i < xh * m1; i += blockDim.x) {         // global [y][x] -> [x][y], x < xh
+      const int y = i / xh, x = i - y * xh;
+      b0[x * m1 + y] = data[plane + (long long)y * m0 + x];
     }
     __syncthreads();
-    stockham_lines(src, dst, m1, m0, tw1, plan1, +1);                 // y lines
+    stockham_lines(src, dst, m1, xh, tw1, plan1, +1);                 // y lines
     for (int i = threadIdx.x; i < np; i += blockDim.x) {              // [x][y] -> [y][x]
       const int y = i / m0, x = i - y * m0;
-      dst[i] = src[x * m1 + y];
+      if (x < xh) {
+        dst[i] = src[x * m1 + y];
+      } else {                                                        // X(m0 - kx) = conj(X(kx))
+        const double2 c = src[(m0 - x) * m1 + y];
+        dst[i] = double2{c.x, -c.y};
+      }
     }
     __syncthreads();
     { double2* t = src; src = dst; dst = t; }
@@ -690,21 +697,24 @@ cudaError_t launch_hartree_xc_fused(double2* work, const int m[3], const int n[3
     for (int i = 0; i < nrad[0]; ++i) p0.rad[i] = rad[0][i];
     for (int i = 0; i < nrad[1]; ++i) p1.rad[i] = rad[1][i];
     const int grid = m[2] * batch;
+    // one system: the y and z passes only on the x frequencies kx <= m0/2 (see k_fft_planes)
+    const int xhp = batch == 1 ? m[0] / 2 + 1 : m[0];
     if ((e = cudaFuncSetAttribute(k_fft_planes<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)plane_smem)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_fft_planes<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)plane_smem)) != cudaSuccess) return e;
     k_fft_planes<true><<<grid, kFftThreads, plane_smem, s>>>(work, m[0], m[1], m[2], tw[0], tw[1], p0, p1, rho,
-                                                             0, nullptr);
+                                                             0, nullptr, xhp);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     FftHooks h3 = base;
     h3.spectral = 1;
     for (int a = 0; a < 3; ++a) h3.L[a] = m[a] * h[a];
     h3.inv_n = 1.0 / ((double)m[0] * m[1] * m[2]);
-    if ((e = launch_fft_axis_hooked(work, m, 2, -1, tw[2], rad[2], nrad[2], s, batch, 0, 0, &h3)) != cudaSuccess)
+    if ((e = launch_fft_axis_hooked(work, m, 2, -1, tw[2], rad[2], nrad[2], s, batch, 0, 0, &h3,
+                                    batch == 1 ? xhp : 0)) != cudaSuccess)
       return e;
     k_fft_planes<false><<<grid, kFftThreads, plane_smem, s>>>(work, m[0], m[1], m[2], tw[0], tw[1], p0, p1, rho,
-                                                              xc, vhxc);
+                                                              xc, vhxc, xhp);
     if (nlaunch) *nlaunch = 3;
     return cudaGetLastError();
   }
