@@ -360,11 +360,16 @@ __global__ void __launch_bounds__(256) k_residual(const double* __restrict__ Vne
 // step).  One thread sets the handle, so there are no racing calls.
 __global__ void __launch_bounds__(256) k_decide(const double* __restrict__ res, double thr,
                                                 const double* __restrict__ vnew, double* __restrict__ vhxc,
-                                                int n, double* fb, cudaGraphConditionalHandle handle) {
+                                                double* __restrict__ vnext, int n, double* fb,
+                                                cudaGraphConditionalHandle handle) {
   const double r = *res;
   const bool ok = (r <= thr) && (r == r) && (r < 1e300);   // finite and within the threshold
   if (ok)
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) vhxc[p] = vnew[p];
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+      const double v = vnew[p];
+      vhxc[p] = v;
+      vnext[p] = v;
+    }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     if (!ok) *fb += 1.0;
     cudaGraphSetConditional(handle, ok ? 0u : 1u);
@@ -841,11 +846,11 @@ cudaError_t nn_predict_fused(const NNBuffers& B, const NNGrid& g, const NNPredic
   return cudaLaunchCooperativeKernel((const void*)k_nn_predict, dim3((unsigned)nb), dim3(kFusedThreads), args, 0, s);
 }
 
-cudaError_t launch_decide(const double* res, double thr, const double* vnew, double* vhxc, int n, double* fb,
-                         cudaGraphConditionalHandle handle, cudaStream_t s) {
+cudaError_t launch_decide(const double* res, double thr, const double* vnew, double* vhxc, double* vnext, int n,
+                          double* fb, cudaGraphConditionalHandle handle, cudaStream_t s) {
   int nb = (n + 255) / 256;
   nb = nb < 1 ? 1 : (nb > 152 ? 152 : nb);
-  k_decide<<<nb, 256, 0, s>>>(res, thr, vnew, vhxc, n, fb, handle);
+  k_decide<<<nb, 256, 0, s>>>(res, thr, vnew, vhxc, vnext, n, fb, handle);
   return cudaGetLastError();
 }
 

@@ -129,6 +129,8 @@ struct tdks_ctx {
   double* d_step_obs = nullptr;  // [8]: J[3], d[3], N
   double* d_partials = nullptr;   // [304][4] grid_sum partials (residual, dipole)
   unsigned* d_ticket = nullptr;   // grid_sum ticket, zero between launches
+  double* d_partials_obs = nullptr;   // the same for the dipole of a step graph's parallel branch
+  unsigned* d_ticket_obs = nullptr;
   int red_blocks = 0;
   std::vector<void*> allocs;
   // potential history (V_Hxc at t, t-dt, t-2dt, t-3dt) and the predictor
@@ -187,6 +189,8 @@ struct tdks_ctx {
   cudaStream_t cap = nullptr, cap2 = nullptr;   // private streams the graphs are captured on
   cudaStream_t side2 = nullptr;      // side stream of the tile path inside a fallback body
   cudaStream_t body_side = nullptr;  // set to side2 while a fallback body is captured
+  cudaStream_t obs_side = nullptr;   // parallel branch of a step graph: J and the dipole
+  cudaEvent_t ev_obs_fork = nullptr, ev_obs_join = nullptr;
   double* d_apf = nullptr;       // [6] A'(t+dt/2) and A' of the observables, read by the step graph
   double* d_fb = nullptr;        // fallback count (device)
   double fb_seen = 0;            // fallbacks already added to the launch count
@@ -974,6 +978,9 @@ tdks_status tdks_init(const tdks_grid* grid, const tdks_cell* cell, const tdks_a
   if ((s = dalloc(c, &c->d_partials, (size_t)c->red_blocks * 4)) != TDKS_OK) return bail(s);
   if ((s = dalloc(c, &c->d_ticket, 1)) != TDKS_OK) return bail(s);
   cudaMemsetAsync(c->d_ticket, 0, sizeof(unsigned), c->stream);
+  if ((s = dalloc(c, &c->d_partials_obs, (size_t)c->red_blocks * 4)) != TDKS_OK) return bail(s);
+  if ((s = dalloc(c, &c->d_ticket_obs, 1)) != TDKS_OK) return bail(s);
+  cudaMemsetAsync(c->d_ticket_obs, 0, sizeof(unsigned), c->stream);
 
   // FFT set-up: periodic transforms are n^3, isolated ones (2n)^3 (zero padding)
   for (int a = 0; a < 3; ++a) {
@@ -1043,6 +1050,8 @@ void tdks_destroy(tdks_ctx* c) {
   for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->ev_obs_fork) cudaEventDestroy(c->ev_obs_fork);
+  if (c->ev_obs_join) cudaEventDestroy(c->ev_obs_join);
   if (c->side) cudaStreamDestroy(c->side);
   for (void* p : c->allocs) cudaFree(p);
   if (c->h_resid) cudaFreeHost(c->h_resid);
@@ -1055,6 +1064,7 @@ void tdks_destroy(tdks_ctx* c) {
   if (c->cap) cudaStreamDestroy(c->cap);
   if (c->cap2) cudaStreamDestroy(c->cap2);
   if (c->side2) cudaStreamDestroy(c->side2);
+  if (c->obs_side) cudaStreamDestroy(c->obs_side);
   delete c;
 }
 
@@ -1692,8 +1702,43 @@ static tdks_status sync_fallbacks(tdks_ctx* c) {
 // Predicted step, main path (inside a step-graph capture): the prediction of V~(t+dt) from the
 // history (the network or the cubic), the corrector T4[V_loc + (V_Hxc(t) + V~)/2] with its density,
 // V_Hxc(t+dt) into d_vnew and the misfit into d_resid.
+// J (from the orbital kernel's per-orbital sums) and the dipole of rho, into the step observables;
+// `partials` / `ticket` are the grid_sum buffers of the dipole.
+static tdks_status step_observables(tdks_ctx* c, bool at_start, double* partials, unsigned* ticket) {
+  Phase ph(c, 4);
+  if (c->grid.periodic) {
+    TDKS_CUDA(launch_reduce_current(c->d_orb_obs, c->nk, c->norb, c->d_kw, 1.0 / c->omega, 1, c->d_step_obs,
+                                    c->stream, c->ncell));
+    c->launches += 1;
+  } else {
+    TDKS_CUDA(cudaMemsetAsync(c->d_step_obs, 0, 3 * sizeof(double), c->stream));
+  }
+  if (!at_start) {
+    TDKS_CUDA(launch_dipole(c->d_rho, c->d_rho0, c->grid.n, c->grid.h, c->grid.periodic, partials, ticket,
+                            c->d_step_obs, c->stream));
+    c->launches += 1;
+  }
+  return TDKS_OK;
+}
+
+// Inside a step graph the step's J and dipole run on a parallel branch beside the Hartree solve
+// (whose FFT kernels occupy few SMs): they need only what the orbital kernel left (the per-orbital
+// sums and the density).  The graph joins the branch before the accept / fallback decision, and a
+// fallback body computes them again from its own orbitals.
+static tdks_status fork_step_observables(tdks_ctx* c, bool at_start) {
+  TDKS_CUDA(cudaEventRecord(c->ev_obs_fork, c->stream));
+  TDKS_CUDA(cudaStreamWaitEvent(c->obs_side, c->ev_obs_fork, 0));
+  const cudaStream_t main = c->stream;
+  c->stream = c->obs_side;
+  const tdks_status st = step_observables(c, at_start, c->d_partials_obs, c->d_ticket_obs);
+  c->stream = main;
+  TDKS_TRY(st);
+  TDKS_CUDA(cudaEventRecord(c->ev_obs_join, c->obs_side));
+  return TDKS_OK;
+}
+
 static tdks_status predicted_main(tdks_ctx* c, void* u, const double Amid[3], double dt, const double* Aobs,
-                                  bool obs_start) {
+                                  bool obs_start, bool obs_branch = false) {
   const size_t gb = c->npts * sizeof(double);
   const size_t obytes = (size_t)c->nk * c->norb * c->npts * (is_f32(c) ? sizeof(float2) : sizeof(double2));
   const NNGrid g = nn_grid(c);
@@ -1723,32 +1768,16 @@ static tdks_status predicted_main(tdks_ctx* c, void* u, const double Amid[3], do
   const tdks_status cs = orbital_kernel(c, 1, u, u, Amid, dt, c->d_rho, 1, Aobs, obs_start);
   c->cur_backup = nullptr;
   TDKS_TRY(cs);
+  if (obs_branch) TDKS_TRY(fork_step_observables(c, obs_start));
   TDKS_TRY(hxc(c, c->d_rho, c->d_vnew, u));
   TDKS_CUDA(launch_residual(c->d_vnew, c->d_vpred, c->npts, c->d_partials, c->d_ticket, c->d_resid, c->stream));
   c->launches += 1;
   return TDKS_OK;
 }
 
-// The rest of the step graph after the conditional fallback: V_Hxc(t+dt) into the history slot the
-// next step reads as V0, J and the dipole.
-static tdks_status step_tail(tdks_ctx* c, bool at_start) {
-  double* next0 = c->d_vhist + (size_t)((c->hist_head + 1) % 4) * c->npts;
-  TDKS_CUDA(cudaMemcpyAsync(next0, c->d_vhxc, c->npts * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-  Phase ph(c, 4);
-  if (c->grid.periodic) {
-    TDKS_CUDA(launch_reduce_current(c->d_orb_obs, c->nk, c->norb, c->d_kw, 1.0 / c->omega, 1, c->d_step_obs,
-                                    c->stream, c->ncell));
-    c->launches += 1;
-  } else {
-    TDKS_CUDA(cudaMemsetAsync(c->d_step_obs, 0, 3 * sizeof(double), c->stream));
-  }
-  if (!at_start) {
-    TDKS_CUDA(launch_dipole(c->d_rho, c->d_rho0, c->grid.n, c->grid.h, c->grid.periodic, c->d_partials, c->d_ticket,
-                            c->d_step_obs, c->stream));
-    c->launches += 1;
-  }
-  return TDKS_OK;
-}
+// The history slot the next step reads as V0: an accepted step's decision kernel writes V_Hxc(t+dt)
+// there, a fallback body copies it at its end.
+static double* next_hist_slot(tdks_ctx* c) { return c->d_vhist + (size_t)((c->hist_head + 1) % 4) * c->npts; }
 
 // Add the step-graph timings of the last execution of slot v to the phase times.
 static tdks_status collect_graph(tdks_ctx* c, tdks_ctx::StepGraph& g) {
@@ -1789,6 +1818,9 @@ static tdks_status build_step_graph(tdks_ctx* c, void* u, double dt, const doubl
   if (!c->cap) TDKS_CUDA(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
   if (!c->cap2) TDKS_CUDA(cudaStreamCreateWithFlags(&c->cap2, cudaStreamNonBlocking));
   if (c->tiled && !c->side2) TDKS_CUDA(cudaStreamCreateWithFlags(&c->side2, cudaStreamNonBlocking));
+  if (!c->obs_side) TDKS_CUDA(cudaStreamCreateWithFlags(&c->obs_side, cudaStreamNonBlocking));
+  if (!c->ev_obs_fork) TDKS_CUDA(cudaEventCreateWithFlags(&c->ev_obs_fork, cudaEventDisableTiming));
+  if (!c->ev_obs_join) TDKS_CUDA(cudaEventCreateWithFlags(&c->ev_obs_join, cudaEventDisableTiming));
   const cudaStream_t main = c->stream;
   const bool prof = c->profiling;
   const long long launches0 = c->launches;
@@ -1804,7 +1836,8 @@ static tdks_status build_step_graph(tdks_ctx* c, void* u, double dt, const doubl
   tdks_status st = TDKS_OK;
   cudaError_t e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeRelaxed);
   if (e == cudaSuccess) {
-    st = predicted_main(c, u, zero, dt, Aobs, obs_start);   // the kernels read A' from the device pointers
+    st = predicted_main(c, u, zero, dt, Aobs, obs_start, true);   // the kernels read A' from the device pointers
+    if (st == TDKS_OK) e = cudaStreamWaitEvent(c->cap, c->ev_obs_join, 0);   // join J and the dipole
     cudaGraph_t cg = nullptr;
     const cudaGraphNode_t* deps = nullptr;
     size_t ndeps = 0;
@@ -1816,7 +1849,8 @@ static tdks_status build_step_graph(tdks_ctx* c, void* u, double dt, const doubl
     if (st == TDKS_OK && e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&handle, cg, 0, cudaGraphCondAssignDefault);
     if (st == TDKS_OK && e == cudaSuccess) {
       Phase ph(c, 5);
-      e = launch_decide(c->d_resid, c->pred_thr, c->d_vnew, c->d_vhxc, c->npts, c->d_fb, handle, c->stream);
+      e = launch_decide(c->d_resid, c->pred_thr, c->d_vnew, c->d_vhxc, next_hist_slot(c), c->npts, c->d_fb, handle,
+                        c->stream);
       c->launches += 1;
     }
     if (st == TDKS_OK && e == cudaSuccess) e = cudaStreamGetCaptureInfo(c->cap, &cst, nullptr, &cg, &deps, nullptr, &ndeps);
@@ -1844,6 +1878,10 @@ static tdks_status build_step_graph(tdks_ctx* c, void* u, double dt, const doubl
       if (e == cudaSuccess) {
         e = cudaMemcpyAsync(u, c->d_backup, obytes, cudaMemcpyDeviceToDevice, c->stream);
         if (e == cudaSuccess) st = pc_step(c, u, zero, Aobs ? zero : nullptr, obs_start, dt);
+        if (e == cudaSuccess && st == TDKS_OK) st = step_observables(c, obs_start, c->d_partials, c->d_ticket);
+        if (e == cudaSuccess && st == TDKS_OK)
+          e = cudaMemcpyAsync(next_hist_slot(c), c->d_vhxc, c->npts * sizeof(double), cudaMemcpyDeviceToDevice,
+                              c->stream);
         const cudaError_t e2 = cudaStreamEndCapture(c->cap2, &body);
         if (e == cudaSuccess) e = e2;
       }
@@ -1854,7 +1892,6 @@ static tdks_status build_step_graph(tdks_ctx* c, void* u, double dt, const doubl
       c->cap_recs = prof ? &g.recs : nullptr;
       c->profiling = prof;
     }
-    if (st == TDKS_OK && e == cudaSuccess) st = step_tail(c, obs_start);
     const cudaError_t e2 = cudaStreamEndCapture(c->cap, &g.graph);
     if (e == cudaSuccess) e = e2;
   }
@@ -1972,20 +2009,7 @@ tdks_status tdks_step(tdks_ctx* c, void* u, double t, double dt) {
   c->cur_ap_mid = c->cur_ap_end = nullptr;
   TDKS_TRY(st);
   TDKS_TRY(hist_push(c, c->d_vhxc));
-  Phase ph(c, 4);
-  c->launches += c->grid.periodic ? 1 : 0;   // reduce_current
-  if (c->grid.periodic) {
-    TDKS_CUDA(launch_reduce_current(c->d_orb_obs, c->nk, c->norb, c->d_kw, 1.0 / c->omega, 1,
-                                    c->d_step_obs, c->stream, c->ncell));
-  } else {
-    TDKS_CUDA(cudaMemsetAsync(c->d_step_obs, 0, 3 * sizeof(double), c->stream));
-  }
-  if (!at_start) {
-    TDKS_CUDA(launch_dipole(c->d_rho, c->d_rho0, c->grid.n, c->grid.h, c->grid.periodic,
-                            c->d_partials, c->d_ticket, c->d_step_obs, c->stream));   // cell 0
-    c->launches += 1;
-  }
-  return TDKS_OK;
+  return step_observables(c, at_start, c->d_partials, c->d_ticket);   // cell 0's dipole
 }
 
 tdks_status tdks_ms_init(tdks_ctx* c, int nX, int m0, double dX, const double* A_now, const double* A_prev) {

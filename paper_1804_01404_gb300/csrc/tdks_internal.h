@@ -240,10 +240,10 @@ cudaError_t nn_apply(const NNBuffers& B, const NNGrid& g, const double* V0, cons
 cudaError_t launch_residual(const double* Vnew, const double* Vpred, int n, double* partials, unsigned* ticket,
                             double* res, cudaStream_t s);
 // Device-side acceptance of a predicted potential (a kernel inside a captured graph that owns `handle`):
-// vhxc <- vnew if *res <= thr (finite), else *fb += 1 and the conditional `handle` is set to 1 (0 when
-// accepted).
-cudaError_t launch_decide(const double* res, double thr, const double* vnew, double* vhxc, int n, double* fb,
-                          cudaGraphConditionalHandle handle, cudaStream_t s);
+// vhxc <- vnew and vnext <- vnew (the potential history's next slot) if *res <= thr (finite), else
+// *fb += 1 and the conditional `handle` is set to 1 (0 when accepted).
+cudaError_t launch_decide(const double* res, double thr, const double* vnew, double* vhxc, double* vnext, int n,
+                          double* fb, cudaGraphConditionalHandle handle, cudaStream_t s);
 // dst[0..5] <- v[0..5] (six doubles passed by value, so the host buffer may change right after the call)
 cudaError_t launch_store6(double* dst, const double v[6], cudaStream_t s);
 
