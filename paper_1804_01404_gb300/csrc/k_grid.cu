@@ -7,6 +7,7 @@
 // stages there, and writes the lines back in natural order.
 #include <cstring>
 
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include "ff.cuh"
@@ -21,6 +22,9 @@ namespace {
 constexpr int kFftThreads = 256;
 constexpr int kMaxRadices = 16;
 constexpr size_t kPlaneSmemLimit = 160 * 1024;   // xy-plane kernels: twiddles + two plane buffers
+// the cluster-split plane kernels ask for at least this much shared memory, so that no two of their
+// CTAs share an SM (and its FP64 pipes)
+constexpr size_t kPlaneClusterMinSmem = 116 * 1024;
 
 struct FftPlanArgs {
   int nrad;
@@ -149,12 +153,71 @@ __device__ __forceinline__ void stockham_lines(double2*& src, double2*& dst, int
   }
 }
 
+// The same transform computed output by output, for kernels whose lines are few: an FP64
+// instruction occupies its SM sub-partition for the same time whether one lane or all 32 are active,
+// and one warp's FP64 instructions do not overlap, so a stage costs about the longest chain of FP64
+// instructions any thread runs.  A butterfly per thread runs the whole radix-R DFT (a radix-5 step
+// with its twiddles: about 50 FP64 instructions); here thread t forms element q of line t / n alone,
+//   dst[q] = sum_r src[jb + r n/R] exp(dir 2 pi i r (k tstep + m n/R) / n),
+// with q = g Ns R + m Ns + k, jb = g Ns + k, tstep = n / (Ns R) (the stage twiddle and the R-point
+// DFT factor merge into one table entry): 4 (R - 1) FMAs, or 2 (R - 1) adds where the factors are
+// +-1, +-i (the first stage of radix 2 or 4).  Threads read src and write dst; the caller
+// synchronises between stages.
+__device__ __forceinline__ void stage_out(const double2* __restrict__ src, double2* __restrict__ dst, int n,
+                                          int nl, int R, int Ns, const double2* __restrict__ tw, int dir) {
+  const int nr = n / R, span = Ns * R, tstep = n / span;
+  for (int t = threadIdx.x; t < nl * n; t += blockDim.x) {
+    const int j = t / n, q = t - j * n;
+    const int g = q / span, rem = q - g * span;
+    const int m = rem / Ns, k = rem - m * Ns;
+    const double2* sl = src + j * n + g * Ns + k;
+    double2 acc = sl[0];
+    if (Ns == 1 && (R == 2 || R == 4)) {
+      // factor (-dir i)^(r m) for R = 4, (-1)^(r m) for R = 2: x (-i)^p = (b, -a), (-a, -b), (-b, a)
+      for (int r = 1; r < R; ++r) {
+        const double2 x = sl[r * nr];
+        int p = (R == 4 ? r * m : 2 * r * m) & 3;
+        if (dir > 0) p = (4 - p) & 3;
+        const double re = (p & 1) ? x.y : x.x, im = (p & 1) ? x.x : x.y;
+        acc.x = fma(p < 2 ? 1.0 : -1.0, re, acc.x);
+        acc.y = fma((p == 0 || p == 3) ? 1.0 : -1.0, im, acc.y);
+      }
+    } else {
+      const int step = k * tstep + m * nr;
+      for (int r = 1; r < R; ++r) {
+        const double2 x = sl[r * nr];
+        double2 w = tw[(r * step) % n];
+        if (dir > 0) w.y = -w.y;
+        acc.x = fma(x.x, w.x, acc.x);
+        acc.x = fma(-x.y, w.y, acc.x);
+        acc.y = fma(x.x, w.y, acc.y);
+        acc.y = fma(x.y, w.x, acc.y);
+      }
+    }
+    dst[t] = acc;
+  }
+}
+
+// All stages of stage_out over nl lines (ping-pong between src and dst; on return src holds the
+// result).
+__device__ __forceinline__ void lines_out(double2*& src, double2*& dst, int n, int nl, const double2* tw,
+                                          const FftPlanArgs& plan, int dir) {
+  int Ns = 1;
+  for (int s = 0; s < plan.nrad; ++s) {
+    stage_out(src, dst, n, nl, plan.rad[s], Ns, tw, dir);
+    __syncthreads();
+    double2* t = src; src = dst; dst = t;
+    Ns *= plan.rad[s];
+  }
+}
+
 // Optional work fused into a line pass, so the Hartree + exchange solve takes five launches:
 //   load_real  (x pass, forward): lines are read from a real array [n2*batch][n1][n0], zero padded
 //              to the transform box, instead of from `data` (replaces a packing kernel);
 //   spectral   (z pass): after the forward transform each value is multiplied by the Poisson
-//              factor of its wave vector (periodic: 4 pi / G^2 / N, G = 0 dropped; isolated: the
-//              Hockney spectrum ghat times gscale) and the line is transformed back in place;
+//              factor of its wave vector (periodic: 4 pi / G^2 / N, G = 0 dropped, from the table
+//              ghat when one is given, else computed; isolated: the Hockney spectrum ghat times
+//              gscale) and the line is transformed back in place;
 //   store_epi  (x pass, inverse): instead of writing the line back, the inside points n0 x n1 x n2
 //              get vhxc = Re(value) + V_xc(rho) (lda.cuh: xc = 1 exchange, 2 exchange + correlation).
 __device__ __forceinline__ double freq(int m, int n) { return (m <= (n - 1) / 2) ? m : m - n; }
@@ -230,19 +293,23 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_lines(double2* data, int n,
   double2* dst = b1;
   stockham_lines(src, dst, n, nl, tw, plan, dir);
   if (hk.spectral) {
+    const int cellsz = m0 * m1 * m2;
     for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
       const int j = idx / n, e = idx - j * n;
-      int x, y, z;
-      coords3(j, e, x, y, z);
       double f;
-      if (hk.spectral == 1) {
+      if (hk.ghat) {   // table of one box: offset of the element within its cell (sizes < 2^31)
+        const int l = l0 + j, clo = (int)cnt_lo;
+        const int off = (l % clo) * (int)s_lo + (l / clo) * (int)s_hi + e * (int)estride;
+        f = hk.ghat[off % cellsz];
+        if (hk.spectral == 2) f *= hk.gscale;
+      } else {
+        int x, y, z;
+        coords3(j, e, x, y, z);
         const int zc = z % m2;
         const double gx = 2.0 * kPi * freq(x, m0) / hk.L[0], gy = 2.0 * kPi * freq(y, m1) / hk.L[1],
                      gz = 2.0 * kPi * freq(zc, m2) / hk.L[2];
         const double g2 = gx * gx + gy * gy + gz * gz;
         f = (g2 == 0.0) ? 0.0 : 4.0 * kPi / g2 * hk.inv_n;
-      } else {
-        f = hk.ghat[((long long)z * m1 + y) * m0 + x] * hk.gscale;
       }
       const double2 v = src[idx];
       src[idx] = double2{v.x * f, v.y * f};
@@ -275,8 +342,9 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_lines(double2* data, int n,
 // in one launch, one CTA per (z plane, cell), with the plane transposed in shared memory between
 // the two line sets.  xh < m0: only the x frequencies kx < xh (kx <= m0/2) go through the y (and z)
 // passes: the density is real and the Poisson factor real and even, so after the inverse z and y
-// passes every x line satisfies X(m0 - kx) = conj(X(kx)), and the inverse x pass rebuilds the rest.  Forward (FWD): the real density plane rho[cell][z] is transformed along x,
-// then y, and written to data.  Inverse: the plane of data is transformed back along y, then x, and
+// passes every x line satisfies X(m0 - kx) = conj(X(kx)), and the inverse x pass rebuilds the rest.
+// Forward (FWD): the real density plane rho[cell][z] is transformed along x, then y, and written to
+// data.  Inverse: the plane of data is transformed back along y, then x, and
 // the epilogue writes vhxc = Re(value) + V_xc(rho) (lda.cuh).  Twiddle tables tw0
 // (length m0) and tw1 (length m1); shared memory: m0 + m1 twiddles and two m0 m1 buffers.
 template <bool FWD>
@@ -336,6 +404,147 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_planes(double2* data, int m
       v += lda_vxc(rho[plane + i], xc);
       vhxc[plane + i] = v;
     }
+  }
+}
+
+// The same two passes for one periodic cell, each z plane split over a thread-block cluster of CL
+// CTAs so that the FP64 butterflies of a plane run on CL SMs (the FP64 pipes of the few SMs of one
+// CTA per plane are the limit otherwise).  CTA r of a cluster owns the rows y in [r m1 / CL,
+// (r+1) m1 / CL) for the x pass and the columns kx in [r xh / CL, (r+1) xh / CL) for the y pass; the
+// transpose between the passes writes each value into the shared memory of the CTA that owns it
+// (distributed shared memory), then the cluster barrier.  The lines are transformed output by output
+// (lines_out), one thread per element.  Forward: rows of the density -> x spectra
+// -> columns kx < xh -> y spectra -> data.  Inverse: columns of data -> y inverse -> rows, with
+// X(m0 - kx) = conj(X(kx)) filling kx >= xh -> x inverse -> vhxc = Re + V_xc(rho).  Shared memory:
+// m0 + m1 twiddles, two row buffers of rmax x m0 and two column buffers of cmax x m1.
+template <bool FWD>
+__global__ void __launch_bounds__(kFftThreads) k_fft_planes_cluster(double2* data, int m0, int m1, int xh,
+                                                                    const double2* __restrict__ tw0_g,
+                                                                    const double2* __restrict__ tw1_g,
+                                                                    FftPlanArgs plan0, FftPlanArgs plan1,
+                                                                    const double* __restrict__ rho, int xc,
+                                                                    double* __restrict__ vhxc, int rmax, int cmax) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int CL = (int)cluster.num_blocks();
+  const int r = (int)cluster.block_rank();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* tw0 = reinterpret_cast<double2*>(smem_raw);
+  double2* tw1 = tw0 + m0;
+  double2* rowA = tw1 + m1;
+  double2* rowB = rowA + (size_t)rmax * m0;
+  double2* colA = rowB + (size_t)rmax * m0;
+  double2* colB = colA + (size_t)cmax * m1;
+  // every CTA of the cluster must be running before any writes into its shared memory: arrive here,
+  // wait just before the first remote store
+  asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+  for (int t = threadIdx.x; t < m0; t += blockDim.x) tw0[t] = tw0_g[t];
+  for (int t = threadIdx.x; t < m1; t += blockDim.x) tw1[t] = tw1_g[t];
+  const int y0 = r * m1 / CL, ny = (r + 1) * m1 / CL - y0;
+  const int x0 = r * xh / CL, nc = (r + 1) * xh / CL - x0;
+  const long long plane = (long long)(blockIdx.x / CL) * m0 * m1;
+  if (FWD) {
+    for (int i = threadIdx.x; i < ny * m0; i += blockDim.x)
+      rowA[i] = double2{rho[plane + (long long)y0 * m0 + i], 0.0};
+    __syncthreads();
+    double2* src = rowA;
+    double2* dst = rowB;
+    lines_out(src, dst, m0, ny, tw0, plan0, -1);                    // x lines of the own rows
+    asm volatile("barrier.cluster.wait.aligned;" ::: "memory");
+    for (int i = threadIdx.x; i < ny * xh; i += blockDim.x) {        // row spectra -> column owners
+      const int yy = i / xh, kx = i - yy * xh;
+      int o = 0;
+      while (o + 1 < CL && (o + 1) * xh / CL <= kx) ++o;
+      double2* col = cluster.map_shared_rank(colA, o);
+      col[(kx - o * xh / CL) * m1 + y0 + yy] = src[yy * m0 + kx];
+    }
+    cluster.sync();
+    src = colA;
+    dst = colB;
+    lines_out(src, dst, m1, nc, tw1, plan1, -1);                    // y lines of the own columns
+    for (int i = threadIdx.x; i < m1 * nc; i += blockDim.x) {
+      const int y = i / nc, c = i - y * nc;
+      data[plane + (long long)y * m0 + x0 + c] = src[c * m1 + y];
+    }
+  } else {
+    for (int i = threadIdx.x; i < m1 * nc; i += blockDim.x) {
+      const int y = i / nc, c = i - y * nc;
+      colA[c * m1 + y] = data[plane + (long long)y * m0 + x0 + c];
+    }
+    __syncthreads();
+    double2* src = colA;
+    double2* dst = colB;
+    lines_out(src, dst, m1, nc, tw1, plan1, +1);                    // y lines of the own columns
+    asm volatile("barrier.cluster.wait.aligned;" ::: "memory");
+    for (int i = threadIdx.x; i < nc * m1; i += blockDim.x) {        // -> row owners, with the mirror
+      const int c = i / m1, y = i - c * m1, kx = x0 + c;
+      int o = 0;
+      while (o + 1 < CL && (o + 1) * m1 / CL <= y) ++o;
+      double2* row = cluster.map_shared_rank(rowA, o) + (size_t)(y - o * m1 / CL) * m0;
+      const double2 v = src[c * m1 + y];
+      row[kx] = v;
+      if (kx >= 1 && m0 - kx >= xh) row[m0 - kx] = double2{v.x, -v.y};
+    }
+    cluster.sync();
+    src = rowA;
+    dst = rowB;
+    lines_out(src, dst, m0, ny, tw0, plan0, +1);                    // x lines of the own rows
+    for (int i = threadIdx.x; i < ny * m0; i += blockDim.x) {
+      const long long o = plane + (long long)y0 * m0 + i;
+      vhxc[o] = src[i].x + lda_vxc(rho[o], xc);
+    }
+  }
+}
+
+// The z pass of one periodic cell after the cluster plane kernels: the z lines of the x frequencies
+// kx < xh (all y), LZ lines per CTA, forward, times the Poisson factor pfac of the element, inverse,
+// in place; output by output (lines_out), one thread per element.
+__global__ void __launch_bounds__(kFftThreads) k_fft_zcol(double2* data, int m0, int m1, int m2, int xh, int LZ,
+                                                         const double2* __restrict__ tw_g, FftPlanArgs plan,
+                                                         const double* __restrict__ pfac) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* tw = reinterpret_cast<double2*>(smem_raw);
+  double2* b0 = tw + m2;
+  double2* b1 = b0 + (size_t)LZ * m2;
+  for (int t = threadIdx.x; t < m2; t += blockDim.x) tw[t] = tw_g[t];
+  const int nlines = xh * m1, l0 = blockIdx.x * LZ;
+  const int nl = min(LZ, nlines - l0);
+  const int d01 = m0 * m1;
+  for (int t = threadIdx.x; t < nl * m2; t += blockDim.x) {   // element e of line j, consecutive lines in x
+    const int e = t / nl, j = t - e * nl, l = l0 + j;
+    const int y = l / xh, x = l - y * xh;
+    b0[j * m2 + e] = data[x + y * m0 + e * d01];
+  }
+  __syncthreads();
+  double2* src = b0;
+  double2* dst = b1;
+  lines_out(src, dst, m2, nl, tw, plan, -1);
+  for (int t = threadIdx.x; t < nl * m2; t += blockDim.x) {
+    const int j = t / m2, e = t - j * m2, l = l0 + j;
+    const int y = l / xh, x = l - y * xh;
+    const double f = pfac[x + y * m0 + e * d01];
+    src[t] = double2{src[t].x * f, src[t].y * f};
+  }
+  __syncthreads();
+  lines_out(src, dst, m2, nl, tw, plan, +1);
+  for (int t = threadIdx.x; t < nl * m2; t += blockDim.x) {
+    const int e = t / nl, j = t - e * nl, l = l0 + j;
+    const int y = l / xh, x = l - y * xh;
+    data[x + y * m0 + e * d01] = src[j * m2 + e];
+  }
+}
+
+// The periodic Poisson factor of every wave vector of one box: 4 pi / G^2 * inv_n, 0 at G = 0
+// (the same arithmetic as the computed form of the spectral hook).
+__global__ void k_poisson_table(double* __restrict__ t, int m0, int m1, int m2, double L0, double L1, double L2,
+                                double inv_n) {
+  const int total = m0 * m1 * m2;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    const int x = i % m0, y = (i / m0) % m1, z = i / (m0 * m1);
+    const double gx = 2.0 * kPi * freq(x, m0) / L0, gy = 2.0 * kPi * freq(y, m1) / L1,
+                 gz = 2.0 * kPi * freq(z, m2) / L2;
+    const double g2 = gx * gx + gy * gy + gz * gz;
+    t[i] = (g2 == 0.0) ? 0.0 : 4.0 * kPi / g2 * inv_n;
   }
 }
 
@@ -674,6 +883,109 @@ cudaError_t launch_fft_axis_hooked(double2* data, const int dims[3], int axis, i
   return cudaGetLastError();
 }
 
+namespace {
+
+size_t plane_cluster_smem(const int m[3], int cl) {
+  const int xh = m[0] / 2 + 1;
+  const int rmax = (m[1] + cl - 1) / cl, cmax = (xh + cl - 1) / cl;
+  const size_t need = ((size_t)m[0] + m[1] + 2 * (size_t)rmax * m[0] + 2 * (size_t)cmax * m[1]) * sizeof(double2);
+  return need > kPlaneClusterMinSmem ? need : kPlaneClusterMinSmem;
+}
+
+}  // namespace
+
+int hartree_plane_cluster(const int m[3], int batch, int periodic) {
+  const size_t plane_smem = ((size_t)m[0] + m[1] + 2 * (size_t)m[0] * m[1]) * sizeof(double2);
+  if (!periodic || batch != 1 || plane_smem > kPlaneSmemLimit) return 0;
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  const int xh = m[0] / 2 + 1;
+  for (int cl = 8; cl >= 2; --cl) {
+    if (cl > m[1] || cl > xh || m[2] * cl > nsm) continue;
+    const size_t smem = plane_cluster_smem(m, cl);
+    if (cudaFuncSetAttribute(k_fft_planes_cluster<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(m[2] * cl));
+    cfg.blockDim = dim3(kFftThreads);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)cl;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, (const void*)k_fft_planes_cluster<true>, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    if (nclusters >= m[2]) return cl;     // every plane's cluster resident at once
+  }
+  return 0;
+}
+
+namespace {
+
+template <bool FWD>
+cudaError_t launch_planes_cluster(double2* work, const int m[3], int cl, const double2* tw0, const double2* tw1,
+                                  const FftPlanArgs& p0, const FftPlanArgs& p1, const double* rho, int xc,
+                                  double* vhxc, cudaStream_t s) {
+  const int xh = m[0] / 2 + 1;
+  const int rmax = (m[1] + cl - 1) / cl, cmax = (xh + cl - 1) / cl;
+  const size_t smem = plane_cluster_smem(m, cl);
+  cudaError_t e = cudaFuncSetAttribute(k_fft_planes_cluster<FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  // one thread per element of the larger line set (rows or columns)
+  int threads = rmax * m[0] > cmax * m[1] ? rmax * m[0] : cmax * m[1];
+  threads = (threads + 31) / 32 * 32;
+  if (threads > kFftThreads) threads = kFftThreads;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(m[2] * cl));
+  cfg.blockDim = dim3((unsigned)threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)cl;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_fft_planes_cluster<FWD>, work, m[0], m[1], xh, tw0, tw1, p0, p1, rho, xc, vhxc,
+                            rmax, cmax);
+}
+
+// z pass of one cell for the cluster plane path: LZ lines per CTA so that the CTAs about fill the SMs
+cudaError_t launch_zcol(double2* work, const int m[3], const double2* tw2, const FftPlanArgs& p2,
+                        const double* pfac, cudaStream_t s) {
+  int dev = 0, nsm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const int xh = m[0] / 2 + 1, nlines = xh * m[1];
+  int LZ = (nlines + nsm - 1) / nsm;
+  while (LZ > 1 && LZ * m[2] > kFftThreads) --LZ;
+  int threads = (LZ * m[2] + 31) / 32 * 32;
+  if (threads > kFftThreads) threads = kFftThreads;
+  const size_t smem = ((size_t)m[2] + 2 * (size_t)LZ * m[2]) * sizeof(double2);
+  if ((e = cudaFuncSetAttribute(k_fft_zcol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+    return e;
+  k_fft_zcol<<<(nlines + LZ - 1) / LZ, threads, smem, s>>>(work, m[0], m[1], m[2], xh, LZ, tw2, p2, pfac);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
 // Hartree (periodic 4 pi / G^2, or Hockney with the kernel spectrum ghat) + exchange in five line
 // passes: x forward from the real density, y forward, z forward-multiply-inverse, y inverse, and
 // x inverse writing vhxc (see FftHooks).  Periodic boxes whose xy-plane fits in shared memory take
@@ -682,7 +994,8 @@ cudaError_t launch_fft_axis_hooked(double2* data, const int dims[3], int axis, i
 cudaError_t launch_hartree_xc_fused(double2* work, const int m[3], const int n[3], int batch, int periodic,
                                     const double h[3], const double* ghat, double gscale,
                                     double2* const tw[3], const int* const rad[3], const int nrad[3],
-                                    const double* rho, int xc, double* vhxc, cudaStream_t s, int* nlaunch) {
+                                    const double* rho, int xc, double* vhxc, cudaStream_t s, int* nlaunch,
+                                    int plane_cl) {
   FftHooks base;
   std::memset(&base, 0, sizeof(base));
   base.n0 = n[0]; base.n1 = n[1]; base.n2 = n[2];
@@ -699,23 +1012,39 @@ cudaError_t launch_hartree_xc_fused(double2* work, const int m[3], const int n[3
     const int grid = m[2] * batch;
     // one system: the y and z passes only on the x frequencies kx <= m0/2 (see k_fft_planes)
     const int xhp = batch == 1 ? m[0] / 2 + 1 : m[0];
-    if ((e = cudaFuncSetAttribute(k_fft_planes<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)plane_smem)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_fft_planes<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)plane_smem)) != cudaSuccess) return e;
-    k_fft_planes<true><<<grid, kFftThreads, plane_smem, s>>>(work, m[0], m[1], m[2], tw[0], tw[1], p0, p1, rho,
-                                                             0, nullptr, xhp);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    FftHooks h3 = base;
-    h3.spectral = 1;
-    for (int a = 0; a < 3; ++a) h3.L[a] = m[a] * h[a];
-    h3.inv_n = 1.0 / ((double)m[0] * m[1] * m[2]);
-    if ((e = launch_fft_axis_hooked(work, m, 2, -1, tw[2], rad[2], nrad[2], s, batch, 0, 0, &h3,
-                                    batch == 1 ? xhp : 0)) != cudaSuccess)
-      return e;
+    const bool split = plane_cl >= 2 && batch == 1 && ghat && nrad[2] <= kMaxRadices;
+    if (split) {
+      if ((e = launch_planes_cluster<true>(work, m, plane_cl, tw[0], tw[1], p0, p1, rho, 0, nullptr, s)) !=
+          cudaSuccess)
+        return e;
+    } else {
+      if ((e = cudaFuncSetAttribute(k_fft_planes<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)plane_smem)) != cudaSuccess) return e;
+      if ((e = cudaFuncSetAttribute(k_fft_planes<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)plane_smem)) != cudaSuccess) return e;
+      k_fft_planes<true><<<grid, kFftThreads, plane_smem, s>>>(work, m[0], m[1], m[2], tw[0], tw[1], p0, p1, rho,
+                                                               0, nullptr, xhp);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (split) {
+      FftPlanArgs p2;
+      p2.nrad = nrad[2];
+      for (int i = 0; i < nrad[2]; ++i) p2.rad[i] = rad[2][i];
+      if ((e = launch_zcol(work, m, tw[2], p2, ghat, s)) != cudaSuccess) return e;
+    } else {
+      FftHooks h3 = base;
+      h3.spectral = 1;
+      for (int a = 0; a < 3; ++a) h3.L[a] = m[a] * h[a];
+      h3.inv_n = 1.0 / ((double)m[0] * m[1] * m[2]);
+      h3.ghat = ghat;
+      if ((e = launch_fft_axis_hooked(work, m, 2, -1, tw[2], rad[2], nrad[2], s, batch, 0, 0, &h3,
+                                      batch == 1 ? xhp : 0)) != cudaSuccess)
+        return e;
+    }
+    if (nlaunch) *nlaunch = 3;
+    if (split) return launch_planes_cluster<false>(work, m, plane_cl, tw[0], tw[1], p0, p1, rho, xc, vhxc, s);
     k_fft_planes<false><<<grid, kFftThreads, plane_smem, s>>>(work, m[0], m[1], m[2], tw[0], tw[1], p0, p1, rho,
                                                               xc, vhxc, xhp);
-    if (nlaunch) *nlaunch = 3;
     return cudaGetLastError();
   }
   if (nlaunch) *nlaunch = 5;
@@ -821,6 +1150,13 @@ cudaError_t launch_hockney_kernel(double2* g, const int m[3], const int n[3], co
                                   double g0, cudaStream_t s) {
   const long long tot = (long long)m[0] * m[1] * m[2];
   k_hockney<<<grid_for(tot, 256), 256, 0, s>>>(g, m[0], m[1], m[2], n[0], n[1], n[2], h[0], h[1], h[2], g0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_poisson_table(double* t, const int m[3], const double h[3], cudaStream_t s) {
+  const long long tot = (long long)m[0] * m[1] * m[2];
+  k_poisson_table<<<grid_for(tot, 256), 256, 0, s>>>(t, m[0], m[1], m[2], m[0] * h[0], m[1] * h[1], m[2] * h[2],
+                                                     1.0 / (double)tot);
   return cudaGetLastError();
 }
 

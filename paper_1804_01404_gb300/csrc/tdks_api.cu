@@ -124,6 +124,7 @@ struct tdks_ctx {
   double2* d_fft = nullptr;
   double2* d_tw[3] = {nullptr, nullptr, nullptr};
   double* d_ghat = nullptr;
+  int plane_cl = 0;               // cluster size of the Hartree xy-plane passes (0: one CTA per plane)
   // observables
   double* d_orb_obs = nullptr;   // [nk*norb*8]
   double* d_step_obs = nullptr;  // [8]: J[3], d[3], N
@@ -567,7 +568,7 @@ tdks_status hxc_lda(tdks_ctx* c, const double* rho, double* vhxc) {
     int nl = 0;
     TDKS_CUDA(launch_hartree_xc_fused(c->d_fft, c->m, c->grid.n, c->ncell, c->grid.periodic, c->grid.h,
                                       c->d_ghat, c->dV / npad, c->d_tw, rad, nrad, rho, c->opt.xc,
-                                      vhxc, c->stream, &nl));
+                                      vhxc, c->stream, &nl, c->plane_cl));
     c->launches += nl;
     return TDKS_OK;
   }
@@ -1008,6 +1009,11 @@ tdks_status tdks_init(const tdks_grid* grid, const tdks_cell* cell, const tdks_a
         return bail(fail(TDKS_ECUDA, "V_loc transform"));
     if (launch_real_part(c->d_fft, c->d_vloc, np, 1.0, c->stream) != cudaSuccess)
       return bail(fail(TDKS_ECUDA, "real part"));
+    // the Poisson factor of every wave vector, read by the z pass of the Hartree solve
+    if ((s = dalloc(c, &c->d_ghat, np)) != TDKS_OK) return bail(s);
+    if (launch_poisson_table(c->d_ghat, c->m, grid->h, c->stream) != cudaSuccess)
+      return bail(fail(TDKS_ECUDA, "Poisson factor table"));
+    c->plane_cl = hartree_plane_cluster(c->m, c->ncell, 1);
   } else {
     std::vector<double> at(5 * (size_t)natom);
     for (int i = 0; i < natom; ++i) {

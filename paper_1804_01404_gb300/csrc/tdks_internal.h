@@ -248,13 +248,19 @@ cudaError_t launch_decide(const double* res, double thr, const double* vnew, dou
 cudaError_t launch_store6(double* dst, const double v[6], cudaStream_t s);
 
 // Grid kernels (k_grid.cu)
-// Hartree + exchange in five fused FFT line passes: vhxc = V_H[rho] (+ V_x[rho] if xc).  work: the
-// transform box m^3 per cell (m = n periodic, 2n isolated); batch: cells (periodic only).
+// Hartree + exchange in five fused FFT line passes (three for periodic boxes whose xy-plane fits in
+// shared memory): vhxc = V_H[rho] (+ V_x[rho] if xc).  work: the transform box m^3 per cell (m = n
+// periodic, 2n isolated); batch: cells (periodic only); ghat: the periodic Poisson factors
+// (launch_poisson_table) or the Hockney spectrum.  plane_cl >= 2 (one periodic cell): the xy-plane
+// passes split each plane over a cluster of plane_cl CTAs (hartree_plane_cluster).
 cudaError_t launch_hartree_xc_fused(double2* work, const int m[3], const int n[3], int batch, int periodic,
                                     const double h[3], const double* ghat, double gscale,
                                     double2* const tw[3], const int* const rad[3], const int nrad[3],
                                     const double* rho, int xc, double* vhxc, cudaStream_t s,
-                                    int* nlaunch = nullptr);
+                                    int* nlaunch = nullptr, int plane_cl = 0);
+// Cluster size for the xy-plane passes of one periodic cell of transform box m: the largest of 8 .. 2
+// whose clusters (one CTA per SM) are all resident at once, 0 where the split does not apply.
+int hartree_plane_cluster(const int m[3], int batch, int periodic);
 // batch = number of consecutive [dims2][dims1][dims0] arrays transformed together
 // lim_lo / lim_hi > 0: transform only the lines whose two other coordinates (lo: the faster of
 // them, hi: the slower, batch included for the last axis) are below the limits
@@ -289,6 +295,8 @@ cudaError_t launch_hockney_kernel(double2* g, const int m[3], const int n[3], co
                                   double g0, cudaStream_t s);
 cudaError_t launch_real_part(const double2* src, double* dst, size_t count, double scale,
                              cudaStream_t s);
+// t[(z m1 + y) m0 + x] = 4 pi / G^2 / (m0 m1 m2) of the periodic box m x h, 0 at G = 0
+cudaError_t launch_poisson_table(double* t, const int m[3], const double h[3], cudaStream_t s);
 // dipole: partials then final (deterministic two-pass); out[3..5] = d, out[6] = int rho
 // out[3..5] = dipole, out[6] = electron count; partials: [304][4] doubles, ticket: grid_sum ticket
 cudaError_t launch_dipole(const double* rho, const double* rho0, const int n[3], const double h[3],
