@@ -415,7 +415,8 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_planes(double2* data, int m
 // (distributed shared memory), then the cluster barrier.  The lines are transformed output by output
 // (lines_out), one thread per element.  Forward: rows of the density -> x spectra
 // -> columns kx < xh -> y spectra -> data.  Inverse: columns of data -> y inverse -> rows, with
-// X(m0 - kx) = conj(X(kx)) filling kx >= xh -> x inverse -> vhxc = Re + V_xc(rho).  Shared memory:
+// X(m0 - kx) = conj(X(kx)) filling kx >= xh -> x inverse -> vhxc = Re + vhxc (V_xc(rho), written by the
+// z pass launch; V_H alone for xc = 0).  Shared memory:
 // m0 + m1 twiddles, two row buffers of rmax x m0 and two column buffers of cmax x m1.
 template <bool FWD>
 __global__ void __launch_bounds__(kFftThreads) k_fft_planes_cluster(double2* data, int m0, int m1, int xh,
@@ -489,19 +490,30 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_planes_cluster(double2* dat
     src = rowA;
     dst = rowB;
     lines_out(src, dst, m0, ny, tw0, plan0, +1);                    // x lines of the own rows
-    for (int i = threadIdx.x; i < ny * m0; i += blockDim.x) {
+    for (int i = threadIdx.x; i < ny * m0; i += blockDim.x) {   // V_xc from the z pass launch
       const long long o = plane + (long long)y0 * m0 + i;
-      vhxc[o] = src[i].x + lda_vxc(rho[o], xc);
+      vhxc[o] = xc > 0 ? src[i].x + vhxc[o] : src[i].x;
     }
   }
 }
 
 // The z pass of one periodic cell after the cluster plane kernels: the z lines of the x frequencies
 // kx < xh (all y), LZ lines per CTA, forward, times the Poisson factor pfac of the element, inverse,
-// in place; output by output (lines_out), one thread per element.
+// in place; output by output (lines_out), one thread per element.  The CTAs past the z lines form
+// V_xc(rho) of every point into vxc (xc > 0), which the inverse plane kernel adds to V_H: the
+// exchange-correlation chains run beside the z transforms instead of after the last one.
 __global__ void __launch_bounds__(kFftThreads) k_fft_zcol(double2* data, int m0, int m1, int m2, int xh, int LZ,
                                                          const double2* __restrict__ tw_g, FftPlanArgs plan,
-                                                         const double* __restrict__ pfac) {
+                                                         const double* __restrict__ pfac,
+                                                         const double* __restrict__ rho, int xc,
+                                                         double* __restrict__ vxc) {
+  const int nzb = (xh * m1 + LZ - 1) / LZ;
+  if ((int)blockIdx.x >= nzb) {
+    const int npts = m0 * m1 * m2;
+    for (int p = (blockIdx.x - nzb) * blockDim.x + threadIdx.x; p < npts; p += (gridDim.x - nzb) * blockDim.x)
+      vxc[p] = lda_vxc(rho[p], xc);
+    return;
+  }
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double2* tw = reinterpret_cast<double2*>(smem_raw);
   double2* b0 = tw + m2;
@@ -965,9 +977,10 @@ cudaError_t launch_planes_cluster(double2* work, const int m[3], int cl, const d
                             rmax, cmax);
 }
 
-// z pass of one cell for the cluster plane path: LZ lines per CTA so that the CTAs about fill the SMs
+// z pass of one cell for the cluster plane path: LZ lines per CTA so that the CTAs about fill the SMs;
+// with xc > 0 further CTAs write V_xc(rho) to vxc
 cudaError_t launch_zcol(double2* work, const int m[3], const double2* tw2, const FftPlanArgs& p2,
-                        const double* pfac, cudaStream_t s) {
+                        const double* pfac, const double* rho, int xc, double* vxc, cudaStream_t s) {
   int dev = 0, nsm = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -980,7 +993,9 @@ cudaError_t launch_zcol(double2* work, const int m[3], const double2* tw2, const
   const size_t smem = ((size_t)m[2] + 2 * (size_t)LZ * m[2]) * sizeof(double2);
   if ((e = cudaFuncSetAttribute(k_fft_zcol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
     return e;
-  k_fft_zcol<<<(nlines + LZ - 1) / LZ, threads, smem, s>>>(work, m[0], m[1], m[2], xh, LZ, tw2, p2, pfac);
+  const int nzb = (nlines + LZ - 1) / LZ;
+  const int nxb = xc > 0 ? (m[0] * m[1] * m[2] + threads - 1) / threads : 0;
+  k_fft_zcol<<<nzb + nxb, threads, smem, s>>>(work, m[0], m[1], m[2], xh, LZ, tw2, p2, pfac, rho, xc, vxc);
   return cudaGetLastError();
 }
 
@@ -1030,7 +1045,7 @@ cudaError_t launch_hartree_xc_fused(double2* work, const int m[3], const int n[3
       FftPlanArgs p2;
       p2.nrad = nrad[2];
       for (int i = 0; i < nrad[2]; ++i) p2.rad[i] = rad[2][i];
-      if ((e = launch_zcol(work, m, tw[2], p2, ghat, s)) != cudaSuccess) return e;
+      if ((e = launch_zcol(work, m, tw[2], p2, ghat, rho, xc, vhxc, s)) != cudaSuccess) return e;
     } else {
       FftHooks h3 = base;
       h3.spectral = 1;
