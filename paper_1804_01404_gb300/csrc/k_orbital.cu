@@ -93,11 +93,17 @@ constexpr size_t kSmemLimit = 220 * 1024;
 constexpr int kNTip = 448;
 // FP32 fixed geometries (GEOM != 0): two x-adjacent points per thread, at most kNTpair threads.
 constexpr int kNTpair = 416;
+// ... and with two copies (scheme 2) kProjWarpsGeom further warps that only project: the projection
+// of a stage reads the current copy while the stencil writes the other, so it runs beside the
+// local pass instead of delaying the warps that would otherwise take an atom each before their
+// column segments (the barrier after the local pass waits for the slowest warp).
+constexpr int kProjWarpsGeom = 2;
 // ... and with one copy swept in place (scheme 3): one thread per column pair, at most kNTpairIP, two
 // CTAs per SM.
 constexpr int kNTpairIP = 224;
 template <typename T, bool IP, int GEOM = 0> constexpr int kMaxThreads() {
-  return (GEOM != 0 && sizeof(T) == 4) ? (IP ? kNTpairIP : kNTpair) : (IP ? kNTip : kNTof<T>());
+  return (GEOM != 0 && sizeof(T) == 4) ? (IP ? kNTpairIP : kNTpair + 32 * kProjWarpsGeom)
+                                       : (IP ? kNTip : kNTof<T>());
 }
 template <typename T, bool IP> constexpr int kMinBlocks() { return (IP && sizeof(T) == 4) ? 2 : 1; }
 
@@ -293,9 +299,9 @@ __device__ __forceinline__ typename Cplx<T>::type local_h(const OrbArgs<T>& a,
 template <typename T>
 __device__ __forceinline__ void project_tab(const OrbArgs<T>& a, const typename Cplx<T>::type* v,
                                             const typename Cplx<T>::type* ph, const int* tidx,
-                                            const T* tbeta, typename Cplx<T>::type* ec) {
+                                            const T* tbeta, typename Cplx<T>::type* ec, int warp, int nw) {
   using C = typename Cplx<T>::type;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31;
   for (int at = warp; at < a.natom; at += nw) {
     T acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     const int e1 = a.atom_off[at + 1];
@@ -1030,6 +1036,10 @@ __global__ void __launch_bounds__(kMaxThreads<T, IP, GEOM>(), kMinBlocks<T, IP>(
 
   const int nitems = nxy * a.nseg;
   constexpr int NSTAGE = (MODE == 1) ? 4 : 1;
+  // two copies with the grid size built in (FP32): the last kProjWarpsGeom warps project, the nit
+  // threads before them take the column segments
+  const bool sep_proj = GEOM != 0 && !IP && sizeof(T) == 4 && a.natom > 0;
+  const int nit = sep_proj ? (int)blockDim.x - 32 * kProjWarpsGeom : (int)blockDim.x;
   // per-thread partial sums of the observables {|u|^2, Im(conj(u) D1_a u) x3, Re(conj(u) H u)}
   T os[5] = {0, 0, 0, 0, 0};
 #pragma unroll 1
@@ -1037,7 +1047,11 @@ __global__ void __launch_bounds__(kMaxThreads<T, IP, GEOM>(), kMinBlocks<T, IP>(
     if constexpr (GEOM != 0) {
       // the projection only reads the current vector; the scatter that reads ec waits for the
       // barrier after the local pass (the in-place sweep replaces the vector: it waits here)
-      if (a.natom > 0) project_tab<T>(a, L.v, L.ph, tidx, tbeta, L.ec);
+      if (a.natom > 0) {
+        const int w = threadIdx.x >> 5;
+        if (!sep_proj) project_tab<T>(a, L.v, L.ph, tidx, tbeta, L.ec, w, blockDim.x >> 5);
+        else if (w >= nit / 32) project_tab<T>(a, L.v, L.ph, tidx, tbeta, L.ec, w - nit / 32, kProjWarpsGeom);
+      }
       if (IP) __syncthreads();
     } else if (a.natom > 0) {
       project<T>(a, L.v, L.ph, L.ec);
@@ -1110,7 +1124,7 @@ __global__ void __launch_bounds__(kMaxThreads<T, IP, GEOM>(), kMinBlocks<T, IP>(
         if constexpr (sizeof(T) == 4) {
           constexpr int npair_items = GeomP<GEOM>::NP * GeomP<GEOM>::NSEG;
 #pragma unroll 1
-          for (int item = threadIdx.x; item < npair_items; item += blockDim.x)
+          for (int item = threadIdx.x; item < npair_items && (int)threadIdx.x < nit; item += nit)
             fixed_pair<GEOM, MODE, ACC && PER>(a, item, sv, sn, Vc, psi, diag0, q, coef, os);
         } else {
 #pragma unroll 1
@@ -1348,6 +1362,7 @@ cudaError_t dispatch_geom(const OrbArgs<T>& a, cudaStream_t s) {
   int nt = ((items + 31) / 32) * 32;
   const int ntmax = sizeof(T) == 4 ? kNTpair : kNTof<T>();
   if (nt > ntmax) nt = ntmax;
+  if (sizeof(T) == 4 && a.natom > 0) nt += 32 * kProjWarpsGeom;   // the projecting warps (see k_cell)
   return g == 1 ? launch_cell<T, 1, true, true, OBS, false, 1>(a, nullptr, smem, nt, s)
                 : launch_cell<T, 1, true, true, OBS, false, 2>(a, nullptr, smem, nt, s);
 }
