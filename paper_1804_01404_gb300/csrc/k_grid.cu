@@ -13,6 +13,7 @@
 #include "ff.cuh"
 #include "grid_sum.cuh"
 #include "lda.cuh"
+#include "pdl.cuh"
 #include "tdks_internal.h"
 
 namespace tdks {
@@ -439,8 +440,10 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_planes_cluster(double2* dat
   // every CTA of the cluster must be running before any writes into its shared memory: arrive here,
   // wait just before the first remote store
   asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
-  for (int t = threadIdx.x; t < m0; t += blockDim.x) tw0[t] = tw0_g[t];
+  pdl_trigger();
+  for (int t = threadIdx.x; t < m0; t += blockDim.x) tw0[t] = tw0_g[t];     // tables fixed at set-up
   for (int t = threadIdx.x; t < m1; t += blockDim.x) tw1[t] = tw1_g[t];
+  pdl_wait();                                                                 // the kernel before
   const int y0 = r * m1 / CL, ny = (r + 1) * m1 / CL - y0;
   const int x0 = r * xh / CL, nc = (r + 1) * xh / CL - x0;
   const long long plane = (long long)(blockIdx.x / CL) * m0 * m1;
@@ -507,6 +510,8 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_zcol(double2* data, int m0,
                                                          const double* __restrict__ pfac,
                                                          const double* __restrict__ rho, int xc,
                                                          double* __restrict__ vxc) {
+  pdl_trigger();
+  pdl_wait();
   const int nzb = (xh * m1 + LZ - 1) / LZ;
   if ((int)blockIdx.x >= nzb) {
     const int npts = m0 * m1 * m2;
@@ -812,6 +817,7 @@ constexpr int kFoldLanes = 4;
 __global__ void __launch_bounds__(256) k_fold_density(const float* __restrict__ r32, int nk, int npts,
                                                       const double* __restrict__ kw, double* __restrict__ rho,
                                                       long long n) {
+  pdl_trigger();                                    // the Hartree solve may be scheduled (pdl.cuh)
   extern __shared__ float wsplit[];                 // [nk][2]
   for (int k = threadIdx.x; k < nk; k += blockDim.x) {
     const double w = kw[k];
@@ -961,20 +967,8 @@ cudaError_t launch_planes_cluster(double2* work, const int m[3], int cl, const d
   int threads = rmax * m[0] > cmax * m[1] ? rmax * m[0] : cmax * m[1];
   threads = (threads + 31) / 32 * 32;
   if (threads > kFftThreads) threads = kFftThreads;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(m[2] * cl));
-  cfg.blockDim = dim3((unsigned)threads);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = (unsigned)cl;
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_fft_planes_cluster<FWD>, work, m[0], m[1], xh, tw0, tw1, p0, p1, rho, xc, vhxc,
-                            rmax, cmax);
+  return launch_pdl(k_fft_planes_cluster<FWD>, dim3((unsigned)(m[2] * cl)), dim3((unsigned)threads), smem, s, cl,
+                    work, m[0], m[1], xh, tw0, tw1, p0, p1, rho, xc, vhxc, rmax, cmax);
 }
 
 // z pass of one cell for the cluster plane path: LZ lines per CTA so that the CTAs about fill the SMs;
@@ -995,8 +989,8 @@ cudaError_t launch_zcol(double2* work, const int m[3], const double2* tw2, const
     return e;
   const int nzb = (nlines + LZ - 1) / LZ;
   const int nxb = xc > 0 ? (m[0] * m[1] * m[2] + threads - 1) / threads : 0;
-  k_fft_zcol<<<nzb + nxb, threads, smem, s>>>(work, m[0], m[1], m[2], xh, LZ, tw2, p2, pfac, rho, xc, vxc);
-  return cudaGetLastError();
+  return launch_pdl(k_fft_zcol, dim3((unsigned)(nzb + nxb)), dim3((unsigned)threads), smem, s, 0, work, m[0], m[1],
+                    m[2], xh, LZ, tw2, p2, pfac, rho, xc, vxc);
 }
 
 }  // namespace

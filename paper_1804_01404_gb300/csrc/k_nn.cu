@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include "grid_sum.cuh"
+#include "pdl.cuh"
 #include "tdks_internal.h"
 
 namespace tdks {
@@ -342,6 +343,8 @@ __global__ void k_nn_apply(const double* __restrict__ V0, const double* __restri
 // res = ||Vnew - Vpred||_2 / ||Vnew||_2, summed over all CTAs by grid_sum
 __global__ void __launch_bounds__(256) k_residual(const double* __restrict__ Vnew, const double* __restrict__ Vpred,
                                                   int n, double* partials, unsigned* ticket, double* res) {
+  pdl_trigger();
+  pdl_wait();
   __shared__ double tot[2];
   double acc[2] = {0, 0};
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
@@ -861,8 +864,8 @@ cudaError_t launch_store6(double* dst, const double v[6], cudaStream_t s) {
 
 cudaError_t launch_residual(const double* Vnew, const double* Vpred, int n, double* partials, unsigned* ticket,
                             double* res, cudaStream_t s) {
-  k_residual<<<grid_sum_blocks(n, 256), 256, 0, s>>>(Vnew, Vpred, n, partials, ticket, res);
-  return cudaGetLastError();
+  return launch_pdl(k_residual, dim3((unsigned)grid_sum_blocks(n, 256)), dim3(256), 0, s, 0, Vnew, Vpred, n, partials,
+                    ticket, res);
 }
 
 }  // namespace tdks
