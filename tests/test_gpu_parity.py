@@ -41,8 +41,11 @@ def _systems():
     e.atoms = [W.Atom(at.R, at.Z) for at in e.atoms]
     f = W.tiny(periodic=True, n=(4, 5, 9), natom=1, norb=1)   # smallest allowed axis (4)
     f.h = (0.8, 0.7, 0.5)
+    # odd x extent (the Hermitian rebuild of the Hartree solve mirrors kx = 1..4 to 8..5) and radix
+    # 3 and 7 lines in the FFT of one periodic cell
+    g = W.tiny(periodic=True, n=(9, 6, 7), natom=1, norb=2)
     return {"tiny-periodic": a, "tiny-isolated-ragged": b, "small-periodic": c,
-            "diamond-2k": d, "cluster-22": e, "min-axis": f}
+            "diamond-2k": d, "cluster-22": e, "min-axis": f, "odd-periodic": g}
 
 
 SYSTEMS = _systems()
