@@ -425,7 +425,9 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_planes_cluster(double2* dat
                                                                     const double2* __restrict__ tw1_g,
                                                                     FftPlanArgs plan0, FftPlanArgs plan1,
                                                                     const double* __restrict__ rho, int xc,
-                                                                    double* __restrict__ vhxc, int rmax, int cmax) {
+                                                                    double* __restrict__ vhxc, int rmax, int cmax,
+                                                                    const double* __restrict__ vpred, double* partials,
+                                                                    unsigned* ticket, double* res) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
   const int CL = (int)cluster.num_blocks();
@@ -493,9 +495,20 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_planes_cluster(double2* dat
     src = rowA;
     dst = rowB;
     lines_out(src, dst, m0, ny, tw0, plan0, +1);                    // x lines of the own rows
+    double acc[2] = {0.0, 0.0};                                  // misfit sums (vpred given)
     for (int i = threadIdx.x; i < ny * m0; i += blockDim.x) {   // V_xc from the z pass launch
       const long long o = plane + (long long)y0 * m0 + i;
-      vhxc[o] = xc > 0 ? src[i].x + vhxc[o] : src[i].x;
+      const double v = xc > 0 ? src[i].x + vhxc[o] : src[i].x;
+      vhxc[o] = v;
+      if (vpred) {
+        const double d = v - vpred[o];
+        acc[0] += d * d;
+        acc[1] += v * v;
+      }
+    }
+    if (vpred) {                                                 // the same for every CTA
+      __shared__ double tot[2];
+      if (grid_sum<2>(acc, partials, ticket, tot) && threadIdx.x == 0) *res = sqrt(tot[0] / fmax(tot[1], 1e-300));
     }
   }
 }
@@ -956,7 +969,7 @@ namespace {
 template <bool FWD>
 cudaError_t launch_planes_cluster(double2* work, const int m[3], int cl, const double2* tw0, const double2* tw1,
                                   const FftPlanArgs& p0, const FftPlanArgs& p1, const double* rho, int xc,
-                                  double* vhxc, cudaStream_t s) {
+                                  double* vhxc, cudaStream_t s, const ResidualArgs* ra = nullptr) {
   const int xh = m[0] / 2 + 1;
   const int rmax = (m[1] + cl - 1) / cl, cmax = (xh + cl - 1) / cl;
   const size_t smem = plane_cluster_smem(m, cl);
@@ -967,8 +980,12 @@ cudaError_t launch_planes_cluster(double2* work, const int m[3], int cl, const d
   int threads = rmax * m[0] > cmax * m[1] ? rmax * m[0] : cmax * m[1];
   threads = (threads + 31) / 32 * 32;
   if (threads > kFftThreads) threads = kFftThreads;
+  const double* vpred = ra ? ra->vpred : nullptr;
+  double* partials = ra ? ra->partials : nullptr;
+  unsigned* ticket = ra ? ra->ticket : nullptr;
+  double* res = ra ? ra->res : nullptr;
   return launch_pdl(k_fft_planes_cluster<FWD>, dim3((unsigned)(m[2] * cl)), dim3((unsigned)threads), smem, s, cl,
-                    work, m[0], m[1], xh, tw0, tw1, p0, p1, rho, xc, vhxc, rmax, cmax);
+                    work, m[0], m[1], xh, tw0, tw1, p0, p1, rho, xc, vhxc, rmax, cmax, vpred, partials, ticket, res);
 }
 
 // z pass of one cell for the cluster plane path: LZ lines per CTA so that the CTAs about fill the SMs;
@@ -1004,7 +1021,7 @@ cudaError_t launch_hartree_xc_fused(double2* work, const int m[3], const int n[3
                                     const double h[3], const double* ghat, double gscale,
                                     double2* const tw[3], const int* const rad[3], const int nrad[3],
                                     const double* rho, int xc, double* vhxc, cudaStream_t s, int* nlaunch,
-                                    int plane_cl) {
+                                    int plane_cl, ResidualArgs* resid) {
   FftHooks base;
   std::memset(&base, 0, sizeof(base));
   base.n0 = n[0]; base.n1 = n[1]; base.n2 = n[2];
@@ -1051,7 +1068,13 @@ cudaError_t launch_hartree_xc_fused(double2* work, const int m[3], const int n[3
         return e;
     }
     if (nlaunch) *nlaunch = 3;
-    if (split) return launch_planes_cluster<false>(work, m, plane_cl, tw[0], tw[1], p0, p1, rho, xc, vhxc, s);
+    if (split) {
+      const bool with_res = resid && resid->vpred && m[2] * plane_cl <= 304;   // partials [304][2]
+      e = launch_planes_cluster<false>(work, m, plane_cl, tw[0], tw[1], p0, p1, rho, xc, vhxc, s,
+                                       with_res ? resid : nullptr);
+      if (e == cudaSuccess && with_res) resid->done = 1;
+      return e;
+    }
     k_fft_planes<false><<<grid, kFftThreads, plane_smem, s>>>(work, m[0], m[1], m[2], tw[0], tw[1], p0, p1, rho,
                                                               xc, vhxc, xhp);
     return cudaGetLastError();

@@ -124,6 +124,7 @@ struct tdks_ctx {
   double2* d_fft = nullptr;
   double2* d_tw[3] = {nullptr, nullptr, nullptr};
   double* d_ghat = nullptr;
+  ResidualArgs* res_args = nullptr;  // set around a predicted step's Hartree solve (see predicted_main)
   int plane_cl = 0;               // cluster size of the Hartree xy-plane passes (0: one CTA per plane)
   // observables
   double* d_orb_obs = nullptr;   // [nk*norb*8]
@@ -568,7 +569,7 @@ tdks_status hxc_lda(tdks_ctx* c, const double* rho, double* vhxc) {
     int nl = 0;
     TDKS_CUDA(launch_hartree_xc_fused(c->d_fft, c->m, c->grid.n, c->ncell, c->grid.periodic, c->grid.h,
                                       c->d_ghat, c->dV / npad, c->d_tw, rad, nrad, rho, c->opt.xc,
-                                      vhxc, c->stream, &nl, c->plane_cl));
+                                      vhxc, c->stream, &nl, c->plane_cl, c->res_args));
     c->launches += nl;
     return TDKS_OK;
   }
@@ -1775,9 +1776,17 @@ static tdks_status predicted_main(tdks_ctx* c, void* u, const double Amid[3], do
   c->cur_backup = nullptr;
   TDKS_TRY(cs);
   if (obs_branch) TDKS_TRY(fork_step_observables(c, obs_start));
-  TDKS_TRY(hxc(c, c->d_rho, c->d_vnew, u));
-  TDKS_CUDA(launch_residual(c->d_vnew, c->d_vpred, c->npts, c->d_partials, c->d_ticket, c->d_resid, c->stream));
-  c->launches += 1;
+  // the misfit: formed by the Hartree solve's last launch where it can (one periodic cell, xc
+  // without the TB-mBJ exchange, which is added after it), else by its own kernel
+  ResidualArgs ra{c->d_vpred, c->d_partials, c->d_ticket, c->d_resid, 0};
+  c->res_args = c->opt.xc != 3 ? &ra : nullptr;
+  const tdks_status hs = hxc(c, c->d_rho, c->d_vnew, u);
+  c->res_args = nullptr;
+  TDKS_TRY(hs);
+  if (!ra.done) {
+    TDKS_CUDA(launch_residual(c->d_vnew, c->d_vpred, c->npts, c->d_partials, c->d_ticket, c->d_resid, c->stream));
+    c->launches += 1;
+  }
   return TDKS_OK;
 }
 

@@ -248,6 +248,16 @@ cudaError_t launch_decide(const double* res, double thr, const double* vnew, dou
 cudaError_t launch_store6(double* dst, const double v[6], cudaStream_t s);
 
 // Grid kernels (k_grid.cu)
+// The misfit of a predicted potential, sqrt(sum (V - vpred)^2 / sum V^2) over the points of V (as
+// launch_residual forms it), when the Hartree solve can form it in its last launch: partials
+// [304][2] and ticket as for grid_sum; done is set to 1 when it did.
+struct ResidualArgs {
+  const double* vpred;
+  double* partials;
+  unsigned* ticket;
+  double* res;
+  int done;
+};
 // Hartree + exchange in five fused FFT line passes (three for periodic boxes whose xy-plane fits in
 // shared memory): vhxc = V_H[rho] (+ V_x[rho] if xc).  work: the transform box m^3 per cell (m = n
 // periodic, 2n isolated); batch: cells (periodic only); ghat: the periodic Poisson factors
@@ -257,7 +267,7 @@ cudaError_t launch_hartree_xc_fused(double2* work, const int m[3], const int n[3
                                     const double h[3], const double* ghat, double gscale,
                                     double2* const tw[3], const int* const rad[3], const int nrad[3],
                                     const double* rho, int xc, double* vhxc, cudaStream_t s,
-                                    int* nlaunch = nullptr, int plane_cl = 0);
+                                    int* nlaunch = nullptr, int plane_cl = 0, ResidualArgs* resid = nullptr);
 // Cluster size for the xy-plane passes of one periodic cell of transform box m: the largest of 8 .. 2
 // whose clusters (one CTA per SM) are all resident at once, 0 where the split does not apply.
 int hartree_plane_cluster(const int m[3], int batch, int periodic);
