@@ -184,10 +184,13 @@ __device__ __forceinline__ void stage_out(const double2* __restrict__ src, doubl
         acc.y = fma((p == 0 || p == 3) ? 1.0 : -1.0, im, acc.y);
       }
     } else {
-      const int step = k * tstep + m * nr;
+      const int step = k * tstep + m * nr;             // < n, so (r step) mod n by one wrap per r
+      int ti = 0;
       for (int r = 1; r < R; ++r) {
         const double2 x = sl[r * nr];
-        double2 w = tw[(r * step) % n];
+        ti += step;
+        ti -= ti >= n ? n : 0;
+        double2 w = tw[ti];
         if (dir > 0) w.y = -w.y;
         acc.x = fma(x.x, w.x, acc.x);
         acc.x = fma(-x.y, w.y, acc.x);
@@ -209,6 +212,66 @@ __device__ __forceinline__ void lines_out(double2*& src, double2*& dst, int n, i
     __syncthreads();
     double2* t = src; src = dst; dst = t;
     Ns *= plan.rad[s];
+  }
+}
+
+// stage_out with the line length, radix and stage span known at compile time (the index divisions
+// become multiplications); the same arithmetic.
+template <int N, int R, int NS>
+__device__ __forceinline__ void stage_out_c(const double2* __restrict__ src, double2* __restrict__ dst, int nl,
+                                            const double2* __restrict__ tw, int dir) {
+  constexpr int nr = N / R, span = NS * R, tstep = N / span;
+  for (int t = threadIdx.x; t < nl * N; t += blockDim.x) {
+    const int j = t / N, q = t - j * N;
+    const int g = q / span, rem = q - g * span;
+    const int m = rem / NS, k = rem - m * NS;
+    const double2* sl = src + j * N + g * NS + k;
+    double2 acc = sl[0];
+    if constexpr (NS == 1 && (R == 2 || R == 4)) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        const double2 x = sl[r * nr];
+        int p = (R == 4 ? r * m : 2 * r * m) & 3;
+        if (dir > 0) p = (4 - p) & 3;
+        const double re = (p & 1) ? x.y : x.x, im = (p & 1) ? x.x : x.y;
+        acc.x = fma(p < 2 ? 1.0 : -1.0, re, acc.x);
+        acc.y = fma((p == 0 || p == 3) ? 1.0 : -1.0, im, acc.y);
+      }
+    } else {
+      const int step = k * tstep + m * nr;
+      int ti = 0;
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        const double2 x = sl[r * nr];
+        ti += step;
+        ti -= ti >= N ? N : 0;
+        double2 w = tw[ti];
+        if (dir > 0) w.y = -w.y;
+        acc.x = fma(x.x, w.x, acc.x);
+        acc.x = fma(-x.y, w.y, acc.x);
+        acc.y = fma(x.x, w.y, acc.y);
+        acc.y = fma(x.y, w.x, acc.y);
+      }
+    }
+    dst[t] = acc;
+  }
+}
+
+// Lines of a compiled length N (N > 0: 16 = 4 x 4, 20 = 4 x 5, the radix plans of fft_radices) or
+// of the runtime length n and plan (N = 0).
+template <int N>
+__device__ __forceinline__ void lines_any(double2*& src, double2*& dst, int n, int nl, const double2* tw,
+                                          const FftPlanArgs& plan, int dir) {
+  if constexpr (N == 0) {
+    lines_out(src, dst, n, nl, tw, plan, dir);
+  } else {
+    static_assert(N == 16 || N == 20, "compiled line lengths: 16 and 20");
+    stage_out_c<N, 4, 1>(src, dst, nl, tw, dir);
+    __syncthreads();
+    { double2* t = src; src = dst; dst = t; }
+    stage_out_c<N, N / 4, 4>(src, dst, nl, tw, dir);
+    __syncthreads();
+    { double2* t = src; src = dst; dst = t; }
   }
 }
 
@@ -418,9 +481,10 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_planes(double2* data, int m
 // -> columns kx < xh -> y spectra -> data.  Inverse: columns of data -> y inverse -> rows, with
 // X(m0 - kx) = conj(X(kx)) filling kx >= xh -> x inverse -> vhxc = Re + vhxc (V_xc(rho), written by the
 // z pass launch; V_H alone for xc = 0).  Shared memory:
-// m0 + m1 twiddles, two row buffers of rmax x m0 and two column buffers of cmax x m1.
-template <bool FWD>
-__global__ void __launch_bounds__(kFftThreads) k_fft_planes_cluster(double2* data, int m0, int m1, int xh,
+// m0 + m1 twiddles, two row buffers of rmax x m0 and two column buffers of cmax x m1.  N > 0: a cube
+// of edge N (16 or 20) compiled in.
+template <bool FWD, int N>
+__global__ void __launch_bounds__(kFftThreads) k_fft_planes_cluster(double2* data, int m0_, int m1_, int xh_,
                                                                     const double2* __restrict__ tw0_g,
                                                                     const double2* __restrict__ tw1_g,
                                                                     FftPlanArgs plan0, FftPlanArgs plan1,
@@ -430,8 +494,10 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_planes_cluster(double2* dat
                                                                     unsigned* ticket, double* res) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
+  const int m0 = N > 0 ? N : m0_, m1 = N > 0 ? N : m1_, xh = N > 0 ? N / 2 + 1 : xh_;
   const int CL = (int)cluster.num_blocks();
   const int r = (int)cluster.block_rank();
+  __shared__ int rb[9], cb[9];                      // first row / column of each rank (CL <= 8)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double2* tw0 = reinterpret_cast<double2*>(smem_raw);
   double2* tw1 = tw0 + m0;
@@ -445,6 +511,10 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_planes_cluster(double2* dat
   pdl_trigger();
   for (int t = threadIdx.x; t < m0; t += blockDim.x) tw0[t] = tw0_g[t];     // tables fixed at set-up
   for (int t = threadIdx.x; t < m1; t += blockDim.x) tw1[t] = tw1_g[t];
+  if (threadIdx.x <= (unsigned)CL) {
+    rb[threadIdx.x] = (int)threadIdx.x * m1 / CL;
+    cb[threadIdx.x] = (int)threadIdx.x * xh / CL;
+  }
   pdl_wait();                                                                 // the kernel before
   const int y0 = r * m1 / CL, ny = (r + 1) * m1 / CL - y0;
   const int x0 = r * xh / CL, nc = (r + 1) * xh / CL - x0;
@@ -455,19 +525,19 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_planes_cluster(double2* dat
     __syncthreads();
     double2* src = rowA;
     double2* dst = rowB;
-    lines_out(src, dst, m0, ny, tw0, plan0, -1);                    // x lines of the own rows
+    lines_any<N>(src, dst, m0, ny, tw0, plan0, -1);                 // x lines of the own rows
     asm volatile("barrier.cluster.wait.aligned;" ::: "memory");
     for (int i = threadIdx.x; i < ny * xh; i += blockDim.x) {        // row spectra -> column owners
       const int yy = i / xh, kx = i - yy * xh;
       int o = 0;
-      while (o + 1 < CL && (o + 1) * xh / CL <= kx) ++o;
+      while (o + 1 < CL && cb[o + 1] <= kx) ++o;
       double2* col = cluster.map_shared_rank(colA, o);
-      col[(kx - o * xh / CL) * m1 + y0 + yy] = src[yy * m0 + kx];
+      col[(kx - cb[o]) * m1 + y0 + yy] = src[yy * m0 + kx];
     }
     cluster.sync();
     src = colA;
     dst = colB;
-    lines_out(src, dst, m1, nc, tw1, plan1, -1);                    // y lines of the own columns
+    lines_any<N>(src, dst, m1, nc, tw1, plan1, -1);                 // y lines of the own columns
     for (int i = threadIdx.x; i < m1 * nc; i += blockDim.x) {
       const int y = i / nc, c = i - y * nc;
       data[plane + (long long)y * m0 + x0 + c] = src[c * m1 + y];
@@ -480,13 +550,13 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_planes_cluster(double2* dat
     __syncthreads();
     double2* src = colA;
     double2* dst = colB;
-    lines_out(src, dst, m1, nc, tw1, plan1, +1);                    // y lines of the own columns
+    lines_any<N>(src, dst, m1, nc, tw1, plan1, +1);                 // y lines of the own columns
     asm volatile("barrier.cluster.wait.aligned;" ::: "memory");
     for (int i = threadIdx.x; i < nc * m1; i += blockDim.x) {        // -> row owners, with the mirror
       const int c = i / m1, y = i - c * m1, kx = x0 + c;
       int o = 0;
-      while (o + 1 < CL && (o + 1) * m1 / CL <= y) ++o;
-      double2* row = cluster.map_shared_rank(rowA, o) + (size_t)(y - o * m1 / CL) * m0;
+      while (o + 1 < CL && rb[o + 1] <= y) ++o;
+      double2* row = cluster.map_shared_rank(rowA, o) + (size_t)(y - rb[o]) * m0;
       const double2 v = src[c * m1 + y];
       row[kx] = v;
       if (kx >= 1 && m0 - kx >= xh) row[m0 - kx] = double2{v.x, -v.y};
@@ -494,7 +564,7 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_planes_cluster(double2* dat
     cluster.sync();
     src = rowA;
     dst = rowB;
-    lines_out(src, dst, m0, ny, tw0, plan0, +1);                    // x lines of the own rows
+    lines_any<N>(src, dst, m0, ny, tw0, plan0, +1);                 // x lines of the own rows
     double acc[2] = {0.0, 0.0};                                  // misfit sums (vpred given)
     for (int i = threadIdx.x; i < ny * m0; i += blockDim.x) {   // V_xc from the z pass launch
       const long long o = plane + (long long)y0 * m0 + i;
@@ -518,11 +588,13 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_planes_cluster(double2* dat
 // in place; output by output (lines_out), one thread per element.  The CTAs past the z lines form
 // V_xc(rho) of every point into vxc (xc > 0), which the inverse plane kernel adds to V_H: the
 // exchange-correlation chains run beside the z transforms instead of after the last one.
-__global__ void __launch_bounds__(kFftThreads) k_fft_zcol(double2* data, int m0, int m1, int m2, int xh, int LZ,
+template <int N>
+__global__ void __launch_bounds__(kFftThreads) k_fft_zcol(double2* data, int m0_, int m1_, int m2_, int xh_, int LZ,
                                                          const double2* __restrict__ tw_g, FftPlanArgs plan,
                                                          const double* __restrict__ pfac,
                                                          const double* __restrict__ rho, int xc,
                                                          double* __restrict__ vxc) {
+  const int m0 = N > 0 ? N : m0_, m1 = N > 0 ? N : m1_, m2 = N > 0 ? N : m2_, xh = N > 0 ? N / 2 + 1 : xh_;
   pdl_trigger();
   pdl_wait();
   const int nzb = (xh * m1 + LZ - 1) / LZ;
@@ -548,7 +620,7 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_zcol(double2* data, int m0,
   __syncthreads();
   double2* src = b0;
   double2* dst = b1;
-  lines_out(src, dst, m2, nl, tw, plan, -1);
+  lines_any<N>(src, dst, m2, nl, tw, plan, -1);
   for (int t = threadIdx.x; t < nl * m2; t += blockDim.x) {
     const int j = t / m2, e = t - j * m2, l = l0 + j;
     const int y = l / xh, x = l - y * xh;
@@ -556,7 +628,7 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_zcol(double2* data, int m0,
     src[t] = double2{src[t].x * f, src[t].y * f};
   }
   __syncthreads();
-  lines_out(src, dst, m2, nl, tw, plan, +1);
+  lines_any<N>(src, dst, m2, nl, tw, plan, +1);
   for (int t = threadIdx.x; t < nl * m2; t += blockDim.x) {
     const int e = t / nl, j = t - e * nl, l = l0 + j;
     const int y = l / xh, x = l - y * xh;
@@ -938,7 +1010,7 @@ int hartree_plane_cluster(const int m[3], int batch, int periodic) {
   for (int cl = 8; cl >= 2; --cl) {
     if (cl > m[1] || cl > xh || m[2] * cl > nsm) continue;
     const size_t smem = plane_cluster_smem(m, cl);
-    if (cudaFuncSetAttribute(k_fft_planes_cluster<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+    if (cudaFuncSetAttribute(k_fft_planes_cluster<true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess) {
       cudaGetLastError();
       return 0;
@@ -955,7 +1027,7 @@ int hartree_plane_cluster(const int m[3], int batch, int periodic) {
     cfg.attrs = at;
     cfg.numAttrs = 1;
     int nclusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&nclusters, (const void*)k_fft_planes_cluster<true>, &cfg) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&nclusters, (const void*)k_fft_planes_cluster<true, 0>, &cfg) != cudaSuccess) {
       cudaGetLastError();
       continue;
     }
@@ -966,6 +1038,11 @@ int hartree_plane_cluster(const int m[3], int batch, int periodic) {
 
 namespace {
 
+// The cube edge compiled into the single-cell kernels (16 or 20), 0 for other boxes.
+int compiled_edge(const int m[3]) {
+  return (m[0] == m[1] && m[1] == m[2] && (m[0] == 16 || m[0] == 20)) ? m[0] : 0;
+}
+
 template <bool FWD>
 cudaError_t launch_planes_cluster(double2* work, const int m[3], int cl, const double2* tw0, const double2* tw1,
                                   const FftPlanArgs& p0, const FftPlanArgs& p1, const double* rho, int xc,
@@ -973,8 +1050,10 @@ cudaError_t launch_planes_cluster(double2* work, const int m[3], int cl, const d
   const int xh = m[0] / 2 + 1;
   const int rmax = (m[1] + cl - 1) / cl, cmax = (xh + cl - 1) / cl;
   const size_t smem = plane_cluster_smem(m, cl);
-  cudaError_t e = cudaFuncSetAttribute(k_fft_planes_cluster<FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  const int edge = compiled_edge(m);
+  auto kern = edge == 20 ? k_fft_planes_cluster<FWD, 20> : edge == 16 ? k_fft_planes_cluster<FWD, 16>
+                                                                       : k_fft_planes_cluster<FWD, 0>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   // one thread per element of the larger line set (rows or columns)
   int threads = rmax * m[0] > cmax * m[1] ? rmax * m[0] : cmax * m[1];
@@ -984,8 +1063,8 @@ cudaError_t launch_planes_cluster(double2* work, const int m[3], int cl, const d
   double* partials = ra ? ra->partials : nullptr;
   unsigned* ticket = ra ? ra->ticket : nullptr;
   double* res = ra ? ra->res : nullptr;
-  return launch_pdl(k_fft_planes_cluster<FWD>, dim3((unsigned)(m[2] * cl)), dim3((unsigned)threads), smem, s, cl,
-                    work, m[0], m[1], xh, tw0, tw1, p0, p1, rho, xc, vhxc, rmax, cmax, vpred, partials, ticket, res);
+  return launch_pdl(kern, dim3((unsigned)(m[2] * cl)), dim3((unsigned)threads), smem, s, cl, work, m[0], m[1], xh,
+                    tw0, tw1, p0, p1, rho, xc, vhxc, rmax, cmax, vpred, partials, ticket, res);
 }
 
 // z pass of one cell for the cluster plane path: LZ lines per CTA so that the CTAs about fill the SMs;
@@ -1002,12 +1081,14 @@ cudaError_t launch_zcol(double2* work, const int m[3], const double2* tw2, const
   int threads = (LZ * m[2] + 31) / 32 * 32;
   if (threads > kFftThreads) threads = kFftThreads;
   const size_t smem = ((size_t)m[2] + 2 * (size_t)LZ * m[2]) * sizeof(double2);
-  if ((e = cudaFuncSetAttribute(k_fft_zcol, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+  const int edge = compiled_edge(m);
+  auto kern = edge == 20 ? k_fft_zcol<20> : edge == 16 ? k_fft_zcol<16> : k_fft_zcol<0>;
+  if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
     return e;
   const int nzb = (nlines + LZ - 1) / LZ;
   const int nxb = xc > 0 ? (m[0] * m[1] * m[2] + threads - 1) / threads : 0;
-  return launch_pdl(k_fft_zcol, dim3((unsigned)(nzb + nxb)), dim3((unsigned)threads), smem, s, 0, work, m[0], m[1],
-                    m[2], xh, LZ, tw2, p2, pfac, rho, xc, vxc);
+  return launch_pdl(kern, dim3((unsigned)(nzb + nxb)), dim3((unsigned)threads), smem, s, 0, work, m[0], m[1], m[2],
+                    xh, LZ, tw2, p2, pfac, rho, xc, vxc);
 }
 
 }  // namespace
