@@ -895,10 +895,11 @@ __global__ void __launch_bounds__(256) k_orbital_dots(const C* __restrict__ u, c
   }
 }
 
-// rho[cell][p] = sum_k w_k rho32[cell][k][p].  Four lanes share a point, each summing every fourth
-// k in float-float (ff.cuh) with the weights split into float pairs once per CTA, then the lanes add
-// their sums by shuffles; one FP64 conversion per point.
-constexpr int kFoldLanes = 4;
+// rho[cell][p] = sum_k w_k rho32[cell][k][p].  Eight lanes share a point, each summing every eighth
+// k in float-float (ff.cuh) with the weights split into float pairs once per CTA, four loads in
+// flight before their sums (the partials were just written: L2 latency), then the lanes add their
+// sums by shuffles; one FP64 conversion per point.  32-bit indices (the host checks the size).
+constexpr int kFoldLanes = 8;
 __global__ void __launch_bounds__(256) k_fold_density(const float* __restrict__ r32, int nk, int npts,
                                                       const double* __restrict__ kw, double* __restrict__ rho,
                                                       long long n) {
@@ -911,17 +912,28 @@ __global__ void __launch_bounds__(256) k_fold_density(const float* __restrict__ 
     wsplit[2 * k + 1] = (float)(w - (double)wh);
   }
   __syncthreads();
-  const long long total = n * kFoldLanes;
-  for (long long t0 = (long long)blockIdx.x * blockDim.x; t0 < total; t0 += (long long)gridDim.x * blockDim.x) {
-    const long long t = t0 + threadIdx.x;           // every lane of the warp runs the iteration
+  const int total = (int)n * kFoldLanes;
+  for (int t0 = blockIdx.x * blockDim.x; t0 < total; t0 += gridDim.x * blockDim.x) {
+    const int t = t0 + threadIdx.x;                 // every lane of the warp runs the iteration
     const bool act = t < total;
-    const long long i = act ? t / kFoldLanes : 0;
-    const int part = (int)(t % kFoldLanes);
+    const int i = act ? t / kFoldLanes : 0;
+    const int part = t % kFoldLanes;
     FF acc{0.f, 0.f};
     if (act) {
-      const long long cell = i / npts, p = i - cell * npts;
-      for (int k = part; k < nk; k += kFoldLanes)
-        acc = ff_add(acc, ff_mul(wsplit[2 * k], wsplit[2 * k + 1], r32[(cell * nk + k) * npts + p]));
+      const int cell = i / npts, p = i - cell * npts;
+      const float* base = r32 + cell * nk * npts + p;
+      int k = part;
+      for (; k + 3 * kFoldLanes < nk; k += 4 * kFoldLanes) {
+        float x[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) x[j] = base[(k + j * kFoldLanes) * npts];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int kk = k + j * kFoldLanes;
+          acc = ff_add(acc, ff_mul(wsplit[2 * kk], wsplit[2 * kk + 1], x[j]));
+        }
+      }
+      for (; k < nk; k += kFoldLanes) acc = ff_add(acc, ff_mul(wsplit[2 * k], wsplit[2 * k + 1], base[k * npts]));
     }
 #pragma unroll
     for (int o = 1; o < kFoldLanes; o <<= 1) acc = ff_add(acc, ff_shfl_xor(acc, o));
@@ -1365,6 +1377,7 @@ cudaError_t launch_ms_current(const double* step_obs, int ncell, int m0, double*
 cudaError_t launch_fold_density(const float* rho32, int nk, int npts, const double* kw, double* rho,
                                 cudaStream_t s, int ncell) {
   const long long n = (long long)npts * ncell;
+  if (n * kFoldLanes >= (1LL << 31) || n * nk >= (1LL << 31)) return cudaErrorInvalidValue;   // 32-bit indices
   k_fold_density<<<grid_for(n * kFoldLanes, 256), 256, 2 * sizeof(float) * (size_t)nk, s>>>(rho32, nk, npts, kw,
                                                                                             rho, n);
   return cudaGetLastError();

@@ -99,7 +99,9 @@ struct tdks_ctx {
   double *d_vloc = nullptr, *d_vhxc = nullptr, *d_vpred = nullptr, *d_rho = nullptr,
          *d_rho0 = nullptr, *d_rho_tmp = nullptr, *d_v64 = nullptr;
   float* d_v32 = nullptr;
-  float* d_rho32 = nullptr;      // [nk][npts] per-k FP32 density partials (FP32 orbitals)
+  float* d_rho32 = nullptr;      // [nk][npts] per-k FP32 density partials (FP32 orbitals); zero
+                                 // outside an orbital kernel and its fold (zeroed after each fold)
+  bool defer_r32_zero = false;   // the caller zeroes d_rho32 after the fold (a parallel graph branch)
   void* d_scratch = nullptr;     // [norb_tot][npts] complex, only for cells whose two copies exceed smem
   // large isolated grids (tile kernels): two Horner buffers and the projection coefficients
   bool tiled = false;
@@ -480,9 +482,8 @@ tdks_status orbital_kernel(tdks_ctx* c, int mode, const void* in, void* out, con
   if (is_f32(c)) {
     auto a = make_args<float>(c, in, out, c->d_v32, Ap, dt, rho, write_out);
     if (rho) {
-      // per-k FP32 partial densities, folded into rho in FP64 afterwards (a memset here costs less
-      // in a step than zeroing them in the fold kernel, measured)
-      TDKS_CUDA(cudaMemsetAsync(c->d_rho32, 0, sizeof(float) * (size_t)c->ncell * c->nk * c->npts, c->stream));
+      // per-k FP32 partial densities (zero on entry), folded into rho in FP64 afterwards and zeroed
+      // again by a memset (cheaper in a step than zeroing them in the fold kernel, measured)
       a.rho = nullptr;
       a.rho32 = c->d_rho32;
     }
@@ -498,6 +499,8 @@ tdks_status orbital_kernel(tdks_ctx* c, int mode, const void* in, void* out, con
     if (rho) {
       TDKS_CUDA(launch_fold_density(c->d_rho32, c->nk, c->npts, c->d_kw, rho, c->stream, c->ncell));
       c->launches += 1;
+      if (!c->defer_r32_zero)
+        TDKS_CUDA(cudaMemsetAsync(c->d_rho32, 0, sizeof(float) * (size_t)c->ncell * c->nk * c->npts, c->stream));
     }
   } else {
     auto a = make_args<double>(c, in, out, c->d_v64, Ap, dt, rho, write_out);
@@ -945,8 +948,10 @@ tdks_status tdks_init(const tdks_grid* grid, const tdks_cell* cell, const tdks_a
     return bail(fail(TDKS_ECUDA, "memset"));
   if ((s = dalloc(c, &c->d_apf, 6)) != TDKS_OK) return bail(s);
   if (cudaMallocHost((void**)&c->h_resid, 16 * sizeof(double)) != cudaSuccess) return bail(fail(TDKS_ENOMEM, "pinned"));
-  if (is_f32(c) && !c->tiled)
+  if (is_f32(c) && !c->tiled) {
     if ((s = dalloc(c, &c->d_rho32, npc * (size_t)nk)) != TDKS_OK) return bail(s);
+    cudaMemsetAsync(c->d_rho32, 0, sizeof(float) * npc * (size_t)nk, c->stream);
+  }
   cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
   if (c->tiled) {
     const size_t csz = is_f32(c) ? sizeof(float2) : sizeof(double2);
@@ -1732,12 +1737,15 @@ static tdks_status step_observables(tdks_ctx* c, bool at_start, double* partials
 // (whose FFT kernels occupy few SMs): they need only what the orbital kernel left (the per-orbital
 // sums and the density).  The graph joins the branch before the accept / fallback decision, and a
 // fallback body computes them again from its own orbitals.
-static tdks_status fork_step_observables(tdks_ctx* c, bool at_start) {
+static tdks_status fork_step_observables(tdks_ctx* c, bool at_start, bool zero_r32) {
   TDKS_CUDA(cudaEventRecord(c->ev_obs_fork, c->stream));
   TDKS_CUDA(cudaStreamWaitEvent(c->obs_side, c->ev_obs_fork, 0));
   const cudaStream_t main = c->stream;
   c->stream = c->obs_side;
-  const tdks_status st = step_observables(c, at_start, c->d_partials_obs, c->d_ticket_obs);
+  tdks_status st = step_observables(c, at_start, c->d_partials_obs, c->d_ticket_obs);
+  if (st == TDKS_OK && zero_r32 &&   // the per-k density partials, consumed by the fold
+      cudaMemsetAsync(c->d_rho32, 0, sizeof(float) * (size_t)c->ncell * c->nk * c->npts, c->stream) != cudaSuccess)
+    st = fail(TDKS_ECUDA, "memset of the density partials");
   c->stream = main;
   TDKS_TRY(st);
   TDKS_CUDA(cudaEventRecord(c->ev_obs_join, c->obs_side));
@@ -1772,10 +1780,14 @@ static tdks_status predicted_main(tdks_ctx* c, void* u, const double Amid[3], do
   }
   if (!step_pot_done) TDKS_TRY(set_step_potential(c, 0.5, c->d_vpred, 0.5));
   c->cur_backup = c->tiled ? nullptr : c->d_backup;
+  // in a step graph the per-k density partials are zeroed on the observables branch
+  const bool defer = obs_branch && rho_overwritten(c);
+  c->defer_r32_zero = defer;
   const tdks_status cs = orbital_kernel(c, 1, u, u, Amid, dt, c->d_rho, 1, Aobs, obs_start);
+  c->defer_r32_zero = false;
   c->cur_backup = nullptr;
   TDKS_TRY(cs);
-  if (obs_branch) TDKS_TRY(fork_step_observables(c, obs_start));
+  if (obs_branch) TDKS_TRY(fork_step_observables(c, obs_start, defer));
   // the misfit: formed by the Hartree solve's last launch where it can (one periodic cell, xc
   // without the TB-mBJ exchange, which is added after it), else by its own kernel
   ResidualArgs ra{c->d_vpred, c->d_partials, c->d_ticket, c->d_resid, 0};
