@@ -896,22 +896,14 @@ __global__ void __launch_bounds__(256) k_orbital_dots(const C* __restrict__ u, c
 }
 
 // rho[cell][p] = sum_k w_k rho32[cell][k][p].  Eight lanes share a point, each summing every eighth
-// k in float-float (ff.cuh) with the weights split into float pairs once per CTA, four loads in
+// k in float-float (ff.cuh) with the weights as float pairs (split once at set-up), four loads in
 // flight before their sums (the partials were just written: L2 latency), then the lanes add their
 // sums by shuffles; one FP64 conversion per point.  32-bit indices (the host checks the size).
 constexpr int kFoldLanes = 8;
 __global__ void __launch_bounds__(256) k_fold_density(const float* __restrict__ r32, int nk, int npts,
-                                                      const double* __restrict__ kw, double* __restrict__ rho,
+                                                      const float* __restrict__ wsplit, double* __restrict__ rho,
                                                       long long n) {
   pdl_trigger();                                    // the Hartree solve may be scheduled (pdl.cuh)
-  extern __shared__ float wsplit[];                 // [nk][2]
-  for (int k = threadIdx.x; k < nk; k += blockDim.x) {
-    const double w = kw[k];
-    const float wh = (float)w;
-    wsplit[2 * k] = wh;
-    wsplit[2 * k + 1] = (float)(w - (double)wh);
-  }
-  __syncthreads();
   const int total = (int)n * kFoldLanes;
   for (int t0 = blockIdx.x * blockDim.x; t0 < total; t0 += gridDim.x * blockDim.x) {
     const int t = t0 + threadIdx.x;                 // every lane of the warp runs the iteration
@@ -930,10 +922,11 @@ __global__ void __launch_bounds__(256) k_fold_density(const float* __restrict__ 
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           const int kk = k + j * kFoldLanes;
-          acc = ff_add(acc, ff_mul(wsplit[2 * kk], wsplit[2 * kk + 1], x[j]));
+          acc = ff_add(acc, ff_mul(__ldg(wsplit + 2 * kk), __ldg(wsplit + 2 * kk + 1), x[j]));
         }
       }
-      for (; k < nk; k += kFoldLanes) acc = ff_add(acc, ff_mul(wsplit[2 * k], wsplit[2 * k + 1], base[k * npts]));
+      for (; k < nk; k += kFoldLanes)
+        acc = ff_add(acc, ff_mul(__ldg(wsplit + 2 * k), __ldg(wsplit + 2 * k + 1), base[k * npts]));
     }
 #pragma unroll
     for (int o = 1; o < kFoldLanes; o <<= 1) acc = ff_add(acc, ff_shfl_xor(acc, o));
@@ -1374,12 +1367,11 @@ cudaError_t launch_ms_current(const double* step_obs, int ncell, int m0, double*
   return cudaGetLastError();
 }
 
-cudaError_t launch_fold_density(const float* rho32, int nk, int npts, const double* kw, double* rho,
+cudaError_t launch_fold_density(const float* rho32, int nk, int npts, const float* wsplit, double* rho,
                                 cudaStream_t s, int ncell) {
   const long long n = (long long)npts * ncell;
   if (n * kFoldLanes >= (1LL << 31) || n * nk >= (1LL << 31)) return cudaErrorInvalidValue;   // 32-bit indices
-  k_fold_density<<<grid_for(n * kFoldLanes, 256), 256, 2 * sizeof(float) * (size_t)nk, s>>>(rho32, nk, npts, kw,
-                                                                                            rho, n);
+  k_fold_density<<<grid_for(n * kFoldLanes, 256), 256, 0, s>>>(rho32, nk, npts, wsplit, rho, n);
   return cudaGetLastError();
 }
 

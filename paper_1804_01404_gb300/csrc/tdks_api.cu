@@ -95,6 +95,7 @@ struct tdks_ctx {
   double *d_beta64 = nullptr, *d_d64 = nullptr, *d_E64 = nullptr;
   float *d_beta32 = nullptr, *d_d32 = nullptr, *d_E32 = nullptr;
   double *d_kpts = nullptr, *d_kw = nullptr;
+  float* d_kwsplit = nullptr;    // [nk][2]: each k weight as a float pair (the density fold)
   // grid arrays
   double *d_vloc = nullptr, *d_vhxc = nullptr, *d_vpred = nullptr, *d_rho = nullptr,
          *d_rho0 = nullptr, *d_rho_tmp = nullptr, *d_v64 = nullptr;
@@ -497,7 +498,7 @@ tdks_status orbital_kernel(tdks_ctx* c, int mode, const void* in, void* out, con
       TDKS_CUDA(launch_smem_orbital<float>(a, mode, static_cast<float2*>(c->d_scratch), c->stream));
     }
     if (rho) {
-      TDKS_CUDA(launch_fold_density(c->d_rho32, c->nk, c->npts, c->d_kw, rho, c->stream, c->ncell));
+      TDKS_CUDA(launch_fold_density(c->d_rho32, c->nk, c->npts, c->d_kwsplit, rho, c->stream, c->ncell));
       c->launches += 1;
       if (!c->defer_r32_zero)
         TDKS_CUDA(cudaMemsetAsync(c->d_rho32, 0, sizeof(float) * (size_t)c->ncell * c->nk * c->npts, c->stream));
@@ -925,6 +926,15 @@ tdks_status tdks_init(const tdks_grid* grid, const tdks_cell* cell, const tdks_a
   }
   if ((s = upload(c, &c->d_kpts, c->kpts)) != TDKS_OK) return bail(s);
   if ((s = upload(c, &c->d_kw, c->kw)) != TDKS_OK) return bail(s);
+  {
+    std::vector<float> ws(2 * c->kw.size());
+    for (size_t k = 0; k < c->kw.size(); ++k) {
+      const float hi = (float)c->kw[k];
+      ws[2 * k] = hi;
+      ws[2 * k + 1] = (float)(c->kw[k] - (double)hi);
+    }
+    if ((s = upload(c, &c->d_kwsplit, ws)) != TDKS_OK) return bail(s);
+  }
 
   const size_t np = c->npts;
   const size_t npc = np * c->ncell;        // per-cell arrays

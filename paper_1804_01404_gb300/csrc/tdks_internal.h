@@ -351,8 +351,9 @@ cudaError_t launch_maxwell(const double* A_prev, const double* A_now, double* A_
 // I[m0 + c] = step_obs[c*8 + 2]
 cudaError_t launch_ms_current(const double* step_obs, int ncell, int m0, double* I, cudaStream_t s);
 cudaError_t launch_f32_from_f64(const double* src, float* dst, size_t count, cudaStream_t s);
-// rho[c][p] = sum_k w_k rho32[c][k][p] in FP64 (fixed order)
-cudaError_t launch_fold_density(const float* rho32, int nk, int npts, const double* kw, double* rho,
+// rho[c][p] = sum_k w_k rho32[c][k][p] in FP64 (fixed order); wsplit[2k], wsplit[2k+1]: w_k as a
+// float pair, hi = (float)w_k and lo = (float)(w_k - hi)
+cudaError_t launch_fold_density(const float* rho32, int nk, int npts, const float* wsplit, double* rho,
                                 cudaStream_t s, int ncell = 1);
 
 }  // namespace tdks
