@@ -307,9 +307,12 @@ struct FftHooks {
 };
 
 // data: 3D array [dims2][dims1][dims0]; transform lines along one axis.  Line l starts at
-// (l % cnt_lo) * s_lo + (l / cnt_lo) * s_hi (the two other coordinates), elements estride apart.
+// (l % cnt_lo) * s_lo + (l / cnt_lo) * s_hi (the two other coordinates), elements estride apart; with
+// cnt_mid > 0 the second coordinate h = l / cnt_lo is split further, (h % cnt_mid) * s_hi +
+// (h / cnt_mid) * s_cell (the z lines of the x frequencies kx < xh of every cell of a batch).
 __global__ void __launch_bounds__(kFftThreads) k_fft_lines(double2* data, int n, int nlines, int LB,
                                                           long long cnt_lo, long long s_lo, long long s_hi,
+                                                          long long cnt_mid, long long s_cell,
                                                           long long estride, int xaxis,
                                                           const double2* __restrict__ tw_g,
                                                           FftPlanArgs plan, int dir, int m0, int m1, int m2,
@@ -322,9 +325,14 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_lines(double2* data, int n,
   const int nl = min(LB, nlines - l0);
   for (int t = threadIdx.x; t < n; t += blockDim.x) tw[t] = tw_g[t];
   const int tot = nl * n;
+  auto line_start = [&](long long l) -> long long {
+    const long long h = l / cnt_lo;
+    if (cnt_mid > 0) return (l % cnt_lo) * s_lo + (h % cnt_mid) * s_hi + (h / cnt_mid) * s_cell;
+    return (l % cnt_lo) * s_lo + h * s_hi;
+  };
   // grid coordinates (x, y, z within the box, cell) of element e of local line j
   auto coords3 = [&](int j, int e, int& x, int& y, int& z) {
-    const long long start = ((l0 + j) % cnt_lo) * s_lo + ((l0 + j) / cnt_lo) * s_hi + e * estride;
+    const long long start = line_start(l0 + j) + e * estride;
     x = (int)(start % m0);
     const long long r = start / m0;
     y = (int)(r % m1);
@@ -333,8 +341,7 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_lines(double2* data, int n,
   for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
     int j, e;
     if (xaxis) { j = idx / n; e = idx - j * n; } else { e = idx / nl; j = idx - e * nl; }
-    const long long l = l0 + j;
-    const long long start = (l % cnt_lo) * s_lo + (l / cnt_lo) * s_hi;
+    const long long start = line_start(l0 + j);
     if (hk.load_real) {
       int x, y, z;
       coords3(j, e, x, y, z);
@@ -362,8 +369,7 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_lines(double2* data, int n,
       const int j = idx / n, e = idx - j * n;
       double f;
       if (hk.ghat) {   // table of one box: offset of the element within its cell (sizes < 2^31)
-        const int l = l0 + j, clo = (int)cnt_lo;
-        const int off = (l % clo) * (int)s_lo + (l / clo) * (int)s_hi + e * (int)estride;
+        const int off = (int)(line_start(l0 + j) + e * estride);
         f = hk.ghat[off % cellsz];
         if (hk.spectral == 2) f *= hk.gscale;
       } else {
@@ -395,9 +401,7 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_lines(double2* data, int n,
         hk.vhxc[o] = v;
       }
     } else if (hk.store_lim <= 0 || e < hk.store_lim) {
-      const long long l = l0 + j;
-      const long long start = (l % cnt_lo) * s_lo + (l / cnt_lo) * s_hi;
-      data[start + e * estride] = src[j * n + e];
+      data[line_start(l0 + j) + e * estride] = src[j * n + e];
     }
   }
 }
@@ -954,7 +958,7 @@ cudaError_t launch_fft_axis(double2* data, const int dims[3], int axis, int dir,
   return launch_fft_axis_hooked(data, dims, axis, dir, tw, radices, nrad, s, batch, lim_lo, lim_hi, &hk);
 }
 
-// zx_lim > 0 (z axis, batch 1): only the z lines of x < zx_lim, every y.
+// zx_lim > 0 (z axis): only the z lines of x < zx_lim, every y (and every cell of a batch).
 cudaError_t launch_fft_axis_hooked(double2* data, const int dims[3], int axis, int dir, const double2* tw,
                                    const int* radices, int nrad, cudaStream_t s, int batch, int lim_lo,
                                    int lim_hi, const void* hooks, int zx_lim) {
@@ -965,11 +969,15 @@ cudaError_t launch_fft_axis_hooked(double2* data, const int dims[3], int axis, i
   plan.nrad = nrad;
   for (int i = 0; i < nrad; ++i) plan.rad[i] = radices[i];
   // the two other coordinates of a line: lo (faster) and hi; hi of the last axis runs over the batch
-  long long cnt_lo, cnt_hi, s_lo, s_hi, estride;
+  long long cnt_lo, cnt_hi, s_lo, s_hi, estride, cnt_mid = 0, s_cell = 0;
   const long long d01 = (long long)dims[0] * dims[1];
   if (axis == 0) { cnt_lo = dims[1]; cnt_hi = (long long)dims[2] * batch; s_lo = dims[0]; s_hi = d01; estride = 1; }
   else if (axis == 1) { cnt_lo = dims[0]; cnt_hi = (long long)dims[2] * batch; s_lo = 1; s_hi = d01; estride = dims[0]; }
   else if (zx_lim > 0 && batch == 1) { cnt_lo = zx_lim; cnt_hi = dims[1]; s_lo = 1; s_hi = dims[0]; estride = d01; }
+  else if (zx_lim > 0) {                 // x < zx_lim, every y, every cell
+    cnt_lo = zx_lim; cnt_hi = (long long)dims[1] * batch; s_lo = 1; s_hi = dims[0];
+    cnt_mid = dims[1]; s_cell = d01 * dims[2]; estride = d01;
+  }
   else { cnt_lo = d01; cnt_hi = batch; s_lo = 1; s_hi = d01 * dims[2]; estride = d01; }
   // pruned transforms: only the lines with lo < lim_lo and hi < lim_hi (a zero-padded input, or
   // an output of which only a corner is used)
@@ -986,7 +994,7 @@ cudaError_t launch_fft_axis_hooked(double2* data, const int dims[3], int axis, i
                                        (int)smem);
   if (e != cudaSuccess) return e;
   const int grid = (nlines + LB - 1) / LB;
-  k_fft_lines<<<grid, kFftThreads, smem, s>>>(data, n, nlines, LB, use_lo, s_lo, s_hi, estride,
+  k_fft_lines<<<grid, kFftThreads, smem, s>>>(data, n, nlines, LB, use_lo, s_lo, s_hi, cnt_mid, s_cell, estride,
                                               axis == 0 ? 1 : 0, tw, plan, dir, dims[0], dims[1], dims[2], hk);
   return cudaGetLastError();
 }
@@ -1122,8 +1130,8 @@ cudaError_t launch_hartree_xc_fused(double2* work, const int m[3], const int n[3
     for (int i = 0; i < nrad[0]; ++i) p0.rad[i] = rad[0][i];
     for (int i = 0; i < nrad[1]; ++i) p1.rad[i] = rad[1][i];
     const int grid = m[2] * batch;
-    // one system: the y and z passes only on the x frequencies kx <= m0/2 (see k_fft_planes)
-    const int xhp = batch == 1 ? m[0] / 2 + 1 : m[0];
+    // the y and z passes only on the x frequencies kx <= m0/2 (see k_fft_planes)
+    const int xhp = m[0] / 2 + 1;
     const bool split = plane_cl >= 2 && batch == 1 && ghat && nrad[2] <= kMaxRadices;
     if (split) {
       if ((e = launch_planes_cluster<true>(work, m, plane_cl, tw[0], tw[1], p0, p1, rho, 0, nullptr, s)) !=
@@ -1150,7 +1158,7 @@ cudaError_t launch_hartree_xc_fused(double2* work, const int m[3], const int n[3
       h3.inv_n = 1.0 / ((double)m[0] * m[1] * m[2]);
       h3.ghat = ghat;
       if ((e = launch_fft_axis_hooked(work, m, 2, -1, tw[2], rad[2], nrad[2], s, batch, 0, 0, &h3,
-                                      batch == 1 ? xhp : 0)) != cudaSuccess)
+                                      xhp)) != cudaSuccess)
         return e;
     }
     if (nlaunch) *nlaunch = 3;
@@ -1169,8 +1177,8 @@ cudaError_t launch_hartree_xc_fused(double2* work, const int m[3], const int n[3
   // The density is real and the Poisson factor (4 pi / G^2, or the spectrum of the even Green's
   // function) real and even, so every x line of the spectrum, after the y and z transforms in
   // either direction, satisfies X(m0 - k) = conj(X(k)): the y and z passes only transform the
-  // x frequencies k <= m0/2, and the inverse x pass rebuilds the rest (one system per launch).
-  const int xh = batch == 1 ? m[0] / 2 + 1 : 0;
+  // x frequencies k <= m0/2, and the inverse x pass rebuilds the rest.
+  const int xh = m[0] / 2 + 1;
   FftHooks h1 = base;
   h1.load_real = 1;
   h1.rsrc = rho;
