@@ -607,7 +607,7 @@ def threshold_sweep(s, psi0, params, t0, warmup, steps, flush, J64, dev,
 
 
 def summary(line):
-    """The figures the line is judged on, repeated in one short object at its end: the dominant
+    """The headline figures of the line, repeated in one short object at its end: the dominant
     kernel's roofline fraction, the cluster hpsi against the measured HBM bandwidth (whole call and
     stencil kernel alone), the predictor arms' steps/s and J errors, end to end and the CPU oracle."""
     def g(d, *keys):
