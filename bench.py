@@ -415,10 +415,12 @@ def gpu_arm(args, rank, world, local_rank):
     host_in = u2.cpu().pin_memory()
     state = ctx2.get_state()
     host_out = torch.empty_like(host_in).pin_memory()
-    # every step's observables go to one of two pinned host blocks (tdks_copy_step_observables) and
-    # are unpacked on the host after the next step is queued, so the stream never waits for the host
-    ring = [torch.zeros(T.STEP_OBS_DOUBLES, dtype=torch.float64).pin_memory() for _ in range(2)]
-    evs = [torch.cuda.Event() for _ in range(2)]
+    # every step's observables go to one of three pinned host blocks (tdks_copy_step_observables) and
+    # are unpacked on the host two steps later, so the stream never waits for the host (and a late
+    # wake-up of the host thread has two queued steps of slack)
+    LAG = 2
+    ring = [torch.zeros(T.STEP_OBS_DOUBLES, dtype=torch.float64).pin_memory() for _ in range(LAG + 1)]
+    evs = [torch.cuda.Event() for _ in range(LAG + 1)]
     cstream = ctx2.stream
     obs_read = []
     u2.zero_()
@@ -428,15 +430,16 @@ def gpu_arm(args, rank, world, local_rank):
     ctx2.set_state(state)
     for i in range(args.steps):
         ctx2.step(u2, tt, s.dt)
-        ctx2.copy_step_observables(ring[i % 2])
-        evs[i % 2].record(cstream)
-        if i > 0:
-            evs[(i - 1) % 2].synchronize()
-            obs_read.append(ctx2.unpack_step_observables(ring[(i - 1) % 2]))
+        ctx2.copy_step_observables(ring[i % (LAG + 1)])
+        evs[i % (LAG + 1)].record(cstream)
+        if i >= LAG:
+            evs[(i - LAG) % (LAG + 1)].synchronize()
+            obs_read.append(ctx2.unpack_step_observables(ring[(i - LAG) % (LAG + 1)]))
         tt += s.dt
     host_out.copy_(u2, non_blocking=True)
-    evs[(args.steps - 1) % 2].synchronize()
-    obs_read.append(ctx2.unpack_step_observables(ring[(args.steps - 1) % 2]))
+    for i in range(max(0, args.steps - LAG), args.steps):
+        evs[i % (LAG + 1)].synchronize()
+        obs_read.append(ctx2.unpack_step_observables(ring[i % (LAG + 1)]))
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - tic
     assert len(obs_read) == args.steps and all(np.isfinite(o["J"]).all() for o in obs_read)
@@ -447,7 +450,7 @@ def gpu_arm(args, rank, world, local_rank):
            "d2h_bytes_per_step": psi_bytes / args.steps + T.STEP_OBS_DOUBLES * 8,
            "note": "a run resumed from host memory: psi and the context state of a checkpoint uploaded, psi "
                    "downloaded once per K steps; J, dipole, misfit and fallback count of every step copied "
-                   "to pinned host memory and unpacked on the host one step later (the next step is queued "
+                   "to pinned host memory and unpacked on the host two steps later (the next steps are queued "
                    "first); context and step graphs set up by a warm-up run before the timed region"}
     ctx2.close()
 
