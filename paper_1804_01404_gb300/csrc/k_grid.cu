@@ -495,7 +495,9 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_planes_cluster(double2* dat
                                                                     const double* __restrict__ rho, int xc,
                                                                     double* __restrict__ vhxc, int rmax, int cmax,
                                                                     const double* __restrict__ vpred, double* partials,
-                                                                    unsigned* ticket, double* res) {
+                                                                    unsigned* ticket, double* res, int decide, double thr,
+                                                                    double* __restrict__ vnext, double* fb,
+                                                                    cudaGraphConditionalHandle handle) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
   const int m0 = N > 0 ? N : m0_, m1 = N > 0 ? N : m1_, xh = N > 0 ? N / 2 + 1 : xh_;
@@ -574,6 +576,7 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_planes_cluster(double2* dat
       const long long o = plane + (long long)y0 * m0 + i;
       const double v = xc > 0 ? src[i].x + vhxc[o] : src[i].x;
       vhxc[o] = v;
+      if (decide) vnext[o] = v;
       if (vpred) {
         const double d = v - vpred[o];
         acc[0] += d * d;
@@ -582,7 +585,15 @@ __global__ void __launch_bounds__(kFftThreads) k_fft_planes_cluster(double2* dat
     }
     if (vpred) {                                                 // the same for every CTA
       __shared__ double tot[2];
-      if (grid_sum<2>(acc, partials, ticket, tot) && threadIdx.x == 0) *res = sqrt(tot[0] / fmax(tot[1], 1e-300));
+      if (grid_sum<2>(acc, partials, ticket, tot) && threadIdx.x == 0) {
+        const double r = sqrt(tot[0] / fmax(tot[1], 1e-300));
+        *res = r;
+        if (decide) {                                            // as k_decide
+          const bool ok = (r <= thr) && (r == r) && (r < 1e300);
+          if (!ok) *fb += 1.0;
+          cudaGraphSetConditional(handle, ok ? 0u : 1u);
+        }
+      }
     }
   }
 }
@@ -1076,8 +1087,14 @@ cudaError_t launch_planes_cluster(double2* work, const int m[3], int cl, const d
   double* partials = ra ? ra->partials : nullptr;
   unsigned* ticket = ra ? ra->ticket : nullptr;
   double* res = ra ? ra->res : nullptr;
+  const int decide = ra ? ra->decide : 0;
+  const double thr = ra ? ra->thr : 0.0;
+  double* vnext = ra ? ra->vnext : nullptr;
+  double* fb = ra ? ra->fb : nullptr;
+  const cudaGraphConditionalHandle handle = ra ? ra->handle : cudaGraphConditionalHandle{};
   return launch_pdl(kern, dim3((unsigned)(m[2] * cl)), dim3((unsigned)threads), smem, s, cl, work, m[0], m[1], xh,
-                    tw0, tw1, p0, p1, rho, xc, vhxc, rmax, cmax, vpred, partials, ticket, res);
+                    tw0, tw1, p0, p1, rho, xc, vhxc, rmax, cmax, vpred, partials, ticket, res, decide, thr, vnext,
+                    fb, handle);
 }
 
 // z pass of one cell for the cluster plane path: LZ lines per CTA so that the CTAs about fill the SMs;
@@ -1162,6 +1179,7 @@ cudaError_t launch_hartree_xc_fused(double2* work, const int m[3], const int n[3
         return e;
     }
     if (nlaunch) *nlaunch = 3;
+    if (resid && resid->decide && !split) return cudaErrorInvalidValue;   // the caller expected the fused form
     if (split) {
       const bool with_res = resid && resid->vpred && m[2] * plane_cl <= 304;   // partials [304][2]
       e = launch_planes_cluster<false>(work, m, plane_cl, tw[0], tw[1], p0, p1, rho, xc, vhxc, s,

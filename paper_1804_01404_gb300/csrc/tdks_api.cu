@@ -128,6 +128,11 @@ struct tdks_ctx {
   double2* d_tw[3] = {nullptr, nullptr, nullptr};
   double* d_ghat = nullptr;
   ResidualArgs* res_args = nullptr;  // set around a predicted step's Hartree solve (see predicted_main)
+  // while a step graph is captured: its conditional handle, and whether the Hartree solve's last
+  // launch took the decision (then the graph has no k_decide and its V_Hxc went straight to d_vhxc)
+  bool cap_decide = false;
+  cudaGraphConditionalHandle cap_handle = 0;
+  bool cap_decided = false;
   int plane_cl = 0;               // cluster size of the Hartree xy-plane passes (0: one CTA per plane)
   // observables
   double* d_orb_obs = nullptr;   // [nk*norb*8]
@@ -1762,6 +1767,10 @@ static tdks_status fork_step_observables(tdks_ctx* c, bool at_start, bool zero_r
   return TDKS_OK;
 }
 
+// The history slot the next step reads as V0: an accepted step's decision writes V_Hxc(t+dt)
+// there, a fallback body copies it at its end.
+static double* next_hist_slot(tdks_ctx* c) { return c->d_vhist + (size_t)((c->hist_head + 1) % 4) * c->npts; }
+
 static tdks_status predicted_main(tdks_ctx* c, void* u, const double Amid[3], double dt, const double* Aobs,
                                   bool obs_start, bool obs_branch = false) {
   const size_t gb = c->npts * sizeof(double);
@@ -1799,12 +1808,18 @@ static tdks_status predicted_main(tdks_ctx* c, void* u, const double Amid[3], do
   TDKS_TRY(cs);
   if (obs_branch) TDKS_TRY(fork_step_observables(c, obs_start, defer));
   // the misfit: formed by the Hartree solve's last launch where it can (one periodic cell, xc
-  // without the TB-mBJ exchange, which is added after it), else by its own kernel
-  ResidualArgs ra{c->d_vpred, c->d_partials, c->d_ticket, c->d_resid, 0};
+  // without the TB-mBJ exchange, which is added after it), else by its own kernel.  In a step graph
+  // that launch also takes the accept decision: V_Hxc(t+dt) goes straight to d_vhxc and to the next
+  // history slot (a fallback body restores d_vhxc from the history first).
+  const bool fuse = c->opt.xc != 3 && c->opt.hartree && c->plane_cl >= 2;
+  const bool decide = obs_branch && c->cap_decide && fuse;
+  ResidualArgs ra{c->d_vpred, c->d_partials, c->d_ticket, c->d_resid, 0, decide ? 1 : 0, c->pred_thr,
+                  decide ? next_hist_slot(c) : nullptr, c->d_fb, c->cap_handle};
   c->res_args = c->opt.xc != 3 ? &ra : nullptr;
-  const tdks_status hs = hxc(c, c->d_rho, c->d_vnew, u);
+  const tdks_status hs = hxc(c, c->d_rho, decide ? c->d_vhxc : c->d_vnew, u);
   c->res_args = nullptr;
   TDKS_TRY(hs);
+  c->cap_decided = decide && ra.done;
   if (!ra.done) {
     TDKS_CUDA(launch_residual(c->d_vnew, c->d_vpred, c->npts, c->d_partials, c->d_ticket, c->d_resid, c->stream));
     c->launches += 1;
@@ -1812,9 +1827,7 @@ static tdks_status predicted_main(tdks_ctx* c, void* u, const double Amid[3], do
   return TDKS_OK;
 }
 
-// The history slot the next step reads as V0: an accepted step's decision kernel writes V_Hxc(t+dt)
-// there, a fallback body copies it at its end.
-static double* next_hist_slot(tdks_ctx* c) { return c->d_vhist + (size_t)((c->hist_head + 1) % 4) * c->npts; }
+
 
 // Add the step-graph timings of the last execution of slot v to the phase times.
 static tdks_status collect_graph(tdks_ctx* c, tdks_ctx::StepGraph& g) {
@@ -1873,18 +1886,25 @@ static tdks_status build_step_graph(tdks_ctx* c, void* u, double dt, const doubl
   tdks_status st = TDKS_OK;
   cudaError_t e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeRelaxed);
   if (e == cudaSuccess) {
-    st = predicted_main(c, u, zero, dt, Aobs, obs_start, true);   // the kernels read A' from the device pointers
-    if (st == TDKS_OK) e = cudaStreamWaitEvent(c->cap, c->ev_obs_join, 0);   // join J and the dipole
     cudaGraph_t cg = nullptr;
     const cudaGraphNode_t* deps = nullptr;
     size_t ndeps = 0;
     cudaStreamCaptureStatus cst;
-    cudaGraphConditionalHandle handle;
+    cudaGraphConditionalHandle handle = 0;
     cudaGraphNode_t cn = nullptr;
     cudaGraph_t body = nullptr;
-    if (st == TDKS_OK) e = cudaStreamGetCaptureInfo(c->cap, &cst, nullptr, &cg, nullptr, nullptr, nullptr);
-    if (st == TDKS_OK && e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&handle, cg, 0, cudaGraphCondAssignDefault);
-    if (st == TDKS_OK && e == cudaSuccess) {
+    // the conditional handle first: the Hartree solve's last launch may set it (see predicted_main)
+    e = cudaStreamGetCaptureInfo(c->cap, &cst, nullptr, &cg, nullptr, nullptr, nullptr);
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&handle, cg, 0, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess) {
+      c->cap_decide = true;
+      c->cap_handle = handle;
+      c->cap_decided = false;
+      st = predicted_main(c, u, zero, dt, Aobs, obs_start, true);   // the kernels read A' from the device pointers
+      c->cap_decide = false;
+    }
+    if (st == TDKS_OK && e == cudaSuccess) e = cudaStreamWaitEvent(c->cap, c->ev_obs_join, 0);   // join J and the dipole
+    if (st == TDKS_OK && e == cudaSuccess && !c->cap_decided) {
       Phase ph(c, 5);
       e = launch_decide(c->d_resid, c->pred_thr, c->d_vnew, c->d_vhxc, next_hist_slot(c), c->npts, c->d_fb, handle,
                         c->stream);
@@ -1913,7 +1933,11 @@ static tdks_status build_step_graph(tdks_ctx* c, void* u, double dt, const doubl
       std::memcpy(bc0, c->calls, sizeof(bc0));
       e = cudaStreamBeginCaptureToGraph(c->cap2, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
       if (e == cudaSuccess) {
-        e = cudaMemcpyAsync(u, c->d_backup, obytes, cudaMemcpyDeviceToDevice, c->stream);
+        // V_Hxc(t) back from the history (the predicted step may have written its own into d_vhxc),
+        // and the orbitals from the backup
+        e = cudaMemcpyAsync(c->d_vhxc, hist_slot(c, 0), c->npts * sizeof(double), cudaMemcpyDeviceToDevice,
+                            c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(u, c->d_backup, obytes, cudaMemcpyDeviceToDevice, c->stream);
         if (e == cudaSuccess) st = pc_step(c, u, zero, Aobs ? zero : nullptr, obs_start, dt);
         if (e == cudaSuccess && st == TDKS_OK) st = step_observables(c, obs_start, c->d_partials, c->d_ticket);
         if (e == cudaSuccess && st == TDKS_OK)

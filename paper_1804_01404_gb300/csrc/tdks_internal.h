@@ -250,13 +250,21 @@ cudaError_t launch_store6(double* dst, const double v[6], cudaStream_t s);
 // Grid kernels (k_grid.cu)
 // The misfit of a predicted potential, sqrt(sum (V - vpred)^2 / sum V^2) over the points of V (as
 // launch_residual forms it), when the Hartree solve can form it in its last launch: partials
-// [304][2] and ticket as for grid_sum; done is set to 1 when it did.
+// [304][2] and ticket as for grid_sum; done is set to 1 when it did.  With decide set (inside a
+// step graph) that launch also takes the decision k_decide takes: the potential goes to vnext as
+// well, and the last CTA counts a fallback in *fb and sets the graph's conditional `handle` to 1
+// when the misfit is above thr or not finite (0 otherwise).
 struct ResidualArgs {
   const double* vpred;
   double* partials;
   unsigned* ticket;
   double* res;
   int done;
+  int decide;
+  double thr;
+  double* vnext;
+  double* fb;
+  cudaGraphConditionalHandle handle;
 };
 // Hartree + exchange in five fused FFT line passes (three for periodic boxes whose xy-plane fits in
 // shared memory): vhxc = V_H[rho] (+ V_x[rho] if xc).  work: the transform box m^3 per cell (m = n
