@@ -533,7 +533,6 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_nn_predict(FusedArgs A) {
   float (&b1s)[16] = Ws.b1s;
   float (&b2s)[16] = Ws.b2s;
   uint2 (&Bf)[27][2][32] = Ws.Bf;
-  __shared__ double red[5][8];
   __shared__ double st[5];
   __shared__ int ok_s;
   const NNGrid& g = A.g;
@@ -567,18 +566,20 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_nn_predict(FusedArgs A) {
       const double d1 = v0 - v1, d2 = d1 - (v1 - v2), d3 = d2 - ((v1 - v2) - (v2 - v3));
       acc[0] += d1 * d1; acc[1] += d2 * d2; acc[2] += d3 * d3; acc[3] += v0; acc[4] += v0 * v0;
     }
+    // the CTA's sums: warp j takes value j of all threads (eight adds per lane, then a shuffle
+    // tree), 13 FP64 additions in a warp's chain instead of 25 shuffle steps plus 8 (one warp's FP64
+    // instructions do not overlap on this GPU)
+    __shared__ double rs[5][kFusedThreads];
 #pragma unroll
-    for (int j = 0; j < 5; ++j) {
-      double x = acc[j];
+    for (int j = 0; j < 5; ++j) rs[j][tid] = acc[j];
+    __syncthreads();
+    if (warp < 5) {
+      double x = 0;
+#pragma unroll
+      for (int i = 0; i < kFusedThreads / 32; ++i) x += rs[warp][lane + 32 * i];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-      if (lane == 0) red[j][warp] = x;
-    }
-    __syncthreads();
-    if (tid < 5) {
-      double x = 0;
-      for (int w = 0; w < kFusedThreads / 32; ++w) x += red[tid][w];
-      A.part[(size_t)blockIdx.x * 5 + tid] = x;
+      if (lane == 0) A.part[(size_t)blockIdx.x * 5 + warp] = x;
     }
   }
   if (!fused_barrier(A, 1, &ok_s)) return;
@@ -590,8 +591,12 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_nn_predict(FusedArgs A) {
       xs[j] = b < gridDim.x ? __ldcg(&A.part[(size_t)b * 5 + warp]) : 0.0;
     }
     double x = 0;
+    const int nb32 = (int)((gridDim.x + 31) >> 5);   // only the words that hold partials
 #pragma unroll
-    for (int j = 0; j <= kFusedMaxBlocks / 32; ++j) x += xs[j];
+    for (int j = 0; j <= kFusedMaxBlocks / 32; ++j) {
+      if (j >= nb32) break;
+      x += xs[j];
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
     if (lane == 0) st[warp] = x;
@@ -602,8 +607,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_nn_predict(FusedArgs A) {
   __shared__ double sc[9];
   if (tid < 4) {
     const double mean = st[3] * A.inv_n;
-    double s0, r0;
-    sqrt_and_rsqrt(st[4] * A.inv_n, s0, r0);                       // rms(V0)
+    // rms(V0) only sets the floor of the scales: FP32 is enough (and off the FP64 pipe)
+    const double s0 = (double)sqrtf((float)fmin(st[4] * A.inv_n, 1e30));
     const double fl = 1e-13 * s0 + 1e-300;
     const double a = (tid < 3) ? st[tid] * A.inv_n : fmax(st[4] * A.inv_n - mean * mean, 0.0);
     double sj = 0.0, rj = 0.0;
