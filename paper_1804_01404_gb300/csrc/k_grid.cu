@@ -4,7 +4,10 @@
 // FFT: batched 1D Stockham transforms in shared memory, one launch per axis, mixed radix
 // (4, 2, 3, 5, ...).  A CTA loads LB lines of the 3D array into shared memory -- for the y and z
 // axes the LB lines are consecutive in x, so every global access is coalesced -- runs all radix
-// stages there, and writes the lines back in natural order.
+// stages there, and writes the lines back in natural order.  Periodic boxes whose xy-plane fits in
+// shared memory take the x and y passes in one launch per direction (k_fft_planes: one CTA per
+// plane; for a single cell k_fft_planes_cluster splits each plane over a thread-block cluster and
+// transforms output by output, since its FP64 work would otherwise sit on a few SMs).
 #include <cstring>
 
 #include <cooperative_groups.h>
